@@ -1,0 +1,960 @@
+/*
+ * vpmc_oracle.c -- plain, slow, FP64 CPU oracle of the aperture-aware proton
+ * Monte Carlo hot path (Feng et al., "Modelling small block aperture in an
+ * in-house developed GPU-accelerated Monte Carlo-based dose engine", 2023).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load this library.  It shares no source,
+ * header, table generator or constant with the CUDA path under
+ * paper_2307_01416_gb300/csrc; both are written from the same statement of
+ * the method (paper Sec. 2.A-2.E plus the physics readings listed in the
+ * header comments below).
+ *
+ * What the method computes, in the paper's order:
+ *   Sec. 2.A  every history is created up front with one identical model
+ *             (virtual particles: no secondary spawning);
+ *   Sec. 2.B  histories cross an optional range shifter (homogeneous slab),
+ *             then a 30 mm brass aperture: inside the aperture slab the
+ *             crossing-number test decides at every step whether the particle
+ *             is in the opening (straight flight, unchanged velocity and
+ *             direction) or in brass (state updated from brass physics);
+ *   Sec. 2.C  energy is scored into a dose grid or into per-spot
+ *             influence-matrix columns;
+ *   Sec. 2.E  13 robust scenarios perturb the stopping-power ratio and the
+ *             isocentre.
+ * The physics of a condensed-history step (Bethe-Bloch tables, Highland
+ * scattering, Bohr straggling, 1.2 %/cm nuclear removal, 1 mm / 1 %-energy
+ * step rule) is the reading of the engine's physics that this project uses;
+ * every such reading is listed in the design doc.
+ *
+ * Functions without an independent pin say so in their comment
+ * ("parity unpinned").
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Physical constants (PDG).                                           */
+/* ------------------------------------------------------------------ */
+#define ORC_K_BETHE 0.307075     /* 4 pi N_A r_e^2 m_e c^2, MeV cm^2/mol */
+#define ORC_ME 0.51099895        /* electron rest energy, MeV            */
+#define ORC_MP 938.272           /* proton rest energy, MeV              */
+#define ORC_ECUT 0.5             /* transport cut-off, MeV               */
+#define ORC_MEV_PER_G_TO_GY 1.602176634e-10
+#define ORC_NE 2501              /* energy grid E_k = 0.1 k, k=0..2500   */
+#define ORC_NR 4096              /* uniform residual-range grid          */
+
+enum { ORC_WATER = 0, ORC_PMMA = 1, ORC_BRASS = 2, ORC_NMAT = 3 };
+
+/* Material data: Z/A, mean excitation energy (MeV), density (g/cc),
+ * radiation length (g/cm^2). */
+typedef struct { double za, I, rho, X0; } orc_material;
+static const orc_material ORC_MAT[ORC_NMAT] = {
+    {0.555087, 75.0e-6, 1.00, 36.08},   /* water                         */
+    {0.539369, 74.0e-6, 1.19, 40.55},   /* PMMA range shifter             */
+    {0.4573, 330.0e-6, 8.53, 12.9},     /* brass 63 % Cu / 37 % Zn         */
+};
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).                  */
+/* ------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 23-bit uniform in (0,1): ((x >> 9) + 1/2) * 2^-23, exactly representable
+ * in both FP32 and FP64. */
+double orc_uniform(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+/* Box-Muller: two independent standard normals from two uniforms. */
+void orc_box_muller(double u1, double u2, double z[2])
+{
+    double r = sqrt(-2.0 * log(u1));
+    double phi = 2.0 * M_PI * u2;
+    z[0] = r * cos(phi);
+    z[1] = r * sin(phi);
+}
+
+/* RNG stream of one history: key = (seed low word, spot id ^ seed high word);
+ * counter = (history, step, slot, 0). */
+typedef struct { uint32_t key[2]; uint32_t hist; } orc_stream;
+
+static void stream_block(const orc_stream* st, uint32_t step, uint32_t slot, double u[4])
+{
+    uint32_t ctr[4] = {st->hist, step, slot, 0u}, x[4];
+    orc_philox4x32_10(ctr, st->key, x);
+    for (int i = 0; i < 4; ++i) u[i] = orc_uniform(x[i]);
+}
+
+/* Four normals from one Philox block (two Box-Muller pairs). */
+static void stream_normals4(const orc_stream* st, uint32_t step, uint32_t slot, double z[4])
+{
+    double u[4];
+    stream_block(st, step, slot, u);
+    orc_box_muller(u[0], u[1], z);
+    orc_box_muller(u[2], u[3], z + 2);
+}
+
+/* ------------------------------------------------------------------ */
+/* Stopping power and range tables.                                    */
+/* ------------------------------------------------------------------ */
+/* Bethe-Bloch mass electronic stopping power, MeV cm^2/g, without shell or
+ * density-effect corrections, with the full T_max. */
+double orc_stopping_power(int mat, double T)
+{
+    const orc_material* m = &ORC_MAT[mat];
+    double gamma = 1.0 + T / ORC_MP;
+    double beta2 = 1.0 - 1.0 / (gamma * gamma);
+    double bg2 = beta2 * gamma * gamma;
+    double ratio = ORC_ME / ORC_MP;
+    double tmax = 2.0 * ORC_ME * bg2 / (1.0 + 2.0 * gamma * ratio + ratio * ratio);
+    double arg = 2.0 * ORC_ME * bg2 * tmax / (m->I * m->I);
+    return ORC_K_BETHE * m->za / beta2 * (0.5 * log(arg) - beta2);
+}
+
+typedef struct {
+    double R[ORC_NE];     /* R(E_k), mm * g/cc (areal range times 10)       */
+    double Einv[ORC_NR];  /* E at R_j = j * dR                              */
+    double dR;
+} orc_table;
+
+static orc_table g_tab[ORC_NMAT];
+static int g_tab_ready = 0;
+
+/* Integrand of the CSDA range in mm*g/cc per MeV. */
+static double range_integrand(int mat, double E) { return 10.0 / orc_stopping_power(mat, E); }
+
+/* Composite Simpson over [a, b] with n (even) sub-intervals. */
+static double simpson(int mat, double a, double b, int n)
+{
+    double h = (b - a) / n;
+    double s = range_integrand(mat, a) + range_integrand(mat, b);
+    for (int i = 1; i < n; ++i) s += (i & 1 ? 4.0 : 2.0) * range_integrand(mat, a + i * h);
+    return s * h / 3.0;
+}
+
+static void build_table(int mat, orc_table* t)
+{
+    /* R(E_k) = integral_{E_cut}^{E_k} dE / S(E), 0.001 MeV Simpson sub-grid. */
+    t->R[0] = 0.0;
+    for (int k = 1; k < ORC_NE; ++k) {
+        double lo = 0.1 * (k - 1), hi = 0.1 * k;
+        if (hi <= ORC_ECUT) { t->R[k] = 0.0; continue; }
+        if (lo < ORC_ECUT) lo = ORC_ECUT;
+        t->R[k] = t->R[k - 1] + simpson(mat, lo, hi, 100);
+    }
+    /* E(R) on a uniform R grid: inverse of the piecewise-linear R(E). */
+    double rmax = t->R[ORC_NE - 1];
+    t->dR = rmax / (ORC_NR - 1);
+    int k = 0;
+    for (int j = 0; j < ORC_NR; ++j) {
+        double r = j * t->dR;
+        if (j == ORC_NR - 1) { t->Einv[j] = 0.1 * (ORC_NE - 1); break; }
+        if (r <= 0.0) { t->Einv[j] = ORC_ECUT; continue; }
+        while (k + 1 < ORC_NE - 1 && t->R[k + 1] < r) ++k;
+        /* now R[k] < r <= R[k+1] (R[k] may be 0 below the cut) */
+        double f = (r - t->R[k]) / (t->R[k + 1] - t->R[k]);
+        double e0 = 0.1 * k;
+        if (e0 < ORC_ECUT) e0 = ORC_ECUT;   /* R is 0 up to the cut */
+        t->Einv[j] = e0 + f * (0.1 * (k + 1) - e0);
+    }
+}
+
+void orc_init_tables(void)
+{
+    if (g_tab_ready) return;
+    for (int m = 0; m < ORC_NMAT; ++m) build_table(m, &g_tab[m]);
+    g_tab_ready = 1;
+}
+
+double orc_table_R(int mat, int k) { orc_init_tables(); return g_tab[mat].R[k]; }
+double orc_table_Einv(int mat, int j) { orc_init_tables(); return g_tab[mat].Einv[j]; }
+double orc_table_dR(int mat) { orc_init_tables(); return g_tab[mat].dR; }
+
+/* Residual range R(E) by linear interpolation on the 0.1 MeV grid. */
+double orc_range(int mat, double E)
+{
+    const orc_table* t = &g_tab[mat];
+    if (E <= 0.0) return 0.0;
+    double x = E * 10.0;
+    int i = (int)floor(x);
+    if (i > ORC_NE - 2) i = ORC_NE - 2;
+    double f = x - i;
+    return t->R[i] + f * (t->R[i + 1] - t->R[i]);
+}
+
+/* Energy E(R) by linear interpolation on the uniform R grid. */
+double orc_energy(int mat, double R)
+{
+    const orc_table* t = &g_tab[mat];
+    if (R <= 0.0) return ORC_ECUT;
+    double x = R / t->dR;
+    int j = (int)floor(x);
+    if (j > ORC_NR - 2) j = ORC_NR - 2;
+    double f = x - j;
+    return t->Einv[j] + f * (t->Einv[j + 1] - t->Einv[j]);
+}
+
+/* Linear stopping-power ratio of PMMA to water at energy T. */
+double orc_spr_pmma(double T)
+{
+    return orc_stopping_power(ORC_PMMA, T) * ORC_MAT[ORC_PMMA].rho / orc_stopping_power(ORC_WATER, T);
+}
+
+/* ------------------------------------------------------------------ */
+/* HU -> (mass density, stopping-power ratio): 4-segment curve.        */
+/* ------------------------------------------------------------------ */
+typedef struct { double hu[5], rho[5], spr[5]; } orc_curve;
+
+void orc_hu_props(const orc_curve* c, double hu, double* rho, double* spr)
+{
+    double h = hu;
+    if (h < c->hu[0]) h = c->hu[0];
+    if (h > 3071.0) h = 3071.0;
+    int s = 0;
+    while (s < 3 && h >= c->hu[s + 1]) ++s;
+    double f = (h - c->hu[s]) / (c->hu[s + 1] - c->hu[s]);
+    *rho = c->rho[s] + f * (c->rho[s + 1] - c->rho[s]);
+    *spr = c->spr[s] + f * (c->spr[s + 1] - c->spr[s]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Aperture geometry: crossing-number test (paper Sec. 2.B, ref [67]). */
+/* ------------------------------------------------------------------ */
+/* poly: n vertices, xy interleaved, BEV mm.  Half-open edge rule. */
+int orc_point_in_polygon(const double* poly, int n, double x, double y)
+{
+    int inside = 0;
+    for (int i = 0, j = n - 1; i < n; j = i++) {
+        double xi = poly[2 * i], yi = poly[2 * i + 1];
+        double xj = poly[2 * j], yj = poly[2 * j + 1];
+        if ((yi > y) != (yj > y)) {
+            double xc = xi + (y - yi) * (xj - xi) / (yj - yi);
+            if (x < xc) inside = !inside;
+        }
+    }
+    return inside;
+}
+
+/* Smallest s > 0 at which (x, y) + s (dx, dy) crosses a polygon edge. */
+double orc_first_wall_hit(const double* poly, int n, double x, double y, double dx, double dy)
+{
+    double best = INFINITY;
+    for (int i = 0; i < n; ++i) {
+        int j = (i + 1) % n;
+        double ex = poly[2 * j] - poly[2 * i], ey = poly[2 * j + 1] - poly[2 * i + 1];
+        double den = dx * ey - dy * ex;
+        if (den == 0.0) continue;
+        double wx = poly[2 * i] - x, wy = poly[2 * i + 1] - y;
+        double s = (wx * ey - wy * ex) / den;
+        double lam = (wx * dy - wy * dx) / den;
+        if (s > 0.0 && lam >= 0.0 && lam <= 1.0 && s < best) best = s;
+    }
+    return best;
+}
+
+
+/* ------------------------------------------------------------------ */
+/* Problem description (the oracle's own structs).                     */
+/* ------------------------------------------------------------------ */
+typedef struct { int nx, ny, nz; double dx, dy, dz, ox, oy, oz; } orc_grid;
+
+typedef struct {
+    double dir[3], bevx[3], iso[3];   /* beam axis w, BEV x axis u, isocentre */
+    double source_to_iso;             /* source plane at t = -source_to_iso   */
+    int rs_present;
+    double rs_wet, rs_radius, rs_down_to_iso;
+    int ap_present;
+    double ap_thickness, ap_down_to_iso;
+    int poly_offset, nvert;           /* vertices in the shared xy array      */
+} orc_beam;
+
+typedef struct {
+    int beam;
+    int spot_key;           /* spot id in the RNG key                        */
+    double energy, x, y, sigma, div_mrad;
+    int64_t h_begin, n_hist;
+    double weight;
+} orc_spot;
+
+typedef struct { double shift[3]; double spr_scale; } orc_scen;
+
+typedef struct {
+    uint64_t seed;
+    int mcs, straggling, nuclear;
+    int frac_bits;
+} orc_opts;
+
+typedef struct {
+    const orc_grid* ct;
+    const int16_t* hu;
+    const orc_curve* curve;
+    const orc_grid* sg;     /* scoring grid, same extent as ct */
+    const orc_beam* beams;
+    const double* poly_xy;
+} orc_problem;
+
+enum { FATE_STOP = 0, FATE_NUC = 1, FATE_LEAK = 2, FATE_RS = 3, FATE_AP = 4, FATE_ERR = 5 };
+
+typedef struct {
+    int32_t fate;
+    int32_t steps;      /* condensed-history steps of the history            */
+    double e_dep;       /* energy scored in the patient grid, MeV            */
+    double e_end;       /* kinetic energy when the history left, MeV         */
+    double pos[3];      /* end position, patient coordinates, mm             */
+    int64_t q_dep;      /* sum of the history's fixed-point grid deposits    */
+} orc_record;
+
+/* Tallies: 0 energy in, 1 scored in grid, 2 leaked, 3 range shifter,
+ * 4 aperture, 5 nuclear (included in 1, 3, 4), 6 histories, 7 steps,
+ * 8 histories stopped by the iteration cap. */
+#define ORC_NTALLY 9
+
+/* ------------------------------------------------------------------ */
+/* One condensed-history step (range shifter, brass and patient alike). */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int table;      /* range/energy table                              */
+    double kappa;   /* table units (mm*g/cc) consumed per mm of path   */
+    double rho;     /* mass density, g/cc                              */
+    double za;      /* Z/A for straggling                              */
+    double X0;      /* radiation length, g/cm^2                        */
+} orc_medium;
+
+typedef struct {
+    double p[3], d[3];
+    double E, nlam;
+    double R;           /* residual range in the current medium's table units */
+    uint32_t step;
+} orc_particle;
+
+enum { LIM_NONE = 0, LIM_GEOM = 1, LIM_NUC = 2 };
+
+typedef struct {
+    double s;           /* step length, mm                      */
+    double dE;          /* deposited energy, MeV                */
+    int limiter;
+    int killed;         /* 1 stopped at the cut-off, 2 nuclear   */
+    double disp[3];     /* lateral displacement from scattering  */
+} orc_step;
+
+/* Duff et al. 2017, "Building an orthonormal basis, revisited". */
+static void orthonormal_basis(const double n[3], double b1[3], double b2[3])
+{
+    double sign = copysign(1.0, n[2]);
+    double a = -1.0 / (sign + n[2]);
+    double b = n[0] * n[1] * a;
+    b1[0] = 1.0 + sign * n[0] * n[0] * a; b1[1] = sign * b; b1[2] = -sign * n[0];
+    b2[0] = b; b2[1] = sign + n[1] * n[1] * a; b2[2] = -n[1];
+}
+
+/* Highland width (PDG form) for a step of s mm in medium med at energy T. */
+double orc_highland(double T, double s_mm, double rho, double X0)
+{
+    double x = s_mm * rho / (X0 * 10.0);
+    if (x < 1e-6) return 0.0;
+    double bcp = T * (T + 2.0 * ORC_MP) / (T + ORC_MP);
+    return 13.6 / bcp * sqrt(x) * (1.0 + 0.038 * log(x));
+}
+
+/* Bohr straggling variance (MeV^2) for s mm at energy T. */
+double orc_bohr_var(double T, double s_mm, double rho, double za)
+{
+    double gamma = 1.0 + T / ORC_MP;
+    double beta2 = 1.0 - 1.0 / (gamma * gamma);
+    return 0.1569 * rho * za * (s_mm * 0.1) * (1.0 - 0.5 * beta2) / (1.0 - beta2);
+}
+
+static void ch_step(const orc_medium* med, orc_particle* pt, double s_geom,
+                    const orc_opts* op, const orc_stream* st, orc_step* out)
+{
+    double E = pt->E;
+    /* step rule: min(1 mm, 1 % energy loss, geometry, nuclear point).  The
+     * residual range R0 is carried with the particle inside one medium so
+     * that the CSDA range is conserved exactly by the table lookups. */
+    double R0 = pt->R;
+    double s1 = (R0 - orc_range(med->table, 0.99 * E)) / med->kappa;
+    if (!(s1 > 0.0)) s1 = R0 / med->kappa;
+    double mu = op->nuclear ? 0.0012 * med->rho : 0.0;
+    double s = 1.0;
+    int lim = LIM_NONE;
+    if (s1 < s) s = s1;
+    if (s_geom < s) { s = s_geom; lim = LIM_GEOM; }
+    if (mu > 0.0) {
+        double snuc = pt->nlam / mu;
+        if (snuc < s) { s = snuc; lim = LIM_NUC; }
+    }
+    pt->step += 1;
+    if (lim == LIM_NUC) pt->nlam = 0.0; else pt->nlam -= mu * s;
+
+    /* mean energy loss from the range table (CSDA) */
+    double R1 = R0 - s * med->kappa;
+    double Emean = R1 > 0.0 ? orc_energy(med->table, R1) : ORC_ECUT;
+    double dE = E - Emean;
+    if (op->straggling) {
+        double z[4];
+        stream_normals4(st, pt->step, 2u, z);
+        dE += sqrt(orc_bohr_var(E, s, med->rho, med->za)) * z[0];
+    }
+    if (dE < 0.0) dE = 0.0;
+    if (dE > E) dE = E;
+    double Enew = E - dE;
+    /* carried range: R1, corrected by the range equivalent of the straggling */
+    double Rnew = R1;
+    if (op->straggling) {
+        Rnew = R1 + (orc_range(med->table, Enew) - orc_range(med->table, Emean));
+        if (!(Rnew > 0.0)) Rnew = orc_range(med->table, Enew);
+    }
+    pt->R = Rnew;
+
+    out->s = s;
+    out->limiter = lim;
+    out->disp[0] = out->disp[1] = out->disp[2] = 0.0;
+    out->killed = 0;
+    if (lim == LIM_NUC) out->killed = 2;
+    else if (Enew <= ORC_ECUT) out->killed = 1;
+    if (out->killed) { out->dE = E; pt->E = 0.0; }
+    else { out->dE = dE; pt->E = Enew; }
+
+    /* advance along the direction at the start of the step */
+    for (int k = 0; k < 3; ++k) pt->p[k] += s * pt->d[k];
+
+    if (op->mcs && !out->killed) {
+        double theta0 = orc_highland(E, s, med->rho, med->X0);
+        double z[4];
+        stream_normals4(st, pt->step, 1u, z);
+        /* two projected planes, each a correlated (angle, offset) pair */
+        double th1 = z[1] * theta0, th2 = z[3] * theta0;
+        double dx1 = s * theta0 * (z[0] / sqrt(12.0) + 0.5 * z[1]);
+        double dx2 = s * theta0 * (z[2] / sqrt(12.0) + 0.5 * z[3]);
+        double e1[3], e2[3];
+        orthonormal_basis(pt->d, e1, e2);
+        for (int k = 0; k < 3; ++k) out->disp[k] = dx1 * e1[k] + dx2 * e2[k];
+        double th = sqrt(th1 * th1 + th2 * th2);
+        double c = cos(th), sc = th > 0.0 ? sin(th) / th : 1.0;
+        double nd[3], nn = 0.0;
+        for (int k = 0; k < 3; ++k) { nd[k] = c * pt->d[k] + sc * (th1 * e1[k] + th2 * e2[k]); nn += nd[k] * nd[k]; }
+        nn = sqrt(nn);
+        for (int k = 0; k < 3; ++k) pt->d[k] = nd[k] / nn;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* One history (paper Sec. 2.A, 2.B, 2.E).                             */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const orc_problem* pb;
+    const orc_scen* sc;
+    const orc_opts* op;
+    int mode;               /* 0 dose grid (weighted), 1 per-spot columns */
+    int64_t* q;             /* deposit target                             */
+    int64_t nvox;
+} orc_run_ctx;
+
+#define ORC_MAX_ITER 1000000
+
+static void beam_axes(const orc_beam* bm, double u[3], double v[3], double w[3])
+{
+    for (int k = 0; k < 3; ++k) { w[k] = bm->dir[k]; u[k] = bm->bevx[k]; }
+    v[0] = w[1] * u[2] - w[2] * u[1];
+    v[1] = w[2] * u[0] - w[0] * u[2];
+    v[2] = w[0] * u[1] - w[1] * u[0];
+}
+
+static void bev_to_patient(const orc_beam* bm, const orc_scen* sc, const double pb[3], double out[3])
+{
+    double u[3], v[3], w[3];
+    beam_axes(bm, u, v, w);
+    for (int k = 0; k < 3; ++k) out[k] = bm->iso[k] + sc->shift[k] + pb[0] * u[k] + pb[1] * v[k] + pb[2] * w[k];
+}
+
+static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_index, int64_t h,
+                              orc_record* rec, double* tl)
+{
+    const orc_problem* pb = rc->pb;
+    const orc_beam* bm = &pb->beams[sp->beam];
+    const orc_opts* op = rc->op;
+    const double fscale = ldexp(1.0, op->frac_bits);
+    orc_stream st;
+    st.key[0] = (uint32_t)op->seed;
+    st.key[1] = (uint32_t)(op->seed >> 32) ^ (uint32_t)sp->spot_key;
+    st.hist = (uint32_t)h;
+
+    orc_particle pt;
+    memset(&pt, 0, sizeof pt);
+    memset(rec, 0, sizeof *rec);
+    rec->fate = FATE_ERR;
+
+    /* source (slot 0, step 0): (x, y) at the isocentre plane and two
+     * projected angles; slot 3 gives the nuclear mean-free-path count. */
+    double z[4];
+    stream_normals4(&st, 0u, 0u, z);
+    double a0 = sp->x + sp->sigma * z[0];
+    double b0 = sp->y + sp->sigma * z[1];
+    double tha = sp->div_mrad * 1e-3 * z[2];
+    double thb = sp->div_mrad * 1e-3 * z[3];
+    double nrm = sqrt(1.0 + tha * tha + thb * thb);
+    double tsrc = -bm->source_to_iso;
+    /* BEV coordinates (a, b, t): t along the beam, origin at isocentre */
+    pt.d[0] = tha / nrm; pt.d[1] = thb / nrm; pt.d[2] = 1.0 / nrm;
+    pt.p[0] = a0 + tsrc * tha; pt.p[1] = b0 + tsrc * thb; pt.p[2] = tsrc;
+    pt.E = sp->energy;
+    if (op->nuclear) {
+        double u[4];
+        stream_block(&st, 0u, 3u, u);
+        pt.nlam = -log(u[0]);
+    } else {
+        pt.nlam = INFINITY;
+    }
+    tl[0] += pt.E;
+    tl[6] += 1.0;
+
+    long iter = 0;
+    int in_patient = 0;
+    double P[3] = {0, 0, 0};
+    orc_step so;
+
+    /* ---- range shifter: homogeneous slab of finite radius ---- */
+    if (bm->rs_present) {
+        double thick = bm->rs_wet / orc_spr_pmma(150.0);
+        double tdn = -bm->rs_down_to_iso, tup = tdn - thick;
+        double sdr = (tup - pt.p[2]) / pt.d[2];
+        for (int k = 0; k < 3; ++k) pt.p[k] += sdr * pt.d[k];
+        orc_medium med = {ORC_PMMA, ORC_MAT[ORC_PMMA].rho, ORC_MAT[ORC_PMMA].rho, ORC_MAT[ORC_PMMA].za, ORC_MAT[ORC_PMMA].X0};
+        pt.R = orc_range(ORC_PMMA, pt.E);
+        for (;;) {
+            if (++iter > ORC_MAX_ITER) goto fail;
+            double r2 = pt.p[0] * pt.p[0] + pt.p[1] * pt.p[1];
+            if (r2 > bm->rs_radius * bm->rs_radius) {
+                /* outside the shifter: straight flight to its exit plane */
+                if (pt.d[2] <= 0.0) goto leak;
+                double sf = (tdn - pt.p[2]) / pt.d[2];
+                for (int k = 0; k < 3; ++k) pt.p[k] += sf * pt.d[k];
+                break;
+            }
+            double sg = INFINITY;
+            int down = 1;
+            if (pt.d[2] > 0.0) sg = (tdn - pt.p[2]) / pt.d[2];
+            else if (pt.d[2] < 0.0) { sg = (tup - pt.p[2]) / pt.d[2]; down = 0; }
+            ch_step(&med, &pt, sg, op, &st, &so);
+            tl[3] += so.dE;
+            tl[7] += 1.0;
+            rec->steps += 1;
+            if (so.killed) {
+                if (so.killed == 2) tl[5] += so.dE;
+                rec->fate = FATE_RS;
+                goto done;
+            }
+            for (int k = 0; k < 3; ++k) pt.p[k] += so.disp[k];
+            if (so.limiter == LIM_GEOM) {
+                if (!down) goto leak;
+                break;
+            }
+        }
+    }
+
+    /* ---- aperture block (paper Sec. 2.B) ---- */
+    if (bm->ap_present) {
+        const double* poly = pb->poly_xy + 2 * (int64_t)bm->poly_offset;
+        double tdn = -bm->ap_down_to_iso, tup = tdn - bm->ap_thickness;
+        if (pt.d[2] <= 0.0) goto leak;
+        double sdr = (tup - pt.p[2]) / pt.d[2];
+        for (int k = 0; k < 3; ++k) pt.p[k] += sdr * pt.d[k];
+        orc_medium med = {ORC_BRASS, ORC_MAT[ORC_BRASS].rho, ORC_MAT[ORC_BRASS].rho, ORC_MAT[ORC_BRASS].za, ORC_MAT[ORC_BRASS].X0};
+        int forced_brass = 0;
+        pt.R = orc_range(ORC_BRASS, pt.E);
+        for (;;) {
+            if (++iter > ORC_MAX_ITER) goto fail;
+            double sg = INFINITY;
+            int down = 1;
+            if (pt.d[2] > 0.0) sg = (tdn - pt.p[2]) / pt.d[2];
+            else if (pt.d[2] < 0.0) { sg = (tup - pt.p[2]) / pt.d[2]; down = 0; }
+            int in_open = !forced_brass && orc_point_in_polygon(poly, bm->nvert, pt.p[0], pt.p[1]);
+            if (in_open) {
+                /* opening: keep velocity and direction up to a wall or the exit */
+                double sw = orc_first_wall_hit(poly, bm->nvert, pt.p[0], pt.p[1], pt.d[0], pt.d[1]);
+                if (sw < sg) {
+                    for (int k = 0; k < 3; ++k) pt.p[k] += sw * pt.d[k];
+                    forced_brass = 1;
+                    continue;
+                }
+                if (!isfinite(sg)) goto fail;
+                for (int k = 0; k < 3; ++k) pt.p[k] += sg * pt.d[k];
+                if (!down) goto leak;
+                break;
+            }
+            /* brass: condensed-history step with brass physics */
+            forced_brass = 0;
+            ch_step(&med, &pt, sg, op, &st, &so);
+            tl[4] += so.dE;
+            tl[7] += 1.0;
+            rec->steps += 1;
+            if (so.killed) {
+                if (so.killed == 2) tl[5] += so.dE;
+                rec->fate = FATE_AP;
+                goto done;
+            }
+            for (int k = 0; k < 3; ++k) pt.p[k] += so.disp[k];
+            if (so.limiter == LIM_GEOM) {
+                if (!down) goto leak;
+                break;
+            }
+        }
+    }
+
+    /* ---- patient / phantom grid ---- */
+    {
+        const orc_grid* g = pb->ct;
+        const orc_grid* sgd = pb->sg;
+        double u[3], v[3], w[3], D[3];
+        beam_axes(bm, u, v, w);
+        for (int k = 0; k < 3; ++k) {
+            P[k] = bm->iso[k] + rc->sc->shift[k] + pt.p[0] * u[k] + pt.p[1] * v[k] + pt.p[2] * w[k];
+            D[k] = pt.d[0] * u[k] + pt.d[1] * v[k] + pt.d[2] * w[k];
+        }
+        in_patient = 1;
+        const double lo[3] = {g->ox, g->oy, g->oz};
+        const int n[3] = {g->nx, g->ny, g->nz};
+        const double dl[3] = {g->dx, g->dy, g->dz};
+        const int ns[3] = {sgd->nx, sgd->ny, sgd->nz};
+        const double dls[3] = {sgd->dx, sgd->dy, sgd->dz};
+        double hi[3];
+        for (int k = 0; k < 3; ++k) hi[k] = lo[k] + n[k] * dl[k];
+        /* ray / box entry */
+        double tmin = -INFINITY, tmax = INFINITY;
+        for (int k = 0; k < 3; ++k) {
+            if (D[k] != 0.0) {
+                double t1 = (lo[k] - P[k]) / D[k], t2 = (hi[k] - P[k]) / D[k];
+                if (t1 > t2) { double tt = t1; t1 = t2; t2 = tt; }
+                if (t1 > tmin) tmin = t1;
+                if (t2 < tmax) tmax = t2;
+            } else if (P[k] < lo[k] || P[k] > hi[k]) {
+                tmax = -INFINITY;
+            }
+        }
+        double tin = tmin > 0.0 ? tmin : 0.0;
+        if (!(tmax > tin)) goto leak;
+        for (int k = 0; k < 3; ++k) P[k] += tin * D[k];
+        int ic[3], is[3];
+        for (int k = 0; k < 3; ++k) {
+            int a = (int)floor((P[k] - lo[k]) / dl[k]);
+            ic[k] = a < 0 ? 0 : (a > n[k] - 1 ? n[k] - 1 : a);
+            int b = (int)floor((P[k] - lo[k]) / dls[k]);
+            is[k] = b < 0 ? 0 : (b > ns[k] - 1 ? ns[k] - 1 : b);
+        }
+        pt.R = orc_range(ORC_WATER, pt.E);
+        for (;;) {
+            if (++iter > ORC_MAX_ITER) goto fail;
+            int64_t cidx = ic[0] + (int64_t)n[0] * (ic[1] + (int64_t)n[1] * ic[2]);
+            double rho, spr;
+            orc_hu_props(pb->curve, (double)pb->hu[cidx], &rho, &spr);
+            orc_medium med = {ORC_WATER, spr * rc->sc->spr_scale, rho, ORC_MAT[ORC_WATER].za, ORC_MAT[ORC_WATER].X0};
+            /* distance to the next voxel boundary of either grid */
+            double dc[3], ds[3], svox = INFINITY;
+            for (int k = 0; k < 3; ++k) {
+                dc[k] = ds[k] = INFINITY;
+                if (D[k] > 0.0) {
+                    dc[k] = (lo[k] + (ic[k] + 1) * dl[k] - P[k]) / D[k];
+                    ds[k] = (lo[k] + (is[k] + 1) * dls[k] - P[k]) / D[k];
+                } else if (D[k] < 0.0) {
+                    dc[k] = (lo[k] + ic[k] * dl[k] - P[k]) / D[k];
+                    ds[k] = (lo[k] + is[k] * dls[k] - P[k]) / D[k];
+                }
+                if (dc[k] < 0.0) dc[k] = 0.0;
+                if (ds[k] < 0.0) ds[k] = 0.0;
+                if (dc[k] < svox) svox = dc[k];
+                if (ds[k] < svox) svox = ds[k];
+            }
+            int64_t sidx = is[0] + (int64_t)ns[0] * (is[1] + (int64_t)ns[1] * is[2]);
+            for (int k = 0; k < 3; ++k) { pt.p[k] = P[k]; pt.d[k] = D[k]; }
+            ch_step(&med, &pt, svox, op, &st, &so);
+            tl[7] += 1.0;
+            rec->steps += 1;
+            /* score the step's deposit in the voxel where the step starts */
+            {
+                int64_t q = (int64_t)nearbyint(so.dE * (rc->mode == 0 ? sp->weight : 1.0) * fscale);
+                int64_t* dst = rc->mode == 0 ? &rc->q[sidx] : &rc->q[(int64_t)spot_index * rc->nvox + sidx];
+#pragma omp atomic
+                *dst += q;
+                rec->e_dep += so.dE;
+                rec->q_dep += (int64_t)nearbyint(so.dE * fscale);
+                tl[1] += so.dE;
+            }
+            if (so.killed) {
+                if (so.killed == 2) tl[5] += so.dE;
+                rec->fate = so.killed == 2 ? FATE_NUC : FATE_STOP;
+                for (int k = 0; k < 3; ++k) P[k] = pt.p[k];
+                goto done;
+            }
+            if (so.limiter == LIM_GEOM) {
+                int out = 0;
+                for (int k = 0; k < 3; ++k) {
+                    int sgn = D[k] > 0.0 ? 1 : -1;
+                    if (D[k] != 0.0 && dc[k] == svox) ic[k] += sgn;
+                    if (D[k] != 0.0 && ds[k] == svox) is[k] += sgn;
+                    if (ic[k] < 0 || ic[k] >= n[k] || is[k] < 0 || is[k] >= ns[k]) out = 1;
+                }
+                if (out) { for (int k = 0; k < 3; ++k) P[k] = pt.p[k]; goto leak; }
+            }
+            /* lateral displacement, confined to the current voxel of both grids */
+            for (int k = 0; k < 3; ++k) {
+                double vlo = lo[k] + ic[k] * dl[k], vhi = lo[k] + (ic[k] + 1) * dl[k];
+                double slo = lo[k] + is[k] * dls[k], shi = lo[k] + (is[k] + 1) * dls[k];
+                if (slo > vlo) vlo = slo;
+                if (shi < vhi) vhi = shi;
+                double x = pt.p[k] + so.disp[k];
+                P[k] = x < vlo ? vlo : (x > vhi ? vhi : x);
+                D[k] = pt.d[k];
+            }
+        }
+    }
+
+leak:
+    rec->fate = FATE_LEAK;
+    rec->e_end = pt.E;
+    tl[2] += pt.E;
+    goto finish;
+fail:
+    rec->fate = FATE_ERR;
+    rec->e_end = pt.E;
+    tl[2] += pt.E;
+    tl[8] += 1.0;
+    goto finish;
+done:
+finish:
+    if (in_patient) { for (int k = 0; k < 3; ++k) rec->pos[k] = P[k]; }
+    else bev_to_patient(bm, rc->sc, pt.p, rec->pos);
+}
+
+/* ------------------------------------------------------------------ */
+/* Driver: all histories of all given spots for one scenario.          */
+/* ------------------------------------------------------------------ */
+/* mode 0: q is one grid of the scoring grid's size, deposits weighted by
+ *         the spot weight;  mode 1: q holds n_spots unweighted columns.
+ * tally: ORC_NTALLY doubles (added to).  rec: optional per-history records
+ * in spot order, history order; only the first rec_cap are written. */
+int orc_run(const orc_grid* ct, const int16_t* hu, const orc_curve* curve, const orc_grid* sg,
+            const orc_beam* beams, const double* poly_xy,
+            const orc_spot* spots, int n_spots, const orc_scen* sc, const orc_opts* op,
+            int mode, int64_t* q, double* tally, orc_record* rec, int64_t rec_cap, int nthreads)
+{
+    orc_init_tables();
+    orc_problem pb = {ct, hu, curve, sg, beams, poly_xy};
+    orc_run_ctx rc = {&pb, sc, op, mode, q, (int64_t)sg->nx * sg->ny * sg->nz};
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (n_spots + 1));
+    if (!off) return -1;
+    off[0] = 0;
+    for (int i = 0; i < n_spots; ++i) off[i + 1] = off[i] + spots[i].n_hist;
+    int64_t total = off[n_spots];
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        double tl[ORC_NTALLY] = {0};
+        orc_record tmp;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t gi = 0; gi < total; ++gi) {
+            int lo = 0, hi = n_spots;           /* find spot: off[lo] <= gi < off[lo+1] */
+            while (hi - lo > 1) { int mid = (lo + hi) / 2; if (off[mid] <= gi) lo = mid; else hi = mid; }
+            const orc_spot* sp = &spots[lo];
+            int64_t h = sp->h_begin + (gi - off[lo]);
+            orc_record* r = (rec && gi < rec_cap) ? &rec[gi] : &tmp;
+            transport_history(&rc, sp, lo, h, r, tl);
+        }
+#pragma omp critical
+        for (int i = 0; i < ORC_NTALLY; ++i) tally[i] += tl[i];
+    }
+    free(off);
+    return 0;
+}
+
+/* Number of threads the oracle's parallel loop uses. */
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Scoring-voxel density and dose (dose to medium).                    */
+/* ------------------------------------------------------------------ */
+/* Volume-weighted mean density of the CT voxels overlapping each scoring
+ * voxel (both grids share their origin and extent). */
+void orc_scoring_density(const orc_grid* ct, const int16_t* hu, const orc_curve* curve,
+                         const orc_grid* sg, double* rho_out)
+{
+    const int n[3] = {ct->nx, ct->ny, ct->nz};
+    const double dl[3] = {ct->dx, ct->dy, ct->dz};
+    const int ns[3] = {sg->nx, sg->ny, sg->nz};
+    const double dls[3] = {sg->dx, sg->dy, sg->dz};
+    for (int K = 0; K < ns[2]; ++K)
+        for (int J = 0; J < ns[1]; ++J)
+            for (int I = 0; I < ns[0]; ++I) {
+                int S[3] = {I, J, K};
+                int c0[3], c1[3];
+                for (int k = 0; k < 3; ++k) {
+                    double a = S[k] * dls[k], b = (S[k] + 1) * dls[k];
+                    c0[k] = (int)floor(a / dl[k]);
+                    c1[k] = (int)ceil(b / dl[k]);
+                    if (c0[k] < 0) c0[k] = 0;
+                    if (c1[k] > n[k]) c1[k] = n[k];
+                }
+                double acc = 0.0, vol = 0.0;
+                for (int z = c0[2]; z < c1[2]; ++z)
+                    for (int y = c0[1]; y < c1[1]; ++y)
+                        for (int x = c0[0]; x < c1[0]; ++x) {
+                            int C[3] = {x, y, z};
+                            double ov = 1.0;
+                            for (int k = 0; k < 3; ++k) {
+                                double a = S[k] * dls[k], b = (S[k] + 1) * dls[k];
+                                double c = C[k] * dl[k], d = (C[k] + 1) * dl[k];
+                                double l = (b < d ? b : d) - (a > c ? a : c);
+                                ov *= l > 0.0 ? l : 0.0;
+                            }
+                            if (ov <= 0.0) continue;
+                            double rho, spr;
+                            orc_hu_props(curve, (double)hu[x + (int64_t)n[0] * (y + (int64_t)n[1] * z)], &rho, &spr);
+                            acc += ov * rho;
+                            vol += ov;
+                        }
+                rho_out[I + (int64_t)ns[0] * (J + (int64_t)ns[1] * K)] = acc / vol;
+            }
+}
+
+/* Dose (Gy) from fixed-point energy sums: q * 2^-F MeV / (rho * V). */
+void orc_dose_from_q(const int64_t* q, int64_t nvox, const double* rho, double voxel_mm3,
+                     int frac_bits, double* dose)
+{
+    double scale = ldexp(1.0, -frac_bits) * ORC_MEV_PER_G_TO_GY / (voxel_mm3 * 1e-3);
+    for (int64_t i = 0; i < nvox; ++i) dose[i] = (double)q[i] * scale / rho[i];
+}
+
+/* ------------------------------------------------------------------ */
+/* Global 3D gamma pass rate (paper Sec. 2.D, ref [80]).              */
+/* ------------------------------------------------------------------ */
+static double trilinear(const double* g, int nx, int ny, int nz, double fx, double fy, double fz, int* ok)
+{
+    if (fx < 0.0 || fy < 0.0 || fz < 0.0 || fx > nx - 1 || fy > ny - 1 || fz > nz - 1) { *ok = 0; return 0.0; }
+    int x0 = (int)floor(fx), y0 = (int)floor(fy), z0 = (int)floor(fz);
+    if (x0 > nx - 2) x0 = nx - 2 < 0 ? 0 : nx - 2;
+    if (y0 > ny - 2) y0 = ny - 2 < 0 ? 0 : ny - 2;
+    if (z0 > nz - 2) z0 = nz - 2 < 0 ? 0 : nz - 2;
+    double ax = fx - x0, ay = fy - y0, az = fz - z0;
+    int x1 = x0 + 1 < nx ? x0 + 1 : x0, y1 = y0 + 1 < ny ? y0 + 1 : y0, z1 = z0 + 1 < nz ? z0 + 1 : z0;
+#define G(x, y, z) g[(x) + (int64_t)nx * ((y) + (int64_t)ny * (z))]
+    double c00 = G(x0, y0, z0) * (1 - ax) + G(x1, y0, z0) * ax;
+    double c10 = G(x0, y1, z0) * (1 - ax) + G(x1, y1, z0) * ax;
+    double c01 = G(x0, y0, z1) * (1 - ax) + G(x1, y0, z1) * ax;
+    double c11 = G(x0, y1, z1) * (1 - ax) + G(x1, y1, z1) * ax;
+#undef G
+    *ok = 1;
+    double c0 = c00 * (1 - ay) + c10 * ay, c1 = c01 * (1 - ay) + c11 * ay;
+    return c0 * (1 - az) + c1 * az;
+}
+
+/* Pass rate (%) of eval against ref: dose criterion dd_frac of the ref
+ * maximum, distance dta_mm, evaluated on ref voxels >= thr_frac of the ref
+ * maximum.  The eval dose is interpolated on a sub-grid of spacing 1/subdiv
+ * voxel; since gamma <= 1 needs |r| <= dta, the search stops at dta. */
+double orc_gamma_pass_rate(const double* ref, const double* eval, int nx, int ny, int nz,
+                           double dx, double dy, double dz, double dd_frac, double dta_mm,
+                           double thr_frac, int subdiv, int64_t* n_evaluated)
+{
+    int64_t nv = (int64_t)nx * ny * nz;
+    double dmax = 0.0;
+    for (int64_t i = 0; i < nv; ++i) if (ref[i] > dmax) dmax = ref[i];
+    double dd = dd_frac * dmax, thr = thr_frac * dmax;
+    int rx = (int)ceil(dta_mm / dx * subdiv), ry = (int)ceil(dta_mm / dy * subdiv), rz = (int)ceil(dta_mm / dz * subdiv);
+    /* offsets within the DTA sphere, sorted by distance */
+    int64_t cap = (int64_t)(2 * rx + 1) * (2 * ry + 1) * (2 * rz + 1);
+    double* off = (double*)malloc(sizeof(double) * 4 * cap);
+    int64_t m = 0;
+    for (int k = -rz; k <= rz; ++k)
+        for (int j = -ry; j <= ry; ++j)
+            for (int i = -rx; i <= rx; ++i) {
+                double ox = i * dx / subdiv, oy = j * dy / subdiv, oz = k * dz / subdiv;
+                double r2 = ox * ox + oy * oy + oz * oz;
+                if (r2 > dta_mm * dta_mm) continue;
+                off[4 * m] = r2; off[4 * m + 1] = (double)i / subdiv; off[4 * m + 2] = (double)j / subdiv; off[4 * m + 3] = (double)k / subdiv;
+                ++m;
+            }
+    /* insertion sort by r2 (small m) */
+    for (int64_t a = 1; a < m; ++a) {
+        double t[4] = {off[4 * a], off[4 * a + 1], off[4 * a + 2], off[4 * a + 3]};
+        int64_t b = a - 1;
+        while (b >= 0 && off[4 * b] > t[0]) { memcpy(&off[4 * (b + 1)], &off[4 * b], 4 * sizeof(double)); --b; }
+        memcpy(&off[4 * (b + 1)], t, 4 * sizeof(double));
+    }
+    int64_t npass = 0, neval = 0;
+#pragma omp parallel for reduction(+ : npass, neval) schedule(dynamic, 256)
+    for (int64_t idx = 0; idx < nv; ++idx) {
+        if (ref[idx] < thr || ref[idx] <= 0.0) continue;
+        int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((int64_t)nx * ny));
+        ++neval;
+        for (int64_t o = 0; o < m; ++o) {
+            int ok;
+            double de = trilinear(eval, nx, ny, nz, x + off[4 * o + 1], y + off[4 * o + 2], z + off[4 * o + 3], &ok);
+            if (!ok) continue;
+            double g2 = off[4 * o] / (dta_mm * dta_mm) + (de - ref[idx]) * (de - ref[idx]) / (dd * dd);
+            if (g2 <= 1.0) { ++npass; break; }
+        }
+    }
+    free(off);
+    if (n_evaluated) *n_evaluated = neval;
+    return neval ? 100.0 * (double)npass / (double)neval : 100.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* One condensed-history step from a fresh state, for unit tests.      */
+/* ------------------------------------------------------------------ */
+/* The particle starts at the origin moving along +z with energy E and the
+ * medium's full residual range.  out[0..10] = s, dE, limiter, killed, E',
+ * d'[3], disp[3]. */
+void orc_step_sample(int table, double kappa, double rho, double za, double X0,
+                     double E, double s_geom, int mcs, int straggling, int nuclear, double nlam,
+                     uint64_t seed, int spot_key, uint32_t hist, uint32_t step, double* out)
+{
+    orc_init_tables();
+    orc_medium med = {table, kappa, rho, za, X0};
+    orc_opts op = {seed, mcs, straggling, nuclear, 24};
+    orc_stream st;
+    st.key[0] = (uint32_t)seed;
+    st.key[1] = (uint32_t)(seed >> 32) ^ (uint32_t)spot_key;
+    st.hist = hist;
+    orc_particle pt;
+    memset(&pt, 0, sizeof pt);
+    pt.d[2] = 1.0;
+    pt.E = E;
+    pt.nlam = nlam;
+    pt.R = orc_range(table, E);
+    pt.step = step;
+    orc_step so;
+    ch_step(&med, &pt, s_geom, &op, &st, &so);
+    out[0] = so.s; out[1] = so.dE; out[2] = so.limiter; out[3] = so.killed; out[4] = pt.E;
+    for (int k = 0; k < 3; ++k) { out[5 + k] = pt.d[k]; out[8 + k] = so.disp[k]; }
+}

@@ -1,0 +1,376 @@
+"""Seeded synthetic inputs for the aperture-aware proton Monte Carlo engine.
+
+This module builds geometry, spot lists and robust scenarios with the shapes of
+the paper's workloads (water phantoms with brass apertures, Sec. 2.D.2; brain
+SRS plans with small targets, Sec. 2.D.3 and Table 1; 13 robust scenarios,
+Sec. 2.E). It generates inputs only: it contains none of the transport
+arithmetic. The CUDA path and the CPU oracle both take these inputs.
+
+Coordinates are millimetres, energies MeV. A grid's HU array is int16 with x
+fastest, i.e. numpy shape (nz, ny, nx).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# Public spot record (one row per pencil-beam spot).
+SPOT_DTYPE = np.dtype(
+    [
+        ("beam", np.int32),
+        ("energy", np.float64),      # MeV, mono-energetic (Sec. 2.D.2)
+        ("x", np.float64),           # BEV position at the isocentre plane, mm
+        ("y", np.float64),
+        ("sigma", np.float64),       # in-air spot sigma at the isocentre plane, mm
+        ("div_mrad", np.float64),    # angular spread (per projected plane), mrad
+        ("n_hist", np.int64),
+        ("weight", np.float64),      # dose weight per history (dose path only)
+    ]
+)
+
+
+@dataclasses.dataclass
+class Grid:
+    shape: Tuple[int, int, int]            # (nx, ny, nz)
+    spacing: Tuple[float, float, float]    # (dx, dy, dz), mm
+    origin: Tuple[float, float, float]     # corner of voxel (0, 0, 0), mm
+
+    @property
+    def nvox(self) -> int:
+        return int(self.shape[0] * self.shape[1] * self.shape[2])
+
+    @property
+    def voxel_mm3(self) -> float:
+        return float(self.spacing[0] * self.spacing[1] * self.spacing[2])
+
+    def centers(self, axis: int) -> np.ndarray:
+        return self.origin[axis] + (np.arange(self.shape[axis]) + 0.5) * self.spacing[axis]
+
+
+@dataclasses.dataclass
+class HUCurve:
+    """Four-segment piecewise-linear HU -> (mass density, SPR) curve."""
+    hu: Tuple[float, ...] = (-1000.0, -100.0, 0.0, 200.0, 1600.0)
+    density: Tuple[float, ...] = (0.0012, 0.93, 1.00, 1.10, 1.90)
+    spr: Tuple[float, ...] = (0.001, 0.93, 1.00, 1.09, 1.80)
+
+
+@dataclasses.dataclass
+class Beam:
+    """One treatment field. The beam axis is `direction`; `bev_x` is the first
+    beam's-eye-view axis (perpendicular to it); the second is direction x bev_x.
+    Devices are placed by the distance of their downstream face to the
+    isocentre (Sec. 2.B: aperture 150 mm, range shifter 190 mm)."""
+    direction: Tuple[float, float, float]
+    bev_x: Tuple[float, float, float]
+    iso: Tuple[float, float, float]
+    source_to_iso: float
+    rs_present: bool = False
+    rs_wet: float = 45.0
+    rs_radius: float = 30.5
+    rs_down_to_iso: float = 190.0
+    ap_present: bool = False
+    ap_thickness: float = 30.0
+    ap_down_to_iso: float = 150.0
+    polygon: Optional[np.ndarray] = None   # (n, 2) BEV mm, opening contour
+
+
+@dataclasses.dataclass
+class Scenario:
+    shift: Tuple[float, float, float] = (0.0, 0.0, 0.0)   # isocentre shift, mm
+    spr_scale: float = 1.0
+
+
+@dataclasses.dataclass
+class Options:
+    seed: int = 1234
+    mcs: bool = True
+    straggling: bool = True
+    nuclear: bool = True
+    frac_bits: int = 24
+
+    @property
+    def deterministic(self) -> bool:
+        return not self.mcs and not self.straggling
+
+
+@dataclasses.dataclass
+class Problem:
+    ct: Grid
+    hu: np.ndarray          # int16, shape (nz, ny, nx)
+    curve: HUCurve
+    scoring: Grid           # same origin and extent as ct
+    beams: List[Beam]
+
+
+def make_spots(rows: Sequence[Tuple]) -> np.ndarray:
+    return np.array([tuple(r) for r in rows], dtype=SPOT_DTYPE)
+
+
+# --------------------------------------------------------------------------
+# Helpers that shape the inputs (no transport physics).
+# --------------------------------------------------------------------------
+def regular_polygon(radius: float, n: int, center=(0.0, 0.0), phase: float = 0.0) -> np.ndarray:
+    """Regular n-gon inscribed in a circle (the circular openings of Sec. 2.D.2)."""
+    t = phase + 2.0 * np.pi * np.arange(n) / n
+    return np.stack([center[0] + radius * np.cos(t), center[1] + radius * np.sin(t)], axis=1)
+
+
+def square_polygon(half_width: float) -> np.ndarray:
+    a = float(half_width)
+    return np.array([[-a, -a], [a, -a], [a, a], [-a, a]], dtype=np.float64)
+
+
+def spot_sigma_mm(energy_mev) -> np.ndarray:
+    """In-air spot sigma, linear from 5 mm at 71.3 MeV to 2 mm at 228.8 MeV (Sec. 1)."""
+    e = np.asarray(energy_mev, dtype=np.float64)
+    return 5.0 + (e - 71.3) * (2.0 - 5.0) / (228.8 - 71.3)
+
+
+# Bragg-Kleeman rule R = alpha E^p (water), used only to place energy layers
+# at a chosen water-equivalent spacing.  It is an input recipe, not the
+# engine's range-energy relation.
+_BK_ALPHA_MM = 0.022
+_BK_P = 1.77
+
+
+def bk_energy_for_range(r_mm) -> np.ndarray:
+    return (np.asarray(r_mm, dtype=np.float64) / _BK_ALPHA_MM) ** (1.0 / _BK_P)
+
+
+def bk_range_for_energy(e_mev) -> np.ndarray:
+    return _BK_ALPHA_MM * np.asarray(e_mev, dtype=np.float64) ** _BK_P
+
+
+def layer_energies(e_first: float, e_last: float, wet_step_mm: float = 3.0) -> np.ndarray:
+    """Energies whose water ranges are spaced wet_step_mm apart, from e_first up
+    to at most e_last."""
+    r0 = bk_range_for_energy(e_first)
+    r1 = bk_range_for_energy(e_last)
+    n = int(math.floor((r1 - r0) / wet_step_mm + 1e-9)) + 1
+    return bk_energy_for_range(r0 + wet_step_mm * np.arange(n))
+
+
+def grid_spots_in_disk(radius: float, spacing: float) -> np.ndarray:
+    m = int(math.ceil(radius / spacing))
+    g = spacing * np.arange(-m, m + 1)
+    xx, yy = np.meshgrid(g, g, indexing="xy")
+    keep = np.hypot(xx, yy) <= radius + 1e-9
+    return np.stack([xx[keep], yy[keep]], axis=1)
+
+
+def split_histories(total: int, n: int) -> np.ndarray:
+    """Split `total` histories over n spots evenly, remainder to the lowest ids."""
+    base = np.full(n, total // n, dtype=np.int64)
+    base[: total % n] += 1
+    return base
+
+
+def robust_scenarios(shift_mm: float = 3.0, range_frac: float = 0.035) -> List[Scenario]:
+    """13 scenarios (Sec. 2.E): nominal; +/- shift along x, y, z; and for each
+    axis and sign, the shift combined with SPR scaled by (1 +/- range_frac)."""
+    out = [Scenario()]
+    for ax in range(3):
+        for sgn in (1.0, -1.0):
+            s = [0.0, 0.0, 0.0]
+            s[ax] = sgn * shift_mm
+            out.append(Scenario(tuple(s), 1.0))
+    for ax in range(3):
+        for sgn in (1.0, -1.0):
+            s = [0.0, 0.0, 0.0]
+            s[ax] = sgn * shift_mm
+            out.append(Scenario(tuple(s), 1.0 + sgn * range_frac))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Water phantoms.
+# --------------------------------------------------------------------------
+def water_phantom(shape, spacing, origin) -> Tuple[Grid, np.ndarray]:
+    g = Grid(tuple(int(v) for v in shape), tuple(float(v) for v in spacing), tuple(float(v) for v in origin))
+    hu = np.zeros((g.shape[2], g.shape[1], g.shape[0]), dtype=np.int16)
+    return g, hu
+
+
+def pencil_beam_water(n_hist: int = 100_000, energy: float = 100.0, sigma: float = 4.0,
+                      div_mrad: float = 2.0, shape=(50, 50, 150), spacing=(2.0, 2.0, 2.0)):
+    """Water phantom 10x10x30 cm at 2 mm, one pencil beam along +z entering at
+    the surface z = 0 (source plane on the surface)."""
+    ext = [shape[i] * spacing[i] for i in range(3)]
+    g, hu = water_phantom(shape, spacing, (-ext[0] / 2, -ext[1] / 2, 0.0))
+    beam = Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0), source_to_iso=0.0)
+    pb = Problem(ct=g, hu=hu, curve=HUCurve(), scoring=g, beams=[beam])
+    spots = make_spots([(0, energy, 0.0, 0.0, sigma, div_mrad, n_hist, 1.0)])
+    return pb, spots
+
+
+def water_aperture_case(opening_diameter_mm: float, range_shifter: bool, hist_per_layer: int = 1_000_000,
+                        e_first: float = 100.0, e_last: float = 160.0, n_vertices: int = 256,
+                        shape=(100, 100, 150), spacing=(2.0, 2.0, 2.0), max_layers: Optional[int] = None):
+    """Water phantom 20x20x30 cm at 2 mm; 30 mm brass aperture whose downstream
+    face is 100 mm upstream of the surface; circular opening (regular n-gon);
+    optional 45 mm-WET range shifter 10 mm upstream of the aperture.  Spots on a
+    3 mm square grid covering the opening plus 1 cm; layers 3 mm WET apart."""
+    ext = [shape[i] * spacing[i] for i in range(3)]
+    g, hu = water_phantom(shape, spacing, (-ext[0] / 2, -ext[1] / 2, 0.0))
+    r_open = 0.5 * opening_diameter_mm
+    ap_down = 100.0
+    rs_down = ap_down + 30.0 + 10.0
+    src = (rs_down + 45.0 + 10.0) if range_shifter else (ap_down + 30.0 + 10.0)
+    beam = Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0), source_to_iso=src,
+                rs_present=range_shifter, rs_wet=45.0, rs_radius=30.5, rs_down_to_iso=rs_down,
+                ap_present=True, ap_thickness=30.0, ap_down_to_iso=ap_down,
+                polygon=regular_polygon(r_open, n_vertices))
+    pb = Problem(ct=g, hu=hu, curve=HUCurve(), scoring=g, beams=[beam])
+    energies = layer_energies(e_first, e_last, 3.0)
+    if max_layers is not None:
+        energies = energies[:max_layers]
+    xy = grid_spots_in_disk(r_open + 10.0, 3.0)
+    rows = []
+    for e in energies:
+        nh = split_histories(hist_per_layer, len(xy))
+        sig = float(spot_sigma_mm(e))
+        for (x, y), n in zip(xy, nh):
+            rows.append((0, float(e), float(x), float(y), sig, 2.0, int(n), 1.0))
+    return pb, make_spots(rows)
+
+
+WATER_APERTURE_CASES = [(d, rs) for rs in (False, True) for d in (10.0, 20.0, 30.0, 40.0)]
+
+
+# --------------------------------------------------------------------------
+# Synthetic heterogeneous head (brain SRS, Sec. 2.D.3).
+# --------------------------------------------------------------------------
+HEAD_SHAPE = (256, 256, 160)
+HEAD_SPACING = (1.0, 1.0, 1.5)
+HEAD_SEMI_AXES = (75.0, 95.0, 100.0)
+
+
+def head_ct(seed: int = 1234, shape=HEAD_SHAPE, spacing=HEAD_SPACING, semi_axes=HEAD_SEMI_AXES,
+            skull_mm: float = 6.0):
+    """Ellipsoidal head: brain HU ~ N(30, 10) inside a skull shell of HU
+    U(900, 1500), two air cavities (HU -1000) of radius U(10, 20) mm in the
+    anterior brain (the side the 0 deg beam enters), air outside."""
+    rng = np.random.default_rng(seed)
+    ext = [shape[i] * spacing[i] for i in range(3)]
+    g = Grid(tuple(shape), tuple(spacing), tuple(-e / 2 for e in ext))
+    x = g.centers(0)[None, None, :]
+    y = g.centers(1)[None, :, None]
+    z = g.centers(2)[:, None, None]
+    a, b, c = semi_axes
+    outer = (x / a) ** 2 + (y / b) ** 2 + (z / c) ** 2 <= 1.0
+    ai, bi, ci = a - skull_mm, b - skull_mm, c - skull_mm
+    inner = (x / ai) ** 2 + (y / bi) ** 2 + (z / ci) ** 2 <= 1.0
+    hu = np.full((shape[2], shape[1], shape[0]), -1000.0)
+    brain = rng.normal(30.0, 10.0, size=hu.shape)
+    skull = rng.uniform(900.0, 1500.0, size=hu.shape)
+    hu = np.where(outer, skull, hu)
+    hu = np.where(inner, brain, hu)
+    cavities = []
+    for _ in range(2):
+        r = rng.uniform(10.0, 20.0)
+        cx = rng.uniform(-35.0, 35.0)
+        cy = rng.uniform(-(bi - r - 5.0), -20.0)
+        cz = rng.uniform(-40.0, 40.0)
+        cavities.append((cx, cy, cz, r))
+        sph = (x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2 <= r * r
+        hu = np.where(sph & inner, -1000.0, hu)
+    hu = np.clip(np.rint(hu), -1024, 3071).astype(np.int16)
+    return g, hu, cavities
+
+
+def target_radius(volume_cc: float) -> float:
+    return (3.0 * volume_cc * 1000.0 / (4.0 * np.pi)) ** (1.0 / 3.0)
+
+
+def head_target(volume_cc: float, seed: int = 1235, semi_axes=HEAD_SEMI_AXES, skull_mm: float = 6.0):
+    """Spherical target at a depth U(20, 70) mm below the skin along the 0 deg
+    beam (+y), kept inside the brain."""
+    rng = np.random.default_rng(seed)
+    r = target_radius(volume_cc)
+    a, b, c = [s - skull_mm for s in semi_axes]
+    dx, dz = rng.uniform(-20.0, 20.0, size=2)
+    depth = rng.uniform(20.0, 70.0)
+    ya, yb, yc = semi_axes
+    y_skin = -yb * math.sqrt(max(0.0, 1.0 - (dx / ya) ** 2 - (dz / yc) ** 2))
+    cy = y_skin + depth
+    center = np.array([dx, cy, dz])
+    # pull toward the centre until the sphere sits inside the brain ellipsoid
+    for _ in range(200):
+        pts = center[None, :] + r * np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
+        if np.all((pts[:, 0] / a) ** 2 + (pts[:, 1] / b) ** 2 + (pts[:, 2] / c) ** 2 <= 1.0):
+            break
+        center *= 0.97
+    return center, r
+
+
+def gantry_beam(gantry_deg: float, iso, source_to_iso: float, **kw) -> Beam:
+    """Coplanar beam in the axial (x-y) plane: gantry 0 -> +y, 90 -> -x, 270 -> +x."""
+    t = math.radians(gantry_deg)
+    w = np.array([-math.sin(t), math.cos(t), 0.0])
+    w[np.abs(w) < 1e-15] = 0.0
+    u = np.cross(w, np.array([0.0, 0.0, 1.0]))
+    u /= np.linalg.norm(u)
+    return Beam(direction=tuple(w), bev_x=tuple(u), iso=tuple(float(v) for v in iso), source_to_iso=source_to_iso, **kw)
+
+
+def radiological_depths(g: Grid, hu: np.ndarray, curve: HUCurve, start, direction, length: float,
+                        step: float = 0.5):
+    """Ray sum of SPR along a line (nearest voxel, `step` mm) -- used only to
+    choose layer energies for the synthetic plans."""
+    s = np.arange(0.0, length, step) + 0.5 * step
+    pts = np.asarray(start)[None, :] + s[:, None] * np.asarray(direction)[None, :]
+    idx = np.floor((pts - np.asarray(g.origin)[None, :]) / np.asarray(g.spacing)[None, :]).astype(int)
+    ok = np.all((idx >= 0) & (idx < np.asarray(g.shape)[None, :]), axis=1)
+    h = np.full(len(s), -1000.0)
+    h[ok] = hu[idx[ok, 2], idx[ok, 1], idx[ok, 0]]
+    spr = np.interp(np.clip(h, curve.hu[0], 3071.0), curve.hu, curve.spr)
+    return s, np.cumsum(spr * step)
+
+
+def head_plan(volume_cc: float = 8.4, ct_seed: int = 1234, target_seed: int = 1235, gantries=(0.0, 90.0, 270.0),
+              range_shifter: bool = True, spot_spacing: float = 3.0, margin_mm: float = 5.0, n_vertices: int = 64,
+              hist_lo: int = 1000, hist_hi: int = 20000, hist_seed: int = 77, scoring_mm: float = 2.0):
+    """Three-field SRS plan on the synthetic head: apertures = target projection
+    + margin (regular n-gon), 45 mm WET range shifter, spots on a 3 mm grid over
+    the opening, layers 3 mm WET apart covering the target depth +/- 5 mm,
+    n_hist per spot log-uniform in [hist_lo, hist_hi]."""
+    g, hu, _ = head_ct(ct_seed)
+    center, r_t = head_target(volume_cc, target_seed)
+    ext = [g.shape[i] * g.spacing[i] for i in range(3)]
+    sshape = tuple(int(round(ext[i] / scoring_mm)) for i in range(3))
+    sg = Grid(sshape, (scoring_mm,) * 3, g.origin)
+    curve = HUCurve()
+    beams, rows = [], []
+    rng = np.random.default_rng(hist_seed)
+    for bi, gdeg in enumerate(gantries):
+        r_open = r_t + margin_mm
+        bm = gantry_beam(gdeg, center, source_to_iso=190.0 + 45.0 + 10.0 if range_shifter else 190.0,
+                         rs_present=range_shifter, rs_wet=45.0, rs_radius=30.5, rs_down_to_iso=190.0,
+                         ap_present=True, ap_thickness=30.0, ap_down_to_iso=150.0,
+                         polygon=regular_polygon(r_open, n_vertices))
+        beams.append(bm)
+        w = np.asarray(bm.direction)
+        start = center - 200.0 * w
+        s, wet = radiological_depths(g, hu, curve, start, w, 400.0)
+        d_near = 200.0 - r_t
+        d_far = 200.0 + r_t
+        wet_near = float(np.interp(d_near, s, wet))
+        wet_far = float(np.interp(d_far, s, wet))
+        rs = 45.0 if range_shifter else 0.0
+        e_lo = float(bk_energy_for_range(max(wet_near - 5.0 + rs, 1.0)))
+        e_hi = float(bk_energy_for_range(wet_far + 5.0 + rs))
+        e_lo = min(max(e_lo, 70.0), 230.0)
+        e_hi = min(max(e_hi, e_lo), 230.0)
+        energies = layer_energies(e_lo, e_hi, 3.0)
+        xy = grid_spots_in_disk(r_open + spot_spacing, spot_spacing)
+        for e in energies:
+            nh = np.exp(rng.uniform(np.log(hist_lo), np.log(hist_hi), size=len(xy))).astype(np.int64)
+            sig = float(spot_sigma_mm(e))
+            for (x, y), n in zip(xy, nh):
+                rows.append((bi, float(e), float(x), float(y), sig, 2.0, int(n), 1.0))
+    pb = Problem(ct=g, hu=hu, curve=curve, scoring=sg, beams=beams)
+    return pb, make_spots(rows), center, r_t

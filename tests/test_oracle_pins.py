@@ -1,0 +1,256 @@
+"""Pins of the FP64 CPU oracle against facts outside itself.
+
+Each test ties one oracle function to a published value, a closed form, an
+invariant or an independent brute-force computation, so that a plausible
+mistake (dropped term, wrong sign or index, transposed operand) fails here.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special, stats
+
+from oracle import oracle as O
+from paper_2307_01416_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------------- RNG
+def test_philox_known_answers():
+    """Philox4x32-10 against the Random123 known-answer vectors (Salmon et al. 2011)."""
+    for r in _read_golden("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_uniform_map_exact_and_open():
+    """u = ((x >> 9) + 1/2) 2^-23: inside (0,1), exactly representable in FP32."""
+    for x in (0, 1, 511, 512, 0x7FFFFFFF, 0xFFFFFFFF, 0x12345678):
+        u = O.uniform(x)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+        assert u == ((x >> 9) + 0.5) / 2.0 ** 23
+    assert O.uniform(0) == 2.0 ** -24
+    assert O.uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+
+
+def test_box_muller_normals_distribution():
+    """Normals from Philox + Box-Muller pass a KS test against N(0,1) and the
+    two members of a pair are uncorrelated."""
+    rng_keys = (1234, 7)
+    z = []
+    for h in range(40000):
+        x = O.philox4x32_10((h, 3, 1, 0), rng_keys)
+        u = [O.uniform(int(v)) for v in x]
+        z.extend(O.box_muller(u[0], u[1]))
+        z.extend(O.box_muller(u[2], u[3]))
+    z = np.array(z)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert abs(z.mean()) < 4.0 / math.sqrt(len(z))
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / len(z))
+    pairs = z.reshape(-1, 2)
+    assert abs(np.corrcoef(pairs[:, 0], pairs[:, 1])[0, 1]) < 4.0 / math.sqrt(len(pairs))
+
+
+# ----------------------------------------------------------------- tables
+def test_bethe_against_pstar():
+    """Water stopping power and CSDA range against NIST PSTAR (ICRU 49)."""
+    for r in _read_golden("pstar_water.txt"):
+        e, s_ref, r_ref, ts, tr = map(float, r)
+        s = O.stopping_power(O.WATER, e)
+        assert abs(s / s_ref - 1.0) < ts, (e, s, s_ref)
+        rng_gcm2 = O.csda_range(O.WATER, e) / 10.0
+        assert abs(rng_gcm2 / r_ref - 1.0) < tr, (e, rng_gcm2, r_ref)
+
+
+def test_brass_stops_below_about_155_mev():
+    """Sec. 2.B: 30 mm of brass stops protons up to about 155 MeV."""
+    rho = 8.53
+    assert O.csda_range(O.BRASS, 150.0) / rho < 30.0
+    assert O.csda_range(O.BRASS, 160.0) / rho > 30.0
+
+
+def test_range_table_against_adaptive_quadrature():
+    """R(E_k) of the Simpson table against scipy adaptive quadrature of 10/S."""
+    R = O.range_table(O.WATER)
+    assert np.all(R[:6] == 0.0) and np.all(np.diff(R[5:]) > 0)
+    for k in (6, 7, 10, 55, 200, 1000, 1500, 2500):
+        ref, _ = integrate.quad(lambda e: 10.0 / O.stopping_power(O.WATER, e), 0.5, 0.1 * k,
+                                epsabs=0, epsrel=1e-12, limit=400)
+        assert abs(R[k] / ref - 1.0) < 1e-7, (k, R[k], ref)
+    for mat in (O.PMMA, O.BRASS):
+        R = O.range_table(mat)
+        ref, _ = integrate.quad(lambda e: 10.0 / O.stopping_power(mat, e), 0.5, 150.0, epsrel=1e-12, limit=400)
+        assert abs(R[1500] / ref - 1.0) < 1e-7
+
+
+def test_energy_table_is_inverse_of_range_interpolant():
+    """E(R_j) on the uniform R grid inverts the piecewise-linear R(E)."""
+    for mat in (O.WATER, O.PMMA, O.BRASS):
+        R = O.range_table(mat)
+        Ek = 0.1 * np.arange(O.NE)
+        Einv = O.energy_table(mat)
+        dR = O.table_dR(mat)
+        Rj = dR * np.arange(O.NR)
+        # R(E) along the interpolant at the tabulated inverse energies
+        back = np.interp(Einv[1:-1], Ek[5:], R[5:])
+        assert np.allclose(back, Rj[1:-1], rtol=1e-12, atol=1e-12)
+        assert Einv[0] == 0.5 and abs(Einv[-1] - 250.0) < 1e-12
+        assert np.all(np.diff(Einv) > 0)
+
+
+def test_pmma_spr_is_plausible():
+    """PMMA stopping-power ratio near 1.16 (typical measured 1.15-1.17)."""
+    assert 1.14 < O.spr_pmma(150.0) < 1.18
+
+
+# ----------------------------------------------------------------- HU curve
+def test_hu_curve_is_piecewise_linear_through_knots():
+    c = W.HUCurve()
+    hus = np.linspace(-1000, 1600, 131)
+    for h in hus:
+        rho, spr = O.hu_props(c, h)
+        assert abs(rho - np.interp(h, c.hu, c.density)) < 1e-12
+        assert abs(spr - np.interp(h, c.hu, c.spr)) < 1e-12
+    # clamp below the first knot, linear extrapolation of the last segment above it
+    assert O.hu_props(c, -1024) == O.hu_props(c, -1000)
+    slope = (c.density[4] - c.density[3]) / (c.hu[4] - c.hu[3])
+    assert abs(O.hu_props(c, 3071)[0] - (c.density[4] + slope * (3071 - 1600))) < 1e-12
+    assert O.hu_props(c, 5000) == O.hu_props(c, 3071)
+
+
+# ----------------------------------------------------------------- aperture geometry
+def test_crossing_number_convex_matches_half_planes():
+    """Crossing number vs an independent half-plane test on convex polygons."""
+    rng = np.random.default_rng(3)
+    for n in (3, 4, 7, 64, 256):
+        poly = W.regular_polygon(12.0, n, phase=0.37)
+        pts = rng.uniform(-15, 15, size=(3000, 2))
+        ex = np.roll(poly, -1, axis=0) - poly
+        cross = ex[None, :, 0] * (pts[:, None, 1] - poly[None, :, 1]) - ex[None, :, 1] * (pts[:, None, 0] - poly[None, :, 0])
+        inside_ref = np.all(cross > 0, axis=1)
+        margin = np.min(np.abs(cross), axis=1) / np.linalg.norm(ex, axis=1).max()
+        for p, ref, m in zip(pts, inside_ref, margin):
+            if m > 1e-9:
+                assert O.point_in_polygon(poly, p[0], p[1]) == ref
+
+
+def test_crossing_number_nonconvex_matches_winding_number():
+    """Star (non-convex) polygon: crossing number vs the winding number from summed angles."""
+    t = 2 * np.pi * np.arange(10) / 10
+    r = np.where(np.arange(10) % 2 == 0, 15.0, 6.0)
+    poly = np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
+    rng = np.random.default_rng(4)
+    for p in rng.uniform(-16, 16, size=(3000, 2)):
+        v = poly - p[None, :]
+        ang = np.arctan2(v[:, 1], v[:, 0])
+        d = np.diff(np.concatenate([ang, ang[:1]]))
+        d = (d + np.pi) % (2 * np.pi) - np.pi
+        wn = int(round(d.sum() / (2 * np.pi)))
+        assert O.point_in_polygon(poly, p[0], p[1]) == (wn != 0)
+
+
+def test_first_wall_hit_square_closed_form():
+    sq = W.square_polygon(10.0)
+    rng = np.random.default_rng(5)
+    for _ in range(500):
+        x, y = rng.uniform(-9.9, 9.9, size=2)
+        phi = rng.uniform(0, 2 * np.pi)
+        dx, dy = math.cos(phi) * 0.3, math.sin(phi) * 0.3
+        cand = []
+        for (lim, c, dc) in ((10.0, x, dx), (-10.0, x, dx), (10.0, y, dy), (-10.0, y, dy)):
+            if dc != 0 and (lim - c) / dc > 0:
+                cand.append((lim - c) / dc)
+        assert abs(O.first_wall_hit(sq, x, y, dx, dy) - min(cand)) < 1e-9
+    assert O.first_wall_hit(sq, 1.0, 2.0, 0.0, 0.0) == float("inf")
+
+
+# ----------------------------------------------------------------- single-step physics
+def test_bohr_variance_constant_from_fundamental_constants():
+    """0.1569 MeV^2 cm^2/g = 4 pi N_A r_e^2 (m_e c^2)^2 (Bohr), and the
+    relativistic factor (1 - beta^2/2)/(1 - beta^2)."""
+    from scipy import constants as K
+    re_cm = K.physical_constants["classical electron radius"][0] * 100.0
+    mec2 = K.physical_constants["electron mass energy equivalent in MeV"][0]
+    const = 4 * math.pi * K.N_A * re_cm ** 2 * mec2 ** 2
+    assert abs(const / 0.1569 - 1.0) < 1e-3
+    mp = K.physical_constants["proton mass energy equivalent in MeV"][0]
+    for T in (10.0, 100.0, 200.0):
+        pc = math.sqrt(T * (T + 2 * mp))
+        b2 = (pc / (T + mp)) ** 2
+        ref = const * 1.0 * 0.555087 * 0.1 * (1 - b2 / 2) / (1 - b2)
+        assert abs(O.bohr_var(T, 1.0, 1.0, 0.555087) / ref - 1.0) < 2e-3
+
+
+def test_highland_against_momentum_form():
+    """Highland theta0 with beta c p built from p = sqrt(T^2 + 2 T M) and
+    beta = pc/E (an independent route to the same quantity)."""
+    mp = 938.272
+    for T, s, rho, X0 in ((100.0, 1.0, 1.0, 36.08), (150.0, 0.5, 8.53, 12.9), (60.0, 1.0, 1.19, 40.55)):
+        pc = math.sqrt(T * T + 2 * T * mp)
+        beta = pc / (T + mp)
+        x = s * 0.1 * rho / X0
+        ref = 13.6 / (beta * pc) * math.sqrt(x) * (1 + 0.038 * math.log(x))
+        assert abs(O.highland(T, s, rho, X0) / ref - 1.0) < 1e-12
+    assert O.highland(100.0, 1e-8, 1.0, 36.08) == 0.0
+
+
+def test_mcs_step_moments():
+    """One water step: projected-angle variance theta0^2, lateral variance
+    s^2 theta0^2 / 3, angle-offset correlation sqrt(3)/2 (PDG); both planes."""
+    T, s = 150.0, 1.0
+    th0 = O.highland(T, s, 1.0, 36.08)
+    n = 20000
+    ang, off = [], []
+    for h in range(n):
+        r = O.step_sample(O.WATER, 1.0, 1.0, 0.555087, 36.08, T, mcs=True, straggling=False, hist=h, step=5)
+        assert r["s"] == pytest.approx(s)
+        ang.append(r["d"][:2] / r["d"][2])
+        off.append(r["disp"][:2])
+    ang, off = np.array(ang), np.array(off)
+    for k in range(2):
+        va = ang[:, k].var()
+        vo = off[:, k].var()
+        assert abs(va / th0 ** 2 - 1.0) < 4 * math.sqrt(2.0 / n)
+        assert abs(vo / (s * s * th0 ** 2 / 3.0) - 1.0) < 4 * math.sqrt(2.0 / n)
+        assert abs(np.corrcoef(ang[:, k], off[:, k])[0, 1] - math.sqrt(3) / 2) < 0.02
+    assert abs(np.corrcoef(ang[:, 0], ang[:, 1])[0, 1]) < 4 / math.sqrt(n)
+
+
+def test_straggling_step_variance():
+    T, s = 100.0, 1.0
+    var = O.bohr_var(T, s, 1.0, 0.555087)
+    dE = np.array([O.step_sample(O.WATER, 1.0, 1.0, 0.555087, 36.08, T, mcs=False, straggling=True, hist=h)["dE"]
+                   for h in range(20000)])
+    mean = O.step_sample(O.WATER, 1.0, 1.0, 0.555087, 36.08, T, mcs=False, straggling=False)["dE"]
+    assert abs(dE.var() / var - 1.0) < 4 * math.sqrt(2.0 / len(dE))
+    assert abs(dE.mean() - mean) < 4 * math.sqrt(var / len(dE))
+    # CSDA mean loss = E - E(R(E) - s)
+    assert abs(mean - (T - O.energy_at_range(O.WATER, O.csda_range(O.WATER, T) - s))) < 1e-12
+
+
+def test_step_rule_limits():
+    """s = min(1 mm, 1 % energy step, geometry, nuclear point)."""
+    r = O.step_sample(O.WATER, 1.0, 1.0, 0.555087, 36.08, 200.0, mcs=False, straggling=False)
+    assert r["s"] == 1.0 and r["limiter"] == 0
+    r = O.step_sample(O.WATER, 1.0, 1.0, 0.555087, 36.08, 20.0, mcs=False, straggling=False)
+    s1 = O.csda_range(O.WATER, 20.0) - O.csda_range(O.WATER, 19.8)
+    assert abs(r["s"] - s1) < 1e-12 and r["s"] < 1.0
+    r = O.step_sample(O.WATER, 1.0, 1.0, 0.555087, 36.08, 200.0, s_geom=0.25, mcs=False, straggling=False)
+    assert r["s"] == 0.25 and r["limiter"] == 1
+    r = O.step_sample(O.WATER, 1.0, 1.0, 0.555087, 36.08, 200.0, mcs=False, straggling=False, nuclear=True,
+                      nlam=0.0006)
+    assert abs(r["s"] - 0.5) < 1e-12 and r["killed"] == 2 and r["dE"] == 200.0

@@ -1,0 +1,248 @@
+"""Transport-level pins of the FP64 oracle: closed forms, invariants and
+brute-force enumeration on tiny grids."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+from scipy.ndimage import map_coordinates
+
+from oracle import oracle as O
+from paper_2307_01416_gb300 import workloads as W
+
+DET = W.Options(seed=1234, mcs=False, straggling=False, nuclear=False)
+
+
+def _one_beam_problem(ct, hu, sg=None, beam=None):
+    beam = beam or W.Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0), source_to_iso=5.0)
+    return W.Problem(ct=ct, hu=hu, curve=W.HUCurve(), scoring=sg or ct, beams=[beam])
+
+
+def test_csda_end_point_every_history():
+    """Deterministic, nuclear off, no lateral spread: every history stops at
+    depth R(E0) (water) -- the range-table loss conserves the CSDA range."""
+    pb, spots = W.pencil_beam_water(n_hist=200, energy=120.0, sigma=0.0, div_mrad=0.0)
+    q, tl, rec = O.run(pb, O.oracle_spots(spots), W.Scenario(), DET, records=200)
+    assert np.all(rec["fate"] == O.FATE_STOP)
+    r0 = O.csda_range(O.WATER, 120.0)
+    assert np.max(np.abs(rec["pos"][:, 2] / r0 - 1.0)) < 1e-9
+    # with SPR scaling (range uncertainty scenario) the depth scales by 1/k
+    q, tl, rec = O.run(pb, O.oracle_spots(spots), W.Scenario(spr_scale=1.035), DET, records=200)
+    assert np.max(np.abs(rec["pos"][:, 2] * 1.035 / r0 - 1.0)) < 1e-9
+
+
+def _chords(p0, w, lo, spacing_list, shape_list, t_max=1e9):
+    """Brute force: break points where the ray crosses a boundary plane of any
+    of the grids, sorted; returns segment (t0, t1) list inside the box."""
+    hi = lo + np.asarray(shape_list[0]) * np.asarray(spacing_list[0])
+    ts = [0.0]
+    for sp, sh in zip(spacing_list, shape_list):
+        for k in range(3):
+            if w[k] == 0:
+                continue
+            for m in range(sh[k] + 1):
+                t = (lo[k] + m * sp[k] - p0[k]) / w[k]
+                if t > 0:
+                    ts.append(t)
+    ts = np.unique(np.array(ts))
+    segs = []
+    for a, b in zip(ts[:-1], ts[1:]):
+        mid = p0 + 0.5 * (a + b) * w
+        if np.all(mid > lo) and np.all(mid < hi) and b - a > 1e-12:
+            segs.append((a, b, mid))
+    return segs
+
+
+@pytest.mark.parametrize("two_grids", [False, True])
+@pytest.mark.parametrize("energy", [22.0, 90.0])
+def test_straight_track_brute_force(two_grids, energy):
+    """Per-voxel deposits of a straight track in a tiny mixed-HU grid equal
+    E(R_in) - E(R_out), R decreasing by chord x SPR, enumerated by hand."""
+    rng = np.random.default_rng(11)
+    if two_grids:
+        ct = W.Grid((6, 6, 8), (1.0, 1.0, 1.5), (-3.0, -3.0, 0.0))
+        sg = W.Grid((3, 3, 6), (2.0, 2.0, 2.0), (-3.0, -3.0, 0.0))
+    else:
+        ct = W.Grid((3, 3, 4), (2.0, 2.0, 2.0), (-3.0, -3.0, 0.0))
+        sg = ct
+    hu = rng.choice(np.array([-1000, -100, 0, 500, 1200, 2000], dtype=np.int16),
+                    size=(ct.shape[2], ct.shape[1], ct.shape[0]))
+    w = np.array([0.21, -0.13, 1.0])
+    w /= np.linalg.norm(w)
+    u = np.cross(w, [0.0, 1.0, 0.0]); u /= np.linalg.norm(u)
+    iso = np.array([-0.4, 0.3, 0.0])
+    beam = W.Beam(direction=tuple(w), bev_x=tuple(u), iso=tuple(iso), source_to_iso=4.0)
+    pb = _one_beam_problem(ct, hu, sg, beam)
+    spots = W.make_spots([(0, energy, 0.0, 0.0, 0.0, 0.0, 3, 1.0)])
+    q, tl, rec = O.run(pb, O.oracle_spots(spots), W.Scenario(), DET, records=3)
+    dep = q.astype(np.float64) * 2.0 ** -24 / 3.0
+
+    p0 = iso - 4.0 * w
+    lo = np.array(ct.origin)
+    segs = _chords(p0, w, lo, [ct.spacing, sg.spacing], [ct.shape, sg.shape])
+    ref = np.zeros(sg.nvox)
+    R = O.csda_range(O.WATER, energy)
+    E = energy
+    stopped = False
+    for a, b, mid in segs:
+        ic = np.floor((mid - lo) / np.array(ct.spacing)).astype(int)
+        isg = np.floor((mid - lo) / np.array(sg.spacing)).astype(int)
+        _, spr = O.hu_props(pb.curve, float(hu[ic[2], ic[1], ic[0]]))
+        vi = isg[0] + sg.shape[0] * (isg[1] + sg.shape[1] * isg[2])
+        R1 = R - (b - a) * spr
+        if R1 <= 0:
+            ref[vi] += E
+            stopped = True
+            break
+        E1 = O.energy_at_range(O.WATER, R1)
+        ref[vi] += E - E1
+        R, E = R1, E1
+    assert np.allclose(dep, ref, atol=2e-5, rtol=0), np.abs(dep - ref).max()
+    fate = O.FATE_STOP if stopped else O.FATE_LEAK
+    assert np.all(rec["fate"] == fate)
+    if not stopped:
+        assert abs(rec["e_end"][0] - E) < 1e-9
+
+
+def test_nuclear_survival_is_exponential():
+    """Primary removal at 1.2 %/cm: survival to depth z is exp(-0.0012 z/mm)."""
+    n = 60000
+    pb, spots = W.pencil_beam_water(n_hist=n, energy=200.0, sigma=0.0, div_mrad=0.0)
+    op = W.Options(seed=99, mcs=False, straggling=False, nuclear=True)
+    q, tl, rec = O.run(pb, O.oracle_spots(spots), W.Scenario(), op, records=n)
+    zn = np.where(rec["fate"] == O.FATE_NUC, rec["pos"][:, 2], np.inf)
+    for z in (25.0, 75.0, 150.0, 240.0):
+        p = math.exp(-0.0012 * z)
+        surv = np.mean(zn > z)
+        assert abs(surv - p) < 4.0 * math.sqrt(p * (1 - p) / n), (z, surv, p)
+    # energy removed by nuclear events is deposited locally (conservation)
+    assert abs(tl["e_dep"] - tl["e_in"]) / tl["e_in"] < 1e-9
+
+
+def _aperture_case(polygon, x0=0.0, y0=0.0, sigma=4.0, n=60000, energy=150.0):
+    ct = W.Grid((20, 20, 10), (2.0, 2.0, 2.0), (-20.0, -20.0, 0.0))
+    hu = np.zeros((10, 20, 20), dtype=np.int16)
+    beam = W.Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0), source_to_iso=150.0,
+                  ap_present=True, ap_thickness=30.0, ap_down_to_iso=100.0, polygon=polygon)
+    pb = _one_beam_problem(ct, hu, beam=beam)
+    spots = W.make_spots([(0, energy, x0, y0, sigma, 0.0, n, 1.0)])
+    op = W.Options(seed=5, mcs=False, straggling=False, nuclear=True)
+    q, tl, rec = O.run(pb, O.oracle_spots(spots), W.Scenario(), op, records=n)
+    return np.mean(rec["fate"] != O.FATE_AP), tl
+
+
+def test_aperture_transmission_square_closed_form():
+    """Geometric transmission through a square opening of half-width a
+    (brass stops every proton below ~155 MeV, Sec. 2.B):
+    T = prod over axes of [erf((a - c)/s sqrt2) + erf((a + c)/s sqrt2)] / 2."""
+    a, s = 5.0, 4.0
+    for (x0, y0) in ((0.0, 0.0), (3.0, -2.0)):
+        t, tl = _aperture_case(W.square_polygon(a), x0, y0, s)
+        ref = 1.0
+        for c in (x0, y0):
+            ref *= 0.5 * (special.erf((a - c) / (s * math.sqrt(2))) + special.erf((a + c) / (s * math.sqrt(2))))
+        n = 60000
+        assert abs(t - ref) < 4 * math.sqrt(ref * (1 - ref) / n), (x0, y0, t, ref)
+        assert abs(tl["e_in"] - tl["e_dep"] - tl["e_ap"] - tl["e_leak"]) / tl["e_in"] < 1e-9
+
+
+def test_aperture_transmission_circle():
+    """256-gon opening of radius r, centred spot: T = 1 - exp(-r^2 / 2 s^2)
+    minus the polygon's area deficit (relative ~1e-4)."""
+    r, s, n = 6.0, 4.0, 60000
+    t, _ = _aperture_case(W.regular_polygon(r, 256), sigma=s, n=n)
+    ref = 1.0 - math.exp(-r * r / (2 * s * s))
+    assert abs(t - ref) < 4 * math.sqrt(ref * (1 - ref) / n) + 2e-4
+
+
+def test_energy_conservation_all_modes():
+    """E_in = scored + leaked + range shifter + aperture, to 1e-6, for the
+    water/aperture/range-shifter geometry and the heterogeneous head, in
+    deterministic and full modes, with a shifted scenario."""
+    pb, spots = W.water_aperture_case(20.0, True, hist_per_layer=2000, max_layers=3,
+                                      shape=(40, 40, 60), spacing=(2.0, 2.0, 2.0))
+    for op in (DET, W.Options(seed=3)):
+        q, tl, _ = O.run(pb, O.oracle_spots(spots), W.Scenario((1.0, -2.0, 0.5), 1.02), op)
+        tot = q.sum() * 2.0 ** -24 + tl["e_leak"] + tl["e_rs"] + tl["e_ap"]
+        assert abs(tot / tl["e_in"] - 1.0) < 1e-6
+        assert tl["e_rs"] > 0 and tl["e_ap"] > 0 and tl["errors"] == 0
+    g, hu, _ = W.head_ct(1234, shape=(64, 64, 40), spacing=(4.0, 4.0, 6.0))
+    beam = W.gantry_beam(90.0, (0.0, -20.0, 0.0), source_to_iso=245.0, rs_present=True, ap_present=True,
+                         polygon=W.regular_polygon(15.0, 64))
+    pb = W.Problem(ct=g, hu=hu, curve=W.HUCurve(), scoring=g, beams=[beam])
+    spots = W.make_spots([(0, 130.0, x, y, 3.0, 2.0, 300, 1.0) for x in (-6, 0, 6) for y in (-6, 0, 6)])
+    q, tl, _ = O.run(pb, O.oracle_spots(spots), W.Scenario((0.0, 3.0, 0.0), 0.965), W.Options(seed=8))
+    tot = q.sum() * 2.0 ** -24 + tl["e_leak"] + tl["e_rs"] + tl["e_ap"]
+    assert abs(tot / tl["e_in"] - 1.0) < 1e-6
+
+
+def test_columns_sum_to_dose_grid_and_threshold():
+    """Per-spot columns (mode 1) sum exactly to the unit-weight dose grid
+    (mode 0); the CSR keeps exactly the entries >= 1e-4 x column max."""
+    pb, spots = W.water_aperture_case(10.0, False, hist_per_layer=600, max_layers=2,
+                                      shape=(20, 20, 50), spacing=(2.0, 2.0, 2.0))
+    op = W.Options(seed=21)
+    cols, _, _ = O.run(pb, O.oracle_spots(spots), W.Scenario(), op, mode=1)
+    grid, _, _ = O.run(pb, O.oracle_spots(spots), W.Scenario(), op, mode=0)
+    assert np.array_equal(cols.sum(axis=0), grid)
+    im = O.influence_matrix(pb, spots, [W.Scenario()], op)[0].tocsc()
+    rho = O.scoring_density(pb)
+    d = cols * 2.0 ** -24 * O.MEV_PER_G_TO_GY / (pb.scoring.voxel_mm3 * 1e-3) / rho[None, :]
+    d /= spots["n_hist"][:, None]
+    for j in range(len(spots)):
+        col = d[j]
+        kept = np.zeros(col.shape, bool)
+        kept[im.indices[im.indptr[j]:im.indptr[j + 1]]] = True
+        thr = 1e-4 * col.max()
+        assert np.array_equal(kept, (col >= thr) & (col > 0))
+        np.testing.assert_array_equal(im[:, j].toarray().ravel()[kept], col[kept].astype(np.float32))
+
+
+def test_gamma_against_brute_force():
+    """C gamma vs a Python brute force of the same definition (global,
+    1/subdiv-voxel trilinear sub-grid, DTA sphere) on small random fields."""
+    rng = np.random.default_rng(2)
+    nz, ny, nx = 4, 5, 6
+    sp = (2.0, 2.0, 2.0)
+    ref = np.abs(rng.normal(1.0, 0.4, size=(nz, ny, nx)))
+    ev = ref * rng.normal(1.0, 0.03, size=ref.shape)
+    assert O.gamma_pass_rate(ref, ref, sp) == 100.0
+    dmax = ref.max()
+    sub = 5
+    r = int(math.ceil(2.0 / sp[0] * sub))
+    offs = [(i / sub, j / sub, k / sub) for k in range(-r, r + 1) for j in range(-r, r + 1) for i in range(-r, r + 1)
+            if (i * sp[0] / sub) ** 2 + (j * sp[1] / sub) ** 2 + (k * sp[2] / sub) ** 2 <= 4.0]
+    npass = neval = 0
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if ref[z, y, x] < 0.1 * dmax:
+                    continue
+                neval += 1
+                for (i, j, k) in offs:
+                    fx, fy, fz = x + i, y + j, z + k
+                    if not (0 <= fx <= nx - 1 and 0 <= fy <= ny - 1 and 0 <= fz <= nz - 1):
+                        continue
+                    de = map_coordinates(ev, [[fz], [fy], [fx]], order=1)[0]
+                    dist2 = (i * sp[0]) ** 2 + (j * sp[1]) ** 2 + (k * sp[2]) ** 2
+                    if dist2 / 4.0 + (de - ref[z, y, x]) ** 2 / (0.02 * dmax) ** 2 <= 1.0:
+                        npass += 1
+                        break
+    assert abs(O.gamma_pass_rate(ref, ev, sp) - 100.0 * npass / neval) < 1e-9
+    const = np.ones((4, 4, 4))
+    assert O.gamma_pass_rate(const, const * 1.019, sp) == 100.0
+    assert O.gamma_pass_rate(const, const * 1.021, sp) == 0.0
+
+
+def test_scoring_density_volume_weighted():
+    """Scoring-voxel density = volume-weighted mean of overlapping CT voxels
+    (brute force on a common 0.5 mm sub-grid)."""
+    rng = np.random.default_rng(7)
+    ct = W.Grid((4, 4, 4), (1.0, 1.0, 1.5), (-2.0, -2.0, 0.0))
+    sg = W.Grid((2, 2, 3), (2.0, 2.0, 2.0), (-2.0, -2.0, 0.0))
+    hu = rng.integers(-1000, 1600, size=(4, 4, 4)).astype(np.int16)
+    pb = W.Problem(ct=ct, hu=hu, curve=W.HUCurve(), scoring=sg, beams=[])
+    rho_ct = np.vectorize(lambda h: O.hu_props(pb.curve, float(h))[0])(hu)
+    fine = np.repeat(np.repeat(np.repeat(rho_ct, 3, axis=0), 2, axis=1), 2, axis=2)  # 0.5 mm cells
+    ref = fine.reshape(3, 4, 2, 4, 2, 4).mean(axis=(1, 3, 5))
+    assert np.allclose(O.scoring_density(pb), ref.ravel(), rtol=1e-12)
