@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the robust influence-matrix set (one step = one 13-scenario set).
+
+Workload: synthetic heterogeneous head (256x256x160 CT at 1x1x1.5 mm, 2 mm
+scoring grid), 8.4 cc spherical target, three coplanar fields (0/90/270 deg)
+with 45 mm WET range shifter and brass apertures conformed to the target
+projection + 5 mm, 3 mm spot grid, layers 3 mm WET apart, 1e3-2e4 histories
+per spot (log-uniform), 13 robust scenarios (nominal, +/-3 mm shifts, +/-3.5 %
+range with each shift sign).  Full physics (Highland, Bohr, nuclear removal).
+
+metric: protons/s (histories of the whole set / time) and seconds per set.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2307_01416_gb300 import workloads as W  # noqa: E402
+
+METRIC = "protons/s; s per 13-scenario influence-matrix set at 0.5% unc."
+WORKLOAD = ("13-scenario robust influence-matrix set, synthetic head 256x256x160 CT (1x1x1.5 mm), 2 mm scoring grid, "
+            "8.4 cc target, 3 fields 0/90/270 deg, 45 mm WET range shifter, brass apertures (target + 5 mm), "
+            "3 mm spots, 1e3-2e4 histories/spot")
+# Lane-operations of one condensed-history step of the full-physics method
+# (the model and its itemisation are stated in the design doc).
+OPS_PER_STEP = 370
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["vpmc", "reference"], default="vpmc")
+    ap.add_argument("--small", action="store_true", help="reduced history counts (quick check, not a bench line)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="small fixed-launch transport case for ncu captures (dose path, nominal scenario)")
+    return ap.parse_args()
+
+
+def build_workload(small: bool):
+    pb, spots, center, r = W.head_plan(8.4)
+    if small:
+        spots = spots.copy()
+        spots["n_hist"] = np.maximum(spots["n_hist"] // 50, 20)
+    return pb, spots, W.robust_scenarios()
+
+
+# ----------------------------------------------------------------------------- clocks
+REASONS = ["clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+           "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = "index,clocks.sm,clocks.max.sm,power.draw," + ",".join(REASONS)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 4 + len(REASONS):
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        active = set()
+        for r in rows:
+            for name, v in zip(REASONS, r[4:4 + len(REASONS)]):
+                if v.lower() == "active":
+                    active.add(name.split(".")[-1])
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(active), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(pb, spots, target_hist: int, seed: int = 1234):
+    """Deterministic subset: every k-th spot of the nominal scenario with its
+    full history count, about target_hist histories in total."""
+    k = max(1, int(round(spots["n_hist"].sum() / max(target_hist, 1))))
+    idx = np.arange(0, len(spots), k)
+    return idx
+
+
+def time_oracle(pb, spots, idx, opts):
+    from oracle import oracle as O
+    O.lib()
+    sp = O.oracle_spots(spots[idx], spot_keys=idx)
+    t0 = time.perf_counter()
+    _, tl, _ = O.run(pb, sp, W.Scenario(), opts, mode=0)
+    dt = time.perf_counter() - t0
+    return tl, dt, O.max_threads()
+
+
+def cpu_baseline(pb, spots, seconds: float):
+    from oracle import oracle as O
+    opts = W.Options(seed=1234)
+    # calibrate on a small subset, then run a subset sized for `seconds`
+    idx = oracle_sample(pb, spots, 20000)
+    tl, dt, cores = time_oracle(pb, spots, idx, opts)
+    rate = tl["histories"] / dt
+    idx = oracle_sample(pb, spots, int(rate * seconds))
+    tl, dt, cores = time_oracle(pb, spots, idx, opts)
+    return {"value": tl["histories"] / dt, "unit": "protons/s", "cores": cores, "kind": "oracle",
+            "sample": "nominal scenario, every %d-th spot (%d spots, %d histories, %.1f s FP64 C oracle, OpenMP)"
+                      % (max(1, len(spots) // max(len(idx), 1)), len(idx), int(tl["histories"]), dt)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    pb, spots, scens = build_workload(False)
+    from oracle import oracle as O
+    O.lib()
+    opts = W.Options(seed=1234)
+    idx0 = oracle_sample(pb, spots, 20000)
+    tl, dt, cores = time_oracle(pb, spots, idx0, opts)
+    rate = tl["histories"] / dt
+    idx = oracle_sample(pb, spots, int(rate * 8.0))
+    for _ in range(args.warmup):
+        time_oracle(pb, spots, idx0, opts)
+    hist, tot = 0.0, 0.0
+    for _ in range(args.steps):
+        tl, dt, cores = time_oracle(pb, spots, idx, opts)
+        hist += tl["histories"]
+        tot += dt
+    value = hist / tot
+    set_hist = float(spots["n_hist"].sum()) * len(scens)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "protons/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "every %d-th spot of the nominal scenario, %d histories per step"
+                       % (max(1, len(spots) // len(idx)), int(hist / args.steps))},
+            "s_per_im_set": set_hist / value,
+            "cpu_baseline": {"value": value, "unit": "protons/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d histories per step" % int(hist / args.steps)},
+            "e2e": {"value": value, "unit": "protons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.ncu_case:
+        return run_ncu_case(args)
+    import torch
+    import torch.distributed as dist
+    from paper_2307_01416_gb300 import vpmc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pb, spots, scens = build_workload(args.small)
+    # independent problems per rank (weak scaling): each rank computes its own set
+    opts = W.Options(seed=1234 + 7919 * rank)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        eng = vpmc.Engine(pb, stream=stream)
+        launches = 0
+        for _ in range(args.warmup):
+            mats, st = eng.influence_matrix(spots, scens, opts)
+            del mats
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        kern_ms, steps, hist, nnz = 0.0, 0, 0, 0
+        for _ in range(args.steps):
+            flush.fill_(1.0)                       # evict L2 between sets
+            mats, st = eng.influence_matrix(spots, scens, opts)
+            kern_ms += st["ms"]
+            steps += st["steps"]
+            hist += st["histories"]
+            launches += st["launches"] + 1
+            nnz = sum(int(m["val"].numel()) for m in mats)
+            del mats
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        t = ev0.elapsed_time(ev1) / 1000.0
+    if world > 1:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+        hh = torch.tensor([float(hist)], device="cuda")
+        dist.all_reduce(hh)
+        hist_all = float(hh.item())
+    else:
+        hist_all = float(hist)
+    value = hist_all / t
+    ms_per_step = 1000.0 * t / args.steps
+
+    out = None
+    if rank == 0:
+        peaks = measured_peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_tops = nsm * 4 * 32 * sm_max * 1e6 / 1e12
+        achieved = steps * OPS_PER_STEP / (kern_ms / 1000.0) / 1e12
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "transport_traffic.json")
+        if os.path.exists(tpath):
+            try:
+                tj = json.load(open(tpath))
+                traffic = tj.get("bytes_per_step", 0) * steps / args.steps if tj.get("valid") else None
+            except (OSError, ValueError):
+                traffic = None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved / peak_tops, "traffic": traffic, "kernel": "k_transport",
+                "peak_note": "%d SMs x 4 sub-partitions x 32 lanes x %.0f MHz (max SM clock) lane-ops/s; "
+                             "%d lane-ops per condensed-history step" % (nsm, sm_max, OPS_PER_STEP),
+                "kernel_ms_per_step": kern_ms / args.steps, "steps_per_launch": steps / args.steps}
+        e2e = None
+        if not args.no_e2e:
+            e2e = e2e_leg(pb, spots, scens, opts, args)
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(pb, spots, args.cpu_seconds)
+        set_hist = float(spots["n_hist"].sum()) * len(scens)
+        out = {"metric": METRIC, "value": value, "unit": "protons/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD + (" (reduced histories)" if args.small else ""),
+                          "scenarios": len(scens), "spots_per_scenario": int(len(spots)),
+                          "histories_per_set": int(set_hist), "nnz_per_set": nnz,
+                          "l2": "512 MiB buffer written between sets; the set's 100+ GB column scratch exceeds L2",
+                          "parallelism": "independent sets per GPU" if world > 1 else "1 GPU"},
+               "s_per_im_set": ms_per_step / 1000.0,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_ncu_case(args):
+    """Every 10th spot of the set's nominal scenario (about 3.3e6 histories,
+    full physics) through vpmc_run_spots with a fixed launch (512 threads,
+    warp-aggregated atomics, chunk 32): one k_transport launch per step and a
+    16 MB scoring grid, small enough for a full ncu capture."""
+    import torch
+    from paper_2307_01416_gb300 import vpmc
+    pb, spots, scens = build_workload(False)
+    sub = spots[::10]
+    torch.cuda.set_device(0)
+    eng = vpmc.Engine(pb)
+    opts = W.Options(seed=1234)
+    for i in range(args.warmup + args.steps):
+        dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=512, aggregate=1, chunk=32)
+        print(json.dumps({"case": "ncu", "iter": i, "histories": st["histories"], "steps": st["steps"],
+                          "kernel_ms": st["ms"], "steps_per_s": st["steps"] / (st["ms"] / 1000.0)}))
+    eng.close()
+    return 0
+
+
+def e2e_leg(pb, spots, scens, opts, args):
+    """The same metric through the public API from host buffers: each step
+    creates the geometry from the host CT, sets the fields, computes the set
+    and copies every CSR back to pinned host memory."""
+    import torch
+    from paper_2307_01416_gb300 import vpmc
+    steps = max(1, min(args.steps, 2))
+    host = None
+    t_tot, h2d, d2h = 0.0, 0, 0
+    hist = 0
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eng = vpmc.Engine(pb, host_ct=True)
+        mats, st = eng.influence_matrix(spots, scens, opts)
+        if host is None:
+            host = [{k: torch.empty(m[k].shape, dtype=m[k].dtype, pin_memory=True) for k in ("row_ptr", "col", "val")}
+                    for m in mats]
+        nb = 0
+        for m, h in zip(mats, host):
+            for k in ("row_ptr", "col", "val"):
+                if h[k].numel() != m[k].numel():
+                    h[k] = torch.empty(m[k].shape, dtype=m[k].dtype, pin_memory=True)
+                h[k].copy_(m[k], non_blocking=True)
+                nb += m[k].numel() * m[k].element_size()
+        torch.cuda.synchronize()
+        eng.close()
+        dt = time.perf_counter() - t0
+        if i == 0:
+            continue                                   # first pass allocates the pinned buffers
+        t_tot += dt
+        hist += st["histories"]
+        d2h = nb
+        h2d = pb.hu.nbytes + len(spots) * 56 + len(scens) * 32
+    return {"value": hist / t_tot, "unit": "protons/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": steps}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

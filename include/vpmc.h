@@ -1,0 +1,193 @@
+/*
+ * vpmc.h -- C ABI of the GB300-native aperture-aware proton Monte Carlo engine.
+ *
+ * The engine transports independent proton histories (one identical model
+ * per history, paper Sec. 2.A) through an optional range shifter and a brass
+ * aperture block (Sec. 2.B: 30 mm brass; in the aperture slab a
+ * crossing-number test decides at every step whether the particle is in the
+ * opening -- straight flight -- or in brass -- brass physics) and a voxelised
+ * CT grid, and scores deposited energy into a dose grid or into per-spot
+ * influence-matrix columns (Sec. 2.C, sparse matrices) for robust scenarios
+ * (Sec. 2.E: stopping-power-ratio scaling and isocentre shifts).
+ *
+ * Conventions for every entry point:
+ *   - Units: mm, MeV, mrad for spot divergence; coordinates are the CT
+ *     grid's (patient) frame.  Grids are x-fastest.
+ *   - The caller owns every input; the library copies geometry, polygons,
+ *     spots and scenarios during the call, so they may be freed on return.
+ *   - Device work is enqueued on the context's CUDA stream.  Calls that return
+ *     sizes or statistics synchronise that stream; the others are
+ *     asynchronous (documented per call).
+ *   - Errors: a vpmc_status is returned and a message is kept per thread
+ *     (vpmc_last_error).  No C++ exception crosses this boundary.  A kernel
+ *     that meets an inconsistent state (iteration cap of a history, box
+ *     overflow) records it in a device status word that the host reads.
+ *   - Nothing here allocates host memory that the caller must free, except
+ *     the CSR buffers of vpmc_influence_matrix (vpmc_free_csr).
+ */
+#ifndef VPMC_H
+#define VPMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vpmc_ctx vpmc_ctx; /* opaque; one per (CUDA device, stream, CT) */
+
+typedef enum {
+    VPMC_OK = 0,
+    VPMC_ERR_ARG = -1,         /* invalid argument (message says which)       */
+    VPMC_ERR_CUDA = -2,        /* a CUDA runtime call failed                  */
+    VPMC_ERR_OOM = -3,         /* device memory exhausted                     */
+    VPMC_ERR_TIMEOUT = -4,     /* a history reached the iteration cap         */
+    VPMC_ERR_STATE = -5,       /* call out of order (e.g. beam not set)       */
+    VPMC_ERR_DEVICE_FLAG = -6  /* a kernel latched an error in its status word */
+} vpmc_status;
+
+/* Four-segment piecewise-linear HU -> (mass density g/cc, stopping-power
+ * ratio to water) curve: 5 knots, HU ascending.  HU is clamped to
+ * [hu[0], 3071]; above hu[4] the last segment is extended. */
+typedef struct { double hu[5], density[5], spr[5]; } vpmc_hu_curve;
+
+/* Regular grid: n voxels per axis of size d (mm); origin = corner of voxel
+ * (0,0,0).  Arrays on it are x-fastest: index = x + nx*(y + ny*z). */
+typedef struct { int nx, ny, nz; double dx, dy, dz; double origin[3]; } vpmc_grid;
+
+/* One field (Sec. 2.B, 2.D).  dir = beam axis w (unit), bev_x = first
+ * beam's-eye-view axis u (unit, orthogonal to w); second axis v = w x u.
+ * Positions along the beam are t (mm) relative to the isocentre, downstream
+ * positive; devices are placed by the distance of their downstream face to
+ * the isocentre (paper: aperture 150 mm, range shifter 190 mm).  The source
+ * plane is t = -source_to_iso_mm and must lie upstream of every device.
+ * Range shifter: PMMA slab of water-equivalent thickness rs_wet_mm (geometric
+ * thickness = rs_wet_mm / SPR_PMMA(150 MeV)) and radius rs_radius_mm.
+ * Aperture: non-divergent brass block of thickness ap_thickness_mm whose
+ * opening is the polygon poly_xy (n_vertices (u, v) pairs in mm, any
+ * orientation, simple); at most 1024 vertices over all beams of a context. */
+typedef struct {
+    double dir[3], bev_x[3], iso[3];
+    double source_to_iso_mm;
+    int rs_present;
+    double rs_wet_mm, rs_radius_mm, rs_down_to_iso_mm;
+    int ap_present;
+    double ap_thickness_mm, ap_down_to_iso_mm;
+    const double* poly_xy;
+    int n_vertices;
+} vpmc_beam;
+
+/* One pencil-beam spot (Sec. 2.D.2): mono-energetic (energy_mev <= 250),
+ * position (x_mm, y_mm) and Gaussian sigma_mm at the isocentre plane in BEV
+ * coordinates, per-plane angular sigma div_mrad, n_hist histories (< 2^32).
+ * weight multiplies every deposit of the spot in vpmc_run_spots (dose per
+ * history x weight); vpmc_influence_matrix ignores it. */
+typedef struct {
+    int beam;
+    double energy_mev, x_mm, y_mm, sigma_mm, div_mrad;
+    int64_t n_hist;
+    double weight;
+} vpmc_spot;
+
+/* Robust scenario (Sec. 2.E): isocentre shift (patient frame) and SPR scale. */
+typedef struct { double shift_mm[3]; double spr_scale; } vpmc_scenario;
+
+/* Per-history record (optional output of vpmc_run_spots). */
+typedef struct {
+    int64_t q_dep;    /* fixed-point sum of the history's grid deposits (2^-frac_bits MeV) */
+    int32_t fate;     /* 0 stopped, 1 nuclear, 2 left the grid / missed, 3 absorbed in range
+                         shifter, 4 absorbed in aperture, 5 iteration cap reached */
+    int32_t steps;    /* condensed-history steps */
+    float e_dep;      /* energy scored in the grid, MeV */
+    float e_end;      /* kinetic energy when it left the simulation, MeV */
+    float pos[3];     /* end position, patient frame, mm */
+    float pad;
+} vpmc_history_record;
+
+typedef struct {
+    uint64_t seed;          /* Philox key: (seed low word, spot index ^ seed high word)  */
+    int mcs;                /* Highland multiple scattering on/off                        */
+    int straggling;         /* Bohr straggling on/off                                     */
+    int nuclear;            /* nuclear removal (1.2 %/cm x density) on/off                */
+    int frac_bits;          /* fixed-point scale of deposits, 2^-frac_bits MeV (default 24) */
+    int aggregate;          /* -1 autotuned, 0 plain atomics, 1 warp-aggregated atomics   */
+    int block_size;         /* 0 autotuned, else threads per block (multiple of 32)       */
+    int blocks_per_sm;      /* 0 autotuned                                                */
+    int chunk;              /* histories taken per warp refill (0 = default)              */
+    vpmc_history_record* history_out;  /* device buffer or NULL                          */
+    int64_t history_cap;    /* records for global history index < history_cap            */
+} vpmc_opts;
+
+/* Totals of one call.  Energies in MeV (fixed-point sums, unweighted). */
+typedef struct {
+    int64_t histories, steps, errors;
+    double e_in, e_dep, e_leak, e_rs, e_aperture, e_nuc;
+    float ms;               /* device time of the transport launch(es), CUDA events */
+    int64_t launches;       /* kernels this call launched (autotuning included) */
+} vpmc_stats;
+
+/* Sparse influence matrix of one scenario: rows = scoring voxels (x-fastest),
+ * columns = spot indices; row_ptr int64[n_rows+1], col int32[nnz] sorted
+ * within each row, val float32[nnz] = dose per primary proton (Gy).  All three
+ * buffers are device memory allocated by the library. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    int64_t* row_ptr;
+    int32_t* col;
+    float* val;
+} vpmc_csr;
+
+/* Fill opts with defaults: seed 1234, all physics on, frac_bits 24,
+ * autotuned launch, no records. */
+void vpmc_default_opts(vpmc_opts* opts);
+
+/* Create a context (Sec. 2.A physics tables; Sec. 2.D.3 patient CT).
+ * hu: int16 CT on ct's grid, host pointer (hu_on_device = 0) or device
+ * pointer of the current device (hu_on_device = 1); copied.  dose_grid: the
+ * scoring grid; it must have the CT's origin and extent (its voxel size may
+ * differ); dose is dose-to-medium with the volume-weighted mean density of
+ * the overlapping CT voxels.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream).  Builds the stopping-power/range tables (Bethe-Bloch,
+ * FP64 on the host, stored FP32), the HU lookup table and the scoring-voxel
+ * densities; synchronises the stream.  On error *out is NULL. */
+vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_device, const vpmc_grid* ct,
+                                 const vpmc_hu_curve* curve, const vpmc_grid* dose_grid, void* cuda_stream);
+
+/* Set field beam_id (0..15) (Sec. 2.B: range shifter and aperture geometry,
+ * crossing-number opening).  Copies the polygon and builds its BEV
+ * classification raster.  Synchronous. */
+vpmc_status vpmc_set_aperture(vpmc_ctx* ctx, int beam_id, const vpmc_beam* beam);
+
+/* Dose of a set of spots in one scenario (Sec. 2.C, 2.D): transports every
+ * history, accumulates 64-bit fixed-point sums and writes dose_dev (device
+ * float32 array on the scoring grid, caller-owned) = sum over deposits of
+ * dE * weight / (rho * V) in Gy.  scen may be NULL (nominal).  Asynchronous
+ * on the context stream unless stats_out is non-NULL, in which case it
+ * synchronises and fills the totals. */
+vpmc_status vpmc_run_spots(vpmc_ctx* ctx, const vpmc_spot* spots, int n_spots, const vpmc_scenario* scen,
+                           const vpmc_opts* opts, float* dose_dev, vpmc_stats* stats_out);
+
+/* Influence matrices for n_scen scenarios (Sec. 2.C sparse matrices, Sec.
+ * 2.E 13 robust scenarios): every (scenario, spot) column in one persistent
+ * launch, unweighted; column j of scenario s = dose per primary of spot j;
+ * entries below rel_threshold x the column maximum are dropped.  Spots must
+ * be sorted by beam id.  out: array of n_scen vpmc_csr filled with
+ * library-allocated device buffers (free with vpmc_free_csr).  Synchronous. */
+vpmc_status vpmc_influence_matrix(vpmc_ctx* ctx, const vpmc_spot* spots, int n_spots, const vpmc_scenario* scen,
+                                  int n_scen, const vpmc_opts* opts, float rel_threshold, vpmc_csr* out,
+                                  vpmc_stats* stats_out);
+
+/* Free the device buffers of n CSR matrices and zero the structs. */
+vpmc_status vpmc_free_csr(vpmc_csr* csr, int n);
+
+/* Destroy a context and free its device memory. */
+void vpmc_destroy(vpmc_ctx* ctx);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* vpmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VPMC_H */

@@ -73,7 +73,9 @@ SPOT_DTYPE = np.dtype([("beam", np.int32), ("spot_key", np.int32), ("energy", np
                        ("y", np.float64), ("sigma", np.float64), ("div_mrad", np.float64),
                        ("h_begin", np.int64), ("n_hist", np.int64), ("weight", np.float64)], align=True)
 RECORD_DTYPE = np.dtype([("fate", np.int32), ("steps", np.int32), ("e_dep", np.float64), ("e_end", np.float64),
-                         ("pos", np.float64, (3,)), ("q_dep", np.int64)], align=True)
+                         ("pos", np.float64, (3,)), ("q_dep", np.int64), ("flags", np.int32), ("pad", np.int32)],
+                        align=True)
+FLAG_NEAR_WALL, FLAG_NEAR_RIM = 1, 2
 
 _lib = None
 _lock = threading.Lock()
@@ -106,6 +108,8 @@ def lib():
             L.orc_point_in_polygon.restype = C.c_int
             L.orc_first_wall_hit.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
             L.orc_first_wall_hit.restype = C.c_double
+            L.orc_wall_distance.argtypes = [dp, C.c_int, C.c_double, C.c_double]
+            L.orc_wall_distance.restype = C.c_double
             L.orc_highland.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
             L.orc_highland.restype = C.c_double
             L.orc_bohr_var.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
@@ -204,6 +208,11 @@ def point_in_polygon(poly: np.ndarray, x: float, y: float) -> bool:
 def first_wall_hit(poly: np.ndarray, x, y, dx, dy) -> float:
     p = np.ascontiguousarray(poly, dtype=np.float64)
     return lib().orc_first_wall_hit(_dp(p), len(p), float(x), float(y), float(dx), float(dy))
+
+
+def wall_distance(poly: np.ndarray, x, y) -> float:
+    p = np.ascontiguousarray(poly, dtype=np.float64)
+    return lib().orc_wall_distance(_dp(p), len(p), float(x), float(y))
 
 
 def highland(e, s_mm, rho, x0_gcm2) -> float:

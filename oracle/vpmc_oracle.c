@@ -273,6 +273,24 @@ double orc_first_wall_hit(const double* poly, int n, double x, double y, double 
 }
 
 
+/* Distance from (x, y) to the polygon boundary. */
+double orc_wall_distance(const double* poly, int n, double x, double y)
+{
+    double best = INFINITY;
+    for (int i = 0; i < n; ++i) {
+        int j = (i + 1) % n;
+        double ax = poly[2 * i], ay = poly[2 * i + 1];
+        double ex = poly[2 * j] - ax, ey = poly[2 * j + 1] - ay;
+        double t = ((x - ax) * ex + (y - ay) * ey) / (ex * ex + ey * ey);
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+        double dx = ax + t * ex - x, dy = ay + t * ey - y;
+        double d = sqrt(dx * dx + dy * dy);
+        if (d < best) best = d;
+    }
+    return best;
+}
+
 /* ------------------------------------------------------------------ */
 /* Problem description (the oracle's own structs).                     */
 /* ------------------------------------------------------------------ */
@@ -319,10 +337,18 @@ typedef struct {
     int32_t fate;
     int32_t steps;      /* condensed-history steps of the history            */
     double e_dep;       /* energy scored in the patient grid, MeV            */
-    double e_end;       /* kinetic energy when the history left, MeV         */
+    double e_end;       /* kinetic energy when it left, MeV                  */
     double pos[3];      /* end position, patient coordinates, mm             */
     int64_t q_dep;      /* sum of the history's fixed-point grid deposits    */
+    int32_t flags;      /* bit 0: a step started within ORC_TIE_MM of an
+                           aperture wall; bit 1: of the range-shifter rim    */
+    int32_t pad;
 } orc_record;
+
+/* Distance below which a device boundary makes a history ill-conditioned:
+ * at grazing incidence a rounding-level shift of the position changes which
+ * side of the boundary a step starts on. */
+#define ORC_TIE_MM 0.01
 
 /* Tallies: 0 energy in, 1 scored in grid, 2 leaked, 3 range shifter,
  * 4 aperture, 5 nuclear (included in 1, 3, 4), 6 histories, 7 steps,
@@ -470,7 +496,7 @@ typedef struct {
     int64_t nvox;
 } orc_run_ctx;
 
-#define ORC_MAX_ITER 1000000
+#define ORC_MAX_ITER 200000
 
 static void beam_axes(const orc_beam* bm, double u[3], double v[3], double w[3])
 {
@@ -544,6 +570,7 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
         for (;;) {
             if (++iter > ORC_MAX_ITER) goto fail;
             double r2 = pt.p[0] * pt.p[0] + pt.p[1] * pt.p[1];
+            if (fabs(sqrt(r2) - bm->rs_radius) < ORC_TIE_MM) rec->flags |= 2;
             if (r2 > bm->rs_radius * bm->rs_radius) {
                 /* outside the shifter: straight flight to its exit plane */
                 if (pt.d[2] <= 0.0) goto leak;
@@ -555,6 +582,7 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
             int down = 1;
             if (pt.d[2] > 0.0) sg = (tdn - pt.p[2]) / pt.d[2];
             else if (pt.d[2] < 0.0) { sg = (tup - pt.p[2]) / pt.d[2]; down = 0; }
+            if (sg < 0.0) sg = 0.0;   /* scattering offsets can leave it past the plane */
             ch_step(&med, &pt, sg, op, &st, &so);
             tl[3] += so.dE;
             tl[7] += 1.0;
@@ -588,6 +616,8 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
             int down = 1;
             if (pt.d[2] > 0.0) sg = (tdn - pt.p[2]) / pt.d[2];
             else if (pt.d[2] < 0.0) { sg = (tup - pt.p[2]) / pt.d[2]; down = 0; }
+            if (sg < 0.0) sg = 0.0;   /* scattering offsets can leave it past the plane */
+            if (orc_wall_distance(poly, bm->nvert, pt.p[0], pt.p[1]) < ORC_TIE_MM) rec->flags |= 1;
             int in_open = !forced_brass && orc_point_in_polygon(poly, bm->nvert, pt.p[0], pt.p[1]);
             if (in_open) {
                 /* opening: keep velocity and direction up to a wall or the exit */

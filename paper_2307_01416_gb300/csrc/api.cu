@@ -1,0 +1,1074 @@
+// C ABI of the transport library: context, fields, dose and influence matrices.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vpmc.h"
+#include "tables.h"
+#include "vpmc_internal.cuh"
+
+using namespace vpmc;
+
+namespace {
+
+thread_local std::string g_error;
+
+vpmc_status fail(vpmc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                             \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? VPMC_ERR_OOM : VPMC_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+struct TuneResult {
+    bool valid = false;
+    int block = 512;
+    int aggregate = 1;
+    int chunk = 32;
+};
+
+}  // namespace
+
+struct vpmc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Grid3 ctg{}, sg{};
+    double ct_spacing[3]{}, sg_spacing[3]{};
+    bool same_grid = false;
+    long long nvox = 0;
+    double curve15[15]{};
+    int16_t* d_ct = nullptr;
+    TablesImage* d_tables = nullptr;
+    double* d_curve = nullptr;
+    double* d_rho = nullptr;
+    unsigned long long* d_acc = nullptr;       // dose accumulator (scoring grid)
+    // fields
+    bool beam_set[kMaxBeams]{};
+    DevBeam beams[kMaxBeams]{};
+    std::vector<double> poly[kMaxBeams];
+    std::vector<unsigned char> raster[kMaxBeams];
+    double src_raster_lo[kMaxBeams][2]{};
+    DevBeam* d_beams = nullptr;
+    float2* d_poly = nullptr;
+    int n_poly = 0;
+    unsigned char* d_raster = nullptr;
+    // per-launch buffers
+    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_stats = nullptr;
+    int* d_status = nullptr;
+    DevScen* d_scens = nullptr;
+    DevItem* d_items = nullptr;
+    size_t items_cap = 0;
+    DevBox* d_boxes = nullptr;
+    size_t boxes_cap = 0;
+    int* d_item_flags = nullptr;
+    size_t flags_cap = 0;
+    unsigned long long* d_scratch = nullptr;
+    size_t scratch_cap = 0;                    // elements
+    TuneResult tune_dose, tune_im;
+    long long launches = 0;                    // kernels launched since creation
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+Grid3 to_grid3(const vpmc_grid& g)
+{
+    Grid3 r;
+    r.n[0] = g.nx; r.n[1] = g.ny; r.n[2] = g.nz;
+    r.d[0] = (float)g.dx; r.d[1] = (float)g.dy; r.d[2] = (float)g.dz;
+    for (int k = 0; k < 3; ++k) r.lo[k] = (float)g.origin[k];
+    return r;
+}
+
+vpmc_status grow(vpmc_ctx* c, DevItem** p, size_t* cap, size_t n)
+{
+    if (n <= *cap) return VPMC_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    CUDA_TRY(dev_alloc(p, n));
+    *cap = n;
+    (void)c;
+    return VPMC_OK;
+}
+
+vpmc_status grow_boxes(vpmc_ctx* c, size_t n)
+{
+    if (n <= c->boxes_cap) return VPMC_OK;
+    cudaFree(c->d_boxes);
+    c->d_boxes = nullptr;
+    c->boxes_cap = 0;
+    CUDA_TRY(dev_alloc(&c->d_boxes, n));
+    c->boxes_cap = n;
+    return VPMC_OK;
+}
+
+vpmc_status grow_flags(vpmc_ctx* c, size_t n)
+{
+    if (n <= c->flags_cap) return VPMC_OK;
+    cudaFree(c->d_item_flags);
+    c->d_item_flags = nullptr;
+    c->flags_cap = 0;
+    CUDA_TRY(dev_alloc(&c->d_item_flags, n));
+    c->flags_cap = n;
+    return VPMC_OK;
+}
+
+vpmc_status grow_scratch(vpmc_ctx* c, size_t n)
+{
+    if (n <= c->scratch_cap) return VPMC_OK;
+    cudaFree(c->d_scratch);
+    c->d_scratch = nullptr;
+    c->scratch_cap = 0;
+    CUDA_TRY(dev_alloc(&c->d_scratch, n));
+    c->scratch_cap = n;
+    return VPMC_OK;
+}
+
+vpmc_status upload_beams(vpmc_ctx* c)
+{
+    std::vector<float2> poly;
+    std::vector<unsigned char> ras;
+    DevBeam tmp[kMaxBeams];
+    for (int b = 0; b < kMaxBeams; ++b) {
+        tmp[b] = c->beams[b];
+        if (!c->beam_set[b] || !c->beams[b].ap) continue;
+        tmp[b].poly_off = (int)poly.size();
+        for (size_t i = 0; i + 1 < c->poly[b].size(); i += 2)
+            poly.push_back(make_float2((float)c->poly[b][i], (float)c->poly[b][i + 1]));
+        tmp[b].ras_off = (int)ras.size();
+        ras.insert(ras.end(), c->raster[b].begin(), c->raster[b].end());
+    }
+    if (poly.size() > (size_t)kMaxPolyVerts)
+        return fail(VPMC_ERR_ARG, "aperture polygons have %zu vertices in total (max %d)", poly.size(), kMaxPolyVerts);
+    cudaFree(c->d_poly);
+    cudaFree(c->d_raster);
+    c->d_poly = nullptr;
+    c->d_raster = nullptr;
+    CUDA_TRY(dev_alloc(&c->d_poly, std::max<size_t>(poly.size(), 1)));
+    CUDA_TRY(dev_alloc(&c->d_raster, std::max<size_t>(ras.size(), 1)));
+    if (!poly.empty()) CUDA_TRY(cudaMemcpy(c->d_poly, poly.data(), poly.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    if (!ras.empty()) CUDA_TRY(cudaMemcpy(c->d_raster, ras.data(), ras.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_beams, tmp, sizeof(tmp), cudaMemcpyHostToDevice));
+    c->n_poly = (int)poly.size();
+    return VPMC_OK;
+}
+
+// Checks shared by the dose and influence-matrix paths.
+vpmc_status check_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots)
+{
+    if (n_spots < 0 || (n_spots > 0 && !spots)) return fail(VPMC_ERR_ARG, "spots: null pointer or negative count");
+    for (int i = 0; i < n_spots; ++i) {
+        const vpmc_spot& s = spots[i];
+        if (s.beam < 0 || s.beam >= kMaxBeams || !c->beam_set[s.beam])
+            return fail(VPMC_ERR_STATE, "spot %d: beam %d was not set with vpmc_set_aperture", i, s.beam);
+        if (!(s.energy_mev > 0.5 && s.energy_mev <= 250.0))
+            return fail(VPMC_ERR_ARG, "spot %d: energy %g MeV outside (0.5, 250]", i, s.energy_mev);
+        if (s.n_hist < 0 || s.n_hist >= (1ll << 32))
+            return fail(VPMC_ERR_ARG, "spot %d: n_hist %lld outside [0, 2^32)", i, (long long)s.n_hist);
+        if (!(s.sigma_mm >= 0.0) || !(s.div_mrad >= 0.0) || !std::isfinite(s.x_mm) || !std::isfinite(s.y_mm))
+            return fail(VPMC_ERR_ARG, "spot %d: invalid position, sigma or divergence", i);
+    }
+    return VPMC_OK;
+}
+
+vpmc_status check_opts(const vpmc_opts* o)
+{
+    if (!o) return VPMC_OK;
+    if (o->frac_bits < 0 || o->frac_bits > 40) return fail(VPMC_ERR_ARG, "frac_bits %d outside [0, 40]", o->frac_bits);
+    if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 512 || o->block_size % 32))
+        return fail(VPMC_ERR_ARG, "block_size %d: must be 0 or a multiple of 32 in [32, 512]", o->block_size);
+    if (o->blocks_per_sm < 0 || o->blocks_per_sm > 1)
+        return fail(VPMC_ERR_ARG, "blocks_per_sm %d: the kernel's shared memory allows one block per SM", o->blocks_per_sm);
+    if (o->chunk < 0 || o->chunk > 4096) return fail(VPMC_ERR_ARG, "chunk %d outside [0, 4096]", o->chunk);
+    if (o->history_cap < 0 || (o->history_cap > 0 && !o->history_out))
+        return fail(VPMC_ERR_ARG, "history_cap > 0 needs history_out");
+    return VPMC_OK;
+}
+
+TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
+{
+    TransportParams p{};
+    p.tables = c->d_tables;
+    p.ct = c->d_ct;
+    p.ctg = c->ctg;
+    p.sg = c->sg;
+    p.same_grid = c->same_grid ? 1 : 0;
+    p.beams = c->d_beams;
+    p.n_beams = kMaxBeams;
+    p.scens = c->d_scens;
+    p.poly = c->d_poly;
+    p.n_poly = c->n_poly;
+    p.raster = c->d_raster;
+    p.items = c->d_items;
+    p.boxes = c->d_boxes;
+    p.counter = c->d_counter;
+    p.stats = c->d_stats;
+    p.status = c->d_status;
+    p.item_flags = c->d_item_flags;
+    p.key0 = (uint32_t)o.seed;
+    p.key1_hi = (uint32_t)(o.seed >> 32);
+    p.mcs = o.mcs;
+    p.straggling = o.straggling;
+    p.nuclear = o.nuclear;
+    p.fscale = std::ldexp(1.0f, o.frac_bits);
+    p.records = reinterpret_cast<HistRecord*>(o.history_out);
+    p.rec_cap = o.history_out ? o.history_cap : 0;
+    return p;
+}
+
+vpmc_status reset_counters(vpmc_ctx* c)
+{
+    CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * kNStats, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    return VPMC_OK;
+}
+
+// Chooses block size, warp aggregation and refill chunk by timing short
+// launches over a prefix of the work (results are discarded).
+vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc_opts& o,
+                     unsigned long long* scratch, size_t scratch_elems)
+{
+    const long long sample = std::min<long long>(p.total, (long long)c->num_sms * 512 * 6);
+    if (sample <= 0) { out->valid = true; return VPMC_OK; }
+    p.total = sample;
+    p.records = nullptr;
+    p.rec_cap = 0;
+    struct Cand { int block, agg, chunk; };
+    std::vector<Cand> cands;
+    for (int block : {256, 384, 512})
+        for (int agg : {0, 1})
+            for (int chunk : {32, 128}) {
+                if (o.block_size && block != o.block_size) continue;
+                if (o.aggregate >= 0 && agg != o.aggregate) continue;
+                if (o.chunk && chunk != o.chunk) continue;
+                cands.push_back({block, agg, chunk});
+            }
+    if (cands.empty()) cands.push_back({o.block_size ? o.block_size : 512, o.aggregate >= 0 ? o.aggregate : 1,
+                                        o.chunk ? o.chunk : 32});
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep)
+        for (const Cand& cd : cands) {
+            vpmc_status st = reset_counters(c);
+            if (st != VPMC_OK) return st;
+            p.aggregate = cd.agg;
+            p.chunk = cd.chunk;
+            CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+            CUDA_TRY(launch_transport(p, c->num_sms, cd.block, c->stream));
+            ++c->launches;
+            CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+            CUDA_TRY(cudaEventSynchronize(c->ev1));
+            float ms = 0.0f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            if (rep == 1 && ms < best) {
+                best = ms;
+                out->block = cd.block;
+                out->aggregate = cd.agg;
+                out->chunk = cd.chunk;
+            }
+        }
+    out->valid = true;
+    if (scratch && scratch_elems)
+        CUDA_TRY(cudaMemsetAsync(scratch, 0, scratch_elems * sizeof(unsigned long long), c->stream));
+    return VPMC_OK;
+}
+
+void resolve_launch(const vpmc_opts& o, const TuneResult& t, int* block, int* agg, int* chunk)
+{
+    *block = o.block_size ? o.block_size : t.block;
+    *agg = o.aggregate >= 0 ? o.aggregate : t.aggregate;
+    *chunk = o.chunk ? o.chunk : t.chunk;
+}
+
+vpmc_status read_stats(vpmc_ctx* c, int frac_bits, vpmc_stats* acc, bool add)
+{
+    unsigned long long h[kNStats];
+    CUDA_TRY(cudaMemcpy(h, c->d_stats, sizeof h, cudaMemcpyDeviceToHost));
+    const double sc = std::ldexp(1.0, -frac_bits);
+    if (!add) *acc = vpmc_stats{};
+    acc->e_dep += h[kStDep] * sc;
+    acc->e_leak += h[kStLeak] * sc;
+    acc->e_rs += h[kStRS] * sc;
+    acc->e_aperture += h[kStAp] * sc;
+    acc->e_nuc += h[kStNuc] * sc;
+    acc->steps += (int64_t)h[kStSteps];
+    acc->errors += (int64_t)h[kStErr];
+    return VPMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vpmc_default_opts(vpmc_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->seed = 1234;
+    o->mcs = 1;
+    o->straggling = 1;
+    o->nuclear = 1;
+    o->frac_bits = 24;
+    o->aggregate = -1;
+}
+
+const char* vpmc_last_error(void) { return g_error.c_str(); }
+
+vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_device, const vpmc_grid* ct,
+                                 const vpmc_hu_curve* curve, const vpmc_grid* dose_grid, void* cuda_stream)
+{
+    g_error.clear();
+    if (!out) return fail(VPMC_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!hu || !ct || !curve || !dose_grid) return fail(VPMC_ERR_ARG, "null argument");
+    for (const vpmc_grid* g : {ct, dose_grid}) {
+        if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0))
+            return fail(VPMC_ERR_ARG, "grid with non-positive size or spacing");
+        if ((long long)g->nx * g->ny * g->nz > (1ll << 31))
+            return fail(VPMC_ERR_ARG, "grid larger than 2^31 voxels");
+    }
+    const double cd[3] = {ct->dx, ct->dy, ct->dz}, sd[3] = {dose_grid->dx, dose_grid->dy, dose_grid->dz};
+    const int cn[3] = {ct->nx, ct->ny, ct->nz}, sn[3] = {dose_grid->nx, dose_grid->ny, dose_grid->nz};
+    for (int k = 0; k < 3; ++k) {
+        const double ext = cn[k] * cd[k];
+        if (std::fabs(sn[k] * sd[k] - ext) > 1e-6 * ext || std::fabs(ct->origin[k] - dose_grid->origin[k]) > 1e-6 * ext)
+            return fail(VPMC_ERR_ARG, "dose grid must share the CT's origin and extent (axis %d)", k);
+    }
+    for (int i = 0; i < 4; ++i)
+        if (!(curve->hu[i + 1] > curve->hu[i])) return fail(VPMC_ERR_ARG, "HU knots must be ascending");
+    for (int i = 0; i < 5; ++i)
+        if (!(curve->density[i] > 0) || !(curve->spr[i] > 0))
+            return fail(VPMC_ERR_ARG, "HU curve densities and SPRs must be positive");
+
+    vpmc_ctx* c = new vpmc_ctx();
+    auto cleanup = [&](vpmc_status st) {
+        vpmc_destroy(c);
+        return st;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return cleanup(fail(VPMC_ERR_CUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if ((size_t)smem_optin < transport_smem_bytes())
+        return cleanup(fail(VPMC_ERR_CUDA, "device allows %d B shared memory per block, kernel needs %zu", smem_optin,
+                            transport_smem_bytes()));
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreate(&c->stream) != cudaSuccess) return cleanup(fail(VPMC_ERR_CUDA, "stream creation"));
+        c->own_stream = true;
+    }
+    c->ctg = to_grid3(*ct);
+    c->sg = to_grid3(*dose_grid);
+    for (int k = 0; k < 3; ++k) { c->ct_spacing[k] = cd[k]; c->sg_spacing[k] = sd[k]; }
+    c->same_grid = true;
+    for (int k = 0; k < 3; ++k) c->same_grid = c->same_grid && cn[k] == sn[k] && cd[k] == sd[k];
+    c->nvox = (long long)sn[0] * sn[1] * sn[2];
+    for (int i = 0; i < 5; ++i) {
+        c->curve15[i] = curve->hu[i];
+        c->curve15[5 + i] = curve->density[i];
+        c->curve15[10 + i] = curve->spr[i];
+    }
+    const long long nct = (long long)cn[0] * cn[1] * cn[2];
+    vpmc_status st = VPMC_OK;
+#define CTX_TRY(expr)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (expr);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return cleanup(fail(e_ == cudaErrorMemoryAllocation ? VPMC_ERR_OOM : VPMC_ERR_CUDA, "%s: %s", #expr, \
+                                cudaGetErrorString(e_)));                                               \
+    } while (0)
+    CTX_TRY(dev_alloc(&c->d_ct, nct));
+    CTX_TRY(cudaMemcpyAsync(c->d_ct, hu, nct * sizeof(int16_t),
+                            hu_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    std::vector<unsigned char> img_bytes(sizeof(TablesImage));
+    TablesImage* img = reinterpret_cast<TablesImage*>(img_bytes.data());
+    build_tables(c->curve15, img);
+    CTX_TRY(dev_alloc(&c->d_tables, 1));
+    CTX_TRY(cudaMemcpyAsync(c->d_tables, img, sizeof(TablesImage), cudaMemcpyHostToDevice, c->stream));
+    CTX_TRY(dev_alloc(&c->d_curve, 15));
+    CTX_TRY(cudaMemcpyAsync(c->d_curve, c->curve15, sizeof(c->curve15), cudaMemcpyHostToDevice, c->stream));
+    CTX_TRY(dev_alloc(&c->d_rho, c->nvox));
+    CTX_TRY(launch_scoring_density(c->d_ct, c->ctg, c->sg, c->d_curve, c->ct_spacing, c->sg_spacing, c->d_rho,
+                                   c->stream));
+    CTX_TRY(dev_alloc(&c->d_beams, kMaxBeams));
+    CTX_TRY(dev_alloc(&c->d_counter, 1));
+    CTX_TRY(dev_alloc(&c->d_stats, kNStats));
+    CTX_TRY(dev_alloc(&c->d_status, 1));
+    CTX_TRY(dev_alloc(&c->d_scens, kMaxScen));
+    CTX_TRY(cudaEventCreate(&c->ev0));
+    CTX_TRY(cudaEventCreate(&c->ev1));
+    CTX_TRY(cudaStreamSynchronize(c->stream));
+#undef CTX_TRY
+    st = upload_beams(c);
+    if (st != VPMC_OK) return cleanup(st);
+    *out = c;
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
+{
+    g_error.clear();
+    if (!c || !b) return fail(VPMC_ERR_ARG, "null argument");
+    if (beam_id < 0 || beam_id >= kMaxBeams) return fail(VPMC_ERR_ARG, "beam_id %d outside [0, %d)", beam_id, kMaxBeams);
+    const double nw = std::sqrt(b->dir[0] * b->dir[0] + b->dir[1] * b->dir[1] + b->dir[2] * b->dir[2]);
+    const double nu = std::sqrt(b->bev_x[0] * b->bev_x[0] + b->bev_x[1] * b->bev_x[1] + b->bev_x[2] * b->bev_x[2]);
+    const double dot = b->dir[0] * b->bev_x[0] + b->dir[1] * b->bev_x[1] + b->dir[2] * b->bev_x[2];
+    if (std::fabs(nw - 1.0) > 1e-6 || std::fabs(nu - 1.0) > 1e-6 || std::fabs(dot) > 1e-6)
+        return fail(VPMC_ERR_ARG, "dir and bev_x must be orthonormal");
+    DevBeam d{};
+    for (int k = 0; k < 3; ++k) {
+        d.w[k] = (float)b->dir[k];
+        d.u[k] = (float)b->bev_x[k];
+        d.iso[k] = (float)b->iso[k];
+    }
+    const double v[3] = {b->dir[1] * b->bev_x[2] - b->dir[2] * b->bev_x[1],
+                         b->dir[2] * b->bev_x[0] - b->dir[0] * b->bev_x[2],
+                         b->dir[0] * b->bev_x[1] - b->dir[1] * b->bev_x[0]};
+    for (int k = 0; k < 3; ++k) d.v[k] = (float)v[k];
+    d.t_src = (float)(-b->source_to_iso_mm);
+    double first_device = 1e300;
+    d.rs = b->rs_present ? 1 : 0;
+    if (d.rs) {
+        if (!(b->rs_wet_mm > 0) || !(b->rs_radius_mm > 0)) return fail(VPMC_ERR_ARG, "range shifter: bad WET or radius");
+        const double thick = b->rs_wet_mm / pmma_stopping_power_ratio(150.0);
+        d.rs_tdn = (float)(-b->rs_down_to_iso_mm);
+        d.rs_tup = (float)(-b->rs_down_to_iso_mm - thick);
+        d.rs_r2 = (float)(b->rs_radius_mm * b->rs_radius_mm);
+        first_device = std::min(first_device, -b->rs_down_to_iso_mm - thick);
+    }
+    d.ap = b->ap_present ? 1 : 0;
+    std::vector<double> poly;
+    std::vector<unsigned char> ras;
+    if (d.ap) {
+        if (!b->poly_xy || b->n_vertices < 3) return fail(VPMC_ERR_ARG, "aperture needs a polygon of >= 3 vertices");
+        if (!(b->ap_thickness_mm > 0)) return fail(VPMC_ERR_ARG, "aperture thickness must be positive");
+        d.ap_tdn = (float)(-b->ap_down_to_iso_mm);
+        d.ap_tup = (float)(-b->ap_down_to_iso_mm - b->ap_thickness_mm);
+        first_device = std::min(first_device, -b->ap_down_to_iso_mm - b->ap_thickness_mm);
+        if (d.rs && -b->rs_down_to_iso_mm > -b->ap_down_to_iso_mm - b->ap_thickness_mm + 1e-9)
+            return fail(VPMC_ERR_ARG, "range shifter must lie upstream of the aperture");
+        poly.assign(b->poly_xy, b->poly_xy + 2 * b->n_vertices);
+        for (double x : poly)
+            if (!std::isfinite(x)) return fail(VPMC_ERR_ARG, "aperture polygon has a non-finite vertex");
+        ras.resize(kRaster * kRaster);
+        build_raster(poly.data(), b->n_vertices, ras.data(), d.ras_lo, d.ras_inv);
+        d.nvert = b->n_vertices;
+    }
+    if (first_device < 1e300 && !(-b->source_to_iso_mm < first_device))
+        return fail(VPMC_ERR_ARG, "source plane must lie upstream of every device");
+    const bool prev_set = c->beam_set[beam_id];
+    const DevBeam prev = c->beams[beam_id];
+    std::vector<double> prev_poly = c->poly[beam_id];
+    std::vector<unsigned char> prev_ras = c->raster[beam_id];
+    c->beams[beam_id] = d;
+    c->poly[beam_id] = poly;
+    c->raster[beam_id] = ras;
+    c->beam_set[beam_id] = true;
+    vpmc_status st = upload_beams(c);
+    if (st != VPMC_OK) {
+        c->beams[beam_id] = prev;
+        c->poly[beam_id] = prev_poly;
+        c->raster[beam_id] = prev_ras;
+        c->beam_set[beam_id] = prev_set;
+        return st;
+    }
+    c->tune_dose.valid = c->tune_im.valid = false;
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, const vpmc_scenario* scen,
+                           const vpmc_opts* opts_in, float* dose_dev, vpmc_stats* stats_out)
+{
+    g_error.clear();
+    if (!c || !dose_dev) return fail(VPMC_ERR_ARG, "null context or dose buffer");
+    const long long launches0 = c->launches;
+    vpmc_opts o;
+    vpmc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    vpmc_status st = check_opts(&o);
+    if (st != VPMC_OK) return st;
+    st = check_spots(c, spots, n_spots);
+    if (st != VPMC_OK) return st;
+    DevScen sc{{0.0f, 0.0f, 0.0f}, 1.0f};
+    if (scen) {
+        if (!(scen->spr_scale > 0)) return fail(VPMC_ERR_ARG, "scenario spr_scale must be positive");
+        for (int k = 0; k < 3; ++k) sc.shift[k] = (float)scen->shift_mm[k];
+        sc.spr_scale = (float)scen->spr_scale;
+    }
+    // work items: one per spot with histories
+    std::vector<DevItem> items;
+    long long total = 0;
+    double qmax = 0.0, e_in = 0.0;
+    const double fs = std::ldexp(1.0, o.frac_bits);
+    for (int i = 0; i < n_spots; ++i) {
+        const vpmc_spot& s = spots[i];
+        if (s.n_hist == 0) continue;
+        DevItem it{};
+        it.hist_off = total;
+        it.E0 = (float)s.energy_mev;
+        it.x = (float)s.x_mm;
+        it.y = (float)s.y_mm;
+        it.sigma = (float)s.sigma_mm;
+        it.div_rad = (float)(s.div_mrad * 1e-3);
+        it.wscale = (float)(s.weight * fs);
+        it.spot = i;
+        it.scen = 0;
+        it.beam = s.beam;
+        it.box = 0;
+        if (!(s.weight >= 0.0)) return fail(VPMC_ERR_ARG, "spot %d: negative weight", i);
+        items.push_back(it);
+        total += s.n_hist;
+        qmax += (double)s.n_hist * s.energy_mev * std::max(s.weight, 1.0) * fs;
+        e_in += (double)s.n_hist * s.energy_mev;
+    }
+    if (qmax >= 9.0e18) return fail(VPMC_ERR_ARG, "fixed-point range exceeded: lower frac_bits or weights");
+    CUDA_TRY(cudaMemsetAsync(dose_dev, 0, c->nvox * sizeof(float), c->stream));
+    if (!c->d_acc) CUDA_TRY(dev_alloc(&c->d_acc, c->nvox));
+    CUDA_TRY(cudaMemsetAsync(c->d_acc, 0, c->nvox * sizeof(unsigned long long), c->stream));
+    vpmc_stats stats{};
+    if (!items.empty()) {
+        // sentinel keeps hist_off lookups in range
+        st = grow(c, &c->d_items, &c->items_cap, items.size());
+        if (st != VPMC_OK) return st;
+        st = grow_boxes(c, 1);
+        if (st != VPMC_OK) return st;
+        st = grow_flags(c, items.size());
+        if (st != VPMC_OK) return st;
+        DevBox box{};
+        box.base = 0;
+        for (int k = 0; k < 3; ++k) { box.lo[k] = 0; box.n[k] = c->sg.n[k]; }
+        CUDA_TRY(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice,
+                                 c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->d_boxes, &box, sizeof box, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->d_scens, &sc, sizeof sc, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->d_item_flags, 0, items.size() * sizeof(int), c->stream));
+        TransportParams p = base_params(c, o);
+        p.items = c->d_items;
+        p.n_items = (int)items.size();
+        p.boxes = c->d_boxes;
+        p.n_scen = 1;
+        p.total = total;
+        p.scratch = c->d_acc;
+        p.item_flags = c->d_item_flags;
+        const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
+        if (want_tune && !c->tune_dose.valid) {
+            st = autotune(c, p, &c->tune_dose, o, c->d_acc, (size_t)c->nvox);
+            if (st != VPMC_OK) return st;
+        }
+        int block, agg, chunk;
+        resolve_launch(o, c->tune_dose, &block, &agg, &chunk);
+        p.aggregate = agg;
+        p.chunk = chunk;
+        st = reset_counters(c);
+        if (st != VPMC_OK) return st;
+        CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+        CUDA_TRY(launch_transport(p, c->num_sms, block, c->stream));
+        ++c->launches;
+        CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    }
+    const double scale = std::ldexp(1.0, -o.frac_bits) * 1.602176634e-10 /
+                         (c->sg_spacing[0] * c->sg_spacing[1] * c->sg_spacing[2] * 1e-3);
+    CUDA_TRY(launch_dose_normalise(c->d_acc, c->d_rho, c->nvox, scale, dose_dev, c->stream));
+    ++c->launches;
+    if (stats_out) {
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (!items.empty()) {
+            st = read_stats(c, o.frac_bits, &stats, false);
+            if (st != VPMC_OK) return st;
+            float ms = 0.0f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            stats.ms = ms;
+            int status = 0;
+            CUDA_TRY(cudaMemcpy(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost));
+            stats.histories = total;
+            stats.e_in = e_in;
+            stats.launches = c->launches - launches0;
+            *stats_out = stats;
+            if (status & 1) return fail(VPMC_ERR_TIMEOUT, "%lld histories reached the iteration cap", (long long)stats.errors);
+        } else {
+            stats.launches = c->launches - launches0;
+            *stats_out = stats;
+        }
+    }
+    return VPMC_OK;
+}
+
+namespace {
+
+struct BoxSpec { int lo[3], n[3]; };
+
+// Axis-aligned box (scoring voxels) that holds the field of beam b in
+// scenario sc: the aperture opening (or the spots' extent) plus a lateral
+// margin, over the grid's whole depth along the beam.
+BoxSpec field_box(vpmc_ctx* c, int b, const vpmc_scenario& sc, const vpmc_spot* spots, int n_spots, double margin)
+{
+    const DevBeam& B = c->beams[b];
+    double a0 = 1e300, a1 = -1e300, b0 = 1e300, b1 = -1e300;
+    if (B.ap) {
+        const std::vector<double>& p = c->poly[b];
+        for (size_t i = 0; i + 1 < p.size(); i += 2) {
+            a0 = std::min(a0, p[i]); a1 = std::max(a1, p[i]);
+            b0 = std::min(b0, p[i + 1]); b1 = std::max(b1, p[i + 1]);
+        }
+    } else {
+        for (int i = 0; i < n_spots; ++i)
+            if (spots[i].beam == b) {
+                const double r = 4.0 * spots[i].sigma_mm;
+                a0 = std::min(a0, spots[i].x_mm - r); a1 = std::max(a1, spots[i].x_mm + r);
+                b0 = std::min(b0, spots[i].y_mm - r); b1 = std::max(b1, spots[i].y_mm + r);
+            }
+    }
+    a0 -= margin; a1 += margin; b0 -= margin; b1 += margin;
+    double lo[3], hi[3], base[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = c->sg.lo[k];
+        hi[k] = c->sg.lo[k] + c->sg.n[k] * c->sg_spacing[k];
+        base[k] = (double)B.iso[k] + sc.shift_mm[k];
+    }
+    // depth range: projections of the grid corners on the beam axis
+    double t0 = 1e300, t1 = -1e300;
+    for (int m = 0; m < 8; ++m) {
+        double t = 0.0;
+        for (int k = 0; k < 3; ++k) t += (((m >> k) & 1 ? hi[k] : lo[k]) - base[k]) * (double)B.w[k];
+        t0 = std::min(t0, t);
+        t1 = std::max(t1, t);
+    }
+    double plo[3] = {1e300, 1e300, 1e300}, phi[3] = {-1e300, -1e300, -1e300};
+    for (int m = 0; m < 8; ++m) {
+        const double a = m & 1 ? a1 : a0, bb = m & 2 ? b1 : b0, t = m & 4 ? t1 : t0;
+        for (int k = 0; k < 3; ++k) {
+            const double x = base[k] + a * B.u[k] + bb * B.v[k] + t * B.w[k];
+            plo[k] = std::min(plo[k], x);
+            phi[k] = std::max(phi[k], x);
+        }
+    }
+    BoxSpec s;
+    for (int k = 0; k < 3; ++k) {
+        int i0 = (int)std::floor((plo[k] - lo[k]) / c->sg_spacing[k]);
+        int i1 = (int)std::ceil((phi[k] - lo[k]) / c->sg_spacing[k]);
+        i0 = std::max(i0, 0);
+        i1 = std::min(i1, c->sg.n[k]);
+        s.lo[k] = i0;
+        s.n[k] = std::max(i1 - i0, 0);
+    }
+    return s;
+}
+
+long long box_elems(const BoxSpec& s) { return (long long)s.n[0] * s.n[1] * s.n[2]; }
+
+}  // namespace
+
+vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, const vpmc_scenario* scen,
+                                  int n_scen, const vpmc_opts* opts_in, float rel_threshold, vpmc_csr* out,
+                                  vpmc_stats* stats_out)
+{
+    g_error.clear();
+    if (!c || !out || !scen || n_scen <= 0) return fail(VPMC_ERR_ARG, "null argument or no scenario");
+    const long long launches0 = c->launches;
+    if (n_scen > kMaxScen) return fail(VPMC_ERR_ARG, "at most %d scenarios per call", kMaxScen);
+    if (!(rel_threshold >= 0.0f && rel_threshold < 1.0f)) return fail(VPMC_ERR_ARG, "rel_threshold outside [0, 1)");
+    for (int s = 0; s < n_scen; ++s) out[s] = vpmc_csr{};
+    vpmc_opts o;
+    vpmc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    vpmc_status st = check_opts(&o);
+    if (st != VPMC_OK) return st;
+    st = check_spots(c, spots, n_spots);
+    if (st != VPMC_OK) return st;
+    for (int i = 1; i < n_spots; ++i)
+        if (spots[i].beam < spots[i - 1].beam) return fail(VPMC_ERR_ARG, "spots must be sorted by beam id");
+    for (int s = 0; s < n_scen; ++s)
+        if (!(scen[s].spr_scale > 0)) return fail(VPMC_ERR_ARG, "scenario %d: spr_scale must be positive", s);
+    const double fs = std::ldexp(1.0, o.frac_bits);
+    for (int i = 0; i < n_spots; ++i)
+        if ((double)spots[i].n_hist * spots[i].energy_mev * fs >= 9.0e18)
+            return fail(VPMC_ERR_ARG, "spot %d: fixed-point range exceeded, lower frac_bits", i);
+
+    // beams in use
+    int nb = 0;
+    for (int i = 0; i < n_spots; ++i) nb = std::max(nb, spots[i].beam + 1);
+    std::vector<int> beam_first(nb, -1), beam_count(nb, 0);
+    for (int i = 0; i < n_spots; ++i) {
+        if (beam_first[spots[i].beam] < 0) beam_first[spots[i].beam] = i;
+        beam_count[spots[i].beam] += 1;
+    }
+    // per-scenario item tables: item j of scenario s = spot j (every spot gets
+    // an item so that the CSR pass can index items by spot)
+    std::vector<DevScen> dscen(n_scen);
+    for (int s = 0; s < n_scen; ++s) {
+        for (int k = 0; k < 3; ++k) dscen[s].shift[k] = (float)scen[s].shift_mm[k];
+        dscen[s].spr_scale = (float)scen[s].spr_scale;
+    }
+    std::vector<BoxSpec> spec((size_t)n_scen * nb);
+    for (int s = 0; s < n_scen; ++s)
+        for (int b = 0; b < nb; ++b)
+            if (beam_count[b]) spec[(size_t)s * nb + b] = field_box(c, b, scen[s], spots, n_spots, 25.0);
+    long long per_scen_elems_max = 0;
+    std::vector<long long> scen_elems(n_scen, 0);
+    for (int s = 0; s < n_scen; ++s) {
+        for (int b = 0; b < nb; ++b) scen_elems[s] += box_elems(spec[(size_t)s * nb + b]) * beam_count[b];
+        per_scen_elems_max = std::max(per_scen_elems_max, scen_elems[s]);
+    }
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const long long rerun_reserve = 32 * c->nvox;   // room for overflow re-runs
+    const long long budget = (long long)((double)(free_b + c->scratch_cap * 8) * 0.70 / 8.0) - rerun_reserve;
+    if (per_scen_elems_max > budget)
+        return fail(VPMC_ERR_OOM, "one scenario needs %.1f GB of column scratch, %.1f GB available",
+                    per_scen_elems_max * 8e-9, budget * 8e-9);
+
+    vpmc_stats stats{};
+    std::vector<double> item_scale(n_spots);
+    const double vol_cm3 = c->sg_spacing[0] * c->sg_spacing[1] * c->sg_spacing[2] * 1e-3;
+    for (int j = 0; j < n_spots; ++j)
+        item_scale[j] = spots[j].n_hist > 0 ? std::ldexp(1.0, -o.frac_bits) * 1.602176634e-10 / vol_cm3 /
+                                                  (double)spots[j].n_hist
+                                            : 0.0;
+    double* d_colmax = nullptr;
+    double* d_item_scale = nullptr;
+    long long* d_rowcnt = nullptr;
+    long long* d_scan_tmp = nullptr;
+    int* d_beam_meta = nullptr;
+    auto release = [&]() {
+        cudaFree(d_colmax); cudaFree(d_item_scale); cudaFree(d_rowcnt); cudaFree(d_scan_tmp); cudaFree(d_beam_meta);
+    };
+#define IM_TRY(expr)                                                                                    \
+    do {                                                                                                \
+        cudaError_t e_ = (expr);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            release();                                                                                  \
+            vpmc_free_csr(out, n_scen);                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? VPMC_ERR_OOM : VPMC_ERR_CUDA, "%s: %s", #expr, \
+                        cudaGetErrorString(e_));                                                        \
+        }                                                                                               \
+    } while (0)
+#define IM_ST(expr)                                                                                     \
+    do {                                                                                                \
+        vpmc_status s_ = (expr);                                                                        \
+        if (s_ != VPMC_OK) { release(); vpmc_free_csr(out, n_scen); return s_; }                        \
+    } while (0)
+    IM_TRY(dev_alloc(&d_colmax, n_spots));
+    IM_TRY(dev_alloc(&d_item_scale, n_spots));
+    IM_TRY(cudaMemcpy(d_item_scale, item_scale.data(), n_spots * sizeof(double), cudaMemcpyHostToDevice));
+    IM_TRY(dev_alloc(&d_rowcnt, c->nvox + 1));
+    IM_TRY(dev_alloc(&d_scan_tmp, scan_tmp_elems(c->nvox + 1)));
+    IM_TRY(dev_alloc(&d_beam_meta, 5 * (size_t)nb + n_spots + 1));
+    IM_TRY(cudaMemcpy(c->d_scens, dscen.data(), n_scen * sizeof(DevScen), cudaMemcpyHostToDevice));
+    float total_ms = 0.0f;
+
+    int s0 = 0;
+    while (s0 < n_scen) {
+        // a wave = consecutive scenarios whose column scratch fits the budget
+        int s1 = s0;
+        long long wave_elems = 0;
+        while (s1 < n_scen && wave_elems + scen_elems[s1] <= budget) wave_elems += scen_elems[s1++];
+        const int ns = s1 - s0;
+        // items and boxes of the wave: items ordered (scenario, spot)
+        std::vector<DevItem> items((size_t)ns * n_spots);
+        std::vector<DevBox> boxes;
+        std::vector<int> box_of((size_t)ns * nb, -1);
+        long long base = 0;
+        for (int s = s0; s < s1; ++s)
+            for (int b = 0; b < nb; ++b) {
+                if (!beam_count[b]) continue;
+                const BoxSpec& sp = spec[(size_t)s * nb + b];
+                box_of[(size_t)(s - s0) * nb + b] = (int)boxes.size();
+                DevBox bx{};
+                bx.base = base;
+                for (int k = 0; k < 3; ++k) { bx.lo[k] = sp.lo[k]; bx.n[k] = sp.n[k]; }
+                boxes.push_back(bx);
+                // one box per (scenario, beam); each item gets its own copy of the
+                // box's shape at its own base offset
+                base += box_elems(sp) * beam_count[b];
+            }
+        // per-item boxes (distinct bases, shared shapes)
+        std::vector<DevBox> item_boxes;
+        item_boxes.reserve(items.size() + 64);
+        long long total = 0;
+        for (int s = s0; s < s1; ++s) {
+            std::vector<long long> next_base(nb, 0);
+            for (int b = 0; b < nb; ++b)
+                if (box_of[(size_t)(s - s0) * nb + b] >= 0) next_base[b] = boxes[box_of[(size_t)(s - s0) * nb + b]].base;
+            for (int j = 0; j < n_spots; ++j) {
+                const vpmc_spot& sp = spots[j];
+                DevItem it{};
+                it.hist_off = total;
+                it.E0 = (float)sp.energy_mev;
+                it.x = (float)sp.x_mm;
+                it.y = (float)sp.y_mm;
+                it.sigma = (float)sp.sigma_mm;
+                it.div_rad = (float)(sp.div_mrad * 1e-3);
+                it.wscale = (float)fs;
+                it.spot = j;
+                it.scen = s;
+                it.beam = sp.beam;
+                DevBox bx = boxes[box_of[(size_t)(s - s0) * nb + sp.beam]];
+                bx.base = next_base[sp.beam];
+                next_base[sp.beam] += box_elems(spec[(size_t)s * nb + sp.beam]);
+                it.box = (int)item_boxes.size();
+                item_boxes.push_back(bx);
+                items[(size_t)(s - s0) * n_spots + j] = it;
+                total += sp.n_hist;
+            }
+        }
+        const long long main_elems = base;
+        // the transport kernel needs items with histories in hist_off order;
+        // zero-history items share the next item's offset and are never found
+        IM_ST(grow(c, &c->d_items, &c->items_cap, items.size()));
+        IM_ST(grow_boxes(c, item_boxes.size() + 64));
+        IM_ST(grow_flags(c, items.size()));
+        IM_ST(grow_scratch(c, (size_t)(main_elems + rerun_reserve)));
+        IM_TRY(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice,
+                               c->stream));
+        IM_TRY(cudaMemcpyAsync(c->d_boxes, item_boxes.data(), item_boxes.size() * sizeof(DevBox),
+                               cudaMemcpyHostToDevice, c->stream));
+        TransportParams p = base_params(c, o);
+        p.items = c->d_items;
+        p.n_items = (int)items.size();
+        p.boxes = c->d_boxes;
+        p.n_scen = n_scen;
+        p.total = total;
+        p.scratch = c->d_scratch;
+        p.item_flags = c->d_item_flags;
+        p.records = nullptr;
+        p.rec_cap = 0;
+        const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
+        if (want_tune && !c->tune_im.valid) IM_ST(autotune(c, p, &c->tune_im, o, nullptr, 0));
+        int block, agg, chunk;
+        resolve_launch(o, c->tune_im, &block, &agg, &chunk);
+        p.aggregate = agg;
+        p.chunk = chunk;
+        // the wave's zeroing and transport launch, captured as one CUDA graph
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        IM_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(c->d_scratch, 0, (size_t)main_elems * sizeof(unsigned long long), c->stream);
+        cudaMemsetAsync(c->d_item_flags, 0, items.size() * sizeof(int), c->stream);
+        cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
+        cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * kNStats, c->stream);
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        cudaEventRecord(c->ev0, c->stream);
+        launch_transport(p, c->num_sms, block, c->stream);
+        ++c->launches;
+        cudaEventRecord(c->ev1, c->stream);
+        IM_TRY(cudaStreamEndCapture(c->stream, &graph));
+        cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
+        if (ge == cudaSuccess) ge = cudaGraphLaunch(exec, c->stream);
+        if (ge == cudaSuccess) ge = cudaStreamSynchronize(c->stream);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        IM_TRY(ge);
+        float ms = 0.0f;
+        IM_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        total_ms += ms;
+        IM_ST(read_stats(c, o.frac_bits, &stats, true));
+        int status = 0;
+        IM_TRY(cudaMemcpy(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost));
+        if (status & 1) {
+            release();
+            vpmc_free_csr(out, n_scen);
+            return fail(VPMC_ERR_TIMEOUT, "histories reached the iteration cap");
+        }
+        // items whose deposits left their box: re-run them into full-grid boxes
+        std::vector<int> flags(items.size());
+        IM_TRY(cudaMemcpy(flags.data(), c->d_item_flags, flags.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        std::vector<int> ovf;
+        for (size_t i = 0; i < flags.size(); ++i)
+            if (flags[i]) ovf.push_back((int)i);
+        if (!ovf.empty()) {
+            if ((long long)ovf.size() * c->nvox > rerun_reserve)
+                IM_ST(grow_scratch(c, (size_t)(main_elems + (long long)ovf.size() * c->nvox)));
+            std::vector<DevItem> rr;
+            long long rtotal = 0;
+            for (size_t r = 0; r < ovf.size(); ++r) {
+                DevItem it = items[ovf[r]];
+                DevBox bx{};
+                bx.base = main_elems + (long long)r * c->nvox;
+                for (int k = 0; k < 3; ++k) { bx.lo[k] = 0; bx.n[k] = c->sg.n[k]; }
+                it.box = (int)item_boxes.size();
+                item_boxes.push_back(bx);
+                items[ovf[r]].box = it.box;   // the CSR pass reads the re-run column
+                it.hist_off = rtotal;
+                rtotal += spots[it.spot].n_hist;
+                rr.push_back(it);
+            }
+            IM_ST(grow_boxes(c, item_boxes.size()));
+            IM_TRY(cudaMemcpy(c->d_boxes, item_boxes.data(), item_boxes.size() * sizeof(DevBox), cudaMemcpyHostToDevice));
+            DevItem* d_rr = nullptr;
+            IM_TRY(dev_alloc(&d_rr, rr.size()));
+            cudaError_t e = cudaMemcpy(d_rr, rr.data(), rr.size() * sizeof(DevItem), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(c->d_scratch + main_elems, 0, ovf.size() * (size_t)c->nvox * 8, c->stream);
+            TransportParams q = p;
+            q.items = d_rr;
+            q.n_items = (int)rr.size();
+            q.total = rtotal;
+            if (e == cudaSuccess && reset_counters(c) != VPMC_OK) e = cudaErrorUnknown;
+            if (e == cudaSuccess) e = launch_transport(q, c->num_sms, block, c->stream);
+            ++c->launches;
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            cudaFree(d_rr);
+            IM_TRY(e);
+            IM_TRY(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice));
+        }
+        // CSR per scenario
+        for (int s = s0; s < s1; ++s) {
+            const int first = (s - s0) * n_spots;
+            IM_TRY(launch_column_max(c->d_scratch, c->d_items, c->d_boxes, c->d_rho, c->sg, first, n_spots, d_colmax,
+                                     c->stream));
+            ++c->launches;
+            // beam tables and overflowed items of this scenario
+            std::vector<int> meta(5 * (size_t)nb + n_spots + 1, 0);
+            int* m_first = meta.data();
+            int* m_count = m_first + nb;
+            int* m_box = m_count + nb;
+            int* m_ofirst = m_box + nb;
+            int* m_ocount = m_ofirst + nb;
+            int* m_olist = m_ocount + nb;
+            int no = 0;
+            for (int b = 0; b < nb; ++b) {
+                m_first[b] = std::max(beam_first[b], 0);
+                m_count[b] = beam_count[b];
+                m_box[b] = box_of[(size_t)(s - s0) * nb + b] >= 0 ? items[(size_t)first + m_first[b]].box : 0;
+                m_ofirst[b] = no;
+                for (int j = 0; j < beam_count[b]; ++j) {
+                    const int it = first + beam_first[b] + j;
+                    if (flags[it]) m_olist[no++] = beam_first[b] + j;
+                }
+                m_ocount[b] = no - m_ofirst[b];
+            }
+            // a beam's box: any of its non-overflowed items (all share its shape)
+            for (int b = 0; b < nb; ++b)
+                for (int j = 0; j < beam_count[b]; ++j)
+                    if (!flags[first + beam_first[b] + j]) { m_box[b] = items[(size_t)first + beam_first[b] + j].box; break; }
+            IM_TRY(cudaMemcpy(d_beam_meta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CsrBuildParams cp{};
+            cp.scratch = c->d_scratch;
+            cp.items = c->d_items + first;
+            cp.boxes = c->d_boxes;
+            cp.rho = c->d_rho;
+            cp.colmax = d_colmax;
+            cp.beam_first = d_beam_meta;
+            cp.beam_count = d_beam_meta + nb;
+            cp.beam_box = d_beam_meta + 2 * nb;
+            cp.ovf_beam_first = d_beam_meta + 3 * nb;
+            cp.ovf_beam_count = d_beam_meta + 4 * nb;
+            cp.ovf_items = d_beam_meta + 5 * nb;
+            cp.n_beams = nb;
+            cp.sg = c->sg;
+            cp.nvox = c->nvox;
+            cp.rel_threshold = rel_threshold;
+            cp.item_scale = d_item_scale;
+            cp.row_count = d_rowcnt;
+            IM_TRY(launch_csr_pass(cp, 0, c->stream));
+            ++c->launches;
+            vpmc_csr& csr = out[s];
+            csr.n_rows = c->nvox;
+            csr.n_cols = n_spots;
+            IM_TRY(dev_alloc(&csr.row_ptr, c->nvox + 1));
+            IM_TRY(cudaMemsetAsync(d_rowcnt + c->nvox, 0, sizeof(long long), c->stream));
+            IM_TRY(launch_exclusive_scan(d_rowcnt, reinterpret_cast<long long*>(csr.row_ptr), c->nvox + 1, d_scan_tmp,
+                                          c->stream));
+            c->launches += scan_launches(c->nvox + 1);
+            long long nnz = 0;
+            IM_TRY(cudaMemcpyAsync(&nnz, csr.row_ptr + c->nvox, sizeof nnz, cudaMemcpyDeviceToHost, c->stream));
+            IM_TRY(cudaStreamSynchronize(c->stream));
+            csr.nnz = nnz;
+            IM_TRY(dev_alloc(&csr.col, nnz));
+            IM_TRY(dev_alloc(&csr.val, nnz));
+            cp.row_ptr = reinterpret_cast<const long long*>(csr.row_ptr);
+            cp.col = csr.col;
+            cp.val = csr.val;
+            IM_TRY(launch_csr_pass(cp, 1, c->stream));
+            ++c->launches;
+        }
+        IM_TRY(cudaStreamSynchronize(c->stream));
+        s0 = s1;
+    }
+    release();
+#undef IM_TRY
+#undef IM_ST
+    if (stats_out) {
+        double e_in = 0.0;
+        long long h = 0;
+        for (int j = 0; j < n_spots; ++j) {
+            e_in += (double)spots[j].n_hist * spots[j].energy_mev;
+            h += spots[j].n_hist;
+        }
+        stats.e_in = e_in * n_scen;
+        stats.histories = h * n_scen;
+        stats.ms = total_ms;
+        stats.launches = c->launches - launches0;
+        *stats_out = stats;
+    }
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_free_csr(vpmc_csr* csr, int n)
+{
+    if (!csr || n < 0) return fail(VPMC_ERR_ARG, "null csr array");
+    for (int i = 0; i < n; ++i) {
+        cudaFree(csr[i].row_ptr);
+        cudaFree(csr[i].col);
+        cudaFree(csr[i].val);
+        csr[i] = vpmc_csr{};
+    }
+    return VPMC_OK;
+}
+
+void vpmc_destroy(vpmc_ctx* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_ct);
+    cudaFree(c->d_tables);
+    cudaFree(c->d_curve);
+    cudaFree(c->d_rho);
+    cudaFree(c->d_acc);
+    cudaFree(c->d_beams);
+    cudaFree(c->d_poly);
+    cudaFree(c->d_raster);
+    cudaFree(c->d_counter);
+    cudaFree(c->d_stats);
+    cudaFree(c->d_status);
+    cudaFree(c->d_scens);
+    cudaFree(c->d_items);
+    cudaFree(c->d_boxes);
+    cudaFree(c->d_item_flags);
+    cudaFree(c->d_scratch);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+// Finalisation kernels: scoring-voxel density, fixed-point -> dose, and the
+// influence-matrix columns -> CSR (paper Sec. 2.C: sparse matrix storage).
+//
+// FP64 appears only here (dose normalisation and thresholds); transport is FP32.
+#include "vpmc_internal.cuh"
+
+namespace vpmc {
+namespace {
+
+__device__ double curve_density(const double* c, double hu)
+{
+    const double h = fmin(fmax(hu, c[0]), 3071.0);
+    int s = 0;
+    while (s < 3 && h >= c[s + 1]) ++s;
+    const double t = (h - c[s]) / (c[s + 1] - c[s]);
+    return c[5 + s] + t * (c[5 + s + 1] - c[5 + s]);
+}
+
+// Volume-weighted mean density of the CT voxels overlapping each scoring voxel.
+__global__ void k_scoring_density(const int16_t* __restrict__ ct, Grid3 ctg, Grid3 sg, const double* __restrict__ c15,
+                                  double ctd0, double ctd1, double ctd2, double sgd0, double sgd1, double sgd2,
+                                  double* __restrict__ rho_out)
+{
+    const long long nv = (long long)sg.n[0] * sg.n[1] * sg.n[2];
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const double dct[3] = {ctd0, ctd1, ctd2}, dsg[3] = {sgd0, sgd1, sgd2};
+    const int S[3] = {(int)(v % sg.n[0]), (int)((v / sg.n[0]) % sg.n[1]), (int)(v / ((long long)sg.n[0] * sg.n[1]))};
+    int c0[3], c1[3];
+    for (int k = 0; k < 3; ++k) {
+        c0[k] = max((int)floor(S[k] * dsg[k] / dct[k]), 0);
+        c1[k] = min((int)ceil((S[k] + 1) * dsg[k] / dct[k]), ctg.n[k]);
+    }
+    double acc = 0.0, vol = 0.0;
+    for (int z = c0[2]; z < c1[2]; ++z)
+        for (int y = c0[1]; y < c1[1]; ++y)
+            for (int x = c0[0]; x < c1[0]; ++x) {
+                const int C[3] = {x, y, z};
+                double ov = 1.0;
+                for (int k = 0; k < 3; ++k) {
+                    const double a = S[k] * dsg[k], b = (S[k] + 1) * dsg[k];
+                    const double lo = fmax(a, C[k] * dct[k]), hi = fmin(b, (C[k] + 1) * dct[k]);
+                    ov *= fmax(hi - lo, 0.0);
+                }
+                if (ov <= 0.0) continue;
+                const double rho = curve_density(c15, (double)ct[x + (long long)ctg.n[0] * (y + (long long)ctg.n[1] * z)]);
+                acc += ov * rho;
+                vol += ov;
+            }
+    rho_out[v] = acc / vol;
+}
+
+__global__ void k_dose_normalise(const unsigned long long* __restrict__ acc, const double* __restrict__ rho,
+                                 long long nvox, double scale, float* __restrict__ dose)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x)
+        dose[v] = (float)((double)acc[v] * scale / rho[v]);
+}
+
+__device__ __forceinline__ long long box_local(const DevBox& b, int x, int y, int z)
+{
+    const int lx = x - b.lo[0], ly = y - b.lo[1], lz = z - b.lo[2];
+    if (lx < 0 || ly < 0 || lz < 0 || lx >= b.n[0] || ly >= b.n[1] || lz >= b.n[2]) return -1;
+    return lx + (long long)b.n[0] * (ly + (long long)b.n[1] * lz);
+}
+
+// One block per item: maximum over the item's box of q / rho.
+__global__ void k_column_max(const unsigned long long* __restrict__ scratch, const DevItem* __restrict__ items,
+                             const DevBox* __restrict__ boxes, const double* __restrict__ rho, Grid3 sg,
+                             int first_item, double* __restrict__ colmax)
+{
+    const int it = first_item + blockIdx.x;
+    const DevBox b = boxes[items[it].box];
+    const long long n = (long long)b.n[0] * b.n[1] * b.n[2];
+    double m = 0.0;
+    for (long long l = threadIdx.x; l < n; l += blockDim.x) {
+        const unsigned long long q = scratch[b.base + l];
+        if (q == 0ull) continue;
+        const int x = b.lo[0] + (int)(l % b.n[0]);
+        const int y = b.lo[1] + (int)((l / b.n[0]) % b.n[1]);
+        const int z = b.lo[2] + (int)(l / ((long long)b.n[0] * b.n[1]));
+        m = fmax(m, (double)q / rho[x + (long long)sg.n[0] * (y + (long long)sg.n[1] * z)]);
+    }
+    __shared__ double red[32];
+    for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) colmax[blockIdx.x] = m;
+    }
+}
+
+// One thread per scoring voxel (row).  Items are visited beam by beam and, in
+// a beam, in spot order, so a row's entries come out sorted by column.  Items
+// whose deposits overflowed the beam's box were re-run into full-grid boxes;
+// for voxels outside the beam box only those are visited.
+__global__ void k_csr_rows(const CsrBuildParams p, int fill)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= p.nvox) return;
+    const int x = (int)(v % p.sg.n[0]);
+    const int y = (int)((v / p.sg.n[0]) % p.sg.n[1]);
+    const int z = (int)(v / ((long long)p.sg.n[0] * p.sg.n[1]));
+    const double inv_rho = 1.0 / p.rho[v];
+    long long count = 0;
+    long long pos = fill ? p.row_ptr[v] : 0;
+    for (int b = 0; b < p.n_beams; ++b) {
+        const int cnt = p.beam_count[b];
+        if (cnt == 0) continue;
+        const bool in_box = box_local(p.boxes[p.beam_box[b]], x, y, z) >= 0;
+        const int n_iter = in_box ? cnt : p.ovf_beam_count[b];
+        for (int t = 0; t < n_iter; ++t) {
+            const int it = in_box ? p.beam_first[b] + t : p.ovf_items[p.ovf_beam_first[b] + t];
+            const DevItem I = p.items[it];
+            const long long l = box_local(p.boxes[I.box], x, y, z);
+            if (l < 0) continue;
+            const unsigned long long q = p.scratch[p.boxes[I.box].base + l];
+            if (q == 0ull) continue;
+            const double r = (double)q * inv_rho;
+            if (r < p.rel_threshold * p.colmax[it]) continue;
+            if (fill) {
+                p.col[pos] = I.spot;
+                p.val[pos] = (float)(r * p.item_scale[it]);
+                ++pos;
+            } else {
+                ++count;
+            }
+        }
+    }
+    if (!fill) p.row_count[v] = count;
+}
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+
+// Exclusive scan of each 4096-element tile; tile totals to block_sums.
+__global__ void k_scan_tiles(const long long* __restrict__ in, long long* __restrict__ out, long long n,
+                             long long* __restrict__ block_sums)
+{
+    __shared__ long long warp_tot[32];
+    const long long base = (long long)blockIdx.x * kScanBlock * kScanItems + (long long)threadIdx.x * kScanItems;
+    long long v[kScanItems];
+    long long run = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        run += v[i];
+    }
+    // inclusive warp scan of per-thread totals
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < (kScanBlock >> 5) ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        warp_tot[lane] = w;   // inclusive
+    }
+    __syncthreads();
+    long long excl = inc - run + (warp > 0 ? warp_tot[warp - 1] : 0);
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = excl;
+        excl += v[i];
+    }
+    if (threadIdx.x == kScanBlock - 1) block_sums[blockIdx.x] = excl;
+}
+
+__global__ void k_scan_add(long long* __restrict__ out, long long n, const long long* __restrict__ offsets)
+{
+    const long long base = (long long)blockIdx.x * kScanBlock * kScanItems;
+    const long long add = offsets[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanBlock * kScanItems; i += kScanBlock)
+        if (base + i < n) out[base + i] += add;
+}
+
+}  // namespace
+
+cudaError_t launch_scoring_density(const int16_t* ct, Grid3 ctg, Grid3 sg, const double* curve15_dev,
+                                   const double ct_spacing[3], const double sg_spacing[3], double* rho_out,
+                                   cudaStream_t s)
+{
+    const long long nv = (long long)sg.n[0] * sg.n[1] * sg.n[2];
+    const int block = 256;
+    const long long grid = (nv + block - 1) / block;
+    k_scoring_density<<<(unsigned)grid, block, 0, s>>>(ct, ctg, sg, curve15_dev, ct_spacing[0], ct_spacing[1],
+                                                        ct_spacing[2], sg_spacing[0], sg_spacing[1], sg_spacing[2],
+                                                        rho_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dose_normalise(const unsigned long long* acc, const double* rho, long long nvox, double scale,
+                                  float* dose, cudaStream_t s)
+{
+    const int block = 256;
+    long long grid = (nvox + block - 1) / block;
+    if (grid > 152 * 64) grid = 152 * 64;
+    k_dose_normalise<<<(unsigned)grid, block, 0, s>>>(acc, rho, nvox, scale, dose);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_column_max(const unsigned long long* scratch, const DevItem* items, const DevBox* boxes,
+                              const double* rho, const Grid3 sg, int first_item, int n_items, double* colmax,
+                              cudaStream_t s)
+{
+    if (n_items <= 0) return cudaSuccess;
+    k_column_max<<<n_items, 256, 0, s>>>(scratch, items, boxes, rho, sg, first_item, colmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_pass(const CsrBuildParams& p, int fill, cudaStream_t s)
+{
+    const int block = 128;
+    const long long grid = (p.nvox + block - 1) / block;
+    k_csr_rows<<<(unsigned)grid, block, 0, s>>>(p, fill);
+    return cudaGetLastError();
+}
+
+int scan_launches(long long n)
+{
+    const long long tile = (long long)kScanBlock * kScanItems;
+    const long long nb = (n + tile - 1) / tile;
+    if (nb <= 0) return 0;
+    if (nb == 1) return 1;
+    return 2 + scan_launches(nb);
+}
+
+size_t scan_tmp_elems(long long n)
+{
+    size_t total = 0;
+    const long long tile = (long long)kScanBlock * kScanItems;
+    while (n > 1) {
+        const long long nb = (n + tile - 1) / tile;
+        total += (size_t)(2 * nb + 1);
+        n = nb;
+    }
+    return total + 2;
+}
+
+// Exclusive scan of n int64 values (out may not alias in); out[n] is not written.
+cudaError_t launch_exclusive_scan(const long long* in, long long* out, long long n, long long* tmp, cudaStream_t s)
+{
+    const long long tile = (long long)kScanBlock * kScanItems;
+    const long long nb = (n + tile - 1) / tile;
+    if (nb <= 0) return cudaSuccess;
+    long long* sums = tmp;
+    long long* sums_scan = tmp + nb;
+    k_scan_tiles<<<(unsigned)nb, kScanBlock, 0, s>>>(in, out, n, sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nb == 1) return e;
+    e = launch_exclusive_scan(sums, sums_scan, nb, tmp + 2 * nb + 1, s);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(out, n, sums_scan);
+    return cudaGetLastError();
+}
+
+}  // namespace vpmc

@@ -1,0 +1,190 @@
+// Host-side construction of the transport tables (FP64, rounded to FP32 on
+// upload) and of the aperture classification raster.
+//
+// Stopping power: Bethe-Bloch mass electronic stopping power without shell or
+// density-effect corrections and with the full maximum energy transfer.
+// Residual range R(E_k) on the 0.1 MeV grid: integral of 1/S from the 0.5 MeV
+// transport cut-off, composite Simpson on a 0.001 MeV sub-grid.  E(R) on a
+// uniform grid of 4096 residual ranges: inverse of the piecewise-linear R(E).
+// Units: R in mm * g/cc (areal range in g/cm^2 times 10).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tables.h"
+
+namespace vpmc {
+namespace {
+
+struct MaterialData {
+    double z_over_a, mean_excitation_mev, density, radiation_length_gcm2;
+};
+
+// water (patient media, scaled by SPR), PMMA (range shifter), brass 63/37 Cu/Zn
+constexpr MaterialData kMaterials[kNMat] = {
+    {0.555087, 75.0e-6, 1.00, 36.08},
+    {0.539369, 74.0e-6, 1.19, 40.55},
+    {0.4573, 330.0e-6, 8.53, 12.9},
+};
+
+constexpr double kKBethe = 0.307075;      // MeV cm^2 / mol
+constexpr double kElectronMass = 0.51099895;
+constexpr double kProtonMass = 938.272;
+constexpr double kCutoff = 0.5;
+
+double bethe_mass_stopping_power(const MaterialData& m, double kinetic)
+{
+    const double gamma = 1.0 + kinetic / kProtonMass;
+    const double beta_sq = 1.0 - 1.0 / (gamma * gamma);
+    const double bg_sq = beta_sq * gamma * gamma;
+    const double mass_ratio = kElectronMass / kProtonMass;
+    const double t_max = 2.0 * kElectronMass * bg_sq / (1.0 + 2.0 * gamma * mass_ratio + mass_ratio * mass_ratio);
+    const double log_arg = 2.0 * kElectronMass * bg_sq * t_max /
+                           (m.mean_excitation_mev * m.mean_excitation_mev);
+    return kKBethe * m.z_over_a / beta_sq * (0.5 * std::log(log_arg) - beta_sq);
+}
+
+// integral of 10 / S over [a, b] by composite Simpson with `panels` (even) panels
+double range_increment(const MaterialData& m, double a, double b, int panels)
+{
+    const double h = (b - a) / panels;
+    double acc = 10.0 / bethe_mass_stopping_power(m, a) + 10.0 / bethe_mass_stopping_power(m, b);
+    for (int i = 1; i < panels; ++i) {
+        const double w = (i % 2 == 1) ? 4.0 : 2.0;
+        acc += w * 10.0 / bethe_mass_stopping_power(m, a + i * h);
+    }
+    return acc * h / 3.0;
+}
+
+void build_material(const MaterialData& m, std::vector<double>& range, std::vector<double>& energy, double& d_range)
+{
+    range.assign(kNE, 0.0);
+    for (int k = 1; k < kNE; ++k) {
+        const double upper = 0.1 * k;
+        if (upper <= kCutoff) continue;                 // zero range below the cut-off
+        const double lower = std::max(0.1 * (k - 1), kCutoff);
+        range[k] = range[k - 1] + range_increment(m, lower, upper, 100);
+    }
+    energy.assign(kNR, 0.0);
+    d_range = range[kNE - 1] / (kNR - 1);
+    int k = 0;
+    for (int j = 0; j < kNR; ++j) {
+        if (j == kNR - 1) { energy[j] = 0.1 * (kNE - 1); break; }
+        const double r = j * d_range;
+        if (r <= 0.0) { energy[j] = kCutoff; continue; }
+        while (k + 1 < kNE - 1 && range[k + 1] < r) ++k;
+        const double e_lo = std::max(0.1 * k, kCutoff);
+        const double e_hi = 0.1 * (k + 1);
+        energy[j] = e_lo + (r - range[k]) / (range[k + 1] - range[k]) * (e_hi - e_lo);
+    }
+}
+
+void curve_props(const double* c15, double hu, double* rho, double* spr)
+{
+    const double* knot = c15;
+    const double* dens = c15 + 5;
+    const double* ratio = c15 + 10;
+    const double h = std::min(std::max(hu, knot[0]), 3071.0);
+    int seg = 0;
+    while (seg < 3 && h >= knot[seg + 1]) ++seg;
+    const double t = (h - knot[seg]) / (knot[seg + 1] - knot[seg]);
+    *rho = dens[seg] + t * (dens[seg + 1] - dens[seg]);
+    *spr = ratio[seg] + t * (ratio[seg + 1] - ratio[seg]);
+}
+
+bool segment_hits_box(double ax, double ay, double bx, double by, double x0, double y0, double x1, double y1)
+{
+    // Liang-Barsky clip of segment a->b against the box [x0,x1] x [y0,y1]
+    double t0 = 0.0, t1 = 1.0;
+    const double dx = bx - ax, dy = by - ay;
+    const double p[4] = {-dx, dx, -dy, dy};
+    const double q[4] = {ax - x0, x1 - ax, ay - y0, y1 - ay};
+    for (int i = 0; i < 4; ++i) {
+        if (p[i] == 0.0) {
+            if (q[i] < 0.0) return false;
+        } else {
+            const double t = q[i] / p[i];
+            if (p[i] < 0.0) t0 = std::max(t0, t);
+            else t1 = std::min(t1, t);
+            if (t0 > t1) return false;
+        }
+    }
+    return true;
+}
+
+bool crossing_number_inside(const double* xy, int n, double x, double y)
+{
+    bool inside = false;
+    for (int i = 0, j = n - 1; i < n; j = i++) {
+        const double xi = xy[2 * i], yi = xy[2 * i + 1], xj = xy[2 * j], yj = xy[2 * j + 1];
+        if ((yi > y) != (yj > y) && x < xi + (y - yi) * (xj - xi) / (yj - yi)) inside = !inside;
+    }
+    return inside;
+}
+
+}  // namespace
+
+double pmma_stopping_power_ratio(double kinetic)
+{
+    return bethe_mass_stopping_power(kMaterials[kPMMA], kinetic) * kMaterials[kPMMA].density /
+           bethe_mass_stopping_power(kMaterials[kWater], kinetic);
+}
+
+void build_tables(const double* curve15, TablesImage* img)
+{
+    std::memset(img, 0, sizeof(TablesImage));
+    for (int mat = 0; mat < kNMat; ++mat) {
+        std::vector<double> range, energy;
+        double d_range = 0.0;
+        build_material(kMaterials[mat], range, energy, d_range);
+        for (int k = 0; k < kNE; ++k) img->R[mat][k] = (float)range[k];
+        for (int k = kNE; k < kNEPad; ++k) img->R[mat][k] = (float)range[kNE - 1];
+        for (int j = 0; j < kNR; ++j) img->Einv[mat][j] = (float)energy[j];
+        img->mat[mat].za = (float)kMaterials[mat].z_over_a;
+        img->mat[mat].rho = (float)kMaterials[mat].density;
+        img->mat[mat].x0_mmgcc = (float)(kMaterials[mat].radiation_length_gcm2 * 10.0);
+        img->mat[mat].inv_dR = (float)(1.0 / d_range);
+    }
+    for (int i = 0; i < kNHU; ++i) {
+        double rho, spr;
+        curve_props(curve15, (double)(kHULo + i), &rho, &spr);
+        img->hu[i] = make_float2((float)rho, (float)spr);
+    }
+}
+
+void build_raster(const double* xy, int n, unsigned char* cells, float lo[2], float inv[2])
+{
+    double xmin = xy[0], xmax = xy[0], ymin = xy[1], ymax = xy[1];
+    for (int i = 1; i < n; ++i) {
+        xmin = std::min(xmin, xy[2 * i]); xmax = std::max(xmax, xy[2 * i]);
+        ymin = std::min(ymin, xy[2 * i + 1]); ymax = std::max(ymax, xy[2 * i + 1]);
+    }
+    // cover the polygon with a margin so that every point outside the raster is
+    // outside the polygon
+    const double pad = 0.02 * std::max(xmax - xmin, ymax - ymin) + 0.1;
+    xmin -= pad; xmax += pad; ymin -= pad; ymax += pad;
+    const double cw = (xmax - xmin) / kRaster, ch = (ymax - ymin) / kRaster;
+    lo[0] = (float)xmin; lo[1] = (float)ymin;
+    inv[0] = (float)(1.0 / cw); inv[1] = (float)(1.0 / ch);
+    // FP32 placement of a point can move it by a few ulps across a cell border,
+    // so a cell is classified only if no edge comes within eps of it
+    const double eps = 1e-3 * std::max(cw, ch) + 1e-4 * (std::fabs(xmin) + std::fabs(ymin) + 1.0);
+    for (int cy = 0; cy < kRaster; ++cy)
+        for (int cx = 0; cx < kRaster; ++cx) {
+            const double x0 = xmin + cx * cw - eps, x1 = xmin + (cx + 1) * cw + eps;
+            const double y0 = ymin + cy * ch - eps, y1 = ymin + (cy + 1) * ch + eps;
+            bool edge = false;
+            for (int i = 0; i < n && !edge; ++i) {
+                const int j = (i + 1) % n;
+                edge = segment_hits_box(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1], x0, y0, x1, y1);
+            }
+            unsigned char c = 2;
+            if (!edge) c = crossing_number_inside(xy, n, xmin + (cx + 0.5) * cw, ymin + (cy + 0.5) * ch) ? 1 : 0;
+            cells[cy * kRaster + cx] = c;
+        }
+}
+
+void hu_curve_props(const double* curve15, double hu, double* rho, double* spr) { curve_props(curve15, hu, rho, spr); }
+
+}  // namespace vpmc

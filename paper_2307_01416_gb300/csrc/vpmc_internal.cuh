@@ -1,0 +1,178 @@
+// Internal types of the GB300 transport library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vpmc {
+
+// Physics tables (built in FP64 on the host, stored FP32; staged in shared memory).
+constexpr int kNE = 2501;            // E_k = 0.1 k MeV, k = 0..2500
+constexpr int kNEPad = 2504;         // row stride (16-byte multiple)
+constexpr int kNR = 4096;            // uniform residual-range grid
+constexpr int kNMat = 3;             // 0 water (patient media, SPR-scaled), 1 PMMA, 2 brass
+constexpr int kHULo = -1024;
+constexpr int kNHU = 4096;           // HU -1024..3071
+constexpr int kMaxBeams = 16;
+constexpr int kMaxScen = 64;
+constexpr int kMaxPolyVerts = 1024;
+constexpr int kRaster = 64;          // BEV classification raster per beam (cells per side)
+constexpr float kEcut = 0.5f;        // MeV
+constexpr int kMaxIter = 200000;     // iterations per history before it is stopped as an error
+
+enum Material { kWater = 0, kPMMA = 1, kBrass = 2 };
+enum Fate { kStop = 0, kNuc = 1, kLeak = 2, kAbsRS = 3, kAbsAp = 4, kErr = 5 };
+enum Stat { kStDep = 0, kStLeak, kStRS, kStAp, kStNuc, kStSteps, kStErr, kNStats };
+
+struct MatConst {
+    float za;          // Z/A
+    float rho;         // g/cc (PMMA, brass); 1 for water
+    float x0_mmgcc;    // radiation length in mm * g/cc
+    float inv_dR;      // 1 / (uniform R-grid step)
+};
+
+struct TablesImage {                 // global-memory image, copied to shared memory
+    float R[kNMat][kNEPad];          // residual range R(E_k), mm * g/cc
+    float Einv[kNMat][kNR];          // E at R_j = j * dR
+    float2 hu[kNHU];                 // (density, SPR) per HU
+    MatConst mat[kNMat];
+};
+
+struct DevBeam {
+    float w[3], u[3], v[3], iso[3];
+    float t_src;
+    int rs;
+    float rs_tup, rs_tdn, rs_r2;
+    int ap;
+    float ap_tup, ap_tdn;
+    int poly_off, nvert;
+    float ras_lo[2], ras_inv[2];     // raster origin and 1/cell size
+    int ras_off;                     // offset into the raster byte array
+    int pad;
+};
+
+struct DevScen {
+    float shift[3];
+    float spr_scale;
+};
+
+// One work item = one (scenario, spot) pair: a contiguous range of global
+// history indices and the box of the scoring grid its deposits go to.
+struct DevItem {
+    long long hist_off;              // global index of the item's first history
+    float E0, x, y, sigma;
+    float div_rad, wscale;           // wscale = 2^F (x weight in the dose path)
+    int spot;                        // spot index: RNG key and CSR column
+    int scen;
+    int beam;
+    int box;                         // index into the box table
+};
+
+struct DevBox {
+    long long base;                  // element offset into the uint64 scratch
+    int lo[3];                       // first scoring voxel of the box
+    int n[3];                        // box extent in voxels
+};
+
+struct Grid3 {
+    int n[3];
+    float d[3];
+    float lo[3];
+};
+
+struct HistRecord {                  // mirrors vpmc_history_record
+    long long q_dep;
+    int fate;
+    int steps;
+    float e_dep;
+    float e_end;
+    float pos[3];
+    float pad;
+};
+
+struct TransportParams {
+    const TablesImage* tables;
+    const int16_t* ct;
+    Grid3 ctg, sg;
+    int same_grid;
+    const DevBeam* beams;
+    int n_beams;
+    const DevScen* scens;
+    int n_scen;
+    const float2* poly;
+    int n_poly;
+    const unsigned char* raster;
+    const DevItem* items;
+    int n_items;
+    const DevBox* boxes;
+    long long total;                 // total histories
+    unsigned long long* counter;     // global work counter
+    unsigned long long* scratch;     // deposit target
+    int* item_flags;                 // per item: 1 when a deposit fell outside its box
+    unsigned long long* stats;       // kNStats counters
+    int* status;                     // device status word (bit 0: iteration cap)
+    HistRecord* records;
+    long long rec_cap;
+    uint32_t key0, key1_hi;
+    int mcs, straggling, nuclear;
+    float fscale;                    // 2^F
+    int aggregate;
+    int chunk;
+};
+
+// Shared-memory layout of the transport kernel.
+struct SharedLayout {
+    static constexpr size_t R = 0;
+    static constexpr size_t Einv = R + sizeof(float) * kNMat * kNEPad;
+    static constexpr size_t HU = Einv + sizeof(float) * kNMat * kNR;
+    static constexpr size_t Mat = HU + sizeof(float2) * kNHU;
+    static constexpr size_t Beams = Mat + sizeof(MatConst) * kNMat;
+    static constexpr size_t Scens = Beams + sizeof(DevBeam) * kMaxBeams;
+    static constexpr size_t Poly = Scens + sizeof(DevScen) * kMaxScen;
+    static constexpr size_t Bytes = Poly + sizeof(float2) * kMaxPolyVerts;
+};
+
+// Host-side launchers (transport.cu, finalize.cu).
+cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s);
+size_t transport_smem_bytes();
+cudaError_t transport_func_attributes(int* regs, int* max_threads);
+
+cudaError_t launch_scoring_density(const int16_t* ct, Grid3 ctg, Grid3 sg, const double* curve15_dev,
+                                   const double ct_spacing[3], const double sg_spacing[3], double* rho_out,
+                                   cudaStream_t s);
+cudaError_t launch_dose_normalise(const unsigned long long* acc, const double* rho, long long nvox, double scale,
+                                  float* dose, cudaStream_t s);
+cudaError_t launch_column_max(const unsigned long long* scratch, const DevItem* items, const DevBox* boxes,
+                              const double* rho, const Grid3 sg, int first_item, int n_items, double* colmax,
+                              cudaStream_t s);
+
+struct CsrBuildParams {
+    const unsigned long long* scratch;
+    const DevItem* items;            // items of one scenario, sorted by beam then spot
+    const DevBox* boxes;
+    const double* rho;               // scoring-voxel densities
+    const double* colmax;            // per item max of q / rho
+    const int* beam_first;           // per beam: first item index (relative), -1 if none
+    const int* beam_count;
+    const int* beam_box;             // per beam: the shared box of its non-overflowed items
+    const int* ovf_items;            // overflowed items (full-grid boxes), sorted by beam then spot
+    const int* ovf_beam_first;       // per beam: first entry in ovf_items
+    const int* ovf_beam_count;
+    const int* item_ovf;             // per item: 1 if overflowed
+    int n_beams;
+    Grid3 sg;
+    long long nvox;
+    double rel_threshold;
+    const double* item_scale;        // per item: 2^-F * (MeV/g -> Gy) / (V(cm^3) * n_hist)
+    long long* row_count;            // [nvox + 1]
+    const long long* row_ptr;        // for the fill pass
+    int* col;
+    float* val;
+};
+cudaError_t launch_csr_pass(const CsrBuildParams& p, int fill, cudaStream_t s);
+cudaError_t launch_exclusive_scan(const long long* in, long long* out, long long n, long long* block_tmp,
+                                  cudaStream_t s);
+size_t scan_tmp_elems(long long n);
+int scan_launches(long long n);
+
+}  // namespace vpmc

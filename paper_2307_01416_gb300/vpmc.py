@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in include/vpmc.h (argument marshalling only).
+
+Every step of transport and scoring runs in libvpmc.so's CUDA kernels; this
+module converts workloads.* inputs to the ABI structs, hands torch device
+buffers to the library and wraps its outputs.  It raises if the library is
+missing or no CUDA device is present: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvpmc.so")
+
+VPMC_OK = 0
+_STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_TIMEOUT", -5: "ERR_STATE",
+           -6: "ERR_DEVICE_FLAG"}
+
+FATE_STOP, FATE_NUC, FATE_LEAK, FATE_RS, FATE_AP, FATE_ERR = range(6)
+
+
+class VpmcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("vpmc %s: %s" % (_STATUS.get(status, str(status)), message))
+        self.status = status
+
+
+class vpmc_hu_curve(C.Structure):
+    _fields_ = [("hu", C.c_double * 5), ("density", C.c_double * 5), ("spr", C.c_double * 5)]
+
+
+class vpmc_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dz", C.c_double), ("origin", C.c_double * 3)]
+
+
+class vpmc_beam(C.Structure):
+    _fields_ = [("dir", C.c_double * 3), ("bev_x", C.c_double * 3), ("iso", C.c_double * 3),
+                ("source_to_iso_mm", C.c_double),
+                ("rs_present", C.c_int), ("rs_wet_mm", C.c_double), ("rs_radius_mm", C.c_double),
+                ("rs_down_to_iso_mm", C.c_double),
+                ("ap_present", C.c_int), ("ap_thickness_mm", C.c_double), ("ap_down_to_iso_mm", C.c_double),
+                ("poly_xy", C.POINTER(C.c_double)), ("n_vertices", C.c_int)]
+
+
+class vpmc_spot(C.Structure):
+    _fields_ = [("beam", C.c_int), ("energy_mev", C.c_double), ("x_mm", C.c_double), ("y_mm", C.c_double),
+                ("sigma_mm", C.c_double), ("div_mrad", C.c_double), ("n_hist", C.c_int64), ("weight", C.c_double)]
+
+
+class vpmc_scenario(C.Structure):
+    _fields_ = [("shift_mm", C.c_double * 3), ("spr_scale", C.c_double)]
+
+
+class vpmc_opts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("mcs", C.c_int), ("straggling", C.c_int), ("nuclear", C.c_int),
+                ("frac_bits", C.c_int), ("aggregate", C.c_int), ("block_size", C.c_int),
+                ("blocks_per_sm", C.c_int), ("chunk", C.c_int), ("history_out", C.c_void_p),
+                ("history_cap", C.c_int64)]
+
+
+class vpmc_stats(C.Structure):
+    _fields_ = [("histories", C.c_int64), ("steps", C.c_int64), ("errors", C.c_int64), ("e_in", C.c_double),
+                ("e_dep", C.c_double), ("e_leak", C.c_double), ("e_rs", C.c_double), ("e_aperture", C.c_double),
+                ("e_nuc", C.c_double), ("ms", C.c_float), ("launches", C.c_int64)]
+
+
+class vpmc_csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("n_cols", C.c_int64), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+RECORD_DTYPE = np.dtype([("q_dep", np.int64), ("fate", np.int32), ("steps", np.int32), ("e_dep", np.float32),
+                         ("e_end", np.float32), ("pos", np.float32, (3,)), ("pad", np.float32)])
+assert RECORD_DTYPE.itemsize == 40
+
+EXPORTED = ["vpmc_default_opts", "vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots",
+            "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_destroy", "vpmc_last_error"]
+
+_lib = None
+
+
+def lib():
+    """Load libvpmc.so (built by __graft_entry__.build() / build_ext.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libvpmc.so is not built (%s); run `python -c 'import __graft_entry__ as g; g.build()'`"
+                           % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.vpmc_default_opts.argtypes = [C.POINTER(vpmc_opts)]
+    L.vpmc_default_opts.restype = None
+    L.vpmc_last_error.argtypes = []
+    L.vpmc_last_error.restype = C.c_char_p
+    L.vpmc_create_geometry.argtypes = [C.POINTER(vp), vp, C.c_int, C.POINTER(vpmc_grid), C.POINTER(vpmc_hu_curve),
+                                       C.POINTER(vpmc_grid), vp]
+    L.vpmc_set_aperture.argtypes = [vp, C.c_int, C.POINTER(vpmc_beam)]
+    L.vpmc_run_spots.argtypes = [vp, C.POINTER(vpmc_spot), C.c_int, C.POINTER(vpmc_scenario), C.POINTER(vpmc_opts),
+                                 vp, C.POINTER(vpmc_stats)]
+    L.vpmc_influence_matrix.argtypes = [vp, C.POINTER(vpmc_spot), C.c_int, C.POINTER(vpmc_scenario), C.c_int,
+                                        C.POINTER(vpmc_opts), C.c_float, C.POINTER(vpmc_csr), C.POINTER(vpmc_stats)]
+    L.vpmc_free_csr.argtypes = [C.POINTER(vpmc_csr), C.c_int]
+    L.vpmc_destroy.argtypes = [vp]
+    L.vpmc_destroy.restype = None
+    for f in ("vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots", "vpmc_influence_matrix",
+              "vpmc_free_csr"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != VPMC_OK:
+        raise VpmcError(status, lib().vpmc_last_error().decode())
+
+
+def _grid(g: W.Grid) -> vpmc_grid:
+    return vpmc_grid(g.shape[0], g.shape[1], g.shape[2], g.spacing[0], g.spacing[1], g.spacing[2],
+                     (C.c_double * 3)(*g.origin))
+
+
+def _curve(c: W.HUCurve) -> vpmc_hu_curve:
+    return vpmc_hu_curve((C.c_double * 5)(*c.hu), (C.c_double * 5)(*c.density), (C.c_double * 5)(*c.spr))
+
+
+def make_opts(o: W.Options, aggregate: int = -1, block_size: int = 0, chunk: int = 0) -> vpmc_opts:
+    v = vpmc_opts()
+    lib().vpmc_default_opts(C.byref(v))
+    v.seed, v.mcs, v.straggling, v.nuclear, v.frac_bits = int(o.seed), int(o.mcs), int(o.straggling), int(o.nuclear), \
+        int(o.frac_bits)
+    v.aggregate, v.block_size, v.chunk = aggregate, block_size, chunk
+    return v
+
+
+def spot_array(spots: np.ndarray):
+    arr = (vpmc_spot * max(len(spots), 1))()
+    for i, s in enumerate(spots):
+        arr[i] = vpmc_spot(int(s["beam"]), float(s["energy"]), float(s["x"]), float(s["y"]), float(s["sigma"]),
+                           float(s["div_mrad"]), int(s["n_hist"]), float(s["weight"]))
+    return arr
+
+
+def scenario_struct(sc: W.Scenario) -> vpmc_scenario:
+    return vpmc_scenario((C.c_double * 3)(*sc.shift), float(sc.spr_scale))
+
+
+class Engine:
+    """One geometry (CT + scoring grid + fields) on the current CUDA device."""
+
+    def __init__(self, problem: W.Problem, stream=None, host_ct: bool = False):
+        """host_ct: hand the library the host CT array (it copies it to the
+        device) instead of a device tensor."""
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("vpmc needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.problem = problem
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._ctx = C.c_void_p()
+        ct, sg, cv = _grid(problem.ct), _grid(problem.scoring), _curve(problem.curve)
+        hu_host = np.ascontiguousarray(problem.hu, dtype=np.int16)
+        if host_ct:
+            ptr, on_dev, keep = hu_host.ctypes.data, 0, hu_host
+        else:
+            keep = torch.from_numpy(hu_host).to(self.device)
+            ptr, on_dev = keep.data_ptr(), 1
+        _check(lib().vpmc_create_geometry(C.byref(self._ctx), C.c_void_p(ptr), on_dev, C.byref(ct), C.byref(cv),
+                                          C.byref(sg), C.c_void_p(self.stream.cuda_stream)))
+        del keep
+        for i, b in enumerate(problem.beams):
+            self.set_beam(i, b)
+
+    def set_beam(self, beam_id: int, b: W.Beam):
+        poly = None
+        nv = 0
+        if b.ap_present:
+            poly = np.ascontiguousarray(b.polygon, dtype=np.float64)
+            nv = len(poly)
+        s = vpmc_beam((C.c_double * 3)(*b.direction), (C.c_double * 3)(*b.bev_x), (C.c_double * 3)(*b.iso),
+                      float(b.source_to_iso), int(b.rs_present), float(b.rs_wet), float(b.rs_radius),
+                      float(b.rs_down_to_iso), int(b.ap_present), float(b.ap_thickness), float(b.ap_down_to_iso),
+                      poly.ctypes.data_as(C.POINTER(C.c_double)) if poly is not None else None, nv)
+        _check(lib().vpmc_set_aperture(self._ctx, int(beam_id), C.byref(s)))
+
+    def run_spots(self, spots: np.ndarray, scenario: Optional[W.Scenario] = None, opts: Optional[W.Options] = None,
+                  records: int = 0, dose_out=None, stats: bool = True, **launch):
+        """Dose (Gy, float32 tensor shaped (nz, ny, nx) on the device), stats
+        dict (if stats) and per-history records (numpy, if records > 0)."""
+        torch = self.torch
+        o = make_opts(opts or W.Options(), **launch)
+        g = self.problem.scoring
+        dose = dose_out if dose_out is not None else torch.empty((g.shape[2], g.shape[1], g.shape[0]),
+                                                                 dtype=torch.float32, device=self.device)
+        rec = None
+        if records:
+            rec = torch.zeros((records, RECORD_DTYPE.itemsize), dtype=torch.uint8, device=self.device)
+            o.history_out = rec.data_ptr()
+            o.history_cap = records
+        arr = spot_array(spots)
+        sc = scenario_struct(scenario) if scenario is not None else None
+        st = vpmc_stats()
+        _check(lib().vpmc_run_spots(self._ctx, arr, len(spots), C.byref(sc) if sc is not None else None, C.byref(o),
+                                    C.c_void_p(dose.data_ptr()), C.byref(st) if stats else None))
+        out_stats = _stats_dict(st) if stats else None
+        out_rec = None
+        if rec is not None:
+            self.stream.synchronize()
+            out_rec = rec.cpu().numpy().view(RECORD_DTYPE).reshape(records)
+        return dose, out_stats, out_rec
+
+    def influence_matrix(self, spots: np.ndarray, scenarios: Sequence[W.Scenario], opts: Optional[W.Options] = None,
+                         rel_threshold: float = 1e-4, **launch):
+        """Per-scenario CSR (dict of torch device tensors row_ptr int64, col
+        int32, val float32) and the stats dict."""
+        torch = self.torch
+        o = make_opts(opts or W.Options(), **launch)
+        arr = spot_array(spots)
+        scs = (vpmc_scenario * len(scenarios))(*[scenario_struct(s) for s in scenarios])
+        out = (vpmc_csr * len(scenarios))()
+        st = vpmc_stats()
+        _check(lib().vpmc_influence_matrix(self._ctx, arr, len(spots), scs, len(scenarios), C.byref(o),
+                                           float(rel_threshold), out, C.byref(st)))
+        mats = []
+        try:
+            for m in out:
+                mats.append(_csr_to_torch(m, self.device))
+        finally:
+            lib().vpmc_free_csr(out, len(scenarios))
+        return mats, _stats_dict(st)
+
+    def close(self):
+        if self._ctx:
+            lib().vpmc_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stats_dict(st: vpmc_stats) -> dict:
+    return {f: getattr(st, f) for f, _ in vpmc_stats._fields_}
+
+
+class _DeviceView:
+    """Zero-copy view of a library-owned device buffer for torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
+                                          "version": 3, "strides": None}
+
+
+def _csr_to_torch(m: vpmc_csr, device):
+    """Copy library-owned CSR buffers into torch-owned tensors (device to device)."""
+    import torch
+    out = {}
+    for name, ptr, n, ts, dt in (("row_ptr", m.row_ptr, m.n_rows + 1, "<i8", torch.int64),
+                                 ("col", m.col, m.nnz, "<i4", torch.int32),
+                                 ("val", m.val, m.nnz, "<f4", torch.float32)):
+        if n == 0:
+            out[name] = torch.empty(0, dtype=dt, device=device)
+        else:
+            out[name] = torch.as_tensor(_DeviceView(ptr, n, ts), device=device).clone()
+    out["shape"] = (int(m.n_rows), int(m.n_cols))
+    return out

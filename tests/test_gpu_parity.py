@@ -1,0 +1,212 @@
+"""GPU (C-ABI) vs FP64 CPU oracle parity on the same seeded inputs.
+
+Deterministic mode (scattering and straggling off, nuclear removal on): every
+history must match the oracle's fate, and its scored energy and end position
+to 1e-4 relative.  Full mode: per-voxel agreement within the combined
+statistical uncertainty and a 2%/2mm/10% gamma pass rate >= 99.5 %.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2307_01416_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DET = W.Options(seed=1234, mcs=False, straggling=False, nuclear=True)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    return torch
+
+
+def _engine(pb):
+    from paper_2307_01416_gb300 import vpmc
+    return vpmc.Engine(pb)
+
+
+def _per_history_parity(pb, spots, scen, op, records=None, max_flagged=0.01):
+    """Histories whose step starts came within 10 um of an aperture wall or
+    the range-shifter rim (oracle flag) are ill-conditioned in FP32: at
+    grazing incidence a rounding-level position change moves a brass chord by
+    ~500x as much.  Every other history must match the oracle's fate, scored
+    energy and end position to 1e-4 relative; flagged ones must be rare."""
+    n = int(spots["n_hist"].sum()) if records is None else records
+    eng = _engine(pb)
+    dose, st, rec = eng.run_spots(spots, scen, op, records=n)
+    q_o, tl, orec = O.run(pb, O.oracle_spots(spots), scen, op, records=n)
+    eng.close()
+    assert st["errors"] == 0 and tl["errors"] == 0
+    ok = orec["flags"] == 0
+    assert np.mean(~ok) <= max_flagged, np.mean(~ok)
+    bad_fate = np.flatnonzero((rec["fate"] != orec["fate"]) & ok)
+    assert bad_fate.size == 0, bad_fate[:10]
+    scale = np.maximum(np.abs(orec["e_dep"]), 1.0)
+    err = np.where(ok, np.abs(rec["e_dep"] - orec["e_dep"]) / scale, 0.0)
+    assert err.max() < 1e-4, (err.max(), np.argmax(err))
+    path = np.maximum(np.linalg.norm(orec["pos"], axis=1), 10.0)
+    perr = np.where(ok, np.linalg.norm(rec["pos"] - orec["pos"], axis=1) / path, 0.0)
+    assert perr.max() < 1e-4, (perr.max(), np.argmax(perr))
+    leak = ok & (orec["fate"] == O.FATE_LEAK)
+    if leak.any():
+        assert np.max(np.abs(rec["e_end"][leak] - orec["e_end"][leak]) / np.maximum(orec["e_end"][leak], 1.0)) < 1e-4
+    # totals over all histories (flagged included) and device energy conservation
+    assert abs(rec["e_dep"].astype(np.float64).sum() / max(orec["e_dep"].sum(), 1.0) - 1.0) < 1e-3
+    tot = st["e_dep"] + st["e_leak"] + st["e_rs"] + st["e_aperture"]
+    assert abs(tot / st["e_in"] - 1.0) < 1e-6
+    return dose, st, rec, q_o, orec
+
+
+def test_water_pencil_beam_per_history(torch_cuda):
+    pb, spots = W.pencil_beam_water(n_hist=20000)
+    dose, st, rec, q_o, orec = _per_history_parity(pb, spots, W.Scenario(), DET)
+    assert (rec["fate"] == O.FATE_NUC).sum() > 100
+    # per-voxel deposits of the deterministic run agree too
+    d_o = O.dose_from_q(pb, q_o, DET.frac_bits).reshape(dose.shape)
+    d_g = dose.cpu().numpy().astype(np.float64)
+    assert np.abs(d_g.sum() / d_o.sum() - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("rs", [False, True])
+def test_aperture_and_range_shifter_per_history(torch_cuda, rs):
+    pb, spots = W.water_aperture_case(10.0, rs, hist_per_layer=3000, max_layers=3, shape=(50, 50, 100))
+    dose, st, rec, _, orec = _per_history_parity(pb, spots, W.Scenario(), DET)
+    assert (rec["fate"] == O.FATE_AP).sum() > 100 and (rec["fate"] <= O.FATE_NUC).sum() > 100
+    if rs:
+        assert st["e_rs"] > 0
+
+
+def test_heterogeneous_head_scenario_per_history(torch_cuda):
+    g, hu, _ = W.head_ct(1234, shape=(96, 96, 64), spacing=(2.5, 2.5, 3.75))
+    sg = W.Grid((48, 48, 40), (5.0, 5.0, 6.0), g.origin)
+    center = (0.0, -25.0, 5.0)
+    beams = [W.gantry_beam(gd, center, 245.0, rs_present=True, ap_present=True,
+                           polygon=W.regular_polygon(16.0, 64)) for gd in (0.0, 90.0, 270.0)]
+    pb = W.Problem(ct=g, hu=hu, curve=W.HUCurve(), scoring=sg, beams=beams)
+    rows = [(b, e, x, y, W.spot_sigma_mm(e), 2.0, 400, 1.0) for b in range(3) for e in (120.0, 140.0)
+            for x in (-9.0, 0.0, 9.0) for y in (-9.0, 0.0, 9.0)]
+    spots = W.make_spots(rows)
+    _per_history_parity(pb, spots, W.Scenario((2.0, -3.0, 1.0), 1.035), DET)
+
+
+def test_launch_configuration_does_not_change_results(torch_cuda):
+    """64-bit fixed-point sums are order independent: block size, refill
+    chunk and warp aggregation give bit-identical grids (full physics)."""
+    torch = torch_cuda
+    pb, spots = W.water_aperture_case(20.0, True, hist_per_layer=20000, max_layers=2, shape=(40, 40, 60))
+    eng = _engine(pb)
+    op = W.Options(seed=7)
+    ref = None
+    for block, agg, chunk in ((512, 1, 32), (256, 0, 128), (384, 1, 64)):
+        d, st, _ = eng.run_spots(spots, W.Scenario(), op, block_size=block, aggregate=agg, chunk=chunk)
+        d = d.cpu().numpy()
+        if ref is None:
+            ref, ref_st = d, st
+        else:
+            assert np.array_equal(d, ref)
+            assert st["steps"] == ref_st["steps"] and st["e_dep"] == ref_st["e_dep"]
+    eng.close()
+
+
+def _batched_dose(run, n_batches):
+    ds = np.stack([run(b) for b in range(n_batches)])
+    return ds.mean(axis=0), ds.std(axis=0, ddof=1) / math.sqrt(n_batches)
+
+
+def _statistical_parity(pb, spots, op_seed_gpu, op_seed_orc, n_batches=40, scen=W.Scenario()):
+    eng = _engine(pb)
+    rho = O.scoring_density(pb)
+
+    def gpu(b):
+        d, _, _ = eng.run_spots(spots, scen, W.Options(seed=op_seed_gpu + b))
+        return d.cpu().numpy().astype(np.float64).ravel()
+
+    def orc(b):
+        q, _, _ = O.run(pb, O.oracle_spots(spots), scen, W.Options(seed=op_seed_orc + b))
+        return O.dose_from_q(pb, q, 24, rho)
+
+    mg, sg_ = _batched_dose(gpu, n_batches)
+    mo, so = _batched_dose(orc, n_batches)
+    eng.close()
+    dmax = mo.max()
+    sel = mo >= 0.1 * dmax
+    z = np.abs(mg - mo)[sel] / np.sqrt(sg_[sel] ** 2 + so[sel] ** 2)
+    frac3 = np.mean(z > 3.0)
+    g = pb.scoring
+    shp = (g.shape[2], g.shape[1], g.shape[0])
+    gam = O.gamma_pass_rate(mo.reshape(shp), mg.reshape(shp), g.spacing)
+    return frac3, z.max(), gam, sel.sum()
+
+
+def test_full_physics_water_statistical(torch_cuda):
+    pb, spots = W.pencil_beam_water(n_hist=2500)
+    frac3, zmax, gam, nsel = _statistical_parity(pb, spots, 1000, 5000)
+    assert nsel > 200
+    assert frac3 <= 0.005 and zmax < 5.0, (frac3, zmax)
+    assert gam >= 99.5, gam
+
+
+def test_full_physics_aperture_statistical(torch_cuda):
+    pb, spots = W.water_aperture_case(20.0, True, hist_per_layer=6000, max_layers=2, shape=(50, 50, 100))
+    frac3, zmax, gam, nsel = _statistical_parity(pb, spots, 2000, 6000)
+    assert nsel > 200
+    assert frac3 <= 0.005 and zmax < 5.0, (frac3, zmax)
+    assert gam >= 99.5, gam
+
+
+def _dense(csr):
+    import scipy.sparse as sps
+    rp = csr["row_ptr"].cpu().numpy()
+    col = csr["col"].cpu().numpy()
+    val = csr["val"].cpu().numpy()
+    return sps.csr_matrix((val, col, rp), shape=csr["shape"]).toarray()
+
+
+def test_influence_matrix_deterministic_parity(torch_cuda):
+    """Per-scenario CSR of the GPU vs the oracle's plain IM definition."""
+    pb, spots = W.water_aperture_case(10.0, False, hist_per_layer=2000, max_layers=2, shape=(30, 30, 60))
+    scens = W.robust_scenarios()[:3] + W.robust_scenarios()[7:9]
+    eng = _engine(pb)
+    mats, st = eng.influence_matrix(spots, scens, DET)
+    eng.close()
+    ref = O.influence_matrix(pb, spots, scens, DET)
+    for m, r in zip(mats, ref):
+        rp = m["row_ptr"].cpu().numpy()
+        col = m["col"].cpu().numpy()
+        # columns sorted within rows
+        for i in np.flatnonzero(np.diff(rp) > 1)[:2000]:
+            seg = col[rp[i]:rp[i + 1]]
+            assert np.all(np.diff(seg) > 0)
+        g = _dense(m)
+        o = r.toarray()
+        cmax = o.max(axis=0, keepdims=True)
+        both = (g > 0) & (o > 0)
+        rel = np.abs(g - o)[both] / o[both]
+        assert np.quantile(rel, 0.999) < 1e-3 and np.max(np.abs(g - o) / np.maximum(cmax, 1e-30)) < 1e-3
+        only = (g > 0) ^ (o > 0)
+        # entries kept on one side only must sit at the threshold
+        assert np.all(np.maximum(g, o)[only] < 1.01e-4 * np.broadcast_to(cmax, g.shape)[only])
+    tot = st["e_dep"] + st["e_leak"] + st["e_rs"] + st["e_aperture"]
+    assert abs(tot / st["e_in"] - 1.0) < 1e-6
+
+
+def test_influence_matrix_columns_sum_to_dose(torch_cuda):
+    """Full physics: IM columns x n_hist summed over spots equal the unit-weight
+    dose of the same spots (same seed, same histories), up to the dropped
+    sub-threshold entries."""
+    pb, spots = W.water_aperture_case(20.0, True, hist_per_layer=4000, max_layers=2, shape=(40, 40, 60))
+    op = W.Options(seed=11)
+    eng = _engine(pb)
+    mats, _ = eng.influence_matrix(spots, [W.Scenario()], op, rel_threshold=0.0)
+    dose, _, _ = eng.run_spots(spots, W.Scenario(), op)
+    eng.close()
+    g = _dense(mats[0]) * spots["n_hist"][None, :].astype(np.float64)
+    d = dose.cpu().numpy().ravel().astype(np.float64)
+    assert np.allclose(g.sum(axis=1), d, rtol=1e-5, atol=1e-6 * d.max())

@@ -163,6 +163,17 @@ def test_crossing_number_nonconvex_matches_winding_number():
         assert O.point_in_polygon(poly, p[0], p[1]) == (wn != 0)
 
 
+def test_wall_distance_square_closed_form():
+    sq = W.square_polygon(10.0)
+    rng = np.random.default_rng(8)
+    for x, y in rng.uniform(-14, 14, size=(400, 2)):
+        if abs(x) <= 10 and abs(y) <= 10:
+            ref = min(10 - abs(x), 10 - abs(y))
+        else:
+            ref = math.hypot(max(abs(x) - 10, 0.0), max(abs(y) - 10, 0.0))
+        assert abs(O.wall_distance(sq, x, y) - ref) < 1e-12
+
+
 def test_first_wall_hit_square_closed_form():
     sq = W.square_polygon(10.0)
     rng = np.random.default_rng(5)

@@ -246,3 +246,19 @@ def test_scoring_density_volume_weighted():
     fine = np.repeat(np.repeat(np.repeat(rho_ct, 3, axis=0), 2, axis=1), 2, axis=2)  # 0.5 mm cells
     ref = fine.reshape(3, 4, 2, 4, 2, 4).mean(axis=(1, 3, 5))
     assert np.allclose(O.scoring_density(pb), ref.ravel(), rtol=1e-12)
+
+
+def test_full_physics_head_plan_sample_is_finite_and_conserves():
+    """Full physics through range shifter, aperture and heterogeneous head: no
+    history is stopped by the iteration cap, energies stay finite (scattering
+    offsets that carry a particle past a slab's exit plane give a zero-length
+    exit step, not a negative one), and energy is conserved."""
+    pb, spots, _, _ = W.head_plan(8.4)
+    idx = np.arange(0, len(spots), 37)
+    sp = O.oracle_spots(spots[idx], spot_keys=idx, n_hist=np.full(len(idx), 60))
+    q, tl, rec = O.run(pb, sp, W.Scenario((0.0, 3.0, 0.0), 1.035), W.Options(seed=5), records=len(idx) * 60)
+    assert tl["errors"] == 0
+    assert np.all(np.isfinite(rec["e_dep"])) and np.all(np.isfinite(rec["pos"]))
+    tot = q.sum() * 2.0 ** -24 + tl["e_leak"] + tl["e_rs"] + tl["e_ap"]
+    assert abs(tot / tl["e_in"] - 1.0) < 1e-6
+    assert tl["e_rs"] > 0 and tl["e_ap"] > 0 and tl["e_dep"] > 0
