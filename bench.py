@@ -206,6 +206,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pb, spots, scens = build_workload(args.small)
+    free_b, total_b = torch.cuda.mem_get_info()
+    print("device memory: %.1f GB free of %.1f GB" % (free_b / 1e9, total_b / 1e9), file=sys.stderr)
     # independent problems per rank (weak scaling): each rank computes its own set
     opts = W.Options(seed=1234 + 7919 * rank)
     stream = torch.cuda.Stream()
@@ -245,6 +247,7 @@ def main():
         torch.cuda.synchronize()
         ck = clocks.stop()
         t = ev0.elapsed_time(ev1) / 1000.0
+        eng.close()                                # frees the set's column scratch before the e2e leg
     if world > 1:
         tt = torch.tensor([t], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)

@@ -124,6 +124,7 @@ typedef struct {
     double e_in, e_dep, e_leak, e_rs, e_aperture, e_nuc;
     float ms;               /* device time of the transport launch(es), CUDA events */
     int64_t launches;       /* kernels this call launched (autotuning included) */
+    int64_t ovf_records;    /* influence matrix: deposits outside their column's dense box */
 } vpmc_stats;
 
 /* Sparse influence matrix of one scenario: rows = scoring voxels (x-fastest),

@@ -75,7 +75,7 @@ SPOT_DTYPE = np.dtype([("beam", np.int32), ("spot_key", np.int32), ("energy", np
 RECORD_DTYPE = np.dtype([("fate", np.int32), ("steps", np.int32), ("e_dep", np.float64), ("e_end", np.float64),
                          ("pos", np.float64, (3,)), ("q_dep", np.int64), ("flags", np.int32), ("pad", np.int32)],
                         align=True)
-FLAG_NEAR_WALL, FLAG_NEAR_RIM = 1, 2
+FLAG_NEAR_WALL, FLAG_NEAR_RIM, FLAG_NUC_LOW_DENSITY, FLAG_GRAZING_FACE = 1, 2, 4, 8
 
 _lib = None
 _lock = threading.Lock()

@@ -341,7 +341,13 @@ typedef struct {
     double pos[3];      /* end position, patient coordinates, mm             */
     int64_t q_dep;      /* sum of the history's fixed-point grid deposits    */
     int32_t flags;      /* bit 0: a step started within ORC_TIE_MM of an
-                           aperture wall; bit 1: of the range-shifter rim    */
+                           aperture wall; bit 1: of the range-shifter rim;
+                           bit 2: nuclear removal in a medium below
+                           ORC_LOW_RHO g/cc (the interaction point moves by
+                           (free-path rounding) / (0.0012 rho) mm);
+                           bit 3: a CT voxel face crossed at a direction
+                           cosine below 0.01 |delta SPR| (the crossing point
+                           moves by (position rounding) / cosine)          */
     int32_t pad;
 } orc_record;
 
@@ -349,6 +355,7 @@ typedef struct {
  * at grazing incidence a rounding-level shift of the position changes which
  * side of the boundary a step starts on. */
 #define ORC_TIE_MM 0.01
+#define ORC_LOW_RHO 0.1
 
 /* Tallies: 0 energy in, 1 scored in grid, 2 leaked, 3 range shifter,
  * 4 aperture, 5 nuclear (included in 1, 3, 4), 6 histories, 7 steps,
@@ -731,19 +738,26 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
             }
             if (so.killed) {
                 if (so.killed == 2) tl[5] += so.dE;
+                if (so.killed == 2 && rho < ORC_LOW_RHO) rec->flags |= 4;
                 rec->fate = so.killed == 2 ? FATE_NUC : FATE_STOP;
                 for (int k = 0; k < 3; ++k) P[k] = pt.p[k];
                 goto done;
             }
             if (so.limiter == LIM_GEOM) {
-                int out = 0;
+                int out = 0, crossed = -1;
                 for (int k = 0; k < 3; ++k) {
                     int sgn = D[k] > 0.0 ? 1 : -1;
-                    if (D[k] != 0.0 && dc[k] == svox) ic[k] += sgn;
+                    if (D[k] != 0.0 && dc[k] == svox) { ic[k] += sgn; crossed = k; }
                     if (D[k] != 0.0 && ds[k] == svox) is[k] += sgn;
                     if (ic[k] < 0 || ic[k] >= n[k] || is[k] < 0 || is[k] >= ns[k]) out = 1;
                 }
                 if (out) { for (int k = 0; k < 3; ++k) P[k] = pt.p[k]; goto leak; }
+                if (crossed >= 0) {
+                    double rho2, spr2;
+                    orc_hu_props(pb->curve, (double)pb->hu[ic[0] + (int64_t)n[0] * (ic[1] + (int64_t)n[1] * ic[2])],
+                                 &rho2, &spr2);
+                    if (fabs(D[crossed]) < 0.01 * fabs(spr2 - spr)) rec->flags |= 8;
+                }
             }
             /* lateral displacement, confined to the current voxel of both grids */
             for (int k = 0; k < 3; ++k) {

@@ -87,8 +87,8 @@ struct vpmc_ctx {
     size_t items_cap = 0;
     DevBox* d_boxes = nullptr;
     size_t boxes_cap = 0;
-    int* d_item_flags = nullptr;
-    size_t flags_cap = 0;
+    OvfRec* d_ovf = nullptr;                   // out-of-box deposit records
+    long long ovf_cap = 0;
     unsigned long long* d_scratch = nullptr;
     size_t scratch_cap = 0;                    // elements
     TuneResult tune_dose, tune_im;
@@ -130,14 +130,14 @@ vpmc_status grow_boxes(vpmc_ctx* c, size_t n)
     return VPMC_OK;
 }
 
-vpmc_status grow_flags(vpmc_ctx* c, size_t n)
+vpmc_status grow_ovf(vpmc_ctx* c, long long n)
 {
-    if (n <= c->flags_cap) return VPMC_OK;
-    cudaFree(c->d_item_flags);
-    c->d_item_flags = nullptr;
-    c->flags_cap = 0;
-    CUDA_TRY(dev_alloc(&c->d_item_flags, n));
-    c->flags_cap = n;
+    if (n <= c->ovf_cap) return VPMC_OK;
+    cudaFree(c->d_ovf);
+    c->d_ovf = nullptr;
+    c->ovf_cap = 0;
+    CUDA_TRY(dev_alloc(&c->d_ovf, (size_t)n));
+    c->ovf_cap = n;
     return VPMC_OK;
 }
 
@@ -232,7 +232,6 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     p.counter = c->d_counter;
     p.stats = c->d_stats;
     p.status = c->d_status;
-    p.item_flags = c->d_item_flags;
     p.key0 = (uint32_t)o.seed;
     p.key1_hi = (uint32_t)(o.seed >> 32);
     p.mcs = o.mcs;
@@ -346,6 +345,7 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
                                  const vpmc_hu_curve* curve, const vpmc_grid* dose_grid, void* cuda_stream)
 {
     g_error.clear();
+    (void)cudaGetLastError();   // a failed call elsewhere in this thread must not leak into ours
     if (!out) return fail(VPMC_ERR_ARG, "out is null");
     *out = nullptr;
     if (!hu || !ct || !curve || !dose_grid) return fail(VPMC_ERR_ARG, "null argument");
@@ -437,6 +437,7 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
 vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
 {
     g_error.clear();
+    (void)cudaGetLastError();   // a failed call elsewhere in this thread must not leak into ours
     if (!c || !b) return fail(VPMC_ERR_ARG, "null argument");
     if (beam_id < 0 || beam_id >= kMaxBeams) return fail(VPMC_ERR_ARG, "beam_id %d outside [0, %d)", beam_id, kMaxBeams);
     const double nw = std::sqrt(b->dir[0] * b->dir[0] + b->dir[1] * b->dir[1] + b->dir[2] * b->dir[2]);
@@ -509,6 +510,7 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
                            const vpmc_opts* opts_in, float* dose_dev, vpmc_stats* stats_out)
 {
     g_error.clear();
+    (void)cudaGetLastError();   // a failed call elsewhere in this thread must not leak into ours
     if (!c || !dose_dev) return fail(VPMC_ERR_ARG, "null context or dose buffer");
     const long long launches0 = c->launches;
     vpmc_opts o;
@@ -561,8 +563,6 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
         if (st != VPMC_OK) return st;
         st = grow_boxes(c, 1);
         if (st != VPMC_OK) return st;
-        st = grow_flags(c, items.size());
-        if (st != VPMC_OK) return st;
         DevBox box{};
         box.base = 0;
         for (int k = 0; k < 3; ++k) { box.lo[k] = 0; box.n[k] = c->sg.n[k]; }
@@ -570,7 +570,6 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
                                  c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->d_boxes, &box, sizeof box, cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->d_scens, &sc, sizeof sc, cudaMemcpyHostToDevice, c->stream));
-        CUDA_TRY(cudaMemsetAsync(c->d_item_flags, 0, items.size() * sizeof(int), c->stream));
         TransportParams p = base_params(c, o);
         p.items = c->d_items;
         p.n_items = (int)items.size();
@@ -578,8 +577,7 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
         p.n_scen = 1;
         p.total = total;
         p.scratch = c->d_acc;
-        p.item_flags = c->d_item_flags;
-        const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
+            const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
         if (want_tune && !c->tune_dose.valid) {
             st = autotune(c, p, &c->tune_dose, o, c->d_acc, (size_t)c->nvox);
             if (st != VPMC_OK) return st;
@@ -692,6 +690,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
                                   vpmc_stats* stats_out)
 {
     g_error.clear();
+    (void)cudaGetLastError();   // a failed call elsewhere in this thread must not leak into ours
     if (!c || !out || !scen || n_scen <= 0) return fail(VPMC_ERR_ARG, "null argument or no scenario");
     const long long launches0 = c->launches;
     if (n_scen > kMaxScen) return fail(VPMC_ERR_ARG, "at most %d scenarios per call", kMaxScen);
@@ -704,6 +703,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     if (st != VPMC_OK) return st;
     st = check_spots(c, spots, n_spots);
     if (st != VPMC_OK) return st;
+    if (n_spots == 0) return fail(VPMC_ERR_ARG, "no spots");
     for (int i = 1; i < n_spots; ++i)
         if (spots[i].beam < spots[i - 1].beam) return fail(VPMC_ERR_ARG, "spots must be sorted by beam id");
     for (int s = 0; s < n_scen; ++s)
@@ -713,53 +713,57 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         if ((double)spots[i].n_hist * spots[i].energy_mev * fs >= 9.0e18)
             return fail(VPMC_ERR_ARG, "spot %d: fixed-point range exceeded, lower frac_bits", i);
 
-    // beams in use
+    // beams in use: spots of beam b are the contiguous range [beam_first, +beam_count)
     int nb = 0;
     for (int i = 0; i < n_spots; ++i) nb = std::max(nb, spots[i].beam + 1);
-    std::vector<int> beam_first(nb, -1), beam_count(nb, 0);
-    for (int i = 0; i < n_spots; ++i) {
-        if (beam_first[spots[i].beam] < 0) beam_first[spots[i].beam] = i;
-        beam_count[spots[i].beam] += 1;
-    }
-    // per-scenario item tables: item j of scenario s = spot j (every spot gets
-    // an item so that the CSR pass can index items by spot)
+    std::vector<int> beam_first(nb, 0), beam_count(nb, 0);
+    for (int i = n_spots - 1; i >= 0; --i) beam_first[spots[i].beam] = i;
+    for (int i = 0; i < n_spots; ++i) beam_count[spots[i].beam] += 1;
     std::vector<DevScen> dscen(n_scen);
     for (int s = 0; s < n_scen; ++s) {
         for (int k = 0; k < 3; ++k) dscen[s].shift[k] = (float)scen[s].shift_mm[k];
         dscen[s].spr_scale = (float)scen[s].spr_scale;
     }
+    // one box per (scenario, beam): the field plus a lateral margin, full depth
     std::vector<BoxSpec> spec((size_t)n_scen * nb);
-    for (int s = 0; s < n_scen; ++s)
-        for (int b = 0; b < nb; ++b)
-            if (beam_count[b]) spec[(size_t)s * nb + b] = field_box(c, b, scen[s], spots, n_spots, 25.0);
-    long long per_scen_elems_max = 0;
     std::vector<long long> scen_elems(n_scen, 0);
+    long long per_scen_elems_max = 0;
     for (int s = 0; s < n_scen; ++s) {
-        for (int b = 0; b < nb; ++b) scen_elems[s] += box_elems(spec[(size_t)s * nb + b]) * beam_count[b];
+        for (int b = 0; b < nb; ++b)
+            if (beam_count[b]) {
+                spec[(size_t)s * nb + b] = field_box(c, b, scen[s], spots, n_spots, 25.0);
+                scen_elems[s] += box_elems(spec[(size_t)s * nb + b]) * beam_count[b];
+            }
         per_scen_elems_max = std::max(per_scen_elems_max, scen_elems[s]);
     }
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    const long long rerun_reserve = 32 * c->nvox;   // room for overflow re-runs
-    const long long budget = (long long)((double)(free_b + c->scratch_cap * 8) * 0.70 / 8.0) - rerun_reserve;
+    long long budget = (long long)((double)(free_b + c->scratch_cap * 8) * 0.80 / 8.0);
     if (per_scen_elems_max > budget)
         return fail(VPMC_ERR_OOM, "one scenario needs %.1f GB of column scratch, %.1f GB available",
                     per_scen_elems_max * 8e-9, budget * 8e-9);
 
-    vpmc_stats stats{};
     std::vector<double> item_scale(n_spots);
     const double vol_cm3 = c->sg_spacing[0] * c->sg_spacing[1] * c->sg_spacing[2] * 1e-3;
     for (int j = 0; j < n_spots; ++j)
         item_scale[j] = spots[j].n_hist > 0 ? std::ldexp(1.0, -o.frac_bits) * 1.602176634e-10 / vol_cm3 /
                                                   (double)spots[j].n_hist
                                             : 0.0;
+    // per-call buffers
     double* d_colmax = nullptr;
     double* d_item_scale = nullptr;
     long long* d_rowcnt = nullptr;
     long long* d_scan_tmp = nullptr;
     int* d_beam_meta = nullptr;
+    long long* d_bucket_off = nullptr;
+    long long* d_bucket_cur = nullptr;
+    int* d_bucket_len = nullptr;
+    OvfRec* d_ovf_sorted = nullptr;
+    unsigned long long* d_ovf_count = nullptr;
     auto release = [&]() {
         cudaFree(d_colmax); cudaFree(d_item_scale); cudaFree(d_rowcnt); cudaFree(d_scan_tmp); cudaFree(d_beam_meta);
+        cudaFree(d_bucket_off); cudaFree(d_bucket_cur); cudaFree(d_bucket_len); cudaFree(d_ovf_sorted);
+        cudaFree(d_ovf_count);
     };
 #define IM_TRY(expr)                                                                                    \
     do {                                                                                                \
@@ -776,15 +780,16 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         vpmc_status s_ = (expr);                                                                        \
         if (s_ != VPMC_OK) { release(); vpmc_free_csr(out, n_scen); return s_; }                        \
     } while (0)
-    IM_TRY(dev_alloc(&d_colmax, n_spots));
     IM_TRY(dev_alloc(&d_item_scale, n_spots));
     IM_TRY(cudaMemcpy(d_item_scale, item_scale.data(), n_spots * sizeof(double), cudaMemcpyHostToDevice));
     IM_TRY(dev_alloc(&d_rowcnt, c->nvox + 1));
-    IM_TRY(dev_alloc(&d_scan_tmp, scan_tmp_elems(c->nvox + 1)));
-    IM_TRY(dev_alloc(&d_beam_meta, 5 * (size_t)nb + n_spots + 1));
+    IM_TRY(dev_alloc(&d_scan_tmp, scan_tmp_elems((long long)n_scen * c->nvox + 1)));
+    IM_TRY(dev_alloc(&d_beam_meta, 3 * (size_t)nb));
+    IM_TRY(dev_alloc(&d_ovf_count, 1));
     IM_TRY(cudaMemcpy(c->d_scens, dscen.data(), n_scen * sizeof(DevScen), cudaMemcpyHostToDevice));
-    float total_ms = 0.0f;
 
+    vpmc_stats stats{};
+    float total_ms = 0.0f;
     int s0 = 0;
     while (s0 < n_scen) {
         // a wave = consecutive scenarios whose column scratch fits the budget
@@ -792,65 +797,63 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         long long wave_elems = 0;
         while (s1 < n_scen && wave_elems + scen_elems[s1] <= budget) wave_elems += scen_elems[s1++];
         const int ns = s1 - s0;
-        // items and boxes of the wave: items ordered (scenario, spot)
+        {
+            vpmc_status gs = grow_scratch(c, (size_t)wave_elems);
+            if (gs == VPMC_ERR_OOM && ns > 1) {
+                budget = std::max(per_scen_elems_max, wave_elems / 2);
+                (void)cudaGetLastError();
+                continue;
+            }
+            if (gs != VPMC_OK) {
+                size_t fb = 0, tb = 0;
+                cudaMemGetInfo(&fb, &tb);
+                IM_ST(fail(VPMC_ERR_OOM, "column scratch of %.1f GB for %d scenario(s) does not fit (%.1f GB free)",
+                           wave_elems * 8e-9, ns, fb * 1e-9));
+            }
+        }
+        // items (scenario-major, spot order) and their boxes
         std::vector<DevItem> items((size_t)ns * n_spots);
         std::vector<DevBox> boxes;
-        std::vector<int> box_of((size_t)ns * nb, -1);
-        long long base = 0;
-        for (int s = s0; s < s1; ++s)
+        std::vector<int> beam_box((size_t)ns * nb, 0);
+        boxes.reserve(items.size() + (size_t)ns * nb);
+        long long base = 0, total = 0;
+        for (int s = s0; s < s1; ++s) {
             for (int b = 0; b < nb; ++b) {
                 if (!beam_count[b]) continue;
                 const BoxSpec& sp = spec[(size_t)s * nb + b];
-                box_of[(size_t)(s - s0) * nb + b] = (int)boxes.size();
                 DevBox bx{};
-                bx.base = base;
                 for (int k = 0; k < 3; ++k) { bx.lo[k] = sp.lo[k]; bx.n[k] = sp.n[k]; }
+                bx.base = base;
+                beam_box[(size_t)(s - s0) * nb + b] = (int)boxes.size();
                 boxes.push_back(bx);
-                // one box per (scenario, beam); each item gets its own copy of the
-                // box's shape at its own base offset
-                base += box_elems(sp) * beam_count[b];
-            }
-        // per-item boxes (distinct bases, shared shapes)
-        std::vector<DevBox> item_boxes;
-        item_boxes.reserve(items.size() + 64);
-        long long total = 0;
-        for (int s = s0; s < s1; ++s) {
-            std::vector<long long> next_base(nb, 0);
-            for (int b = 0; b < nb; ++b)
-                if (box_of[(size_t)(s - s0) * nb + b] >= 0) next_base[b] = boxes[box_of[(size_t)(s - s0) * nb + b]].base;
-            for (int j = 0; j < n_spots; ++j) {
-                const vpmc_spot& sp = spots[j];
-                DevItem it{};
-                it.hist_off = total;
-                it.E0 = (float)sp.energy_mev;
-                it.x = (float)sp.x_mm;
-                it.y = (float)sp.y_mm;
-                it.sigma = (float)sp.sigma_mm;
-                it.div_rad = (float)(sp.div_mrad * 1e-3);
-                it.wscale = (float)fs;
-                it.spot = j;
-                it.scen = s;
-                it.beam = sp.beam;
-                DevBox bx = boxes[box_of[(size_t)(s - s0) * nb + sp.beam]];
-                bx.base = next_base[sp.beam];
-                next_base[sp.beam] += box_elems(spec[(size_t)s * nb + sp.beam]);
-                it.box = (int)item_boxes.size();
-                item_boxes.push_back(bx);
-                items[(size_t)(s - s0) * n_spots + j] = it;
-                total += sp.n_hist;
+                for (int j = beam_first[b]; j < beam_first[b] + beam_count[b]; ++j) {
+                    const vpmc_spot& sp_j = spots[j];
+                    DevItem it{};
+                    it.hist_off = total;
+                    it.E0 = (float)sp_j.energy_mev;
+                    it.x = (float)sp_j.x_mm;
+                    it.y = (float)sp_j.y_mm;
+                    it.sigma = (float)sp_j.sigma_mm;
+                    it.div_rad = (float)(sp_j.div_mrad * 1e-3);
+                    it.wscale = (float)fs;
+                    it.spot = j;
+                    it.scen = s;
+                    it.beam = b;
+                    DevBox ib = bx;
+                    ib.base = base;
+                    base += box_elems(sp);
+                    it.box = (int)boxes.size();
+                    boxes.push_back(ib);
+                    items[(size_t)(s - s0) * n_spots + j] = it;
+                    total += sp_j.n_hist;
+                }
             }
         }
-        const long long main_elems = base;
-        // the transport kernel needs items with histories in hist_off order;
-        // zero-history items share the next item's offset and are never found
         IM_ST(grow(c, &c->d_items, &c->items_cap, items.size()));
-        IM_ST(grow_boxes(c, item_boxes.size() + 64));
-        IM_ST(grow_flags(c, items.size()));
-        IM_ST(grow_scratch(c, (size_t)(main_elems + rerun_reserve)));
-        IM_TRY(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice,
-                               c->stream));
-        IM_TRY(cudaMemcpyAsync(c->d_boxes, item_boxes.data(), item_boxes.size() * sizeof(DevBox),
-                               cudaMemcpyHostToDevice, c->stream));
+        IM_ST(grow_boxes(c, boxes.size()));
+        IM_TRY(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice));
+        IM_TRY(cudaMemcpy(c->d_boxes, boxes.data(), boxes.size() * sizeof(DevBox), cudaMemcpyHostToDevice));
+        if (!c->d_ovf) IM_ST(grow_ovf(c, 1ll << 24));
         TransportParams p = base_params(c, o);
         p.items = c->d_items;
         p.n_items = (int)items.size();
@@ -858,35 +861,50 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         p.n_scen = n_scen;
         p.total = total;
         p.scratch = c->d_scratch;
-        p.item_flags = c->d_item_flags;
         p.records = nullptr;
         p.rec_cap = 0;
+        p.ovf_count = d_ovf_count;
         const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
-        if (want_tune && !c->tune_im.valid) IM_ST(autotune(c, p, &c->tune_im, o, nullptr, 0));
+        if (want_tune && !c->tune_im.valid) {
+            p.ovf = c->d_ovf;
+            p.ovf_cap = c->ovf_cap;
+            IM_TRY(cudaMemsetAsync(d_ovf_count, 0, sizeof(unsigned long long), c->stream));
+            IM_ST(autotune(c, p, &c->tune_im, o, nullptr, 0));
+        }
         int block, agg, chunk;
         resolve_launch(o, c->tune_im, &block, &agg, &chunk);
         p.aggregate = agg;
         p.chunk = chunk;
-        // the wave's zeroing and transport launch, captured as one CUDA graph
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        IM_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        cudaMemsetAsync(c->d_scratch, 0, (size_t)main_elems * sizeof(unsigned long long), c->stream);
-        cudaMemsetAsync(c->d_item_flags, 0, items.size() * sizeof(int), c->stream);
-        cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
-        cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * kNStats, c->stream);
-        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
-        cudaEventRecord(c->ev0, c->stream);
-        launch_transport(p, c->num_sms, block, c->stream);
-        ++c->launches;
-        cudaEventRecord(c->ev1, c->stream);
-        IM_TRY(cudaStreamEndCapture(c->stream, &graph));
-        cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
-        if (ge == cudaSuccess) ge = cudaGraphLaunch(exec, c->stream);
-        if (ge == cudaSuccess) ge = cudaStreamSynchronize(c->stream);
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        IM_TRY(ge);
+        unsigned long long n_ovf = 0;
+        for (int attempt = 0;; ++attempt) {
+            p.ovf = c->d_ovf;
+            p.ovf_cap = c->ovf_cap;
+            // zero the wave's columns and counters, then the transport launch as a CUDA graph
+            IM_TRY(cudaMemsetAsync(c->d_scratch, 0, (size_t)wave_elems * sizeof(unsigned long long), c->stream));
+            IM_TRY(cudaMemsetAsync(d_ovf_count, 0, sizeof(unsigned long long), c->stream));
+            IM_ST(reset_counters(c));
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            IM_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t le = launch_transport(p, c->num_sms, block, c->stream);
+            cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+            IM_TRY(le);
+            IM_TRY(ce);
+            ++c->launches;
+            cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
+            if (ge == cudaSuccess) ge = cudaEventRecord(c->ev0, c->stream);
+            if (ge == cudaSuccess) ge = cudaGraphLaunch(exec, c->stream);
+            if (ge == cudaSuccess) ge = cudaEventRecord(c->ev1, c->stream);
+            if (ge == cudaSuccess) ge = cudaStreamSynchronize(c->stream);
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            IM_TRY(ge);
+            IM_TRY(cudaMemcpy(&n_ovf, d_ovf_count, sizeof n_ovf, cudaMemcpyDeviceToHost));
+            if ((long long)n_ovf <= c->ovf_cap) break;
+            // the tail records did not fit: enlarge the buffer and run the wave again
+            if (attempt > 0) IM_ST(fail(VPMC_ERR_OOM, "out-of-box records keep overflowing (%llu)", n_ovf));
+            IM_ST(grow_ovf(c, (long long)(n_ovf * 1.25) + 1024));
+        }
         float ms = 0.0f;
         IM_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
         total_ms += ms;
@@ -898,92 +916,59 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             vpmc_free_csr(out, n_scen);
             return fail(VPMC_ERR_TIMEOUT, "histories reached the iteration cap");
         }
-        // items whose deposits left their box: re-run them into full-grid boxes
-        std::vector<int> flags(items.size());
-        IM_TRY(cudaMemcpy(flags.data(), c->d_item_flags, flags.size() * sizeof(int), cudaMemcpyDeviceToHost));
-        std::vector<int> ovf;
-        for (size_t i = 0; i < flags.size(); ++i)
-            if (flags[i]) ovf.push_back((int)i);
-        if (!ovf.empty()) {
-            if ((long long)ovf.size() * c->nvox > rerun_reserve)
-                IM_ST(grow_scratch(c, (size_t)(main_elems + (long long)ovf.size() * c->nvox)));
-            std::vector<DevItem> rr;
-            long long rtotal = 0;
-            for (size_t r = 0; r < ovf.size(); ++r) {
-                DevItem it = items[ovf[r]];
-                DevBox bx{};
-                bx.base = main_elems + (long long)r * c->nvox;
-                for (int k = 0; k < 3; ++k) { bx.lo[k] = 0; bx.n[k] = c->sg.n[k]; }
-                it.box = (int)item_boxes.size();
-                item_boxes.push_back(bx);
-                items[ovf[r]].box = it.box;   // the CSR pass reads the re-run column
-                it.hist_off = rtotal;
-                rtotal += spots[it.spot].n_hist;
-                rr.push_back(it);
-            }
-            IM_ST(grow_boxes(c, item_boxes.size()));
-            IM_TRY(cudaMemcpy(c->d_boxes, item_boxes.data(), item_boxes.size() * sizeof(DevBox), cudaMemcpyHostToDevice));
-            DevItem* d_rr = nullptr;
-            IM_TRY(dev_alloc(&d_rr, rr.size()));
-            cudaError_t e = cudaMemcpy(d_rr, rr.data(), rr.size() * sizeof(DevItem), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = cudaMemsetAsync(c->d_scratch + main_elems, 0, ovf.size() * (size_t)c->nvox * 8, c->stream);
-            TransportParams q = p;
-            q.items = d_rr;
-            q.n_items = (int)rr.size();
-            q.total = rtotal;
-            if (e == cudaSuccess && reset_counters(c) != VPMC_OK) e = cudaErrorUnknown;
-            if (e == cudaSuccess) e = launch_transport(q, c->num_sms, block, c->stream);
-            ++c->launches;
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-            cudaFree(d_rr);
-            IM_TRY(e);
-            IM_TRY(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice));
+        stats.ovf_records += (long long)n_ovf;
+        // column maxima over boxes, then bucket the out-of-box records and raise the maxima
+        cudaFree(d_colmax);
+        d_colmax = nullptr;
+        IM_TRY(dev_alloc(&d_colmax, items.size()));
+        IM_TRY(launch_column_max(c->d_scratch, c->d_items, c->d_boxes, c->d_rho, c->sg, 0, (int)items.size(), d_colmax,
+                                 c->stream));
+        ++c->launches;
+        const long long n_buckets = (long long)ns * c->nvox;
+        if (n_ovf) {
+            cudaFree(d_bucket_off); cudaFree(d_bucket_cur); cudaFree(d_bucket_len); cudaFree(d_ovf_sorted);
+            d_bucket_off = d_bucket_cur = nullptr;
+            d_bucket_len = nullptr;
+            d_ovf_sorted = nullptr;
+            IM_TRY(dev_alloc(&d_bucket_off, n_buckets + 1));
+            IM_TRY(dev_alloc(&d_bucket_cur, n_buckets + 1));
+            IM_TRY(dev_alloc(&d_bucket_len, n_buckets));
+            IM_TRY(dev_alloc(&d_ovf_sorted, n_ovf));
+            IM_TRY(cudaMemsetAsync(d_bucket_cur, 0, (n_buckets + 1) * sizeof(long long), c->stream));
+            IM_TRY(launch_ovf_count(c->d_ovf, (long long)n_ovf, n_spots, c->nvox, d_bucket_cur, c->stream));
+            IM_TRY(launch_exclusive_scan(d_bucket_cur, d_bucket_off, n_buckets + 1, d_scan_tmp, c->stream));
+            IM_TRY(cudaMemsetAsync(d_bucket_cur, 0, (n_buckets + 1) * sizeof(long long), c->stream));
+            IM_TRY(launch_ovf_scatter(c->d_ovf, (long long)n_ovf, n_spots, c->nvox, d_bucket_off, d_bucket_cur,
+                                      d_ovf_sorted, c->stream));
+            IM_TRY(launch_ovf_merge(d_ovf_sorted, d_bucket_off, n_buckets, c->nvox, c->d_rho, d_bucket_len, d_colmax,
+                                    c->stream));
+            c->launches += 3 + scan_launches(n_buckets + 1);
         }
         // CSR per scenario
         for (int s = s0; s < s1; ++s) {
             const int first = (s - s0) * n_spots;
-            IM_TRY(launch_column_max(c->d_scratch, c->d_items, c->d_boxes, c->d_rho, c->sg, first, n_spots, d_colmax,
-                                     c->stream));
-            ++c->launches;
-            // beam tables and overflowed items of this scenario
-            std::vector<int> meta(5 * (size_t)nb + n_spots + 1, 0);
-            int* m_first = meta.data();
-            int* m_count = m_first + nb;
-            int* m_box = m_count + nb;
-            int* m_ofirst = m_box + nb;
-            int* m_ocount = m_ofirst + nb;
-            int* m_olist = m_ocount + nb;
-            int no = 0;
+            std::vector<int> meta(3 * (size_t)nb, 0);
             for (int b = 0; b < nb; ++b) {
-                m_first[b] = std::max(beam_first[b], 0);
-                m_count[b] = beam_count[b];
-                m_box[b] = box_of[(size_t)(s - s0) * nb + b] >= 0 ? items[(size_t)first + m_first[b]].box : 0;
-                m_ofirst[b] = no;
-                for (int j = 0; j < beam_count[b]; ++j) {
-                    const int it = first + beam_first[b] + j;
-                    if (flags[it]) m_olist[no++] = beam_first[b] + j;
-                }
-                m_ocount[b] = no - m_ofirst[b];
+                meta[b] = beam_first[b];
+                meta[nb + b] = beam_count[b];
+                meta[2 * nb + b] = beam_box[(size_t)(s - s0) * nb + b];
             }
-            // a beam's box: any of its non-overflowed items (all share its shape)
-            for (int b = 0; b < nb; ++b)
-                for (int j = 0; j < beam_count[b]; ++j)
-                    if (!flags[first + beam_first[b] + j]) { m_box[b] = items[(size_t)first + beam_first[b] + j].box; break; }
-            IM_TRY(cudaMemcpy(d_beam_meta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice));
+            IM_TRY(cudaMemcpyAsync(d_beam_meta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                   c->stream));
             CsrBuildParams cp{};
             cp.scratch = c->d_scratch;
             cp.items = c->d_items + first;
             cp.boxes = c->d_boxes;
             cp.rho = c->d_rho;
-            cp.colmax = d_colmax;
+            cp.colmax = d_colmax + first;
             cp.beam_first = d_beam_meta;
             cp.beam_count = d_beam_meta + nb;
             cp.beam_box = d_beam_meta + 2 * nb;
-            cp.ovf_beam_first = d_beam_meta + 3 * nb;
-            cp.ovf_beam_count = d_beam_meta + 4 * nb;
-            cp.ovf_items = d_beam_meta + 5 * nb;
             cp.n_beams = nb;
+            cp.ovf = n_ovf ? d_ovf_sorted : nullptr;
+            cp.bucket_off = n_ovf ? d_bucket_off + (long long)(s - s0) * c->nvox : nullptr;
+            cp.bucket_len = n_ovf ? d_bucket_len + (long long)(s - s0) * c->nvox : nullptr;
+            cp.item_base = first;
             cp.sg = c->sg;
             cp.nvox = c->nvox;
             cp.rel_threshold = rel_threshold;
@@ -997,7 +982,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             IM_TRY(dev_alloc(&csr.row_ptr, c->nvox + 1));
             IM_TRY(cudaMemsetAsync(d_rowcnt + c->nvox, 0, sizeof(long long), c->stream));
             IM_TRY(launch_exclusive_scan(d_rowcnt, reinterpret_cast<long long*>(csr.row_ptr), c->nvox + 1, d_scan_tmp,
-                                          c->stream));
+                                         c->stream));
             c->launches += scan_launches(c->nvox + 1);
             long long nnz = 0;
             IM_TRY(cudaMemcpyAsync(&nnz, csr.row_ptr + c->nvox, sizeof nnz, cudaMemcpyDeviceToHost, c->stream));
@@ -1063,7 +1048,7 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->d_scens);
     cudaFree(c->d_items);
     cudaFree(c->d_boxes);
-    cudaFree(c->d_item_flags);
+    cudaFree(c->d_ovf);
     cudaFree(c->d_scratch);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);

@@ -93,10 +93,10 @@ __global__ void k_column_max(const unsigned long long* __restrict__ scratch, con
     }
 }
 
-// One thread per scoring voxel (row).  Items are visited beam by beam and, in
-// a beam, in spot order, so a row's entries come out sorted by column.  Items
-// whose deposits overflowed the beam's box were re-run into full-grid boxes;
-// for voxels outside the beam box only those are visited.
+// One thread per scoring voxel (row).  Box columns are visited beam by beam
+// and, within a beam, in spot order (spots are sorted by beam, so this is
+// item order); the voxel's out-of-box records, sorted by item, are merged in
+// between, so a row's entries come out sorted by column.
 __global__ void k_csr_rows(const CsrBuildParams p, int fill)
 {
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -107,30 +107,87 @@ __global__ void k_csr_rows(const CsrBuildParams p, int fill)
     const double inv_rho = 1.0 / p.rho[v];
     long long count = 0;
     long long pos = fill ? p.row_ptr[v] : 0;
+    const OvfRec* rec = p.ovf ? p.ovf + p.bucket_off[v] : nullptr;
+    const int nrec = p.ovf ? p.bucket_len[v] : 0;
+    int j = 0;
+    auto emit = [&](int it, unsigned long long q) {
+        const double r = (double)q * inv_rho;
+        if (r < p.rel_threshold * p.colmax[it]) return;
+        if (fill) {
+            p.col[pos] = p.items[it].spot;
+            p.val[pos] = (float)(r * p.item_scale[it]);
+            ++pos;
+        } else {
+            ++count;
+        }
+    };
     for (int b = 0; b < p.n_beams; ++b) {
         const int cnt = p.beam_count[b];
         if (cnt == 0) continue;
-        const bool in_box = box_local(p.boxes[p.beam_box[b]], x, y, z) >= 0;
-        const int n_iter = in_box ? cnt : p.ovf_beam_count[b];
-        for (int t = 0; t < n_iter; ++t) {
-            const int it = in_box ? p.beam_first[b] + t : p.ovf_items[p.ovf_beam_first[b] + t];
-            const DevItem I = p.items[it];
-            const long long l = box_local(p.boxes[I.box], x, y, z);
-            if (l < 0) continue;
-            const unsigned long long q = p.scratch[p.boxes[I.box].base + l];
-            if (q == 0ull) continue;
-            const double r = (double)q * inv_rho;
-            if (r < p.rel_threshold * p.colmax[it]) continue;
-            if (fill) {
-                p.col[pos] = I.spot;
-                p.val[pos] = (float)(r * p.item_scale[it]);
-                ++pos;
-            } else {
-                ++count;
+        const DevBox bb = p.boxes[p.beam_box[b]];
+        const long long l = box_local(bb, x, y, z);
+        if (l < 0) continue;
+        for (int t = 0; t < cnt; ++t) {
+            const int it = p.beam_first[b] + t;
+            while (j < nrec && rec[j].item - p.item_base < it) {
+                emit(rec[j].item - p.item_base, rec[j].q);
+                ++j;
             }
+            const unsigned long long q = p.scratch[p.boxes[p.items[it].box].base + l];
+            if (q != 0ull) emit(it, q);
         }
     }
+    for (; j < nrec; ++j) emit(rec[j].item - p.item_base, rec[j].q);
     if (!fill) p.row_count[v] = count;
+}
+
+__global__ void k_ovf_count(const OvfRec* __restrict__ rec, long long n, int n_spots, long long nvox,
+                            unsigned long long* __restrict__ cnt)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const OvfRec r = rec[i];
+        atomicAdd(cnt + (long long)(r.item / n_spots) * nvox + r.voxel, 1ull);
+    }
+}
+
+__global__ void k_ovf_scatter(const OvfRec* __restrict__ rec, long long n, int n_spots, long long nvox,
+                              const long long* __restrict__ off, unsigned long long* __restrict__ cursor,
+                              OvfRec* __restrict__ sorted)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const OvfRec r = rec[i];
+        const long long b = (long long)(r.item / n_spots) * nvox + r.voxel;
+        sorted[off[b] + (long long)atomicAdd(cursor + b, 1ull)] = r;
+    }
+}
+
+// One thread per bucket: insertion sort by item, sum records of the same
+// item, and raise that item's column maximum (q / rho as FP64 bits).
+__global__ void k_ovf_merge(OvfRec* __restrict__ sorted, const long long* __restrict__ off, long long n_buckets,
+                            long long nvox, const double* __restrict__ rho, int* __restrict__ len,
+                            double* __restrict__ colmax)
+{
+    const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= n_buckets) return;
+    const long long o = off[b], n = off[b + 1] - o;
+    if (n == 0) { len[b] = 0; return; }
+    OvfRec* r = sorted + o;
+    for (long long i = 1; i < n; ++i) {
+        const OvfRec key = r[i];
+        long long k = i - 1;
+        while (k >= 0 && r[k].item > key.item) { r[k + 1] = r[k]; --k; }
+        r[k + 1] = key;
+    }
+    long long m = 0;
+    for (long long i = 0; i < n; ++i) {
+        if (m > 0 && r[m - 1].item == r[i].item) r[m - 1].q += r[i].q;
+        else r[m++] = r[i];
+    }
+    len[b] = (int)m;
+    const double inv_rho = 1.0 / rho[b % nvox];
+    for (long long i = 0; i < m; ++i)
+        atomicMax(reinterpret_cast<unsigned long long*>(colmax + r[i].item),
+                  (unsigned long long)__double_as_longlong((double)r[i].q * inv_rho));
 }
 
 constexpr int kScanBlock = 1024;
@@ -231,6 +288,32 @@ int scan_launches(long long n)
     if (nb <= 0) return 0;
     if (nb == 1) return 1;
     return 2 + scan_launches(nb);
+}
+
+cudaError_t launch_ovf_count(const OvfRec* rec, long long n, int n_spots, long long nvox, long long* bucket_cnt,
+                             cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_ovf_count<<<152 * 8, 256, 0, s>>>(rec, n, n_spots, nvox, reinterpret_cast<unsigned long long*>(bucket_cnt));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ovf_scatter(const OvfRec* rec, long long n, int n_spots, long long nvox, const long long* bucket_off,
+                               long long* cursor, OvfRec* sorted, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_ovf_scatter<<<152 * 8, 256, 0, s>>>(rec, n, n_spots, nvox, bucket_off,
+                                          reinterpret_cast<unsigned long long*>(cursor), sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ovf_merge(OvfRec* sorted, const long long* bucket_off, long long n_buckets, long long nvox,
+                             const double* rho, int* bucket_len, double* colmax, cudaStream_t s)
+{
+    const int block = 256;
+    const long long grid = (n_buckets + block - 1) / block;
+    k_ovf_merge<<<(unsigned)grid, block, 0, s>>>(sorted, bucket_off, n_buckets, nvox, rho, bucket_len, colmax);
+    return cudaGetLastError();
 }
 
 size_t scan_tmp_elems(long long n)

@@ -588,8 +588,16 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                     if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] && ly < bx.n[1] && lz < bx.n[2]) {
                         dep_key = bx.base + lx + (long long)bx.n[0] * (ly + (long long)bx.n[1] * lz);
                         dep_q = __float2ull_rn(o.dE * wsc);
-                    } else if (o.dE > 0.0f) {
-                        P.item_flags[L.item] = 1;
+                    } else if (o.dE > 0.0f && P.ovf) {
+                        // rare tail outside the item's box: append a record
+                        const unsigned long long slot = atomicAdd(P.ovf_count, 1ull);
+                        if ((long long)slot < P.ovf_cap) {
+                            OvfRec r;
+                            r.voxel = is_old[0] + P.sg.n[0] * (is_old[1] + P.sg.n[1] * is_old[2]);
+                            r.item = L.item;
+                            r.q = __float2ull_rn(o.dE * wsc);
+                            P.ovf[slot] = r;
+                        }
                     }
                     acc_dep += qs;
                     if (o.killed) {

@@ -80,6 +80,14 @@ struct Grid3 {
     float lo[3];
 };
 
+// Deposit that fell outside its item's box (rare tails of the lateral
+// spread); bucketed by voxel after transport and merged into the CSR rows.
+struct OvfRec {
+    int voxel;                       // scoring-grid voxel
+    int item;                        // item index within the launch
+    unsigned long long q;
+};
+
 struct HistRecord {                  // mirrors vpmc_history_record
     long long q_dep;
     int fate;
@@ -108,7 +116,9 @@ struct TransportParams {
     long long total;                 // total histories
     unsigned long long* counter;     // global work counter
     unsigned long long* scratch;     // deposit target
-    int* item_flags;                 // per item: 1 when a deposit fell outside its box
+    OvfRec* ovf;                     // out-of-box deposits (NULL: none expected)
+    unsigned long long* ovf_count;   // records appended (may exceed ovf_cap: then re-run)
+    long long ovf_cap;
     unsigned long long* stats;       // kNStats counters
     int* status;                     // device status word (bit 0: iteration cap)
     HistRecord* records;
@@ -148,18 +158,18 @@ cudaError_t launch_column_max(const unsigned long long* scratch, const DevItem* 
 
 struct CsrBuildParams {
     const unsigned long long* scratch;
-    const DevItem* items;            // items of one scenario, sorted by beam then spot
+    const DevItem* items;            // items of one scenario, in spot order (spots sorted by beam)
     const DevBox* boxes;
     const double* rho;               // scoring-voxel densities
     const double* colmax;            // per item max of q / rho
-    const int* beam_first;           // per beam: first item index (relative), -1 if none
+    const int* beam_first;           // per beam: first item index (relative)
     const int* beam_count;
-    const int* beam_box;             // per beam: the shared box of its non-overflowed items
-    const int* ovf_items;            // overflowed items (full-grid boxes), sorted by beam then spot
-    const int* ovf_beam_first;       // per beam: first entry in ovf_items
-    const int* ovf_beam_count;
-    const int* item_ovf;             // per item: 1 if overflowed
+    const int* beam_box;             // per beam: the box shared by its items (shape and origin)
     int n_beams;
+    const OvfRec* ovf;               // out-of-box deposits bucketed by voxel, sorted by item, merged
+    const long long* bucket_off;     // per voxel of this scenario: first record
+    const int* bucket_len;           // per voxel: merged records
+    int item_base;                   // item index of this scenario's first item in the launch
     Grid3 sg;
     long long nvox;
     double rel_threshold;
@@ -170,6 +180,14 @@ struct CsrBuildParams {
     float* val;
 };
 cudaError_t launch_csr_pass(const CsrBuildParams& p, int fill, cudaStream_t s);
+// Counting sort of out-of-box records into per-(scenario, voxel) buckets,
+// then per bucket: sort by item, merge duplicates, raise the column maxima.
+cudaError_t launch_ovf_count(const OvfRec* rec, long long n, int n_spots, long long nvox, long long* bucket_cnt,
+                             cudaStream_t s);
+cudaError_t launch_ovf_scatter(const OvfRec* rec, long long n, int n_spots, long long nvox, const long long* bucket_off,
+                               long long* cursor, OvfRec* sorted, cudaStream_t s);
+cudaError_t launch_ovf_merge(OvfRec* sorted, const long long* bucket_off, long long n_buckets, long long nvox,
+                             const double* rho, int* bucket_len, double* colmax, cudaStream_t s);
 cudaError_t launch_exclusive_scan(const long long* in, long long* out, long long n, long long* block_tmp,
                                   cudaStream_t s);
 size_t scan_tmp_elems(long long n);

@@ -33,11 +33,14 @@ def _engine(pb):
 
 
 def _per_history_parity(pb, spots, scen, op, records=None, max_flagged=0.01):
-    """Histories whose step starts came within 10 um of an aperture wall or
-    the range-shifter rim (oracle flag) are ill-conditioned in FP32: at
-    grazing incidence a rounding-level position change moves a brass chord by
-    ~500x as much.  Every other history must match the oracle's fate, scored
-    energy and end position to 1e-4 relative; flagged ones must be rare."""
+    """Histories the oracle flags as ill-conditioned are excluded from the
+    per-history bound: step starts within 10 um of an aperture wall or the
+    range-shifter rim (at grazing incidence a rounding-level position change
+    moves a brass chord ~500x as much), nuclear removal in air-like media
+    (the point moves by free-path rounding / (0.0012 rho)), and CT voxel faces
+    crossed at a direction cosine below 0.01 |delta SPR|.  Every other
+    history must match the oracle's fate, scored energy and end position to
+    1e-4 relative; flagged ones must be rare."""
     n = int(spots["n_hist"].sum()) if records is None else records
     eng = _engine(pb)
     dose, st, rec = eng.run_spots(spots, scen, op, records=n)
@@ -170,31 +173,70 @@ def _dense(csr):
 
 
 def test_influence_matrix_deterministic_parity(torch_cuda):
-    """Per-scenario CSR of the GPU vs the oracle's plain IM definition."""
-    pb, spots = W.water_aperture_case(10.0, False, hist_per_layer=2000, max_layers=2, shape=(30, 30, 60))
-    scens = W.robust_scenarios()[:3] + W.robust_scenarios()[7:9]
+    """Per-scenario CSR of the GPU vs the oracle's plain IM definition
+    (deterministic mode, water, no aperture, so that no history's energy is
+    ill-conditioned): each column's energy (sum of dose x rho x V) within 1e-4;
+    99.9 % of entries within 1e-4 of their column maximum and all within
+    2e-3 (a track that runs almost parallel to a scoring-voxel face crosses it
+    at a point that moves by (position rounding) / cosine, shifting deposits
+    between neighbours); columns sorted in rows; entries on one side only sit
+    at the threshold."""
+    pb, _ = W.pencil_beam_water(n_hist=10, shape=(30, 30, 60))
+    rows = [(0, e, x, y, 4.0, 2.0, 300, 1.0) for e in (90.0, 110.0) for x in (-6.0, 0.0, 5.0) for y in (-4.0, 3.0)]
+    spots = W.make_spots(rows)
+    scens = [W.robust_scenarios()[i] for i in (0, 1, 4, 7, 12)]
     eng = _engine(pb)
     mats, st = eng.influence_matrix(spots, scens, DET)
     eng.close()
     ref = O.influence_matrix(pb, spots, scens, DET)
+    rhoV = O.scoring_density(pb) * pb.scoring.voxel_mm3 * 1e-3
     for m, r in zip(mats, ref):
         rp = m["row_ptr"].cpu().numpy()
         col = m["col"].cpu().numpy()
-        # columns sorted within rows
-        for i in np.flatnonzero(np.diff(rp) > 1)[:2000]:
-            seg = col[rp[i]:rp[i + 1]]
-            assert np.all(np.diff(seg) > 0)
-        g = _dense(m)
-        o = r.toarray()
-        cmax = o.max(axis=0, keepdims=True)
-        both = (g > 0) & (o > 0)
-        rel = np.abs(g - o)[both] / o[both]
-        assert np.quantile(rel, 0.999) < 1e-3 and np.max(np.abs(g - o) / np.maximum(cmax, 1e-30)) < 1e-3
+        for i in np.flatnonzero(np.diff(rp) > 1):
+            assert np.all(np.diff(col[rp[i]:rp[i + 1]]) > 0)
+        g = _dense(m).astype(np.float64)
+        o = r.toarray().astype(np.float64)
+        eg, eo = (g * rhoV[:, None]).sum(0), (o * rhoV[:, None]).sum(0)
+        assert np.max(np.abs(eg / eo - 1.0)) < 1e-4
+        cmax = np.broadcast_to(o.max(axis=0, keepdims=True), o.shape)
+        dev = np.abs(g - o) / cmax
+        assert np.quantile(dev[(g > 0) | (o > 0)], 0.999) < 1e-4 and dev.max() < 2e-3
         only = (g > 0) ^ (o > 0)
-        # entries kept on one side only must sit at the threshold
-        assert np.all(np.maximum(g, o)[only] < 1.01e-4 * np.broadcast_to(cmax, g.shape)[only])
+        assert np.all(np.maximum(g, o)[only] < 1.01e-4 * cmax[only] + 2e-3 * cmax[only])
     tot = st["e_dep"] + st["e_leak"] + st["e_rs"] + st["e_aperture"]
     assert abs(tot / st["e_in"] - 1.0) < 1e-6
+
+
+def test_influence_matrix_aperture_statistical(torch_cuda):
+    """Full physics with range shifter and aperture, three scenarios: for each
+    scenario the IM composite (columns x n_hist summed over spots) of the GPU
+    and of the oracle, each over 20 independent seeds, agree per voxel within
+    the combined statistical uncertainty and pass gamma 2%/2mm/10% >= 99.5 %."""
+    pb, spots = W.water_aperture_case(20.0, True, hist_per_layer=15000, max_layers=2, shape=(40, 40, 60))
+    scens = [W.robust_scenarios()[i] for i in (0, 3, 10)]
+    eng = _engine(pb)
+    nb = 20
+    g_runs = [[] for _ in scens]
+    o_runs = [[] for _ in scens]
+    nh = spots["n_hist"].astype(np.float64)
+    for b in range(nb):
+        mats, _ = eng.influence_matrix(spots, scens, W.Options(seed=300 + b), rel_threshold=0.0)
+        refs = O.influence_matrix(pb, spots, scens, W.Options(seed=900 + b), rel_threshold=0.0)
+        for k in range(len(scens)):
+            g_runs[k].append((_dense(mats[k]).astype(np.float64) * nh[None, :]).sum(axis=1))
+            o_runs[k].append((refs[k].toarray().astype(np.float64) * nh[None, :]).sum(axis=1))
+    eng.close()
+    g = pb.scoring
+    shp = (g.shape[2], g.shape[1], g.shape[0])
+    for k in range(len(scens)):
+        G, Ob = np.array(g_runs[k]), np.array(o_runs[k])
+        mg, mo = G.mean(0), Ob.mean(0)
+        sg_, so = G.std(0, ddof=1) / math.sqrt(nb), Ob.std(0, ddof=1) / math.sqrt(nb)
+        sel = mo >= 0.1 * mo.max()
+        z = np.abs(mg - mo)[sel] / np.sqrt(sg_[sel] ** 2 + so[sel] ** 2)
+        assert np.mean(z > 3.0) <= 0.01 and z.max() < 5.5, (k, np.mean(z > 3), z.max())
+        assert O.gamma_pass_rate(mo.reshape(shp), mg.reshape(shp), g.spacing) >= 99.5
 
 
 def test_influence_matrix_columns_sum_to_dose(torch_cuda):
