@@ -307,7 +307,7 @@ def main():
 def run_ncu_case(args):
     """Every 10th spot of the set's nominal scenario (about 3.3e6 histories,
     full physics) through vpmc_run_spots with a fixed launch (512 threads,
-    warp-aggregated atomics, chunk 32): one k_transport launch per step and a
+    warp-aggregated atomics, chunk 32, 640 threads): one k_transport launch per step and a
     16 MB scoring grid, small enough for a full ncu capture."""
     import torch
     from paper_2307_01416_gb300 import vpmc
@@ -317,7 +317,7 @@ def run_ncu_case(args):
     eng = vpmc.Engine(pb)
     opts = W.Options(seed=1234)
     for i in range(args.warmup + args.steps):
-        dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=512, aggregate=1, chunk=32)
+        dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=640, aggregate=1, chunk=32)
         print(json.dumps({"case": "ncu", "iter": i, "histories": st["histories"], "steps": st["steps"],
                           "kernel_ms": st["ms"], "steps_per_s": st["steps"] / (st["ms"] / 1000.0)}))
     eng.close()

@@ -73,8 +73,8 @@ SPOT_DTYPE = np.dtype([("beam", np.int32), ("spot_key", np.int32), ("energy", np
                        ("y", np.float64), ("sigma", np.float64), ("div_mrad", np.float64),
                        ("h_begin", np.int64), ("n_hist", np.int64), ("weight", np.float64)], align=True)
 RECORD_DTYPE = np.dtype([("fate", np.int32), ("steps", np.int32), ("e_dep", np.float64), ("e_end", np.float64),
-                         ("pos", np.float64, (3,)), ("q_dep", np.int64), ("flags", np.int32), ("pad", np.int32)],
-                        align=True)
+                         ("pos", np.float64, (3,)), ("q_dep", np.int64), ("flags", np.int32), ("pad", np.int32),
+                         ("path", np.float64), ("track", np.float64)], align=True)
 FLAG_NEAR_WALL, FLAG_NEAR_RIM, FLAG_NUC_LOW_DENSITY, FLAG_GRAZING_FACE = 1, 2, 4, 8
 
 _lib = None

@@ -349,6 +349,8 @@ typedef struct {
                            cosine below 0.01 |delta SPR| (the crossing point
                            moves by (position rounding) / cosine)          */
     int32_t pad;
+    double path;        /* path length travelled in the patient grid, mm     */
+    double track;       /* whole track length from the source plane, mm      */
 } orc_record;
 
 /* Distance below which a device boundary makes a history ill-conditioned:
@@ -572,6 +574,7 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
         double tdn = -bm->rs_down_to_iso, tup = tdn - thick;
         double sdr = (tup - pt.p[2]) / pt.d[2];
         for (int k = 0; k < 3; ++k) pt.p[k] += sdr * pt.d[k];
+        rec->track += sdr;
         orc_medium med = {ORC_PMMA, ORC_MAT[ORC_PMMA].rho, ORC_MAT[ORC_PMMA].rho, ORC_MAT[ORC_PMMA].za, ORC_MAT[ORC_PMMA].X0};
         pt.R = orc_range(ORC_PMMA, pt.E);
         for (;;) {
@@ -583,6 +586,7 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
                 if (pt.d[2] <= 0.0) goto leak;
                 double sf = (tdn - pt.p[2]) / pt.d[2];
                 for (int k = 0; k < 3; ++k) pt.p[k] += sf * pt.d[k];
+                rec->track += sf;
                 break;
             }
             double sg = INFINITY;
@@ -591,6 +595,7 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
             else if (pt.d[2] < 0.0) { sg = (tup - pt.p[2]) / pt.d[2]; down = 0; }
             if (sg < 0.0) sg = 0.0;   /* scattering offsets can leave it past the plane */
             ch_step(&med, &pt, sg, op, &st, &so);
+            rec->track += so.s;
             tl[3] += so.dE;
             tl[7] += 1.0;
             rec->steps += 1;
@@ -614,6 +619,7 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
         if (pt.d[2] <= 0.0) goto leak;
         double sdr = (tup - pt.p[2]) / pt.d[2];
         for (int k = 0; k < 3; ++k) pt.p[k] += sdr * pt.d[k];
+        rec->track += sdr;
         orc_medium med = {ORC_BRASS, ORC_MAT[ORC_BRASS].rho, ORC_MAT[ORC_BRASS].rho, ORC_MAT[ORC_BRASS].za, ORC_MAT[ORC_BRASS].X0};
         int forced_brass = 0;
         pt.R = orc_range(ORC_BRASS, pt.E);
@@ -631,17 +637,20 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
                 double sw = orc_first_wall_hit(poly, bm->nvert, pt.p[0], pt.p[1], pt.d[0], pt.d[1]);
                 if (sw < sg) {
                     for (int k = 0; k < 3; ++k) pt.p[k] += sw * pt.d[k];
+                    rec->track += sw;
                     forced_brass = 1;
                     continue;
                 }
                 if (!isfinite(sg)) goto fail;
                 for (int k = 0; k < 3; ++k) pt.p[k] += sg * pt.d[k];
+                rec->track += sg;
                 if (!down) goto leak;
                 break;
             }
             /* brass: condensed-history step with brass physics */
             forced_brass = 0;
             ch_step(&med, &pt, sg, op, &st, &so);
+            rec->track += so.s;
             tl[4] += so.dE;
             tl[7] += 1.0;
             rec->steps += 1;
@@ -691,6 +700,7 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
         double tin = tmin > 0.0 ? tmin : 0.0;
         if (!(tmax > tin)) goto leak;
         for (int k = 0; k < 3; ++k) P[k] += tin * D[k];
+        rec->track += tin;
         int ic[3], is[3];
         for (int k = 0; k < 3; ++k) {
             int a = (int)floor((P[k] - lo[k]) / dl[k]);
@@ -726,6 +736,8 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
             ch_step(&med, &pt, svox, op, &st, &so);
             tl[7] += 1.0;
             rec->steps += 1;
+            rec->path += so.s;
+            rec->track += so.s;
             /* score the step's deposit in the voxel where the step starts */
             {
                 int64_t q = (int64_t)nearbyint(so.dE * (rc->mode == 0 ? sp->weight : 1.0) * fscale);

@@ -203,8 +203,8 @@ vpmc_status check_opts(const vpmc_opts* o)
 {
     if (!o) return VPMC_OK;
     if (o->frac_bits < 0 || o->frac_bits > 40) return fail(VPMC_ERR_ARG, "frac_bits %d outside [0, 40]", o->frac_bits);
-    if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 512 || o->block_size % 32))
-        return fail(VPMC_ERR_ARG, "block_size %d: must be 0 or a multiple of 32 in [32, 512]", o->block_size);
+    if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 640 || o->block_size % 32))
+        return fail(VPMC_ERR_ARG, "block_size %d: must be 0 or a multiple of 32 in [32, 640]", o->block_size);
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 1)
         return fail(VPMC_ERR_ARG, "blocks_per_sm %d: the kernel's shared memory allows one block per SM", o->blocks_per_sm);
     if (o->chunk < 0 || o->chunk > 4096) return fail(VPMC_ERR_ARG, "chunk %d outside [0, 4096]", o->chunk);
@@ -263,7 +263,7 @@ vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc
     p.rec_cap = 0;
     struct Cand { int block, agg, chunk; };
     std::vector<Cand> cands;
-    for (int block : {256, 384, 512})
+    for (int block : {384, 512, 640})
         for (int agg : {0, 1})
             for (int chunk : {32, 128}) {
                 if (o.block_size && block != o.block_size) continue;

@@ -143,7 +143,7 @@ void build_tables(const double* curve15, TablesImage* img)
         for (int j = 0; j < kNR; ++j) img->Einv[mat][j] = (float)energy[j];
         img->mat[mat].za = (float)kMaterials[mat].z_over_a;
         img->mat[mat].rho = (float)kMaterials[mat].density;
-        img->mat[mat].x0_mmgcc = (float)(kMaterials[mat].radiation_length_gcm2 * 10.0);
+        img->mat[mat].inv_x0 = (float)(1.0 / (kMaterials[mat].radiation_length_gcm2 * 10.0));
         img->mat[mat].inv_dR = (float)(1.0 / d_range);
     }
     for (int i = 0; i < kNHU; ++i) {

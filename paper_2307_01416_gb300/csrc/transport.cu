@@ -44,12 +44,42 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
 // ((x >> 9) + 1/2) * 2^-23: 23-bit uniform in (0, 1), exact in FP32.
 __device__ __forceinline__ float u01(uint32_t x) { return fmaf(__uint2float_rn(x >> 9), 0x1p-23f, 0x1p-24f); }
 
+// Box-Muller with accurate functions (source sampling, once per history).
 __device__ __forceinline__ float2 box_muller(float u1, float u2)
 {
     const float r = sqrtf(-2.0f * logf(u1));
     float s, c;
     sincospif(2.0f * u2, &s, &c);
     return make_float2(r * c, r * s);
+}
+
+// Box-Muller with hardware approximations (per-step physics).  u1 <= 1 - 2^-24,
+// so -2 ln u1 > 0; the clamp only guards the approximate logarithm.
+__device__ __forceinline__ float2 box_muller_fast(float u1, float u2)
+{
+    const float l = fmaxf(-2.0f * __logf(u1), 0.0f);
+    const float r = l * rsqrtf(fmaxf(l, 1e-30f));
+    float s, c;
+    __sincosf(6.28318530717958647f * u2, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
+// Two Philox4x32-10 blocks with the same key, rounds interleaved for ILP.
+__device__ __forceinline__ void philox_pair(uint4& a, uint4& b, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t ah0 = __umulhi(0xD2511F53u, a.x), al0 = 0xD2511F53u * a.x;
+        const uint32_t ah1 = __umulhi(0xCD9E8D57u, a.z), al1 = 0xCD9E8D57u * a.z;
+        const uint32_t bh0 = __umulhi(0xD2511F53u, b.x), bl0 = 0xD2511F53u * b.x;
+        const uint32_t bh1 = __umulhi(0xCD9E8D57u, b.z), bl1 = 0xCD9E8D57u * b.z;
+        a = make_uint4(ah1 ^ a.y ^ k.x, al1, ah0 ^ a.w ^ k.y, al0);
+        b = make_uint4(bh1 ^ b.y ^ k.x, bl1, bh0 ^ b.w ^ k.y, bl0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
 }
 
 __device__ __forceinline__ float range_of(const float* __restrict__ R, float E)
@@ -124,7 +154,7 @@ __device__ __forceinline__ bool in_opening(const DevBeam& B, const float2* __res
 __device__ __forceinline__ void orthonormal_basis(const float n[3], float b1[3], float b2[3])
 {
     const float sign = copysignf(1.0f, n[2]);
-    const float a = -1.0f / (sign + n[2]);
+    const float a = __fdividef(-1.0f, sign + n[2]);
     const float b = n[0] * n[1] * a;
     b1[0] = 1.0f + sign * n[0] * n[0] * a;
     b1[1] = sign * b;
@@ -169,7 +199,7 @@ __device__ __forceinline__ void deposit_aggregated(unsigned long long* __restric
 
 struct Medium {
     int table;
-    float kappa, rho, za, x0;
+    float kappa, rho, za, inv_x0;
 };
 
 struct StepResult {
@@ -211,29 +241,36 @@ __device__ __forceinline__ void ch_step(const Smem& S, const Medium& m, float s_
     const float inv_dR = S.mat[m.table].inv_dR;
     const float E = L.E;
     const float R0 = L.R;
-    float s1 = (R0 - range_of(Rt, 0.99f * E)) / m.kappa;
-    if (!(s1 > 0.0f)) s1 = R0 / m.kappa;
+    const float inv_kappa = __fdividef(1.0f, m.kappa);
+    float s1 = (R0 - range_of(Rt, 0.99f * E)) * inv_kappa;
+    if (!(s1 > 0.0f)) s1 = R0 * inv_kappa;
     const float mu = P.nuclear ? 0.0012f * m.rho : 0.0f;
     float s = 1.0f;
     int lim = 0;
     if (s1 < s) s = s1;
     if (s_geom < s) { s = s_geom; lim = 1; }
     if (mu > 0.0f) {
-        const float sn = L.nlam / mu;
+        const float sn = __fdividef(L.nlam, mu);
         if (sn < s) { s = sn; lim = 2; }
     }
     L.step += 1;
     if (lim == 2) L.nlam = 0.0f; else L.nlam -= mu * s;
 
+    // random numbers of this step: slot 1 (scattering) and slot 2 (straggling)
+    uint4 r1 = make_uint4(L.hist, L.step, 1u, 0u), r2 = make_uint4(L.hist, L.step, 2u, 0u);
+    if (P.mcs || P.straggling) philox_pair(r1, r2, key);
+
     const float R1 = R0 - s * m.kappa;
     const float Emean = R1 > 0.0f ? energy_of(Et, inv_dR, R1) : kEcut;
     float dE = E - Emean;
-    const float beta2 = E * (E + 2.0f * kMp) / ((E + kMp) * (E + kMp));
+    const float etot = E + kMp;
+    const float pc2 = E * (E + 2.0f * kMp);               // (pc)^2
+    const float inv_etot = __fdividef(1.0f, etot);
     if (P.straggling) {
-        const uint4 x = philox(make_uint4(L.hist, L.step, 2u, 0u), key);
-        const float2 z = box_muller(u01(x.x), u01(x.y));
-        const float var = 0.01569f * m.rho * m.za * s * (1.0f - 0.5f * beta2) / (1.0f - beta2);
-        dE += sqrtf(var) * z.x;
+        const float beta2 = pc2 * inv_etot * inv_etot;
+        const float2 z = box_muller_fast(u01(r2.x), u01(r2.y));
+        const float var = 0.01569f * m.rho * m.za * s * __fdividef(1.0f - 0.5f * beta2, 1.0f - beta2);
+        dE += fast_sqrt(var) * z.x;
     }
     dE = fminf(fmaxf(dE, 0.0f), E);
     const float Enew = E - dE;
@@ -255,24 +292,24 @@ __device__ __forceinline__ void ch_step(const Smem& S, const Medium& m, float s_
     for (int k = 0; k < 3; ++k) L.p[k] = fmaf(s, L.d[k], L.p[k]);
 
     if (P.mcs && !o.killed) {
-        const float x = s * m.rho / m.x0;
+        const float x = s * m.rho * m.inv_x0;
         float th0 = 0.0f;
         if (x >= 1e-6f) {
-            const float bcp = E * (E + 2.0f * kMp) / (E + kMp);
-            th0 = 13.6f / bcp * sqrtf(x) * (1.0f + 0.038f * logf(x));
+            const float bcp = pc2 * inv_etot;                 // beta c p
+            th0 = __fdividef(13.6f, bcp) * fast_sqrt(x) * (1.0f + 0.038f * __logf(x));
         }
-        const uint4 r = philox(make_uint4(L.hist, L.step, 1u, 0u), key);
-        const float2 za = box_muller(u01(r.x), u01(r.y));
-        const float2 zb = box_muller(u01(r.z), u01(r.w));
+        const float2 za = box_muller_fast(u01(r1.x), u01(r1.y));
+        const float2 zb = box_muller_fast(u01(r1.z), u01(r1.w));
         const float th1 = za.y * th0, th2 = zb.y * th0;
         const float dx1 = s * th0 * fmaf(za.x, 0.28867513459481287f, 0.5f * za.y);
         const float dx2 = s * th0 * fmaf(zb.x, 0.28867513459481287f, 0.5f * zb.y);
         float e1[3], e2[3];
         orthonormal_basis(L.d, e1, e2);
-        const float th = sqrtf(th1 * th1 + th2 * th2);
+        const float th2sq = th1 * th1 + th2 * th2;
+        const float th = fast_sqrt(th2sq);
         float sn, c;
-        sincosf(th, &sn, &c);
-        const float sc = th > 0.0f ? sn / th : 1.0f;
+        __sincosf(th, &sn, &c);
+        const float sc = th > 0.0f ? __fdividef(sn, th) : 1.0f;
         float nd[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -297,7 +334,7 @@ __device__ __forceinline__ void bev_to_patient(const DevBeam& B, const DevScen& 
 __device__ int enter_next_stage(const Smem& S, const TransportParams& P, const DevBeam& B, const DevScen& sc,
                                 Lane& L, int from)
 {
-    if (from < 0 && B.rs) {
+    if (from < 0 && B.rs) {   // just born
         const float sdr = (B.rs_tup - L.p[2]) / L.d[2];
 #pragma unroll
         for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
@@ -350,19 +387,26 @@ __device__ int enter_next_stage(const Smem& S, const TransportParams& P, const D
     return -1;
 }
 
-__device__ __forceinline__ int find_item(const DevItem* __restrict__ items, int n, long long g)
+// Largest i with items[i].hist_off <= g, searched by the whole warp: each
+// round the 32 lanes probe 32 evenly spaced entries (g is warp-uniform).
+__device__ __forceinline__ int find_item_warp(const DevItem* __restrict__ items, int n, long long g, int lane)
 {
-    int lo = 0, hi = n;   // items[lo].hist_off <= g < items[lo+1].hist_off
+    int lo = 0, hi = n;
     while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(&items[mid].hist_off) <= g) lo = mid; else hi = mid;
+        const int step = (hi - lo + 31) >> 5;
+        const int idx = lo + lane * step;
+        const bool le = idx < hi && __ldg(&items[idx].hist_off) <= g;
+        const unsigned m = __ballot_sync(kFull, le);
+        const int last = 31 - __clz(m);
+        lo = lo + last * step;
+        hi = min(lo + step, hi);
     }
     return lo;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
+__global__ void __launch_bounds__(640, 1) k_transport(const TransportParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     // stage the tables, beams, scenarios and polygons into shared memory
@@ -393,6 +437,7 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     long long pool_next = 0, pool_end = 0;      // warp-uniform
+    int pool_item = 0;                          // item of pool_next (warp-uniform)
     bool alive = false, done = false;
     Lane L;
     L.item = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.nsteps = 0; L.stage = 0; L.forced = 0;
@@ -404,7 +449,7 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
     uint2 key = make_uint2(0u, 0u);
 
     for (;;) {
-        // ---- refill lanes whose history has ended ----
+        // ---- hand new histories to lanes whose history has ended ----
         unsigned need = __ballot_sync(kFull, !alive && !done);
         while (need) {
             if (pool_next >= pool_end) {
@@ -424,12 +469,14 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                 }
                 pool_next = (long long)base;
                 pool_end = min((long long)base + P.chunk, P.total);
+                pool_item = find_item_warp(P.items, P.n_items, pool_next, lane);
             }
             const int take = (int)min((long long)__popc(need), pool_end - pool_next);
             const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
             if (mine) {
                 const long long g = pool_next + __popc(need & lt_mask);
-                const int it = find_item(P.items, P.n_items, g);
+                int it = pool_item;
+                while (it + 1 < P.n_items && __ldg(&P.items[it + 1].hist_off) <= g) ++it;
                 const DevItem I = P.items[it];
                 const DevBeam& B = S.beams[I.beam];
                 L.item = it;
@@ -456,19 +503,8 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                 } else {
                     L.nlam = __int_as_float(0x7f800000);
                 }
+                L.stage = -1;                       // enters its first stage in the next iteration
                 alive = true;
-                const int f = enter_next_stage(S, P, B, S.scens[I.scen], L, -1);
-                if (f >= 0) {
-                    // missed everything: record and retire at once
-                    acc_leak += __float2ull_rn(L.E * P.fscale);
-                    if (P.records && g < P.rec_cap) {
-                        HistRecord r;
-                        r.q_dep = 0; r.fate = f; r.steps = 0; r.e_dep = 0.0f; r.e_end = L.E;
-                        r.pos[0] = L.p[0]; r.pos[1] = L.p[1]; r.pos[2] = L.p[2]; r.pad = 0.0f;
-                        P.records[g] = r;
-                    }
-                    alive = false;
-                }
             }
             pool_next += take;
             need = __ballot_sync(kFull, !alive && !done);
@@ -481,8 +517,10 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
         // ---- one iteration of every live history ----
         long long dep_key = -1;
         unsigned long long dep_q = 0ull;
-        int fate = -1;
         if (alive) {
+            int fate = -1;
+            bool advance = false;                   // move to the next stage after this iteration
+            const int from = L.stage;
             const DevItem& I = P.items[L.item];
             const int beam = __ldg(&I.beam);
             const int scn = __ldg(&I.scen);
@@ -491,8 +529,11 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
             Medium m;
             float s_geom = __int_as_float(0x7f800000);
             bool do_ch = false, down = true;
+            float dc[3], ds[3];
             if (++L.iters > kMaxIter) {
                 fate = kErr;
+            } else if (L.stage < 0) {
+                advance = true;
             } else if (L.stage == 0) {
                 // ---- range shifter ----
                 if (L.p[0] * L.p[0] + L.p[1] * L.p[1] > B.rs_r2) {
@@ -501,14 +542,14 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                         const float sf = (B.rs_tdn - L.p[2]) / L.d[2];
 #pragma unroll
                         for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sf, L.d[k], L.p[k]);
-                        fate = enter_next_stage(S, P, B, SC, L, 0);
+                        advance = true;
                     }
                 } else {
                     if (L.d[2] > 0.0f) s_geom = (B.rs_tdn - L.p[2]) / L.d[2];
                     else if (L.d[2] < 0.0f) { s_geom = (B.rs_tup - L.p[2]) / L.d[2]; down = false; }
                     s_geom = fmaxf(s_geom, 0.0f);   // scattering offsets can leave it past the plane
                     m.table = kPMMA; m.kappa = S.mat[kPMMA].rho; m.rho = m.kappa; m.za = S.mat[kPMMA].za;
-                    m.x0 = S.mat[kPMMA].x0_mmgcc;
+                    m.inv_x0 = S.mat[kPMMA].inv_x0;
                     do_ch = true;
                 }
             } else if (L.stage == 1) {
@@ -528,12 +569,12 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                     } else {
 #pragma unroll
                         for (int k = 0; k < 3; ++k) L.p[k] = fmaf(s_geom, L.d[k], L.p[k]);
-                        fate = down ? enter_next_stage(S, P, B, SC, L, 1) : kLeak;
+                        if (down) advance = true; else fate = kLeak;
                     }
                 } else {
                     L.forced = 0;
                     m.table = kBrass; m.kappa = S.mat[kBrass].rho; m.rho = m.kappa; m.za = S.mat[kBrass].za;
-                    m.x0 = S.mat[kBrass].x0_mmgcc;
+                    m.inv_x0 = S.mat[kBrass].inv_x0;
                     do_ch = true;
                 }
             } else {
@@ -542,32 +583,29 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                 const int h = min(max((int)__ldg(P.ct + cidx), kHULo), kHULo + kNHU - 1);
                 const float2 rs = S.hu[h - kHULo];
                 m.table = kWater; m.kappa = rs.y * SC.spr_scale; m.rho = rs.x; m.za = S.mat[kWater].za;
-                m.x0 = S.mat[kWater].x0_mmgcc;
+                m.inv_x0 = S.mat[kWater].inv_x0;
                 do_ch = true;
-            }
-
-            float dc[3], ds[3];
-            if (do_ch && L.stage == 2) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     dc[k] = ds[k] = __int_as_float(0x7f800000);
                     const float Dk = L.d[k];
                     if (Dk != 0.0f) {
+                        const float inv = __fdividef(1.0f, Dk);
                         const int up = Dk > 0.0f ? 1 : 0;
                         const float bc = P.ctg.lo[k] + (float)(L.ic[k] + up) * P.ctg.d[k];
-                        dc[k] = fmaxf((bc - L.p[k]) / Dk, 0.0f);
+                        dc[k] = fmaxf((bc - L.p[k]) * inv, 0.0f);
                         if (P.same_grid) ds[k] = dc[k];
                         else {
                             const float bs = P.sg.lo[k] + (float)(L.is[k] + up) * P.sg.d[k];
-                            ds[k] = fmaxf((bs - L.p[k]) / Dk, 0.0f);
+                            ds[k] = fmaxf((bs - L.p[k]) * inv, 0.0f);
                         }
                     }
                     s_geom = fminf(s_geom, fminf(dc[k], ds[k]));
                 }
             }
 
-            StepResult o;
             if (do_ch) {
+                StepResult o;
                 const float d_old[3] = {L.d[0], L.d[1], L.d[2]};
                 const int is_old[3] = {L.is[0], L.is[1], L.is[2]};
                 ch_step(S, m, s_geom, L, P, key, o);
@@ -585,9 +623,10 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                     const DevBox bx = P.boxes[__ldg(&I.box)];
                     const int lx = is_old[0] - bx.lo[0], ly = is_old[1] - bx.lo[1], lz = is_old[2] - bx.lo[2];
                     const float wsc = __ldg(&I.wscale);
+                    const unsigned long long q = wsc == P.fscale ? qs : __float2ull_rn(o.dE * wsc);
                     if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] && ly < bx.n[1] && lz < bx.n[2]) {
                         dep_key = bx.base + lx + (long long)bx.n[0] * (ly + (long long)bx.n[1] * lz);
-                        dep_q = __float2ull_rn(o.dE * wsc);
+                        dep_q = q;
                     } else if (o.dE > 0.0f && P.ovf) {
                         // rare tail outside the item's box: append a record
                         const unsigned long long slot = atomicAdd(P.ovf_count, 1ull);
@@ -595,7 +634,7 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                             OvfRec r;
                             r.voxel = is_old[0] + P.sg.n[0] * (is_old[1] + P.sg.n[1] * is_old[2]);
                             r.item = L.item;
-                            r.q = __float2ull_rn(o.dE * wsc);
+                            r.q = q;
                             P.ovf[slot] = r;
                         }
                     }
@@ -609,7 +648,7 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                     if (L.stage <= 1) {
 #pragma unroll
                         for (int k = 0; k < 3; ++k) L.p[k] += o.disp[k];
-                        if (o.lim == 1) fate = down ? enter_next_stage(S, P, B, SC, L, L.stage) : kLeak;
+                        if (o.lim == 1) { if (down) advance = true; else fate = kLeak; }
                     } else {
                         if (o.lim == 1) {
                             bool out = false;
@@ -636,6 +675,9 @@ __global__ void __launch_bounds__(512, 1) k_transport(const TransportParams P)
                     }
                 }
             }
+            // the single place where a history changes stage
+            if (advance && fate < 0) fate = enter_next_stage(S, P, B, SC, L, from);
+            // the single place where a history ends
             if (fate >= 0) {
                 if (fate == kLeak || fate == kErr) acc_leak += __float2ull_rn(L.E * P.fscale);
                 if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }

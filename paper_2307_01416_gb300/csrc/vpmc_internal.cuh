@@ -27,7 +27,7 @@ enum Stat { kStDep = 0, kStLeak, kStRS, kStAp, kStNuc, kStSteps, kStErr, kNStats
 struct MatConst {
     float za;          // Z/A
     float rho;         // g/cc (PMMA, brass); 1 for water
-    float x0_mmgcc;    // radiation length in mm * g/cc
+    float inv_x0;      // 1 / radiation length in mm * g/cc
     float inv_dR;      // 1 / (uniform R-grid step)
 };
 

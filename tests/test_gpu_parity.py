@@ -54,8 +54,8 @@ def _per_history_parity(pb, spots, scen, op, records=None, max_flagged=0.01):
     scale = np.maximum(np.abs(orec["e_dep"]), 1.0)
     err = np.where(ok, np.abs(rec["e_dep"] - orec["e_dep"]) / scale, 0.0)
     assert err.max() < 1e-4, (err.max(), np.argmax(err))
-    path = np.maximum(np.linalg.norm(orec["pos"], axis=1), 10.0)
-    perr = np.where(ok, np.linalg.norm(rec["pos"] - orec["pos"], axis=1) / path, 0.0)
+    track = np.maximum(orec["track"], 1.0)        # track length from the source plane, mm
+    perr = np.where(ok, np.linalg.norm(rec["pos"] - orec["pos"], axis=1) / track, 0.0)
     assert perr.max() < 1e-4, (perr.max(), np.argmax(perr))
     leak = ok & (orec["fate"] == O.FATE_LEAK)
     if leak.any():
