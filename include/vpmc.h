@@ -111,7 +111,7 @@ typedef struct {
     int nuclear;            /* nuclear removal (1.2 %/cm x density) on/off                */
     int frac_bits;          /* fixed-point scale of deposits, 2^-frac_bits MeV (default 24) */
     int aggregate;          /* -1 autotuned, 0 plain atomics, 1 warp-aggregated atomics   */
-    int block_size;         /* 0 autotuned, else threads per block (multiple of 32, <= 640) */
+    int block_size;         /* 0 autotuned, else patient-kernel threads per block (multiple of 32, <= 768) */
     int blocks_per_sm;      /* 0 autotuned                                                */
     int chunk;              /* histories taken per warp refill (0 = default)              */
     vpmc_history_record* history_out;  /* device buffer or NULL                          */

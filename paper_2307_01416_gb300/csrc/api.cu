@@ -46,8 +46,9 @@ cudaError_t dev_alloc(T** p, size_t n)
 
 struct TuneResult {
     bool valid = false;
-    int block = 512;
-    int aggregate = 1;
+    int dev_block = 512;     // k_devices threads per block
+    int block = 640;         // k_patient threads per block
+    int aggregate = 0;
     int chunk = 32;
 };
 
@@ -89,6 +90,9 @@ struct vpmc_ctx {
     size_t boxes_cap = 0;
     OvfRec* d_ovf = nullptr;                   // out-of-box deposit records
     long long ovf_cap = 0;
+    PhaseRec* d_phase = nullptr;               // hand-off from the devices to the patient kernel
+    long long phase_cap = 0;
+    unsigned long long* d_phase_count = nullptr;
     unsigned long long* d_scratch = nullptr;
     size_t scratch_cap = 0;                    // elements
     TuneResult tune_dose, tune_im;
@@ -134,10 +138,23 @@ vpmc_status grow_ovf(vpmc_ctx* c, long long n)
 {
     if (n <= c->ovf_cap) return VPMC_OK;
     cudaFree(c->d_ovf);
+    cudaFree(c->d_phase);
+    cudaFree(c->d_phase_count);
     c->d_ovf = nullptr;
     c->ovf_cap = 0;
     CUDA_TRY(dev_alloc(&c->d_ovf, (size_t)n));
     c->ovf_cap = n;
+    return VPMC_OK;
+}
+
+vpmc_status grow_phase(vpmc_ctx* c, long long n)
+{
+    if (n <= c->phase_cap) return VPMC_OK;
+    cudaFree(c->d_phase);
+    c->d_phase = nullptr;
+    c->phase_cap = 0;
+    CUDA_TRY(dev_alloc(&c->d_phase, (size_t)n));
+    c->phase_cap = n;
     return VPMC_OK;
 }
 
@@ -203,8 +220,8 @@ vpmc_status check_opts(const vpmc_opts* o)
 {
     if (!o) return VPMC_OK;
     if (o->frac_bits < 0 || o->frac_bits > 40) return fail(VPMC_ERR_ARG, "frac_bits %d outside [0, 40]", o->frac_bits);
-    if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 640 || o->block_size % 32))
-        return fail(VPMC_ERR_ARG, "block_size %d: must be 0 or a multiple of 32 in [32, 640]", o->block_size);
+    if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 768 || o->block_size % 32))
+        return fail(VPMC_ERR_ARG, "block_size %d: must be 0 or a multiple of 32 in [32, 768]", o->block_size);
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 1)
         return fail(VPMC_ERR_ARG, "blocks_per_sm %d: the kernel's shared memory allows one block per SM", o->blocks_per_sm);
     if (o->chunk < 0 || o->chunk > 4096) return fail(VPMC_ERR_ARG, "chunk %d outside [0, 4096]", o->chunk);
@@ -240,6 +257,9 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     p.fscale = std::ldexp(1.0f, o.frac_bits);
     p.records = reinterpret_cast<HistRecord*>(o.history_out);
     p.rec_cap = o.history_out ? o.history_cap : 0;
+    p.phase = c->d_phase;
+    p.phase_cap = c->phase_cap;
+    p.phase_count = c->d_phase_count;
     return p;
 }
 
@@ -251,60 +271,110 @@ vpmc_status reset_counters(vpmc_ctx* c)
     return VPMC_OK;
 }
 
-// Chooses block size, warp aggregation and refill chunk by timing short
-// launches over a prefix of the work (results are discarded).
-vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc_opts& o,
-                     unsigned long long* scratch, size_t scratch_elems)
+constexpr long long kMaxBatch = 1ll << 26;    // histories per devices -> patient hand-off batch
+
+vpmc_status ensure_phase(vpmc_ctx* c, long long total)
 {
-    const long long sample = std::min<long long>(p.total, (long long)c->num_sms * 512 * 6);
-    if (sample <= 0) { out->valid = true; return VPMC_OK; }
-    p.total = sample;
-    p.records = nullptr;
-    p.rec_cap = 0;
-    struct Cand { int block, agg, chunk; };
-    std::vector<Cand> cands;
-    for (int block : {384, 512, 640})
-        for (int agg : {0, 1})
-            for (int chunk : {32, 128}) {
-                if (o.block_size && block != o.block_size) continue;
-                if (o.aggregate >= 0 && agg != o.aggregate) continue;
-                if (o.chunk && chunk != o.chunk) continue;
-                cands.push_back({block, agg, chunk});
-            }
-    if (cands.empty()) cands.push_back({o.block_size ? o.block_size : 512, o.aggregate >= 0 ? o.aggregate : 1,
-                                        o.chunk ? o.chunk : 32});
-    float best = 1e30f;
-    for (int rep = 0; rep < 2; ++rep)
-        for (const Cand& cd : cands) {
-            vpmc_status st = reset_counters(c);
-            if (st != VPMC_OK) return st;
-            p.aggregate = cd.agg;
-            p.chunk = cd.chunk;
-            CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-            CUDA_TRY(launch_transport(p, c->num_sms, cd.block, c->stream));
-            ++c->launches;
-            CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
-            CUDA_TRY(cudaEventSynchronize(c->ev1));
-            float ms = 0.0f;
-            CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-            if (rep == 1 && ms < best) {
-                best = ms;
-                out->block = cd.block;
-                out->aggregate = cd.agg;
-                out->chunk = cd.chunk;
-            }
-        }
-    out->valid = true;
-    if (scratch && scratch_elems)
-        CUDA_TRY(cudaMemsetAsync(scratch, 0, scratch_elems * sizeof(unsigned long long), c->stream));
+    return grow_phase(c, std::max<long long>(std::min(total, kMaxBatch), 1));
+}
+
+// Enqueues the transport of histories [0, total) of p's items: batches of at
+// most phase_cap histories, each the devices kernel then the patient kernel.
+vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, const TuneResult& t)
+{
+    p.phase = c->d_phase;
+    p.phase_cap = c->phase_cap;
+    p.phase_count = c->d_phase_count;
+    p.aggregate = t.aggregate;
+    p.chunk = t.chunk;
+    for (long long h0 = 0; h0 < total; h0 += c->phase_cap) {
+        p.hist_begin = h0;
+        p.total = std::min(total, h0 + c->phase_cap);
+        CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->d_phase_count, 0, sizeof(unsigned long long), c->stream));
+        CUDA_TRY(launch_devices(p, c->num_sms, t.dev_block, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
+        CUDA_TRY(launch_patient(p, c->num_sms, t.block, c->stream));
+        c->launches += 2;
+    }
     return VPMC_OK;
 }
 
-void resolve_launch(const vpmc_opts& o, const TuneResult& t, int* block, int* agg, int* chunk)
+float time_launch(vpmc_ctx* c, cudaError_t (*fn)(const TransportParams&, int, int, cudaStream_t),
+                  const TransportParams& p, int block)
 {
-    *block = o.block_size ? o.block_size : t.block;
-    *agg = o.aggregate >= 0 ? o.aggregate : t.aggregate;
-    *chunk = o.chunk ? o.chunk : t.chunk;
+    cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
+    cudaEventRecord(c->ev0, c->stream);
+    cudaError_t e = fn(p, c->num_sms, block, c->stream);
+    cudaEventRecord(c->ev1, c->stream);
+    if (e != cudaSuccess || cudaEventSynchronize(c->ev1) != cudaSuccess) return 1e30f;
+    ++c->launches;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    return ms;
+}
+
+// Chooses the two kernels' block sizes, warp aggregation and refill chunk by
+// timing short launches over a prefix of the work (results are discarded;
+// the caller zeroes the scoring buffers afterwards).
+vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc_opts& o)
+{
+    const long long sample = std::min<long long>(p.total, (long long)c->num_sms * 640 * 4);
+    TuneResult best;
+    best.valid = true;
+    if (o.block_size) best.block = o.block_size;
+    if (o.aggregate >= 0) best.aggregate = o.aggregate;
+    if (o.chunk) best.chunk = o.chunk;
+    if (sample <= 0) { *out = best; return VPMC_OK; }
+    p.records = nullptr;
+    p.rec_cap = 0;
+    p.hist_begin = 0;
+    p.total = sample;
+    p.chunk = best.chunk;
+    p.aggregate = best.aggregate;
+    // devices kernel block size (its output is identical for every choice)
+    float t_best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep)
+        for (int block : {384, 512, 640}) {
+            CUDA_TRY(cudaMemsetAsync(c->d_phase_count, 0, sizeof(unsigned long long), c->stream));
+            vpmc_status st = reset_counters(c);
+            if (st != VPMC_OK) return st;
+            const float ms = time_launch(c, launch_devices, p, block);
+            if (rep == 1 && ms < t_best) { t_best = ms; best.dev_block = block; }
+        }
+    // patient kernel on the histories the last devices launch handed over
+    t_best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep)
+        for (int block : {512, 640, 768})
+            for (int agg : {0, 1})
+                for (int chunk : {32, 128}) {
+                    if (o.block_size && block != o.block_size) continue;
+                    if (o.aggregate >= 0 && agg != o.aggregate) continue;
+                    if (o.chunk && chunk != o.chunk) continue;
+                    p.aggregate = agg;
+                    p.chunk = chunk;
+                    vpmc_status st = reset_counters(c);
+                    if (st != VPMC_OK) return st;
+                    const float ms = time_launch(c, launch_patient, p, block);
+                    if (rep == 1 && ms < t_best) {
+                        t_best = ms;
+                        best.block = block;
+                        best.aggregate = agg;
+                        best.chunk = chunk;
+                    }
+                }
+    *out = best;
+    return VPMC_OK;
+}
+
+TuneResult resolve_launch(const vpmc_opts& o, const TuneResult& t)
+{
+    TuneResult r = t;
+    if (o.block_size) r.block = o.block_size;
+    if (o.aggregate >= 0) r.aggregate = o.aggregate;
+    if (o.chunk) r.chunk = o.chunk;
+    if (!t.valid) r.dev_block = 512;
+    return r;
 }
 
 vpmc_status read_stats(vpmc_ctx* c, int frac_bits, vpmc_stats* acc, bool add)
@@ -377,9 +447,10 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    if ((size_t)smem_optin < transport_smem_bytes())
-        return cleanup(fail(VPMC_ERR_CUDA, "device allows %d B shared memory per block, kernel needs %zu", smem_optin,
-                            transport_smem_bytes()));
+    const size_t smem_need = std::max(devices_smem_bytes(), patient_smem_bytes());
+    if ((size_t)smem_optin < smem_need)
+        return cleanup(fail(VPMC_ERR_CUDA, "device allows %d B shared memory per block, kernels need %zu", smem_optin,
+                            smem_need));
     if (cuda_stream) {
         c->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -421,6 +492,7 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
                                    c->stream));
     CTX_TRY(dev_alloc(&c->d_beams, kMaxBeams));
     CTX_TRY(dev_alloc(&c->d_counter, 1));
+    CTX_TRY(dev_alloc(&c->d_phase_count, 1));
     CTX_TRY(dev_alloc(&c->d_stats, kNStats));
     CTX_TRY(dev_alloc(&c->d_status, 1));
     CTX_TRY(dev_alloc(&c->d_scens, kMaxScen));
@@ -577,20 +649,20 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
         p.n_scen = 1;
         p.total = total;
         p.scratch = c->d_acc;
-            const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
+        st = ensure_phase(c, total);
+        if (st != VPMC_OK) return st;
+        const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
         if (want_tune && !c->tune_dose.valid) {
-            st = autotune(c, p, &c->tune_dose, o, c->d_acc, (size_t)c->nvox);
+            st = autotune(c, p, &c->tune_dose, o);
             if (st != VPMC_OK) return st;
+            CUDA_TRY(cudaMemsetAsync(c->d_acc, 0, c->nvox * sizeof(unsigned long long), c->stream));
         }
-        int block, agg, chunk;
-        resolve_launch(o, c->tune_dose, &block, &agg, &chunk);
-        p.aggregate = agg;
-        p.chunk = chunk;
+        const TuneResult t = resolve_launch(o, c->tune_dose);
         st = reset_counters(c);
         if (st != VPMC_OK) return st;
         CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-        CUDA_TRY(launch_transport(p, c->num_sms, block, c->stream));
-        ++c->launches;
+        st = enqueue_transport(c, p, total, t);
+        if (st != VPMC_OK) return st;
         CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
     }
     const double scale = std::ldexp(1.0, -o.frac_bits) * 1.602176634e-10 /
@@ -854,6 +926,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         IM_TRY(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice));
         IM_TRY(cudaMemcpy(c->d_boxes, boxes.data(), boxes.size() * sizeof(DevBox), cudaMemcpyHostToDevice));
         if (!c->d_ovf) IM_ST(grow_ovf(c, 1ll << 24));
+        IM_ST(ensure_phase(c, total));
         TransportParams p = base_params(c, o);
         p.items = c->d_items;
         p.n_items = (int)items.size();
@@ -869,28 +942,24 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             p.ovf = c->d_ovf;
             p.ovf_cap = c->ovf_cap;
             IM_TRY(cudaMemsetAsync(d_ovf_count, 0, sizeof(unsigned long long), c->stream));
-            IM_ST(autotune(c, p, &c->tune_im, o, nullptr, 0));
+            IM_ST(autotune(c, p, &c->tune_im, o));
         }
-        int block, agg, chunk;
-        resolve_launch(o, c->tune_im, &block, &agg, &chunk);
-        p.aggregate = agg;
-        p.chunk = chunk;
+        const TuneResult tr = resolve_launch(o, c->tune_im);
         unsigned long long n_ovf = 0;
         for (int attempt = 0;; ++attempt) {
             p.ovf = c->d_ovf;
             p.ovf_cap = c->ovf_cap;
-            // zero the wave's columns and counters, then the transport launch as a CUDA graph
+            // zero the wave's columns and counters; the transport batches run as one CUDA graph
             IM_TRY(cudaMemsetAsync(c->d_scratch, 0, (size_t)wave_elems * sizeof(unsigned long long), c->stream));
             IM_TRY(cudaMemsetAsync(d_ovf_count, 0, sizeof(unsigned long long), c->stream));
             IM_ST(reset_counters(c));
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             IM_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t le = launch_transport(p, c->num_sms, block, c->stream);
+            vpmc_status qs = enqueue_transport(c, p, total, tr);
             cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
-            IM_TRY(le);
+            IM_ST(qs);
             IM_TRY(ce);
-            ++c->launches;
             cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
             if (ge == cudaSuccess) ge = cudaEventRecord(c->ev0, c->stream);
             if (ge == cudaSuccess) ge = cudaGraphLaunch(exec, c->stream);

@@ -1,15 +1,18 @@
-// Persistent proton transport kernel for sm_103a.
+// Persistent proton transport kernels for sm_103a.
 //
 // One history per thread (paper Sec. 2.A: every history follows one identical
 // model, so no secondary particles are spawned).  Warps are persistent: a warp
-// takes chunks of consecutive global history indices from one counter and hands
-// them to lanes whose history has ended, so dead lanes are refilled at once.
-// Each history crosses, in order, an optional range shifter, the brass aperture
-// (Sec. 2.B: at every step inside the aperture slab a crossing-number test
-// decides opening -> straight flight, or brass -> condensed-history step with
-// brass physics), and the voxelised patient, where every step's deposit is
-// scored into a 64-bit fixed-point accumulator (optionally aggregated over the
-// lanes of a warp that hit the same voxel, then one atomic per voxel).
+// takes chunks of consecutive work indices from one counter and hands them to
+// lanes whose history has ended, so dead lanes are refilled at once.
+// Transport runs in two kernels so that the lanes of a warp execute the same
+// geometry: k_devices carries each history through the optional range shifter
+// and the brass aperture (Sec. 2.B: at every step inside the aperture slab a
+// crossing-number test decides opening -> straight flight, or brass ->
+// condensed-history step with brass physics) and hands the survivors' phase
+// space at the end of the beam line to k_patient, which transports them through
+// the voxelised patient and scores every step's deposit into a 64-bit
+// fixed-point accumulator (optionally aggregated over the lanes of a warp that
+// hit the same voxel, then one atomic per voxel).
 //
 // Physics of one condensed-history step (same definition as the CPU oracle):
 //   step = min(1 mm, 1 % energy-loss length, geometry limit, nuclear point);
@@ -198,8 +201,9 @@ __device__ __forceinline__ void deposit_aggregated(unsigned long long* __restric
 }
 
 struct Medium {
-    int table;
-    float kappa, rho, za, inv_x0;
+    const float* Rt;   // residual range table
+    const float* Et;   // energy table on the uniform range grid
+    float inv_dR, kappa, rho, za, inv_x0;
 };
 
 struct StepResult {
@@ -209,40 +213,28 @@ struct StepResult {
     int killed;     // 1 stopped, 2 nuclear
 };
 
+// State of the history a lane carries.
 struct Lane {
     float p[3], d[3];
     float E, R, nlam;
-    uint32_t step;
-    uint32_t hist;
-    int stage;      // 0 range shifter, 1 aperture, 2 patient
+    uint32_t step;  // condensed-history steps so far (RNG counter)
+    uint32_t hist;  // history index within its spot
+    int stage;      // devices: -1 just born, 0 range shifter, 1 aperture
     int forced;     // aperture: the next step is in brass (after a wall hit)
     int ic[3], is[3];
     int item;
-    int iters, nsteps;
+    int iters;
     long long g;
     unsigned long long qdep;
 };
 
-struct Smem {
-    const float* R;
-    const float* Et;
-    const float2* hu;
-    const MatConst* mat;
-    const DevBeam* beams;
-    const DevScen* scens;
-    const float2* poly;
-};
-
-__device__ __forceinline__ void ch_step(const Smem& S, const Medium& m, float s_geom, Lane& L,
-                                        const TransportParams& P, uint2 key, StepResult& o)
+__device__ __forceinline__ void ch_step(const Medium& m, float s_geom, Lane& L, const TransportParams& P, uint2 key,
+                                        StepResult& o)
 {
-    const float* Rt = S.R + m.table * kNEPad;
-    const float* Et = S.Et + m.table * kNR;
-    const float inv_dR = S.mat[m.table].inv_dR;
     const float E = L.E;
     const float R0 = L.R;
     const float inv_kappa = __fdividef(1.0f, m.kappa);
-    float s1 = (R0 - range_of(Rt, 0.99f * E)) * inv_kappa;
+    float s1 = (R0 - range_of(m.Rt, 0.99f * E)) * inv_kappa;
     if (!(s1 > 0.0f)) s1 = R0 * inv_kappa;
     const float mu = P.nuclear ? 0.0012f * m.rho : 0.0f;
     float s = 1.0f;
@@ -261,11 +253,10 @@ __device__ __forceinline__ void ch_step(const Smem& S, const Medium& m, float s_
     if (P.mcs || P.straggling) philox_pair(r1, r2, key);
 
     const float R1 = R0 - s * m.kappa;
-    const float Emean = R1 > 0.0f ? energy_of(Et, inv_dR, R1) : kEcut;
+    const float Emean = R1 > 0.0f ? energy_of(m.Et, m.inv_dR, R1) : kEcut;
     float dE = E - Emean;
-    const float etot = E + kMp;
     const float pc2 = E * (E + 2.0f * kMp);               // (pc)^2
-    const float inv_etot = __fdividef(1.0f, etot);
+    const float inv_etot = __fdividef(1.0f, E + kMp);
     if (P.straggling) {
         const float beta2 = pc2 * inv_etot * inv_etot;
         const float2 z = box_muller_fast(u01(r2.x), u01(r2.y));
@@ -276,8 +267,8 @@ __device__ __forceinline__ void ch_step(const Smem& S, const Medium& m, float s_
     const float Enew = E - dE;
     float Rnew = R1;
     if (P.straggling) {
-        Rnew = R1 + (range_of(Rt, Enew) - range_of(Rt, Emean));
-        if (!(Rnew > 0.0f)) Rnew = range_of(Rt, Enew);
+        Rnew = R1 + (range_of(m.Rt, Enew) - range_of(m.Rt, Emean));
+        if (!(Rnew > 0.0f)) Rnew = range_of(m.Rt, Enew);
     }
     L.R = Rnew;
 
@@ -294,10 +285,7 @@ __device__ __forceinline__ void ch_step(const Smem& S, const Medium& m, float s_
     if (P.mcs && !o.killed) {
         const float x = s * m.rho * m.inv_x0;
         float th0 = 0.0f;
-        if (x >= 1e-6f) {
-            const float bcp = pc2 * inv_etot;                 // beta c p
-            th0 = __fdividef(13.6f, bcp) * fast_sqrt(x) * (1.0f + 0.038f * __logf(x));
-        }
+        if (x >= 1e-6f) th0 = __fdividef(13.6f, pc2 * inv_etot) * fast_sqrt(x) * (1.0f + 0.038f * __logf(x));
         const float2 za = box_muller_fast(u01(r1.x), u01(r1.y));
         const float2 zb = box_muller_fast(u01(r1.z), u01(r1.w));
         const float th1 = za.y * th0, th2 = zb.y * th0;
@@ -305,8 +293,7 @@ __device__ __forceinline__ void ch_step(const Smem& S, const Medium& m, float s_
         const float dx2 = s * th0 * fmaf(zb.x, 0.28867513459481287f, 0.5f * zb.y);
         float e1[3], e2[3];
         orthonormal_basis(L.d, e1, e2);
-        const float th2sq = th1 * th1 + th2 * th2;
-        const float th = fast_sqrt(th2sq);
+        const float th = fast_sqrt(th1 * th1 + th2 * th2);
         float sn, c;
         __sincosf(th, &sn, &c);
         const float sc = th > 0.0f ? __fdividef(sn, th) : 1.0f;
@@ -329,64 +316,6 @@ __device__ __forceinline__ void bev_to_patient(const DevBeam& B, const DevScen& 
         out[k] = B.iso[k] + sc.shift[k] + pb[0] * B.u[k] + pb[1] * B.v[k] + pb[2] * B.w[k];
 }
 
-// Move the history into the next stage after `from` (-1: just born).  Returns
-// a fate >= 0 if the history ends here (left the geometry), else -1.
-__device__ int enter_next_stage(const Smem& S, const TransportParams& P, const DevBeam& B, const DevScen& sc,
-                                Lane& L, int from)
-{
-    if (from < 0 && B.rs) {   // just born
-        const float sdr = (B.rs_tup - L.p[2]) / L.d[2];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
-        L.R = range_of(S.R + kPMMA * kNEPad, L.E);
-        L.stage = 0;
-        return -1;
-    }
-    if (from < 1 && B.ap) {
-        if (!(L.d[2] > 0.0f)) return kLeak;
-        const float sdr = (B.ap_tup - L.p[2]) / L.d[2];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
-        L.R = range_of(S.R + kBrass * kNEPad, L.E);
-        L.stage = 1;
-        L.forced = 0;
-        return -1;
-    }
-    // patient: BEV -> patient frame, ray / grid box entry
-    float Pp[3], D[3];
-    bev_to_patient(B, sc, L.p, Pp);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) D[k] = L.d[0] * B.u[k] + L.d[1] * B.v[k] + L.d[2] * B.w[k];
-    float tmin = -__int_as_float(0x7f800000), tmax = __int_as_float(0x7f800000);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float lo = P.ctg.lo[k], hi = P.ctg.lo[k] + P.ctg.n[k] * P.ctg.d[k];
-        if (D[k] != 0.0f) {
-            float t1 = (lo - Pp[k]) / D[k], t2 = (hi - Pp[k]) / D[k];
-            if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
-            tmin = fmaxf(tmin, t1);
-            tmax = fminf(tmax, t2);
-        } else if (Pp[k] < lo || Pp[k] > hi) {
-            tmax = -__int_as_float(0x7f800000);
-        }
-    }
-    const float tin = fmaxf(tmin, 0.0f);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { L.p[k] = Pp[k]; L.d[k] = D[k]; }
-    L.stage = 2;
-    if (!(tmax > tin)) return kLeak;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        L.p[k] = fmaf(tin, D[k], Pp[k]);
-        const int a = (int)floorf((L.p[k] - P.ctg.lo[k]) / P.ctg.d[k]);
-        L.ic[k] = min(max(a, 0), P.ctg.n[k] - 1);
-        const int b = (int)floorf((L.p[k] - P.sg.lo[k]) / P.sg.d[k]);
-        L.is[k] = min(max(b, 0), P.sg.n[k] - 1);
-    }
-    L.R = range_of(S.R + kWater * kNEPad, L.E);
-    return -1;
-}
-
 // Largest i with items[i].hist_off <= g, searched by the whole warp: each
 // round the 32 lanes probe 32 evenly spaced entries (g is warp-uniform).
 __device__ __forceinline__ int find_item_warp(const DevItem* __restrict__ items, int n, long long g, int lane)
@@ -404,88 +333,132 @@ __device__ __forceinline__ int find_item_warp(const DevItem* __restrict__ items,
     return lo;
 }
 
+// Warp-uniform pool of work indices [pool_next, pool_end) taken from a global
+// counter in chunks.  Returns false once the work (or the launch) has ended.
+struct WorkPool {
+    long long next = 0, end = 0;
+    __device__ __forceinline__ bool refill(const TransportParams& P, long long begin, long long total, int lane)
+    {
+        unsigned long long base = 0;
+        int abort = 0;
+        if (lane == 0) {
+            base = atomicAdd(P.counter, (unsigned long long)P.chunk);
+            abort = *reinterpret_cast<volatile int*>(P.status);   // a latched error ends the launch early
+        }
+        base = __shfl_sync(kFull, base, 0);
+        abort = __shfl_sync(kFull, abort, 0);
+        const long long b = begin + (long long)base;
+        if (abort || b >= total) return false;
+        next = b;
+        end = min(b + P.chunk, total);
+        return true;
+    }
+};
+
+__device__ __forceinline__ void write_record(const TransportParams& P, const Lane& L, int fate, const float pos[3],
+                                             unsigned long long acc_dep)
+{
+    HistRecord r;
+    r.q_dep = (long long)(acc_dep - L.qdep);
+    r.fate = fate;
+    r.steps = (int)L.step;
+    r.e_dep = (float)((double)(acc_dep - L.qdep) / (double)P.fscale);
+    r.e_end = (fate == kLeak || fate == kErr) ? L.E : 0.0f;
+    r.pos[0] = pos[0]; r.pos[1] = pos[1]; r.pos[2] = pos[2];
+    r.pad = 0.0f;
+    P.records[L.g] = r;
+}
+
+__device__ __forceinline__ void warp_add_stats(const TransportParams& P, unsigned long long (&v)[kNStats], int lane)
+{
+#pragma unroll
+    for (int k = 0; k < kNStats; ++k) {
+        unsigned long long x = v[k];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == 0 && x) atomicAdd(P.stats + k, x);
+    }
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(640, 1) k_transport(const TransportParams P)
+// ============================================================================
+// Range shifter and aperture.
+// ============================================================================
+__global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    // stage the tables, beams, scenarios and polygons into shared memory
     {
-        const int4* src = reinterpret_cast<const int4*>(P.tables);
-        int4* dst = reinterpret_cast<int4*>(smem);
-        constexpr int n16 = (int)(SharedLayout::Beams / 16);
-        static_assert(SharedLayout::Beams % 16 == 0, "table image must be a 16-byte multiple");
-        static_assert(sizeof(TablesImage) == SharedLayout::Beams, "table image layout");
-        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
-        DevBeam* bm = reinterpret_cast<DevBeam*>(smem + SharedLayout::Beams);
+        // PMMA and brass rows of the tables, material constants, beams, scenarios, polygons
+        float* R = reinterpret_cast<float*>(smem + DevicesSmem::R);
+        float* Et = reinterpret_cast<float*>(smem + DevicesSmem::Einv);
+        for (int i = threadIdx.x; i < kNEPad; i += blockDim.x) {
+            R[i] = P.tables->R[kPMMA][i];
+            R[kNEPad + i] = P.tables->R[kBrass][i];
+        }
+        for (int i = threadIdx.x; i < kNR; i += blockDim.x) {
+            Et[i] = P.tables->Einv[kPMMA][i];
+            Et[kNR + i] = P.tables->Einv[kBrass][i];
+        }
+        MatConst* mt = reinterpret_cast<MatConst*>(smem + DevicesSmem::Mat);
+        if (threadIdx.x < kNMat) mt[threadIdx.x] = P.tables->mat[threadIdx.x];
+        DevBeam* bm = reinterpret_cast<DevBeam*>(smem + DevicesSmem::Beams);
         for (int i = threadIdx.x; i < P.n_beams; i += blockDim.x) bm[i] = P.beams[i];
-        DevScen* sc = reinterpret_cast<DevScen*>(smem + SharedLayout::Scens);
+        DevScen* sc = reinterpret_cast<DevScen*>(smem + DevicesSmem::Scens);
         for (int i = threadIdx.x; i < P.n_scen; i += blockDim.x) sc[i] = P.scens[i];
-        float2* pl = reinterpret_cast<float2*>(smem + SharedLayout::Poly);
+        float2* pl = reinterpret_cast<float2*>(smem + DevicesSmem::Poly);
         for (int i = threadIdx.x; i < P.n_poly; i += blockDim.x) pl[i] = P.poly[i];
     }
     __syncthreads();
-    Smem S;
-    S.R = reinterpret_cast<const float*>(smem + SharedLayout::R);
-    S.Et = reinterpret_cast<const float*>(smem + SharedLayout::Einv);
-    S.hu = reinterpret_cast<const float2*>(smem + SharedLayout::HU);
-    S.mat = reinterpret_cast<const MatConst*>(smem + SharedLayout::Mat);
-    S.beams = reinterpret_cast<const DevBeam*>(smem + SharedLayout::Beams);
-    S.scens = reinterpret_cast<const DevScen*>(smem + SharedLayout::Scens);
-    S.poly = reinterpret_cast<const float2*>(smem + SharedLayout::Poly);
+    const float* Rpmma = reinterpret_cast<const float*>(smem + DevicesSmem::R);
+    const float* Epmma = reinterpret_cast<const float*>(smem + DevicesSmem::Einv);
+    const MatConst* mat = reinterpret_cast<const MatConst*>(smem + DevicesSmem::Mat);
+    const DevBeam* beams = reinterpret_cast<const DevBeam*>(smem + DevicesSmem::Beams);
+    const DevScen* scens = reinterpret_cast<const DevScen*>(smem + DevicesSmem::Scens);
+    const float2* poly = reinterpret_cast<const float2*>(smem + DevicesSmem::Poly);
+    Medium pmma, brass;
+    pmma.Rt = Rpmma; pmma.Et = Epmma; pmma.inv_dR = mat[kPMMA].inv_dR; pmma.kappa = mat[kPMMA].rho;
+    pmma.rho = mat[kPMMA].rho; pmma.za = mat[kPMMA].za; pmma.inv_x0 = mat[kPMMA].inv_x0;
+    brass.Rt = Rpmma + kNEPad; brass.Et = Epmma + kNR; brass.inv_dR = mat[kBrass].inv_dR; brass.kappa = mat[kBrass].rho;
+    brass.rho = mat[kBrass].rho; brass.za = mat[kBrass].za; brass.inv_x0 = mat[kBrass].inv_x0;
 
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    long long pool_next = 0, pool_end = 0;      // warp-uniform
-    int pool_item = 0;                          // item of pool_next (warp-uniform)
+    WorkPool pool;
+    int pool_item = 0;
     bool alive = false, done = false;
     Lane L;
-    L.item = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.nsteps = 0; L.stage = 0; L.forced = 0;
+    L.item = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.stage = 0; L.forced = 0;
     L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; L.ic[k] = 0; L.is[k] = 0; }
-    unsigned long long acc_dep = 0, acc_leak = 0, acc_rs = 0, acc_ap = 0, acc_nuc = 0;
-    unsigned acc_steps = 0, acc_err = 0;
+    for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; }
+    unsigned long long acc_leak = 0, acc_rs = 0, acc_ap = 0, acc_nuc = 0, acc_steps = 0, acc_err = 0;
     uint2 key = make_uint2(0u, 0u);
 
     for (;;) {
-        // ---- hand new histories to lanes whose history has ended ----
+        // ---- new histories for lanes whose history has ended ----
         unsigned need = __ballot_sync(kFull, !alive && !done);
         while (need) {
-            if (pool_next >= pool_end) {
-                // take the next chunk; stop taking work once any history has
-                // hit the iteration cap (a latched error ends the launch early)
-                unsigned long long base = 0;
-                int abort = 0;
-                if (lane == 0) {
-                    base = atomicAdd(P.counter, (unsigned long long)P.chunk);
-                    abort = *reinterpret_cast<volatile int*>(P.status);
-                }
-                base = __shfl_sync(kFull, base, 0);
-                abort = __shfl_sync(kFull, abort, 0);
-                if (abort || (long long)base >= P.total) {
+            if (pool.next >= pool.end) {
+                if (!pool.refill(P, P.hist_begin, P.total, lane)) {
                     if (!alive) done = true;
                     break;
                 }
-                pool_next = (long long)base;
-                pool_end = min((long long)base + P.chunk, P.total);
-                pool_item = find_item_warp(P.items, P.n_items, pool_next, lane);
+                pool_item = find_item_warp(P.items, P.n_items, pool.next, lane);
             }
-            const int take = (int)min((long long)__popc(need), pool_end - pool_next);
+            const int take = (int)min((long long)__popc(need), pool.end - pool.next);
             const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
             if (mine) {
-                const long long g = pool_next + __popc(need & lt_mask);
+                const long long g = pool.next + __popc(need & lt_mask);
                 int it = pool_item;
                 while (it + 1 < P.n_items && __ldg(&P.items[it + 1].hist_off) <= g) ++it;
                 const DevItem I = P.items[it];
-                const DevBeam& B = S.beams[I.beam];
+                const DevBeam& B = beams[I.beam];
                 L.item = it;
                 L.g = g;
                 L.hist = (uint32_t)(g - I.hist_off);
                 L.step = 0;
                 L.iters = 0;
-                L.nsteps = 0;
-                L.qdep = acc_dep;
                 key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
                 // source: slot 0 -> (x, y) at the isocentre plane and two projected angles
                 const uint4 x = philox(make_uint4(L.hist, 0u, 0u, 0u), key);
@@ -506,7 +479,7 @@ __global__ void __launch_bounds__(640, 1) k_transport(const TransportParams P)
                 L.stage = -1;                       // enters its first stage in the next iteration
                 alive = true;
             }
-            pool_next += take;
+            pool.next += take;
             need = __ballot_sync(kFull, !alive && !done);
         }
         if (!__any_sync(kFull, alive)) {
@@ -515,27 +488,22 @@ __global__ void __launch_bounds__(640, 1) k_transport(const TransportParams P)
         }
 
         // ---- one iteration of every live history ----
-        long long dep_key = -1;
-        unsigned long long dep_q = 0ull;
+        bool handoff = false;
         if (alive) {
             int fate = -1;
-            bool advance = false;                   // move to the next stage after this iteration
-            const int from = L.stage;
+            bool advance = false;
             const DevItem& I = P.items[L.item];
-            const int beam = __ldg(&I.beam);
-            const int scn = __ldg(&I.scen);
-            const DevBeam& B = S.beams[beam];
-            const DevScen& SC = S.scens[scn];
+            const DevBeam& B = beams[__ldg(&I.beam)];
             Medium m;
+            bool do_ch = false;
             float s_geom = __int_as_float(0x7f800000);
-            bool do_ch = false, down = true;
-            float dc[3], ds[3];
+            bool down = true;
             if (++L.iters > kMaxIter) {
                 fate = kErr;
             } else if (L.stage < 0) {
                 advance = true;
             } else if (L.stage == 0) {
-                // ---- range shifter ----
+                // ---- range shifter: homogeneous slab of finite radius ----
                 if (L.p[0] * L.p[0] + L.p[1] * L.p[1] > B.rs_r2) {
                     if (!(L.d[2] > 0.0f)) fate = kLeak;
                     else {
@@ -548,18 +516,18 @@ __global__ void __launch_bounds__(640, 1) k_transport(const TransportParams P)
                     if (L.d[2] > 0.0f) s_geom = (B.rs_tdn - L.p[2]) / L.d[2];
                     else if (L.d[2] < 0.0f) { s_geom = (B.rs_tup - L.p[2]) / L.d[2]; down = false; }
                     s_geom = fmaxf(s_geom, 0.0f);   // scattering offsets can leave it past the plane
-                    m.table = kPMMA; m.kappa = S.mat[kPMMA].rho; m.rho = m.kappa; m.za = S.mat[kPMMA].za;
-                    m.inv_x0 = S.mat[kPMMA].inv_x0;
+                    m = pmma;
                     do_ch = true;
                 }
-            } else if (L.stage == 1) {
+            } else {
                 // ---- aperture block ----
                 if (L.d[2] > 0.0f) s_geom = (B.ap_tdn - L.p[2]) / L.d[2];
                 else if (L.d[2] < 0.0f) { s_geom = (B.ap_tup - L.p[2]) / L.d[2]; down = false; }
-                s_geom = fmaxf(s_geom, 0.0f);       // scattering offsets can leave it past the plane
-                const bool open = !L.forced && in_opening(B, S.poly, P.raster, L.p[0], L.p[1]);
+                s_geom = fmaxf(s_geom, 0.0f);
+                const bool open = !L.forced && in_opening(B, poly, P.raster, L.p[0], L.p[1]);
                 if (open) {
-                    const float sw = first_wall_hit(S.poly + B.poly_off, B.nvert, L.p[0], L.p[1], L.d[0], L.d[1]);
+                    // opening: keep velocity and direction up to a wall or the exit
+                    const float sw = first_wall_hit(poly + B.poly_off, B.nvert, L.p[0], L.p[1], L.d[0], L.d[1]);
                     if (sw < s_geom) {
 #pragma unroll
                         for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sw, L.d[k], L.p[k]);
@@ -573,18 +541,224 @@ __global__ void __launch_bounds__(640, 1) k_transport(const TransportParams P)
                     }
                 } else {
                     L.forced = 0;
-                    m.table = kBrass; m.kappa = S.mat[kBrass].rho; m.rho = m.kappa; m.za = S.mat[kBrass].za;
-                    m.inv_x0 = S.mat[kBrass].inv_x0;
+                    m = brass;
                     do_ch = true;
                 }
+            }
+            if (do_ch) {
+                StepResult o;
+                ch_step(m, s_geom, L, P, key, o);
+                acc_steps += 1;
+                const unsigned long long qs = __float2ull_rn(o.dE * P.fscale);
+                if (L.stage == 0) acc_rs += qs; else acc_ap += qs;
+                if (o.killed) {
+                    if (o.killed == 2) acc_nuc += qs;
+                    fate = L.stage == 0 ? kAbsRS : kAbsAp;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) L.p[k] += o.disp[k];
+                    if (o.lim == 1) { if (down) advance = true; else fate = kLeak; }
+                }
+            }
+            if (advance && fate < 0) {
+                // the single place where a history changes stage
+                const int from = L.stage;
+                if (from < 0 && B.rs) {
+                    const float sdr = (B.rs_tup - L.p[2]) / L.d[2];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
+                    L.R = range_of(pmma.Rt, L.E);
+                    L.stage = 0;
+                } else if (from < 1 && B.ap) {
+                    if (!(L.d[2] > 0.0f)) fate = kLeak;
+                    else {
+                        const float sdr = (B.ap_tup - L.p[2]) / L.d[2];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
+                        L.R = range_of(brass.Rt, L.E);
+                        L.stage = 1;
+                        L.forced = 0;
+                    }
+                } else {
+                    handoff = true;                 // leaves the beam line: on to the patient kernel
+                }
+            }
+            if (fate >= 0) {
+                // the single place where a history ends in this kernel
+                if (fate == kLeak || fate == kErr) acc_leak += __float2ull_rn(L.E * P.fscale);
+                if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }
+                if (P.records && L.g < P.rec_cap) {
+                    float pos[3];
+                    bev_to_patient(B, scens[__ldg(&I.scen)], L.p, pos);
+                    write_record(P, L, fate, pos, 0ull);
+                }
+                alive = false;
+            }
+        }
+        // ---- hand-off of the histories that left the beam line (one atomic per warp) ----
+        const unsigned hmask = __ballot_sync(kFull, handoff);
+        if (hmask) {
+            unsigned long long base = 0;
+            const int leader = __ffs(hmask) - 1;
+            if (lane == leader) base = atomicAdd(P.phase_count, (unsigned long long)__popc(hmask));
+            base = __shfl_sync(kFull, base, leader);
+            if (handoff) {
+                const long long slot = (long long)base + __popc(hmask & lt_mask);
+                const DevItem& I = P.items[L.item];
+                const DevBeam& B = beams[__ldg(&I.beam)];
+                const DevScen& SC = scens[__ldg(&I.scen)];
+                if (slot < P.phase_cap) {
+                    PhaseRec r;
+                    bev_to_patient(B, SC, L.p, r.p);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) r.d[k] = L.d[0] * B.u[k] + L.d[1] * B.v[k] + L.d[2] * B.w[k];
+                    r.E = L.E;
+                    r.nlam = L.nlam;
+                    r.step = L.step;
+                    r.item = L.item;
+                    r.g = L.g;
+                    P.phase[slot] = r;
+                } else {
+                    atomicOr(P.status, 2);          // hand-off buffer too small (host sizes it to the batch)
+                }
+                alive = false;
+            }
+        }
+    }
+    unsigned long long v[kNStats] = {0ull, acc_leak, acc_rs, acc_ap, acc_nuc, acc_steps, acc_err};
+    warp_add_stats(P, v, lane);
+}
+
+// ============================================================================
+// Voxelised patient.
+// ============================================================================
+__global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    {
+        float* R = reinterpret_cast<float*>(smem + PatientSmem::R);
+        float* Et = reinterpret_cast<float*>(smem + PatientSmem::Einv);
+        for (int i = threadIdx.x; i < kNEPad; i += blockDim.x) R[i] = P.tables->R[kWater][i];
+        for (int i = threadIdx.x; i < kNR; i += blockDim.x) Et[i] = P.tables->Einv[kWater][i];
+        float2* hu = reinterpret_cast<float2*>(smem + PatientSmem::HU);
+        for (int i = threadIdx.x; i < kNHU; i += blockDim.x) hu[i] = P.tables->hu[i];
+        MatConst* mt = reinterpret_cast<MatConst*>(smem + PatientSmem::Mat);
+        if (threadIdx.x < kNMat) mt[threadIdx.x] = P.tables->mat[threadIdx.x];
+        DevScen* sc = reinterpret_cast<DevScen*>(smem + PatientSmem::Scens);
+        for (int i = threadIdx.x; i < P.n_scen; i += blockDim.x) sc[i] = P.scens[i];
+    }
+    __syncthreads();
+    Medium water;
+    water.Rt = reinterpret_cast<const float*>(smem + PatientSmem::R);
+    water.Et = reinterpret_cast<const float*>(smem + PatientSmem::Einv);
+    const float2* hu_lut = reinterpret_cast<const float2*>(smem + PatientSmem::HU);
+    const MatConst* mat = reinterpret_cast<const MatConst*>(smem + PatientSmem::Mat);
+    const DevScen* scens = reinterpret_cast<const DevScen*>(smem + PatientSmem::Scens);
+    water.inv_dR = mat[kWater].inv_dR;
+    water.za = mat[kWater].za;
+    water.inv_x0 = mat[kWater].inv_x0;
+
+    const long long total = min((long long)*P.phase_count, P.phase_cap);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    WorkPool pool;
+    bool alive = false, done = false;
+    Lane L;
+    L.item = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.stage = 2; L.forced = 0;
+    L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; L.ic[k] = 0; L.is[k] = 0; }
+    unsigned long long acc_dep = 0, acc_leak = 0, acc_nuc = 0, acc_steps = 0, acc_err = 0;
+    uint2 key = make_uint2(0u, 0u);
+    float spr_scale = 1.0f;
+    DevBox bx;
+    bx.base = 0; bx.lo[0] = bx.lo[1] = bx.lo[2] = 0; bx.n[0] = bx.n[1] = bx.n[2] = 0;
+    float wsc = 0.0f;
+
+    for (;;) {
+        // ---- histories handed over by the devices kernel ----
+        unsigned need = __ballot_sync(kFull, !alive && !done);
+        while (need) {
+            if (pool.next >= pool.end) {
+                if (!pool.refill(P, 0, total, lane)) {
+                    if (!alive) done = true;
+                    break;
+                }
+            }
+            const int take = (int)min((long long)__popc(need), pool.end - pool.next);
+            const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
+            if (mine) {
+                const PhaseRec r = P.phase[pool.next + __popc(need & lt_mask)];
+                const DevItem I = P.items[r.item];
+                L.item = r.item;
+                L.g = r.g;
+                L.hist = (uint32_t)(r.g - I.hist_off);
+                L.step = r.step;
+                L.iters = 0;
+                L.E = r.E;
+                L.nlam = r.nlam;
+                L.qdep = acc_dep;
+                key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
+                spr_scale = scens[I.scen].spr_scale;
+                bx = P.boxes[I.box];
+                wsc = I.wscale;
+                // ray / grid box entry
+                float tmin = -__int_as_float(0x7f800000), tmax = __int_as_float(0x7f800000);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float lo = P.ctg.lo[k], hi = P.ctg.lo[k] + P.ctg.n[k] * P.ctg.d[k];
+                    if (r.d[k] != 0.0f) {
+                        float t1 = (lo - r.p[k]) / r.d[k], t2 = (hi - r.p[k]) / r.d[k];
+                        if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
+                        tmin = fmaxf(tmin, t1);
+                        tmax = fminf(tmax, t2);
+                    } else if (r.p[k] < lo || r.p[k] > hi) {
+                        tmax = -__int_as_float(0x7f800000);
+                    }
+                }
+                const float tin = fmaxf(tmin, 0.0f);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { L.p[k] = r.p[k]; L.d[k] = r.d[k]; }
+                if (!(tmax > tin)) {
+                    // misses the grid
+                    acc_leak += __float2ull_rn(L.E * P.fscale);
+                    if (P.records && L.g < P.rec_cap) write_record(P, L, kLeak, L.p, acc_dep);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        L.p[k] = fmaf(tin, L.d[k], L.p[k]);
+                        const int a = (int)floorf((L.p[k] - P.ctg.lo[k]) / P.ctg.d[k]);
+                        L.ic[k] = min(max(a, 0), P.ctg.n[k] - 1);
+                        const int b = (int)floorf((L.p[k] - P.sg.lo[k]) / P.sg.d[k]);
+                        L.is[k] = min(max(b, 0), P.sg.n[k] - 1);
+                    }
+                    L.R = range_of(water.Rt, L.E);
+                    alive = true;
+                }
+            }
+            pool.next += take;
+            need = __ballot_sync(kFull, !alive && !done);
+        }
+        if (!__any_sync(kFull, alive)) {
+            if (__all_sync(kFull, done || alive)) break;
+            continue;
+        }
+
+        // ---- one condensed-history step of every live history ----
+        long long dep_key = -1;
+        unsigned long long dep_q = 0ull;
+        if (alive) {
+            int fate = -1;
+            if (++L.iters > kMaxIter) {
+                fate = kErr;
             } else {
-                // ---- patient ----
                 const long long cidx = L.ic[0] + (long long)P.ctg.n[0] * (L.ic[1] + (long long)P.ctg.n[1] * L.ic[2]);
                 const int h = min(max((int)__ldg(P.ct + cidx), kHULo), kHULo + kNHU - 1);
-                const float2 rs = S.hu[h - kHULo];
-                m.table = kWater; m.kappa = rs.y * SC.spr_scale; m.rho = rs.x; m.za = S.mat[kWater].za;
-                m.inv_x0 = S.mat[kWater].inv_x0;
-                do_ch = true;
+                const float2 rs = hu_lut[h - kHULo];
+                water.kappa = rs.y * spr_scale;
+                water.rho = rs.x;
+                // distance to the next voxel boundary of either grid
+                float dc[3], ds[3], s_geom = __int_as_float(0x7f800000);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     dc[k] = ds[k] = __int_as_float(0x7f800000);
@@ -602,98 +776,62 @@ __global__ void __launch_bounds__(640, 1) k_transport(const TransportParams P)
                     }
                     s_geom = fminf(s_geom, fminf(dc[k], ds[k]));
                 }
-            }
-
-            if (do_ch) {
                 StepResult o;
                 const float d_old[3] = {L.d[0], L.d[1], L.d[2]};
-                const int is_old[3] = {L.is[0], L.is[1], L.is[2]};
-                ch_step(S, m, s_geom, L, P, key, o);
-                L.nsteps += 1;
+                const int lx = L.is[0] - bx.lo[0], ly = L.is[1] - bx.lo[1], lz = L.is[2] - bx.lo[2];
+                const int vox = L.is[0] + P.sg.n[0] * (L.is[1] + P.sg.n[1] * L.is[2]);
+                ch_step(water, s_geom, L, P, key, o);
                 acc_steps += 1;
                 const unsigned long long qs = __float2ull_rn(o.dE * P.fscale);
-                if (L.stage == 0) {
-                    acc_rs += qs;
-                    if (o.killed) { if (o.killed == 2) acc_nuc += qs; fate = kAbsRS; }
-                } else if (L.stage == 1) {
-                    acc_ap += qs;
-                    if (o.killed) { if (o.killed == 2) acc_nuc += qs; fate = kAbsAp; }
-                } else {
-                    // score into the scoring voxel where the step started
-                    const DevBox bx = P.boxes[__ldg(&I.box)];
-                    const int lx = is_old[0] - bx.lo[0], ly = is_old[1] - bx.lo[1], lz = is_old[2] - bx.lo[2];
-                    const float wsc = __ldg(&I.wscale);
-                    const unsigned long long q = wsc == P.fscale ? qs : __float2ull_rn(o.dE * wsc);
-                    if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] && ly < bx.n[1] && lz < bx.n[2]) {
-                        dep_key = bx.base + lx + (long long)bx.n[0] * (ly + (long long)bx.n[1] * lz);
-                        dep_q = q;
-                    } else if (o.dE > 0.0f && P.ovf) {
-                        // rare tail outside the item's box: append a record
-                        const unsigned long long slot = atomicAdd(P.ovf_count, 1ull);
-                        if ((long long)slot < P.ovf_cap) {
-                            OvfRec r;
-                            r.voxel = is_old[0] + P.sg.n[0] * (is_old[1] + P.sg.n[1] * is_old[2]);
-                            r.item = L.item;
-                            r.q = q;
-                            P.ovf[slot] = r;
-                        }
-                    }
-                    acc_dep += qs;
-                    if (o.killed) {
-                        if (o.killed == 2) acc_nuc += qs;
-                        fate = o.killed == 2 ? kNuc : kStop;
+                const unsigned long long q = wsc == P.fscale ? qs : __float2ull_rn(o.dE * wsc);
+                // score into the scoring voxel where the step started
+                if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] && ly < bx.n[1] && lz < bx.n[2]) {
+                    dep_key = bx.base + lx + (long long)bx.n[0] * (ly + (long long)bx.n[1] * lz);
+                    dep_q = q;
+                } else if (o.dE > 0.0f && P.ovf) {
+                    // rare tail outside the item's box: append a record
+                    const unsigned long long slot = atomicAdd(P.ovf_count, 1ull);
+                    if ((long long)slot < P.ovf_cap) {
+                        OvfRec rr;
+                        rr.voxel = vox;
+                        rr.item = L.item;
+                        rr.q = q;
+                        P.ovf[slot] = rr;
                     }
                 }
-                if (fate < 0) {
-                    if (L.stage <= 1) {
+                acc_dep += qs;
+                if (o.killed) {
+                    if (o.killed == 2) acc_nuc += qs;
+                    fate = o.killed == 2 ? kNuc : kStop;
+                } else {
+                    if (o.lim == 1) {
+                        bool out = false;
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) L.p[k] += o.disp[k];
-                        if (o.lim == 1) { if (down) advance = true; else fate = kLeak; }
-                    } else {
-                        if (o.lim == 1) {
-                            bool out = false;
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const int sg = d_old[k] > 0.0f ? 1 : -1;
-                                if (d_old[k] != 0.0f && dc[k] == o.s) L.ic[k] += sg;
-                                if (d_old[k] != 0.0f && ds[k] == o.s) L.is[k] += sg;
-                                out |= L.ic[k] < 0 || L.ic[k] >= P.ctg.n[k] || L.is[k] < 0 || L.is[k] >= P.sg.n[k];
-                            }
-                            if (out) fate = kLeak;
+                        for (int k = 0; k < 3; ++k) {
+                            const int sg = d_old[k] > 0.0f ? 1 : -1;
+                            if (d_old[k] != 0.0f && dc[k] == o.s) L.ic[k] += sg;
+                            if (d_old[k] != 0.0f && ds[k] == o.s) L.is[k] += sg;
+                            out |= L.ic[k] < 0 || L.ic[k] >= P.ctg.n[k] || L.is[k] < 0 || L.is[k] >= P.sg.n[k];
                         }
-                        if (fate < 0) {
-                            // lateral displacement, confined to the current voxel of both grids
+                        if (out) fate = kLeak;
+                    }
+                    if (fate < 0) {
+                        // lateral displacement, confined to the current voxel of both grids
 #pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const float vlo = fmaxf(P.ctg.lo[k] + (float)L.ic[k] * P.ctg.d[k],
-                                                        P.sg.lo[k] + (float)L.is[k] * P.sg.d[k]);
-                                const float vhi = fminf(P.ctg.lo[k] + (float)(L.ic[k] + 1) * P.ctg.d[k],
-                                                        P.sg.lo[k] + (float)(L.is[k] + 1) * P.sg.d[k]);
-                                L.p[k] = fminf(fmaxf(L.p[k] + o.disp[k], vlo), vhi);
-                            }
+                        for (int k = 0; k < 3; ++k) {
+                            const float vlo = fmaxf(P.ctg.lo[k] + (float)L.ic[k] * P.ctg.d[k],
+                                                    P.sg.lo[k] + (float)L.is[k] * P.sg.d[k]);
+                            const float vhi = fminf(P.ctg.lo[k] + (float)(L.ic[k] + 1) * P.ctg.d[k],
+                                                    P.sg.lo[k] + (float)(L.is[k] + 1) * P.sg.d[k]);
+                            L.p[k] = fminf(fmaxf(L.p[k] + o.disp[k], vlo), vhi);
                         }
                     }
                 }
             }
-            // the single place where a history changes stage
-            if (advance && fate < 0) fate = enter_next_stage(S, P, B, SC, L, from);
-            // the single place where a history ends
             if (fate >= 0) {
                 if (fate == kLeak || fate == kErr) acc_leak += __float2ull_rn(L.E * P.fscale);
                 if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }
-                if (P.records && L.g < P.rec_cap) {
-                    HistRecord r;
-                    float pos[3] = {L.p[0], L.p[1], L.p[2]};
-                    if (L.stage < 2) bev_to_patient(B, SC, L.p, pos);
-                    r.q_dep = (long long)(acc_dep - L.qdep);
-                    r.fate = fate;
-                    r.steps = L.nsteps;
-                    r.e_dep = (float)((double)(acc_dep - L.qdep) / (double)P.fscale);
-                    r.e_end = (fate == kLeak || fate == kErr) ? L.E : 0.0f;
-                    r.pos[0] = pos[0]; r.pos[1] = pos[1]; r.pos[2] = pos[2];
-                    r.pad = 0.0f;
-                    P.records[L.g] = r;
-                }
+                if (P.records && L.g < P.rec_cap) write_record(P, L, fate, L.p, acc_dep);
                 alive = false;
             }
         }
@@ -701,40 +839,38 @@ __global__ void __launch_bounds__(640, 1) k_transport(const TransportParams P)
         if (P.aggregate) deposit_aggregated(P.scratch, dep_key, dep_q);
         else if (dep_key >= 0 && dep_q) atomicAdd(P.scratch + dep_key, dep_q);
     }
-
-    // ---- per-warp totals ----
-    unsigned long long v[kNStats] = {acc_dep, acc_leak, acc_rs, acc_ap, acc_nuc, acc_steps, acc_err};
-#pragma unroll
-    for (int k = 0; k < kNStats; ++k) {
-        unsigned long long x = v[k];
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-        if (lane == 0 && x) atomicAdd(P.stats + k, x);
-    }
+    unsigned long long v[kNStats] = {acc_dep, acc_leak, 0ull, 0ull, acc_nuc, acc_steps, acc_err};
+    warp_add_stats(P, v, lane);
 }
 
-size_t transport_smem_bytes() { return SharedLayout::Bytes; }
+size_t devices_smem_bytes() { return DevicesSmem::Bytes; }
+size_t patient_smem_bytes() { return PatientSmem::Bytes; }
+int devices_max_block() { return 640; }
+int patient_max_block() { return 768; }
 
-cudaError_t transport_func_attributes(int* regs, int* max_threads)
-{
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, k_transport);
-    if (e != cudaSuccess) return e;
-    *regs = a.numRegs;
-    *max_threads = a.maxThreadsPerBlock;
-    return cudaSuccess;
-}
-
-cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s)
+cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SharedLayout::Bytes);
+        cudaError_t e = cudaFuncSetAttribute(k_devices, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)DevicesSmem::Bytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_transport<<<grid, block, SharedLayout::Bytes, s>>>(p);
+    k_devices<<<grid, block, DevicesSmem::Bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_patient(const TransportParams& p, int grid, int block, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_patient, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)PatientSmem::Bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_patient<<<grid, block, PatientSmem::Bytes, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,16 @@ struct OvfRec {
     unsigned long long q;
 };
 
+// A history at the end of the beam-line devices, handed to the patient
+// kernel: position and direction in the patient frame (scenario shift applied).
+struct PhaseRec {
+    float p[3], d[3];
+    float E, nlam;
+    uint32_t step;                   // condensed-history steps so far (RNG counter)
+    int item;
+    long long g;                     // global history index
+};
+
 struct HistRecord {                  // mirrors vpmc_history_record
     long long q_dep;
     int fate;
@@ -116,6 +126,10 @@ struct TransportParams {
     long long total;                 // total histories
     unsigned long long* counter;     // global work counter
     unsigned long long* scratch;     // deposit target
+    long long hist_begin;            // devices kernel: first global history of the batch
+    PhaseRec* phase;                 // histories handed from the devices to the patient kernel
+    unsigned long long* phase_count;
+    long long phase_cap;
     OvfRec* ovf;                     // out-of-box deposits (NULL: none expected)
     unsigned long long* ovf_count;   // records appended (may exceed ovf_cap: then re-run)
     long long ovf_cap;
@@ -130,22 +144,36 @@ struct TransportParams {
     int chunk;
 };
 
-// Shared-memory layout of the transport kernel.
-struct SharedLayout {
-    static constexpr size_t R = 0;
-    static constexpr size_t Einv = R + sizeof(float) * kNMat * kNEPad;
-    static constexpr size_t HU = Einv + sizeof(float) * kNMat * kNR;
-    static constexpr size_t Mat = HU + sizeof(float2) * kNHU;
+// Shared-memory layouts of the two transport kernels.
+struct DevicesSmem {                 // range shifter and aperture
+    static constexpr size_t R = 0;                                            // PMMA, brass
+    static constexpr size_t Einv = R + sizeof(float) * 2 * kNEPad;
+    static constexpr size_t Mat = Einv + sizeof(float) * 2 * kNR;
     static constexpr size_t Beams = Mat + sizeof(MatConst) * kNMat;
     static constexpr size_t Scens = Beams + sizeof(DevBeam) * kMaxBeams;
     static constexpr size_t Poly = Scens + sizeof(DevScen) * kMaxScen;
     static constexpr size_t Bytes = Poly + sizeof(float2) * kMaxPolyVerts;
 };
+struct PatientSmem {                 // voxelised patient
+    static constexpr size_t R = 0;                                            // water
+    static constexpr size_t Einv = R + sizeof(float) * kNEPad;
+    static constexpr size_t HU = Einv + sizeof(float) * kNR;
+    static constexpr size_t Mat = HU + sizeof(float2) * kNHU;
+    static constexpr size_t Scens = Mat + sizeof(MatConst) * kNMat;
+    static constexpr size_t Bytes = Scens + sizeof(DevScen) * kMaxScen;
+};
 
 // Host-side launchers (transport.cu, finalize.cu).
-cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s);
-size_t transport_smem_bytes();
-cudaError_t transport_func_attributes(int* regs, int* max_threads);
+// Transport of histories [p.hist_begin, p.total): the devices kernel, then
+// the patient kernel on the histories it hands over (p.phase must hold
+// p.total - p.hist_begin records).  Both launches are persistent grids of
+// one block per SM.
+cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaStream_t s);
+cudaError_t launch_patient(const TransportParams& p, int grid, int block, cudaStream_t s);
+size_t devices_smem_bytes();
+size_t patient_smem_bytes();
+int patient_max_block();
+int devices_max_block();
 
 cudaError_t launch_scoring_density(const int16_t* ct, Grid3 ctg, Grid3 sg, const double* curve15_dev,
                                    const double ct_spacing[3], const double sg_spacing[3], double* rho_out,
