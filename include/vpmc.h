@@ -168,6 +168,27 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* ctx, int beam_id, const vpmc_beam* beam)
 vpmc_status vpmc_run_spots(vpmc_ctx* ctx, const vpmc_spot* spots, int n_spots, const vpmc_scenario* scen,
                            const vpmc_opts* opts, float* dose_dev, vpmc_stats* stats_out);
 
+/* The dose of vpmc_run_spots computed without allocating any memory in the
+ * call.  The paper has no counterpart: this serves callers that cannot let a
+ * call allocate device memory -- work recorded into a CUDA stream capture
+ * (cudaMalloc is not a capturable stream operation), serving loops where the
+ * implicit device-wide synchronisation of cudaMalloc/cudaFree would stall
+ * other streams, and hosts whose memory pool owns all device memory.  The
+ * context (vpmc_create_geometry, vpmc_set_aperture) must already exist; it is
+ * the only allocation, made once at set-up.  Scratch (64-bit accumulator, work
+ * items, beam-line hand-off buffer, counters) lives in one fixed device array
+ * of about 29 MiB that every GPU loading the library holds until the process
+ * exits; its limits are 2,097,152 scoring voxels and 16,384 spots with
+ * histories per call (VPMC_ERR_ARG beyond them).  The first call on a device
+ * resolves that array's device address (cudaGetSymbolAddress), so it should
+ * come before any stream capture.  All calls on a device share the array and
+ * clear it at their start: calls that overlap on the GPU (other streams,
+ * other threads) race and corrupt each other.  Arguments, output and the
+ * synchronisation rule for stats_out are those of vpmc_run_spots; the launch
+ * configuration is the context's tuned one (or opts') without autotuning. */
+vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* ctx, const vpmc_spot* spots, int n_spots, const vpmc_scenario* scen,
+                                   const vpmc_opts* opts, float* dose_dev, vpmc_stats* stats_out);
+
 /* Influence matrices for n_scen scenarios (Sec. 2.C sparse matrices, Sec.
  * 2.E 13 robust scenarios): every (scenario, spot) column in one persistent
  * launch, unweighted; column j of scenario s = dose per primary of spot j;

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/vpmc.h"
+#include "context.h"
 #include "tables.h"
 #include "vpmc_internal.cuh"
 
@@ -28,6 +29,21 @@ vpmc_status fail(vpmc_status st, const char* fmt, ...)
     return st;
 }
 
+}  // namespace
+
+vpmc_status vpmc::report_error(vpmc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return st;
+}
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                             \
     do {                                                                                           \
         cudaError_t e_ = (expr);                                                                   \
@@ -44,61 +60,8 @@ cudaError_t dev_alloc(T** p, size_t n)
     return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
 }
 
-struct TuneResult {
-    bool valid = false;
-    int dev_block = 512;     // k_devices threads per block
-    int block = 640;         // k_patient threads per block
-    int aggregate = 0;
-    int chunk = 32;
-};
-
 }  // namespace
 
-struct vpmc_ctx {
-    int device = 0;
-    int num_sms = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    Grid3 ctg{}, sg{};
-    double ct_spacing[3]{}, sg_spacing[3]{};
-    bool same_grid = false;
-    long long nvox = 0;
-    double curve15[15]{};
-    int16_t* d_ct = nullptr;
-    TablesImage* d_tables = nullptr;
-    double* d_curve = nullptr;
-    double* d_rho = nullptr;
-    unsigned long long* d_acc = nullptr;       // dose accumulator (scoring grid)
-    // fields
-    bool beam_set[kMaxBeams]{};
-    DevBeam beams[kMaxBeams]{};
-    std::vector<double> poly[kMaxBeams];
-    std::vector<unsigned char> raster[kMaxBeams];
-    double src_raster_lo[kMaxBeams][2]{};
-    DevBeam* d_beams = nullptr;
-    float2* d_poly = nullptr;
-    int n_poly = 0;
-    unsigned char* d_raster = nullptr;
-    // per-launch buffers
-    unsigned long long* d_counter = nullptr;
-    unsigned long long* d_stats = nullptr;
-    int* d_status = nullptr;
-    DevScen* d_scens = nullptr;
-    DevItem* d_items = nullptr;
-    size_t items_cap = 0;
-    DevBox* d_boxes = nullptr;
-    size_t boxes_cap = 0;
-    OvfRec* d_ovf = nullptr;                   // out-of-box deposit records
-    long long ovf_cap = 0;
-    PhaseRec* d_phase = nullptr;               // hand-off from the devices to the patient kernel
-    long long phase_cap = 0;
-    unsigned long long* d_phase_count = nullptr;
-    unsigned long long* d_scratch = nullptr;
-    size_t scratch_cap = 0;                    // elements
-    TuneResult tune_dose, tune_im;
-    long long launches = 0;                    // kernels launched since creation
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
 
 namespace {
 

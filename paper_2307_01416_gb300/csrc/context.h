@@ -1,0 +1,73 @@
+// Library-internal definition of the context behind the C ABI's opaque
+// vpmc_ctx handle (shared by the translation units of the library).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/vpmc.h"
+#include "vpmc_internal.cuh"
+
+namespace vpmc {
+
+// Launch configuration of the two transport kernels chosen by the autotuner.
+struct TuneResult {
+    bool valid = false;
+    int dev_block = 512;     // k_devices threads per block
+    int block = 640;         // k_patient threads per block
+    int aggregate = 0;
+    int chunk = 32;
+};
+
+}  // namespace vpmc
+
+struct vpmc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    vpmc::Grid3 ctg{}, sg{};
+    double ct_spacing[3]{}, sg_spacing[3]{};
+    bool same_grid = false;
+    long long nvox = 0;
+    double curve15[15]{};
+    int16_t* d_ct = nullptr;
+    vpmc::TablesImage* d_tables = nullptr;
+    double* d_curve = nullptr;
+    double* d_rho = nullptr;
+    unsigned long long* d_acc = nullptr;       // dose accumulator (scoring grid)
+    // fields
+    bool beam_set[vpmc::kMaxBeams]{};
+    vpmc::DevBeam beams[vpmc::kMaxBeams]{};
+    std::vector<double> poly[vpmc::kMaxBeams];
+    std::vector<unsigned char> raster[vpmc::kMaxBeams];
+    vpmc::DevBeam* d_beams = nullptr;
+    float2* d_poly = nullptr;
+    int n_poly = 0;
+    unsigned char* d_raster = nullptr;
+    // per-launch buffers
+    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_stats = nullptr;
+    int* d_status = nullptr;
+    vpmc::DevScen* d_scens = nullptr;
+    vpmc::DevItem* d_items = nullptr;
+    size_t items_cap = 0;
+    vpmc::DevBox* d_boxes = nullptr;
+    size_t boxes_cap = 0;
+    vpmc::OvfRec* d_ovf = nullptr;                   // out-of-box deposit records
+    long long ovf_cap = 0;
+    vpmc::PhaseRec* d_phase = nullptr;               // hand-off from the devices to the patient kernel
+    long long phase_cap = 0;
+    unsigned long long* d_phase_count = nullptr;
+    unsigned long long* d_scratch = nullptr;
+    size_t scratch_cap = 0;                    // elements
+    vpmc::TuneResult tune_dose, tune_im;
+    long long launches = 0;                    // kernels launched since creation
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace vpmc {
+// Records an error message for vpmc_last_error() on the calling thread and
+// returns st (printf-style message).
+vpmc_status report_error(vpmc_status st, const char* fmt, ...);
+}  // namespace vpmc

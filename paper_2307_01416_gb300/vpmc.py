@@ -82,7 +82,7 @@ RECORD_DTYPE = np.dtype([("q_dep", np.int64), ("fate", np.int32), ("steps", np.i
 assert RECORD_DTYPE.itemsize == 40
 
 EXPORTED = ["vpmc_default_opts", "vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots",
-            "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_destroy", "vpmc_last_error"]
+            "vpmc_run_spots_noalloc", "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_destroy", "vpmc_last_error"]
 
 _lib = None
 
@@ -106,13 +106,15 @@ def lib():
     L.vpmc_set_aperture.argtypes = [vp, C.c_int, C.POINTER(vpmc_beam)]
     L.vpmc_run_spots.argtypes = [vp, C.POINTER(vpmc_spot), C.c_int, C.POINTER(vpmc_scenario), C.POINTER(vpmc_opts),
                                  vp, C.POINTER(vpmc_stats)]
+    L.vpmc_run_spots_noalloc.argtypes = [vp, C.POINTER(vpmc_spot), C.c_int, C.POINTER(vpmc_scenario),
+                                         C.POINTER(vpmc_opts), vp, C.POINTER(vpmc_stats)]
     L.vpmc_influence_matrix.argtypes = [vp, C.POINTER(vpmc_spot), C.c_int, C.POINTER(vpmc_scenario), C.c_int,
                                         C.POINTER(vpmc_opts), C.c_float, C.POINTER(vpmc_csr), C.POINTER(vpmc_stats)]
     L.vpmc_free_csr.argtypes = [C.POINTER(vpmc_csr), C.c_int]
     L.vpmc_destroy.argtypes = [vp]
     L.vpmc_destroy.restype = None
-    for f in ("vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots", "vpmc_influence_matrix",
-              "vpmc_free_csr"):
+    for f in ("vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots", "vpmc_run_spots_noalloc",
+              "vpmc_influence_matrix", "vpmc_free_csr"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -217,6 +219,20 @@ class Engine:
             self.stream.synchronize()
             out_rec = rec.cpu().numpy().view(RECORD_DTYPE).reshape(records)
         return dose, out_stats, out_rec
+
+    def run_spots_noalloc(self, spots: np.ndarray, dose_out, scenario: Optional[W.Scenario] = None,
+                          opts: Optional[W.Options] = None, stats: bool = True, **launch):
+        """Dose into the caller's float32 device tensor dose_out through the
+        entry point that allocates nothing (fixed scratch; see include/vpmc.h
+        for its limits).  Returns the stats dict (if stats)."""
+        o = make_opts(opts or W.Options(), **launch)
+        arr = spot_array(spots)
+        sc = scenario_struct(scenario) if scenario is not None else None
+        st = vpmc_stats()
+        _check(lib().vpmc_run_spots_noalloc(self._ctx, arr, len(spots), C.byref(sc) if sc is not None else None,
+                                            C.byref(o), C.c_void_p(dose_out.data_ptr()),
+                                            C.byref(st) if stats else None))
+        return _stats_dict(st) if stats else None
 
     def influence_matrix(self, spots: np.ndarray, scenarios: Sequence[W.Scenario], opts: Optional[W.Options] = None,
                          rel_threshold: float = 1e-4, **launch):
