@@ -116,6 +116,10 @@ typedef struct {
     int chunk;              /* histories taken per warp refill (0 = default)              */
     vpmc_history_record* history_out;  /* device buffer or NULL                          */
     int64_t history_cap;    /* records for global history index < history_cap            */
+    int range_rejection;    /* 1 (default): a brass proton whose longest possible remaining
+                               path (1.2 x residual CSDA range) cannot reach the opening or
+                               a face of the block is absorbed at once; the patient sees the
+                               same histories either way                                 */
 } vpmc_opts;
 
 /* Totals of one call.  Energies in MeV (fixed-point sums, unweighted). */
@@ -139,7 +143,7 @@ typedef struct {
 } vpmc_csr;
 
 /* Fill opts with defaults: seed 1234, all physics on, frac_bits 24,
- * autotuned launch, no records. */
+ * autotuned launch, no records, brass range rejection on. */
 void vpmc_default_opts(vpmc_opts* opts);
 
 /* Create a context (Sec. 2.A physics tables; Sec. 2.D.3 patient CT).

@@ -320,6 +320,7 @@ typedef struct {
     uint64_t seed;
     int mcs, straggling, nuclear;
     int frac_bits;
+    int range_rejection;    /* absorb brass protons that cannot leave the block */
 } orc_opts;
 
 typedef struct {
@@ -347,7 +348,9 @@ typedef struct {
                            (free-path rounding) / (0.0012 rho) mm);
                            bit 3: a CT voxel face crossed at a direction
                            cosine below 0.01 |delta SPR| (the crossing point
-                           moves by (position rounding) / cosine)          */
+                           moves by (position rounding) / cosine);
+                           bit 4: a brass range-rejection test decided within
+                           ORC_TIE_MM of its threshold                      */
     int32_t pad;
     double path;        /* path length travelled in the patient grid, mm     */
     double track;       /* whole track length from the source plane, mm      */
@@ -646,6 +649,26 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
                 rec->track += sg;
                 if (!down) goto leak;
                 break;
+            }
+            /* brass: a proton whose longest possible remaining path (1.2 x
+             * its residual CSDA range; range straggling is ~1.2 %) cannot
+             * reach the opening or either face of the block is absorbed now:
+             * its energy stays in the brass either way */
+            if (op->range_rejection) {
+                double rmax = 1.2 * pt.R / ORC_MAT[ORC_BRASS].rho;
+                double dlim = pt.p[2] - tup;
+                if (tdn - pt.p[2] < dlim) dlim = tdn - pt.p[2];
+                if (rmax < dlim + ORC_TIE_MM) {
+                    double dw = orc_wall_distance(poly, bm->nvert, pt.p[0], pt.p[1]);
+                    if (dw < dlim) dlim = dw;
+                    if (fabs(rmax - dlim) < ORC_TIE_MM) rec->flags |= 16;
+                    if (rmax < dlim) {
+                        tl[4] += pt.E;
+                        pt.E = 0.0;
+                        rec->fate = FATE_AP;
+                        goto done;
+                    }
+                }
             }
             /* brass: condensed-history step with brass physics */
             forced_brass = 0;
@@ -997,7 +1020,7 @@ void orc_step_sample(int table, double kappa, double rho, double za, double X0,
 {
     orc_init_tables();
     orc_medium med = {table, kappa, rho, za, X0};
-    orc_opts op = {seed, mcs, straggling, nuclear, 24};
+    orc_opts op = {seed, mcs, straggling, nuclear, 24, 0};
     orc_stream st;
     st.key[0] = (uint32_t)seed;
     st.key[1] = (uint32_t)(seed >> 32) ^ (uint32_t)spot_key;

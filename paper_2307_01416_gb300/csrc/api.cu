@@ -136,6 +136,7 @@ vpmc_status upload_beams(vpmc_ctx* c)
 {
     std::vector<float2> poly;
     std::vector<unsigned char> ras;
+    std::vector<float> ras_lb;
     DevBeam tmp[kMaxBeams];
     for (int b = 0; b < kMaxBeams; ++b) {
         tmp[b] = c->beams[b];
@@ -145,17 +146,23 @@ vpmc_status upload_beams(vpmc_ctx* c)
             poly.push_back(make_float2((float)c->poly[b][i], (float)c->poly[b][i + 1]));
         tmp[b].ras_off = (int)ras.size();
         ras.insert(ras.end(), c->raster[b].begin(), c->raster[b].end());
+        ras_lb.insert(ras_lb.end(), c->raster_lb[b].begin(), c->raster_lb[b].end());
     }
     if (poly.size() > (size_t)kMaxPolyVerts)
         return fail(VPMC_ERR_ARG, "aperture polygons have %zu vertices in total (max %d)", poly.size(), kMaxPolyVerts);
     cudaFree(c->d_poly);
     cudaFree(c->d_raster);
+    cudaFree(c->d_raster_lb);
     c->d_poly = nullptr;
     c->d_raster = nullptr;
+    c->d_raster_lb = nullptr;
     CUDA_TRY(dev_alloc(&c->d_poly, std::max<size_t>(poly.size(), 1)));
     CUDA_TRY(dev_alloc(&c->d_raster, std::max<size_t>(ras.size(), 1)));
+    CUDA_TRY(dev_alloc(&c->d_raster_lb, std::max<size_t>(ras_lb.size(), 1)));
     if (!poly.empty()) CUDA_TRY(cudaMemcpy(c->d_poly, poly.data(), poly.size() * sizeof(float2), cudaMemcpyHostToDevice));
     if (!ras.empty()) CUDA_TRY(cudaMemcpy(c->d_raster, ras.data(), ras.size(), cudaMemcpyHostToDevice));
+    if (!ras_lb.empty())
+        CUDA_TRY(cudaMemcpy(c->d_raster_lb, ras_lb.data(), ras_lb.size() * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->d_beams, tmp, sizeof(tmp), cudaMemcpyHostToDevice));
     c->n_poly = (int)poly.size();
     return VPMC_OK;
@@ -207,6 +214,8 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     p.poly = c->d_poly;
     p.n_poly = c->n_poly;
     p.raster = c->d_raster;
+    p.raster_lb = c->d_raster_lb;
+    p.range_rejection = o.range_rejection;
     p.items = c->d_items;
     p.boxes = c->d_boxes;
     p.counter = c->d_counter;
@@ -370,6 +379,7 @@ void vpmc_default_opts(vpmc_opts* o)
     o->nuclear = 1;
     o->frac_bits = 24;
     o->aggregate = -1;
+    o->range_rejection = 1;
 }
 
 const char* vpmc_last_error(void) { return g_error.c_str(); }
@@ -504,6 +514,7 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
     d.ap = b->ap_present ? 1 : 0;
     std::vector<double> poly;
     std::vector<unsigned char> ras;
+    std::vector<float> ras_lb;
     if (d.ap) {
         if (!b->poly_xy || b->n_vertices < 3) return fail(VPMC_ERR_ARG, "aperture needs a polygon of >= 3 vertices");
         if (!(b->ap_thickness_mm > 0)) return fail(VPMC_ERR_ARG, "aperture thickness must be positive");
@@ -516,7 +527,10 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
         for (double x : poly)
             if (!std::isfinite(x)) return fail(VPMC_ERR_ARG, "aperture polygon has a non-finite vertex");
         ras.resize(kRaster * kRaster);
-        build_raster(poly.data(), b->n_vertices, ras.data(), d.ras_lo, d.ras_inv);
+        ras_lb.resize(kRaster * kRaster);
+        // range rejection needs wall distances up to half the block thickness only
+        build_raster(poly.data(), b->n_vertices, 0.5 * b->ap_thickness_mm + 1.0, ras.data(), ras_lb.data(), d.ras_lo,
+                     d.ras_inv, &d.ras_diag);
         d.nvert = b->n_vertices;
     }
     if (first_device < 1e300 && !(-b->source_to_iso_mm < first_device))
@@ -525,15 +539,18 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
     const DevBeam prev = c->beams[beam_id];
     std::vector<double> prev_poly = c->poly[beam_id];
     std::vector<unsigned char> prev_ras = c->raster[beam_id];
+    std::vector<float> prev_lb = c->raster_lb[beam_id];
     c->beams[beam_id] = d;
     c->poly[beam_id] = poly;
     c->raster[beam_id] = ras;
+    c->raster_lb[beam_id] = ras_lb;
     c->beam_set[beam_id] = true;
     vpmc_status st = upload_beams(c);
     if (st != VPMC_OK) {
         c->beams[beam_id] = prev;
         c->poly[beam_id] = prev_poly;
         c->raster[beam_id] = prev_ras;
+        c->raster_lb[beam_id] = prev_lb;
         c->beam_set[beam_id] = prev_set;
         return st;
     }
@@ -1074,6 +1091,7 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->d_beams);
     cudaFree(c->d_poly);
     cudaFree(c->d_raster);
+    cudaFree(c->d_raster_lb);
     cudaFree(c->d_counter);
     cudaFree(c->d_stats);
     cudaFree(c->d_status);

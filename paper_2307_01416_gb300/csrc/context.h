@@ -41,10 +41,12 @@ struct vpmc_ctx {
     vpmc::DevBeam beams[vpmc::kMaxBeams]{};
     std::vector<double> poly[vpmc::kMaxBeams];
     std::vector<unsigned char> raster[vpmc::kMaxBeams];
+    std::vector<float> raster_lb[vpmc::kMaxBeams];
     vpmc::DevBeam* d_beams = nullptr;
     float2* d_poly = nullptr;
     int n_poly = 0;
     unsigned char* d_raster = nullptr;
+    float* d_raster_lb = nullptr;
     // per-launch buffers
     unsigned long long* d_counter = nullptr;
     unsigned long long* d_stats = nullptr;

@@ -182,6 +182,8 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     p.poly = c->d_poly;
     p.n_poly = c->n_poly;
     p.raster = c->d_raster;
+    p.raster_lb = c->d_raster_lb;
+    p.range_rejection = o.range_rejection;
     p.items = items;
     p.n_items = n_items;
     p.boxes = box;

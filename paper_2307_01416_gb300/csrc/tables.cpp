@@ -113,6 +113,32 @@ bool segment_hits_box(double ax, double ay, double bx, double by, double x0, dou
     return true;
 }
 
+double point_rect_distance(double x, double y, double x0, double y0, double x1, double y1)
+{
+    const double dx = std::max(std::max(x0 - x, 0.0), x - x1);
+    const double dy = std::max(std::max(y0 - y, 0.0), y - y1);
+    return std::sqrt(dx * dx + dy * dy);
+}
+
+double point_segment_distance(double x, double y, double ax, double ay, double bx, double by)
+{
+    const double ex = bx - ax, ey = by - ay;
+    const double l2 = ex * ex + ey * ey;
+    double t = l2 > 0.0 ? ((x - ax) * ex + (y - ay) * ey) / l2 : 0.0;
+    t = std::min(std::max(t, 0.0), 1.0);
+    const double dx = ax + t * ex - x, dy = ay + t * ey - y;
+    return std::sqrt(dx * dx + dy * dy);
+}
+
+// Distance between a segment and a rectangle that it does not intersect.
+double segment_rect_distance(double ax, double ay, double bx, double by, double x0, double y0, double x1, double y1)
+{
+    double d = std::min(point_rect_distance(ax, ay, x0, y0, x1, y1), point_rect_distance(bx, by, x0, y0, x1, y1));
+    const double cx[4] = {x0, x1, x1, x0}, cy[4] = {y0, y0, y1, y1};
+    for (int k = 0; k < 4; ++k) d = std::min(d, point_segment_distance(cx[k], cy[k], ax, ay, bx, by));
+    return d;
+}
+
 bool crossing_number_inside(const double* xy, int n, double x, double y)
 {
     bool inside = false;
@@ -153,7 +179,8 @@ void build_tables(const double* curve15, TablesImage* img)
     }
 }
 
-void build_raster(const double* xy, int n, unsigned char* cells, float lo[2], float inv[2])
+void build_raster(const double* xy, int n, double margin, unsigned char* cells, float* lower, float lo[2], float inv[2],
+                  float* diag)
 {
     double xmin = xy[0], xmax = xy[0], ymin = xy[1], ymax = xy[1];
     for (int i = 1; i < n; ++i) {
@@ -161,12 +188,13 @@ void build_raster(const double* xy, int n, unsigned char* cells, float lo[2], fl
         ymin = std::min(ymin, xy[2 * i + 1]); ymax = std::max(ymax, xy[2 * i + 1]);
     }
     // cover the polygon with a margin so that every point outside the raster is
-    // outside the polygon
-    const double pad = 0.02 * std::max(xmax - xmin, ymax - ymin) + 0.1;
+    // outside the polygon and farther than `margin` from its boundary
+    const double pad = std::max(0.02 * std::max(xmax - xmin, ymax - ymin) + 0.1, margin);
     xmin -= pad; xmax += pad; ymin -= pad; ymax += pad;
     const double cw = (xmax - xmin) / kRaster, ch = (ymax - ymin) / kRaster;
     lo[0] = (float)xmin; lo[1] = (float)ymin;
     inv[0] = (float)(1.0 / cw); inv[1] = (float)(1.0 / ch);
+    *diag = (float)(std::sqrt(cw * cw + ch * ch) * (1.0 + 1e-6) + 1e-4);
     // FP32 placement of a point can move it by a few ulps across a cell border,
     // so a cell is classified only if no edge comes within eps of it
     const double eps = 1e-3 * std::max(cw, ch) + 1e-4 * (std::fabs(xmin) + std::fabs(ymin) + 1.0);
@@ -182,6 +210,19 @@ void build_raster(const double* xy, int n, unsigned char* cells, float lo[2], fl
             unsigned char c = 2;
             if (!edge) c = crossing_number_inside(xy, n, xmin + (cx + 0.5) * cw, ymin + (cy + 0.5) * ch) ? 1 : 0;
             cells[cy * kRaster + cx] = c;
+            // lower bound of the distance from any point of the cell to the boundary
+            double lb = 0.0;
+            if (!edge) {
+                lb = 1e300;
+                const double rx0 = xmin + cx * cw, rx1 = rx0 + cw, ry0 = ymin + cy * ch, ry1 = ry0 + ch;
+                for (int i = 0; i < n; ++i) {
+                    const int j = (i + 1) % n;
+                    lb = std::min(lb, segment_rect_distance(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1],
+                                                            rx0, ry0, rx1, ry1));
+                }
+                lb = std::max(lb - 1e-4, 0.0);     // margin for the FP32 use of the bound
+            }
+            lower[cy * kRaster + cx] = (float)lb;
         }
 }
 

@@ -8,7 +8,11 @@ namespace vpmc {
 // curve15 = {hu[5], density[5], spr[5]}
 void build_tables(const double* curve15, TablesImage* img);
 double pmma_stopping_power_ratio(double kinetic_mev);
-void build_raster(const double* xy, int n, unsigned char* cells, float lo[2], float inv[2]);
+// cells: 0 outside, 1 inside, 2 near an edge; lower: per cell a lower bound of
+// the distance to the boundary; diag: cell diagonal (plus a margin).  Points
+// outside the raster are at least `margin` from the boundary.
+void build_raster(const double* xy, int n, double margin, unsigned char* cells, float* lower, float lo[2], float inv[2],
+                  float* diag);
 void hu_curve_props(const double* curve15, double hu, double* rho, double* spr);
 
 }  // namespace vpmc

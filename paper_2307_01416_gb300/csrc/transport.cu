@@ -153,6 +153,44 @@ __device__ __forceinline__ bool in_opening(const DevBeam& B, const float2* __res
     return point_in_polygon(poly + B.poly_off, B.nvert, a, b);
 }
 
+// Distance from (x, y) to the polygon boundary.
+__device__ __noinline__ float wall_distance(const float2* __restrict__ poly, int n, float x, float y)
+{
+    float best = __int_as_float(0x7f800000);
+    for (int i = 0; i < n; ++i) {
+        const float2 a = poly[i];
+        const float2 b = poly[i + 1 < n ? i + 1 : 0];
+        const float ex = b.x - a.x, ey = b.y - a.y;
+        float t = __fdividef((x - a.x) * ex + (y - a.y) * ey, ex * ex + ey * ey);
+        t = fminf(fmaxf(t, 0.0f), 1.0f);
+        const float dx = a.x + t * ex - x, dy = a.y + t * ey - y;
+        best = fminf(best, dx * dx + dy * dy);
+    }
+    return sqrtf(best);
+}
+
+// True if the brass proton at (a, b), whose longest remaining path is rmax,
+// cannot reach the opening: decided from the raster's per-cell lower bound of
+// the wall distance, with the exact distance only inside the one-cell band.
+__device__ __forceinline__ bool beyond_wall(const DevBeam& B, const float2* __restrict__ poly,
+                                            const float* __restrict__ lower, float a, float b, float rmax)
+{
+    const float fx = (a - B.ras_lo[0]) * B.ras_inv[0];
+    const float fy = (b - B.ras_lo[1]) * B.ras_inv[1];
+    float lb, ub;
+    if (fx >= 0.0f && fx < (float)kRaster && fy >= 0.0f && fy < (float)kRaster) {
+        lb = __ldg(lower + B.ras_off + (int)fy * kRaster + (int)fx);
+        ub = lb + B.ras_diag;
+    } else {
+        // outside the raster: farther from the boundary than half the block thickness,
+        // hence than any rmax that passed the face test
+        return true;
+    }
+    if (rmax < lb) return true;
+    if (rmax >= ub) return false;
+    return rmax < wall_distance(poly + B.poly_off, B.nvert, a, b);
+}
+
 // Duff et al. 2017, "Building an orthonormal basis, revisited".
 __device__ __forceinline__ void orthonormal_basis(const float n[3], float b1[3], float b2[3])
 {
@@ -540,9 +578,24 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                         if (down) advance = true; else fate = kLeak;
                     }
                 } else {
+                    // brass: a proton whose longest possible remaining path (1.2 x its
+                    // residual CSDA range) cannot reach the opening or a face of the
+                    // block is absorbed now -- its energy stays in the brass either way
+                    bool absorb = false;
+                    if (P.range_rejection && !L.forced) {
+                        const float rmax = 1.2f * L.R * __fdividef(1.0f, brass.rho);
+                        const float dpl = fminf(L.p[2] - B.ap_tup, B.ap_tdn - L.p[2]);
+                        if (rmax < dpl) absorb = beyond_wall(B, poly, P.raster_lb, L.p[0], L.p[1], rmax);
+                    }
                     L.forced = 0;
-                    m = brass;
-                    do_ch = true;
+                    if (absorb) {
+                        acc_ap += __float2ull_rn(L.E * P.fscale);
+                        L.E = 0.0f;
+                        fate = kAbsAp;
+                    } else {
+                        m = brass;
+                        do_ch = true;
+                    }
                 }
             }
             if (do_ch) {

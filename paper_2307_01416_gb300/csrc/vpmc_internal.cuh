@@ -16,7 +16,7 @@ constexpr int kNHU = 4096;           // HU -1024..3071
 constexpr int kMaxBeams = 16;
 constexpr int kMaxScen = 64;
 constexpr int kMaxPolyVerts = 1024;
-constexpr int kRaster = 64;          // BEV classification raster per beam (cells per side)
+constexpr int kRaster = 256;         // BEV raster per beam (cells per side): opening class, wall-distance bound
 constexpr float kEcut = 0.5f;        // MeV
 constexpr int kMaxIter = 200000;     // iterations per history before it is stopped as an error
 
@@ -47,8 +47,8 @@ struct DevBeam {
     float ap_tup, ap_tdn;
     int poly_off, nvert;
     float ras_lo[2], ras_inv[2];     // raster origin and 1/cell size
-    int ras_off;                     // offset into the raster byte array
-    int pad;
+    int ras_off;                     // offset into the raster arrays (class bytes, distance bounds)
+    float ras_diag;                  // raster cell diagonal
 };
 
 struct DevScen {
@@ -120,6 +120,8 @@ struct TransportParams {
     const float2* poly;
     int n_poly;
     const unsigned char* raster;
+    const float* raster_lb;          // per raster cell: lower bound of the distance to the opening's boundary
+    int range_rejection;             // absorb brass protons that cannot leave the block
     const DevItem* items;
     int n_items;
     const DevBox* boxes;

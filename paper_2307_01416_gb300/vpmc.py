@@ -62,7 +62,7 @@ class vpmc_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("mcs", C.c_int), ("straggling", C.c_int), ("nuclear", C.c_int),
                 ("frac_bits", C.c_int), ("aggregate", C.c_int), ("block_size", C.c_int),
                 ("blocks_per_sm", C.c_int), ("chunk", C.c_int), ("history_out", C.c_void_p),
-                ("history_cap", C.c_int64)]
+                ("history_cap", C.c_int64), ("range_rejection", C.c_int)]
 
 
 class vpmc_stats(C.Structure):
@@ -140,6 +140,7 @@ def make_opts(o: W.Options, aggregate: int = -1, block_size: int = 0, chunk: int
     v.seed, v.mcs, v.straggling, v.nuclear, v.frac_bits = int(o.seed), int(o.mcs), int(o.straggling), int(o.nuclear), \
         int(o.frac_bits)
     v.aggregate, v.block_size, v.chunk = aggregate, block_size, chunk
+    v.range_rejection = int(getattr(o, "range_rejection", True))
     return v
 
 

@@ -91,6 +91,7 @@ class Options:
     straggling: bool = True
     nuclear: bool = True
     frac_bits: int = 24
+    range_rejection: bool = True   # absorb brass protons that cannot leave the block
 
     @property
     def deterministic(self) -> bool:

@@ -38,7 +38,9 @@ def _per_history_parity(pb, spots, scen, op, records=None, max_flagged=0.01):
     range-shifter rim (at grazing incidence a rounding-level position change
     moves a brass chord ~500x as much), nuclear removal in air-like media
     (the point moves by free-path rounding / (0.0012 rho)), and CT voxel faces
-    crossed at a direction cosine below 0.01 |delta SPR|.  Every other
+    crossed at a direction cosine below 0.01 |delta SPR|, and brass
+    range-rejection decisions taken within 10 um of their threshold (the
+    end point only).  Every other
     history must match the oracle's fate, scored energy and end position to
     1e-4 relative; flagged ones must be rare."""
     n = int(spots["n_hist"].sum()) if records is None else records
@@ -47,12 +49,15 @@ def _per_history_parity(pb, spots, scen, op, records=None, max_flagged=0.01):
     q_o, tl, orec = O.run(pb, O.oracle_spots(spots), scen, op, records=n)
     eng.close()
     assert st["errors"] == 0 and tl["errors"] == 0
+    # a brass range-rejection decision taken within 10 um of its threshold (flag
+    # 16) moves only the recorded end point: fate and scored energy still match
+    cond = (orec["flags"] & ~16) == 0
     ok = orec["flags"] == 0
-    assert np.mean(~ok) <= max_flagged, np.mean(~ok)
-    bad_fate = np.flatnonzero((rec["fate"] != orec["fate"]) & ok)
+    assert np.mean(~cond) <= max_flagged, np.mean(~cond)
+    bad_fate = np.flatnonzero((rec["fate"] != orec["fate"]) & cond)
     assert bad_fate.size == 0, bad_fate[:10]
     scale = np.maximum(np.abs(orec["e_dep"]), 1.0)
-    err = np.where(ok, np.abs(rec["e_dep"] - orec["e_dep"]) / scale, 0.0)
+    err = np.where(cond, np.abs(rec["e_dep"] - orec["e_dep"]) / scale, 0.0)
     assert err.max() < 1e-4, (err.max(), np.argmax(err))
     track = np.maximum(orec["track"], 1.0)        # track length from the source plane, mm
     perr = np.where(ok, np.linalg.norm(rec["pos"] - orec["pos"], axis=1) / track, 0.0)
@@ -252,3 +257,17 @@ def test_influence_matrix_columns_sum_to_dose(torch_cuda):
     g = _dense(mats[0]) * spots["n_hist"][None, :].astype(np.float64)
     d = dose.cpu().numpy().ravel().astype(np.float64)
     assert np.allclose(g.sum(axis=1), d, rtol=1e-5, atol=1e-6 * d.max())
+
+
+def test_range_rejection_leaves_gpu_dose_unchanged(torch_cuda):
+    """Absorbing brass protons that cannot leave the block gives the same
+    patient dose, bit for bit, with far fewer steps."""
+    pb, spots = W.water_aperture_case(10.0, True, hist_per_layer=20000, max_layers=2, shape=(40, 40, 60))
+    eng = _engine(pb)
+    d1, s1, _ = eng.run_spots(spots, W.Scenario(), W.Options(seed=5))
+    d0, s0, _ = eng.run_spots(spots, W.Scenario(), W.Options(seed=5, range_rejection=False))
+    eng.close()
+    assert np.array_equal(d1.cpu().numpy(), d0.cpu().numpy())
+    assert s1["e_dep"] == s0["e_dep"] and s1["e_leak"] == s0["e_leak"]
+    assert abs(s1["e_aperture"] / s0["e_aperture"] - 1.0) < 1e-6
+    assert s1["steps"] < 0.6 * s0["steps"]
