@@ -112,6 +112,23 @@ class ClockSampler:
                 "reasons": sorted(active), "samples": len(rows)}
 
 
+def transport_traffic(steps_per_launch: float):
+    """DRAM bytes (read + write) of one set's transport, scaled from the ncu
+    capture summarised in profiles/k_transport_head_im13.md by condensed-history
+    steps; None when the kernels changed since the capture (source hash)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_transport_traffic.txt")
+    try:
+        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
+    except OSError:
+        return None
+    src = os.path.join(ROOT, "paper_2307_01416_gb300", "csrc", "transport.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if kv.get("transport_cu_sha256") != digest:
+        return None
+    return float(kv["dram_bytes_per_step"]) * steps_per_launch
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -267,16 +284,9 @@ def main():
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
         peak_tops = nsm * 4 * 32 * sm_max * 1e6 / 1e12
         achieved = steps * OPS_PER_STEP / (kern_ms / 1000.0) / 1e12
-        traffic = None
-        tpath = os.path.join(ROOT, "profiles", "transport_traffic.json")
-        if os.path.exists(tpath):
-            try:
-                tj = json.load(open(tpath))
-                traffic = tj.get("bytes_per_step", 0) * steps / args.steps if tj.get("valid") else None
-            except (OSError, ValueError):
-                traffic = None
+        traffic = transport_traffic(steps / args.steps)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                "frac": achieved / peak_tops, "traffic": traffic, "kernel": "k_transport",
+                "frac": achieved / peak_tops, "traffic": traffic, "kernel": "k_devices+k_patient",
                 "peak_note": "%d SMs x 4 sub-partitions x 32 lanes x %.0f MHz (max SM clock) lane-ops/s; "
                              "%d lane-ops per condensed-history step" % (nsm, sm_max, OPS_PER_STEP),
                 "kernel_ms_per_step": kern_ms / args.steps, "steps_per_launch": steps / args.steps}

@@ -105,90 +105,119 @@ __device__ __forceinline__ float energy_of(const float* __restrict__ Et, float i
     return fmaf(f, Et[j + 1] - e0, e0);
 }
 
-// Crossing-number (ray casting) point-in-polygon test, half-open edge rule.
-__device__ __forceinline__ bool point_in_polygon(const float2* __restrict__ poly, int n, float x, float y)
+// Lower bound of the distance from (a, b) to the polygon boundary from the
+// raster (0 outside it or in a cell an edge passes through).
+__device__ __forceinline__ float wall_lower_bound(const DevBeam& B, const float* __restrict__ lower, float a, float b)
 {
-    bool inside = false;
-    float2 pj = poly[n - 1];
-    for (int i = 0; i < n; ++i) {
-        const float2 pi = poly[i];
-        if ((pi.y > y) != (pj.y > y)) {
-            const float xc = pi.x + (y - pi.y) * (pj.x - pi.x) / (pj.y - pi.y);
-            if (x < xc) inside = !inside;
+    const float fx = (a - B.ras_lo[0]) * B.ras_inv[0];
+    const float fy = (b - B.ras_lo[1]) * B.ras_inv[1];
+    if (!(fx >= 0.0f && fx < (float)kRaster && fy >= 0.0f && fy < (float)kRaster)) return 0.0f;
+    return __ldg(lower + B.ras_off + (int)fy * kRaster + (int)fx);
+}
+
+// ---- warp-cooperative exact polygon queries --------------------------------
+// Lanes that need an exact test post a request; the converged warp then serves
+// the requests one by one, each lane evaluating every 32nd edge with the same
+// per-edge arithmetic as a serial loop, and the warp reduces the results.
+// Every lane of the warp must call these (need = false for non-requesters).
+
+// Raster class of (a, b): 0 outside the opening, 1 inside, 2 near an edge.
+__device__ __forceinline__ int raster_class(const DevBeam& B, const unsigned char* __restrict__ raster, float a, float b)
+{
+    const float fx = (a - B.ras_lo[0]) * B.ras_inv[0];
+    const float fy = (b - B.ras_lo[1]) * B.ras_inv[1];
+    if (!(fx >= 0.0f && fx < (float)kRaster && fy >= 0.0f && fy < (float)kRaster)) return 0;
+    return __ldg(raster + B.ras_off + (int)fy * kRaster + (int)fx);
+}
+
+// Crossing number (half-open edge rule) of the requesting lane's point.
+__device__ __forceinline__ bool coop_point_in_polygon(bool need, float x, float y, const float2* __restrict__ poly,
+                                                      int off, int n, int lane)
+{
+    bool result = false;
+    unsigned m = __ballot_sync(kFull, need);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        const float qx = __shfl_sync(kFull, x, src), qy = __shfl_sync(kFull, y, src);
+        const int qo = __shfl_sync(kFull, off, src), qn = __shfl_sync(kFull, n, src);
+        bool c = false;
+        for (int i = lane; i < qn; i += 32) {
+            const float2 pi = poly[qo + i];
+            const float2 pj = poly[qo + (i == 0 ? qn - 1 : i - 1)];
+            if ((pi.y > qy) != (pj.y > qy)) {
+                const float xc = pi.x + (qy - pi.y) * (pj.x - pi.x) / (pj.y - pi.y);
+                if (qx < xc) c = !c;
+            }
         }
-        pj = pi;
+        const bool in = (__popc(__ballot_sync(kFull, c)) & 1) != 0;
+        if (lane == src) result = in;
     }
-    return inside;
+    return result;
 }
 
-// Smallest s > 0 at which (x, y) + s (dx, dy) crosses an edge.
-__device__ __forceinline__ float first_wall_hit(const float2* __restrict__ poly, int n, float x, float y, float dx,
-                                                float dy)
+__device__ __forceinline__ float warp_min(float v)
 {
-    float best = __int_as_float(0x7f800000);
-    for (int i = 0; i < n; ++i) {
-        const float2 a = poly[i];
-        const float2 b = poly[i + 1 < n ? i + 1 : 0];
-        const float ex = b.x - a.x, ey = b.y - a.y;
-        const float den = dx * ey - dy * ex;
-        if (den == 0.0f) continue;
-        const float wx = a.x - x, wy = a.y - y;
-        const float s = (wx * ey - wy * ex) / den;
-        const float lam = (wx * dy - wy * dx) / den;
-        if (s > 0.0f && lam >= 0.0f && lam <= 1.0f && s < best) best = s;
-    }
-    return best;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
 }
 
-// Opening test accelerated by the beam's BEV raster: cells that no edge comes
-// near are wholly inside (1) or outside (0); edge cells (2) run the exact test.
-__device__ __forceinline__ bool in_opening(const DevBeam& B, const float2* __restrict__ poly,
-                                           const unsigned char* __restrict__ raster, float a, float b)
+// Smallest s > 0 at which the requester's ray (x, y) + s (dx, dy) crosses an edge.
+__device__ __forceinline__ float coop_first_wall_hit(bool need, float x, float y, float dx, float dy,
+                                                     const float2* __restrict__ poly, int off, int n, int lane)
 {
-    const float fx = (a - B.ras_lo[0]) * B.ras_inv[0];
-    const float fy = (b - B.ras_lo[1]) * B.ras_inv[1];
-    if (!(fx >= 0.0f && fx < (float)kRaster && fy >= 0.0f && fy < (float)kRaster)) return false;
-    const int c = __ldg(raster + B.ras_off + (int)fy * kRaster + (int)fx);
-    if (c != 2) return c == 1;
-    return point_in_polygon(poly + B.poly_off, B.nvert, a, b);
+    float result = __int_as_float(0x7f800000);
+    unsigned m = __ballot_sync(kFull, need);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        const float qx = __shfl_sync(kFull, x, src), qy = __shfl_sync(kFull, y, src);
+        const float qdx = __shfl_sync(kFull, dx, src), qdy = __shfl_sync(kFull, dy, src);
+        const int qo = __shfl_sync(kFull, off, src), qn = __shfl_sync(kFull, n, src);
+        float best = __int_as_float(0x7f800000);
+        for (int i = lane; i < qn; i += 32) {
+            const float2 a = poly[qo + i];
+            const float2 b = poly[qo + (i + 1 < qn ? i + 1 : 0)];
+            const float ex = b.x - a.x, ey = b.y - a.y;
+            const float den = qdx * ey - qdy * ex;
+            if (den == 0.0f) continue;
+            const float wx = a.x - qx, wy = a.y - qy;
+            const float sh = (wx * ey - wy * ex) / den;
+            const float lam = (wx * qdy - wy * qdx) / den;
+            if (sh > 0.0f && lam >= 0.0f && lam <= 1.0f && sh < best) best = sh;
+        }
+        best = warp_min(best);
+        if (lane == src) result = best;
+    }
+    return result;
 }
 
-// Distance from (x, y) to the polygon boundary.
-__device__ __noinline__ float wall_distance(const float2* __restrict__ poly, int n, float x, float y)
+// Distance from the requester's point to the polygon boundary.
+__device__ __forceinline__ float coop_wall_distance(bool need, float x, float y, const float2* __restrict__ poly,
+                                                    int off, int n, int lane)
 {
-    float best = __int_as_float(0x7f800000);
-    for (int i = 0; i < n; ++i) {
-        const float2 a = poly[i];
-        const float2 b = poly[i + 1 < n ? i + 1 : 0];
-        const float ex = b.x - a.x, ey = b.y - a.y;
-        float t = __fdividef((x - a.x) * ex + (y - a.y) * ey, ex * ex + ey * ey);
-        t = fminf(fmaxf(t, 0.0f), 1.0f);
-        const float dx = a.x + t * ex - x, dy = a.y + t * ey - y;
-        best = fminf(best, dx * dx + dy * dy);
+    float result = 0.0f;
+    unsigned m = __ballot_sync(kFull, need);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        const float qx = __shfl_sync(kFull, x, src), qy = __shfl_sync(kFull, y, src);
+        const int qo = __shfl_sync(kFull, off, src), qn = __shfl_sync(kFull, n, src);
+        float best = __int_as_float(0x7f800000);
+        for (int i = lane; i < qn; i += 32) {
+            const float2 a = poly[qo + i];
+            const float2 b = poly[qo + (i + 1 < qn ? i + 1 : 0)];
+            const float ex = b.x - a.x, ey = b.y - a.y;
+            float t = __fdividef((qx - a.x) * ex + (qy - a.y) * ey, ex * ex + ey * ey);
+            t = fminf(fmaxf(t, 0.0f), 1.0f);
+            const float ddx = a.x + t * ex - qx, ddy = a.y + t * ey - qy;
+            best = fminf(best, ddx * ddx + ddy * ddy);
+        }
+        best = warp_min(best);
+        if (lane == src) result = sqrtf(best);
     }
-    return sqrtf(best);
-}
-
-// True if the brass proton at (a, b), whose longest remaining path is rmax,
-// cannot reach the opening: decided from the raster's per-cell lower bound of
-// the wall distance, with the exact distance only inside the one-cell band.
-__device__ __forceinline__ bool beyond_wall(const DevBeam& B, const float2* __restrict__ poly,
-                                            const float* __restrict__ lower, float a, float b, float rmax)
-{
-    const float fx = (a - B.ras_lo[0]) * B.ras_inv[0];
-    const float fy = (b - B.ras_lo[1]) * B.ras_inv[1];
-    float lb, ub;
-    if (fx >= 0.0f && fx < (float)kRaster && fy >= 0.0f && fy < (float)kRaster) {
-        lb = __ldg(lower + B.ras_off + (int)fy * kRaster + (int)fx);
-        ub = lb + B.ras_diag;
-    } else {
-        // outside the raster: farther from the boundary than half the block thickness,
-        // hence than any rmax that passed the face test
-        return true;
-    }
-    if (rmax < lb) return true;
-    if (rmax >= ub) return false;
-    return rmax < wall_distance(poly + B.poly_off, B.nvert, a, b);
+    return result;
 }
 
 // Duff et al. 2017, "Building an orthonormal basis, revisited".
@@ -527,15 +556,17 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
 
         // ---- one iteration of every live history ----
         bool handoff = false;
+        int fate = -1;
+        bool advance = false;
+        Medium m;
+        bool do_ch = false;
+        float s_geom = __int_as_float(0x7f800000);
+        bool down = true;
+        bool ap_pending = false, was_forced = false, need_pip = false;
+        int cls = 0, q_off = 0, q_n = 0;
         if (alive) {
-            int fate = -1;
-            bool advance = false;
             const DevItem& I = P.items[L.item];
             const DevBeam& B = beams[__ldg(&I.beam)];
-            Medium m;
-            bool do_ch = false;
-            float s_geom = __int_as_float(0x7f800000);
-            bool down = true;
             if (++L.iters > kMaxIter) {
                 fate = kErr;
             } else if (L.stage < 0) {
@@ -558,14 +589,59 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                     do_ch = true;
                 }
             } else {
-                // ---- aperture block ----
+                // ---- aperture block: geometry needing exact polygon tests is
+                // requested here and served below by the whole warp ----
                 if (L.d[2] > 0.0f) s_geom = (B.ap_tdn - L.p[2]) / L.d[2];
                 else if (L.d[2] < 0.0f) { s_geom = (B.ap_tup - L.p[2]) / L.d[2]; down = false; }
-                s_geom = fmaxf(s_geom, 0.0f);
-                const bool open = !L.forced && in_opening(B, poly, P.raster, L.p[0], L.p[1]);
+                s_geom = fmaxf(s_geom, 0.0f);       // scattering offsets can leave it past the plane
+                ap_pending = true;
+                was_forced = L.forced != 0;
+                cls = was_forced ? 0 : raster_class(B, P.raster, L.p[0], L.p[1]);
+                need_pip = cls == 2;
+                q_off = B.poly_off;
+                q_n = B.nvert;
+            }
+        }
+        // ---- exact opening test for lanes near an edge (warp-cooperative) ----
+        const bool pip_in = coop_point_in_polygon(need_pip, L.p[0], L.p[1], poly, q_off, q_n, lane);
+        bool open = false, need_hit = false, need_dist = false, absorb = false;
+        float rmax = 0.0f;
+        if (ap_pending) {
+            const DevBeam& B = beams[__ldg(&P.items[L.item].beam)];
+            open = cls == 1 || (cls == 2 && pip_in);
+            if (open) {
+                // a flight whose lateral travel stays below the wall-distance bound of
+                // its start cell cannot meet a wall
+                const float lat = s_geom * sqrtf(L.d[0] * L.d[0] + L.d[1] * L.d[1]);
+                need_hit = !(lat < wall_lower_bound(B, P.raster_lb, L.p[0], L.p[1]));
+            } else if (P.range_rejection && !was_forced) {
+                // a proton whose longest possible remaining path (1.2 x its residual
+                // CSDA range) cannot reach the opening or a face of the block is
+                // absorbed now -- its energy stays in the brass either way
+                rmax = 1.2f * L.R * __fdividef(1.0f, brass.rho);
+                const float dpl = fminf(L.p[2] - B.ap_tup, B.ap_tdn - L.p[2]);
+                if (rmax < dpl) {
+                    const float fx = (L.p[0] - B.ras_lo[0]) * B.ras_inv[0];
+                    const float fy = (L.p[1] - B.ras_lo[1]) * B.ras_inv[1];
+                    if (!(fx >= 0.0f && fx < (float)kRaster && fy >= 0.0f && fy < (float)kRaster)) {
+                        absorb = true;              // beyond the raster: farther than half the thickness
+                    } else {
+                        const float lb = __ldg(P.raster_lb + B.ras_off + (int)fy * kRaster + (int)fx);
+                        if (rmax < lb) absorb = true;
+                        else if (rmax < lb + B.ras_diag) need_dist = true;
+                    }
+                }
+            }
+        }
+        // ---- exact wall hit and wall distance (warp-cooperative) ----
+        const float sw = coop_first_wall_hit(need_hit, L.p[0], L.p[1], L.d[0], L.d[1], poly, q_off, q_n, lane);
+        const float dw = coop_wall_distance(need_dist, L.p[0], L.p[1], poly, q_off, q_n, lane);
+        if (alive) {
+            const DevItem& I = P.items[L.item];
+            const DevBeam& B = beams[__ldg(&I.beam)];
+            if (ap_pending) {
                 if (open) {
                     // opening: keep velocity and direction up to a wall or the exit
-                    const float sw = first_wall_hit(poly + B.poly_off, B.nvert, L.p[0], L.p[1], L.d[0], L.d[1]);
                     if (sw < s_geom) {
 #pragma unroll
                         for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sw, L.d[k], L.p[k]);
@@ -578,16 +654,8 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                         if (down) advance = true; else fate = kLeak;
                     }
                 } else {
-                    // brass: a proton whose longest possible remaining path (1.2 x its
-                    // residual CSDA range) cannot reach the opening or a face of the
-                    // block is absorbed now -- its energy stays in the brass either way
-                    bool absorb = false;
-                    if (P.range_rejection && !L.forced) {
-                        const float rmax = 1.2f * L.R * __fdividef(1.0f, brass.rho);
-                        const float dpl = fminf(L.p[2] - B.ap_tup, B.ap_tdn - L.p[2]);
-                        if (rmax < dpl) absorb = beyond_wall(B, poly, P.raster_lb, L.p[0], L.p[1], rmax);
-                    }
                     L.forced = 0;
+                    if (need_dist) absorb = rmax < dw;
                     if (absorb) {
                         acc_ap += __float2ull_rn(L.E * P.fscale);
                         L.E = 0.0f;
