@@ -125,6 +125,12 @@ def lib():
             L.orc_gamma_pass_rate.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                               C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int64)]
             L.orc_gamma_pass_rate.restype = C.c_double
+            L.orc_nearest_edge.argtypes = [dp, C.c_int, C.c_double, C.c_double, dp]
+            L.orc_surrogate_features.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double, dp, C.c_double,
+                                                 dp, dp]
+            L.orc_surrogate_tracks.argtypes = [C.POINTER(_Beam), C.c_void_p, C.c_int, C.c_int64, C.POINTER(_Opts),
+                                               dp, C.c_void_p, dp, C.c_void_p, C.c_void_p, C.c_int]
+            L.orc_surrogate_tracks.restype = C.c_int
             L.orc_init_tables()
             _lib = L
     return _lib
@@ -363,3 +369,41 @@ def step_sample(table, kappa, rho, za, x0, e, s_geom=float("inf"), mcs=True, str
     v = list(o)
     return {"s": v[0], "dE": v[1], "limiter": int(v[2]), "killed": int(v[3]), "E": v[4],
             "d": np.array(v[5:8]), "disp": np.array(v[8:11])}
+
+
+# ------------------------------------------------------------ learned surrogate
+def nearest_edge(poly: np.ndarray, x: float, y: float):
+    """(distance, nearest x, nearest y, curvature there) of the polygon boundary."""
+    p = np.ascontiguousarray(poly, dtype=np.float64)
+    out = np.zeros(4)
+    lib().orc_nearest_edge(_dp(p), len(p), float(x), float(y), _dp(out))
+    return tuple(out.tolist())
+
+
+def surrogate_features(poly: np.ndarray, thickness: float, x: float, y: float, d, E: float):
+    """Six surrogate inputs and the edge frame (n_x, n_y, u_n, u_t) of a proton
+    on the block's entrance plane."""
+    p = np.ascontiguousarray(poly, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    f, fr = np.zeros(6), np.zeros(4)
+    lib().orc_surrogate_features(_dp(p), len(p), float(thickness), float(x), float(y), _dp(dd), float(E),
+                                 _dp(f), _dp(fr))
+    return f, fr
+
+
+def surrogate_tracks(beams, n_tracks: int, opts, nthreads: int = 0):
+    """Training tracks of the plain aperture transport, n_tracks per geometry
+    (beams: aperture-only beams).  Returns dict of feat (N, 6), label (N,),
+    target (N, 5), fate (N,) (-1: left through the exit plane) and flags (N,)."""
+    L = lib()
+    arr, xy = _beams(beams)
+    op = _Opts(int(opts.seed), int(opts.mcs), int(opts.straggling), int(opts.nuclear), int(opts.frac_bits),
+               int(getattr(opts, "range_rejection", True)))
+    n = len(beams) * int(n_tracks)
+    feat, target = np.zeros((n, 6)), np.zeros((n, 5))
+    label, fate, flags = (np.zeros(n, dtype=np.int32) for _ in range(3))
+    rc = L.orc_surrogate_tracks(arr, xy.ctypes.data, len(beams), int(n_tracks), C.byref(op), _dp(feat),
+                                label.ctypes.data, _dp(target), fate.ctypes.data, flags.ctypes.data, int(nthreads))
+    if rc != 0:
+        raise RuntimeError("oracle surrogate_tracks failed")
+    return {"feat": feat, "label": label, "target": target, "fate": fate, "flags": flags}

@@ -25,7 +25,7 @@
  * The physics of a condensed-history step (Bethe-Bloch tables, Highland
  * scattering, Bohr straggling, 1.2 %/cm nuclear removal, 1 mm / 1 %-energy
  * step rule) is the reading of the engine's physics that this project uses;
- * every such reading is listed in the design doc.
+ * each reading is stated at the function that implements it.
  *
  * Functions without an independent pin say so in their comment
  * ("parity unpinned").
@@ -525,6 +525,84 @@ static void bev_to_patient(const orc_beam* bm, const orc_scen* sc, const double 
     for (int k = 0; k < 3; ++k) out[k] = bm->iso[k] + sc->shift[k] + pb[0] * u[k] + pb[1] * v[k] + pb[2] * w[k];
 }
 
+/* Aperture block (paper Sec. 2.B) from the particle's state upstream of
+ * it: a straight drift to the entrance plane, then at every step the
+ * crossing-number test.  In the opening the particle keeps its velocity and
+ * direction up to a wall or the exit plane; a wall hit forces the next step
+ * into brass.  In brass it takes a condensed-history step with brass
+ * physics.  Returns 0 when it leaves through the exit plane, else FATE_AP
+ * (absorbed: stopped, nuclear removal or range rejection), FATE_LEAK (left
+ * upstream) or FATE_ERR (iteration cap). */
+static int aperture_block(const orc_beam* bm, const double* poly, orc_particle* pt, const orc_opts* op,
+                          orc_stream* st, orc_record* rec, double* tl, long* iter)
+{
+    double tdn = -bm->ap_down_to_iso, tup = tdn - bm->ap_thickness;
+    if (pt->d[2] <= 0.0) return FATE_LEAK;
+    double sdr = (tup - pt->p[2]) / pt->d[2];
+    for (int k = 0; k < 3; ++k) pt->p[k] += sdr * pt->d[k];
+    rec->track += sdr;
+    orc_medium med = {ORC_BRASS, ORC_MAT[ORC_BRASS].rho, ORC_MAT[ORC_BRASS].rho, ORC_MAT[ORC_BRASS].za, ORC_MAT[ORC_BRASS].X0};
+    orc_step so;
+    int forced_brass = 0;
+    pt->R = orc_range(ORC_BRASS, pt->E);
+    for (;;) {
+        if (++*iter > ORC_MAX_ITER) return FATE_ERR;
+        double sg = INFINITY;
+        int down = 1;
+        if (pt->d[2] > 0.0) sg = (tdn - pt->p[2]) / pt->d[2];
+        else if (pt->d[2] < 0.0) { sg = (tup - pt->p[2]) / pt->d[2]; down = 0; }
+        if (sg < 0.0) sg = 0.0;   /* scattering offsets can leave it past the plane */
+        if (orc_wall_distance(poly, bm->nvert, pt->p[0], pt->p[1]) < ORC_TIE_MM) rec->flags |= 1;
+        int in_open = !forced_brass && orc_point_in_polygon(poly, bm->nvert, pt->p[0], pt->p[1]);
+        if (in_open) {
+            /* opening: keep velocity and direction up to a wall or the exit */
+            double sw = orc_first_wall_hit(poly, bm->nvert, pt->p[0], pt->p[1], pt->d[0], pt->d[1]);
+            if (sw < sg) {
+                for (int k = 0; k < 3; ++k) pt->p[k] += sw * pt->d[k];
+                rec->track += sw;
+                forced_brass = 1;
+                continue;
+            }
+            if (!isfinite(sg)) return FATE_ERR;
+            for (int k = 0; k < 3; ++k) pt->p[k] += sg * pt->d[k];
+            rec->track += sg;
+            return down ? 0 : FATE_LEAK;
+        }
+        /* brass: a proton whose longest possible remaining path (1.2 x
+         * its residual CSDA range; range straggling is ~1.2 %) cannot
+         * reach the opening or either face of the block is absorbed now:
+         * its energy stays in the brass either way */
+        if (op->range_rejection) {
+            double rmax = 1.2 * pt->R / ORC_MAT[ORC_BRASS].rho;
+            double dlim = pt->p[2] - tup;
+            if (tdn - pt->p[2] < dlim) dlim = tdn - pt->p[2];
+            if (rmax < dlim + ORC_TIE_MM) {
+                double dw = orc_wall_distance(poly, bm->nvert, pt->p[0], pt->p[1]);
+                if (dw < dlim) dlim = dw;
+                if (fabs(rmax - dlim) < ORC_TIE_MM) rec->flags |= 16;
+                if (rmax < dlim) {
+                    tl[4] += pt->E;
+                    pt->E = 0.0;
+                    return FATE_AP;
+                }
+            }
+        }
+        /* brass: condensed-history step with brass physics */
+        forced_brass = 0;
+        ch_step(&med, pt, sg, op, st, &so);
+        rec->track += so.s;
+        tl[4] += so.dE;
+        tl[7] += 1.0;
+        rec->steps += 1;
+        if (so.killed) {
+            if (so.killed == 2) tl[5] += so.dE;
+            return FATE_AP;
+        }
+        for (int k = 0; k < 3; ++k) pt->p[k] += so.disp[k];
+        if (so.limiter == LIM_GEOM) return down ? 0 : FATE_LEAK;
+    }
+}
+
 static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_index, int64_t h,
                               orc_record* rec, double* tl)
 {
@@ -617,77 +695,10 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
 
     /* ---- aperture block (paper Sec. 2.B) ---- */
     if (bm->ap_present) {
-        const double* poly = pb->poly_xy + 2 * (int64_t)bm->poly_offset;
-        double tdn = -bm->ap_down_to_iso, tup = tdn - bm->ap_thickness;
-        if (pt.d[2] <= 0.0) goto leak;
-        double sdr = (tup - pt.p[2]) / pt.d[2];
-        for (int k = 0; k < 3; ++k) pt.p[k] += sdr * pt.d[k];
-        rec->track += sdr;
-        orc_medium med = {ORC_BRASS, ORC_MAT[ORC_BRASS].rho, ORC_MAT[ORC_BRASS].rho, ORC_MAT[ORC_BRASS].za, ORC_MAT[ORC_BRASS].X0};
-        int forced_brass = 0;
-        pt.R = orc_range(ORC_BRASS, pt.E);
-        for (;;) {
-            if (++iter > ORC_MAX_ITER) goto fail;
-            double sg = INFINITY;
-            int down = 1;
-            if (pt.d[2] > 0.0) sg = (tdn - pt.p[2]) / pt.d[2];
-            else if (pt.d[2] < 0.0) { sg = (tup - pt.p[2]) / pt.d[2]; down = 0; }
-            if (sg < 0.0) sg = 0.0;   /* scattering offsets can leave it past the plane */
-            if (orc_wall_distance(poly, bm->nvert, pt.p[0], pt.p[1]) < ORC_TIE_MM) rec->flags |= 1;
-            int in_open = !forced_brass && orc_point_in_polygon(poly, bm->nvert, pt.p[0], pt.p[1]);
-            if (in_open) {
-                /* opening: keep velocity and direction up to a wall or the exit */
-                double sw = orc_first_wall_hit(poly, bm->nvert, pt.p[0], pt.p[1], pt.d[0], pt.d[1]);
-                if (sw < sg) {
-                    for (int k = 0; k < 3; ++k) pt.p[k] += sw * pt.d[k];
-                    rec->track += sw;
-                    forced_brass = 1;
-                    continue;
-                }
-                if (!isfinite(sg)) goto fail;
-                for (int k = 0; k < 3; ++k) pt.p[k] += sg * pt.d[k];
-                rec->track += sg;
-                if (!down) goto leak;
-                break;
-            }
-            /* brass: a proton whose longest possible remaining path (1.2 x
-             * its residual CSDA range; range straggling is ~1.2 %) cannot
-             * reach the opening or either face of the block is absorbed now:
-             * its energy stays in the brass either way */
-            if (op->range_rejection) {
-                double rmax = 1.2 * pt.R / ORC_MAT[ORC_BRASS].rho;
-                double dlim = pt.p[2] - tup;
-                if (tdn - pt.p[2] < dlim) dlim = tdn - pt.p[2];
-                if (rmax < dlim + ORC_TIE_MM) {
-                    double dw = orc_wall_distance(poly, bm->nvert, pt.p[0], pt.p[1]);
-                    if (dw < dlim) dlim = dw;
-                    if (fabs(rmax - dlim) < ORC_TIE_MM) rec->flags |= 16;
-                    if (rmax < dlim) {
-                        tl[4] += pt.E;
-                        pt.E = 0.0;
-                        rec->fate = FATE_AP;
-                        goto done;
-                    }
-                }
-            }
-            /* brass: condensed-history step with brass physics */
-            forced_brass = 0;
-            ch_step(&med, &pt, sg, op, &st, &so);
-            rec->track += so.s;
-            tl[4] += so.dE;
-            tl[7] += 1.0;
-            rec->steps += 1;
-            if (so.killed) {
-                if (so.killed == 2) tl[5] += so.dE;
-                rec->fate = FATE_AP;
-                goto done;
-            }
-            for (int k = 0; k < 3; ++k) pt.p[k] += so.disp[k];
-            if (so.limiter == LIM_GEOM) {
-                if (!down) goto leak;
-                break;
-            }
-        }
+        int r = aperture_block(bm, pb->poly_xy + 2 * (int64_t)bm->poly_offset, &pt, op, &st, rec, tl, &iter);
+        if (r == FATE_LEAK) goto leak;
+        if (r == FATE_ERR) goto fail;
+        if (r == FATE_AP) { rec->fate = FATE_AP; goto done; }
     }
 
     /* ---- patient / phantom grid ---- */
@@ -866,6 +877,194 @@ int orc_run(const orc_grid* ct, const int16_t* hu, const orc_curve* curve, const
         for (int i = 0; i < ORC_NTALLY; ++i) tally[i] += tl[i];
     }
     free(off);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Learned aperture surrogate: geometry features and training tracks.  */
+/* ------------------------------------------------------------------ */
+/* The surrogate is not part of the paper: it replaces condensed-history
+ * stepping inside the brass block (Sec. 2.B) by one draw from a learned
+ * distribution.  Its inputs, outputs and training tracks are defined here
+ * from the plain aperture transport above; parity of the learned part is
+ * pinned by that plain path (its dose), not by the paper. */
+#define SUR_DCAP 12.0        /* mm: edge distance beyond which it is clipped     */
+#define SUR_E_LO 70.0        /* MeV: training energies U(E_LO, E_HI)              */
+#define SUR_E_HI 230.0
+#define SUR_ANG_SIGMA 0.04   /* incidence direction cosines N(0, s^2) ...         */
+#define SUR_ANG_MAX 0.12     /* ... clamped to +-ANG_MAX                           */
+#define SUR_DIR_SCALE 0.05   /* exit direction change per target unit              */
+#define SUR_SLOT_ENTRY 5u    /* Philox slot of the incidence angles                */
+
+/* Signed curvature (1/mm) of polygon vertex i: turning angle over half the
+ * two adjacent edge lengths, positive where the opening is locally convex. */
+static double vertex_curvature(const double* poly, int n, int i, double orient)
+{
+    int a = (i + n - 1) % n, b = (i + 1) % n;
+    double e0x = poly[2 * i] - poly[2 * a], e0y = poly[2 * i + 1] - poly[2 * a + 1];
+    double e1x = poly[2 * b] - poly[2 * i], e1y = poly[2 * b + 1] - poly[2 * i + 1];
+    double turn = atan2(e0x * e1y - e0y * e1x, e0x * e1x + e0y * e1y);
+    double len = 0.5 * (sqrt(e0x * e0x + e0y * e0y) + sqrt(e1x * e1x + e1y * e1y));
+    return orient * turn / len;
+}
+
+/* Nearest point of the polygon boundary to (x, y).  out = {distance,
+ * nearest x, nearest y, curvature there}; the curvature is interpolated
+ * linearly along the nearest edge between its vertices' curvatures, so it
+ * does not depend on which of two equidistant edges is taken. */
+void orc_nearest_edge(const double* poly, int n, double x, double y, double out[4])
+{
+    double area2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int j = (i + 1) % n;
+        area2 += poly[2 * i] * poly[2 * j + 1] - poly[2 * j] * poly[2 * i + 1];
+    }
+    double orient = area2 >= 0.0 ? 1.0 : -1.0;
+    double best = INFINITY, bx = 0.0, by = 0.0;
+    int bi = 0;
+    double bt = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int j = (i + 1) % n;
+        double ax = poly[2 * i], ay = poly[2 * i + 1];
+        double ex = poly[2 * j] - ax, ey = poly[2 * j + 1] - ay;
+        double t = ((x - ax) * ex + (y - ay) * ey) / (ex * ex + ey * ey);
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+        double qx = ax + t * ex, qy = ay + t * ey;
+        double d = sqrt((qx - x) * (qx - x) + (qy - y) * (qy - y));
+        if (d < best) { best = d; bx = qx; by = qy; bi = i; bt = t; }
+    }
+    double k0 = vertex_curvature(poly, n, bi, orient);
+    double k1 = vertex_curvature(poly, n, (bi + 1) % n, orient);
+    out[0] = best;
+    out[1] = bx;
+    out[2] = by;
+    out[3] = (1.0 - bt) * k0 + bt * k1;
+}
+
+/* Six surrogate inputs of a proton at (x, y) on the entrance plane of the
+ * block with BEV direction d and energy E.  frame = {n_x, n_y, u_n, u_t}:
+ * n is the unit vector from the nearest boundary point to the proton (into
+ * the brass), t = (-n_y, n_x), u_n and u_t the direction's components. */
+void orc_surrogate_features(const double* poly, int n, double thickness, double x, double y,
+                            const double d[3], double E, double feat[6], double frame[4])
+{
+    double ne[4];
+    orc_nearest_edge(poly, n, x, y, ne);
+    double nx = (x - ne[1]) / ne[0], ny = (y - ne[2]) / ne[0];
+    double un = d[0] * nx + d[1] * ny, ut = -d[0] * ny + d[1] * nx;
+    double rmm = orc_range(ORC_BRASS, E) / ORC_MAT[ORC_BRASS].rho;
+    double dc = ne[0] < SUR_DCAP ? ne[0] : SUR_DCAP;
+    feat[0] = dc / (0.5 * SUR_DCAP) - 1.0;
+    feat[1] = (E - 0.5 * (SUR_E_LO + SUR_E_HI)) / (0.5 * (SUR_E_HI - SUR_E_LO));
+    feat[2] = un / SUR_ANG_SIGMA;
+    feat[3] = ut / SUR_ANG_SIGMA;
+    feat[4] = 8.0 * ne[3] - 1.0;
+    feat[5] = rmm / thickness - 1.0;
+    frame[0] = nx; frame[1] = ny; frame[2] = un; frame[3] = ut;
+}
+
+/* Training tracks: n_tracks histories per geometry g (beam g: aperture
+ * only), each started on the block's entrance plane near the opening and
+ * carried through the block by the plain transport.  Entry of history h of
+ * geometry g, key (seed low, g ^ seed high):
+ *   slot 0, step 0 -> u0..u2: E = E_LO + (E_HI - E_LO) u0; phi = 2 pi u1;
+ *     d = d_hi u2 with d_hi = min(DCAP, 1.2 R_brass(E)) when 1.2 R_brass(E)
+ *     is below the block thickness, else DCAP; the proton starts at radius
+ *     r_circ + d, angle phi, where r_circ is the largest vertex radius;
+ *   slot 5, step 0 -> two normals z0, z1 (first Box-Muller pair):
+ *     theta_n, theta_t = clamp(ANG_SIGMA z, +-ANG_MAX) along the radial and
+ *     tangential unit vectors at phi; d_z = sqrt(1 - theta_n^2 - theta_t^2);
+ *   slot 3, step 0 -> nuclear mean-free-path count, as for a source proton.
+ * Outputs per track (index g * n_tracks + h): feat[6] (orc_surrogate_features
+ * at the entry), label (1: left through the exit plane), target[5] for
+ * label 1 (else zeros):
+ *   y0 = 5 (E_in - E_out) / E_in,
+ *   y1 = (exit - entry) . n - T u_n / w_in,  y2 = (exit - entry) . t - T u_t / w_in,
+ *   y3 = (d_out . n - u_n) / DIR_SCALE,      y4 = (d_out . t - u_t) / DIR_SCALE,
+ * and the plain transport's fate and ill-conditioning flags. */
+int orc_surrogate_tracks(const orc_beam* beams, const double* poly_xy, int n_geom, int64_t n_tracks,
+                         const orc_opts* op, double* feat, int32_t* label, double* target,
+                         int32_t* fate, int32_t* flags, int nthreads)
+{
+    orc_init_tables();
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int64_t total = (int64_t)n_geom * n_tracks;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t gi = 0; gi < total; ++gi) {
+        int g = (int)(gi / n_tracks);
+        int64_t h = gi % n_tracks;
+        const orc_beam* bm = &beams[g];
+        const double* poly = poly_xy + 2 * (int64_t)bm->poly_offset;
+        double T = bm->ap_thickness;
+        double tup = -bm->ap_down_to_iso - T;
+        orc_stream st;
+        st.key[0] = (uint32_t)op->seed;
+        st.key[1] = (uint32_t)(op->seed >> 32) ^ (uint32_t)g;
+        st.hist = (uint32_t)h;
+        double u[4], z[4];
+        stream_block(&st, 0u, 0u, u);
+        double E = SUR_E_LO + (SUR_E_HI - SUR_E_LO) * u[0];
+        double phi = 2.0 * M_PI * u[1];
+        double r12 = 1.2 * orc_range(ORC_BRASS, E) / ORC_MAT[ORC_BRASS].rho;
+        double dhi = (r12 < T) ? (r12 < SUR_DCAP ? r12 : SUR_DCAP) : SUR_DCAP;
+        double dd = dhi * u[2];
+        double rc = 0.0;
+        for (int i = 0; i < bm->nvert; ++i) {
+            double rr = sqrt(poly[2 * i] * poly[2 * i] + poly[2 * i + 1] * poly[2 * i + 1]);
+            if (rr > rc) rc = rr;
+        }
+        double cph = cos(phi), sph = sin(phi);
+        stream_normals4(&st, 0u, SUR_SLOT_ENTRY, z);
+        double tn = SUR_ANG_SIGMA * z[0], tt = SUR_ANG_SIGMA * z[1];
+        if (tn > SUR_ANG_MAX) tn = SUR_ANG_MAX;
+        if (tn < -SUR_ANG_MAX) tn = -SUR_ANG_MAX;
+        if (tt > SUR_ANG_MAX) tt = SUR_ANG_MAX;
+        if (tt < -SUR_ANG_MAX) tt = -SUR_ANG_MAX;
+        orc_particle pt;
+        memset(&pt, 0, sizeof pt);
+        pt.p[0] = (rc + dd) * cph;
+        pt.p[1] = (rc + dd) * sph;
+        pt.p[2] = tup;
+        pt.d[0] = tn * cph - tt * sph;
+        pt.d[1] = tn * sph + tt * cph;
+        pt.d[2] = sqrt(1.0 - tn * tn - tt * tt);
+        pt.E = E;
+        if (op->nuclear) {
+            double un[4];
+            stream_block(&st, 0u, 3u, un);
+            pt.nlam = -log(un[0]);
+        } else {
+            pt.nlam = INFINITY;
+        }
+        double* f = feat + 6 * gi;
+        double fr[4];
+        orc_surrogate_features(poly, bm->nvert, T, pt.p[0], pt.p[1], pt.d, E, f, fr);
+        double x0 = pt.p[0], y0 = pt.p[1], w0 = pt.d[2];
+        orc_record rec;
+        memset(&rec, 0, sizeof rec);
+        double tl[ORC_NTALLY] = {0};
+        long iter = 0;
+        int r = aperture_block(bm, poly, &pt, op, &st, &rec, tl, &iter);
+        double* y = target + 5 * gi;
+        for (int k = 0; k < 5; ++k) y[k] = 0.0;
+        label[gi] = r == 0;
+        fate[gi] = r == 0 ? -1 : r;
+        flags[gi] = rec.flags;
+        if (r == 0) {
+            double nx = fr[0], ny = fr[1], un = fr[2], ut = fr[3];
+            double dx = pt.p[0] - x0, dy = pt.p[1] - y0;
+            y[0] = 5.0 * (E - pt.E) / E;
+            y[1] = dx * nx + dy * ny - T * un / w0;
+            y[2] = -dx * ny + dy * nx - T * ut / w0;
+            y[3] = (pt.d[0] * nx + pt.d[1] * ny - un) / SUR_DIR_SCALE;
+            y[4] = (-pt.d[0] * ny + pt.d[1] * nx - ut) / SUR_DIR_SCALE;
+        }
+    }
     return 0;
 }
 

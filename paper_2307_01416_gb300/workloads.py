@@ -92,6 +92,7 @@ class Options:
     nuclear: bool = True
     frac_bits: int = 24
     range_rejection: bool = True   # absorb brass protons that cannot leave the block
+    surrogate: bool = False        # learned aperture surrogate in place of in-brass stepping
 
     @property
     def deterministic(self) -> bool:
@@ -375,3 +376,25 @@ def head_plan(volume_cc: float = 8.4, ct_seed: int = 1234, target_seed: int = 12
                 rows.append((bi, float(e), float(x), float(y), sig, 2.0, int(n), 1.0))
     pb = Problem(ct=g, hu=hu, curve=curve, scoring=sg, beams=beams)
     return pb, make_spots(rows), center, r_t
+
+
+# --------------------------------------------------------------------------
+# Training geometries of the learned aperture surrogate.
+# --------------------------------------------------------------------------
+SURROGATE_RADII = (4.0, 6.0, 9.0, 14.0, 22.0, 35.0, 60.0, 150.0)
+SURROGATE_SEED = 4321
+
+
+def surrogate_training_beams(radii=SURROGATE_RADII, n_vertices: int = 128, thickness: float = 30.0,
+                             down_to_iso: float = 150.0) -> List[Beam]:
+    """Aperture-only beams whose openings are regular n-gons of the given
+    circumradii, centred on the beam axis: the edge curvatures (1/r) and edge
+    orientations (all angles) the surrogate is trained over.  30 mm brass at
+    150 mm from the isocentre (Sec. 2.B)."""
+    beams = []
+    for r in radii:
+        beams.append(Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0),
+                          source_to_iso=down_to_iso + thickness + 10.0, rs_present=False,
+                          ap_present=True, ap_thickness=thickness, ap_down_to_iso=down_to_iso,
+                          polygon=regular_polygon(float(r), n_vertices)))
+    return beams
