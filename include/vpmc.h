@@ -120,6 +120,12 @@ typedef struct {
                                path (1.2 x residual CSDA range) cannot reach the opening or
                                a face of the block is absorbed at once; the patient sees the
                                same histories either way                                 */
+    int surrogate;          /* 0 (default): plain aperture transport.  1: each proton that
+                               enters the brass within the learned surrogate's training
+                               domain takes one network draw for its state on the block's
+                               exit plane instead of condensed-history stepping (needs
+                               vpmc_surrogate_set_weights or _train first); the others
+                               use the plain path                                         */
 } vpmc_opts;
 
 /* Totals of one call.  Energies in MeV (fixed-point sums, unweighted). */
@@ -205,6 +211,94 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* ctx, const vpmc_spot* spots, int n_s
 
 /* Free the device buffers of n CSR matrices and zero the structs. */
 vpmc_status vpmc_free_csr(vpmc_csr* csr, int n);
+
+/* ------------------------------------------------------------------------
+ * Learned aperture surrogate.  The paper has no counterpart: its aperture
+ * module (Sec. 2.B) reads the brass block's effect from pre-computed brass
+ * transport.  Here a small network, trained on tracks of this library's own
+ * plain aperture transport, draws the state of a proton that enters the
+ * brass near the opening on the block's exit plane in one step.
+ *
+ * Network: 6 inputs -> 128 -> 128 (ReLU) -> 45 outputs.  Outputs: a
+ * transmission logit, then a 4-component diagonal Gaussian mixture over five
+ * exit quantities (mixture logits [4], means [4 x 5], log widths [4 x 5]).
+ * Weights and activations are BF16, sums FP32, on the tensor cores.
+ * Parameters: VPMC_SUR_NPARAMS FP32 values, row-major (outputs x inputs):
+ * W1 [128 x 6], b1 [128], W2 [128 x 128], b2 [128], W3 [45 x 128], b3 [45].
+ *
+ * Inputs of a proton at (x, y) on the block's entrance plane, with direction d
+ * and energy E.  n is the unit vector from the nearest boundary point of the
+ * opening to the proton; t = (-n_y, n_x).
+ *   x0 = min(dist, 12 mm) / 6 mm - 1
+ *   x1 = (E - 150 MeV) / 80 MeV
+ *   x2 = (d . n) / 0.04,  x3 = (d . t) / 0.04
+ *   x4 = 8 mm x (boundary curvature there) - 1
+ *   x5 = (brass CSDA range of E) / (block thickness) - 1
+ * Targets of a transmitted proton:
+ *   y0 = 5 (E_in - E_out) / E_in
+ *   y1 = (exit - entry) . n - T (d_in . n) / d_in,z
+ *   y2 = (exit - entry) . t - T (d_in . t) / d_in,z
+ *   y3 = (d_out - d_in) . n / 0.05,  y4 = (d_out - d_in) . t / 0.05
+ * Training domain: E in [70, 230] MeV, |d . n| and |d . t| <= 0.12,
+ * curvature in [-0.001, 0.26] / mm, block thickness 30 mm.  With
+ * opts->surrogate = 1, a brass entry outside this domain takes the plain
+ * path.  A brass entry whose 1.2 x CSDA range is below both its edge distance
+ * and the thickness is absorbed without a draw.
+ * ------------------------------------------------------------------------ */
+#define VPMC_SUR_NPARAMS 23213
+
+/* Load the network's parameters (host array of VPMC_SUR_NPARAMS floats,
+ * copied) and reset the Adam state.  Synchronous. */
+vpmc_status vpmc_surrogate_set_weights(vpmc_ctx* ctx, const float* params);
+
+/* Fresh parameters: He-normal weights (the output layer scaled by 0.1 / sqrt 2),
+ * zero biases, from a seeded generator on the host.  Resets the Adam state.
+ * Synchronous. */
+vpmc_status vpmc_surrogate_init(vpmc_ctx* ctx, uint64_t seed);
+
+/* Copy the current parameters to a host array of VPMC_SUR_NPARAMS floats. */
+vpmc_status vpmc_surrogate_get_weights(vpmc_ctx* ctx, float* params);
+
+/* Training or evaluation tracks.  Each beam_ids[g] must be set, with an
+ * aperture and no range shifter.  tracks_per_beam histories per beam start on
+ * its entrance plane near the opening.  Track h of list entry g is global
+ * index i = g * tracks_per_beam + h, with Philox key (seed low word,
+ * g ^ seed high word).  Its start, from counter (h, 0, slot, 0):
+ *   slot 0: E = 70 + 160 u0 MeV, angle phi = 2 pi u1, edge distance d = d_hi u2,
+ *           where d_hi = min(12 mm, 1.2 R) if 1.2 x brass CSDA range R is
+ *           below the thickness, else 12 mm; the proton starts at radius
+ *           r_c + d at angle phi, r_c the largest vertex radius;
+ *   slot 5: incidence direction cosines along the radial and tangential
+ *           directions, 0.04 x (first Box-Muller pair), clamped to +-0.12;
+ *   slot 3: the nuclear free path.
+ * Outputs are caller-owned device arrays of n = n_beams x tracks_per_beam
+ * rows: feat_dev [n x 6] (inputs), target_dev [n x 5] (targets, zero unless
+ * transmitted), label_dev [n] (1: left through the exit plane).
+ * use_surrogate = 0: the plain aperture transport with opts' physics.
+ * use_surrogate = 1: one network draw per track (Philox slots 4 and 5 at the
+ * entry step); the targets are the drawn ones.  Synchronous. */
+vpmc_status vpmc_surrogate_tracks(vpmc_ctx* ctx, const int* beam_ids, int n_beams, int64_t tracks_per_beam,
+                                  const vpmc_opts* opts, int use_surrogate, float* feat_dev, float* target_dev,
+                                  int32_t* label_dev);
+
+/* Network outputs for n input rows.  feat_dev: [n x 6] device.
+ * z_dev: [n x 45] device, caller-owned.  Synchronous. */
+vpmc_status vpmc_surrogate_forward(vpmc_ctx* ctx, const float* feat_dev, int64_t n, float* z_dev);
+
+/* Mean loss over n tracks at the current parameters, and its gradient.
+ * Loss of one track: softplus(z0) - label z0, plus (label = 1 only) the
+ * mixture's negative log-likelihood of its targets.  grad_dev: device array
+ * of VPMC_SUR_NPARAMS floats, parameter order.  Synchronous. */
+vpmc_status vpmc_surrogate_gradient(vpmc_ctx* ctx, const float* feat_dev, const float* target_dev,
+                                    const int32_t* label_dev, int64_t n, float* grad_dev, double* loss);
+
+/* Adam training (beta 0.9 / 0.999, eps 1e-8) over n tracks: minibatches of
+ * `batch` rows, `epochs` passes, each in its own batch order.  Learning rate
+ * follows a cosine from lr to lr_min over all steps.  epoch_loss: optional
+ * host array [epochs], the mean loss of each pass.  Synchronous. */
+vpmc_status vpmc_surrogate_train(vpmc_ctx* ctx, const float* feat_dev, const float* target_dev,
+                                 const int32_t* label_dev, int64_t n, int batch, int epochs, float lr, float lr_min,
+                                 float* epoch_loss);
 
 /* Destroy a context and free its device memory. */
 void vpmc_destroy(vpmc_ctx* ctx);

@@ -1,6 +1,7 @@
 // C ABI of the transport library: context, fields, dose and influence matrices.
 #include <algorithm>
 #include <cmath>
+#include <numeric>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -101,8 +102,6 @@ vpmc_status grow_ovf(vpmc_ctx* c, long long n)
 {
     if (n <= c->ovf_cap) return VPMC_OK;
     cudaFree(c->d_ovf);
-    cudaFree(c->d_phase);
-    cudaFree(c->d_phase_count);
     c->d_ovf = nullptr;
     c->ovf_cap = 0;
     CUDA_TRY(dev_alloc(&c->d_ovf, (size_t)n));
@@ -135,6 +134,7 @@ vpmc_status grow_scratch(vpmc_ctx* c, size_t n)
 vpmc_status upload_beams(vpmc_ctx* c)
 {
     std::vector<float2> poly;
+    std::vector<float> kappa;
     std::vector<unsigned char> ras;
     std::vector<float> ras_lb;
     DevBeam tmp[kMaxBeams];
@@ -144,6 +144,9 @@ vpmc_status upload_beams(vpmc_ctx* c)
         tmp[b].poly_off = (int)poly.size();
         for (size_t i = 0; i + 1 < c->poly[b].size(); i += 2)
             poly.push_back(make_float2((float)c->poly[b][i], (float)c->poly[b][i + 1]));
+        const int nv = (int)(c->poly[b].size() / 2);
+        kappa.resize(poly.size());
+        polygon_curvature(c->poly[b].data(), nv, kappa.data() + (poly.size() - nv));
         tmp[b].ras_off = (int)ras.size();
         ras.insert(ras.end(), c->raster[b].begin(), c->raster[b].end());
         ras_lb.insert(ras_lb.end(), c->raster_lb[b].begin(), c->raster_lb[b].end());
@@ -151,12 +154,17 @@ vpmc_status upload_beams(vpmc_ctx* c)
     if (poly.size() > (size_t)kMaxPolyVerts)
         return fail(VPMC_ERR_ARG, "aperture polygons have %zu vertices in total (max %d)", poly.size(), kMaxPolyVerts);
     cudaFree(c->d_poly);
+    cudaFree(c->d_poly_kappa);
     cudaFree(c->d_raster);
     cudaFree(c->d_raster_lb);
     c->d_poly = nullptr;
+    c->d_poly_kappa = nullptr;
     c->d_raster = nullptr;
     c->d_raster_lb = nullptr;
     CUDA_TRY(dev_alloc(&c->d_poly, std::max<size_t>(poly.size(), 1)));
+    CUDA_TRY(dev_alloc(&c->d_poly_kappa, std::max<size_t>(kappa.size(), 1)));
+    if (!kappa.empty())
+        CUDA_TRY(cudaMemcpy(c->d_poly_kappa, kappa.data(), kappa.size() * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(dev_alloc(&c->d_raster, std::max<size_t>(ras.size(), 1)));
     CUDA_TRY(dev_alloc(&c->d_raster_lb, std::max<size_t>(ras_lb.size(), 1)));
     if (!poly.empty()) CUDA_TRY(cudaMemcpy(c->d_poly, poly.data(), poly.size() * sizeof(float2), cudaMemcpyHostToDevice));
@@ -197,6 +205,7 @@ vpmc_status check_opts(const vpmc_opts* o)
     if (o->chunk < 0 || o->chunk > 4096) return fail(VPMC_ERR_ARG, "chunk %d outside [0, 4096]", o->chunk);
     if (o->history_cap < 0 || (o->history_cap > 0 && !o->history_out))
         return fail(VPMC_ERR_ARG, "history_cap > 0 needs history_out");
+    if (o->surrogate != 0 && o->surrogate != 1) return fail(VPMC_ERR_ARG, "surrogate must be 0 or 1");
     return VPMC_OK;
 }
 
@@ -232,6 +241,8 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     p.phase = c->d_phase;
     p.phase_cap = c->phase_cap;
     p.phase_count = c->d_phase_count;
+    p.poly_kappa = c->d_poly_kappa;
+    p.surrogate = o.surrogate && c->sur_ready ? 1 : 0;
     return p;
 }
 
@@ -245,9 +256,25 @@ vpmc_status reset_counters(vpmc_ctx* c)
 
 constexpr long long kMaxBatch = 1ll << 26;    // histories per devices -> patient hand-off batch
 
-vpmc_status ensure_phase(vpmc_ctx* c, long long total)
+vpmc_status grow_queries(vpmc_ctx* c, long long n)
 {
-    return grow_phase(c, std::max<long long>(std::min(total, kMaxBatch), 1));
+    if (!c->d_sq_count) CUDA_TRY(dev_alloc(&c->d_sq_count, 1));
+    if (n <= c->sq_cap) return VPMC_OK;
+    cudaFree(c->d_sq);
+    c->d_sq = nullptr;
+    c->sq_cap = 0;
+    CUDA_TRY(dev_alloc(&c->d_sq, (size_t)n));
+    c->sq_cap = n;
+    return VPMC_OK;
+}
+
+// Hand-off buffer (and, with the surrogate, the query buffer) for one batch.
+vpmc_status ensure_phase(vpmc_ctx* c, long long total, bool surrogate = false)
+{
+    const long long n = std::max<long long>(std::min(total, kMaxBatch), 1);
+    vpmc_status st = grow_phase(c, n);
+    if (st == VPMC_OK && surrogate) st = grow_queries(c, std::min<long long>(n, c->phase_cap));
+    return st;
 }
 
 // Enqueues the transport of histories [0, total) of p's items: batches of at
@@ -259,12 +286,24 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
     p.phase_count = c->d_phase_count;
     p.aggregate = t.aggregate;
     p.chunk = t.chunk;
+    if (p.surrogate) {
+        if (!c->d_sq || c->sq_cap < c->phase_cap) return fail(VPMC_ERR_STATE, "surrogate query buffer not sized");
+        p.sq = c->d_sq;
+        p.sq_cap = c->sq_cap;
+        p.sq_count = c->d_sq_count;
+    }
     for (long long h0 = 0; h0 < total; h0 += c->phase_cap) {
         p.hist_begin = h0;
         p.total = std::min(total, h0 + c->phase_cap);
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
         CUDA_TRY(cudaMemsetAsync(c->d_phase_count, 0, sizeof(unsigned long long), c->stream));
+        if (p.surrogate) CUDA_TRY(cudaMemsetAsync(c->d_sq_count, 0, sizeof(unsigned long long), c->stream));
         CUDA_TRY(launch_devices(p, c->num_sms, t.dev_block, c->stream));
+        if (p.surrogate) {
+            // brass entries in the surrogate's domain: one network draw each
+            CUDA_TRY(launch_sur_infer(c->sur, p, 2 * c->num_sms, c->stream));
+            c->launches += 1;
+        }
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
         CUDA_TRY(launch_patient(p, c->num_sms, t.block, c->stream));
         c->launches += 2;
@@ -302,6 +341,7 @@ vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc
     p.rec_cap = 0;
     p.hist_begin = 0;
     p.total = sample;
+    p.surrogate = 0;            // timed on the plain beam-line path
     p.chunk = best.chunk;
     p.aggregate = best.aggregate;
     // devices kernel block size (its output is identical for every choice)
@@ -380,6 +420,7 @@ void vpmc_default_opts(vpmc_opts* o)
     o->frac_bits = 24;
     o->aggregate = -1;
     o->range_rejection = 1;
+    o->surrogate = 0;
 }
 
 const char* vpmc_last_error(void) { return g_error.c_str(); }
@@ -532,6 +573,9 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
         build_raster(poly.data(), b->n_vertices, 0.5 * b->ap_thickness_mm + 1.0, ras.data(), ras_lb.data(), d.ras_lo,
                      d.ras_inv, &d.ras_diag);
         d.nvert = b->n_vertices;
+        double rc = 0.0;
+        for (int i = 0; i < b->n_vertices; ++i) rc = std::max(rc, std::hypot(poly[2 * i], poly[2 * i + 1]));
+        d.r_circ = (float)rc;
     }
     if (first_device < 1e300 && !(-b->source_to_iso_mm < first_device))
         return fail(VPMC_ERR_ARG, "source plane must lie upstream of every device");
@@ -570,6 +614,7 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
     if (opts_in) o = *opts_in;
     vpmc_status st = check_opts(&o);
     if (st != VPMC_OK) return st;
+    if (o.surrogate && !c->sur_ready) return fail(VPMC_ERR_STATE, "surrogate requested before its weights were set");
     st = check_spots(c, spots, n_spots);
     if (st != VPMC_OK) return st;
     DevScen sc{{0.0f, 0.0f, 0.0f}, 1.0f};
@@ -629,7 +674,7 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
         p.n_scen = 1;
         p.total = total;
         p.scratch = c->d_acc;
-        st = ensure_phase(c, total);
+        st = ensure_phase(c, total, p.surrogate != 0);
         if (st != VPMC_OK) return st;
         const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
         if (want_tune && !c->tune_dose.valid) {
@@ -664,6 +709,12 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
             stats.launches = c->launches - launches0;
             *stats_out = stats;
             if (status & 1) return fail(VPMC_ERR_TIMEOUT, "%lld histories reached the iteration cap", (long long)stats.errors);
+            if (status & 6) return fail(VPMC_ERR_DEVICE_FLAG, "hand-off or query buffer overflow (status %d)", status);
+            if (o.surrogate) {
+                int ss = 0;
+                CUDA_TRY(cudaMemcpy(&ss, c->sur.status, sizeof ss, cudaMemcpyDeviceToHost));
+                if (ss) return fail(VPMC_ERR_TIMEOUT, "surrogate: a tensor-core wait timed out");
+            }
         } else {
             stats.launches = c->launches - launches0;
             *stats_out = stats;
@@ -753,6 +804,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     if (opts_in) o = *opts_in;
     vpmc_status st = check_opts(&o);
     if (st != VPMC_OK) return st;
+    if (o.surrogate && !c->sur_ready) return fail(VPMC_ERR_STATE, "surrogate requested before its weights were set");
     st = check_spots(c, spots, n_spots);
     if (st != VPMC_OK) return st;
     if (n_spots == 0) return fail(VPMC_ERR_ARG, "no spots");
@@ -906,7 +958,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         IM_TRY(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice));
         IM_TRY(cudaMemcpy(c->d_boxes, boxes.data(), boxes.size() * sizeof(DevBox), cudaMemcpyHostToDevice));
         if (!c->d_ovf) IM_ST(grow_ovf(c, 1ll << 24));
-        IM_ST(ensure_phase(c, total));
+        IM_ST(ensure_phase(c, total, o.surrogate && c->sur_ready));
         TransportParams p = base_params(c, o);
         p.items = c->d_items;
         p.n_items = (int)items.size();
@@ -964,6 +1016,20 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             release();
             vpmc_free_csr(out, n_scen);
             return fail(VPMC_ERR_TIMEOUT, "histories reached the iteration cap");
+        }
+        if (status & 6) {
+            release();
+            vpmc_free_csr(out, n_scen);
+            return fail(VPMC_ERR_DEVICE_FLAG, "hand-off or query buffer overflow (status %d)", status);
+        }
+        if (o.surrogate && c->sur_ready) {
+            int ss = 0;
+            IM_TRY(cudaMemcpy(&ss, c->sur.status, sizeof ss, cudaMemcpyDeviceToHost));
+            if (ss) {
+                release();
+                vpmc_free_csr(out, n_scen);
+                return fail(VPMC_ERR_TIMEOUT, "surrogate: a tensor-core wait timed out");
+            }
         }
         stats.ovf_records += (long long)n_ovf;
         // column maxima over boxes, then bucket the out-of-box records and raise the maxima
@@ -1099,11 +1165,296 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->d_items);
     cudaFree(c->d_boxes);
     cudaFree(c->d_ovf);
+    cudaFree(c->d_phase);
+    cudaFree(c->d_phase_count);
     cudaFree(c->d_scratch);
+    cudaFree(c->d_poly_kappa);
+    cudaFree(c->d_sq);
+    cudaFree(c->d_sq_count);
+    cudaFree(c->sur.params);
+    cudaFree(c->sur.grad);
+    cudaFree(c->sur.m);
+    cudaFree(c->sur.v);
+    cudaFree(c->sur.img);
+    cudaFree(c->sur.loss);
+    cudaFree(c->sur.status);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned aperture surrogate.
+// ---------------------------------------------------------------------------
+namespace {
+
+vpmc_status ensure_surrogate(vpmc_ctx* c)
+{
+    if (c->sur.params) return VPMC_OK;
+    SurNet& n = c->sur;
+    CUDA_TRY(dev_alloc(&n.params, sur::kNParams));
+    CUDA_TRY(dev_alloc(&n.grad, sur::kNParams));
+    CUDA_TRY(dev_alloc(&n.m, sur::kNParams));
+    CUDA_TRY(dev_alloc(&n.v, sur::kNParams));
+    CUDA_TRY(dev_alloc(&n.img, sur::kImgBytes));
+    CUDA_TRY(dev_alloc(&n.loss, 2));
+    CUDA_TRY(dev_alloc(&n.status, 1));
+    CUDA_TRY(cudaMemset(n.img, 0, sur::kImgBytes));   // padding rows and columns stay zero
+    return VPMC_OK;
+}
+
+vpmc_status reset_optimizer(vpmc_ctx* c)
+{
+    const size_t b = sur::kNParams * sizeof(float);
+    CUDA_TRY(cudaMemsetAsync(c->sur.grad, 0, b, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->sur.m, 0, b, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->sur.v, 0, b, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->sur.status, 0, sizeof(int), c->stream));
+    c->sur_step = 0;
+    return VPMC_OK;
+}
+
+vpmc_status surrogate_status(vpmc_ctx* c)
+{
+    int ss = 0;
+    CUDA_TRY(cudaMemcpy(&ss, c->sur.status, sizeof ss, cudaMemcpyDeviceToHost));
+    if (ss) return fail(VPMC_ERR_TIMEOUT, "surrogate: a tensor-core wait timed out");
+    return VPMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vpmc_status vpmc_surrogate_set_weights(vpmc_ctx* c, const float* params)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!c || !params) return fail(VPMC_ERR_ARG, "null argument");
+    for (int i = 0; i < sur::kNParams; ++i)
+        if (!std::isfinite(params[i])) return fail(VPMC_ERR_ARG, "parameter %d is not finite", i);
+    vpmc_status st = ensure_surrogate(c);
+    if (st != VPMC_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(c->sur.params, params, sur::kNParams * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    st = reset_optimizer(c);
+    if (st != VPMC_OK) return st;
+    CUDA_TRY(launch_sur_pack(c->sur, c->stream));
+    ++c->launches;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->sur_ready = true;
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_surrogate_init(vpmc_ctx* c, uint64_t seed)
+{
+    g_error.clear();
+    if (!c) return fail(VPMC_ERR_ARG, "null context");
+    // He-normal weights (std sqrt(2 / fan_in); the output layer 0.1 sqrt(1 /
+    // fan_in), so the mixture starts near unit widths), zero biases; normals
+    // from splitmix64 uniforms by Box-Muller.
+    std::vector<float> w(sur::kNParams, 0.0f);
+    uint64_t state = seed;
+    auto next_u = [&]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return ((double)(z >> 11) + 0.5) * 0x1p-53;
+    };
+    auto fill = [&](int off, int count, double sd) {
+        for (int i = 0; i < count; i += 2) {
+            const double r = std::sqrt(-2.0 * std::log(next_u())), a = 6.283185307179586 * next_u();
+            w[off + i] = (float)(sd * r * std::cos(a));
+            if (i + 1 < count) w[off + i + 1] = (float)(sd * r * std::sin(a));
+        }
+    };
+    fill(sur::oW1, sur::kH * sur::kIn, std::sqrt(2.0 / sur::kIn));
+    fill(sur::oW2, sur::kH * sur::kH, std::sqrt(2.0 / sur::kH));
+    fill(sur::oW3, sur::kOut * sur::kH, 0.1 * std::sqrt(1.0 / sur::kH));
+    return vpmc_surrogate_set_weights(c, w.data());
+}
+
+vpmc_status vpmc_surrogate_get_weights(vpmc_ctx* c, float* params)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!c || !params) return fail(VPMC_ERR_ARG, "null argument");
+    if (!c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaMemcpy(params, c->sur.params, sur::kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_surrogate_forward(vpmc_ctx* c, const float* feat_dev, int64_t n, float* z_dev)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!c || (n > 0 && (!feat_dev || !z_dev)) || n < 0) return fail(VPMC_ERR_ARG, "bad argument");
+    if (!c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights");
+    CUDA_TRY(launch_sur_forward(c->sur, feat_dev, n, z_dev, 2 * c->num_sms, c->stream));
+    ++c->launches;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return surrogate_status(c);
+}
+
+vpmc_status vpmc_surrogate_gradient(vpmc_ctx* c, const float* feat_dev, const float* target_dev,
+                                    const int32_t* label_dev, int64_t n, float* grad_dev, double* loss)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!c || n <= 0 || !feat_dev || !target_dev || !label_dev || !grad_dev) return fail(VPMC_ERR_ARG, "bad argument");
+    if (!c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights");
+    CUDA_TRY(cudaMemsetAsync(c->sur.grad, 0, sur::kNParams * sizeof(float), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->sur.loss, 0, 2 * sizeof(double), c->stream));
+    CUDA_TRY(launch_sur_train(c->sur, feat_dev, target_dev, label_dev, 0, n, n, (float)(1.0 / (double)n), c->num_sms,
+                              c->stream));
+    ++c->launches;
+    CUDA_TRY(cudaMemcpyAsync(grad_dev, c->sur.grad, sur::kNParams * sizeof(float), cudaMemcpyDeviceToDevice,
+                             c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->sur.grad, 0, sur::kNParams * sizeof(float), c->stream));
+    double h[2] = {0.0, 0.0};
+    CUDA_TRY(cudaMemcpyAsync(h, c->sur.loss, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (loss) *loss = h[0] / (double)n;
+    return surrogate_status(c);
+}
+
+vpmc_status vpmc_surrogate_train(vpmc_ctx* c, const float* feat_dev, const float* target_dev, const int32_t* label_dev,
+                                 int64_t n, int batch, int epochs, float lr, float lr_min, float* epoch_loss)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!c || n <= 0 || !feat_dev || !target_dev || !label_dev) return fail(VPMC_ERR_ARG, "bad argument");
+    if (batch <= 0 || epochs <= 0 || !(lr > 0.0f) || !(lr_min >= 0.0f) || lr_min > lr)
+        return fail(VPMC_ERR_ARG, "batch and epochs must be positive, 0 <= lr_min <= lr, lr > 0");
+    if (!c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights (set them first)");
+    const long long nb = (n + batch - 1) / batch;
+    const long long steps = nb * (long long)epochs;
+    long long t = 0;
+    for (int e = 0; e < epochs; ++e) {
+        CUDA_TRY(cudaMemsetAsync(c->sur.loss, 0, 2 * sizeof(double), c->stream));
+        // batch order of this epoch: an affine permutation j -> (a j + b) mod nb
+        long long a = (2654435761ll + 2ll * e) % nb;
+        if (a == 0) a = 1;
+        while (std::gcd(a, nb) != 1) ++a;
+        const long long b = (40503ll * (e + 1)) % nb;
+        for (long long j = 0; j < nb; ++j, ++t) {
+            const long long bj = (a * j + b) % nb;
+            const long long first = bj * batch;
+            const long long rows = std::min<long long>(batch, n - first);
+            CUDA_TRY(launch_sur_train(c->sur, feat_dev, target_dev, label_dev, first, rows, n,
+                                      (float)(1.0 / (double)rows), c->num_sms, c->stream));
+            ++c->sur_step;
+            const double cosw = 0.5 * (1.0 + std::cos(3.14159265358979323846 * (double)t / (double)steps));
+            const float lr_t = (float)(lr_min + (lr - lr_min) * cosw);
+            CUDA_TRY(launch_sur_adam(c->sur, c->sur_step, lr_t, c->stream));
+            c->launches += 2;
+        }
+        double h[2] = {0.0, 0.0};
+        CUDA_TRY(cudaMemcpyAsync(h, c->sur.loss, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (epoch_loss) epoch_loss[e] = (float)(h[0] / (double)n);
+        vpmc_status st = surrogate_status(c);
+        if (st != VPMC_OK) return st;
+    }
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_surrogate_tracks(vpmc_ctx* c, const int* beam_ids, int n_beams, int64_t tracks_per_beam,
+                                  const vpmc_opts* opts_in, int use_surrogate, float* feat_dev, float* target_dev,
+                                  int32_t* label_dev)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!c || !beam_ids || n_beams <= 0 || n_beams > kMaxBeams || tracks_per_beam <= 0 || !feat_dev || !target_dev ||
+        !label_dev)
+        return fail(VPMC_ERR_ARG, "bad argument");
+    if (tracks_per_beam >= (1ll << 32)) return fail(VPMC_ERR_ARG, "tracks_per_beam must be below 2^32");
+    vpmc_opts o;
+    vpmc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    vpmc_status st = check_opts(&o);
+    if (st != VPMC_OK) return st;
+    if (use_surrogate && !c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights");
+    std::vector<DevItem> items(n_beams);
+    for (int g = 0; g < n_beams; ++g) {
+        const int b = beam_ids[g];
+        if (b < 0 || b >= kMaxBeams || !c->beam_set[b]) return fail(VPMC_ERR_STATE, "beam %d is not set", b);
+        if (!c->beams[b].ap || c->beams[b].rs)
+            return fail(VPMC_ERR_ARG, "beam %d: training tracks need an aperture and no range shifter", b);
+        DevItem it{};
+        it.hist_off = (long long)g * tracks_per_beam;
+        it.spot = g;
+        it.beam = b;
+        items[g] = it;
+    }
+    const long long total = (long long)n_beams * tracks_per_beam;
+    float* d_frame = nullptr;
+    CUDA_TRY(dev_alloc(&d_frame, (size_t)total * 8));
+    auto done = [&](vpmc_status s) {
+        cudaFree(d_frame);
+        return s;
+    };
+    st = grow(c, &c->d_items, &c->items_cap, items.size());
+    if (st != VPMC_OK) return done(st);
+    const DevScen sc{{0.0f, 0.0f, 0.0f}, 1.0f};
+    const long long batch = std::min<long long>(total, kMaxBatch);
+    st = ensure_phase(c, batch, use_surrogate != 0);
+    if (st != VPMC_OK) return done(st);
+    if (cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(DevItem), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->d_scens, &sc, sizeof sc, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return done(fail(VPMC_ERR_CUDA, "upload of the track items failed"));
+    TransportParams p = base_params(c, o);
+    p.items = c->d_items;
+    p.n_items = n_beams;
+    p.n_scen = 1;
+    p.records = nullptr;
+    p.rec_cap = 0;
+    p.track_mode = 1;
+    p.trk_feat = feat_dev;
+    p.trk_y = target_dev;
+    p.trk_label = label_dev;
+    p.trk_frame = d_frame;
+    p.surrogate = use_surrogate ? 1 : 0;
+    p.sq = c->d_sq;
+    p.sq_cap = c->sq_cap;
+    p.sq_count = c->d_sq_count;
+    p.phase = c->d_phase;
+    p.phase_cap = c->phase_cap;
+    p.phase_count = c->d_phase_count;
+    p.aggregate = 0;
+    p.chunk = 32;
+    st = reset_counters(c);
+    if (st != VPMC_OK) return done(st);
+    if (use_surrogate && cudaMemsetAsync(c->sur.status, 0, sizeof(int), c->stream) != cudaSuccess)
+        return done(fail(VPMC_ERR_CUDA, "status reset failed"));
+    const int block = c->tune_dose.valid ? c->tune_dose.dev_block : 512;
+    for (long long h0 = 0; h0 < total; h0 += batch) {
+        p.hist_begin = h0;
+        p.total = std::min(total, h0 + batch);
+        cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
+        if (e == cudaSuccess && use_surrogate) e = cudaMemsetAsync(c->d_sq_count, 0, sizeof(unsigned long long), c->stream);
+        if (e == cudaSuccess) e = launch_devices(p, c->num_sms, block, c->stream);
+        if (e == cudaSuccess && use_surrogate) e = launch_sur_infer(c->sur, p, 2 * c->num_sms, c->stream);
+        if (e != cudaSuccess) return done(fail(VPMC_ERR_CUDA, "track launch: %s", cudaGetErrorString(e)));
+        c->launches += use_surrogate ? 2 : 1;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return done(fail(VPMC_ERR_CUDA, "track transport: %s", cudaGetErrorString(cudaGetLastError())));
+    int status = 0;
+    if (cudaMemcpy(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return done(fail(VPMC_ERR_CUDA, "status read failed"));
+    if (status & 1) return done(fail(VPMC_ERR_TIMEOUT, "tracks reached the iteration cap"));
+    if (status & 6) return done(fail(VPMC_ERR_DEVICE_FLAG, "query buffer overflow (status %d)", status));
+    if (use_surrogate) {
+        st = surrogate_status(c);
+        if (st != VPMC_OK) return done(st);
+    }
+    return done(VPMC_OK);
 }
 
 }  // extern "C"

@@ -63,6 +63,14 @@ struct vpmc_ctx {
     unsigned long long* d_phase_count = nullptr;
     unsigned long long* d_scratch = nullptr;
     size_t scratch_cap = 0;                    // elements
+    float* d_poly_kappa = nullptr;             // per polygon vertex: signed curvature (surrogate inputs)
+    // learned aperture surrogate
+    vpmc::SurNet sur{};
+    bool sur_ready = false;                    // weights loaded or trained
+    int sur_step = 0;                          // Adam steps taken since the weights were set
+    vpmc::SurQuery* d_sq = nullptr;            // brass entries handed to the surrogate
+    long long sq_cap = 0;
+    unsigned long long* d_sq_count = nullptr;
     vpmc::TuneResult tune_dose, tune_im;
     long long launches = 0;                    // kernels launched since creation
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -1,0 +1,886 @@
+// Learned aperture surrogate on the fifth-generation tensor cores (sm_103a).
+//
+// The network (6 -> 128 -> 128 -> 45, ReLU) maps a proton entering the brass
+// block near the opening to a transmission logit and a 4-component diagonal
+// Gaussian mixture over its state on the block's exit plane.  It is not part
+// of the paper.  It replaces the in-brass stepping of the aperture module
+// (Sec. 2.B), which the paper reads from pre-computed brass transport data.
+//
+// Every layer is one 128-row tile GEMM D[128 x N] (+)= A[128 x K] B[N x K]^T:
+// BF16 operands in shared memory in the canonical no-swizzle K-major layout
+// (8 x 8 core matrices of 128 contiguous bytes), FP32 accumulators in tensor
+// memory, issued by one thread with tcgen05.mma and completed through an
+// mbarrier; the epilogues read the accumulators back with tcgen05.ld, one
+// thread per row.  Training keeps the whole forward and backward of a tile in
+// one CTA: the weight gradients accumulate in tensor memory over the CTA's
+// tiles and the bias gradients ride along as an extra all-ones operand row.
+#include <algorithm>
+#include <cmath>
+
+#include <cuda_bf16.h>
+
+#include "device_common.cuh"
+#include "vpmc_internal.cuh"
+
+namespace vpmc {
+namespace {
+
+using namespace dev;
+using namespace sur;
+
+constexpr int kRows = 128;                // rows (tracks) per tile, one thread each
+constexpr int kWaitLimit = 1 << 22;       // mbarrier polls before a wait is declared failed
+
+// Byte offset of element (r, k) of an R x K operand in the no-swizzle
+// K-major layout: core matrix (r / 8, k / 8) of 8 rows x 16 bytes.
+__host__ __device__ constexpr int kmaj(int r, int k, int K)
+{
+    return ((((r >> 3) * (K >> 3)) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1);
+}
+
+// ---- tensor-core, tensor-memory and mbarrier primitives (inline PTX) ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte
+// offset (next core matrix along K), stride byte offset (next 8-row group),
+// descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait for the completion of the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_saddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(slot_saddr), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane, waited for.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];\n\ttcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // a in the low half (lower address)
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ unsigned short bf16_bits(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+
+// D[128 x N] (+)= A[128 x K] B[N x K]^T from K-major shared-memory operands.
+__device__ __forceinline__ void mma_tile(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int K, int N,
+                                         bool accumulate)
+{
+    const uint32_t idesc = idesc_bf16(kRows, N);
+    const uint32_t sbo = (uint32_t)(K >> 3) << 7;
+    for (int kc = 0; kc < (K >> 4); ++kc) {
+        const uint64_t a = sdesc(a_saddr + (uint32_t)kc * 256u, 128u, sbo);
+        const uint64_t b = sdesc(b_saddr + (uint32_t)kc * 256u, 128u, sbo);
+        umma(d_tmem, a, b, idesc, (accumulate || kc > 0) ? 1u : 0u);
+    }
+}
+
+// Make this thread's generic-proxy shared-memory writes and tensor-memory
+// reads visible to the next tensor-core operation, then synchronise.
+__device__ __forceinline__ void publish()
+{
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+}
+
+// Wait (all threads) for the tensor-core work committed to mbar; the CTA
+// agrees on the outcome.
+__device__ __forceinline__ bool complete(uint32_t mbar, uint32_t& phase)
+{
+    const bool ok = mbar_wait(mbar, phase);
+    phase ^= 1u;
+    const bool all = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    return all;
+}
+
+__device__ __forceinline__ void copy_to_smem(unsigned char* dst, const unsigned char* src, int bytes)
+{
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (int i = threadIdx.x; i < (bytes >> 4); i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+__device__ __forceinline__ void zero_smem(unsigned char* dst, int bytes)
+{
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (int i = threadIdx.x; i < (bytes >> 4); i += blockDim.x) d[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Row r of a [128 x 16] input tile: the 6 features, then zeros.
+__device__ __forceinline__ void store_input_row(unsigned char* X, int r, const float f[6])
+{
+    uint4 lo = make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), 0u);
+    *reinterpret_cast<uint4*>(X + kmaj(r, 0, kInPad)) = lo;
+    *reinterpret_cast<uint4*>(X + kmaj(r, 8, kInPad)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Hidden-layer epilogue of row r: h = relu(D + b) rounded to BF16 into the
+// K-major [128 x 128] tile dst; optionally the transposed copy (dstT, rows =
+// units, K = tile rows) and the ReLU mask (bit c: D + b > 0).
+template <bool kTransposed>
+__device__ __forceinline__ void hidden_epilogue(uint32_t t_row, const float* __restrict__ bias, unsigned char* dst,
+                                                unsigned char* dstT, int r, uint32_t (&mask)[4])
+{
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 16) {
+        float v[16];
+        tmem_ld16(t_row + (uint32_t)c0, v);
+        uint32_t w[8];
+        uint32_t mbits = 0u;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+            const float a0 = v[j] + __ldg(bias + c0 + j), a1 = v[j + 1] + __ldg(bias + c0 + j + 1);
+            mbits |= (a0 > 0.0f ? 1u : 0u) << j;
+            mbits |= (a1 > 0.0f ? 1u : 0u) << (j + 1);
+            const float h0 = fmaxf(a0, 0.0f), h1 = fmaxf(a1, 0.0f);
+            w[j >> 1] = pack_bf16(h0, h1);
+            if (kTransposed) {
+                *reinterpret_cast<unsigned short*>(dstT + kmaj(c0 + j, r, kRows)) = (unsigned short)(w[j >> 1] & 0xFFFFu);
+                *reinterpret_cast<unsigned short*>(dstT + kmaj(c0 + j + 1, r, kRows)) = (unsigned short)(w[j >> 1] >> 16);
+            }
+        }
+        *reinterpret_cast<uint4*>(dst + kmaj(r, c0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(dst + kmaj(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
+        mask[c0 >> 5] |= mbits << (c0 & 31);
+    }
+}
+
+// z = D3 + b3 for row r (48 columns, 45 used).
+__device__ __forceinline__ void output_epilogue(uint32_t t_d3, const float* __restrict__ b3, float (&z)[kOutPad])
+{
+#pragma unroll
+    for (int c0 = 0; c0 < kOutPad; c0 += 16) {
+        float v[16];
+        tmem_ld16(t_d3 + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) z[c0 + j] = v[j] + (c0 + j < kOut ? __ldg(b3 + c0 + j) : 0.0f);
+    }
+}
+
+// ============================================================================
+// Forward: network outputs of n feature rows, and the same network drawing
+// exit states for the transport's queries.
+// ============================================================================
+struct FwdSmem {
+    static constexpr int W = 0;                                   // W1, W2, W3 images
+    static constexpr int X = kImgW2T;                             // [128 x 16]
+    static constexpr int H = X + kRows * kInPad * 2;              // [128 x 128]
+    static constexpr int Bar = H + kRows * kH * 2;
+    static constexpr int Slot = Bar + 8;
+    static constexpr int Bytes = Slot + 8;
+};
+constexpr uint32_t kFwdCols = 256;        // D1 at 0, D2 at 128, D3 at 0
+
+// The three GEMMs of one tile whose inputs are in X; returns false when a
+// tensor-core wait failed.  On return the output accumulator holds z - b3.
+__device__ __forceinline__ bool forward_tile(unsigned char* sm, uint32_t tbase, uint32_t t_row, const SurNet& net,
+                                             uint32_t bar, uint32_t& phase, int r)
+{
+    const uint32_t s0 = smem_addr(sm);
+    uint32_t mask[4] = {0u, 0u, 0u, 0u};
+    publish();
+    if (threadIdx.x == 0) {
+        tc_fence_after();
+        mma_tile(tbase, s0 + FwdSmem::X, s0 + FwdSmem::W + kImgW1, kInPad, kH, false);
+        umma_commit(bar);
+    }
+    if (!complete(bar, phase)) return false;
+    hidden_epilogue<false>(t_row, net.params + ob1, sm + FwdSmem::H, nullptr, r, mask);
+    publish();
+    if (threadIdx.x == 0) {
+        tc_fence_after();
+        mma_tile(tbase + 128u, s0 + FwdSmem::H, s0 + FwdSmem::W + kImgW2, kH, kH, false);
+        umma_commit(bar);
+    }
+    if (!complete(bar, phase)) return false;
+    hidden_epilogue<false>(t_row + 128u, net.params + ob2, sm + FwdSmem::H, nullptr, r, mask);
+    publish();
+    if (threadIdx.x == 0) {
+        tc_fence_after();
+        mma_tile(tbase, s0 + FwdSmem::H, s0 + FwdSmem::W + kImgW3, kH, kOutPad, false);
+        umma_commit(bar);
+    }
+    return complete(bar, phase);
+}
+
+__device__ __forceinline__ void fwd_prologue(unsigned char* sm, const SurNet& net, uint32_t& tbase)
+{
+    copy_to_smem(sm + FwdSmem::W, net.img, kImgW2T);
+    if (threadIdx.x == 0) mbar_init(smem_addr(sm + FwdSmem::Bar));
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_addr(sm + FwdSmem::Slot), kFwdCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tbase = *reinterpret_cast<volatile uint32_t*>(sm + FwdSmem::Slot);
+}
+
+__device__ __forceinline__ void fwd_epilogue_free(unsigned char* sm, uint32_t tbase, uint32_t phase, bool ok,
+                                                  const SurNet& net)
+{
+    if (!ok) {
+        // a wait failed: latch the error and give the tensor core a last
+        // bounded chance to finish before its memory is released
+        if (threadIdx.x == 0) atomicOr(net.status, 1);
+        (void)mbar_wait(smem_addr(sm + FwdSmem::Bar), phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, kFwdCols);
+    }
+}
+
+__global__ void __launch_bounds__(kRows, 2) k_sur_forward(const SurNet net, const float* __restrict__ x, long long n,
+                                                          float* __restrict__ z)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint32_t tbase;
+    fwd_prologue(sm, net, tbase);
+    const int r = threadIdx.x;
+    const uint32_t t_row = tbase + ((uint32_t)((r >> 5) * 32) << 16);
+    const uint32_t bar = smem_addr(sm + FwdSmem::Bar);
+    uint32_t phase = 0u;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile * kRows < n && ok; tile += gridDim.x) {
+        const long long row = tile * kRows + r;
+        float f[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (row < n) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[k] = __ldg(x + 6 * row + k);
+        }
+        store_input_row(sm + FwdSmem::X, r, f);
+        ok = forward_tile(sm, tbase, t_row, net, bar, phase, r);
+        if (!ok) break;
+        float zz[kOutPad];
+        output_epilogue(t_row, net.params + ob3, zz);
+        if (row < n) {
+#pragma unroll
+            for (int j = 0; j < kOut; ++j) z[kOut * row + j] = zz[j];
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    fwd_epilogue_free(sm, tbase, phase, ok, net);
+}
+
+// Draw of one query from the network output z (see the sampler in the oracle):
+// transmitted = u0 < sigmoid(z0); component = first c with u1 < sum pi;
+// y_j = mu_cj + exp(clamp(s_cj)) xi_j with xi from three Box-Muller pairs.
+__device__ __forceinline__ bool sample_exit(const float (&z)[kOutPad], uint4 ua, uint4 ub, float (&y)[kDY])
+{
+    const float p = 1.0f / (1.0f + expf(-z[0]));
+    const bool trans = u01(ua.x) < p;
+    float amax = fmaxf(fmaxf(z[1], z[2]), fmaxf(z[3], z[4]));
+    float e[kNComp], sum = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kNComp; ++c) { e[c] = expf(z[1 + c] - amax); sum += e[c]; }
+    const float u1 = u01(ua.y);
+    int comp = kNComp - 1;
+    float cum = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kNComp; ++c) {
+        cum += e[c] / sum;
+        if (comp == kNComp - 1 && c < kNComp - 1 && u1 < cum) comp = c;
+    }
+    // the loop above takes the first c with u1 < cum_c; the last component otherwise
+    const float2 x01 = box_muller(u01(ua.z), u01(ua.w));
+    const float2 x23 = box_muller(u01(ub.x), u01(ub.y));
+    const float2 x45 = box_muller(u01(ub.z), u01(ub.w));
+    const float xi[kDY] = {x01.x, x01.y, x23.x, x23.y, x45.x};
+#pragma unroll
+    for (int j = 0; j < kDY; ++j) {
+        float mu = 0.0f, s = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kNComp; ++c) {
+            if (c == comp) { mu = z[5 + 5 * c + j]; s = z[25 + 5 * c + j]; }
+        }
+        y[j] = fmaf(expf(fminf(fmaxf(s, kSMin), kSMax)), xi[j], mu);
+    }
+    return trans;
+}
+
+__global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const TransportParams P)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint32_t tbase;
+    fwd_prologue(sm, net, tbase);
+    const int r = threadIdx.x;
+    const int lane = r & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t t_row = tbase + ((uint32_t)((r >> 5) * 32) << 16);
+    const uint32_t bar = smem_addr(sm + FwdSmem::Bar);
+    uint32_t phase = 0u;
+    bool ok = true;
+    const long long nq = min((long long)*P.sq_count, P.sq_cap);
+    unsigned long long acc_ap = 0ull;
+    for (long long tile = blockIdx.x; tile * kRows < nq && ok; tile += gridDim.x) {
+        const long long row = tile * kRows + r;
+        float f[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (row < nq) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[k] = P.sq[row].x[k];
+        }
+        store_input_row(sm + FwdSmem::X, r, f);
+        ok = forward_tile(sm, tbase, t_row, net, bar, phase, r);
+        if (!ok) break;
+        float zz[kOutPad];
+        output_epilogue(t_row, net.params + ob3, zz);
+        tc_fence_before();
+        __syncthreads();
+
+        bool emit = false;
+        PhaseRec rec;
+        if (row < nq) {
+            const SurQuery q = P.sq[row];
+            const DevItem& I = P.items[q.item];
+            const DevBeam& B = P.beams[I.beam];
+            const uint32_t hist = (uint32_t)(q.g - I.hist_off);
+            const uint2 key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
+            const uint4 ua = philox(make_uint4(hist, q.step, 4u, 0u), key);
+            const uint4 ub = philox(make_uint4(hist, q.step, 5u, 0u), key);
+            float y[kDY];
+            const bool trans = sample_exit(zz, ua, ub, y);
+            if (P.track_mode) {
+                if (q.g < P.total) {
+                    P.trk_label[q.g] = trans ? 1 : 0;
+#pragma unroll
+                    for (int j = 0; j < kDY; ++j) P.trk_y[5 * q.g + j] = trans ? y[j] : 0.0f;
+                }
+            } else {
+                const float T = B.ap_tdn - B.ap_tup;
+                const float un = q.dx * q.nx + q.dy * q.ny, ut = q.dy * q.nx - q.dx * q.ny;
+                const float E1 = q.E * (1.0f - 0.2f * y[0]);
+                const float dn = y[1] + T * un / q.dz, dt = y[2] + T * ut / q.dz;
+                float vn = fmaf(kDirScale, y[3], un), vt = fmaf(kDirScale, y[4], ut);
+                const float r2 = vn * vn + vt * vt;
+                if (r2 > 0.75f) {
+                    const float sc = sqrtf(0.75f / r2);
+                    vn *= sc;
+                    vt *= sc;
+                }
+                if (trans && E1 > kEcut && E1 <= q.E && isfinite(dn + dt + vn + vt)) {
+                    const DevScen& SC = P.scens[I.scen];
+                    const float pb[3] = {q.px + dn * q.nx - dt * q.ny, q.py + dn * q.ny + dt * q.nx, B.ap_tdn};
+                    const float db[3] = {vn * q.nx - vt * q.ny, vn * q.ny + vt * q.nx, sqrtf(1.0f - vn * vn - vt * vt)};
+                    bev_to_patient(B, SC, pb, rec.p);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) rec.d[k] = db[0] * B.u[k] + db[1] * B.v[k] + db[2] * B.w[k];
+                    rec.E = E1;
+                    if (P.nuclear) {
+                        const uint4 un6 = philox(make_uint4(hist, q.step, 6u, 0u), key);
+                        rec.nlam = -logf(u01(un6.x));
+                    } else {
+                        rec.nlam = __int_as_float(0x7f800000);
+                    }
+                    rec.step = q.step + 1u;
+                    rec.item = q.item;
+                    rec.g = q.g;
+                    emit = true;
+                    acc_ap += __float2ull_rn((q.E - E1) * P.fscale);
+                } else {
+                    acc_ap += __float2ull_rn(q.E * P.fscale);
+                    if (P.records && q.g < P.rec_cap) {
+                        HistRecord hr;
+                        hr.q_dep = 0;
+                        hr.fate = kAbsAp;
+                        hr.steps = (int)q.step;
+                        hr.e_dep = 0.0f;
+                        hr.e_end = 0.0f;
+                        const float pb[3] = {q.px, q.py, B.ap_tup};
+                        bev_to_patient(B, P.scens[I.scen], pb, hr.pos);
+                        hr.pad = 0.0f;
+                        P.records[q.g] = hr;
+                    }
+                }
+            }
+        }
+        // hand the transmitted protons to the patient kernel (one atomic per warp)
+        const unsigned emask = __ballot_sync(kFull, emit);
+        if (emask) {
+            unsigned long long base = 0;
+            const int leader = __ffs(emask) - 1;
+            if (lane == leader) base = atomicAdd(P.phase_count, (unsigned long long)__popc(emask));
+            base = __shfl_sync(kFull, base, leader);
+            if (emit) {
+                const long long slot = (long long)base + __popc(emask & lt_mask);
+                if (slot < P.phase_cap) P.phase[slot] = rec;
+                else atomicOr(P.status, 2);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc_ap += __shfl_xor_sync(kFull, acc_ap, o);
+    if (lane == 0 && acc_ap) atomicAdd(P.stats + kStAp, acc_ap);
+    fwd_epilogue_free(sm, tbase, phase, ok, net);
+}
+
+// ============================================================================
+// Training: forward, loss, backward and weight-gradient accumulation of the
+// CTA's tiles in one kernel.
+// ============================================================================
+struct TrainSmem {
+    static constexpr int Img = 0;                                  // all five weight images
+    static constexpr int X = kImgBytes;                            // [128 x 16]
+    static constexpr int XT = X + kRows * kInPad * 2;              // [16 x 128]: features, row 6 = ones
+    static constexpr int A = XT + kInPad * kRows * 2;              // [128 x 128]: h1, h2, then da2
+    static constexpr int Bt = A + kRows * kH * 2;                  // [144 x 128]: h1^T, row 128 = ones
+    static constexpr int C = Bt + 144 * kRows * 2;                 // [128 x 128]: h2^T, da2^T, da1^T
+    static constexpr int DZ = C + kH * kRows * 2;                  // [128 x 48]
+    static constexpr int DZT = DZ + kRows * kOutPad * 2;           // [48 x 128]
+    static constexpr int Bar = DZT + kOutPad * kRows * 2;
+    static constexpr int Slot = Bar + 8;
+    static constexpr int Bytes = Slot + 8;
+};
+static_assert(TrainSmem::Bytes <= 232448, "training tile exceeds the shared memory of one CTA");
+// tensor-memory columns: D1/D3/D4 at 0, D2/D5 at 128, dW2 (with db2) at 256,
+// dW3^T at 400, dW1 (with db1) at 448
+constexpr uint32_t kTrainCols = 512, kColW2 = 256, kColW3T = 400, kColW1 = 448;
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Loss of one row and its gradient with respect to z (written out from the
+// loss: BCE of the transmission logit plus, for transmitted tracks, the
+// negative log-likelihood of the mixture).
+__device__ __forceinline__ float row_loss_grad(const float (&z)[kOutPad], float t, const float* __restrict__ yv,
+                                               float (&g)[kOutPad])
+{
+#pragma unroll
+    for (int j = 0; j < kOutPad; ++j) g[j] = 0.0f;
+    const float logit = z[0];
+    const float sig = 1.0f / (1.0f + expf(-logit));
+    g[0] = sig - t;
+    float loss = fmaxf(logit, 0.0f) + log1pf(expf(-fabsf(logit))) - t * logit;
+    if (t > 0.0f) {
+        float y[kDY];
+#pragma unroll
+        for (int j = 0; j < kDY; ++j) y[j] = yv[j];
+        const float amax = fmaxf(fmaxf(z[1], z[2]), fmaxf(z[3], z[4]));
+        float asum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kNComp; ++c) asum += expf(z[1 + c] - amax);
+        const float lse_a = amax + logf(asum);
+        float lc[kNComp];
+#pragma unroll
+        for (int c = 0; c < kNComp; ++c) {
+            float acc = z[1 + c] - lse_a;
+#pragma unroll
+            for (int j = 0; j < kDY; ++j) {
+                const float s = z[25 + 5 * c + j];
+                const float rr = (y[j] - z[5 + 5 * c + j]) * expf(-s);
+                acc += -0.5f * rr * rr - s - 0.91893853320467274f;
+            }
+            lc[c] = acc;
+        }
+        const float lmax = fmaxf(fmaxf(lc[0], lc[1]), fmaxf(lc[2], lc[3]));
+        float lsum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kNComp; ++c) lsum += expf(lc[c] - lmax);
+        const float L = lmax + logf(lsum);
+        loss -= L;
+#pragma unroll
+        for (int c = 0; c < kNComp; ++c) {
+            const float resp = expf(lc[c] - L);
+            const float pi = expf(z[1 + c] - lse_a);
+            g[1 + c] = pi - resp;
+#pragma unroll
+            for (int j = 0; j < kDY; ++j) {
+                const float s = z[25 + 5 * c + j];
+                const float inv2 = expf(-2.0f * s);
+                const float diff = y[j] - z[5 + 5 * c + j];
+                g[5 + 5 * c + j] = -resp * diff * inv2;
+                g[25 + 5 * c + j] = -resp * (diff * diff * inv2 - 1.0f);
+            }
+        }
+    }
+    return loss;
+}
+
+__global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const float* __restrict__ x,
+                                                        const float* __restrict__ yt, const int* __restrict__ label,
+                                                        long long first, long long rows, long long n, float inv_rows)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const uint32_t s0 = smem_addr(sm);
+    const int r = threadIdx.x;
+    const int lane = r & 31;
+    copy_to_smem(sm + TrainSmem::Img, net.img, kImgBytes);
+    zero_smem(sm + TrainSmem::XT, kInPad * kRows * 2);
+    zero_smem(sm + TrainSmem::Bt + kmaj(128, 0, kRows), 16 * kRows * 2);
+    zero_smem(sm + TrainSmem::DZT, kOutPad * kRows * 2);
+    __syncthreads();
+    // constant operand rows: XT row 6 and h1^T row 128 are all ones (bias gradients)
+    {
+        const unsigned short one = bf16_bits(1.0f);
+        *reinterpret_cast<unsigned short*>(sm + TrainSmem::XT + kmaj(6, r, kRows)) = one;
+        *reinterpret_cast<unsigned short*>(sm + TrainSmem::Bt + kmaj(128, r, kRows)) = one;
+    }
+    if (r == 0) mbar_init(s0 + TrainSmem::Bar);
+    if ((r >> 5) == 0) tmem_alloc(s0 + TrainSmem::Slot, kTrainCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(sm + TrainSmem::Slot);
+    const uint32_t t_row = tbase + ((uint32_t)((r >> 5) * 32) << 16);
+    const uint32_t bar = s0 + TrainSmem::Bar;
+    uint32_t phase = 0u;
+    bool ok = true;
+    int tiles_done = 0;
+    double loss_acc = 0.0;
+    const long long end = min(first + rows, n);
+    for (long long tile = blockIdx.x; first + tile * kRows < end && ok; tile += gridDim.x) {
+        const long long row = first + tile * kRows + r;
+        const bool valid = row < end;
+        // ---- inputs ----
+        float f[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (valid) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[k] = __ldg(x + 6 * row + k);
+        }
+        store_input_row(sm + TrainSmem::X, r, f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            *reinterpret_cast<unsigned short*>(sm + TrainSmem::XT + kmaj(k, r, kRows)) = bf16_bits(f[k]);
+        uint32_t m1[4] = {0u, 0u, 0u, 0u}, m2[4] = {0u, 0u, 0u, 0u};
+        // ---- layer 1 ----
+        publish();
+        if (r == 0) {
+            tc_fence_after();
+            mma_tile(tbase, s0 + TrainSmem::X, s0 + TrainSmem::Img + kImgW1, kInPad, kH, false);
+            umma_commit(bar);
+        }
+        if (!(ok = complete(bar, phase))) break;
+        hidden_epilogue<true>(t_row, net.params + ob1, sm + TrainSmem::A, sm + TrainSmem::Bt, r, m1);
+        // ---- layer 2 ----
+        publish();
+        if (r == 0) {
+            tc_fence_after();
+            mma_tile(tbase + 128u, s0 + TrainSmem::A, s0 + TrainSmem::Img + kImgW2, kH, kH, false);
+            umma_commit(bar);
+        }
+        if (!(ok = complete(bar, phase))) break;
+        hidden_epilogue<true>(t_row + 128u, net.params + ob2, sm + TrainSmem::A, sm + TrainSmem::C, r, m2);
+        // ---- output layer ----
+        publish();
+        if (r == 0) {
+            tc_fence_after();
+            mma_tile(tbase, s0 + TrainSmem::A, s0 + TrainSmem::Img + kImgW3, kH, kOutPad, false);
+            umma_commit(bar);
+        }
+        if (!(ok = complete(bar, phase))) break;
+        float zz[kOutPad], g[kOutPad];
+        output_epilogue(t_row, net.params + ob3, zz);
+        float lrow = 0.0f;
+        if (valid) {
+            lrow = row_loss_grad(zz, label[row] > 0 ? 1.0f : 0.0f, yt + 5 * row, g);
+#pragma unroll
+            for (int j = 0; j < kOutPad; ++j) g[j] *= inv_rows;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kOutPad; ++j) g[j] = 0.0f;
+        }
+        loss_acc += (double)lrow;
+        // dz: K-major [128 x 48] and transposed [48 x 128]; b3 gradient by warp sums
+#pragma unroll
+        for (int c0 = 0; c0 < kOutPad; c0 += 8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) w[j >> 1] = pack_bf16(g[c0 + j], g[c0 + j + 1]);
+            *reinterpret_cast<uint4*>(sm + TrainSmem::DZ + kmaj(r, c0, kOutPad)) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (c0 + j < kOut) {
+                    const unsigned short b = (unsigned short)((w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
+                    *reinterpret_cast<unsigned short*>(sm + TrainSmem::DZT + kmaj(c0 + j, r, kRows)) = b;
+                }
+            }
+        }
+#pragma unroll 1
+        for (int j = 0; j < kOut; ++j) {
+            const float s = warp_sum(g[j]);
+            if (lane == 0 && s != 0.0f) atomicAdd(net.grad + ob3 + j, s);
+        }
+        // ---- dh2 = dz W3 and dW3^T += h2^T dz ----
+        publish();
+        if (r == 0) {
+            tc_fence_after();
+            mma_tile(tbase, s0 + TrainSmem::DZ, s0 + TrainSmem::Img + kImgW3T, kOutPad, kH, false);
+            mma_tile(tbase + kColW3T, s0 + TrainSmem::C, s0 + TrainSmem::DZT, kRows, kOutPad, tiles_done > 0);
+            umma_commit(bar);
+        }
+        if (!(ok = complete(bar, phase))) break;
+        // ---- da2 = dh2 * relu'(a2): K-major into A, transposed into C ----
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float v[16];
+            tmem_ld16(t_row + (uint32_t)c0, v);
+            uint32_t w[8];
+            const uint32_t mb = m2[c0 >> 5] >> (c0 & 31);
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                const float a0 = ((mb >> j) & 1u) ? v[j] : 0.0f;
+                const float a1 = ((mb >> (j + 1)) & 1u) ? v[j + 1] : 0.0f;
+                w[j >> 1] = pack_bf16(a0, a1);
+                *reinterpret_cast<unsigned short*>(sm + TrainSmem::C + kmaj(c0 + j, r, kRows)) =
+                    (unsigned short)(w[j >> 1] & 0xFFFFu);
+                *reinterpret_cast<unsigned short*>(sm + TrainSmem::C + kmaj(c0 + j + 1, r, kRows)) =
+                    (unsigned short)(w[j >> 1] >> 16);
+            }
+            *reinterpret_cast<uint4*>(sm + TrainSmem::A + kmaj(r, c0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(sm + TrainSmem::A + kmaj(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+        // ---- dh1 = da2 W2 and [dW2 | db2] += da2^T [h1 | 1] ----
+        publish();
+        if (r == 0) {
+            tc_fence_after();
+            mma_tile(tbase + 128u, s0 + TrainSmem::A, s0 + TrainSmem::Img + kImgW2T, kH, kH, false);
+            mma_tile(tbase + kColW2, s0 + TrainSmem::C, s0 + TrainSmem::Bt, kRows, 144, tiles_done > 0);
+            umma_commit(bar);
+        }
+        if (!(ok = complete(bar, phase))) break;
+        // ---- da1 = dh1 * relu'(a1), transposed into C ----
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float v[16];
+            tmem_ld16(t_row + 128u + (uint32_t)c0, v);
+            const uint32_t mb = m1[c0 >> 5] >> (c0 & 31);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float a = ((mb >> j) & 1u) ? v[j] : 0.0f;
+                *reinterpret_cast<unsigned short*>(sm + TrainSmem::C + kmaj(c0 + j, r, kRows)) = bf16_bits(a);
+            }
+        }
+        // ---- [dW1 | db1] += da1^T [x | 1] ----
+        publish();
+        if (r == 0) {
+            tc_fence_after();
+            mma_tile(tbase + kColW1, s0 + TrainSmem::C, s0 + TrainSmem::XT, kRows, kInPad, tiles_done > 0);
+            umma_commit(bar);
+        }
+        if (!(ok = complete(bar, phase))) break;
+        ++tiles_done;
+    }
+    // ---- loss and the accumulated weight gradients ----
+    const float ls = warp_sum((float)loss_acc);
+    if (lane == 0 && ls != 0.0f) atomicAdd(net.loss, (double)ls);
+    if (ok && tiles_done > 0) {
+        const int h = r;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 144; c0 += 16) {
+            float v[16];
+            tmem_ld16(t_row + kColW2 + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int i = c0 + j;
+                if (i < kH) atomicAdd(net.grad + oW2 + h * kH + i, v[j]);
+                else if (i == kH) atomicAdd(net.grad + ob2 + h, v[j]);
+            }
+        }
+#pragma unroll 1
+        for (int c0 = 0; c0 < kOutPad; c0 += 16) {
+            float v[16];
+            tmem_ld16(t_row + kColW3T + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c0 + j < kOut) atomicAdd(net.grad + oW3 + (c0 + j) * kH + h, v[j]);
+        }
+        {
+            float v[16];
+            tmem_ld16(t_row + kColW1, v);
+#pragma unroll
+            for (int j = 0; j < kIn; ++j) atomicAdd(net.grad + oW1 + h * kIn + j, v[j]);
+            atomicAdd(net.grad + ob1 + h, v[kIn]);
+        }
+    }
+    if (!ok) {
+        if (r == 0) atomicOr(net.status, 1);
+        (void)mbar_wait(bar, phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if ((r >> 5) == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, kTrainCols);
+    }
+}
+
+// ============================================================================
+// Parameter update and BF16 operand images.
+// ============================================================================
+__device__ __forceinline__ void write_images(unsigned char* img, int k, float w)
+{
+    const unsigned short b = bf16_bits(w);
+    if (k >= oW1 && k < ob1) {
+        const int h = (k - oW1) / kIn, f = (k - oW1) % kIn;
+        *reinterpret_cast<unsigned short*>(img + kImgW1 + kmaj(h, f, kInPad)) = b;
+    } else if (k >= oW2 && k < ob2) {
+        const int h = (k - oW2) / kH, i = (k - oW2) % kH;
+        *reinterpret_cast<unsigned short*>(img + kImgW2 + kmaj(h, i, kH)) = b;
+        *reinterpret_cast<unsigned short*>(img + kImgW2T + kmaj(i, h, kH)) = b;
+    } else if (k >= oW3 && k < ob3) {
+        const int o = (k - oW3) / kH, h = (k - oW3) % kH;
+        *reinterpret_cast<unsigned short*>(img + kImgW3 + kmaj(o, h, kH)) = b;
+        *reinterpret_cast<unsigned short*>(img + kImgW3T + kmaj(h, o, kOutPad)) = b;
+    }
+}
+
+__global__ void k_sur_pack(const SurNet net)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < kNParams) write_images(net.img, k, net.params[k]);
+}
+
+// Adam (Kingma & Ba 2015): moments, bias corrections c1 = 1 / (1 - beta1^t),
+// c2 = 1 / (1 - beta2^t); the gradient is cleared for the next step.
+__global__ void k_sur_adam(const SurNet net, float lr, float c1, float c2)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kNParams) return;
+    const float g = net.grad[k];
+    net.grad[k] = 0.0f;
+    const float m = fmaf(0.9f, net.m[k], 0.1f * g);
+    const float v = fmaf(0.999f, net.v[k], 0.001f * g * g);
+    net.m[k] = m;
+    net.v[k] = v;
+    const float w = net.params[k] - lr * (m * c1) / (sqrtf(v * c2) + 1e-8f);
+    net.params[k] = w;
+    write_images(net.img, k, w);
+}
+
+}  // namespace
+
+size_t sur_forward_smem_bytes() { return FwdSmem::Bytes; }
+size_t sur_train_smem_bytes() { return TrainSmem::Bytes; }
+
+cudaError_t launch_sur_pack(const SurNet& net, cudaStream_t s)
+{
+    k_sur_pack<<<(kNParams + 255) / 256, 256, 0, s>>>(net);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_forward(const SurNet& net, const float* x, long long n, float* z, int grid, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sur_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, FwdSmem::Bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (n <= 0) return cudaSuccess;
+    const long long tiles = (n + kRows - 1) / kRows;
+    k_sur_forward<<<(int)std::min<long long>(tiles, grid), kRows, FwdSmem::Bytes, s>>>(net, x, n, z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_infer(const SurNet& net, const TransportParams& p, int grid, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, FwdSmem::Bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_sur_infer<<<grid, kRows, FwdSmem::Bytes, s>>>(net, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_train(const SurNet& net, const float* x, const float* y, const int* label, long long first,
+                             long long rows, long long n, float inv_rows, int grid, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sur_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TrainSmem::Bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long tiles = (rows + kRows - 1) / kRows;
+    if (tiles <= 0) return cudaSuccess;
+    k_sur_train<<<(int)std::min<long long>(tiles, grid), kRows, TrainSmem::Bytes, s>>>(net, x, y, label, first, rows, n,
+                                                                                   inv_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_adam(const SurNet& net, int step, float lr, cudaStream_t s)
+{
+    const float c1 = (float)(1.0 / (1.0 - pow(0.9, step)));
+    const float c2 = (float)(1.0 / (1.0 - pow(0.999, step)));
+    k_sur_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(net, lr, c1, c2);
+    return cudaGetLastError();
+}
+
+}  // namespace vpmc

@@ -228,4 +228,22 @@ void build_raster(const double* xy, int n, double margin, unsigned char* cells, 
 
 void hu_curve_props(const double* curve15, double hu, double* rho, double* spr) { curve_props(curve15, hu, rho, spr); }
 
+void polygon_curvature(const double* xy, int n, float* kappa)
+{
+    double twice_area = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int j = (i + 1) % n;
+        twice_area += xy[2 * i] * xy[2 * j + 1] - xy[2 * j] * xy[2 * i + 1];
+    }
+    const double orient = twice_area < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < n; ++i) {
+        const int a = (i + n - 1) % n, b = (i + 1) % n;
+        const double ax = xy[2 * i] - xy[2 * a], ay = xy[2 * i + 1] - xy[2 * a + 1];
+        const double bx = xy[2 * b] - xy[2 * i], by = xy[2 * b + 1] - xy[2 * i + 1];
+        const double turn = std::atan2(ax * by - ay * bx, ax * bx + ay * by);
+        const double half = 0.5 * (std::hypot(ax, ay) + std::hypot(bx, by));
+        kappa[i] = (float)(orient * turn / half);
+    }
+}
+
 }  // namespace vpmc

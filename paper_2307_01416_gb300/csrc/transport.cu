@@ -23,38 +23,15 @@
 // Random numbers: Philox4x32-10, key = (seed lo, spot ^ seed hi), counter =
 // (history, step, slot, 0): slot 0 source, 1 scattering, 2 straggling,
 // 3 nuclear free path.
+#include "device_common.cuh"
 #include "vpmc_internal.cuh"
 
 namespace vpmc {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using namespace dev;
+
 constexpr float kMp = 938.272f;
-
-__device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// ((x >> 9) + 1/2) * 2^-23: 23-bit uniform in (0, 1), exact in FP32.
-__device__ __forceinline__ float u01(uint32_t x) { return fmaf(__uint2float_rn(x >> 9), 0x1p-23f, 0x1p-24f); }
-
-// Box-Muller with accurate functions (source sampling, once per history).
-__device__ __forceinline__ float2 box_muller(float u1, float u2)
-{
-    const float r = sqrtf(-2.0f * logf(u1));
-    float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    return make_float2(r * c, r * s);
-}
 
 // Box-Muller with hardware approximations (per-step physics).  u1 <= 1 - 2^-24,
 // so -2 ln u1 > 0; the clamp only guards the approximate logarithm.
@@ -220,6 +197,50 @@ __device__ __forceinline__ float coop_wall_distance(bool need, float x, float y,
     return result;
 }
 
+// Nearest boundary point of the requester's (x, y): (distance, nearest x,
+// nearest y, curvature there).  Ties between edges go to the lower edge index;
+// the curvature is interpolated along the nearest edge between its vertices'
+// curvatures, so either of two equidistant edges gives the same value.
+__device__ __forceinline__ float4 coop_nearest_edge(bool need, float x, float y, const float2* __restrict__ poly,
+                                                    const float* __restrict__ kappa, int off, int n, int lane)
+{
+    float4 result = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    unsigned m = __ballot_sync(kFull, need);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        const float qx = __shfl_sync(kFull, x, src), qy = __shfl_sync(kFull, y, src);
+        const int qo = __shfl_sync(kFull, off, src), qn = __shfl_sync(kFull, n, src);
+        float best = __int_as_float(0x7f800000), bt = 0.0f;
+        int bi = 0x7fffffff;
+        for (int i = lane; i < qn; i += 32) {
+            const float2 a = poly[qo + i];
+            const float2 b = poly[qo + (i + 1 < qn ? i + 1 : 0)];
+            const float ex = b.x - a.x, ey = b.y - a.y;
+            float t = ((qx - a.x) * ex + (qy - a.y) * ey) / (ex * ex + ey * ey);
+            t = fminf(fmaxf(t, 0.0f), 1.0f);
+            const float ddx = a.x + t * ex - qx, ddy = a.y + t * ey - qy;
+            const float d2 = ddx * ddx + ddy * ddy;
+            if (d2 < best) { best = d2; bi = i; bt = t; }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const float ob = __shfl_xor_sync(kFull, best, o);
+            const int oi = __shfl_xor_sync(kFull, bi, o);
+            const float ot = __shfl_xor_sync(kFull, bt, o);
+            if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; bt = ot; }
+        }
+        if (lane == src && bi < qn) {
+            const int bj = bi + 1 < qn ? bi + 1 : 0;
+            const float2 a = poly[qo + bi], b = poly[qo + bj];
+            const float k0 = __ldg(kappa + qo + bi), k1 = __ldg(kappa + qo + bj);
+            result = make_float4(sqrtf(best), a.x + bt * (b.x - a.x), a.y + bt * (b.y - a.y),
+                                 fmaf(bt, k1 - k0, k0));
+        }
+    }
+    return result;
+}
+
 // Duff et al. 2017, "Building an orthonormal basis, revisited".
 __device__ __forceinline__ void orthonormal_basis(const float n[3], float b1[3], float b2[3])
 {
@@ -287,7 +308,7 @@ struct Lane {
     uint32_t step;  // condensed-history steps so far (RNG counter)
     uint32_t hist;  // history index within its spot
     int stage;      // devices: -1 just born, 0 range shifter, 1 aperture
-    int forced;     // aperture: the next step is in brass (after a wall hit)
+    int forced;     // aperture: 1 the next step is in brass (after a wall hit), -1 on the entrance plane
     int ic[3], is[3];
     int item;
     int iters;
@@ -376,13 +397,6 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, Lane& L, 
     }
 }
 
-__device__ __forceinline__ void bev_to_patient(const DevBeam& B, const DevScen& sc, const float pb[3], float out[3])
-{
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        out[k] = B.iso[k] + sc.shift[k] + pb[0] * B.u[k] + pb[1] * B.v[k] + pb[2] * B.w[k];
-}
-
 // Largest i with items[i].hist_off <= g, searched by the whole warp: each
 // round the 32 lanes probe 32 evenly spaced entries (g is warp-uniform).
 __device__ __forceinline__ int find_item_warp(const DevItem* __restrict__ items, int n, long long g, int lane)
@@ -452,8 +466,14 @@ __device__ __forceinline__ void warp_add_stats(const TransportParams& P, unsigne
 // ============================================================================
 // Range shifter and aperture.
 // ============================================================================
+// kMode bit 0: brass entries in the surrogate's domain become queries;
+// bit 1: training tracks (histories start on the aperture entrance plane and
+// record the surrogate's inputs and targets).
+template <int kMode>
 __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
 {
+    constexpr bool kSur = (kMode & 1) != 0;
+    constexpr bool kTrack = (kMode & 2) != 0;
     extern __shared__ __align__(16) unsigned char smem[];
     {
         // PMMA and brass rows of the tables, material constants, beams, scenarios, polygons
@@ -527,16 +547,38 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                 L.step = 0;
                 L.iters = 0;
                 key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
-                // source: slot 0 -> (x, y) at the isocentre plane and two projected angles
-                const uint4 x = philox(make_uint4(L.hist, 0u, 0u, 0u), key);
-                const float2 z01 = box_muller(u01(x.x), u01(x.y));
-                const float2 z23 = box_muller(u01(x.z), u01(x.w));
-                const float a0 = fmaf(I.sigma, z01.x, I.x), b0 = fmaf(I.sigma, z01.y, I.y);
-                const float tha = I.div_rad * z23.x, thb = I.div_rad * z23.y;
-                const float nrm = rsqrtf(1.0f + tha * tha + thb * thb);
-                L.d[0] = tha * nrm; L.d[1] = thb * nrm; L.d[2] = nrm;
-                L.p[0] = fmaf(B.t_src, tha, a0); L.p[1] = fmaf(B.t_src, thb, b0); L.p[2] = B.t_src;
-                L.E = I.E0;
+                if (kTrack) {
+                    // training track: born on the aperture's entrance plane near
+                    // the opening (slot 0: energy, angle, edge distance; slot 5:
+                    // incidence angles along the radial and tangential directions)
+                    const uint4 x = philox(make_uint4(L.hist, 0u, 0u, 0u), key);
+                    const float E = fmaf(sur::kEHi - sur::kELo, u01(x.x), sur::kELo);
+                    float sph, cph;
+                    sincospif(2.0f * u01(x.y), &sph, &cph);
+                    const float r12 = 1.2f * range_of(brass.Rt, E) / brass.rho;
+                    const float dhi = r12 < B.ap_tdn - B.ap_tup ? fminf(sur::kDCap, r12) : sur::kDCap;
+                    const float rr = fmaf(dhi, u01(x.z), B.r_circ);
+                    const uint4 a = philox(make_uint4(L.hist, 0u, 5u, 0u), key);
+                    const float2 zz = box_muller(u01(a.x), u01(a.y));
+                    const float tn = fminf(fmaxf(sur::kAngSigma * zz.x, -sur::kAngMax), sur::kAngMax);
+                    const float tt = fminf(fmaxf(sur::kAngSigma * zz.y, -sur::kAngMax), sur::kAngMax);
+                    L.d[0] = tn * cph - tt * sph;
+                    L.d[1] = tn * sph + tt * cph;
+                    L.d[2] = sqrtf(1.0f - tn * tn - tt * tt);
+                    L.p[0] = rr * cph; L.p[1] = rr * sph; L.p[2] = B.ap_tup;
+                    L.E = E;
+                } else {
+                    // source: slot 0 -> (x, y) at the isocentre plane and two projected angles
+                    const uint4 x = philox(make_uint4(L.hist, 0u, 0u, 0u), key);
+                    const float2 z01 = box_muller(u01(x.x), u01(x.y));
+                    const float2 z23 = box_muller(u01(x.z), u01(x.w));
+                    const float a0 = fmaf(I.sigma, z01.x, I.x), b0 = fmaf(I.sigma, z01.y, I.y);
+                    const float tha = I.div_rad * z23.x, thb = I.div_rad * z23.y;
+                    const float nrm = rsqrtf(1.0f + tha * tha + thb * thb);
+                    L.d[0] = tha * nrm; L.d[1] = thb * nrm; L.d[2] = nrm;
+                    L.p[0] = fmaf(B.t_src, tha, a0); L.p[1] = fmaf(B.t_src, thb, b0); L.p[2] = B.t_src;
+                    L.E = I.E0;
+                }
                 if (P.nuclear) {
                     const uint4 y = philox(make_uint4(L.hist, 0u, 3u, 0u), key);
                     L.nlam = -logf(u01(y.x));
@@ -562,7 +604,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
         bool do_ch = false;
         float s_geom = __int_as_float(0x7f800000);
         bool down = true;
-        bool ap_pending = false, was_forced = false, need_pip = false;
+        bool ap_pending = false, was_forced = false, at_entry = false, need_pip = false;
         int cls = 0, q_off = 0, q_n = 0;
         if (alive) {
             const DevItem& I = P.items[L.item];
@@ -595,7 +637,8 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                 else if (L.d[2] < 0.0f) { s_geom = (B.ap_tup - L.p[2]) / L.d[2]; down = false; }
                 s_geom = fmaxf(s_geom, 0.0f);       // scattering offsets can leave it past the plane
                 ap_pending = true;
-                was_forced = L.forced != 0;
+                was_forced = L.forced > 0;
+                at_entry = L.forced < 0;
                 cls = was_forced ? 0 : raster_class(B, P.raster, L.p[0], L.p[1]);
                 need_pip = cls == 2;
                 q_off = B.poly_off;
@@ -633,6 +676,70 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                 }
             }
         }
+        // ---- brass entry: edge frame and surrogate inputs (warp-cooperative) ----
+        const bool entry_q = ap_pending && !open && at_entry && (kTrack || kSur);
+        const float4 ne = coop_nearest_edge(entry_q, L.p[0], L.p[1], poly, P.poly_kappa, q_off, q_n, lane);
+        bool sur_emit = false;
+        float feat[6], fnx = 0.0f, fny = 0.0f;
+        if (entry_q) {
+            const DevBeam& B = beams[__ldg(&P.items[L.item].beam)];
+            const float T = B.ap_tdn - B.ap_tup;
+            const float dist = ne.x;
+            const float inv = dist > 0.0f ? 1.0f / dist : 0.0f;
+            fnx = (L.p[0] - ne.y) * inv;
+            fny = (L.p[1] - ne.z) * inv;
+            const float un = L.d[0] * fnx + L.d[1] * fny, ut = L.d[1] * fnx - L.d[0] * fny;
+            const float rmm = L.R / brass.rho;
+            feat[0] = fminf(dist, sur::kDCap) * (2.0f / sur::kDCap) - 1.0f;
+            feat[1] = (L.E - 0.5f * (sur::kELo + sur::kEHi)) * (2.0f / (sur::kEHi - sur::kELo));
+            feat[2] = un * (1.0f / sur::kAngSigma);
+            feat[3] = ut * (1.0f / sur::kAngSigma);
+            feat[4] = fmaf(8.0f, ne.w, -1.0f);
+            feat[5] = rmm / T - 1.0f;
+            if (kTrack && L.g < P.total) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) P.trk_feat[6 * L.g + k] = feat[k];
+                float* fr = P.trk_frame + 8 * L.g;
+                fr[0] = L.p[0]; fr[1] = L.p[1]; fr[2] = L.d[2]; fr[3] = fnx;
+                fr[4] = fny; fr[5] = un; fr[6] = ut; fr[7] = L.E;
+            }
+            if (kSur) {
+                if (1.2f * rmm < fminf(dist, T)) {
+                    absorb = true;                  // cannot reach the opening or the exit face
+                } else if (L.E >= sur::kELo && L.E <= sur::kEHi && fabsf(un) <= sur::kAngMax &&
+                           fabsf(ut) <= sur::kAngMax && ne.w >= sur::kKappaLo && ne.w <= sur::kKappaHi &&
+                           fabsf(T - sur::kThickness) < 1e-3f && dist > 0.0f) {
+                    sur_emit = true;                // in the training domain: one network draw
+                }
+            }
+        }
+        // ---- surrogate queries of the brass entries in its domain (one atomic per warp) ----
+        const unsigned smask = __ballot_sync(kFull, sur_emit);
+        if (smask) {
+            unsigned long long base = 0;
+            const int leader = __ffs(smask) - 1;
+            if (lane == leader) base = atomicAdd(P.sq_count, (unsigned long long)__popc(smask));
+            base = __shfl_sync(kFull, base, leader);
+            if (sur_emit) {
+                const long long slot = (long long)base + __popc(smask & lt_mask);
+                if (slot < P.sq_cap) {
+                    SurQuery q;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) q.x[k] = feat[k];
+                    q.px = L.p[0]; q.py = L.p[1];
+                    q.dx = L.d[0]; q.dy = L.d[1]; q.dz = L.d[2];
+                    q.E = L.E;
+                    q.nx = fnx; q.ny = fny;
+                    q.step = L.step;
+                    q.item = L.item;
+                    q.g = L.g;
+                    P.sq[slot] = q;
+                } else {
+                    atomicOr(P.status, 4);          // query buffer too small (host sizes it to the batch)
+                }
+                alive = false;
+            }
+        }
         // ---- exact wall hit and wall distance (warp-cooperative) ----
         const float sw = coop_first_wall_hit(need_hit, L.p[0], L.p[1], L.d[0], L.d[1], poly, q_off, q_n, lane);
         const float dw = coop_wall_distance(need_dist, L.p[0], L.p[1], poly, q_off, q_n, lane);
@@ -653,6 +760,8 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                         for (int k = 0; k < 3; ++k) L.p[k] = fmaf(s_geom, L.d[k], L.p[k]);
                         if (down) advance = true; else fate = kLeak;
                     }
+                } else if (sur_emit) {
+                    // handed to the surrogate below
                 } else {
                     L.forced = 0;
                     if (need_dist) absorb = rmax < dw;
@@ -698,7 +807,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                         for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
                         L.R = range_of(brass.Rt, L.E);
                         L.stage = 1;
-                        L.forced = 0;
+                        L.forced = -1;              // on the entrance plane
                     }
                 } else {
                     handoff = true;                 // leaves the beam line: on to the patient kernel
@@ -713,10 +822,34 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                     bev_to_patient(B, scens[__ldg(&I.scen)], L.p, pos);
                     write_record(P, L, fate, pos, 0ull);
                 }
+                if (kTrack && L.g < P.total) {
+                    P.trk_label[L.g] = 0;
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) P.trk_y[5 * L.g + k] = 0.0f;
+                }
                 alive = false;
             }
         }
         // ---- hand-off of the histories that left the beam line (one atomic per warp) ----
+        if (kTrack) {
+            if (handoff) {
+                // training track: targets from the exit state against the entry frame
+                const DevBeam& B = beams[__ldg(&P.items[L.item].beam)];
+                const float T = B.ap_tdn - B.ap_tup;
+                const float* fr = P.trk_frame + 8 * L.g;
+                const float nx = fr[3], ny = fr[4], un = fr[5], ut = fr[6], E0 = fr[7];
+                const float dx = L.p[0] - fr[0], dy = L.p[1] - fr[1];
+                float* y = P.trk_y + 5 * L.g;
+                y[0] = 5.0f * (E0 - L.E) / E0;
+                y[1] = dx * nx + dy * ny - T * un / fr[2];
+                y[2] = dy * nx - dx * ny - T * ut / fr[2];
+                y[3] = (L.d[0] * nx + L.d[1] * ny - un) * (1.0f / sur::kDirScale);
+                y[4] = (L.d[1] * nx - L.d[0] * ny - ut) * (1.0f / sur::kDirScale);
+                P.trk_label[L.g] = 1;
+                alive = false;
+            }
+            handoff = false;
+        }
         const unsigned hmask = __ballot_sync(kFull, handoff);
         if (hmask) {
             unsigned long long base = 0;
@@ -969,17 +1102,29 @@ size_t patient_smem_bytes() { return PatientSmem::Bytes; }
 int devices_max_block() { return 640; }
 int patient_max_block() { return 768; }
 
-cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaStream_t s)
+template <int kMode>
+static cudaError_t launch_devices_mode(const TransportParams& p, int grid, int block, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_devices, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_devices<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)DevicesSmem::Bytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_devices<<<grid, block, DevicesSmem::Bytes, s>>>(p);
+    k_devices<kMode><<<grid, block, DevicesSmem::Bytes, s>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaStream_t s)
+{
+    const int mode = (p.surrogate ? 1 : 0) | (p.track_mode ? 2 : 0);
+    switch (mode) {
+    case 1: return launch_devices_mode<1>(p, grid, block, s);
+    case 2: return launch_devices_mode<2>(p, grid, block, s);
+    case 3: return launch_devices_mode<3>(p, grid, block, s);
+    default: return launch_devices_mode<0>(p, grid, block, s);
+    }
 }
 
 cudaError_t launch_patient(const TransportParams& p, int grid, int block, cudaStream_t s)

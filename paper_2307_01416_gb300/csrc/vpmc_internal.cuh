@@ -49,6 +49,7 @@ struct DevBeam {
     float ras_lo[2], ras_inv[2];     // raster origin and 1/cell size
     int ras_off;                     // offset into the raster arrays (class bytes, distance bounds)
     float ras_diag;                  // raster cell diagonal
+    float r_circ;                    // largest vertex distance from the beam axis (training tracks)
 };
 
 struct DevScen {
@@ -98,6 +99,44 @@ struct PhaseRec {
     long long g;                     // global history index
 };
 
+// ---- learned aperture surrogate (not in the paper: a network drawing the
+// state on the block's exit plane in place of in-brass stepping) ----
+namespace sur {
+constexpr int kIn = 6, kInPad = 16, kH = 128, kOut = 45, kOutPad = 48, kNComp = 4, kDY = 5;
+// FP32 parameter vector: W1 [128 x 6], b1, W2 [128 x 128], b2, W3 [45 x 128], b3 (row-major, out x in)
+constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
+              ob3 = oW3 + kOut * kH;
+constexpr int kNParams = ob3 + kOut;
+// BF16 operand images in the canonical no-swizzle K-major layout of the
+// tensor-core instructions (byte offsets): W1 [128 x 16], W2 [128 x 128],
+// W3 [48 x 128], and the transposes W2^T [128 x 128], W3^T [128 x 48].
+constexpr int kImgW1 = 0;
+constexpr int kImgW2 = kImgW1 + kH * kInPad * 2;
+constexpr int kImgW3 = kImgW2 + kH * kH * 2;
+constexpr int kImgW2T = kImgW3 + kOutPad * kH * 2;
+constexpr int kImgW3T = kImgW2T + kH * kH * 2;
+constexpr int kImgBytes = kImgW3T + kH * kOutPad * 2;
+// Input and target scales, training domain.
+constexpr float kDCap = 12.0f;       // mm: edge distance clip
+constexpr float kELo = 70.0f, kEHi = 230.0f;
+constexpr float kAngSigma = 0.04f, kAngMax = 0.12f;
+constexpr float kDirScale = 0.05f;
+constexpr float kSMin = -8.0f, kSMax = 4.0f;
+constexpr float kThickness = 30.0f;  // block thickness of the training geometries, mm
+constexpr float kKappaLo = -1e-3f, kKappaHi = 0.26f;
+}  // namespace sur
+
+// One proton handed from the beam-line kernel to the surrogate: its state on
+// the block's entrance plane and its edge frame.
+struct SurQuery {
+    float x[6];                      // network inputs
+    float px, py, dx, dy, dz, E;     // BEV position (entrance plane), direction, energy
+    float nx, ny;                    // unit vector from the nearest edge point into the brass
+    uint32_t step;
+    int item;
+    long long g;
+};
+
 struct HistRecord {                  // mirrors vpmc_history_record
     long long q_dep;
     int fate;
@@ -144,6 +183,19 @@ struct TransportParams {
     float fscale;                    // 2^F
     int aggregate;
     int chunk;
+    // learned aperture surrogate
+    int surrogate;                   // brass entries in its domain become queries
+    SurQuery* sq;
+    unsigned long long* sq_count;
+    long long sq_cap;
+    const float* poly_kappa;         // per polygon vertex: signed curvature, 1/mm
+    // training tracks: histories start on the aperture entrance plane and
+    // record the surrogate's inputs and targets, indexed by global history
+    int track_mode;
+    float* trk_feat;                 // [n x 6]
+    float* trk_y;                    // [n x 5]
+    int* trk_label;                  // [n]
+    float* trk_frame;                // [n x 8] entry: x, y, w, n_x, n_y, u_n, u_t, E
 };
 
 // Shared-memory layouts of the two transport kernels.
@@ -176,6 +228,25 @@ size_t devices_smem_bytes();
 size_t patient_smem_bytes();
 int patient_max_block();
 int devices_max_block();
+
+// Learned aperture surrogate (surrogate.cu).
+struct SurNet {
+    float* params;                   // FP32 master parameters [kNParams]
+    float* grad;                     // [kNParams]
+    float* m;                        // Adam moments
+    float* v;
+    unsigned char* img;              // BF16 operand images [kImgBytes]
+    double* loss;                    // [2]: summed loss, rows
+    int* status;                     // bit 0: a tensor-core wait timed out
+};
+cudaError_t launch_sur_pack(const SurNet& net, cudaStream_t s);
+cudaError_t launch_sur_forward(const SurNet& net, const float* x, long long n, float* z, int grid, cudaStream_t s);
+cudaError_t launch_sur_train(const SurNet& net, const float* x, const float* y, const int* label, long long first,
+                             long long rows, long long n, float inv_rows, int grid, cudaStream_t s);
+cudaError_t launch_sur_adam(const SurNet& net, int step, float lr, cudaStream_t s);
+cudaError_t launch_sur_infer(const SurNet& net, const TransportParams& p, int grid, cudaStream_t s);
+size_t sur_forward_smem_bytes();
+size_t sur_train_smem_bytes();
 
 cudaError_t launch_scoring_density(const int16_t* ct, Grid3 ctg, Grid3 sg, const double* curve15_dev,
                                    const double ct_spacing[3], const double sg_spacing[3], double* rho_out,

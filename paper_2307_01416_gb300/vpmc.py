@@ -62,7 +62,7 @@ class vpmc_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("mcs", C.c_int), ("straggling", C.c_int), ("nuclear", C.c_int),
                 ("frac_bits", C.c_int), ("aggregate", C.c_int), ("block_size", C.c_int),
                 ("blocks_per_sm", C.c_int), ("chunk", C.c_int), ("history_out", C.c_void_p),
-                ("history_cap", C.c_int64), ("range_rejection", C.c_int)]
+                ("history_cap", C.c_int64), ("range_rejection", C.c_int), ("surrogate", C.c_int)]
 
 
 class vpmc_stats(C.Structure):
@@ -82,7 +82,12 @@ RECORD_DTYPE = np.dtype([("q_dep", np.int64), ("fate", np.int32), ("steps", np.i
 assert RECORD_DTYPE.itemsize == 40
 
 EXPORTED = ["vpmc_default_opts", "vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots",
-            "vpmc_run_spots_noalloc", "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_destroy", "vpmc_last_error"]
+            "vpmc_run_spots_noalloc", "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_destroy", "vpmc_last_error",
+            "vpmc_surrogate_init", "vpmc_surrogate_set_weights", "vpmc_surrogate_get_weights",
+            "vpmc_surrogate_tracks", "vpmc_surrogate_forward", "vpmc_surrogate_gradient", "vpmc_surrogate_train"]
+
+SUR_NPARAMS = 23213            # VPMC_SUR_NPARAMS
+SUR_IN, SUR_OUT, SUR_Y = 6, 45, 5
 
 _lib = None
 
@@ -113,8 +118,19 @@ def lib():
     L.vpmc_free_csr.argtypes = [C.POINTER(vpmc_csr), C.c_int]
     L.vpmc_destroy.argtypes = [vp]
     L.vpmc_destroy.restype = None
+    fp = C.POINTER(C.c_float)
+    L.vpmc_surrogate_init.argtypes = [vp, C.c_uint64]
+    L.vpmc_surrogate_set_weights.argtypes = [vp, fp]
+    L.vpmc_surrogate_get_weights.argtypes = [vp, fp]
+    L.vpmc_surrogate_tracks.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.c_int64, C.POINTER(vpmc_opts), C.c_int,
+                                        vp, vp, vp]
+    L.vpmc_surrogate_forward.argtypes = [vp, vp, C.c_int64, vp]
+    L.vpmc_surrogate_gradient.argtypes = [vp, vp, vp, vp, C.c_int64, vp, C.POINTER(C.c_double)]
+    L.vpmc_surrogate_train.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_float, fp]
     for f in ("vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots", "vpmc_run_spots_noalloc",
-              "vpmc_influence_matrix", "vpmc_free_csr"):
+              "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_surrogate_init", "vpmc_surrogate_set_weights",
+              "vpmc_surrogate_get_weights", "vpmc_surrogate_tracks", "vpmc_surrogate_forward",
+              "vpmc_surrogate_gradient", "vpmc_surrogate_train"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -141,6 +157,7 @@ def make_opts(o: W.Options, aggregate: int = -1, block_size: int = 0, chunk: int
         int(o.frac_bits)
     v.aggregate, v.block_size, v.chunk = aggregate, block_size, chunk
     v.range_rejection = int(getattr(o, "range_rejection", True))
+    v.surrogate = int(getattr(o, "surrogate", False))
     return v
 
 
@@ -255,6 +272,59 @@ class Engine:
             lib().vpmc_free_csr(out, len(scenarios))
         return mats, _stats_dict(st)
 
+    # ---------------------------------------------------- learned aperture surrogate
+    def surrogate_init(self, seed: int = 0):
+        _check(lib().vpmc_surrogate_init(self._ctx, int(seed)))
+
+    def surrogate_set_weights(self, params: np.ndarray):
+        w = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if w.size != SUR_NPARAMS:
+            raise ValueError("expected %d parameters, got %d" % (SUR_NPARAMS, w.size))
+        _check(lib().vpmc_surrogate_set_weights(self._ctx, w.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def surrogate_get_weights(self) -> np.ndarray:
+        w = np.zeros(SUR_NPARAMS, dtype=np.float32)
+        _check(lib().vpmc_surrogate_get_weights(self._ctx, w.ctypes.data_as(C.POINTER(C.c_float))))
+        return w
+
+    def surrogate_tracks(self, beam_ids: Sequence[int], tracks_per_beam: int, opts: Optional[W.Options] = None,
+                         use_surrogate: bool = False):
+        """Training (plain transport) or evaluation (network draws) tracks:
+        device tensors feat (n, 6), target (n, 5), label (n,) int32."""
+        torch = self.torch
+        n = len(beam_ids) * int(tracks_per_beam)
+        feat = torch.empty((n, SUR_IN), dtype=torch.float32, device=self.device)
+        target = torch.empty((n, SUR_Y), dtype=torch.float32, device=self.device)
+        label = torch.empty(n, dtype=torch.int32, device=self.device)
+        ids = (C.c_int * len(beam_ids))(*[int(b) for b in beam_ids])
+        o = make_opts(opts or W.Options(seed=W.SURROGATE_SEED))
+        _check(lib().vpmc_surrogate_tracks(self._ctx, ids, len(beam_ids), int(tracks_per_beam), C.byref(o),
+                                           int(use_surrogate), C.c_void_p(feat.data_ptr()),
+                                           C.c_void_p(target.data_ptr()), C.c_void_p(label.data_ptr())))
+        return feat, target, label
+
+    def surrogate_forward(self, feat):
+        z = self.torch.empty((feat.shape[0], SUR_OUT), dtype=self.torch.float32, device=self.device)
+        _check(lib().vpmc_surrogate_forward(self._ctx, C.c_void_p(feat.data_ptr()), int(feat.shape[0]),
+                                            C.c_void_p(z.data_ptr())))
+        return z
+
+    def surrogate_gradient(self, feat, target, label):
+        g = self.torch.empty(SUR_NPARAMS, dtype=self.torch.float32, device=self.device)
+        loss = C.c_double()
+        _check(lib().vpmc_surrogate_gradient(self._ctx, C.c_void_p(feat.data_ptr()), C.c_void_p(target.data_ptr()),
+                                             C.c_void_p(label.data_ptr()), int(feat.shape[0]),
+                                             C.c_void_p(g.data_ptr()), C.byref(loss)))
+        return g, loss.value
+
+    def surrogate_train(self, feat, target, label, batch: int = 8192, epochs: int = 1, lr: float = 1e-3,
+                        lr_min: float = 1e-5) -> np.ndarray:
+        losses = np.zeros(int(epochs), dtype=np.float32)
+        _check(lib().vpmc_surrogate_train(self._ctx, C.c_void_p(feat.data_ptr()), C.c_void_p(target.data_ptr()),
+                                          C.c_void_p(label.data_ptr()), int(feat.shape[0]), int(batch), int(epochs),
+                                          float(lr), float(lr_min), losses.ctypes.data_as(C.POINTER(C.c_float))))
+        return losses
+
     def close(self):
         if self._ctx:
             lib().vpmc_destroy(self._ctx)
@@ -292,3 +362,28 @@ def _csr_to_torch(m: vpmc_csr, device):
             out[name] = torch.as_tensor(_DeviceView(ptr, n, ts), device=device).clone()
     out["shape"] = (int(m.n_rows), int(m.n_cols))
     return out
+
+
+def surrogate_training_problem(radii=W.SURROGATE_RADII) -> W.Problem:
+    """A small water phantom with the surrogate's training geometries as its
+    beams (aperture only); the tracks never reach the phantom."""
+    g, hu = W.water_phantom((8, 8, 8), (2.0, 2.0, 2.0), (-8.0, -8.0, 0.0))
+    return W.Problem(ct=g, hu=hu, curve=W.HUCurve(), scoring=g, beams=W.surrogate_training_beams(radii))
+
+
+def train_surrogate(tracks_per_beam: int = 2_000_000, epochs: int = 4, batch: int = 16384, lr: float = 2e-3,
+                    lr_min: float = 2e-5, seed: int = W.SURROGATE_SEED, init_seed: int = 7, engine: "Engine" = None):
+    """Generate training tracks with the plain aperture transport and train the
+    network on the GPU.  Returns (parameters float32[SUR_NPARAMS], per-epoch
+    mean losses)."""
+    own = engine is None
+    eng = engine or Engine(surrogate_training_problem())
+    try:
+        nb = len(eng.problem.beams)
+        feat, target, label = eng.surrogate_tracks(list(range(nb)), tracks_per_beam, W.Options(seed=seed))
+        eng.surrogate_init(init_seed)
+        losses = eng.surrogate_train(feat, target, label, batch=batch, epochs=epochs, lr=lr, lr_min=lr_min)
+        return eng.surrogate_get_weights(), losses
+    finally:
+        if own:
+            eng.close()

@@ -1,0 +1,210 @@
+"""GPU (C-ABI) vs FP64 oracle parity of the learned aperture surrogate: the
+tensor-core forward and backward, one Adam step, the training-track
+generator, and the network's draws; then training on the GPU.
+
+Tolerances: the kernels hold weights and activations in BF16 and sum in FP32;
+the oracle rounds the same operands to BF16 and sums in FP64, so the outputs
+and gradients agree to within a few BF16 roundings (1e-2 relative)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import surrogate_oracle as S
+from paper_2307_01416_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_2307_01416_gb300 import vpmc
+    e = vpmc.Engine(vpmc.surrogate_training_problem())
+    yield e
+    e.close()
+
+
+def _flat(P):
+    return np.concatenate([P[k].reshape(-1) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]).astype(np.float32)
+
+
+def _unflat(w):
+    out, o = {}, 0
+    for k, shape in (("W1", (128, 6)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (45, 128)),
+                     ("b3", (45,))):
+        n = int(np.prod(shape))
+        out[k] = w[o:o + n].astype(np.float64).reshape(shape)
+        o += n
+    assert o == w.size
+    return out
+
+
+def _params(seed):
+    P = S.init_params(seed)
+    g = np.random.default_rng(seed + 100)
+    for k in ("b1", "b2", "b3"):
+        P[k] = g.standard_normal(P[k].shape) * 0.1
+    P["W3"] *= 10.0
+    # round-trip through FP32: the oracle sees exactly the parameters the GPU holds
+    return _unflat(_flat(P))
+
+
+def _batch(n, seed):
+    g = np.random.default_rng(seed)
+    x = np.clip(g.standard_normal((n, 6)), -3, 3).astype(np.float32)
+    t = (g.random(n) < 0.6).astype(np.int32)
+    y = (g.standard_normal((n, 5)) * 1.5 * t[:, None]).astype(np.float32)
+    return x, t, y
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_forward_matches_oracle(eng):
+    import torch
+    P = _params(1)
+    eng.surrogate_set_weights(_flat(P))
+    for n in (1, 127, 128, 1000, 40000):          # ragged tails and several tiles per CTA
+        x, _, _ = _batch(n, 2 + n)
+        z = eng.surrogate_forward(_dev(torch, x)).cpu().numpy().astype(np.float64)
+        zo, _ = S.forward(P, x.astype(np.float64), bf16_ops=True)
+        err = np.abs(z - zo) / np.maximum(np.abs(zo), 1.0)
+        assert err.max() < 1e-2, (n, err.max())
+        # the BF16 model is the right reference: unrounded FP64 differs far more
+        zf, _ = S.forward(P, x.astype(np.float64), bf16_ops=False)
+        if n >= 1000:
+            assert np.abs(z - zo).mean() < 0.5 * np.abs(z - zf).mean()
+
+
+def test_gradient_matches_oracle(eng):
+    import torch
+    P = _params(3)
+    eng.surrogate_set_weights(_flat(P))
+    n = 152 * 128 * 2 + 77                          # 2-3 tiles per CTA: tensor-memory accumulation
+    x, t, y = _batch(n, 4)
+    g, loss = eng.surrogate_gradient(_dev(torch, x), _dev(torch, y), _dev(torch, t))
+    g = g.cpu().numpy().astype(np.float64)
+    xo, to, yo = x.astype(np.float64), t.astype(np.float64), y.astype(np.float64)
+    z, cache = S.forward(P, xo, bf16_ops=True)
+    assert loss == pytest.approx(S.loss(z, to, yo), rel=2e-3)
+    G = S.backward(cache, S.loss_grad(z, to, yo), bf16_ops=True)
+    Gg = _unflat(g.astype(np.float32))
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a, b = Gg[k].reshape(-1), G[k].reshape(-1)
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel < 1e-2, (k, rel)
+
+
+def test_adam_step_matches_oracle(eng):
+    import torch
+    P = _params(5)
+    w0 = _flat(P)
+    eng.surrogate_set_weights(w0)
+    n = 4096
+    x, t, y = _batch(n, 6)
+    lr = 1e-3
+    eng.surrogate_train(_dev(torch, x), _dev(torch, y), _dev(torch, t), batch=n, epochs=1, lr=lr, lr_min=lr)
+    w1 = eng.surrogate_get_weights().astype(np.float64)
+    z, cache = S.forward(P, x.astype(np.float64), bf16_ops=True)
+    G = S.backward(cache, S.loss_grad(z, t.astype(np.float64), y.astype(np.float64)), bf16_ops=True)
+    Q = {k: v.copy() for k, v in P.items()}
+    M = {k: np.zeros_like(v) for k, v in P.items()}
+    V = {k: np.zeros_like(v) for k, v in P.items()}
+    S.adam_step(Q, G, M, V, 1, lr)
+    d_gpu = w1 - w0.astype(np.float64)
+    d_orc = _flat(Q).astype(np.float64) - w0.astype(np.float64)
+    gflat = np.concatenate([G[k].reshape(-1) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+    # first step: -lr g / (|g| + eps); compare where the gradient's sign is clear
+    clear = np.abs(gflat) > 2e-2 * np.abs(gflat).max()
+    assert clear.sum() > 1000
+    np.testing.assert_allclose(d_gpu[clear], d_orc[clear], atol=2e-6)
+    assert np.all(np.abs(d_gpu) <= lr * 1.0001 + 1e-7)
+
+
+DET = W.Options(seed=4321, mcs=False, straggling=False, nuclear=True)
+
+
+def test_track_generator_matches_oracle_deterministic(eng):
+    n = 3000
+    feat, target, label = eng.surrogate_tracks(list(range(8)), n, DET)
+    feat, target, label = feat.cpu().numpy(), target.cpu().numpy(), label.cpu().numpy()
+    r = O.surrogate_tracks(W.surrogate_training_beams(), n, DET)
+    flagged = (r["flags"] & (1 | 16)) != 0
+    assert flagged.mean() < 0.02
+    ok = ~flagged
+    np.testing.assert_allclose(feat[ok], r["feat"][ok], atol=2e-4, rtol=0)
+    mism = np.flatnonzero((label != r["label"]) & ok)
+    assert mism.size <= 2, mism[:10]
+    both = ok & (label == 1) & (r["label"] == 1)
+    np.testing.assert_allclose(target[both], r["target"][both], atol=2e-3, rtol=0)
+
+
+def test_track_generator_full_physics_statistics(eng):
+    op = W.Options(seed=4321)
+    n = 20000
+    feat, target, label = eng.surrogate_tracks(list(range(8)), n, op)
+    label = label.cpu().numpy()
+    target = target.cpu().numpy()
+    r = O.surrogate_tracks(W.surrogate_training_beams(), 4000, W.Options(seed=99))
+    p_g, p_o = label.mean(), r["label"].mean()
+    se = math.sqrt(p_o * (1 - p_o) * (1 / label.size + 1 / r["label"].size))
+    assert abs(p_g - p_o) < 5 * se
+    tg, to = target[label == 1], r["target"][r["label"] == 1]
+    for j in range(5):
+        se = math.sqrt(tg[:, j].var() / len(tg) + to[:, j].var() / len(to))
+        assert abs(tg[:, j].mean() - to[:, j].mean()) < 5 * se + 1e-3, j
+
+
+def test_network_draws_match_oracle(eng):
+    """Evaluation tracks: the entry, the network and the draw (Philox slots 4
+    and 5 at the entry step) against the oracle's features, network and
+    sampler.  Decisions within 1e-3 of a threshold may differ."""
+    P = _params(7)
+    P["b3"][0] = 0.3
+    eng.surrogate_set_weights(_flat(P))
+    n = 2000
+    beams = W.surrogate_training_beams()
+    _, yg, lg = eng.surrogate_tracks(list(range(8)), n, DET, use_surrogate=True)
+    yg, lg = yg.cpu().numpy().astype(np.float64), lg.cpu().numpy()
+    r = O.surrogate_tracks(beams, n, DET)
+    z, _ = S.forward(P, r["feat"], bf16_ops=True)
+    N = len(lg)
+    u = np.zeros((N, 8))
+    for i in range(N):
+        key = [4321, i // n]
+        a = O.philox4x32_10([i % n, 0, 4, 0], key)
+        b = O.philox4x32_10([i % n, 0, 5, 0], key)
+        u[i] = [O.uniform(v) for v in list(a) + list(b)]
+    trans, comp, yo = S.sample(z, u)
+    logit, alpha, _, _ = S.split(z)
+    p = 1.0 / (1.0 + np.exp(-logit))
+    pi = np.exp(alpha - alpha.max(1, keepdims=True))
+    cum = np.cumsum(pi / pi.sum(1, keepdims=True), axis=1)
+    clear_t = np.abs(u[:, 0] - p) > 1e-3
+    clear_c = np.min(np.abs(u[:, 1:2] - cum[:, :3]), axis=1) > 1e-3
+    flagged = (r["flags"] & 1) != 0
+    ok = clear_t & ~flagged
+    assert ok.mean() > 0.97
+    np.testing.assert_array_equal(lg[ok], trans[ok].astype(np.int32))
+    sel = ok & clear_c & trans
+    assert sel.sum() > 500
+    err = np.abs(yg[sel] - yo[sel]) / np.maximum(np.abs(yo[sel]), 1.0)
+    assert err.max() < 2e-2, err.max()
+
+
+def test_training_reduces_loss(eng):
+    op = W.Options(seed=4321)
+    feat, target, label = eng.surrogate_tracks(list(range(8)), 25000, op)
+    eng.surrogate_init(11)
+    g0, loss0 = eng.surrogate_gradient(feat, target, label)
+    losses = eng.surrogate_train(feat, target, label, batch=4096, epochs=4, lr=2e-3, lr_min=1e-4)
+    _, loss1 = eng.surrogate_gradient(feat, target, label)
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < losses[0]
+    assert loss1 < 0.5 * loss0, (loss0, loss1, losses)
