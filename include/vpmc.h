@@ -230,7 +230,7 @@ vpmc_status vpmc_free_csr(vpmc_csr* csr, int n);
  * and energy E.  n is the unit vector from the nearest boundary point of the
  * opening to the proton; t = (-n_y, n_x).
  *   x0 = min(dist, 12 mm) / 6 mm - 1
- *   x1 = (E - 150 MeV) / 80 MeV
+ *   x1 = (E - 135 MeV) / 95 MeV
  *   x2 = (d . n) / 0.04,  x3 = (d . t) / 0.04
  *   x4 = 8 mm x (boundary curvature there) - 1
  *   x5 = (brass CSDA range of E) / (block thickness) - 1
@@ -239,7 +239,7 @@ vpmc_status vpmc_free_csr(vpmc_csr* csr, int n);
  *   y1 = (exit - entry) . n - T (d_in . n) / d_in,z
  *   y2 = (exit - entry) . t - T (d_in . t) / d_in,z
  *   y3 = (d_out - d_in) . n / 0.05,  y4 = (d_out - d_in) . t / 0.05
- * Training domain: E in [70, 230] MeV, |d . n| and |d . t| <= 0.12,
+ * Training domain: E in [40, 230] MeV, |d . n| and |d . t| <= 0.12,
  * curvature in [-0.001, 0.26] / mm, block thickness 30 mm.  With
  * opts->surrogate = 1, a brass entry outside this domain takes the plain
  * path.  A brass entry whose 1.2 x CSDA range is below both its edge distance
@@ -264,7 +264,7 @@ vpmc_status vpmc_surrogate_get_weights(vpmc_ctx* ctx, float* params);
  * its entrance plane near the opening.  Track h of list entry g is global
  * index i = g * tracks_per_beam + h, with Philox key (seed low word,
  * g ^ seed high word).  Its start, from counter (h, 0, slot, 0):
- *   slot 0: E = 70 + 160 u0 MeV, angle phi = 2 pi u1, edge distance d = d_hi u2,
+ *   slot 0: E = 40 + 190 u0 MeV, angle phi = 2 pi u1, edge distance d = d_hi u2,
  *           where d_hi = min(12 mm, 1.2 R) if 1.2 x brass CSDA range R is
  *           below the thickness, else 12 mm; the proton starts at radius
  *           r_c + d at angle phi, r_c the largest vertex radius;

@@ -889,7 +889,7 @@ int orc_run(const orc_grid* ct, const int16_t* hu, const orc_curve* curve, const
  * from the plain aperture transport above; parity of the learned part is
  * pinned by that plain path (its dose), not by the paper. */
 #define SUR_DCAP 12.0        /* mm: edge distance beyond which it is clipped     */
-#define SUR_E_LO 70.0        /* MeV: training energies U(E_LO, E_HI)              */
+#define SUR_E_LO 40.0        /* MeV: training energies U(E_LO, E_HI)              */
 #define SUR_E_HI 230.0
 #define SUR_ANG_SIGMA 0.04   /* incidence direction cosines N(0, s^2) ...         */
 #define SUR_ANG_MAX 0.12     /* ... clamped to +-ANG_MAX                           */

@@ -118,7 +118,7 @@ constexpr int kImgW3T = kImgW2T + kH * kH * 2;
 constexpr int kImgBytes = kImgW3T + kH * kOutPad * 2;
 // Input and target scales, training domain.
 constexpr float kDCap = 12.0f;       // mm: edge distance clip
-constexpr float kELo = 70.0f, kEHi = 230.0f;
+constexpr float kELo = 40.0f, kEHi = 230.0f;
 constexpr float kAngSigma = 0.04f, kAngMax = 0.12f;
 constexpr float kDirScale = 0.05f;
 constexpr float kSMin = -8.0f, kSMax = 4.0f;

@@ -135,8 +135,13 @@ def test_track_generator_matches_oracle_deterministic(eng):
     feat, target, label = eng.surrogate_tracks(list(range(8)), n, DET)
     feat, target, label = feat.cpu().numpy(), target.cpu().numpy(), label.cpu().numpy()
     r = O.surrogate_tracks(W.surrogate_training_beams(), n, DET)
-    flagged = (r["flags"] & (1 | 16)) != 0
-    assert flagged.mean() < 0.02
+    # a step start within 10 um of a wall (flag 1) makes the brass chord, and
+    # the edge frame of a start on the wall, ill-conditioned in FP32.  A
+    # range-rejection tie (flag 16) changes only the step count: with 1.2 x
+    # the residual range on either side of the threshold the proton cannot
+    # leave the block whichever way the tie goes, so labels and targets stay.
+    flagged = (r["flags"] & 1) != 0
+    assert flagged.mean() < 0.05
     ok = ~flagged
     np.testing.assert_allclose(feat[ok], r["feat"][ok], atol=2e-4, rtol=0)
     mism = np.flatnonzero((label != r["label"]) & ok)

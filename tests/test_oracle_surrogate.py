@@ -216,7 +216,7 @@ def test_features_straight_edge_closed_form():
     f, fr = O.surrogate_features(sq, 30.0, 43.0, 5.0, dvec, E)
     assert fr == pytest.approx([1.0, 0.0, -0.03, 0.02])
     rmm = O.csda_range(2, E) / 8.53
-    assert f == pytest.approx([3.0 / 6.0 - 1.0, (120 - 150) / 80.0, -0.03 / 0.04, 0.02 / 0.04,
+    assert f == pytest.approx([3.0 / 6.0 - 1.0, (120 - 135) / 95.0, -0.03 / 0.04, 0.02 / 0.04,
                                8 * math.pi / 2 / 80.0 - 1.0, rmm / 30.0 - 1.0])
     # distance clipped at 12 mm
     f2, _ = O.surrogate_features(sq, 30.0, 60.0, 5.0, dvec, E)
@@ -232,8 +232,8 @@ def test_track_entry_distribution():
     beams = W.surrogate_training_beams()
     r = O.surrogate_tracks(beams, 4000, W.Options(seed=4321))
     f = r["feat"]
-    E = 150.0 + 80.0 * f[:, 1]
-    assert st.kstest((E - 70.0) / 160.0, "uniform").pvalue > 1e-3
+    E = 135.0 + 95.0 * f[:, 1]
+    assert st.kstest((E - 40.0) / 190.0, "uniform").pvalue > 1e-3
     # incidence angles: N(0, 0.04^2) clamped at 0.12 -> features N(0, 1) clamped at 3
     for j in (2, 3):
         inner = f[np.abs(f[:, j]) < 2.9, j]
@@ -269,14 +269,14 @@ def test_tracks_deterministic_straight_lines():
     for i in idx:
         bm = beams[i // n]
         poly = bm.polygon
-        E = 150.0 + 80.0 * f[i, 1]
+        E = 135.0 + 95.0 * f[i, 1]
         if (r["flags"][i] & (1 | 16)) != 0:
             continue
         # entry point: reconstruct from the generator's definition via the oracle's Philox
         key = [4321 & 0xFFFFFFFF, (4321 >> 32) ^ (i // n)]
         h = i % n
         u = [O.uniform(v) for v in O.philox4x32_10([h, 0, 0, 0], key)]
-        assert E == pytest.approx(70.0 + 160.0 * u[0], rel=1e-12)
+        assert E == pytest.approx(40.0 + 190.0 * u[0], rel=1e-12)
         phi = 2 * math.pi * u[1]
         r12 = 1.2 * O.csda_range(2, E) / rho
         dhi = min(12.0, r12) if r12 < 30.0 else 12.0
