@@ -1,0 +1,67 @@
+"""Dose error of the learned aperture surrogate against the plain aperture
+transport (the learned part is pinned by the plain path, not by the paper).
+
+The network is trained on the GPU from plain training tracks, then each case
+runs plain and surrogate transport in 8 paired batches.  A pair shares its
+seed, so histories that never enter the brass are identical in both and the
+difference isolates the surrogate.  Inside the 10 % isodose (tissue voxels,
+density >= 0.5 g/cc) the largest voxel error of the batch mean must stay
+within 1 % of the maximum dose, the mean error within 0.5 %, and the
+2 %/2 mm/10 % gamma pass rate at or above 99.5 %."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2307_01416_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def weights():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_2307_01416_gb300 import vpmc
+    w, losses = vpmc.train_surrogate(tracks_per_beam=4_000_000, epochs=20, batch=16384, lr=2e-3, lr_min=2e-5)
+    assert np.all(np.isfinite(losses)) and losses[-1] < losses[0]
+    return w
+
+
+def _paired(pb, spots, w, nb=8, seed=4242):
+    from paper_2307_01416_gb300 import vpmc
+    e = vpmc.Engine(pb)
+    e.surrogate_set_weights(w)
+    refs, diffs, ms = [], [], []
+    for b in range(nb):
+        d0, s0, _ = e.run_spots(spots, W.Scenario(), W.Options(seed=seed + 17 * b))
+        d1, s1, _ = e.run_spots(spots, W.Scenario(), W.Options(seed=seed + 17 * b, surrogate=True))
+        a0 = d0.cpu().numpy().astype(np.float64)
+        refs.append(a0)
+        diffs.append(d1.cpu().numpy().astype(np.float64) - a0)
+        ms.append((s0["ms"], s1["ms"]))
+        assert s1["errors"] == 0
+    e.close()
+    D, dd = np.mean(refs, 0), np.mean(diffs, 0)
+    rho = O.scoring_density(pb).reshape(D.shape)
+    m = (D >= 0.1 * D.max()) & (rho >= 0.5)
+    dmax = D[m].max()
+    return {"max_err": np.abs(dd)[m].max() / dmax, "mean_err": dd[m].sum() / D[m].sum(),
+            "gamma": O.gamma_pass_rate(D, D + dd, pb.scoring.spacing), "ms": np.median(np.array(ms), 0)}
+
+
+def test_head_plan_dose_error(weights):
+    pb, spots, _, _ = W.head_plan(8.4)
+    r = _paired(pb, spots[::10], weights)
+    assert r["max_err"] <= 0.01, r
+    assert abs(r["mean_err"]) <= 0.005, r
+    assert r["gamma"] >= 99.5, r
+
+
+def test_water_aperture_dose_error(weights):
+    pb, spots = W.water_aperture_case(40.0, True, hist_per_layer=300_000)
+    r = _paired(pb, spots, weights)
+    assert r["max_err"] <= 0.01, r
+    assert abs(r["mean_err"]) <= 0.005, r
+    assert r["gamma"] >= 99.5, r
