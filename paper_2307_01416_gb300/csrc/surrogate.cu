@@ -377,7 +377,6 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
     fwd_prologue(sm, net, tbase);
     const int r = threadIdx.x;
     const int lane = r & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
     const uint32_t t_row = tbase + ((uint32_t)((r >> 5) * 32) << 16);
     const uint32_t bar = smem_addr(sm + FwdSmem::Bar);
     uint32_t phase = 0u;
@@ -465,17 +464,18 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
                 }
             }
         }
-        // hand the transmitted protons to the patient kernel (one atomic per warp)
-        const unsigned emask = __ballot_sync(kFull, emit);
-        if (emask) {
-            unsigned long long base = 0;
-            const int leader = __ffs(emask) - 1;
-            if (lane == leader) base = atomicAdd(P.phase_count, (unsigned long long)__popc(emask));
-            base = __shfl_sync(kFull, base, leader);
-            if (emit) {
-                const long long slot = (long long)base + __popc(emask & lt_mask);
-                if (slot < P.phase_cap) P.phase[slot] = rec;
-                else atomicOr(P.status, 2);
+        // hand-off into the slot the beam-line kernel reserved for this proton;
+        // an absorbed proton leaves the slot empty (item -1)
+        if (row < nq && !P.track_mode) {
+            const long long slot = P.sq[row].slot;
+            if (slot >= 0 && slot < P.phase_cap) {
+                if (!emit) {
+                    rec = PhaseRec{};
+                    rec.item = -1;
+                }
+                P.phase[slot] = rec;
+            } else {
+                atomicOr(P.status, 2);
             }
         }
     }

@@ -714,12 +714,19 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
             }
         }
         // ---- surrogate queries of the brass entries in its domain (one atomic per warp) ----
+        // Each query also reserves its hand-off slot now, in arrival order, so
+        // that the patient kernel meets the protons in the same order as on the
+        // plain path (the influence-matrix columns it scores into stay in L2).
         const unsigned smask = __ballot_sync(kFull, sur_emit);
         if (smask) {
-            unsigned long long base = 0;
+            unsigned long long base = 0, pbase = 0;
             const int leader = __ffs(smask) - 1;
-            if (lane == leader) base = atomicAdd(P.sq_count, (unsigned long long)__popc(smask));
+            if (lane == leader) {
+                base = atomicAdd(P.sq_count, (unsigned long long)__popc(smask));
+                if (!kTrack) pbase = atomicAdd(P.phase_count, (unsigned long long)__popc(smask));
+            }
             base = __shfl_sync(kFull, base, leader);
+            pbase = __shfl_sync(kFull, pbase, leader);
             if (sur_emit) {
                 const long long slot = (long long)base + __popc(smask & lt_mask);
                 if (slot < P.sq_cap) {
@@ -733,6 +740,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                     q.step = L.step;
                     q.item = L.item;
                     q.g = L.g;
+                    q.slot = kTrack ? -1ll : (long long)pbase + __popc(smask & lt_mask);
                     P.sq[slot] = q;
                 } else {
                     atomicOr(P.status, 4);          // query buffer too small (host sizes it to the batch)
@@ -943,51 +951,53 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
             const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
             if (mine) {
                 const PhaseRec r = P.phase[pool.next + __popc(need & lt_mask)];
-                const DevItem I = P.items[r.item];
-                L.item = r.item;
-                L.g = r.g;
-                L.hist = (uint32_t)(r.g - I.hist_off);
-                L.step = r.step;
-                L.iters = 0;
-                L.E = r.E;
-                L.nlam = r.nlam;
-                L.qdep = acc_dep;
-                key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
-                spr_scale = scens[I.scen].spr_scale;
-                bx = P.boxes[I.box];
-                wsc = I.wscale;
-                // ray / grid box entry
-                float tmin = -__int_as_float(0x7f800000), tmax = __int_as_float(0x7f800000);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float lo = P.ctg.lo[k], hi = P.ctg.lo[k] + P.ctg.n[k] * P.ctg.d[k];
-                    if (r.d[k] != 0.0f) {
-                        float t1 = (lo - r.p[k]) / r.d[k], t2 = (hi - r.p[k]) / r.d[k];
-                        if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
-                        tmin = fmaxf(tmin, t1);
-                        tmax = fminf(tmax, t2);
-                    } else if (r.p[k] < lo || r.p[k] > hi) {
-                        tmax = -__int_as_float(0x7f800000);
-                    }
-                }
-                const float tin = fmaxf(tmin, 0.0f);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { L.p[k] = r.p[k]; L.d[k] = r.d[k]; }
-                if (!(tmax > tin)) {
-                    // misses the grid
-                    acc_leak += __float2ull_rn(L.E * P.fscale);
-                    if (P.records && L.g < P.rec_cap) write_record(P, L, kLeak, L.p, acc_dep);
-                } else {
-#pragma unroll
+                if (r.item >= 0) {        // item -1: a slot the aperture surrogate left empty
+                    const DevItem I = P.items[r.item];
+                    L.item = r.item;
+                    L.g = r.g;
+                    L.hist = (uint32_t)(r.g - I.hist_off);
+                    L.step = r.step;
+                    L.iters = 0;
+                    L.E = r.E;
+                    L.nlam = r.nlam;
+                    L.qdep = acc_dep;
+                    key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
+                    spr_scale = scens[I.scen].spr_scale;
+                    bx = P.boxes[I.box];
+                    wsc = I.wscale;
+                    // ray / grid box entry
+                    float tmin = -__int_as_float(0x7f800000), tmax = __int_as_float(0x7f800000);
+    #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        L.p[k] = fmaf(tin, L.d[k], L.p[k]);
-                        const int a = (int)floorf((L.p[k] - P.ctg.lo[k]) / P.ctg.d[k]);
-                        L.ic[k] = min(max(a, 0), P.ctg.n[k] - 1);
-                        const int b = (int)floorf((L.p[k] - P.sg.lo[k]) / P.sg.d[k]);
-                        L.is[k] = min(max(b, 0), P.sg.n[k] - 1);
+                        const float lo = P.ctg.lo[k], hi = P.ctg.lo[k] + P.ctg.n[k] * P.ctg.d[k];
+                        if (r.d[k] != 0.0f) {
+                            float t1 = (lo - r.p[k]) / r.d[k], t2 = (hi - r.p[k]) / r.d[k];
+                            if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
+                            tmin = fmaxf(tmin, t1);
+                            tmax = fminf(tmax, t2);
+                        } else if (r.p[k] < lo || r.p[k] > hi) {
+                            tmax = -__int_as_float(0x7f800000);
+                        }
                     }
-                    L.R = range_of(water.Rt, L.E);
-                    alive = true;
+                    const float tin = fmaxf(tmin, 0.0f);
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) { L.p[k] = r.p[k]; L.d[k] = r.d[k]; }
+                    if (!(tmax > tin)) {
+                        // misses the grid
+                        acc_leak += __float2ull_rn(L.E * P.fscale);
+                        if (P.records && L.g < P.rec_cap) write_record(P, L, kLeak, L.p, acc_dep);
+                    } else {
+    #pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            L.p[k] = fmaf(tin, L.d[k], L.p[k]);
+                            const int a = (int)floorf((L.p[k] - P.ctg.lo[k]) / P.ctg.d[k]);
+                            L.ic[k] = min(max(a, 0), P.ctg.n[k] - 1);
+                            const int b = (int)floorf((L.p[k] - P.sg.lo[k]) / P.sg.d[k]);
+                            L.is[k] = min(max(b, 0), P.sg.n[k] - 1);
+                        }
+                        L.R = range_of(water.Rt, L.E);
+                        alive = true;
+                    }
                 }
             }
             pool.next += take;

@@ -95,7 +95,7 @@ struct PhaseRec {
     float p[3], d[3];
     float E, nlam;
     uint32_t step;                   // condensed-history steps so far (RNG counter)
-    int item;
+    int item;                        // -1: an empty slot (absorbed by the aperture surrogate)
     long long g;                     // global history index
 };
 
@@ -135,6 +135,7 @@ struct SurQuery {
     uint32_t step;
     int item;
     long long g;
+    long long slot;                  // hand-off slot reserved in arrival order (-1: none)
 };
 
 struct HistRecord {                  // mirrors vpmc_history_record

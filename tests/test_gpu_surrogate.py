@@ -204,9 +204,12 @@ def test_network_draws_match_oracle(eng):
     # incidence angles clamped at +-0.12 along the radial direction can project
     # to just over 0.12 on the polygon's edge normal: outside the domain, such
     # entries take the plain path (its label, not a draw)
-    inside = np.all(np.abs(r["feat"][:, 2:4]) < 2.99, axis=1)
+    a = np.abs(r["feat"][:, 2:4])                  # |u| / 0.04; the domain is |u| <= 0.12
+    edge = np.any(np.abs(a - 3.0) < 5e-3, axis=1)   # FP32 and FP64 may fall on either side
+    inside = np.all(a < 3.0, axis=1) & ~edge
+    outside = np.any(a > 3.0, axis=1) & ~edge
     assert inside.mean() > 0.99
-    np.testing.assert_array_equal(lg[~inside & ~flagged], r["label"][~inside & ~flagged])
+    np.testing.assert_array_equal(lg[outside & ~flagged], r["label"][outside & ~flagged])
     ok = clear_t & ~flagged & inside
     assert ok.mean() > 0.95
     np.testing.assert_array_equal(lg[ok], trans[ok].astype(np.int32))
