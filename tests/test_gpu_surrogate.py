@@ -213,12 +213,14 @@ def test_network_draws_match_oracle(eng):
     # an entry whose 1.2 x CSDA range is below both its edge distance and the
     # thickness is absorbed without a draw (the start radius is r_c + d, and a
     # polygon inscribed in that circle can be a little farther away than d)
-    dist = np.where(r["feat"][:, 0] < 1.0, (r["feat"][:, 0] + 1.0) * 6.0, np.inf)
+    clipped = r["feat"][:, 0] >= 1.0                 # edge distance >= 12 mm, value unknown
+    d_lo = np.where(clipped, 12.0, (r["feat"][:, 0] + 1.0) * 6.0)
+    d_hi = np.where(clipped, np.inf, d_lo)
     reach = 1.2 * (r["feat"][:, 5] + 1.0) * 30.0
-    gap = np.minimum(dist, 30.0) - reach
-    absorbed = gap > 1e-3
+    absorbed = reach < np.minimum(d_lo, 30.0) - 1e-3
+    drawn = reach > np.minimum(d_hi, 30.0) + 1e-3
     assert np.all(lg[absorbed] == 0)
-    ok = clear_t & ~flagged & inside & (gap < -1e-3)
+    ok = clear_t & ~flagged & inside & drawn
     assert ok.mean() > 0.95
     np.testing.assert_array_equal(lg[ok], trans[ok].astype(np.int32))
     sel = ok & clear_c & trans
