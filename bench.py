@@ -339,18 +339,51 @@ def run_ncu_case(args):
     return 0
 
 
+# algorithmic FLOPs per row of the surrogate network (6 -> 128 -> 128 -> 45):
+# forward 2 (6*128 + 128*128 + 128*45); a training row adds the backward GEMMs
+# dh2, dW3, dh1, dW2 (with db2) and dW1 (with db1)
+SUR_FWD_FLOP = 2 * (6 * 128 + 128 * 128 + 128 * 45)
+SUR_TRAIN_FLOP = SUR_FWD_FLOP + 2 * (45 * 128 + 45 * 128 + 128 * 128 + 128 * 129 + 128 * 7)
+
+
 def surrogate_leg(pb, spots, scens, opts, args, plain_value):
     """The same set with the learned aperture surrogate: the network is
     trained on the GPU first (plain training tracks, Adam; not timed), then
-    one warm-up set and min(steps, 2) timed sets with opts.surrogate."""
+    one warm-up set and min(steps, 2) timed sets with opts.surrogate.  Also
+    the throughput of the tensor-core forward and training kernels."""
     import dataclasses
     import torch
     from paper_2307_01416_gb300 import vpmc
-    tpb, epochs = 4_000_000, 20
+    tpb, epochs, batch = 4_000_000, 20, 16384
+    tr = vpmc.Engine(vpmc.surrogate_training_problem())
     t0 = time.perf_counter()
-    w, losses = vpmc.train_surrogate(tracks_per_beam=tpb, epochs=epochs, batch=16384, lr=2e-3, lr_min=2e-5)
+    feat, target, label = tr.surrogate_tracks(list(range(8)), tpb, W.Options(seed=W.SURROGATE_SEED))
     torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    gen_s = time.perf_counter() - t0
+    tr.surrogate_init(7)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    losses = tr.surrogate_train(feat, target, label, batch=batch, epochs=epochs, lr=2e-3, lr_min=2e-5)
+    ev1.record()
+    torch.cuda.synchronize()
+    train_s = ev0.elapsed_time(ev1) / 1000.0
+    rows = float(feat.shape[0]) * epochs
+    x = feat[: 1 << 22].contiguous()
+    tr.surrogate_forward(x)
+    ev0.record()
+    for _ in range(5):
+        tr.surrogate_forward(x)
+    ev1.record()
+    torch.cuda.synchronize()
+    fwd_s = ev0.elapsed_time(ev1) / 1000.0 / 5
+    w = tr.surrogate_get_weights()
+    del feat, target, label, x
+    tr.close()
+    peaks = measured_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    fwd_tf = (1 << 22) * SUR_FWD_FLOP / fwd_s / 1e12
+    train_tf = rows * SUR_TRAIN_FLOP / train_s / 1e12
     sopts = dataclasses.replace(opts, surrogate=True)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -377,9 +410,16 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
     value = hist / t
     return {"value": value, "unit": "protons/s", "s_per_im_set": t / n, "sets": n,
             "speedup_vs_plain": value / plain_value, "kernel_ms_per_set": kern_ms / n, "steps_per_set": steps / n,
-            "training": {"tracks": 8 * tpb, "epochs": epochs, "seconds": train_s, "final_loss": float(losses[-1]),
+            "training": {"tracks": 8 * tpb, "epochs": epochs, "batch": batch, "generate_s": gen_s,
+                         "train_s": train_s, "final_loss": float(losses[-1]),
                          "note": "plain brass transport tracks of 8 circular-edge geometries, E 40-230 MeV; "
-                                 "dose error vs the plain path is checked in tests/test_gpu_surrogate_dose.py"}}
+                                 "dose error vs the plain path is checked in tests/test_gpu_surrogate_dose.py"},
+            "tensor_roofline": {"bound": "tensor", "unit": "TFLOP/s", "peak": bf16_peak,
+                                "forward": {"achieved": fwd_tf, "frac": fwd_tf / bf16_peak, "rows": 1 << 22,
+                                            "flop_per_row": SUR_FWD_FLOP},
+                                "train": {"achieved": train_tf, "frac": train_tf / bf16_peak, "rows": rows,
+                                          "flop_per_row": SUR_TRAIN_FLOP},
+                                "peak_note": "bf16_tflops of MEASURED_PEAKS.json (cuBLAS burst)"}}
 
 
 def e2e_leg(pb, spots, scens, opts, args):

@@ -236,6 +236,7 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     p.straggling = o.straggling;
     p.nuclear = o.nuclear;
     p.fscale = std::ldexp(1.0f, o.frac_bits);
+    p.fx32 = o.frac_bits <= 24 ? 1 : 0;
     p.records = reinterpret_cast<HistRecord*>(o.history_out);
     p.rec_cap = o.history_out ? o.history_cap : 0;
     p.phase = c->d_phase;

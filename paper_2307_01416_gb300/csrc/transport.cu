@@ -397,6 +397,14 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, Lane& L, 
     }
 }
 
+// Fixed-point value round-half-even(e * scale) of an energy.  Below 2^32 (any
+// energy up to 250 MeV at scales up to 2^24) the 32-bit conversion gives the
+// same integer as the 64-bit one, which would occupy the FP64 pipe.
+__device__ __forceinline__ unsigned long long to_fixed(float e, float scale, bool fits32)
+{
+    return fits32 ? (unsigned long long)__float2uint_rn(e * scale) : __float2ull_rn(e * scale);
+}
+
 // Largest i with items[i].hist_off <= g, searched by the whole warp: each
 // round the 32 lanes probe 32 evenly spaced entries (g is warp-uniform).
 __device__ __forceinline__ int find_item_warp(const DevItem* __restrict__ items, int n, long long g, int lane)
@@ -774,7 +782,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                     L.forced = 0;
                     if (need_dist) absorb = rmax < dw;
                     if (absorb) {
-                        acc_ap += __float2ull_rn(L.E * P.fscale);
+                        acc_ap += to_fixed(L.E, P.fscale, P.fx32);
                         L.E = 0.0f;
                         fate = kAbsAp;
                     } else {
@@ -787,7 +795,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                 StepResult o;
                 ch_step(m, s_geom, L, P, key, o);
                 acc_steps += 1;
-                const unsigned long long qs = __float2ull_rn(o.dE * P.fscale);
+                const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
                 if (L.stage == 0) acc_rs += qs; else acc_ap += qs;
                 if (o.killed) {
                     if (o.killed == 2) acc_nuc += qs;
@@ -823,7 +831,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
             }
             if (fate >= 0) {
                 // the single place where a history ends in this kernel
-                if (fate == kLeak || fate == kErr) acc_leak += __float2ull_rn(L.E * P.fscale);
+                if (fate == kLeak || fate == kErr) acc_leak += to_fixed(L.E, P.fscale, P.fx32);
                 if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }
                 if (P.records && L.g < P.rec_cap) {
                     float pos[3];
@@ -984,7 +992,7 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
                     for (int k = 0; k < 3; ++k) { L.p[k] = r.p[k]; L.d[k] = r.d[k]; }
                     if (!(tmax > tin)) {
                         // misses the grid
-                        acc_leak += __float2ull_rn(L.E * P.fscale);
+                        acc_leak += to_fixed(L.E, P.fscale, P.fx32);
                         if (P.records && L.g < P.rec_cap) write_record(P, L, kLeak, L.p, acc_dep);
                     } else {
     #pragma unroll
@@ -1016,7 +1024,7 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
             if (++L.iters > kMaxIter) {
                 fate = kErr;
             } else {
-                const long long cidx = L.ic[0] + (long long)P.ctg.n[0] * (L.ic[1] + (long long)P.ctg.n[1] * L.ic[2]);
+                const int cidx = L.ic[0] + P.ctg.n[0] * (L.ic[1] + P.ctg.n[1] * L.ic[2]);   // CT < 2^31 voxels
                 const int h = min(max((int)__ldg(P.ct + cidx), kHULo), kHULo + kNHU - 1);
                 const float2 rs = hu_lut[h - kHULo];
                 water.kappa = rs.y * spr_scale;
@@ -1043,21 +1051,21 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
                 StepResult o;
                 const float d_old[3] = {L.d[0], L.d[1], L.d[2]};
                 const int lx = L.is[0] - bx.lo[0], ly = L.is[1] - bx.lo[1], lz = L.is[2] - bx.lo[2];
-                const int vox = L.is[0] + P.sg.n[0] * (L.is[1] + P.sg.n[1] * L.is[2]);
+                const int is0 = L.is[0], is1 = L.is[1], is2 = L.is[2];
                 ch_step(water, s_geom, L, P, key, o);
                 acc_steps += 1;
-                const unsigned long long qs = __float2ull_rn(o.dE * P.fscale);
-                const unsigned long long q = wsc == P.fscale ? qs : __float2ull_rn(o.dE * wsc);
+                const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
+                const unsigned long long q = wsc == P.fscale ? qs : to_fixed(o.dE, wsc, false);
                 // score into the scoring voxel where the step started
                 if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] && ly < bx.n[1] && lz < bx.n[2]) {
-                    dep_key = bx.base + lx + (long long)bx.n[0] * (ly + (long long)bx.n[1] * lz);
+                    dep_key = bx.base + (long long)(lx + bx.n[0] * (ly + bx.n[1] * lz));   // box < 2^31 voxels
                     dep_q = q;
                 } else if (o.dE > 0.0f && P.ovf) {
                     // rare tail outside the item's box: append a record
                     const unsigned long long slot = atomicAdd(P.ovf_count, 1ull);
                     if ((long long)slot < P.ovf_cap) {
                         OvfRec rr;
-                        rr.voxel = vox;
+                        rr.voxel = is0 + P.sg.n[0] * (is1 + P.sg.n[1] * is2);
                         rr.item = L.item;
                         rr.q = q;
                         P.ovf[slot] = rr;
@@ -1093,7 +1101,7 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
                 }
             }
             if (fate >= 0) {
-                if (fate == kLeak || fate == kErr) acc_leak += __float2ull_rn(L.E * P.fscale);
+                if (fate == kLeak || fate == kErr) acc_leak += to_fixed(L.E, P.fscale, P.fx32);
                 if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }
                 if (P.records && L.g < P.rec_cap) write_record(P, L, fate, L.p, acc_dep);
                 alive = false;

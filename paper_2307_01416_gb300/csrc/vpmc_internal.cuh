@@ -182,6 +182,7 @@ struct TransportParams {
     uint32_t key0, key1_hi;
     int mcs, straggling, nuclear;
     float fscale;                    // 2^F
+    int fx32;                        // 2^F <= 2^24: every energy x 2^F fits 32 bits (E <= 250 MeV)
     int aggregate;
     int chunk;
     // learned aperture surrogate
