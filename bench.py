@@ -51,8 +51,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-aperture leg")
-    ap.add_argument("--ncu-case", action="store_true",
-                    help="small fixed-launch transport case for ncu captures (dose path, nominal scenario)")
+    ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im"], default=None,
+                    help="small fixed-launch transport case for ncu captures (nominal scenario, every 10th spot): "
+                         "'dose' scores one grid, 'im' scores influence-matrix columns")
     return ap.parse_args()
 
 
@@ -321,9 +322,11 @@ def main():
 
 def run_ncu_case(args):
     """Every 10th spot of the set's nominal scenario (about 3.3e6 histories,
-    full physics) through vpmc_run_spots with a fixed launch (512 threads,
-    warp-aggregated atomics, chunk 32, 640 threads): one k_transport launch per step and a
-    16 MB scoring grid, small enough for a full ncu capture."""
+    full physics) with a fixed launch (k_devices 512 threads, k_patient 640,
+    chunk 32): one launch of each transport kernel per step.  'dose' scores a
+    16 MB grid (warp-aggregated atomics); 'im' scores the spots' influence-matrix
+    columns (about 1 GB of column scratch, plain atomics), the bench's own
+    scoring path, small enough for an ncu capture."""
     import torch
     from paper_2307_01416_gb300 import vpmc
     pb, spots, scens = build_workload(False)
@@ -332,9 +335,14 @@ def run_ncu_case(args):
     eng = vpmc.Engine(pb)
     opts = W.Options(seed=1234)
     for i in range(args.warmup + args.steps):
-        dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=640, aggregate=1, chunk=32)
-        print(json.dumps({"case": "ncu", "iter": i, "histories": st["histories"], "steps": st["steps"],
-                          "kernel_ms": st["ms"], "steps_per_s": st["steps"] / (st["ms"] / 1000.0)}))
+        if args.ncu_case == "im":
+            mats, st = eng.influence_matrix(sub, [W.Scenario()], opts, block_size=640, aggregate=0, chunk=32)
+            del mats
+        else:
+            dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=640, aggregate=1, chunk=32)
+        print(json.dumps({"case": "ncu-" + args.ncu_case, "iter": i, "histories": st["histories"],
+                          "steps": st["steps"], "kernel_ms": st["ms"],
+                          "steps_per_s": st["steps"] / (st["ms"] / 1000.0)}))
     eng.close()
     return 0
 
