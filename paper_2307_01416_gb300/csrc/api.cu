@@ -113,9 +113,12 @@ vpmc_status grow_phase(vpmc_ctx* c, long long n)
 {
     if (n <= c->phase_cap) return VPMC_OK;
     cudaFree(c->d_phase);
+    cudaFree(c->d_mid);
     c->d_phase = nullptr;
+    c->d_mid = nullptr;
     c->phase_cap = 0;
     CUDA_TRY(dev_alloc(&c->d_phase, (size_t)n));
+    CUDA_TRY(dev_alloc(&c->d_mid, (size_t)n));
     c->phase_cap = n;
     return VPMC_OK;
 }
@@ -242,6 +245,9 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     p.phase = c->d_phase;
     p.phase_cap = c->phase_cap;
     p.phase_count = c->d_phase_count;
+    p.mid = c->d_mid;
+    p.mid_cap = c->phase_cap;
+    p.mid_count = c->d_mid_count;
     p.poly_kappa = c->d_poly_kappa;
     p.surrogate = o.surrogate && c->sur_ready ? 1 : 0;
     return p;
@@ -285,6 +291,9 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
     p.phase = c->d_phase;
     p.phase_cap = c->phase_cap;
     p.phase_count = c->d_phase_count;
+    p.mid = c->d_mid;
+    p.mid_cap = c->phase_cap;
+    p.mid_count = c->d_mid_count;
     p.aggregate = t.aggregate;
     p.chunk = t.chunk;
     if (p.surrogate) {
@@ -307,20 +316,20 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
         }
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
         CUDA_TRY(launch_patient(p, c->num_sms, t.block, c->stream));
-        c->launches += 2;
+        c->launches += 3;
     }
     return VPMC_OK;
 }
 
 float time_launch(vpmc_ctx* c, cudaError_t (*fn)(const TransportParams&, int, int, cudaStream_t),
-                  const TransportParams& p, int block)
+                  const TransportParams& p, int block, int kernels)
 {
     cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
     cudaEventRecord(c->ev0, c->stream);
     cudaError_t e = fn(p, c->num_sms, block, c->stream);
     cudaEventRecord(c->ev1, c->stream);
     if (e != cudaSuccess || cudaEventSynchronize(c->ev1) != cudaSuccess) return 1e30f;
-    ++c->launches;
+    c->launches += kernels;
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     return ms;
@@ -352,7 +361,7 @@ vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc
             CUDA_TRY(cudaMemsetAsync(c->d_phase_count, 0, sizeof(unsigned long long), c->stream));
             vpmc_status st = reset_counters(c);
             if (st != VPMC_OK) return st;
-            const float ms = time_launch(c, launch_devices, p, block);
+            const float ms = time_launch(c, launch_devices, p, block, 2);
             if (rep == 1 && ms < t_best) { t_best = ms; best.dev_block = block; }
         }
     // patient kernel on the histories the last devices launch handed over
@@ -368,7 +377,7 @@ vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc
                     p.chunk = chunk;
                     vpmc_status st = reset_counters(c);
                     if (st != VPMC_OK) return st;
-                    const float ms = time_launch(c, launch_patient, p, block);
+                    const float ms = time_launch(c, launch_patient, p, block, 1);
                     if (rep == 1 && ms < t_best) {
                         t_best = ms;
                         best.block = block;
@@ -508,6 +517,7 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     CTX_TRY(dev_alloc(&c->d_beams, kMaxBeams));
     CTX_TRY(dev_alloc(&c->d_counter, 1));
     CTX_TRY(dev_alloc(&c->d_phase_count, 1));
+    CTX_TRY(dev_alloc(&c->d_mid_count, 1));
     CTX_TRY(dev_alloc(&c->d_stats, kNStats));
     CTX_TRY(dev_alloc(&c->d_status, 1));
     CTX_TRY(dev_alloc(&c->d_scens, kMaxScen));
@@ -1168,6 +1178,8 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->d_ovf);
     cudaFree(c->d_phase);
     cudaFree(c->d_phase_count);
+    cudaFree(c->d_mid);
+    cudaFree(c->d_mid_count);
     cudaFree(c->d_scratch);
     cudaFree(c->d_poly_kappa);
     cudaFree(c->d_sq);
@@ -1427,6 +1439,9 @@ vpmc_status vpmc_surrogate_tracks(vpmc_ctx* c, const int* beam_ids, int n_beams,
     p.phase = c->d_phase;
     p.phase_cap = c->phase_cap;
     p.phase_count = c->d_phase_count;
+    p.mid = c->d_mid;
+    p.mid_cap = c->phase_cap;
+    p.mid_count = c->d_mid_count;
     p.aggregate = 0;
     p.chunk = 32;
     st = reset_counters(c);

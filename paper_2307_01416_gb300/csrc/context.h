@@ -58,9 +58,11 @@ struct vpmc_ctx {
     size_t boxes_cap = 0;
     vpmc::OvfRec* d_ovf = nullptr;                   // out-of-box deposit records
     long long ovf_cap = 0;
-    vpmc::PhaseRec* d_phase = nullptr;               // hand-off from the devices to the patient kernel
-    long long phase_cap = 0;
+    vpmc::PhaseRec* d_phase = nullptr;               // hand-off from the aperture to the patient kernel
+    vpmc::PhaseRec* d_mid = nullptr;                 // hand-off from the range-shifter to the aperture kernel
+    long long phase_cap = 0;                         // records of each hand-off buffer
     unsigned long long* d_phase_count = nullptr;
+    unsigned long long* d_mid_count = nullptr;
     unsigned long long* d_scratch = nullptr;
     size_t scratch_cap = 0;                    // elements
     float* d_poly_kappa = nullptr;             // per polygon vertex: signed curvature (surrogate inputs)

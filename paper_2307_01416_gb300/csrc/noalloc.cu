@@ -24,7 +24,7 @@ namespace {
 
 constexpr long long kMaxVoxels = 1ll << 21;      // 2,097,152 scoring voxels
 constexpr int kMaxItems = 16384;                 // spots with histories per call
-constexpr long long kBatch = 1ll << 18;          // histories per hand-off batch
+constexpr long long kBatch = 1ll << 17;          // histories per batch (two hand-off buffers of this size)
 constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -33,8 +33,9 @@ constexpr size_t kOffItems = kOffAcc + align256(sizeof(unsigned long long) * kMa
 constexpr size_t kOffBox = kOffItems + align256(sizeof(DevItem) * kMaxItems);
 constexpr size_t kOffScen = kOffBox + align256(sizeof(DevBox));
 constexpr size_t kOffPhase = kOffScen + align256(sizeof(DevScen));
-constexpr size_t kOffCount = kOffPhase + align256(sizeof(PhaseRec) * kBatch);   // counter, phase count, stats
-constexpr size_t kOffStatus = kOffCount + align256(sizeof(unsigned long long) * (2 + kNStats));
+constexpr size_t kOffMid = kOffPhase + align256(sizeof(PhaseRec) * kBatch);
+constexpr size_t kOffCount = kOffMid + align256(sizeof(PhaseRec) * kBatch);      // counter, two hand-off counts, stats
+constexpr size_t kOffStatus = kOffCount + align256(sizeof(unsigned long long) * (3 + kNStats));
 constexpr size_t kScratchBytes = kOffStatus + 256;                              // about 29 MiB
 
 // The scratch of every call on a device (each GPU that loads the library
@@ -107,6 +108,7 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     DevBox* box = reinterpret_cast<DevBox*>(base + kOffBox);
     DevScen* dscen = reinterpret_cast<DevScen*>(base + kOffScen);
     PhaseRec* phase = reinterpret_cast<PhaseRec*>(base + kOffPhase);
+    PhaseRec* mid = reinterpret_cast<PhaseRec*>(base + kOffMid);
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(base + kOffCount);
     int* status = reinterpret_cast<int*>(base + kOffStatus);
 
@@ -165,7 +167,7 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     NA_TRY(cudaMemcpyAsync(dscen, &sc, sizeof sc, cudaMemcpyHostToDevice, c->stream));
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(acc, 0, (size_t)c->nvox * sizeof(unsigned long long), c->stream));
-    NA_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (2 + kNStats), c->stream));
+    NA_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (3 + kNStats), c->stream));
     NA_TRY(cudaMemsetAsync(status, 0, sizeof(int), c->stream));
     NA_TRY(cudaMemsetAsync(dose_dev, 0, (size_t)c->nvox * sizeof(float), c->stream));
 
@@ -189,11 +191,14 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     p.boxes = box;
     p.counter = counters;
     p.phase_count = counters + 1;
-    p.stats = counters + 2;
+    p.mid_count = counters + 2;
+    p.stats = counters + 3;
     p.status = status;
     p.scratch = acc;
     p.phase = phase;
     p.phase_cap = kBatch;
+    p.mid = mid;
+    p.mid_cap = kBatch;
     p.ovf = nullptr;
     p.key0 = (uint32_t)o.seed;
     p.key1_hi = (uint32_t)(o.seed >> 32);
@@ -217,7 +222,7 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
         NA_TRY(launch_devices(p, c->num_sms, dev_block, c->stream));
         NA_TRY(cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), c->stream));
         NA_TRY(launch_patient(p, c->num_sms, block, c->stream));
-        c->launches += 2;
+        c->launches += 3;
     }
     if (n_items) NA_TRY(cudaEventRecord(c->ev1, c->stream));
     const double scale = std::ldexp(1.0, -o.frac_bits) * 1.602176634e-10 /
@@ -226,11 +231,11 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     ++c->launches;
     if (stats_out) {
         NA_TRY(cudaStreamSynchronize(c->stream));
-        unsigned long long h[2 + kNStats];
+        unsigned long long h[3 + kNStats];
         int st_word = 0;
         NA_TRY(cudaMemcpy(h, counters, sizeof h, cudaMemcpyDeviceToHost));
         NA_TRY(cudaMemcpy(&st_word, status, sizeof st_word, cudaMemcpyDeviceToHost));
-        const unsigned long long* v = h + 2;
+        const unsigned long long* v = h + 3;
         const double q = std::ldexp(1.0, -o.frac_bits);
         vpmc_stats r;
         std::memset(&r, 0, sizeof r);
@@ -244,7 +249,7 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
         r.e_aperture = v[kStAp] * q;
         r.e_nuc = v[kStNuc] * q;
         if (n_items) NA_TRY(cudaEventElapsedTime(&r.ms, c->ev0, c->ev1));
-        r.launches = 2 * ((total + kBatch - 1) / kBatch) + 1;
+        r.launches = 3 * ((total + kBatch - 1) / kBatch) + 1;
         *stats_out = r;
         if (st_word & 1) return report_error(VPMC_ERR_TIMEOUT, "%lld histories reached the iteration cap",
                                              (long long)r.errors);

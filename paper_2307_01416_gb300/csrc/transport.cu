@@ -4,15 +4,16 @@
 // model, so no secondary particles are spawned).  Warps are persistent: a warp
 // takes chunks of consecutive work indices from one counter and hands them to
 // lanes whose history has ended, so dead lanes are refilled at once.
-// Transport runs in two kernels so that the lanes of a warp execute the same
-// geometry: k_devices carries each history through the optional range shifter
-// and the brass aperture (Sec. 2.B: at every step inside the aperture slab a
-// crossing-number test decides opening -> straight flight, or brass ->
-// condensed-history step with brass physics) and hands the survivors' phase
-// space at the end of the beam line to k_patient, which transports them through
-// the voxelised patient and scores every step's deposit into a 64-bit
-// fixed-point accumulator (optionally aggregated over the lanes of a warp that
-// hit the same voxel, then one atomic per voxel).
+// Transport runs in three kernels so that the lanes of a warp execute the same
+// geometry, each handing its survivors' phase space to the next:
+// k_source_rs samples the source and carries each history through the
+// optional range shifter; k_aperture takes it through the brass aperture
+// (Sec. 2.B: at every step inside the aperture slab a crossing-number test
+// decides opening -> straight flight, or brass -> condensed-history step with
+// brass physics); k_patient transports it through the voxelised patient and
+// scores every step's deposit into a 64-bit fixed-point accumulator
+// (optionally aggregated over the lanes of a warp that hit the same voxel,
+// then one atomic per voxel).
 //
 // Physics of one condensed-history step (same definition as the CPU oracle):
 //   step = min(1 mm, 1 % energy-loss length, geometry limit, nuclear point);
@@ -472,50 +473,34 @@ __device__ __forceinline__ void warp_add_stats(const TransportParams& P, unsigne
 }  // namespace
 
 // ============================================================================
-// Range shifter and aperture.
+// Source and range shifter.
 // ============================================================================
-// kMode bit 0: brass entries in the surrogate's domain become queries;
-// bit 1: training tracks (histories start on the aperture entrance plane and
-// record the surrogate's inputs and targets).
-template <int kMode>
-__global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
+// Samples each history's source state (slot 0 of its stream) and carries it
+// through the optional range shifter, a homogeneous PMMA slab of finite
+// radius: outside the radius a proton flies straight to the slab's exit plane.
+// Survivors go to the aperture kernel in the beam's-eye frame.  Every lane of
+// a warp runs the same slab step, so the warps stay converged.
+__global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
 {
-    constexpr bool kSur = (kMode & 1) != 0;
-    constexpr bool kTrack = (kMode & 2) != 0;
     extern __shared__ __align__(16) unsigned char smem[];
     {
-        // PMMA and brass rows of the tables, material constants, beams, scenarios, polygons
-        float* R = reinterpret_cast<float*>(smem + DevicesSmem::R);
-        float* Et = reinterpret_cast<float*>(smem + DevicesSmem::Einv);
-        for (int i = threadIdx.x; i < kNEPad; i += blockDim.x) {
-            R[i] = P.tables->R[kPMMA][i];
-            R[kNEPad + i] = P.tables->R[kBrass][i];
-        }
-        for (int i = threadIdx.x; i < kNR; i += blockDim.x) {
-            Et[i] = P.tables->Einv[kPMMA][i];
-            Et[kNR + i] = P.tables->Einv[kBrass][i];
-        }
-        MatConst* mt = reinterpret_cast<MatConst*>(smem + DevicesSmem::Mat);
+        float* R = reinterpret_cast<float*>(smem + SourceSmem::R);
+        float* Et = reinterpret_cast<float*>(smem + SourceSmem::Einv);
+        for (int i = threadIdx.x; i < kNEPad; i += blockDim.x) R[i] = P.tables->R[kPMMA][i];
+        for (int i = threadIdx.x; i < kNR; i += blockDim.x) Et[i] = P.tables->Einv[kPMMA][i];
+        MatConst* mt = reinterpret_cast<MatConst*>(smem + SourceSmem::Mat);
         if (threadIdx.x < kNMat) mt[threadIdx.x] = P.tables->mat[threadIdx.x];
-        DevBeam* bm = reinterpret_cast<DevBeam*>(smem + DevicesSmem::Beams);
+        DevBeam* bm = reinterpret_cast<DevBeam*>(smem + SourceSmem::Beams);
         for (int i = threadIdx.x; i < P.n_beams; i += blockDim.x) bm[i] = P.beams[i];
-        DevScen* sc = reinterpret_cast<DevScen*>(smem + DevicesSmem::Scens);
-        for (int i = threadIdx.x; i < P.n_scen; i += blockDim.x) sc[i] = P.scens[i];
-        float2* pl = reinterpret_cast<float2*>(smem + DevicesSmem::Poly);
-        for (int i = threadIdx.x; i < P.n_poly; i += blockDim.x) pl[i] = P.poly[i];
     }
     __syncthreads();
-    const float* Rpmma = reinterpret_cast<const float*>(smem + DevicesSmem::R);
-    const float* Epmma = reinterpret_cast<const float*>(smem + DevicesSmem::Einv);
-    const MatConst* mat = reinterpret_cast<const MatConst*>(smem + DevicesSmem::Mat);
-    const DevBeam* beams = reinterpret_cast<const DevBeam*>(smem + DevicesSmem::Beams);
-    const DevScen* scens = reinterpret_cast<const DevScen*>(smem + DevicesSmem::Scens);
-    const float2* poly = reinterpret_cast<const float2*>(smem + DevicesSmem::Poly);
-    Medium pmma, brass;
-    pmma.Rt = Rpmma; pmma.Et = Epmma; pmma.inv_dR = mat[kPMMA].inv_dR; pmma.kappa = mat[kPMMA].rho;
+    const MatConst* mat = reinterpret_cast<const MatConst*>(smem + SourceSmem::Mat);
+    const DevBeam* beams = reinterpret_cast<const DevBeam*>(smem + SourceSmem::Beams);
+    Medium pmma;
+    pmma.Rt = reinterpret_cast<const float*>(smem + SourceSmem::R);
+    pmma.Et = reinterpret_cast<const float*>(smem + SourceSmem::Einv);
+    pmma.inv_dR = mat[kPMMA].inv_dR; pmma.kappa = mat[kPMMA].rho;
     pmma.rho = mat[kPMMA].rho; pmma.za = mat[kPMMA].za; pmma.inv_x0 = mat[kPMMA].inv_x0;
-    brass.Rt = Rpmma + kNEPad; brass.Et = Epmma + kNR; brass.inv_dR = mat[kBrass].inv_dR; brass.kappa = mat[kBrass].rho;
-    brass.rho = mat[kBrass].rho; brass.za = mat[kBrass].za; brass.inv_x0 = mat[kBrass].inv_x0;
 
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -527,7 +512,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
     L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; }
-    unsigned long long acc_leak = 0, acc_rs = 0, acc_ap = 0, acc_nuc = 0, acc_steps = 0, acc_err = 0;
+    unsigned long long acc_leak = 0, acc_rs = 0, acc_nuc = 0, acc_steps = 0, acc_err = 0;
     uint2 key = make_uint2(0u, 0u);
 
     for (;;) {
@@ -555,45 +540,245 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                 L.step = 0;
                 L.iters = 0;
                 key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
-                if (kTrack) {
-                    // training track: born on the aperture's entrance plane near
-                    // the opening (slot 0: energy, angle, edge distance; slot 5:
-                    // incidence angles along the radial and tangential directions)
-                    const uint4 x = philox(make_uint4(L.hist, 0u, 0u, 0u), key);
-                    const float E = fmaf(sur::kEHi - sur::kELo, u01(x.x), sur::kELo);
-                    float sph, cph;
-                    sincospif(2.0f * u01(x.y), &sph, &cph);
-                    const float r12 = 1.2f * range_of(brass.Rt, E) / brass.rho;
-                    const float dhi = r12 < B.ap_tdn - B.ap_tup ? fminf(sur::kDCap, r12) : sur::kDCap;
-                    const float rr = fmaf(dhi, u01(x.z), B.r_circ);
-                    const uint4 a = philox(make_uint4(L.hist, 0u, 5u, 0u), key);
-                    const float2 zz = box_muller(u01(a.x), u01(a.y));
-                    const float tn = fminf(fmaxf(sur::kAngSigma * zz.x, -sur::kAngMax), sur::kAngMax);
-                    const float tt = fminf(fmaxf(sur::kAngSigma * zz.y, -sur::kAngMax), sur::kAngMax);
-                    L.d[0] = tn * cph - tt * sph;
-                    L.d[1] = tn * sph + tt * cph;
-                    L.d[2] = sqrtf(1.0f - tn * tn - tt * tt);
-                    L.p[0] = rr * cph; L.p[1] = rr * sph; L.p[2] = B.ap_tup;
-                    L.E = E;
-                } else {
-                    // source: slot 0 -> (x, y) at the isocentre plane and two projected angles
-                    const uint4 x = philox(make_uint4(L.hist, 0u, 0u, 0u), key);
-                    const float2 z01 = box_muller(u01(x.x), u01(x.y));
-                    const float2 z23 = box_muller(u01(x.z), u01(x.w));
-                    const float a0 = fmaf(I.sigma, z01.x, I.x), b0 = fmaf(I.sigma, z01.y, I.y);
-                    const float tha = I.div_rad * z23.x, thb = I.div_rad * z23.y;
-                    const float nrm = rsqrtf(1.0f + tha * tha + thb * thb);
-                    L.d[0] = tha * nrm; L.d[1] = thb * nrm; L.d[2] = nrm;
-                    L.p[0] = fmaf(B.t_src, tha, a0); L.p[1] = fmaf(B.t_src, thb, b0); L.p[2] = B.t_src;
-                    L.E = I.E0;
-                }
+                // source: slot 0 -> (x, y) at the isocentre plane and two projected angles
+                const uint4 x = philox(make_uint4(L.hist, 0u, 0u, 0u), key);
+                const float2 z01 = box_muller(u01(x.x), u01(x.y));
+                const float2 z23 = box_muller(u01(x.z), u01(x.w));
+                const float a0 = fmaf(I.sigma, z01.x, I.x), b0 = fmaf(I.sigma, z01.y, I.y);
+                const float tha = I.div_rad * z23.x, thb = I.div_rad * z23.y;
+                const float nrm = rsqrtf(1.0f + tha * tha + thb * thb);
+                L.d[0] = tha * nrm; L.d[1] = thb * nrm; L.d[2] = nrm;
+                L.p[0] = fmaf(B.t_src, tha, a0); L.p[1] = fmaf(B.t_src, thb, b0); L.p[2] = B.t_src;
+                L.E = I.E0;
                 if (P.nuclear) {
                     const uint4 y = philox(make_uint4(L.hist, 0u, 3u, 0u), key);
                     L.nlam = -logf(u01(y.x));
                 } else {
                     L.nlam = __int_as_float(0x7f800000);
                 }
-                L.stage = -1;                       // enters its first stage in the next iteration
+                L.stage = -1;                       // enters the slab (if any) in the next iteration
+                alive = true;
+            }
+            pool.next += take;
+            need = __ballot_sync(kFull, !alive && !done);
+        }
+        if (!__any_sync(kFull, alive)) {
+            if (__all_sync(kFull, done || alive)) break;
+            continue;
+        }
+
+        // ---- one iteration of every live history ----
+        bool handoff = false;
+        int fate = -1;
+        if (alive) {
+            const DevItem& I = P.items[L.item];
+            const DevBeam& B = beams[__ldg(&I.beam)];
+            if (++L.iters > kMaxIter) {
+                fate = kErr;
+            } else if (L.stage < 0) {
+                if (B.rs) {
+                    const float sdr = (B.rs_tup - L.p[2]) / L.d[2];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
+                    L.R = range_of(pmma.Rt, L.E);
+                    L.stage = 0;
+                } else {
+                    handoff = true;                 // no range shifter
+                }
+            } else if (L.p[0] * L.p[0] + L.p[1] * L.p[1] > B.rs_r2) {
+                // outside the slab's radius: straight flight to its exit plane
+                if (!(L.d[2] > 0.0f)) fate = kLeak;
+                else {
+                    const float sf = (B.rs_tdn - L.p[2]) / L.d[2];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sf, L.d[k], L.p[k]);
+                    handoff = true;
+                }
+            } else {
+                float s_geom = __int_as_float(0x7f800000);
+                bool down = true;
+                if (L.d[2] > 0.0f) s_geom = (B.rs_tdn - L.p[2]) / L.d[2];
+                else if (L.d[2] < 0.0f) { s_geom = (B.rs_tup - L.p[2]) / L.d[2]; down = false; }
+                s_geom = fmaxf(s_geom, 0.0f);       // scattering offsets can leave it past the plane
+                StepResult o;
+                ch_step(pmma, s_geom, L, P, key, o);
+                acc_steps += 1;
+                const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
+                acc_rs += qs;
+                if (o.killed) {
+                    if (o.killed == 2) acc_nuc += qs;
+                    fate = kAbsRS;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) L.p[k] += o.disp[k];
+                    if (o.lim == 1) { if (down) handoff = true; else fate = kLeak; }
+                }
+            }
+            if (fate >= 0) {
+                if (fate == kLeak || fate == kErr) acc_leak += to_fixed(L.E, P.fscale, P.fx32);
+                if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }
+                if (P.records && L.g < P.rec_cap) {
+                    float pos[3];
+                    bev_to_patient(B, P.scens[__ldg(&I.scen)], L.p, pos);
+                    write_record(P, L, fate, pos, 0ull);
+                }
+                alive = false;
+            }
+        }
+        // ---- hand-off to the aperture kernel (one atomic per warp) ----
+        const unsigned hmask = __ballot_sync(kFull, handoff);
+        if (hmask) {
+            unsigned long long base = 0;
+            const int leader = __ffs(hmask) - 1;
+            if (lane == leader) base = atomicAdd(P.mid_count, (unsigned long long)__popc(hmask));
+            base = __shfl_sync(kFull, base, leader);
+            if (handoff) {
+                const long long slot = (long long)base + __popc(hmask & lt_mask);
+                if (slot < P.mid_cap) {
+                    PhaseRec r;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) { r.p[k] = L.p[k]; r.d[k] = L.d[k]; }
+                    r.E = L.E;
+                    r.nlam = L.nlam;
+                    r.step = L.step;
+                    r.item = L.item;
+                    r.g = L.g;
+                    P.mid[slot] = r;
+                } else {
+                    atomicOr(P.status, 2);          // hand-off buffer too small (host sizes it to the batch)
+                }
+                alive = false;
+            }
+        }
+    }
+    unsigned long long v[kNStats] = {0ull, acc_leak, acc_rs, 0ull, acc_nuc, acc_steps, acc_err};
+    warp_add_stats(P, v, lane);
+}
+
+// ============================================================================
+// Aperture block.
+// ============================================================================
+// Takes the histories the source kernel hands over (or, for training tracks,
+// births them on the block's entrance plane) through the aperture block and
+// hands the survivors to the patient kernel.
+// kMode bit 0: brass entries in the surrogate's domain become queries;
+// bit 1: training tracks (histories start on the aperture entrance plane and
+// record the surrogate's inputs and targets).
+template <int kMode>
+__global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
+{
+    constexpr bool kSur = (kMode & 1) != 0;
+    constexpr bool kTrack = (kMode & 2) != 0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    {
+        // brass rows of the tables, material constants, beams, scenarios, polygons
+        float* R = reinterpret_cast<float*>(smem + ApertureSmem::R);
+        float* Et = reinterpret_cast<float*>(smem + ApertureSmem::Einv);
+        for (int i = threadIdx.x; i < kNEPad; i += blockDim.x) R[i] = P.tables->R[kBrass][i];
+        for (int i = threadIdx.x; i < kNR; i += blockDim.x) Et[i] = P.tables->Einv[kBrass][i];
+        MatConst* mt = reinterpret_cast<MatConst*>(smem + ApertureSmem::Mat);
+        if (threadIdx.x < kNMat) mt[threadIdx.x] = P.tables->mat[threadIdx.x];
+        DevBeam* bm = reinterpret_cast<DevBeam*>(smem + ApertureSmem::Beams);
+        for (int i = threadIdx.x; i < P.n_beams; i += blockDim.x) bm[i] = P.beams[i];
+        DevScen* sc = reinterpret_cast<DevScen*>(smem + ApertureSmem::Scens);
+        for (int i = threadIdx.x; i < P.n_scen; i += blockDim.x) sc[i] = P.scens[i];
+        float2* pl = reinterpret_cast<float2*>(smem + ApertureSmem::Poly);
+        for (int i = threadIdx.x; i < P.n_poly; i += blockDim.x) pl[i] = P.poly[i];
+    }
+    __syncthreads();
+    const MatConst* mat = reinterpret_cast<const MatConst*>(smem + ApertureSmem::Mat);
+    const DevBeam* beams = reinterpret_cast<const DevBeam*>(smem + ApertureSmem::Beams);
+    const DevScen* scens = reinterpret_cast<const DevScen*>(smem + ApertureSmem::Scens);
+    const float2* poly = reinterpret_cast<const float2*>(smem + ApertureSmem::Poly);
+    Medium brass;
+    brass.Rt = reinterpret_cast<const float*>(smem + ApertureSmem::R);
+    brass.Et = reinterpret_cast<const float*>(smem + ApertureSmem::Einv);
+    brass.inv_dR = mat[kBrass].inv_dR; brass.kappa = mat[kBrass].rho;
+    brass.rho = mat[kBrass].rho; brass.za = mat[kBrass].za; brass.inv_x0 = mat[kBrass].inv_x0;
+    // histories handed over by the source kernel (training tracks: born here)
+    const long long n_in = kTrack ? P.total : min((long long)*P.mid_count, P.mid_cap);
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    WorkPool pool;
+    int pool_item = 0;
+    bool alive = false, done = false;
+    Lane L;
+    L.item = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.stage = 0; L.forced = 0;
+    L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; }
+    unsigned long long acc_leak = 0, acc_ap = 0, acc_nuc = 0, acc_steps = 0, acc_err = 0;
+    uint2 key = make_uint2(0u, 0u);
+
+    for (;;) {
+        // ---- new histories for lanes whose history has ended ----
+        unsigned need = __ballot_sync(kFull, !alive && !done);
+        while (need) {
+            if (pool.next >= pool.end) {
+                if (!pool.refill(P, kTrack ? P.hist_begin : 0ll, n_in, lane)) {
+                    if (!alive) done = true;
+                    break;
+                }
+                if (kTrack) pool_item = find_item_warp(P.items, P.n_items, pool.next, lane);
+            }
+            const int take = (int)min((long long)__popc(need), pool.end - pool.next);
+            const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
+            if (mine) {
+                const long long g = pool.next + __popc(need & lt_mask);
+                if (kTrack) {
+                    int it = pool_item;
+                    while (it + 1 < P.n_items && __ldg(&P.items[it + 1].hist_off) <= g) ++it;
+                    const DevItem I = P.items[it];
+                    const DevBeam& B = beams[I.beam];
+                    L.item = it;
+                    L.g = g;
+                    L.hist = (uint32_t)(g - I.hist_off);
+                    L.step = 0;
+                    L.iters = 0;
+                    key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
+                    {
+                        // training track: born on the aperture's entrance plane near
+                        // the opening (slot 0: energy, angle, edge distance; slot 5:
+                        // incidence angles along the radial and tangential directions)
+                        const uint4 x = philox(make_uint4(L.hist, 0u, 0u, 0u), key);
+                        const float E = fmaf(sur::kEHi - sur::kELo, u01(x.x), sur::kELo);
+                        float sph, cph;
+                        sincospif(2.0f * u01(x.y), &sph, &cph);
+                        const float r12 = 1.2f * range_of(brass.Rt, E) / brass.rho;
+                        const float dhi = r12 < B.ap_tdn - B.ap_tup ? fminf(sur::kDCap, r12) : sur::kDCap;
+                        const float rr = fmaf(dhi, u01(x.z), B.r_circ);
+                        const uint4 a = philox(make_uint4(L.hist, 0u, 5u, 0u), key);
+                        const float2 zz = box_muller(u01(a.x), u01(a.y));
+                        const float tn = fminf(fmaxf(sur::kAngSigma * zz.x, -sur::kAngMax), sur::kAngMax);
+                        const float tt = fminf(fmaxf(sur::kAngSigma * zz.y, -sur::kAngMax), sur::kAngMax);
+                        L.d[0] = tn * cph - tt * sph;
+                        L.d[1] = tn * sph + tt * cph;
+                        L.d[2] = sqrtf(1.0f - tn * tn - tt * tt);
+                        L.p[0] = rr * cph; L.p[1] = rr * sph; L.p[2] = B.ap_tup;
+                        L.E = E;
+                    }
+                    if (P.nuclear) {
+                        const uint4 y = philox(make_uint4(L.hist, 0u, 3u, 0u), key);
+                        L.nlam = -logf(u01(y.x));
+                    } else {
+                        L.nlam = __int_as_float(0x7f800000);
+                    }
+                } else {
+                    const PhaseRec r = P.mid[g];
+                    const DevItem I = P.items[r.item];
+                    L.item = r.item;
+                    L.g = r.g;
+                    L.hist = (uint32_t)(r.g - I.hist_off);
+                    L.step = r.step;
+                    L.iters = 0;
+                    key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) { L.p[k] = r.p[k]; L.d[k] = r.d[k]; }
+                    L.E = r.E;
+                    L.nlam = r.nlam;
+                }
+                L.stage = -1;                       // enters the block (if any) in the next iteration
                 alive = true;
             }
             pool.next += take;
@@ -621,23 +806,6 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                 fate = kErr;
             } else if (L.stage < 0) {
                 advance = true;
-            } else if (L.stage == 0) {
-                // ---- range shifter: homogeneous slab of finite radius ----
-                if (L.p[0] * L.p[0] + L.p[1] * L.p[1] > B.rs_r2) {
-                    if (!(L.d[2] > 0.0f)) fate = kLeak;
-                    else {
-                        const float sf = (B.rs_tdn - L.p[2]) / L.d[2];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sf, L.d[k], L.p[k]);
-                        advance = true;
-                    }
-                } else {
-                    if (L.d[2] > 0.0f) s_geom = (B.rs_tdn - L.p[2]) / L.d[2];
-                    else if (L.d[2] < 0.0f) { s_geom = (B.rs_tup - L.p[2]) / L.d[2]; down = false; }
-                    s_geom = fmaxf(s_geom, 0.0f);   // scattering offsets can leave it past the plane
-                    m = pmma;
-                    do_ch = true;
-                }
             } else {
                 // ---- aperture block: geometry needing exact polygon tests is
                 // requested here and served below by the whole warp ----
@@ -796,10 +964,10 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
                 ch_step(m, s_geom, L, P, key, o);
                 acc_steps += 1;
                 const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
-                if (L.stage == 0) acc_rs += qs; else acc_ap += qs;
+                acc_ap += qs;
                 if (o.killed) {
                     if (o.killed == 2) acc_nuc += qs;
-                    fate = L.stage == 0 ? kAbsRS : kAbsAp;
+                    fate = kAbsAp;
                 } else {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) L.p[k] += o.disp[k];
@@ -809,13 +977,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
             if (advance && fate < 0) {
                 // the single place where a history changes stage
                 const int from = L.stage;
-                if (from < 0 && B.rs) {
-                    const float sdr = (B.rs_tup - L.p[2]) / L.d[2];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
-                    L.R = range_of(pmma.Rt, L.E);
-                    L.stage = 0;
-                } else if (from < 1 && B.ap) {
+                if (from < 1 && B.ap) {
                     if (!(L.d[2] > 0.0f)) fate = kLeak;
                     else {
                         const float sdr = (B.ap_tup - L.p[2]) / L.d[2];
@@ -895,7 +1057,7 @@ __global__ void __launch_bounds__(640, 1) k_devices(const TransportParams P)
             }
         }
     }
-    unsigned long long v[kNStats] = {0ull, acc_leak, acc_rs, acc_ap, acc_nuc, acc_steps, acc_err};
+    unsigned long long v[kNStats] = {0ull, acc_leak, 0ull, acc_ap, acc_nuc, acc_steps, acc_err};
     warp_add_stats(P, v, lane);
 }
 
@@ -1115,33 +1277,47 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
     warp_add_stats(P, v, lane);
 }
 
-size_t devices_smem_bytes() { return DevicesSmem::Bytes; }
+size_t devices_smem_bytes() { return SourceSmem::Bytes > ApertureSmem::Bytes ? SourceSmem::Bytes : ApertureSmem::Bytes; }
 size_t patient_smem_bytes() { return PatientSmem::Bytes; }
 int devices_max_block() { return 640; }
 int patient_max_block() { return 768; }
 
 template <int kMode>
-static cudaError_t launch_devices_mode(const TransportParams& p, int grid, int block, cudaStream_t s)
+static cudaError_t launch_aperture_mode(const TransportParams& p, int grid, int block, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_devices<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)DevicesSmem::Bytes);
+        cudaError_t e = cudaFuncSetAttribute(k_aperture<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ApertureSmem::Bytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_devices<kMode><<<grid, block, DevicesSmem::Bytes, s>>>(p);
+    k_aperture<kMode><<<grid, block, ApertureSmem::Bytes, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaStream_t s)
 {
     const int mode = (p.surrogate ? 1 : 0) | (p.track_mode ? 2 : 0);
+    if (!p.track_mode) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(k_source_rs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)SourceSmem::Bytes);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        cudaError_t e = cudaMemsetAsync(p.mid_count, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+        k_source_rs<<<grid, 768, SourceSmem::Bytes, s>>>(p);      // 78 registers: 768 threads fit
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    }
     switch (mode) {
-    case 1: return launch_devices_mode<1>(p, grid, block, s);
-    case 2: return launch_devices_mode<2>(p, grid, block, s);
-    case 3: return launch_devices_mode<3>(p, grid, block, s);
-    default: return launch_devices_mode<0>(p, grid, block, s);
+    case 1: return launch_aperture_mode<1>(p, grid, block, s);
+    case 2: return launch_aperture_mode<2>(p, grid, block, s);
+    case 3: return launch_aperture_mode<3>(p, grid, block, s);
+    default: return launch_aperture_mode<0>(p, grid, block, s);
     }
 }
 

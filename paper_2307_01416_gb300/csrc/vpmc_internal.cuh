@@ -168,8 +168,11 @@ struct TransportParams {
     long long total;                 // total histories
     unsigned long long* counter;     // global work counter
     unsigned long long* scratch;     // deposit target
-    long long hist_begin;            // devices kernel: first global history of the batch
-    PhaseRec* phase;                 // histories handed from the devices to the patient kernel
+    long long hist_begin;            // beam-line kernels: first global history of the batch
+    PhaseRec* mid;                   // histories handed from the range-shifter to the aperture kernel (BEV)
+    unsigned long long* mid_count;
+    long long mid_cap;
+    PhaseRec* phase;                 // histories handed from the aperture to the patient kernel
     unsigned long long* phase_count;
     long long phase_cap;
     OvfRec* ovf;                     // out-of-box deposits (NULL: none expected)
@@ -201,10 +204,17 @@ struct TransportParams {
 };
 
 // Shared-memory layouts of the two transport kernels.
-struct DevicesSmem {                 // range shifter and aperture
-    static constexpr size_t R = 0;                                            // PMMA, brass
-    static constexpr size_t Einv = R + sizeof(float) * 2 * kNEPad;
-    static constexpr size_t Mat = Einv + sizeof(float) * 2 * kNR;
+struct SourceSmem {                  // source and range shifter
+    static constexpr size_t R = 0;                                            // PMMA
+    static constexpr size_t Einv = R + sizeof(float) * kNEPad;
+    static constexpr size_t Mat = Einv + sizeof(float) * kNR;
+    static constexpr size_t Beams = Mat + sizeof(MatConst) * kNMat;
+    static constexpr size_t Bytes = Beams + sizeof(DevBeam) * kMaxBeams;
+};
+struct ApertureSmem {                // aperture block
+    static constexpr size_t R = 0;                                            // brass
+    static constexpr size_t Einv = R + sizeof(float) * kNEPad;
+    static constexpr size_t Mat = Einv + sizeof(float) * kNR;
     static constexpr size_t Beams = Mat + sizeof(MatConst) * kNMat;
     static constexpr size_t Scens = Beams + sizeof(DevBeam) * kMaxBeams;
     static constexpr size_t Poly = Scens + sizeof(DevScen) * kMaxScen;
@@ -220,10 +230,11 @@ struct PatientSmem {                 // voxelised patient
 };
 
 // Host-side launchers (transport.cu, finalize.cu).
-// Transport of histories [p.hist_begin, p.total): the devices kernel, then
-// the patient kernel on the histories it hands over (p.phase must hold
-// p.total - p.hist_begin records).  Both launches are persistent grids of
-// one block per SM.
+// Transport of histories [p.hist_begin, p.total): the beam-line kernels
+// (source and range shifter, then the aperture: launch_devices, which resets
+// p.counter between them), then the patient kernel on the histories they hand
+// over (p.mid and p.phase must each hold p.total - p.hist_begin records).
+// All launches are persistent grids of one block per SM.
 cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaStream_t s);
 cudaError_t launch_patient(const TransportParams& p, int grid, int block, cudaStream_t s);
 size_t devices_smem_bytes();
