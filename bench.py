@@ -288,7 +288,7 @@ def main():
         achieved = steps * OPS_PER_STEP / (kern_ms / 1000.0) / 1e12
         traffic = transport_traffic(steps / args.steps)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                "frac": achieved / peak_tops, "traffic": traffic, "kernel": "k_devices+k_patient",
+                "frac": achieved / peak_tops, "traffic": traffic, "kernel": "k_source_rs+k_aperture+k_patient",
                 "peak_note": "%d SMs x 4 sub-partitions x 32 lanes x %.0f MHz (max SM clock) lane-ops/s; "
                              "%d lane-ops per condensed-history step" % (nsm, sm_max, OPS_PER_STEP),
                 "kernel_ms_per_step": kern_ms / args.steps, "steps_per_launch": steps / args.steps}
@@ -322,7 +322,7 @@ def main():
 
 def run_ncu_case(args):
     """Every 10th spot of the set's nominal scenario (about 3.3e6 histories,
-    full physics) with a fixed launch (k_devices 512 threads, k_patient 640,
+    full physics) with a fixed launch (k_source_rs 768 threads, k_aperture 512, k_patient 640,
     chunk 32): one launch of each transport kernel per step.  'dose' scores a
     16 MB grid (warp-aggregated atomics); 'im' scores the spots' influence-matrix
     columns (about 1 GB of column scratch, plain atomics), the bench's own
