@@ -153,6 +153,18 @@ def uniform(x: int) -> float:
     return lib().orc_uniform(int(x) & 0xFFFFFFFF)
 
 
+def step_uniforms(hist: int, step: int, key):
+    """The six 21-bit uniforms of one condensed-history step."""
+    L = lib()
+    if not hasattr(L, "_su_ready"):
+        L.orc_step_uniforms.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_double)]
+        L._su_ready = True
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_double * 6)()
+    L.orc_step_uniforms(int(hist) & 0xFFFFFFFF, int(step) & 0xFFFFFFFF, k, o)
+    return list(o)
+
+
 def box_muller(u1: float, u2: float):
     z = (C.c_double * 2)()
     lib().orc_box_muller(u1, u2, z)

@@ -105,6 +105,22 @@ static void stream_block(const orc_stream* st, uint32_t step, uint32_t slot, dou
     for (int i = 0; i < 4; ++i) u[i] = orc_uniform(x[i]);
 }
 
+/* Six 21-bit uniforms of one condensed-history step from one Philox block,
+ * counter (history, step, 1, 0): the top 21 bits of words 0..3 give u0..u3;
+ * the low 11 bits of word 0 (or 2) followed by the low 10 bits of word 1 (or
+ * 3) give u4 (or u5).  u = (v + 1/2) 2^-21 lies in (0, 1) and is exact in
+ * binary32.  Scattering takes the Box-Muller pairs (u0, u1), (u2, u3);
+ * straggling the first normal of (u4, u5). */
+void orc_step_uniforms(uint32_t hist, uint32_t step, const uint32_t key[2], double u[6])
+{
+    uint32_t ctr[4] = {hist, step, 1u, 0u}, x[4];
+    orc_philox4x32_10(ctr, key, x);
+    const double sc = ldexp(1.0, -21);
+    for (int i = 0; i < 4; ++i) u[i] = ((double)(x[i] >> 11) + 0.5) * sc;
+    u[4] = ((double)(((x[0] & 0x7FFu) << 10) | (x[1] & 0x3FFu)) + 0.5) * sc;
+    u[5] = ((double)(((x[2] & 0x7FFu) << 10) | (x[3] & 0x3FFu)) + 0.5) * sc;
+}
+
 /* Four normals from one Philox block (two Box-Muller pairs). */
 static void stream_normals4(const orc_stream* st, uint32_t step, uint32_t slot, double z[4])
 {
@@ -448,9 +464,11 @@ static void ch_step(const orc_medium* med, orc_particle* pt, double s_geom,
     double R1 = R0 - s * med->kappa;
     double Emean = R1 > 0.0 ? orc_energy(med->table, R1) : ORC_ECUT;
     double dE = E - Emean;
+    double u[6];
+    if (op->mcs || op->straggling) orc_step_uniforms(st->hist, pt->step, st->key, u);
     if (op->straggling) {
-        double z[4];
-        stream_normals4(st, pt->step, 2u, z);
+        double z[2];
+        orc_box_muller(u[4], u[5], z);
         dE += sqrt(orc_bohr_var(E, s, med->rho, med->za)) * z[0];
     }
     if (dE < 0.0) dE = 0.0;
@@ -479,7 +497,8 @@ static void ch_step(const orc_medium* med, orc_particle* pt, double s_geom,
     if (op->mcs && !out->killed) {
         double theta0 = orc_highland(E, s, med->rho, med->X0);
         double z[4];
-        stream_normals4(st, pt->step, 1u, z);
+        orc_box_muller(u[0], u[1], z);
+        orc_box_muller(u[2], u[3], z + 2);
         /* two projected planes, each a correlated (angle, offset) pair */
         double th1 = z[1] * theta0, th2 = z[3] * theta0;
         double dx1 = s * theta0 * (z[0] / sqrt(12.0) + 0.5 * z[1]);

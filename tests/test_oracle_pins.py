@@ -65,6 +65,28 @@ def test_box_muller_normals_distribution():
     assert abs(np.corrcoef(pairs[:, 0], pairs[:, 1])[0, 1]) < 4.0 / math.sqrt(len(pairs))
 
 
+def test_step_uniforms_lattice_uniform_independent():
+    """The six per-step uniforms: on the 21-bit lattice (v + 1/2) 2^-21 inside
+    (0,1), exact in FP32, each uniform (KS), pairwise uncorrelated, and the
+    first four taken from the top bits of four different Philox words (so
+    that a change of any one word changes exactly one of them)."""
+    key = (1234, 99)
+    U = np.array([O.step_uniforms(h, 7 + (h % 5), key) for h in range(30000)])
+    v = U * 2.0 ** 21 - 0.5
+    assert np.all(U > 0) and np.all(U < 1)
+    assert np.all(v == np.round(v)) and np.all(v >= 0) and np.all(v < 2 ** 21)
+    assert np.all(U.astype(np.float32).astype(np.float64) == U)
+    for j in range(6):
+        assert stats.kstest(U[:, j], "uniform").pvalue > 1e-3, j
+    C = np.corrcoef(U.T)
+    off = C[~np.eye(6, dtype=bool)]
+    assert np.max(np.abs(off)) < 5.0 / math.sqrt(len(U))
+    # u0..u3 are the Philox words' top 21 bits: they agree with the pinned generator's output
+    x = O.philox4x32_10((5, 7, 1, 0), key)
+    u = O.step_uniforms(5, 7, key)
+    assert [int(w) >> 11 for w in x] == [int(round(a * 2 ** 21 - 0.5)) for a in u[:4]]
+
+
 # ----------------------------------------------------------------- tables
 def test_bethe_against_pstar():
     """Water stopping power and CSDA range against NIST PSTAR (ICRU 49)."""
