@@ -31,6 +31,9 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
 // ((x >> 9) + 1/2) * 2^-23: 23-bit uniform in (0, 1), exact in FP32.
 __device__ __forceinline__ float u01(uint32_t x) { return fmaf(__uint2float_rn(x >> 9), 0x1p-23f, 0x1p-24f); }
 
+// (v + 1/2) * 2^-21 for a 21-bit v: the per-step uniforms, exact in FP32.
+__device__ __forceinline__ float u21(uint32_t v) { return fmaf(__uint2float_rn(v), 0x1p-21f, 0x1p-22f); }
+
 // Box-Muller with accurate functions (source sampling, once per history).
 __device__ __forceinline__ float2 box_muller(float u1, float u2)
 {

@@ -22,8 +22,9 @@
 //   correlated (angle, offset) pair in two planes; nuclear removal at
 //   0.0012 / mm x density with the removed energy deposited locally.
 // Random numbers: Philox4x32-10, key = (seed lo, spot ^ seed hi), counter =
-// (history, step, slot, 0): slot 0 source, 1 scattering, 2 straggling,
-// 3 nuclear free path.
+// (history, step, slot, 0): slot 0 source (23-bit uniforms), slot 1 one
+// condensed-history step (six 21-bit uniforms for scattering and
+// straggling), slot 3 nuclear free path; the surrogate uses slots 4-6.
 #include "device_common.cuh"
 #include "vpmc_internal.cuh"
 
@@ -34,7 +35,7 @@ using namespace dev;
 
 constexpr float kMp = 938.272f;
 
-// Box-Muller with hardware approximations (per-step physics).  u1 <= 1 - 2^-24,
+// Box-Muller with hardware approximations (per-step physics).  u1 <= 1 - 2^-22,
 // so -2 ln u1 > 0; the clamp only guards the approximate logarithm.
 __device__ __forceinline__ float2 box_muller_fast(float u1, float u2)
 {
@@ -46,22 +47,6 @@ __device__ __forceinline__ float2 box_muller_fast(float u1, float u2)
 }
 
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
-
-// Two Philox4x32-10 blocks with the same key, rounds interleaved for ILP.
-__device__ __forceinline__ void philox_pair(uint4& a, uint4& b, uint2 k)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t ah0 = __umulhi(0xD2511F53u, a.x), al0 = 0xD2511F53u * a.x;
-        const uint32_t ah1 = __umulhi(0xCD9E8D57u, a.z), al1 = 0xCD9E8D57u * a.z;
-        const uint32_t bh0 = __umulhi(0xD2511F53u, b.x), bl0 = 0xD2511F53u * b.x;
-        const uint32_t bh1 = __umulhi(0xCD9E8D57u, b.z), bl1 = 0xCD9E8D57u * b.z;
-        a = make_uint4(ah1 ^ a.y ^ k.x, al1, ah0 ^ a.w ^ k.y, al0);
-        b = make_uint4(bh1 ^ b.y ^ k.x, bl1, bh0 ^ b.w ^ k.y, bl0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-    }
-}
 
 __device__ __forceinline__ float range_of(const float* __restrict__ R, float E)
 {
@@ -337,9 +322,11 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, Lane& L, 
     L.step += 1;
     if (lim == 2) L.nlam = 0.0f; else L.nlam -= mu * s;
 
-    // random numbers of this step: slot 1 (scattering) and slot 2 (straggling)
-    uint4 r1 = make_uint4(L.hist, L.step, 1u, 0u), r2 = make_uint4(L.hist, L.step, 2u, 0u);
-    if (P.mcs || P.straggling) philox_pair(r1, r2, key);
+    // random numbers of this step: one block, counter (history, step, 1, 0),
+    // six 21-bit uniforms -- the top 21 bits of each word (scattering) and the
+    // low bits of words 0|1 and 2|3 (straggling)
+    uint4 r = make_uint4(L.hist, L.step, 1u, 0u);
+    if (P.mcs || P.straggling) r = philox(r, key);
 
     const float R1 = R0 - s * m.kappa;
     const float Emean = R1 > 0.0f ? energy_of(m.Et, m.inv_dR, R1) : kEcut;
@@ -348,7 +335,8 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, Lane& L, 
     const float inv_etot = __fdividef(1.0f, E + kMp);
     if (P.straggling) {
         const float beta2 = pc2 * inv_etot * inv_etot;
-        const float2 z = box_muller_fast(u01(r2.x), u01(r2.y));
+        const float2 z = box_muller_fast(u21(((r.x & 0x7FFu) << 10) | (r.y & 0x3FFu)),
+                                         u21(((r.z & 0x7FFu) << 10) | (r.w & 0x3FFu)));
         const float var = 0.01569f * m.rho * m.za * s * __fdividef(1.0f - 0.5f * beta2, 1.0f - beta2);
         dE += fast_sqrt(var) * z.x;
     }
@@ -375,8 +363,8 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, Lane& L, 
         const float x = s * m.rho * m.inv_x0;
         float th0 = 0.0f;
         if (x >= 1e-6f) th0 = __fdividef(13.6f, pc2 * inv_etot) * fast_sqrt(x) * (1.0f + 0.038f * __logf(x));
-        const float2 za = box_muller_fast(u01(r1.x), u01(r1.y));
-        const float2 zb = box_muller_fast(u01(r1.z), u01(r1.w));
+        const float2 za = box_muller_fast(u21(r.x >> 11), u21(r.y >> 11));
+        const float2 zb = box_muller_fast(u21(r.z >> 11), u21(r.w >> 11));
         const float th1 = za.y * th0, th2 = zb.y * th0;
         const float dx1 = s * th0 * fmaf(za.x, 0.28867513459481287f, 0.5f * za.y);
         const float dx2 = s * th0 * fmaf(zb.x, 0.28867513459481287f, 0.5f * zb.y);
