@@ -36,7 +36,7 @@ WORKLOAD = ("13-scenario robust influence-matrix set, synthetic head 256x256x160
             "3 mm spots, 1e3-2e4 histories/spot")
 # Lane-operations of one condensed-history step of the full-physics method
 # (the model and its itemisation are stated in the design doc).
-OPS_PER_STEP = 370
+OPS_PER_STEP = 300
 L2_FLUSH_BYTES = 512 << 20
 
 
