@@ -122,6 +122,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive FP32 columns of this thread's tensor-memory lane, waited for.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // a in the low half (lower address)
@@ -192,39 +210,40 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t t_row, const float* __r
                                                 unsigned char* dstT, int r, uint32_t (&mask)[4])
 {
 #pragma unroll 1
-    for (int c0 = 0; c0 < kH; c0 += 16) {
-        float v[16];
-        tmem_ld16(t_row + (uint32_t)c0, v);
-        uint32_t w[8];
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+        float v[32];
+        tmem_ld32(t_row + (uint32_t)c0, v);
+        uint32_t w[16];
         uint32_t mbits = 0u;
 #pragma unroll
-        for (int j = 0; j < 16; j += 2) {
+        for (int j = 0; j < 32; j += 2) {
             const float a0 = v[j] + __ldg(bias + c0 + j), a1 = v[j + 1] + __ldg(bias + c0 + j + 1);
             mbits |= (a0 > 0.0f ? 1u : 0u) << j;
             mbits |= (a1 > 0.0f ? 1u : 0u) << (j + 1);
-            const float h0 = fmaxf(a0, 0.0f), h1 = fmaxf(a1, 0.0f);
-            w[j >> 1] = pack_bf16(h0, h1);
+            w[j >> 1] = pack_bf16(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
             if (kTransposed) {
                 *reinterpret_cast<unsigned short*>(dstT + kmaj(c0 + j, r, kRows)) = (unsigned short)(w[j >> 1] & 0xFFFFu);
                 *reinterpret_cast<unsigned short*>(dstT + kmaj(c0 + j + 1, r, kRows)) = (unsigned short)(w[j >> 1] >> 16);
             }
         }
-        *reinterpret_cast<uint4*>(dst + kmaj(r, c0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(dst + kmaj(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
-        mask[c0 >> 5] |= mbits << (c0 & 31);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(dst + kmaj(r, c0 + 8 * q, kH)) =
+                make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        mask[c0 >> 5] = mbits;
     }
 }
 
 // z = D3 + b3 for row r (48 columns, 45 used).
 __device__ __forceinline__ void output_epilogue(uint32_t t_d3, const float* __restrict__ b3, float (&z)[kOutPad])
 {
+    float v[32], u[16];
+    tmem_ld32(t_d3, v);
+    tmem_ld16(t_d3 + 32u, u);
 #pragma unroll
-    for (int c0 = 0; c0 < kOutPad; c0 += 16) {
-        float v[16];
-        tmem_ld16(t_d3 + (uint32_t)c0, v);
+    for (int j = 0; j < 32; ++j) z[j] = v[j] + __ldg(b3 + j);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) z[c0 + j] = v[j] + (c0 + j < kOut ? __ldg(b3 + c0 + j) : 0.0f);
-    }
+    for (int j = 0; j < 16; ++j) z[32 + j] = u[j] + (32 + j < kOut ? __ldg(b3 + 32 + j) : 0.0f);
 }
 
 // ============================================================================
@@ -686,13 +705,13 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
         if (!(ok = complete(bar, phase))) break;
         // ---- da2 = dh2 * relu'(a2): K-major into A, transposed into C ----
 #pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 16) {
-            float v[16];
-            tmem_ld16(t_row + (uint32_t)c0, v);
-            uint32_t w[8];
-            const uint32_t mb = m2[c0 >> 5] >> (c0 & 31);
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float v[32];
+            tmem_ld32(t_row + (uint32_t)c0, v);
+            uint32_t w[16];
+            const uint32_t mb = m2[c0 >> 5];
 #pragma unroll
-            for (int j = 0; j < 16; j += 2) {
+            for (int j = 0; j < 32; j += 2) {
                 const float a0 = ((mb >> j) & 1u) ? v[j] : 0.0f;
                 const float a1 = ((mb >> (j + 1)) & 1u) ? v[j + 1] : 0.0f;
                 w[j >> 1] = pack_bf16(a0, a1);
@@ -701,8 +720,10 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
                 *reinterpret_cast<unsigned short*>(sm + TrainSmem::C + kmaj(c0 + j + 1, r, kRows)) =
                     (unsigned short)(w[j >> 1] >> 16);
             }
-            *reinterpret_cast<uint4*>(sm + TrainSmem::A + kmaj(r, c0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<uint4*>(sm + TrainSmem::A + kmaj(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(sm + TrainSmem::A + kmaj(r, c0 + 8 * q, kH)) =
+                    make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
         // ---- dh1 = da2 W2 and [dW2 | db2] += da2^T [h1 | 1] ----
         publish();
@@ -715,12 +736,12 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
         if (!(ok = complete(bar, phase))) break;
         // ---- da1 = dh1 * relu'(a1), transposed into C ----
 #pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 16) {
-            float v[16];
-            tmem_ld16(t_row + 128u + (uint32_t)c0, v);
-            const uint32_t mb = m1[c0 >> 5] >> (c0 & 31);
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float v[32];
+            tmem_ld32(t_row + 128u + (uint32_t)c0, v);
+            const uint32_t mb = m1[c0 >> 5];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 32; ++j) {
                 const float a = ((mb >> j) & 1u) ? v[j] : 0.0f;
                 *reinterpret_cast<unsigned short*>(sm + TrainSmem::C + kmaj(c0 + j, r, kRows)) = bf16_bits(a);
             }
