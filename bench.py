@@ -207,6 +207,26 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- ranks
+def rank_seed(rank: int) -> int:
+    """Each rank computes its own independent set (weak scaling)."""
+    return 1234 + 7919 * rank
+
+
+def reduce_over_ranks(t: float, hist: float, world: int, device: str):
+    """(max of the ranks' timed seconds, sum of their histories): the job's
+    time is its slowest rank's, its throughput every rank's work."""
+    if world <= 1:
+        return float(t), float(hist)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    hh = torch.tensor([float(hist)], dtype=torch.float64, device=device)
+    dist.all_reduce(hh)
+    return float(tt.item()), float(hh.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     args = parse_args()
@@ -228,7 +248,7 @@ def main():
     free_b, total_b = torch.cuda.mem_get_info()
     print("device memory: %.1f GB free of %.1f GB" % (free_b / 1e9, total_b / 1e9), file=sys.stderr)
     # independent problems per rank (weak scaling): each rank computes its own set
-    opts = W.Options(seed=1234 + 7919 * rank)
+    opts = W.Options(seed=rank_seed(rank))
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -267,15 +287,7 @@ def main():
         ck = clocks.stop()
         t = ev0.elapsed_time(ev1) / 1000.0
         eng.close()                                # frees the set's column scratch before the e2e leg
-    if world > 1:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-        hh = torch.tensor([float(hist)], device="cuda")
-        dist.all_reduce(hh)
-        hist_all = float(hh.item())
-    else:
-        hist_all = float(hist)
+    t, hist_all = reduce_over_ranks(t, hist, world, "cuda")
     value = hist_all / t
     ms_per_step = 1000.0 * t / args.steps
 
