@@ -264,7 +264,7 @@ vpmc_status vpmc_surrogate_get_weights(vpmc_ctx* ctx, float* params);
  * its entrance plane near the opening.  Track h of list entry g is global
  * index i = g * tracks_per_beam + h, with Philox key (seed low word,
  * g ^ seed high word).  Its start, from counter (h, 0, slot, 0):
- *   slot 0: E = 40 + 190 u0 MeV, angle phi = 2 pi u1, edge distance d = d_hi u2,
+ *   slot 0: E = 40 + 190 u0 MeV, angle phi = 2 pi u1, edge distance d = d_hi u2^2,
  *           where d_hi = min(12 mm, 1.2 R) if 1.2 x brass CSDA range R is
  *           below the thickness, else 12 mm; the proton starts at radius
  *           r_c + d at angle phi, r_c the largest vertex radius;

@@ -988,7 +988,8 @@ void orc_surrogate_features(const double* poly, int n, double thickness, double 
  * carried through the block by the plain transport.  Entry of history h of
  * geometry g, key (seed low, g ^ seed high):
  *   slot 0, step 0 -> u0..u2: E = E_LO + (E_HI - E_LO) u0; phi = 2 pi u1;
- *     d = d_hi u2 with d_hi = min(DCAP, 1.2 R_brass(E)) when 1.2 R_brass(E)
+ *     d = d_hi u2^2 (denser near the edge, where the penumbra is made) with
+ *     d_hi = min(DCAP, 1.2 R_brass(E)) when 1.2 R_brass(E)
  *     is below the block thickness, else DCAP; the proton starts at radius
  *     r_circ + d, angle phi, where r_circ is the largest vertex radius;
  *   slot 5, step 0 -> two normals z0, z1 (first Box-Muller pair):
@@ -1031,7 +1032,7 @@ int orc_surrogate_tracks(const orc_beam* beams, const double* poly_xy, int n_geo
         double phi = 2.0 * M_PI * u[1];
         double r12 = 1.2 * orc_range(ORC_BRASS, E) / ORC_MAT[ORC_BRASS].rho;
         double dhi = (r12 < T) ? (r12 < SUR_DCAP ? r12 : SUR_DCAP) : SUR_DCAP;
-        double dd = dhi * u[2];
+        double dd = dhi * u[2] * u[2];
         double rc = 0.0;
         for (int i = 0; i < bm->nvert; ++i) {
             double rr = sqrt(poly[2 * i] * poly[2 * i] + poly[2 * i + 1] * poly[2 * i + 1]);

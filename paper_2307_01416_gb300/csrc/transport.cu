@@ -735,7 +735,8 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                         sincospif(2.0f * u01(x.y), &sph, &cph);
                         const float r12 = 1.2f * range_of(brass.Rt, E) / brass.rho;
                         const float dhi = r12 < B.ap_tdn - B.ap_tup ? fminf(sur::kDCap, r12) : sur::kDCap;
-                        const float rr = fmaf(dhi, u01(x.z), B.r_circ);
+                        const float uz = u01(x.z);
+                        const float rr = fmaf(dhi * uz, uz, B.r_circ);   // d = d_hi u^2: denser near the edge
                         const uint4 a = philox(make_uint4(L.hist, 0u, 5u, 0u), key);
                         const float2 zz = box_muller(u01(a.x), u01(a.y));
                         const float tn = fminf(fmaxf(sur::kAngSigma * zz.x, -sur::kAngMax), sur::kAngMax);

@@ -254,17 +254,19 @@ def _brass_path(poly, p0, d, T, n=4000):
 def test_tracks_deterministic_straight_lines():
     """Without scattering, straggling and nuclear removal a track is a
     straight line: every transmitted track has y1..y4 = 0, and its energy loss
-    follows the CSDA tables along its brass path (brute-force path length)."""
+    follows the CSDA tables along its brass path.  The opening test happens at
+    each step's start and brass steps are not wall-limited, so a track leaving
+    the brass through the wall is charged brass for up to one more step (at
+    most 1 mm) past the straight-line brass length sb (brute force)."""
     beams = W.surrogate_training_beams(radii=(6.0, 22.0, 150.0))
     n = 300
     r = O.surrogate_tracks(beams, n, _det_opts())
     lab, y, f = r["label"], r["target"], r["feat"]
     assert np.all(r["fate"][lab == 0] == O.FATE_AP)
     np.testing.assert_allclose(y[lab == 1][:, 1:], 0.0, atol=1e-9)
-    # re-derive entry states from the features' definitions for a sample of tracks
     rho = 8.53
     g = np.random.default_rng(15)
-    idx = g.choice(len(lab), 60, replace=False)
+    idx = g.choice(len(lab), 80, replace=False)
     checked = 0
     for i in idx:
         bm = beams[i // n]
@@ -281,22 +283,24 @@ def test_tracks_deterministic_straight_lines():
         r12 = 1.2 * O.csda_range(2, E) / rho
         dhi = min(12.0, r12) if r12 < 30.0 else 12.0
         rc = np.max(np.hypot(poly[:, 0], poly[:, 1]))
-        p0 = ((rc + dhi * u[2]) * math.cos(phi), (rc + dhi * u[2]) * math.sin(phi))
+        p0 = ((rc + dhi * u[2] ** 2) * math.cos(phi), (rc + dhi * u[2] ** 2) * math.sin(phi))
         uu = [O.uniform(v) for v in O.philox4x32_10([h, 0, 5, 0], key)]
         z0, z1 = O.box_muller(uu[0], uu[1])
         tn, tt = np.clip(0.04 * z0, -0.12, 0.12), np.clip(0.04 * z1, -0.12, 0.12)
         d = np.array([tn * math.cos(phi) - tt * math.sin(phi), tn * math.sin(phi) + tt * math.cos(phi),
                       math.sqrt(1 - tn * tn - tt * tt)])
         sb, L = _brass_path(poly, p0, d, 30.0)
+        over = 0.0 if sb >= L - 1e-9 else 1.0          # no overshoot when the whole path is brass
         Rb = O.csda_range(2, E)
-        if abs(Rb - rho * sb) < rho * L / 1000:
-            continue                                   # too close to the range end to decide
-        assert lab[i] == (Rb - rho * sb > 0), i
+        dR = rho * L / 4000                             # midpoint sampling: crossings within L / 8000
+        r_hi, r_lo = Rb - rho * sb + dR, Rb - rho * (sb + over) - dR
+        if r_lo <= 0.0 < r_hi:
+            continue                                    # the range ends within the uncertain stretch
+        assert lab[i] == (r_lo > 0.0), i
         if lab[i]:
-            # the midpoint sampling places each crossing within L / 8000
-            dR = rho * L / 4000
-            e_out = O.energy_at_range(2, Rb - rho * sb)
-            tol = 0.5 * abs(O.energy_at_range(2, Rb - rho * sb + dR) - O.energy_at_range(2, max(Rb - rho * sb - dR, 0)))
-            assert E * (1.0 - y[i, 0] / 5.0) == pytest.approx(e_out, abs=tol + 1e-9), i
+            e_out = E * (1.0 - y[i, 0] / 5.0)
+            assert O.energy_at_range(2, r_lo) - 1e-6 <= e_out <= O.energy_at_range(2, r_hi) + 1e-6, i
+            if over == 0.0:
+                assert e_out == pytest.approx(O.energy_at_range(2, Rb - rho * sb), abs=0.05), i
         checked += 1
-    assert checked >= 40
+    assert checked >= 50
