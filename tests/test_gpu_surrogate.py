@@ -144,8 +144,10 @@ def test_track_generator_matches_oracle_deterministic(eng):
     # wall carries the FP32 rounding of p and q (~1e-5 mm at 150 mm) divided
     # by the distance: up to ~1e-3 in the scaled direction features, below the
     # BF16 rounding (4e-3 relative) the network input gets anyway
+    # the edge distance is drawn as d_hi u^2, so about a tenth of the tracks
+    # pass within 10 um of a wall
     flagged = (r["flags"] & 1) != 0
-    assert flagged.mean() < 0.05
+    assert flagged.mean() < 0.15
     ok = ~flagged
     np.testing.assert_allclose(feat[ok], r["feat"][ok], atol=2e-3, rtol=0)
     mism = np.flatnonzero((label != r["label"]) & ok)
@@ -221,7 +223,7 @@ def test_network_draws_match_oracle(eng):
     drawn = reach > np.minimum(d_hi, 30.0) + 1e-3
     assert np.all(lg[absorbed] == 0)
     ok = clear_t & ~flagged & inside & drawn
-    assert ok.mean() > 0.95
+    assert ok.mean() > 0.8
     np.testing.assert_array_equal(lg[ok], trans[ok].astype(np.int32))
     sel = ok & clear_c & trans
     assert sel.sum() > 500
