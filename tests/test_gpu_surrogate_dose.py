@@ -59,8 +59,9 @@ def test_head_plan_dose_error(weights):
     assert r["gamma"] >= 99.5, r
 
 
-def test_water_aperture_dose_error(weights):
-    pb, spots = W.water_aperture_case(40.0, True, hist_per_layer=300_000)
+@pytest.mark.parametrize("opening", [10.0, 40.0])
+def test_water_aperture_dose_error(weights, opening):
+    pb, spots = W.water_aperture_case(opening, True, hist_per_layer=300_000)
     r = _paired(pb, spots, weights)
     assert r["max_err"] <= 0.01, r
     assert abs(r["mean_err"]) <= 0.005, r
