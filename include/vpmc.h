@@ -282,7 +282,8 @@ vpmc_status vpmc_surrogate_tracks(vpmc_ctx* ctx, const int* beam_ids, int n_beam
                                   int32_t* label_dev);
 
 /* Network outputs for n input rows.  feat_dev: [n x 6] device.
- * z_dev: [n x 45] device, caller-owned.  Synchronous. */
+ * z_dev: [n x 45] device, caller-owned.  Both 16-byte aligned (VPMC_ERR_ARG
+ * otherwise): a tile's rows are moved in 16-byte pieces.  Synchronous. */
 vpmc_status vpmc_surrogate_forward(vpmc_ctx* ctx, const float* feat_dev, int64_t n, float* z_dev);
 
 /* Mean loss over n tracks at the current parameters, and its gradient.

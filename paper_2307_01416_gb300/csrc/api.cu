@@ -1306,6 +1306,8 @@ vpmc_status vpmc_surrogate_forward(vpmc_ctx* c, const float* feat_dev, int64_t n
     g_error.clear();
     (void)cudaGetLastError();
     if (!c || (n > 0 && (!feat_dev || !z_dev)) || n < 0) return fail(VPMC_ERR_ARG, "bad argument");
+    if ((reinterpret_cast<uintptr_t>(feat_dev) | reinterpret_cast<uintptr_t>(z_dev)) & 15u)
+        return fail(VPMC_ERR_ARG, "feat_dev and z_dev must be 16-byte aligned");
     if (!c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights");
     CUDA_TRY(launch_sur_forward(c->sur, feat_dev, n, z_dev, 2 * c->num_sms, c->stream));
     ++c->launches;

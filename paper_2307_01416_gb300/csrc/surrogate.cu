@@ -253,8 +253,10 @@ __device__ __forceinline__ void output_epilogue(uint32_t t_d3, const float* __re
 struct FwdSmem {
     static constexpr int W = 0;                                   // W1, W2, W3 images
     static constexpr int X = kImgW2T;                             // [128 x 16]
-    static constexpr int H = X + kRows * kInPad * 2;              // [128 x 128]
-    static constexpr int Bar = H + kRows * kH * 2;
+    static constexpr int H = X + kRows * kInPad * 2;              // [128 x 128]; also the output staging
+    static constexpr int XS = H + kRows * kH * 2;                 // FP32 inputs of a tile, [128 x 6]
+    static constexpr int QS = XS + kRows * kIn * 4;               // a tile's queries (inference)
+    static constexpr int Bar = QS + kRows * (int)sizeof(SurQuery);
     static constexpr int Slot = Bar + 8;
     static constexpr int Bytes = Slot + 8;
 };
@@ -331,22 +333,38 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_forward(const SurNet net, cons
     const uint32_t bar = smem_addr(sm + FwdSmem::Bar);
     uint32_t phase = 0u;
     bool ok = true;
+    float* xs = reinterpret_cast<float*>(sm + FwdSmem::XS);
+    float* zs = reinterpret_cast<float*>(sm + FwdSmem::H);
     for (long long tile = blockIdx.x; tile * kRows < n && ok; tile += gridDim.x) {
-        const long long row = tile * kRows + r;
+        const long long row0 = tile * kRows;
+        const int rows = (int)min((long long)kRows, n - row0);
+        // the tile's inputs, rows x 6 contiguous floats: coalesced 16-byte loads
+        // (row0 * 24 bytes is a multiple of 16 when row0 is a multiple of 128)
+        const float4* xg = reinterpret_cast<const float4*>(x + kIn * row0);
+        const int nx = rows * kIn;
+        for (int i = r; i < (nx >> 2); i += kRows) reinterpret_cast<float4*>(xs)[i] = __ldg(xg + i);
+        for (int i = (nx & ~3) + r; i < nx; i += kRows) xs[i] = __ldg(x + kIn * row0 + i);
+        __syncthreads();
         float f[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (row < n) {
+        if (r < rows) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) f[k] = __ldg(x + 6 * row + k);
+            for (int k = 0; k < 6; ++k) f[k] = xs[kIn * r + k];
         }
         store_input_row(sm + FwdSmem::X, r, f);
         ok = forward_tile(sm, tbase, t_row, net, bar, phase, r);
         if (!ok) break;
         float zz[kOutPad];
         output_epilogue(t_row, net.params + ob3, zz);
-        if (row < n) {
+        // outputs through shared memory (h2 is consumed): rows x 45 contiguous
+        // floats leave with coalesced 16-byte stores (row0 * 180 bytes is a
+        // multiple of 16)
 #pragma unroll
-            for (int j = 0; j < kOut; ++j) z[kOut * row + j] = zz[j];
-        }
+        for (int j = 0; j < kOut; ++j) zs[kOut * r + j] = zz[j];
+        __syncthreads();
+        float4* zg = reinterpret_cast<float4*>(z + kOut * row0);
+        const int nz = rows * kOut;
+        for (int i = r; i < (nz >> 2); i += kRows) zg[i] = reinterpret_cast<const float4*>(zs)[i];
+        for (int i = (nz & ~3) + r; i < nz; i += kRows) z[kOut * row0 + i] = zs[i];
         tc_fence_before();
         __syncthreads();
     }
@@ -402,12 +420,23 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
     bool ok = true;
     const long long nq = min((long long)*P.sq_count, P.sq_cap);
     unsigned long long acc_ap = 0ull;
+    SurQuery* qs = reinterpret_cast<SurQuery*>(sm + FwdSmem::QS);
+    static_assert(sizeof(SurQuery) % 16 == 0, "query records are copied in 16-byte pieces");
     for (long long tile = blockIdx.x; tile * kRows < nq && ok; tile += gridDim.x) {
         const long long row = tile * kRows + r;
+        const int rows = (int)min((long long)kRows, nq - tile * kRows);
+        // the tile's query records, contiguous: coalesced 16-byte loads
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(P.sq + tile * kRows);
+            uint4* dst = reinterpret_cast<uint4*>(qs);
+            const int n16 = rows * (int)(sizeof(SurQuery) / 16);
+            for (int i = r; i < n16; i += kRows) dst[i] = src[i];
+        }
+        __syncthreads();
         float f[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (row < nq) {
+        if (r < rows) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) f[k] = P.sq[row].x[k];
+            for (int k = 0; k < 6; ++k) f[k] = qs[r].x[k];
         }
         store_input_row(sm + FwdSmem::X, r, f);
         ok = forward_tile(sm, tbase, t_row, net, bar, phase, r);
@@ -420,7 +449,7 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
         bool emit = false;
         PhaseRec rec;
         if (row < nq) {
-            const SurQuery q = P.sq[row];
+            const SurQuery q = qs[r];
             const DevItem& I = P.items[q.item];
             const DevBeam& B = P.beams[I.beam];
             const uint32_t hist = (uint32_t)(q.g - I.hist_off);
@@ -486,7 +515,7 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
         // hand-off into the slot the beam-line kernel reserved for this proton;
         // an absorbed proton leaves the slot empty (item -1)
         if (row < nq && !P.track_mode) {
-            const long long slot = P.sq[row].slot;
+            const long long slot = qs[r].slot;
             if (slot >= 0 && slot < P.phase_cap) {
                 if (!emit) {
                     rec = PhaseRec{};
@@ -497,6 +526,7 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
                 atomicOr(P.status, 2);
             }
         }
+        __syncthreads();                            // qs is refilled by the next tile
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) acc_ap += __shfl_xor_sync(kFull, acc_ap, o);
