@@ -1,0 +1,89 @@
+"""Pins of the robust optimiser's oracle: gradients by finite differences,
+target indices on constructed doses, convergence on a problem with a known
+optimum, the non-negativity projection."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import optimizer_oracle as Q
+
+
+def _cls(n, seed):
+    g = np.random.default_rng(seed)
+    c = np.zeros(n, dtype=np.uint8)
+    c[g.random(n) < 0.4] = 1
+    c[(c == 0) & (g.random(n) < 0.5)] = 2
+    return c
+
+
+def test_objective_gradient_finite_differences():
+    p = Q.OptParams(prescription=2.0)
+    cls = _cls(300, 1)
+    d = np.random.default_rng(2).uniform(0.0, 3.0, 300)
+    f, g = Q.objective(d, cls, p)
+    h = 1e-6
+    for i in range(0, 300, 7):
+        dp, dm = d.copy(), d.copy()
+        dp[i] += h
+        dm[i] -= h
+        fd = (Q.objective(dp, cls, p)[0] - Q.objective(dm, cls, p)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-9), i
+
+
+def test_robust_gradient_through_the_transpose():
+    """F(x) = max_s f(A_s x): away from ties its gradient is A_s*^T f'(A_s* x)."""
+    g = np.random.default_rng(3)
+    mats = [sp.random(200, 40, density=0.2, random_state=10 + s, format="csr") for s in range(3)]
+    cls = _cls(200, 4)
+    p = Q.OptParams(prescription=1.0)
+    x = g.uniform(0.5, 1.5, 40)
+    F, fs, s, doses = Q.robust_objective(mats, x, cls, p)
+    assert np.sort(fs)[-1] - np.sort(fs)[-2] > 1e-3          # a clear worst case
+    grad = mats[s].T @ Q.objective(doses[s], cls, p)[1]
+    h = 1e-6
+    for j in range(0, 40, 3):
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fd = (Q.robust_objective(mats, xp, cls, p)[0] - Q.robust_objective(mats, xm, cls, p)[0]) / (2 * h)
+        assert grad[j] == pytest.approx(fd, rel=1e-5, abs=1e-9), j
+
+
+def test_target_indices_constructed_dose():
+    cls = np.zeros(100, dtype=np.uint8)
+    cls[:50] = 1
+    d = np.zeros(100)
+    d[:50] = 2.0
+    d[3] = 1.8          # 0.9 of the prescription
+    d[7] = 2.4          # 1.2 of it
+    d[60:63] = 2.1      # three voxels outside the target at or above it
+    r = Q.target_indices(d, cls, 2.0)
+    assert r["V100"] == pytest.approx(49 / 50)
+    assert r["Dmin"] == pytest.approx(0.9)
+    assert r["CI100"] == pytest.approx((49 + 3) / 50)
+    assert r["RHI100"] == pytest.approx(1.2)
+
+
+def test_converges_on_identity_problem():
+    """One voxel per spot, all target: the optimum is x = D_p (f = 0)."""
+    n = 30
+    mats = [sp.identity(n, format="csr") * (1.0 + 0.01 * s) for s in range(3)]
+    cls = np.ones(n, dtype=np.uint8)
+    p = Q.OptParams(prescription=2.0, lr=0.02)
+    x0 = np.random.default_rng(5).uniform(0.5, 1.5, n)
+    x, hist = Q.optimise(mats, x0, cls, p, 400)
+    assert hist[-1] < 1e-3 * hist[0]
+    # zero objective in every scenario (scales 1.00..1.02) means D_p <= x and
+    # 1.02 x <= 1.05 D_p
+    assert np.all(x >= 2.0 - 0.01) and np.all(1.02 * x <= 1.05 * 2.0 + 0.01)
+
+
+def test_projection_keeps_weights_non_negative():
+    """A ring voxel far above its limit pushes its spot's weight down; the
+    projection stops it at zero."""
+    mats = [sp.csr_matrix(np.array([[1.0, 0.0], [0.0, 1.0]]))]
+    cls = np.array([2, 1], dtype=np.uint8)
+    p = Q.OptParams(prescription=1.0, lr=0.5)
+    x, _ = Q.optimise(mats, np.array([5.0, 1.0]), cls, p, 60)
+    assert x[0] == 0.0 or x[0] <= 0.6 + 1e-6
+    assert np.all(x >= 0.0)
