@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-aperture leg")
+    ap.add_argument("--no-optimizer", action="store_true", help="skip the robust-optimisation leg")
+    ap.add_argument("--opt-iterations", type=int, default=50)
     ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im"], default=None,
                     help="small fixed-launch transport case for ncu captures (nominal scenario, every 10th spot): "
                          "'dose' scores one grid, 'im' scores influence-matrix columns")
@@ -62,7 +64,7 @@ def build_workload(small: bool):
     if small:
         spots = spots.copy()
         spots["n_hist"] = np.maximum(spots["n_hist"] // 50, 20)
-    return pb, spots, W.robust_scenarios()
+    return pb, spots, W.robust_scenarios(), (center, r)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -177,7 +179,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    pb, spots, scens = build_workload(False)
+    pb, spots, scens, _ = build_workload(False)
     from oracle import oracle as O
     O.lib()
     opts = W.Options(seed=1234)
@@ -244,7 +246,7 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    pb, spots, scens = build_workload(args.small)
+    pb, spots, scens, target = build_workload(args.small)
     free_b, total_b = torch.cuda.mem_get_info()
     print("device memory: %.1f GB free of %.1f GB" % (free_b / 1e9, total_b / 1e9), file=sys.stderr)
     # independent problems per rank (weak scaling): each rank computes its own set
@@ -279,6 +281,7 @@ def main():
             hist += st["histories"]
             launches += st["launches"] + 1
             nnz = sum(int(m["val"].numel()) for m in mats)
+            last_mats = mats
             del mats
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -310,6 +313,10 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(pb, spots, args.cpu_seconds)
+        opt = None
+        if not args.no_optimizer and world == 1:
+            opt = optimizer_leg(pb, target, last_mats, args)
+        del last_mats
         sur = None
         if not args.no_surrogate and world == 1 and not args.small:
             sur = surrogate_leg(pb, spots, scens, opts, args, value)
@@ -324,7 +331,7 @@ def main():
                           "parallelism": "independent sets per GPU" if world > 1 else "1 GPU"},
                "s_per_im_set": ms_per_step / 1000.0,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
-               "surrogate": sur}
+               "surrogate": sur, "optimizer": opt}
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
@@ -341,7 +348,7 @@ def run_ncu_case(args):
     scoring path, small enough for an ncu capture."""
     import torch
     from paper_2307_01416_gb300 import vpmc
-    pb, spots, scens = build_workload(False)
+    pb, spots, scens, _ = build_workload(False)
     sub = spots[::10]
     torch.cuda.set_device(0)
     eng = vpmc.Engine(pb)
@@ -440,6 +447,54 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
                                 "train": {"achieved": train_tf, "frac": train_tf / bf16_peak, "rows": rows,
                                           "flop_per_row": SUR_TRAIN_FLOP},
                                 "peak_note": "bf16_tflops of MEASURED_PEAKS.json (cuBLAS burst)"}}
+
+
+def optimizer_bytes(mats, cls: np.ndarray) -> float:
+    """Algorithmic HBM bytes of one robust-optimisation iteration: per
+    scenario the CSR stream (4 B column + 4 B value per entry, 8 B row
+    pointer per row), the voxel class (1 B) and the dose written (4 B) per
+    row; then the transposed product over the target and ring rows of the
+    worst scenario (class 1 B per row; row pointer 8 B, dose 4 B and 8 B per
+    entry of those rows; the mean over scenarios stands for the worst one).
+    The weights (20 KB) stay in L2."""
+    n_rows = int(mats[0]["shape"][0])
+    tr = (cls == 1) | (cls == 2)
+    fwd = sum(8.0 * m["val"].numel() + 13.0 * n_rows for m in mats)
+    nnz_tr = []
+    for m in mats:
+        rp = m["row_ptr"].cpu().numpy()
+        nnz_tr.append(float(np.sum(np.diff(rp)[tr])))
+    return fwd + n_rows + 12.0 * float(tr.sum()) + 8.0 * float(np.mean(nnz_tr))
+
+
+def optimizer_leg(pb, target, mats, args):
+    """Robust spot-weight optimisation over the timed set's 13 influence
+    matrices (target = the 8.4 cc sphere, ring = 10 mm shell around it):
+    3 warm-up iterations, then args.opt_iterations timed on the device."""
+    import torch
+    from paper_2307_01416_gb300 import vpmc
+    center, r_t = target
+    cls_np = W.structure_classes(pb.scoring, center, r_t)
+    cls = torch.from_numpy(cls_np).cuda()
+    x = torch.ones(int(mats[0]["shape"][1]), dtype=torch.float32, device="cuda")
+    d0 = vpmc.weights_dose(mats[0], x)
+    x *= 1.0 / float(d0[cls == 1].mean())
+    vpmc.robust_optimize(mats, cls, x.clone(), 1.0, iterations=3)
+    hist, ms = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=args.opt_iterations)
+    idx = vpmc.target_indices(mats, cls, 1.0, x)
+    per_it = ms / 1000.0 / args.opt_iterations
+    b = optimizer_bytes(mats, cls_np)
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    gbs = b / per_it / 1e9
+    return {"iterations": args.opt_iterations, "ms_per_iteration": 1000.0 * per_it,
+            "objective_first": float(hist[0]), "objective_last": float(hist[-1]),
+            "worst_V100": float(idx[:, 0].min()), "worst_Dmin": float(idx[:, 1].min()),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "bytes_per_iteration": b, "traffic": None,
+                         "kernel": "k_spmv_obj x13 + k_select + k_spmvT + k_adam_proj",
+                         "peak_note": "hbm_gbs of MEASURED_PEAKS.json (STREAM-style copy)"},
+            "note": "13 SpMV, worst-case selection, one transposed SpMV and the Adam step per iteration, "
+                    "all on the device; target 8.4 cc sphere, ring = 10 mm shell"}
 
 
 def e2e_leg(pb, spots, scens, opts, args):

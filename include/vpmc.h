@@ -301,6 +301,51 @@ vpmc_status vpmc_surrogate_train(vpmc_ctx* ctx, const float* feat_dev, const flo
                                  const int32_t* label_dev, int64_t n, int batch, int epochs, float lr, float lr_min,
                                  float* epoch_loss);
 
+/* ------------------------------------------------------------------------
+ * Robust spot-weight optimisation over the scenarios' influence matrices
+ * (Sec. 2.E: robust optimisation over 13 scenarios, judged by the target
+ * indices of Table 3).  The paper's optimiser is an in-house trial-and-error
+ * procedure; this one minimises the worst case over the scenarios of
+ *   f(d) = w_under/|T| sum_T max(0, D_p - d)^2 + w_over/|T| sum_T max(0, d - over_frac D_p)^2
+ *        + w_ring/|R| sum_R max(0, d - ring_frac D_p)^2,      d = A_s x,
+ * with Adam on the spot weights x, clamped at zero after each step.
+ * T and R are the voxels of class 1 (target) and 2 (ring).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    float prescription;     /* D_p, in the matrices' dose units x weight units */
+    float w_under, w_over, w_ring;
+    float over_frac;        /* target overdose above over_frac * D_p */
+    float ring_frac;        /* ring overdose above ring_frac * D_p */
+    float lr;               /* Adam step, in units of the mean initial weight */
+    int iterations;
+} vpmc_opt_params;
+
+/* mats: n_scen CSR (device buffers, e.g. from vpmc_influence_matrix), all of
+ * the same shape, at most 28,000 columns; row_ptr must be non-decreasing from
+ * 0 to nnz (not checked); entries whose column lies outside [0, n_cols) are
+ * skipped.  voxel_class_dev: uint8 [n_rows],
+ * device.  x_dev: float [n_cols], device: the initial weights in, the
+ * optimised weights out.  history: optional host float [iterations], the
+ * worst-case objective before each step.  ms: optional, device time of the
+ * iterations (CUDA events).  stream: a cudaStream_t (NULL = legacy default).
+ * Allocates its own scratch.  Synchronous. */
+vpmc_status vpmc_robust_optimize(const vpmc_csr* mats, int n_scen, const uint8_t* voxel_class_dev,
+                                 const vpmc_opt_params* params, float* x_dev, float* history, float* ms,
+                                 void* stream);
+
+/* dose_dev[i] = sum_j A_ij x_j for one CSR matrix (device float
+ * [n_rows], caller-owned): the dose of the weights x.  Synchronous. */
+vpmc_status vpmc_weights_dose(const vpmc_csr* mat, const float* x_dev, float* dose_dev, void* stream);
+
+/* Target indices (Table 3) of the dose A_s x of each scenario:
+ *   out[4 s + 0] V100 (fraction of T with d >= D_p)
+ *   out[4 s + 1] min_T d / D_p
+ *   out[4 s + 2] CI100 = |{d >= D_p}| / |T|
+ *   out[4 s + 3] RHI100 = max_T d / D_p
+ * out is a host array.  Synchronous. */
+vpmc_status vpmc_target_indices(const vpmc_csr* mats, int n_scen, const uint8_t* voxel_class_dev,
+                                float prescription, const float* x_dev, double* out, void* stream);
+
 /* Destroy a context and free its device memory. */
 void vpmc_destroy(vpmc_ctx* ctx);
 

@@ -60,8 +60,10 @@ def robust_objective(mats: Sequence, x: np.ndarray, cls: np.ndarray, p: OptParam
     return float(fs[s]), fs, s, doses
 
 
-def optimise(mats: Sequence, x0: np.ndarray, cls: np.ndarray, p: OptParams, iterations: int):
-    """Run the iterations; returns (x, worst-case objective before each step)."""
+def optimise(mats: Sequence, x0: np.ndarray, cls: np.ndarray, p: OptParams, iterations: int,
+             trace: List | None = None):
+    """Run the iterations; returns (x, worst-case objective before each step).
+    trace, if given, receives every iteration's per-scenario objectives."""
     x = np.asarray(x0, dtype=np.float64).copy()
     m = np.zeros_like(x)
     v = np.zeros_like(x)
@@ -70,6 +72,8 @@ def optimise(mats: Sequence, x0: np.ndarray, cls: np.ndarray, p: OptParams, iter
     for t in range(1, iterations + 1):
         F, fs, s, doses = robust_objective(mats, x, cls, p)
         hist.append(F)
+        if trace is not None:
+            trace.append(fs)
         _, r = objective(doses[s], cls, p)
         g = np.asarray(mats[s].T @ r, dtype=np.float64)
         m = 0.9 * m + 0.1 * g

@@ -1476,3 +1476,123 @@ vpmc_status vpmc_surrogate_tracks(vpmc_ctx* c, const int* beam_ids, int n_beams,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Robust spot-weight optimisation.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct OptInputs {
+    std::vector<const long long*> rp;
+    std::vector<const int*> col;
+    std::vector<const float*> val;
+    long long n_rows = 0;
+    int n_cols = 0;
+    long long n_target = 0, n_ring = 0;
+};
+
+vpmc_status check_opt_inputs(const vpmc_csr* mats, int n_scen, const uint8_t* cls, OptInputs* in)
+{
+    if (!mats || n_scen <= 0 || n_scen > kMaxScen || !cls) return fail(VPMC_ERR_ARG, "bad matrices or classes");
+    in->n_rows = mats[0].n_rows;
+    in->n_cols = (int)mats[0].n_cols;
+    for (int s = 0; s < n_scen; ++s) {
+        if (mats[s].n_rows != in->n_rows || mats[s].n_cols != mats[0].n_cols)
+            return fail(VPMC_ERR_ARG, "scenario %d: matrix shape differs", s);
+        if (!mats[s].row_ptr || (mats[s].nnz > 0 && (!mats[s].col || !mats[s].val)))
+            return fail(VPMC_ERR_ARG, "scenario %d: null CSR buffer", s);
+        in->rp.push_back(reinterpret_cast<const long long*>(mats[s].row_ptr));
+        in->col.push_back(mats[s].col);
+        in->val.push_back(mats[s].val);
+    }
+    if (in->n_rows <= 0 || in->n_cols <= 0) return fail(VPMC_ERR_ARG, "empty matrices");
+    if ((size_t)in->n_cols > 28000) return fail(VPMC_ERR_ARG, "%d columns: at most 28,000", in->n_cols);
+    std::vector<unsigned char> h((size_t)in->n_rows);
+    if (cudaMemcpy(h.data(), cls, h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(VPMC_ERR_CUDA, "reading the voxel classes: %s", cudaGetErrorString(cudaGetLastError()));
+    for (unsigned char c : h) {
+        in->n_target += c == 1;
+        in->n_ring += c == 2;
+    }
+    return VPMC_OK;
+}
+
+int current_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+vpmc_status vpmc_robust_optimize(const vpmc_csr* mats, int n_scen, const uint8_t* voxel_class_dev,
+                                 const vpmc_opt_params* prm, float* x_dev, float* history, float* ms, void* stream)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!prm || !x_dev) return fail(VPMC_ERR_ARG, "null params or weights");
+    if (prm->iterations < 0 || !(prm->prescription > 0.0f) || !(prm->lr > 0.0f) || !(prm->over_frac >= 1.0f) ||
+        !(prm->ring_frac > 0.0f) || prm->w_under < 0.0f || prm->w_over < 0.0f || prm->w_ring < 0.0f)
+        return fail(VPMC_ERR_ARG, "invalid optimisation parameters");
+    OptInputs in;
+    vpmc_status st = check_opt_inputs(mats, n_scen, voxel_class_dev, &in);
+    if (st != VPMC_OK) return st;
+    if (in.n_target == 0) return fail(VPMC_ERR_ARG, "no target voxels (class 1)");
+    std::vector<float> x0((size_t)in.n_cols);
+    CUDA_TRY(cudaMemcpy(x0.data(), x_dev, x0.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    double mean = 0.0;
+    for (float v : x0) {
+        if (!(v >= 0.0f) || !std::isfinite(v)) return fail(VPMC_ERR_ARG, "initial weights must be finite and >= 0");
+        mean += v;
+    }
+    mean /= (double)x0.size();
+    OptSpec spec;
+    spec.dp = prm->prescription;
+    spec.w_u = prm->w_under;
+    spec.w_o = prm->w_over;
+    spec.w_r = prm->w_ring;
+    spec.over = prm->over_frac;
+    spec.ring = prm->ring_frac;
+    spec.n_target = in.n_target;
+    spec.n_ring = in.n_ring;
+    spec.step = (float)(prm->lr * (mean > 0.0 ? mean : 1.0));
+    spec.eps = 1e-8f;
+    spec.iterations = prm->iterations;
+    float t = 0.0f;
+    CUDA_TRY(run_robust_optimize(in.rp.data(), in.col.data(), in.val.data(), n_scen, in.n_rows, in.n_cols,
+                                 voxel_class_dev, spec, x_dev, history, (cudaStream_t)stream, current_sms(), &t));
+    if (ms) *ms = t;
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_weights_dose(const vpmc_csr* mat, const float* x_dev, float* dose_dev, void* stream)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!mat || !x_dev || !dose_dev || !mat->row_ptr || mat->n_rows <= 0 || mat->n_cols <= 0 ||
+        mat->n_cols > INT32_MAX || (mat->nnz > 0 && (!mat->col || !mat->val)))
+        return fail(VPMC_ERR_ARG, "bad argument");
+    CUDA_TRY(run_weights_dose(reinterpret_cast<const long long*>(mat->row_ptr), mat->col, mat->val, mat->n_rows,
+                              (int)mat->n_cols, x_dev, dose_dev, (cudaStream_t)stream, current_sms()));
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_target_indices(const vpmc_csr* mats, int n_scen, const uint8_t* voxel_class_dev,
+                                float prescription, const float* x_dev, double* out, void* stream)
+{
+    g_error.clear();
+    (void)cudaGetLastError();
+    if (!x_dev || !out || !(prescription > 0.0f)) return fail(VPMC_ERR_ARG, "bad argument");
+    OptInputs in;
+    vpmc_status st = check_opt_inputs(mats, n_scen, voxel_class_dev, &in);
+    if (st != VPMC_OK) return st;
+    CUDA_TRY(run_target_indices(in.rp.data(), in.col.data(), in.val.data(), n_scen, in.n_rows, in.n_cols,
+                                voxel_class_dev, prescription, x_dev, out, (cudaStream_t)stream, current_sms()));
+    return VPMC_OK;
+}
+
+}  // extern "C"

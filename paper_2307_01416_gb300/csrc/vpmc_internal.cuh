@@ -261,6 +261,25 @@ cudaError_t launch_sur_infer(const SurNet& net, const TransportParams& p, int gr
 size_t sur_forward_smem_bytes();
 size_t sur_train_smem_bytes();
 
+// Robust spot-weight optimisation (optimize.cu).  Matrices: n_scen CSR of
+// n_rows x n_cols (device pointers); cls: uint8 voxel classes (1 target,
+// 2 ring); x: device weights, optimised in place.
+struct OptSpec {
+    float dp, w_u, w_o, w_r, over, ring;    // prescription, weights, over- and ring-dose fractions
+    long long n_target, n_ring;
+    float step, eps;                        // Adam step (absolute) and epsilon
+    int iterations;
+};
+size_t opt_spmvT_smem(int n_cols);
+cudaError_t run_robust_optimize(const long long* const* rp, const int* const* col, const float* const* val, int n_scen,
+                                long long n_rows, int n_cols, const unsigned char* cls, const OptSpec& spec, float* x,
+                                float* hist_host, cudaStream_t st, int num_sms, float* ms_out);
+cudaError_t run_weights_dose(const long long* rp, const int* col, const float* val, long long n_rows, int n_cols,
+                             const float* x, float* dose, cudaStream_t st, int num_sms);
+cudaError_t run_target_indices(const long long* const* rp, const int* const* col, const float* const* val, int n_scen,
+                               long long n_rows, int n_cols, const unsigned char* cls, float dp, const float* x,
+                               double* out, cudaStream_t st, int num_sms);
+
 cudaError_t launch_scoring_density(const int16_t* ct, Grid3 ctg, Grid3 sg, const double* curve15_dev,
                                    const double ct_spacing[3], const double sg_spacing[3], double* rho_out,
                                    cudaStream_t s);

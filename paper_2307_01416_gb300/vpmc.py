@@ -65,6 +65,11 @@ class vpmc_opts(C.Structure):
                 ("history_cap", C.c_int64), ("range_rejection", C.c_int), ("surrogate", C.c_int)]
 
 
+class vpmc_opt_params(C.Structure):
+    _fields_ = [("prescription", C.c_float), ("w_under", C.c_float), ("w_over", C.c_float), ("w_ring", C.c_float),
+                ("over_frac", C.c_float), ("ring_frac", C.c_float), ("lr", C.c_float), ("iterations", C.c_int)]
+
+
 class vpmc_stats(C.Structure):
     _fields_ = [("histories", C.c_int64), ("steps", C.c_int64), ("errors", C.c_int64), ("e_in", C.c_double),
                 ("e_dep", C.c_double), ("e_leak", C.c_double), ("e_rs", C.c_double), ("e_aperture", C.c_double),
@@ -84,7 +89,8 @@ assert RECORD_DTYPE.itemsize == 40
 EXPORTED = ["vpmc_default_opts", "vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots",
             "vpmc_run_spots_noalloc", "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_destroy", "vpmc_last_error",
             "vpmc_surrogate_init", "vpmc_surrogate_set_weights", "vpmc_surrogate_get_weights",
-            "vpmc_surrogate_tracks", "vpmc_surrogate_forward", "vpmc_surrogate_gradient", "vpmc_surrogate_train"]
+            "vpmc_surrogate_tracks", "vpmc_surrogate_forward", "vpmc_surrogate_gradient", "vpmc_surrogate_train",
+            "vpmc_robust_optimize", "vpmc_target_indices", "vpmc_weights_dose"]
 
 SUR_NPARAMS = 23213            # VPMC_SUR_NPARAMS
 SUR_IN, SUR_OUT, SUR_Y = 6, 45, 5
@@ -127,6 +133,12 @@ def lib():
     L.vpmc_surrogate_forward.argtypes = [vp, vp, C.c_int64, vp]
     L.vpmc_surrogate_gradient.argtypes = [vp, vp, vp, vp, C.c_int64, vp, C.POINTER(C.c_double)]
     L.vpmc_surrogate_train.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_float, fp]
+    L.vpmc_robust_optimize.argtypes = [C.POINTER(vpmc_csr), C.c_int, vp, C.POINTER(vpmc_opt_params), vp,
+                                       C.POINTER(C.c_float), C.POINTER(C.c_float), vp]
+    L.vpmc_target_indices.argtypes = [C.POINTER(vpmc_csr), C.c_int, vp, C.c_float, vp, C.POINTER(C.c_double), vp]
+    L.vpmc_weights_dose.argtypes = [C.POINTER(vpmc_csr), vp, vp, vp]
+    for f in ("vpmc_robust_optimize", "vpmc_target_indices", "vpmc_weights_dose"):
+        getattr(L, f).restype = C.c_int
     for f in ("vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots", "vpmc_run_spots_noalloc",
               "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_surrogate_init", "vpmc_surrogate_set_weights",
               "vpmc_surrogate_get_weights", "vpmc_surrogate_tracks", "vpmc_surrogate_forward",
@@ -387,3 +399,56 @@ def train_surrogate(tracks_per_beam: int = 2_000_000, epochs: int = 4, batch: in
     finally:
         if own:
             eng.close()
+
+
+# ------------------------------------------------------------------ robust optimisation
+def _csr_array(mats):
+    """vpmc_csr structs over torch CSR dicts (row_ptr int64, col int32, val float32, shape)."""
+    arr = (vpmc_csr * len(mats))()
+    for i, m in enumerate(mats):
+        arr[i].n_rows, arr[i].n_cols = int(m["shape"][0]), int(m["shape"][1])
+        arr[i].nnz = int(m["val"].numel())
+        arr[i].row_ptr = m["row_ptr"].data_ptr()
+        arr[i].col = m["col"].data_ptr() if arr[i].nnz else None
+        arr[i].val = m["val"].data_ptr() if arr[i].nnz else None
+    return arr
+
+
+def robust_optimize(mats, voxel_class, x, prescription: float, iterations: int = 200, lr: float = 0.05,
+                    w_under: float = 1.0, w_over: float = 0.5, w_ring: float = 0.2, over_frac: float = 1.05,
+                    ring_frac: float = 0.6, stream=None):
+    """Optimise the weights x (float32 device tensor, in place) over the
+    scenarios' matrices; returns (worst-case objective per iteration, device ms)."""
+    import torch
+    arr = _csr_array(mats)
+    p = vpmc_opt_params(float(prescription), float(w_under), float(w_over), float(w_ring), float(over_frac),
+                        float(ring_frac), float(lr), int(iterations))
+    hist = np.zeros(max(int(iterations), 1), dtype=np.float32)
+    ms = C.c_float()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().vpmc_robust_optimize(arr, len(mats), C.c_void_p(voxel_class.data_ptr()), C.byref(p),
+                                      C.c_void_p(x.data_ptr()), hist.ctypes.data_as(C.POINTER(C.c_float)),
+                                      C.byref(ms), C.c_void_p(st.cuda_stream)))
+    return hist[:int(iterations)], ms.value
+
+
+def target_indices(mats, voxel_class, prescription: float, x, stream=None) -> np.ndarray:
+    """(n_scen, 4): V100, D_min / D_p, CI100, RHI100 of the dose A_s x."""
+    import torch
+    arr = _csr_array(mats)
+    out = np.zeros(4 * len(mats), dtype=np.float64)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().vpmc_target_indices(arr, len(mats), C.c_void_p(voxel_class.data_ptr()), float(prescription),
+                                     C.c_void_p(x.data_ptr()), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                     C.c_void_p(st.cuda_stream)))
+    return out.reshape(len(mats), 4)
+
+
+def weights_dose(mat, x, stream=None):
+    """Dose A x of one CSR matrix (float32 device tensor)."""
+    import torch
+    arr = _csr_array([mat])
+    d = torch.empty(int(mat["shape"][0]), dtype=torch.float32, device=x.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().vpmc_weights_dose(arr, C.c_void_p(x.data_ptr()), C.c_void_p(d.data_ptr()), C.c_void_p(st.cuda_stream)))
+    return d

@@ -398,3 +398,94 @@ def surrogate_training_beams(radii=SURROGATE_RADII, n_vertices: int = 128, thick
                           ap_present=True, ap_thickness=thickness, ap_down_to_iso=down_to_iso,
                           polygon=regular_polygon(float(r), n_vertices)))
     return beams
+
+
+# --------------------------------------------------------------------------
+# Structures for the robust optimisation (Sec. 2.E, Table 3).
+# --------------------------------------------------------------------------
+def structure_classes(grid: Grid, center, r_target: float, ring_mm: float = 10.0) -> np.ndarray:
+    """uint8 per voxel of grid (x fastest): 1 inside the spherical target,
+    2 in the shell up to ring_mm outside it, 0 elsewhere."""
+    ax = [grid.centers(k) for k in range(3)]
+    X, Y, Z = np.meshgrid(ax[0], ax[1], ax[2], indexing="ij")
+    r = np.sqrt((X - center[0]) ** 2 + (Y - center[1]) ** 2 + (Z - center[2]) ** 2)
+    c = np.zeros(r.shape, dtype=np.uint8)
+    c[r <= r_target + ring_mm] = 2
+    c[r <= r_target] = 1
+    return np.ascontiguousarray(c.transpose(2, 1, 0)).reshape(-1)
+
+
+def synthetic_spot_matrices(shape=(36, 36, 40), n_spots: int = 300, n_scen: int = 3, seed: int = 11,
+                            sigma_vox: float = 1.6, halo: float = 3.0, shift_vox: float = 1.0,
+                            range_frac: float = 0.035, empty_spots: int = 2):
+    """Seeded stand-ins for influence matrices (Sec. 2.C): voxels x spots CSR
+    (dicts of numpy row_ptr int64, col int32, val float32, shape), one per
+    scenario.  Spot j deposits in a lateral box of halo*sigma_vox around its
+    centre, from the entrance (z = 0) to just past its peak depth: a Gaussian
+    lateral profile times a plateau of 0.3 plus a peak of width 2 voxels.
+    Scenario s (like robust_scenarios): 1..6 shift every spot by shift_vox
+    along +x, -x, +y, -y, +z, -z (z moves the peak); 7..12 repeat the shifts
+    with the peak depth scaled by 1 + range_frac (+ shifts) or 1 - range_frac.
+    The last empty_spots spots lie outside the grid (empty columns); rows are
+    voxels x + nx (y + ny z), and most rows far from the spots are empty."""
+    nx, ny, nz = shape
+    g = np.random.default_rng(seed)
+    cx = g.uniform(0.25 * nx, 0.75 * nx, n_spots)
+    cy = g.uniform(0.25 * ny, 0.75 * ny, n_spots)
+    zr = g.uniform(0.35 * nz, 0.8 * nz, n_spots)
+    amp = g.uniform(0.5, 1.5, n_spots)
+    if empty_spots:
+        cx[-empty_spots:] = -10.0 * nx
+    h = int(np.ceil(halo * sigma_vox))
+    shifts = [(0.0, 0.0, 0.0, 1.0)]
+    for k in range(1, n_scen):
+        ax, sgn = ((k - 1) // 2) % 3, (1.0 if (k - 1) % 2 == 0 else -1.0)
+        sc = 1.0 + (sgn * range_frac if k > 6 else 0.0)
+        d = [0.0, 0.0, 0.0]
+        d[ax] = sgn * shift_vox
+        shifts.append((d[0], d[1], d[2], sc))
+    mats = []
+    for (sx, sy, sz, sc) in shifts[:n_scen]:
+        rows, cols, vals = [], [], []
+        for j in range(n_spots):
+            x0, y0, z0 = cx[j] + sx, cy[j] + sy, zr[j] * sc + sz
+            ix = np.arange(int(np.floor(x0)) - h, int(np.floor(x0)) + h + 2)
+            iy = np.arange(int(np.floor(y0)) - h, int(np.floor(y0)) + h + 2)
+            iz = np.arange(0, min(int(np.ceil(z0 + 4.0)), nz))
+            ix, iy = ix[(ix >= 0) & (ix < nx)], iy[(iy >= 0) & (iy < ny)]
+            if ix.size == 0 or iy.size == 0 or iz.size == 0:
+                continue
+            Z, Y, X = np.meshgrid(iz, iy, ix, indexing="ij")
+            r2 = (X + 0.5 - x0) ** 2 + (Y + 0.5 - y0) ** 2
+            dz = Z + 0.5 - z0
+            depth = np.where(dz <= 0.0, 0.3 + np.exp(-0.5 * dz * dz / 4.0), np.exp(-0.5 * dz * dz))
+            v = amp[j] * np.exp(-0.5 * r2 / sigma_vox ** 2) * depth
+            keep = (r2 <= (halo * sigma_vox) ** 2) & (v > 1e-4)
+            rows.append((X + nx * (Y + ny * Z))[keep].astype(np.int64))
+            cols.append(np.full(int(keep.sum()), j, dtype=np.int32))
+            vals.append(v[keep].astype(np.float32))
+        r = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+        c = np.concatenate(cols) if cols else np.zeros(0, np.int32)
+        v = np.concatenate(vals) if vals else np.zeros(0, np.float32)
+        o = np.lexsort((c, r))
+        r, c, v = r[o], c[o], v[o]
+        nvox = nx * ny * nz
+        row_ptr = np.zeros(nvox + 1, dtype=np.int64)
+        np.cumsum(np.bincount(r, minlength=nvox), out=row_ptr[1:])
+        mats.append({"row_ptr": row_ptr, "col": c, "val": v, "shape": (nvox, n_spots)})
+    return mats
+
+
+def synthetic_structure_classes(shape=(36, 36, 40), r_target: float = 7.0, ring: float = 3.0,
+                                center=None) -> np.ndarray:
+    """uint8 classes on the voxel order of synthetic_spot_matrices: 1 in a
+    sphere of radius r_target voxels (centre default: the grid's middle at
+    0.6 of its depth), 2 in the shell of width ring around it."""
+    nx, ny, nz = shape
+    c = center if center is not None else (0.5 * nx, 0.5 * ny, 0.6 * nz)
+    Z, Y, X = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    r = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
+    out = np.zeros(r.shape, dtype=np.uint8)
+    out[r <= r_target + ring] = 2
+    out[r <= r_target] = 1
+    return out.reshape(-1)
