@@ -190,6 +190,12 @@ __device__ __forceinline__ float coop_wall_distance(bool need, float x, float y,
 __device__ __forceinline__ float4 coop_nearest_edge(bool need, float x, float y, const float2* __restrict__ poly,
                                                     const float* __restrict__ kappa, int off, int n, int lane)
 {
+    // Returns (distance, p - q, curvature at q) for the nearest boundary point
+    // q of the query p.  Every difference is taken between nearby points
+    // (a - p, b - a: exact when within a factor two), never as a + t e at the
+    // opening's radius: near the corner between an edge region and a vertex
+    // region two candidates' distances can differ by ~1e-7 mm, below the
+    // rounding of a coordinate of tens of mm.
     float4 result = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned m = __ballot_sync(kFull, need);
     while (m) {
@@ -203,9 +209,10 @@ __device__ __forceinline__ float4 coop_nearest_edge(bool need, float x, float y,
             const float2 a = poly[qo + i];
             const float2 b = poly[qo + (i + 1 < qn ? i + 1 : 0)];
             const float ex = b.x - a.x, ey = b.y - a.y;
-            float t = ((qx - a.x) * ex + (qy - a.y) * ey) / (ex * ex + ey * ey);
+            const float ax = a.x - qx, ay = a.y - qy;
+            float t = -(ax * ex + ay * ey) / (ex * ex + ey * ey);
             t = fminf(fmaxf(t, 0.0f), 1.0f);
-            const float ddx = a.x + t * ex - qx, ddy = a.y + t * ey - qy;
+            const float ddx = fmaf(t, ex, ax), ddy = fmaf(t, ey, ay);
             const float d2 = ddx * ddx + ddy * ddy;
             if (d2 < best) { best = d2; bi = i; bt = t; }
         }
@@ -220,7 +227,7 @@ __device__ __forceinline__ float4 coop_nearest_edge(bool need, float x, float y,
             const int bj = bi + 1 < qn ? bi + 1 : 0;
             const float2 a = poly[qo + bi], b = poly[qo + bj];
             const float k0 = __ldg(kappa + qo + bi), k1 = __ldg(kappa + qo + bj);
-            result = make_float4(sqrtf(best), a.x + bt * (b.x - a.x), a.y + bt * (b.y - a.y),
+            result = make_float4(sqrtf(best), -fmaf(bt, b.x - a.x, a.x - qx), -fmaf(bt, b.y - a.y, a.y - qy),
                                  fmaf(bt, k1 - k0, k0));
         }
     }
@@ -851,8 +858,8 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             const float T = B.ap_tdn - B.ap_tup;
             const float dist = ne.x;
             const float inv = dist > 0.0f ? 1.0f / dist : 0.0f;
-            fnx = (L.p[0] - ne.y) * inv;
-            fny = (L.p[1] - ne.z) * inv;
+            fnx = ne.y * inv;
+            fny = ne.z * inv;
             const float un = L.d[0] * fnx + L.d[1] * fny, ut = L.d[1] * fnx - L.d[0] * fny;
             const float rmm = L.R / brass.rho;
             feat[0] = fminf(dist, sur::kDCap) * (2.0f / sur::kDCap) - 1.0f;

@@ -141,9 +141,12 @@ def test_track_generator_matches_oracle_deterministic(eng):
     # the residual range on either side of the threshold the proton cannot
     # leave the block whichever way the tie goes, so labels and targets stay.
     # the edge normal (p - q) / |p - q| of a start a few tens of um from the
-    # wall carries the FP32 rounding of p and q (~1e-5 mm at 150 mm) divided
-    # by the distance: up to ~1e-3 in the scaled direction features, below the
-    # BF16 rounding (4e-3 relative) the network input gets anyway
+    # wall carries the FP32 rounding of p (~1e-5 mm at 150 mm) divided by the
+    # distance: up to ~1e-3 in the scaled direction features, below the BF16
+    # rounding (4e-3 relative) the network input gets anyway.  The kernel forms
+    # p - q from differences of nearby points, so a start next to the corner
+    # of an edge region and a vertex region (where the two candidates'
+    # distances differ by ~1e-7 mm) still picks the FP64 candidate
     # the edge distance is drawn as d_hi u^2, so about a tenth of the tracks
     # pass within 10 um of a wall
     flagged = (r["flags"] & 1) != 0
