@@ -53,9 +53,12 @@ def parse_args():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-aperture leg")
     ap.add_argument("--no-optimizer", action="store_true", help="skip the robust-optimisation leg")
     ap.add_argument("--opt-iterations", type=int, default=50)
-    ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im"], default=None,
+    ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im", "opt"], default=None,
                     help="small fixed-launch transport case for ncu captures (nominal scenario, every 10th spot): "
-                         "'dose' scores one grid, 'im' scores influence-matrix columns")
+                         "'dose' scores one grid, 'im' scores influence-matrix columns; 'opt' runs the robust "
+                         "optimisation (--opt-iterations per step) over a 13-scenario set of every --opt-stride-th "
+                         "spot")
+    ap.add_argument("--opt-stride", type=int, default=1)
     return ap.parse_args()
 
 
@@ -348,7 +351,9 @@ def run_ncu_case(args):
     scoring path, small enough for an ncu capture."""
     import torch
     from paper_2307_01416_gb300 import vpmc
-    pb, spots, scens, _ = build_workload(False)
+    pb, spots, scens, target = build_workload(False)
+    if args.ncu_case == "opt":
+        return run_opt_case(args, pb, spots, scens, target)
     sub = spots[::10]
     torch.cuda.set_device(0)
     eng = vpmc.Engine(pb)
@@ -363,6 +368,38 @@ def run_ncu_case(args):
                           "steps": st["steps"], "kernel_ms": st["ms"],
                           "steps_per_s": st["steps"] / (st["ms"] / 1000.0)}))
     eng.close()
+    return 0
+
+
+def run_opt_case(args, pb, spots, scens, target):
+    """The robust optimisation over the 13-scenario set of every
+    opt_stride-th spot (stride 1: the bench's full set, 4.7 GB of CSR; stride
+    4: about 1.2 GB): the set is computed once, then warmup + steps calls of
+    opt_iterations iterations."""
+    import torch
+    from paper_2307_01416_gb300 import vpmc
+    torch.cuda.set_device(0)
+    sub = spots[::args.opt_stride]
+    eng = vpmc.Engine(pb)
+    mats, _ = eng.influence_matrix(sub, scens, W.Options(seed=1234))
+    eng.close()
+    cls_np = W.structure_classes(pb.scoring, target[0], target[1])
+    cls = torch.from_numpy(cls_np).cuda()
+    rl = np.diff(mats[0]["row_ptr"].cpu().numpy())
+    nzr = rl[rl > 0]
+    print("rows %d, non-empty %d, nnz/row over non-empty: mean %.1f, p50 %d, p90 %d, p99 %d, max %d; "
+          "target+ring rows %d with %d nnz" % (rl.size, nzr.size, nzr.mean(), np.percentile(nzr, 50),
+                                               np.percentile(nzr, 90), np.percentile(nzr, 99), nzr.max(),
+                                               int(np.sum(cls_np > 0)), int(rl[cls_np > 0].sum())), file=sys.stderr)
+    x0 = torch.ones(len(sub), dtype=torch.float32, device="cuda")
+    x0 *= 1.0 / float(vpmc.weights_dose(mats[0], x0)[cls == 1].mean())
+    b = optimizer_bytes(mats, cls_np)
+    for i in range(args.warmup + args.steps):
+        x = x0.clone()
+        hist, ms = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=args.opt_iterations)
+        per = ms / args.opt_iterations
+        print(json.dumps({"case": "ncu-opt", "iter": i, "spots": int(len(sub)), "ms_per_iteration": per,
+                          "bytes_per_iteration": b, "GB_per_s": b / per / 1e6, "objective_last": float(hist[-1])}))
     return 0
 
 
