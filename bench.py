@@ -396,9 +396,9 @@ def run_opt_case(args, pb, spots, scens, target):
     b = optimizer_bytes(mats, cls_np)
     for i in range(args.warmup + args.steps):
         x = x0.clone()
-        hist, ms = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=args.opt_iterations)
+        hist, ms, setup_ms = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=args.opt_iterations)
         per = ms / args.opt_iterations
-        print(json.dumps({"case": "ncu-opt", "iter": i, "spots": int(len(sub)), "ms_per_iteration": per,
+        print(json.dumps({"case": "ncu-opt", "iter": i, "spots": int(len(sub)), "ms_per_iteration": per, "setup_ms": setup_ms,
                           "bytes_per_iteration": b, "GB_per_s": b / per / 1e6, "objective_last": float(hist[-1])}))
     return 0
 
@@ -517,7 +517,7 @@ def optimizer_leg(pb, target, mats, args):
     d0 = vpmc.weights_dose(mats[0], x)
     x *= 1.0 / float(d0[cls == 1].mean())
     vpmc.robust_optimize(mats, cls, x.clone(), 1.0, iterations=3)
-    hist, ms = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=args.opt_iterations)
+    hist, ms, setup_ms = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=args.opt_iterations)
     idx = vpmc.target_indices(mats, cls, 1.0, x)
     per_it = ms / 1000.0 / args.opt_iterations
     b = optimizer_bytes(mats, cls_np)

@@ -321,14 +321,19 @@ typedef struct {
 } vpmc_opt_params;
 
 /* mats: n_scen CSR (device buffers, e.g. from vpmc_influence_matrix), all of
- * the same shape, at most 28,000 columns; row_ptr must be non-decreasing from
- * 0 to nnz (not checked); entries whose column lies outside [0, n_cols) are
- * skipped.  voxel_class_dev: uint8 [n_rows],
- * device.  x_dev: float [n_cols], device: the initial weights in, the
+ * the same shape, at most 65,535 columns and 2^31 - 1 rows; row_ptr must be
+ * non-decreasing from 0 to nnz (not checked); entries whose column lies
+ * outside [0, n_cols) are skipped.  voxel_class_dev: uint8 [n_rows], device
+ * (1 target, 2 ring, other values ignored; at least one target voxel).
+ * x_dev: float [n_cols], device: the initial weights (finite, >= 0) in, the
  * optimised weights out.  history: optional host float [iterations], the
- * worst-case objective before each step.  ms: optional, device time of the
- * iterations (CUDA events).  stream: a cudaStream_t (NULL = legacy default).
- * Allocates its own scratch.  Synchronous. */
+ * worst-case objective before each step.  ms: optional host float [2]: device
+ * time of the iterations, then of the setup (CUDA events).  stream: a
+ * cudaStream_t (NULL = legacy default).
+ * Only target and ring voxels enter the objective, so the call first copies
+ * their rows of every matrix into a compact form and its transpose (scratch
+ * of about 14 bytes per such entry, allocated and freed by the call), then
+ * iterates on those.  Synchronous. */
 vpmc_status vpmc_robust_optimize(const vpmc_csr* mats, int n_scen, const uint8_t* voxel_class_dev,
                                  const vpmc_opt_params* params, float* x_dev, float* history, float* ms,
                                  void* stream);

@@ -1489,6 +1489,7 @@ struct OptInputs {
     long long n_rows = 0;
     int n_cols = 0;
     long long n_target = 0, n_ring = 0;
+    std::vector<unsigned char> cls;         // host copy of the voxel classes
 };
 
 vpmc_status check_opt_inputs(const vpmc_csr* mats, int n_scen, const uint8_t* cls, OptInputs* in)
@@ -1505,9 +1506,11 @@ vpmc_status check_opt_inputs(const vpmc_csr* mats, int n_scen, const uint8_t* cl
         in->col.push_back(mats[s].col);
         in->val.push_back(mats[s].val);
     }
-    if (in->n_rows <= 0 || in->n_cols <= 0) return fail(VPMC_ERR_ARG, "empty matrices");
-    if ((size_t)in->n_cols > 28000) return fail(VPMC_ERR_ARG, "%d columns: at most 28,000", in->n_cols);
-    std::vector<unsigned char> h((size_t)in->n_rows);
+    if (in->n_rows <= 0 || mats[0].n_cols <= 0) return fail(VPMC_ERR_ARG, "empty matrices");
+    if (mats[0].n_cols > 65535) return fail(VPMC_ERR_ARG, "%lld columns: at most 65,535", (long long)mats[0].n_cols);
+    if (in->n_rows > INT32_MAX) return fail(VPMC_ERR_ARG, "more than 2^31 - 1 rows");
+    std::vector<unsigned char>& h = in->cls;
+    h.resize((size_t)in->n_rows);
     if (cudaMemcpy(h.data(), cls, h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(VPMC_ERR_CUDA, "reading the voxel classes: %s", cudaGetErrorString(cudaGetLastError()));
     for (unsigned char c : h) {
@@ -1562,10 +1565,13 @@ vpmc_status vpmc_robust_optimize(const vpmc_csr* mats, int n_scen, const uint8_t
     spec.step = (float)(prm->lr * (mean > 0.0 ? mean : 1.0));
     spec.eps = 1e-8f;
     spec.iterations = prm->iterations;
-    float t = 0.0f;
+    float t[2] = {0.0f, 0.0f};
     CUDA_TRY(run_robust_optimize(in.rp.data(), in.col.data(), in.val.data(), n_scen, in.n_rows, in.n_cols,
-                                 voxel_class_dev, spec, x_dev, history, (cudaStream_t)stream, current_sms(), &t));
-    if (ms) *ms = t;
+                                 in.cls.data(), spec, x_dev, history, (cudaStream_t)stream, t, nullptr));
+    if (ms) {
+        ms[0] = t[0];
+        ms[1] = t[1];
+    }
     return VPMC_OK;
 }
 

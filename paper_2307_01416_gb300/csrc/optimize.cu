@@ -5,16 +5,20 @@
 // scenarios of quadratic target under- and overdose and ring-overdose
 // penalties, minimised by Adam with non-negative weights.
 //
-// One iteration, all on the device (no host synchronisation):
-//   k_spmv_obj   d_s = A_s x for every scenario s (sub-warp per row, CSR) and
-//                the scenario's objective f_s (block sums, FP64 atomics);
-//   k_select     s* = first s with the largest f_s; records the worst case;
-//   k_spmvT      g = A_s*^T f'(d_s*): each block accumulates its rows'
-//                contributions per spot in shared memory (FP64), then adds
-//                them to g with one atomic per spot;
-//   k_adam_proj  Adam step on x, clamped at zero; clears g.
-// Every kernel streams the matrices once per use: the iteration is bound by
-// HBM (13 SpMV + 1 transposed SpMV over ~0.35 GB of CSR each).
+// Only target and ring voxels enter the objective and its gradient, so one
+// setup pass per call copies those rows of every scenario into
+//   a compact CSR (16-bit spot indices, rows padded to 8 entries: one
+//   16-byte load of columns, two of values per lane and step), and
+//   its transpose (CSC over the same rows, columns padded to 4 entries),
+// and each iteration then runs two kernels, with no host synchronisation:
+//   k_fwd        d_s = A_s x on the compact rows of every scenario (a warp per
+//                row) and the scenario's objective f_s (FP64 block sums);
+//   k_bwd_adam   s* = first s with the largest f_s (every block), records it;
+//                g_j = sum_i A_s*,ij f'(d_i) down spot j's compact column (a
+//                warp per spot, FP64 sum), then Adam on x_j, clamped at zero.
+// Both stream their compact arrays once per iteration: HBM-bound.
+// Full-matrix products (dose of the weights, target indices over all
+// voxels) use k_spmv_obj: a sub-warp per row of the caller's CSR.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -107,61 +111,6 @@ __global__ void k_spmv_obj(const Csr* __restrict__ mats, long long n_rows, int n
     }
 }
 
-__global__ void k_select(const double* __restrict__ fsum, int n_scen, int* __restrict__ worst,
-                         float* __restrict__ hist, int it)
-{
-    int s = 0;
-    for (int k = 1; k < n_scen; ++k)
-        if (fsum[k] > fsum[s]) s = k;
-    *worst = s;
-    if (hist) hist[it] = (float)fsum[s];
-}
-
-// g += A_s*^T f'(d_s*): shared-memory FP64 accumulation per spot, then one
-// global atomic per spot and block.
-__global__ void k_spmvT(const Csr* __restrict__ mats, long long n_rows, int n_cols, const int* __restrict__ worst,
-                        const float* __restrict__ dose, const unsigned char* __restrict__ cls, ObjParams q,
-                        double* __restrict__ g)
-{
-    extern __shared__ double gs[];
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) gs[j] = 0.0;
-    __syncthreads();
-    const int s = *worst;
-    const Csr A = mats[s];
-    const float* d = dose + (long long)s * n_rows;
-    const int sub = threadIdx.x & (kLanesPerRow - 1);
-    const long long groups = (long long)gridDim.x * (blockDim.x / kLanesPerRow);
-    for (long long row = (long long)blockIdx.x * (blockDim.x / kLanesPerRow) + threadIdx.x / kLanesPerRow;
-         row < n_rows; row += groups) {
-        const unsigned char c = __ldg(cls + row);
-        if (c != 1 && c != 2) continue;
-        const float r = obj_grad(__ldg(d + row), c, q);
-        if (r == 0.0f) continue;
-        const long long b = __ldg(A.row_ptr + row), e = __ldg(A.row_ptr + row + 1);
-        for (long long k = b + sub; k < e; k += kLanesPerRow) {
-            const int j = __ldg(A.col + k);
-            if ((unsigned)j < (unsigned)n_cols) atomicAdd(gs + j, (double)(__ldg(A.val + k) * r));
-        }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x)
-        if (gs[j] != 0.0) atomicAdd(g + j, gs[j]);
-}
-
-// Adam (Kingma & Ba 2015) with the weights clamped at zero; clears g.
-__global__ void k_adam_proj(float* __restrict__ x, double* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int n, float step, float c1, float c2, float eps)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const float gj = (float)g[j];
-    g[j] = 0.0;
-    const float mj = fmaf(0.9f, m[j], 0.1f * gj), vj = fmaf(0.999f, v[j], 0.001f * gj * gj);
-    m[j] = mj;
-    v[j] = vj;
-    x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
-}
-
 // Per scenario: [count(d >= D_p in T), count(T), count(d >= D_p), min_T d, max_T d]
 // (min/max as FP32 bit patterns of non-negative doses, atomicMin/Max on ints).
 __global__ void k_indices(const float* __restrict__ dose, long long n_rows, const unsigned char* __restrict__ cls,
@@ -210,33 +159,188 @@ __global__ void k_init_minmax(int* minmax, int n_scen)
     }
 }
 
+constexpr int kPadRow = 8;                      // compact CSR row padding (entries)
+constexpr int kPadCol = 4;                      // CSC column padding (entries)
+
+// len[s n_tr + i] = entries of target/ring row tr_rows[i] in scenario s.
+__global__ void k_tr_len(const Csr* __restrict__ mats, const int* __restrict__ tr_rows, int n_tr,
+                         long long* __restrict__ len)
+{
+    const int s = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tr) return;
+    const long long* rp = mats[s].row_ptr;
+    const int r = __ldg(tr_rows + i);
+    len[(long long)s * n_tr + i] = __ldg(rp + r + 1) - __ldg(rp + r);
+}
+
+// Copies the target/ring rows into the compact CSR (a warp per row and
+// scenario; pads and entries with an out-of-range spot become (0, 0.0)) and
+// counts each spot's entries for the transpose.
+__global__ void k_tr_gather(const Csr* __restrict__ mats, const int* __restrict__ tr_rows, int n_tr, int n_cols,
+                            const long long* __restrict__ crp, unsigned short* __restrict__ ccol,
+                            float* __restrict__ cval, int* __restrict__ ccount)
+{
+    const int s = blockIdx.y, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n_tr) return;
+    const Csr A = mats[s];
+    const int r = __ldg(tr_rows + i);
+    const long long b = __ldg(A.row_ptr + r), len = __ldg(A.row_ptr + r + 1) - b;
+    const long long dst = crp[(long long)s * (n_tr + 1) + i], plen = crp[(long long)s * (n_tr + 1) + i + 1] - dst;
+    for (long long k = lane; k < plen; k += 32) {
+        int j = 0;
+        float v = 0.0f;
+        if (k < len) {
+            j = __ldg(A.col + b + k);
+            if ((unsigned)j < (unsigned)n_cols) {
+                v = __ldg(A.val + b + k);
+                atomicAdd(ccount + (long long)s * n_cols + j, 1);
+            } else {
+                j = 0;
+            }
+        }
+        ccol[dst + k] = (unsigned short)j;
+        cval[dst + k] = v;
+    }
+}
+
+// Scatters the target/ring rows' entries into the transpose: (compact row
+// index, value) in spot j's column segment.  The order inside a segment
+// follows the atomics; the gradient sums it in FP64.
+__global__ void k_csc_fill(const Csr* __restrict__ mats, const int* __restrict__ tr_rows, int n_tr, int n_cols,
+                           const long long* __restrict__ tcp, int* __restrict__ fill, int* __restrict__ trow,
+                           float* __restrict__ tval)
+{
+    const int s = blockIdx.y, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n_tr) return;
+    const Csr A = mats[s];
+    const int r = __ldg(tr_rows + i);
+    const long long b = __ldg(A.row_ptr + r), e = __ldg(A.row_ptr + r + 1);
+    for (long long k = b + lane; k < e; k += 32) {
+        const int j = __ldg(A.col + k);
+        if ((unsigned)j >= (unsigned)n_cols) continue;
+        const long long pos = tcp[(long long)s * (n_cols + 1) + j] + atomicAdd(fill + (long long)s * n_cols + j, 1);
+        trow[pos] = i;
+        tval[pos] = __ldg(A.val + k);
+    }
+}
+
+// d_s on the compact rows and f_s; grid (rows / 8, scenarios), 256 threads.
+__global__ void __launch_bounds__(256) k_fwd(const long long* __restrict__ crp, const unsigned short* __restrict__ ccol,
+                                             const float* __restrict__ cval, int n_tr, const float* __restrict__ x,
+                                             const unsigned char* __restrict__ tr_cls, ObjParams q,
+                                             float* __restrict__ dose_tr, double* __restrict__ fsum)
+{
+    const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 8 + warp;
+    float f = 0.0f;
+    if (i < n_tr) {                                   // warp-uniform
+        const long long b = __ldg(crp + (long long)s * (n_tr + 1) + i);
+        const long long e = __ldg(crp + (long long)s * (n_tr + 1) + i + 1);
+        float acc = 0.0f;
+#pragma unroll 2
+        for (long long k = b + lane * kPadRow; k < e; k += 32 * kPadRow) {
+            const uint4 c = __ldcs(reinterpret_cast<const uint4*>(ccol + k));
+            const float4 v0 = __ldcs(reinterpret_cast<const float4*>(cval + k));
+            const float4 v1 = __ldcs(reinterpret_cast<const float4*>(cval + k + 4));
+            acc = fmaf(v0.x, __ldg(x + (c.x & 0xffffu)), acc);
+            acc = fmaf(v0.y, __ldg(x + (c.x >> 16)), acc);
+            acc = fmaf(v0.z, __ldg(x + (c.y & 0xffffu)), acc);
+            acc = fmaf(v0.w, __ldg(x + (c.y >> 16)), acc);
+            acc = fmaf(v1.x, __ldg(x + (c.z & 0xffffu)), acc);
+            acc = fmaf(v1.y, __ldg(x + (c.z >> 16)), acc);
+            acc = fmaf(v1.z, __ldg(x + (c.w & 0xffffu)), acc);
+            acc = fmaf(v1.w, __ldg(x + (c.w >> 16)), acc);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+        if (lane == 0) {
+            dose_tr[(long long)s * n_tr + i] = acc;
+            f = obj_term(acc, __ldg(tr_cls + i), q);
+        }
+    }
+    __shared__ float part[8];
+    if (lane == 0) part[warp] = f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += part[w];
+        if (t != 0.0f) atomicAdd(fsum + s, (double)t);
+    }
+}
+
+// Worst scenario, gradient down each spot's compact column and the Adam step
+// (Kingma & Ba 2015) clamped at zero; grid (spots / 8), 256 threads.
+__global__ void __launch_bounds__(256) k_bwd_adam(const long long* __restrict__ tcp, const int* __restrict__ trow,
+                                                  const float* __restrict__ tval, int n_cols, int n_tr,
+                                                  const float* __restrict__ dose_tr,
+                                                  const unsigned char* __restrict__ tr_cls, ObjParams q,
+                                                  const double* __restrict__ fsum_cur, double* __restrict__ fsum_next,
+                                                  int n_scen, float* __restrict__ hist, int it, float* __restrict__ x,
+                                                  float* __restrict__ m, float* __restrict__ v, float step, float c1,
+                                                  float c2, float eps)
+{
+    __shared__ int s_star;
+    if (threadIdx.x == 0) {
+        int w = 0;
+        for (int k = 1; k < n_scen; ++k)
+            if (fsum_cur[k] > fsum_cur[w]) w = k;
+        s_star = w;
+        if (blockIdx.x == 0 && hist) hist[it] = (float)fsum_cur[w];
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n_scen) fsum_next[threadIdx.x] = 0.0;
+    __syncthreads();
+    const int s = s_star, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= n_cols) return;                          // warp-uniform
+    const long long b = __ldg(tcp + (long long)s * (n_cols + 1) + j);
+    const long long e = __ldg(tcp + (long long)s * (n_cols + 1) + j + 1);
+    const float* d = dose_tr + (long long)s * n_tr;
+    double acc = 0.0;
+    for (long long k = b + lane * kPadCol; k < e; k += 32 * kPadCol) {
+        const int4 r = __ldcs(reinterpret_cast<const int4*>(trow + k));
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(tval + k));
+        acc += (double)a.x * (double)obj_grad(__ldg(d + r.x), __ldg(tr_cls + r.x), q);
+        acc += (double)a.y * (double)obj_grad(__ldg(d + r.y), __ldg(tr_cls + r.y), q);
+        acc += (double)a.z * (double)obj_grad(__ldg(d + r.z), __ldg(tr_cls + r.z), q);
+        acc += (double)a.w * (double)obj_grad(__ldg(d + r.w), __ldg(tr_cls + r.w), q);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+    if (lane == 0) {
+        const float g = (float)acc;
+        const float mj = fmaf(0.9f, m[j], 0.1f * g), vj = fmaf(0.999f, v[j], 0.001f * g * g);
+        m[j] = mj;
+        v[j] = vj;
+        x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // Host side (called from api.cu).
 // ---------------------------------------------------------------------------
+// Device buffers of the full-matrix target indices.
 struct OptWorkspace {
     Csr* mats = nullptr;
     float* dose = nullptr;          // [S x n_rows]
     double* fsum = nullptr;         // [S]
-    int* worst = nullptr;
-    double* g = nullptr;            // [n_cols]
-    float* m = nullptr;
-    float* v = nullptr;
-    float* hist = nullptr;
     unsigned long long* counts = nullptr;
     int* minmax = nullptr;
 };
 
 static void free_ws(OptWorkspace& w)
 {
-    cudaFree(w.mats); cudaFree(w.dose); cudaFree(w.fsum); cudaFree(w.worst); cudaFree(w.g);
-    cudaFree(w.m); cudaFree(w.v); cudaFree(w.hist); cudaFree(w.counts); cudaFree(w.minmax);
+    cudaFree(w.mats); cudaFree(w.dose); cudaFree(w.fsum); cudaFree(w.counts); cudaFree(w.minmax);
     w = OptWorkspace{};
 }
 
 static cudaError_t alloc_ws(OptWorkspace& w, const long long* const* rp, const int* const* col,
-                            const float* const* val, int n_scen, long long n_rows, int n_cols, int iterations)
+                            const float* const* val, int n_scen, long long n_rows)
 {
     std::vector<Csr> h(n_scen);
     for (int s = 0; s < n_scen; ++s) h[s] = Csr{rp[s], col[s], val[s]};
@@ -245,58 +349,169 @@ static cudaError_t alloc_ws(OptWorkspace& w, const long long* const* rp, const i
     if ((e = cudaMemcpy(w.mats, h.data(), sizeof(Csr) * n_scen, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.dose, sizeof(float) * n_scen * n_rows)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.fsum, sizeof(double) * n_scen)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.worst, sizeof(int))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.g, sizeof(double) * std::max(n_cols, 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.m, sizeof(float) * std::max(n_cols, 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.v, sizeof(float) * std::max(n_cols, 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.hist, sizeof(float) * std::max(iterations, 1))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.counts, sizeof(unsigned long long) * 3 * n_scen)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.minmax, sizeof(int) * 2 * n_scen)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-size_t opt_spmvT_smem(int n_cols) { return sizeof(double) * (size_t)n_cols; }
+// Device buffers of one robust optimisation call.
+struct RobustWs {
+    Csr* mats = nullptr;
+    int* tr_rows = nullptr;
+    unsigned char* tr_cls = nullptr;
+    long long* len = nullptr;
+    long long* crp = nullptr;
+    unsigned short* ccol = nullptr;
+    float* cval = nullptr;
+    int* ccount = nullptr;
+    long long* tcp = nullptr;
+    int* fill = nullptr;
+    int* trow = nullptr;
+    float* tval = nullptr;
+    float* dose_tr = nullptr;
+    double* fsum = nullptr;                     // [2 x S]: this iteration's sums, the next one's
+    float* m = nullptr;
+    float* v = nullptr;
+    float* hist = nullptr;
+    ~RobustWs()
+    {
+        cudaFree(mats); cudaFree(tr_rows); cudaFree(tr_cls); cudaFree(len); cudaFree(crp); cudaFree(ccol);
+        cudaFree(cval); cudaFree(ccount); cudaFree(tcp); cudaFree(fill); cudaFree(trow); cudaFree(tval);
+        cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v); cudaFree(hist);
+    }
+};
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t n)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(n, 1));
+}
 
 cudaError_t run_robust_optimize(const long long* const* rp, const int* const* col, const float* const* val, int n_scen,
-                                long long n_rows, int n_cols, const unsigned char* cls, const OptSpec& spec, float* x,
-                                float* hist_host, cudaStream_t st, int num_sms, float* ms_out)
+                                long long n_rows, int n_cols, const unsigned char* cls_host, const OptSpec& spec,
+                                float* x, float* hist_host, cudaStream_t st, float* ms_out, OptSetupInfo* info)
 {
-    OptWorkspace w;
-    cudaError_t e = alloc_ws(w, rp, col, val, n_scen, n_rows, n_cols, spec.iterations);
-    auto done = [&](cudaError_t r) { free_ws(w); return r; };
-    if (e != cudaSuccess) return done(e);
-    ObjParams q{spec.dp, spec.w_u, spec.w_o, spec.w_r, spec.over, spec.ring,
-                1.0f / (float)std::max<long long>(spec.n_target, 1), 1.0f / (float)std::max<long long>(spec.n_ring, 1)};
-    const size_t smem = opt_spmvT_smem(n_cols);
-    if ((e = cudaFuncSetAttribute(k_spmvT, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return done(e);
-    if ((e = cudaMemsetAsync(w.g, 0, sizeof(double) * n_cols, st)) != cudaSuccess) return done(e);
-    if ((e = cudaMemsetAsync(w.m, 0, sizeof(float) * n_cols, st)) != cudaSuccess) return done(e);
-    if ((e = cudaMemsetAsync(w.v, 0, sizeof(float) * n_cols, st)) != cudaSuccess) return done(e);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, st);
-    const dim3 gs((unsigned)(num_sms * 8), (unsigned)n_scen);
-    for (int it = 0; it < spec.iterations; ++it) {
-        cudaMemsetAsync(w.fsum, 0, sizeof(double) * n_scen, st);
-        k_spmv_obj<<<gs, 256, 0, st>>>(w.mats, n_rows, n_cols, x, cls, q, w.dose, w.fsum);
-        k_select<<<1, 1, 0, st>>>(w.fsum, n_scen, w.worst, w.hist, it);
-        k_spmvT<<<num_sms * 2, 512, smem, st>>>(w.mats, n_rows, n_cols, w.worst, w.dose, cls, q, w.g);
-        const double t = it + 1;
-        k_adam_proj<<<(n_cols + 255) / 256, 256, 0, st>>>(x, w.g, w.m, w.v, n_cols, spec.step,
-                                                         (float)(1.0 / (1.0 - std::pow(0.9, t))),
-                                                         (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
+    RobustWs w;
+    cudaError_t e;
+#define OPT_TRY(expr) do { if ((e = (expr)) != cudaSuccess) return e; } while (0)
+    // target and ring rows, in voxel order
+    std::vector<int> rows;
+    std::vector<unsigned char> rcls;
+    for (long long r = 0; r < n_rows; ++r)
+        if (cls_host[r] == 1 || cls_host[r] == 2) {
+            rows.push_back((int)r);
+            rcls.push_back(cls_host[r]);
+        }
+    const int n_tr = (int)rows.size();
+    const int S = n_scen;
+    std::vector<Csr> h(S);
+    for (int s = 0; s < S; ++s) h[s] = Csr{rp[s], col[s], val[s]};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (auto& q : ev) OPT_TRY(cudaEventCreate(&q));
+    struct EvFree {
+        cudaEvent_t* e;
+        ~EvFree() { for (int k = 0; k < 3; ++k) if (e[k]) cudaEventDestroy(e[k]); }
+    } evfree{ev};
+    OPT_TRY(cudaEventRecord(ev[0], st));
+    OPT_TRY(dalloc(&w.mats, S));
+    OPT_TRY(cudaMemcpyAsync(w.mats, h.data(), sizeof(Csr) * S, cudaMemcpyHostToDevice, st));
+    OPT_TRY(dalloc(&w.tr_rows, n_tr));
+    OPT_TRY(dalloc(&w.tr_cls, n_tr));
+    OPT_TRY(cudaMemcpyAsync(w.tr_rows, rows.data(), sizeof(int) * n_tr, cudaMemcpyHostToDevice, st));
+    OPT_TRY(cudaMemcpyAsync(w.tr_cls, rcls.data(), n_tr, cudaMemcpyHostToDevice, st));
+    // compact row layout
+    OPT_TRY(dalloc(&w.len, (size_t)S * n_tr));
+    k_tr_len<<<dim3((unsigned)((n_tr + 255) / 256), (unsigned)S), 256, 0, st>>>(w.mats, w.tr_rows, n_tr, w.len);
+    OPT_TRY(cudaGetLastError());
+    std::vector<long long> len((size_t)S * n_tr), crp((size_t)S * (n_tr + 1));
+    OPT_TRY(cudaMemcpyAsync(len.data(), w.len, sizeof(long long) * len.size(), cudaMemcpyDeviceToHost, st));
+    OPT_TRY(cudaStreamSynchronize(st));
+    long long total_c = 0, nnz_tr = 0;
+    for (int s = 0; s < S; ++s) {
+        for (int i = 0; i < n_tr; ++i) {
+            crp[(size_t)s * (n_tr + 1) + i] = total_c;
+            const long long l = len[(size_t)s * n_tr + i];
+            nnz_tr += l;
+            total_c += (l + kPadRow - 1) / kPadRow * kPadRow;
+        }
+        crp[(size_t)s * (n_tr + 1) + n_tr] = total_c;
     }
-    cudaEventRecord(e1, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(e);
-    if (ms_out) cudaEventElapsedTime(ms_out, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    OPT_TRY(dalloc(&w.crp, crp.size()));
+    OPT_TRY(cudaMemcpyAsync(w.crp, crp.data(), sizeof(long long) * crp.size(), cudaMemcpyHostToDevice, st));
+    OPT_TRY(dalloc(&w.ccol, (size_t)total_c));
+    OPT_TRY(dalloc(&w.cval, (size_t)total_c));
+    OPT_TRY(dalloc(&w.ccount, (size_t)S * n_cols));
+    OPT_TRY(cudaMemsetAsync(w.ccount, 0, sizeof(int) * (size_t)S * n_cols, st));
+    const dim3 gw((unsigned)((n_tr + 7) / 8), (unsigned)S);
+    k_tr_gather<<<gw, 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount);
+    OPT_TRY(cudaGetLastError());
+    // transpose layout
+    std::vector<int> cnt((size_t)S * n_cols);
+    std::vector<long long> tcp((size_t)S * (n_cols + 1));
+    OPT_TRY(cudaMemcpyAsync(cnt.data(), w.ccount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, st));
+    OPT_TRY(cudaStreamSynchronize(st));
+    long long total_t = 0;
+    for (int s = 0; s < S; ++s) {
+        for (int j = 0; j < n_cols; ++j) {
+            tcp[(size_t)s * (n_cols + 1) + j] = total_t;
+            total_t += ((long long)cnt[(size_t)s * n_cols + j] + kPadCol - 1) / kPadCol * kPadCol;
+        }
+        tcp[(size_t)s * (n_cols + 1) + n_cols] = total_t;
+    }
+    OPT_TRY(dalloc(&w.tcp, tcp.size()));
+    OPT_TRY(cudaMemcpyAsync(w.tcp, tcp.data(), sizeof(long long) * tcp.size(), cudaMemcpyHostToDevice, st));
+    OPT_TRY(dalloc(&w.trow, (size_t)total_t));
+    OPT_TRY(dalloc(&w.tval, (size_t)total_t));
+    OPT_TRY(cudaMemsetAsync(w.trow, 0, sizeof(int) * (size_t)std::max<long long>(total_t, 1), st));
+    OPT_TRY(cudaMemsetAsync(w.tval, 0, sizeof(float) * (size_t)std::max<long long>(total_t, 1), st));
+    OPT_TRY(dalloc(&w.fill, (size_t)S * n_cols));
+    OPT_TRY(cudaMemsetAsync(w.fill, 0, sizeof(int) * (size_t)S * n_cols, st));
+    k_csc_fill<<<gw, 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.tcp, w.fill, w.trow, w.tval);
+    OPT_TRY(cudaGetLastError());
+    // iteration state
+    OPT_TRY(dalloc(&w.dose_tr, (size_t)S * n_tr));
+    OPT_TRY(dalloc(&w.fsum, (size_t)2 * S));
+    OPT_TRY(dalloc(&w.m, (size_t)n_cols));
+    OPT_TRY(dalloc(&w.v, (size_t)n_cols));
+    OPT_TRY(dalloc(&w.hist, (size_t)std::max(spec.iterations, 1)));
+    OPT_TRY(cudaMemsetAsync(w.fsum, 0, sizeof(double) * 2 * S, st));
+    OPT_TRY(cudaMemsetAsync(w.m, 0, sizeof(float) * n_cols, st));
+    OPT_TRY(cudaMemsetAsync(w.v, 0, sizeof(float) * n_cols, st));
+    OPT_TRY(cudaEventRecord(ev[1], st));
+    const ObjParams q{spec.dp, spec.w_u, spec.w_o, spec.w_r, spec.over, spec.ring,
+                      1.0f / (float)std::max<long long>(spec.n_target, 1),
+                      1.0f / (float)std::max<long long>(spec.n_ring, 1)};
+    const dim3 gf((unsigned)std::max((n_tr + 7) / 8, 1), (unsigned)S);
+    const unsigned gb = (unsigned)((n_cols + 7) / 8);
+    for (int it = 0; it < spec.iterations; ++it) {
+        double* cur = w.fsum + (it & 1) * S;
+        double* nxt = w.fsum + ((it + 1) & 1) * S;
+        k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, cur);
+        const double t = it + 1;
+        k_bwd_adam<<<gb, 256, 0, st>>>(w.tcp, w.trow, w.tval, n_cols, n_tr, w.dose_tr, w.tr_cls, q, cur, nxt, S,
+                                       w.hist, it, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
+                                       (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
+    }
+    OPT_TRY(cudaGetLastError());
+    OPT_TRY(cudaEventRecord(ev[2], st));
+    OPT_TRY(cudaStreamSynchronize(st));
+    float setup = 0.0f, iters = 0.0f;
+    cudaEventElapsedTime(&setup, ev[0], ev[1]);
+    cudaEventElapsedTime(&iters, ev[1], ev[2]);
+    if (ms_out) {
+        ms_out[0] = iters;
+        ms_out[1] = setup;
+    }
+    if (info) {
+        info->n_tr = n_tr;
+        info->nnz_tr = nnz_tr;
+        info->compact_entries = total_c;
+        info->transpose_entries = total_t;
+    }
     if (hist_host && spec.iterations > 0)
-        e = cudaMemcpy(hist_host, w.hist, sizeof(float) * spec.iterations, cudaMemcpyDeviceToHost);
-    return done(e);
+        OPT_TRY(cudaMemcpy(hist_host, w.hist, sizeof(float) * spec.iterations, cudaMemcpyDeviceToHost));
+#undef OPT_TRY
+    return cudaSuccess;
 }
 
 cudaError_t run_weights_dose(const long long* rp, const int* col, const float* val, long long n_rows, int n_cols,
@@ -328,7 +543,7 @@ cudaError_t run_target_indices(const long long* const* rp, const int* const* col
                                double* out, cudaStream_t st, int num_sms)
 {
     OptWorkspace w;
-    cudaError_t e = alloc_ws(w, rp, col, val, n_scen, n_rows, 1, 1);
+    cudaError_t e = alloc_ws(w, rp, col, val, n_scen, n_rows);
     auto done = [&](cudaError_t r) { free_ws(w); return r; };
     if (e != cudaSuccess) return done(e);
     ObjParams q{dp, 0, 0, 0, 1, 1, 0, 0};

@@ -270,10 +270,13 @@ struct OptSpec {
     float step, eps;                        // Adam step (absolute) and epsilon
     int iterations;
 };
-size_t opt_spmvT_smem(int n_cols);
+struct OptSetupInfo {
+    long long n_tr, nnz_tr;                 // target + ring rows; their entries over all scenarios
+    long long compact_entries, transpose_entries;   // padded sizes of the compact CSR and its transpose
+};
 cudaError_t run_robust_optimize(const long long* const* rp, const int* const* col, const float* const* val, int n_scen,
-                                long long n_rows, int n_cols, const unsigned char* cls, const OptSpec& spec, float* x,
-                                float* hist_host, cudaStream_t st, int num_sms, float* ms_out);
+                                long long n_rows, int n_cols, const unsigned char* cls_host, const OptSpec& spec,
+                                float* x, float* hist_host, cudaStream_t st, float* ms_out, OptSetupInfo* info);
 cudaError_t run_weights_dose(const long long* rp, const int* col, const float* val, long long n_rows, int n_cols,
                              const float* x, float* dose, cudaStream_t st, int num_sms);
 cudaError_t run_target_indices(const long long* const* rp, const int* const* col, const float* const* val, int n_scen,

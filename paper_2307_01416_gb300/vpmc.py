@@ -418,18 +418,19 @@ def robust_optimize(mats, voxel_class, x, prescription: float, iterations: int =
                     w_under: float = 1.0, w_over: float = 0.5, w_ring: float = 0.2, over_frac: float = 1.05,
                     ring_frac: float = 0.6, stream=None):
     """Optimise the weights x (float32 device tensor, in place) over the
-    scenarios' matrices; returns (worst-case objective per iteration, device ms)."""
+    scenarios' matrices; returns (worst-case objective per iteration, device ms
+    of the iterations, device ms of the setup)."""
     import torch
     arr = _csr_array(mats)
     p = vpmc_opt_params(float(prescription), float(w_under), float(w_over), float(w_ring), float(over_frac),
                         float(ring_frac), float(lr), int(iterations))
     hist = np.zeros(max(int(iterations), 1), dtype=np.float32)
-    ms = C.c_float()
+    ms = (C.c_float * 2)()
     st = stream if stream is not None else torch.cuda.current_stream()
     _check(lib().vpmc_robust_optimize(arr, len(mats), C.c_void_p(voxel_class.data_ptr()), C.byref(p),
                                       C.c_void_p(x.data_ptr()), hist.ctypes.data_as(C.POINTER(C.c_float)),
-                                      C.byref(ms), C.c_void_p(st.cuda_stream)))
-    return hist[:int(iterations)], ms.value
+                                      ms, C.c_void_p(st.cuda_stream)))
+    return hist[:int(iterations)], ms[0], ms[1]
 
 
 def target_indices(mats, voxel_class, prescription: float, x, stream=None) -> np.ndarray:

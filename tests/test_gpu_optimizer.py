@@ -80,10 +80,10 @@ def test_trajectory_matches_oracle(torch, name):
     N = 60
     x_ref, h_ref = Q.optimise([_sp(m) for m in mats], x0.astype(np.float64), cls, p, N)
     x = torch.from_numpy(x0.copy()).cuda()
-    h, ms = vpmc.robust_optimize([_dev(torch, m) for m in mats], torch.from_numpy(cls).cuda(), x, DP,
+    h, ms, setup = vpmc.robust_optimize([_dev(torch, m) for m in mats], torch.from_numpy(cls).cuda(), x, DP,
                                  iterations=N, lr=0.1)
     xg = x.cpu().numpy().astype(np.float64)
-    assert ms > 0.0
+    assert ms > 0.0 and setup > 0.0
     assert np.max(np.abs(h - h_ref) / h_ref) <= 1e-4, (h[:5], h_ref[:5])
     assert np.max(np.abs(xg - x_ref)) <= 1e-4 * np.mean(x0)
     assert np.all(xg >= 0.0)
@@ -99,7 +99,7 @@ def test_zero_iterations_and_errors(torch):
     dm = [_dev(torch, m) for m in mats]
     c = torch.from_numpy(cls).cuda()
     x = torch.from_numpy(x0.copy()).cuda()
-    h, _ = vpmc.robust_optimize(dm, c, x, DP, iterations=0)
+    h, _, _ = vpmc.robust_optimize(dm, c, x, DP, iterations=0)
     assert h.size == 0 and np.array_equal(x.cpu().numpy(), x0)
     with pytest.raises(RuntimeError):                        # no target voxels
         vpmc.robust_optimize(dm, torch.zeros_like(c), x, DP, iterations=2)
@@ -114,8 +114,8 @@ def test_zero_iterations_and_errors(torch):
         nv = int(np.prod(shape))
         wide = {"row_ptr": torch.zeros(nv + 1, dtype=torch.int64, device="cuda"),
                 "col": torch.zeros(1, dtype=torch.int32, device="cuda"),
-                "val": torch.zeros(1, dtype=torch.float32, device="cuda"), "shape": (nv, 28_001)}
-        vpmc.robust_optimize([wide], c, torch.ones(28_001, device="cuda"), DP, iterations=1)
+                "val": torch.zeros(1, dtype=torch.float32, device="cuda"), "shape": (nv, 65_536)}
+        vpmc.robust_optimize([wide], c, torch.ones(65_536, device="cuda"), DP, iterations=1)
     assert np.array_equal(x.cpu().numpy(), x0)
 
 
@@ -136,10 +136,10 @@ def test_head_influence_matrices_full_size(torch):
     x = torch.ones(len(spots), dtype=torch.float32, device="cuda")
     d0 = vpmc.weights_dose(mats[0], x)
     x *= 1.0 / float(d0[cls == 1].mean())
-    h, ms = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=40, lr=0.05)
+    h, ms, _ = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=40, lr=0.05)
     assert np.all(np.isfinite(h)) and h[-1] < 0.98 * h[0]
     assert float(x.min()) >= 0.0
-    h1, _ = vpmc.robust_optimize(mats, cls, x.clone(), 1.0, iterations=1, lr=0.05)
+    h1, _, _ = vpmc.robust_optimize(mats, cls, x.clone(), 1.0, iterations=1, lr=0.05)
     p = Q.OptParams(prescription=1.0)
     fs = []
     for m in mats:
