@@ -487,21 +487,25 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
 
 
 def optimizer_bytes(mats, cls: np.ndarray) -> float:
-    """Algorithmic HBM bytes of one robust-optimisation iteration: per
-    scenario the CSR stream (4 B column + 4 B value per entry, 8 B row
-    pointer per row), the voxel class (1 B) and the dose written (4 B) per
-    row; then the transposed product over the target and ring rows of the
-    worst scenario (class 1 B per row; row pointer 8 B, dose 4 B and 8 B per
-    entry of those rows; the mean over scenarios stands for the worst one).
-    The weights (20 KB) stay in L2."""
-    n_rows = int(mats[0]["shape"][0])
+    """Algorithmic HBM bytes of one robust-optimisation iteration on the
+    compact target/ring rows the optimiser builds once per call (rows whose
+    voxel is neither target nor ring do not enter the objective):
+    forward, per scenario: 2 B spot index + 4 B value per entry, 8 B row
+    pointer + 4 B dose written + 1 B class per row; gradient, for the worst
+    scenario (the mean over scenarios stands for it): 4 B row index + 4 B
+    value per entry, 8 B column pointer per spot, 4 B dose + 1 B class per
+    row; Adam: x, m, v read and written (24 B per spot).  Padding entries
+    are not counted."""
+    n_cols = int(mats[0]["shape"][1])
     tr = (cls == 1) | (cls == 2)
-    fwd = sum(8.0 * m["val"].numel() + 13.0 * n_rows for m in mats)
+    n_tr = float(tr.sum())
     nnz_tr = []
     for m in mats:
         rp = m["row_ptr"].cpu().numpy()
         nnz_tr.append(float(np.sum(np.diff(rp)[tr])))
-    return fwd + n_rows + 12.0 * float(tr.sum()) + 8.0 * float(np.mean(nnz_tr))
+    fwd = sum(6.0 * z + 13.0 * n_tr for z in nnz_tr)
+    bwd = 8.0 * float(np.mean(nnz_tr)) + 8.0 * n_cols + 5.0 * n_tr
+    return fwd + bwd + 24.0 * n_cols
 
 
 def optimizer_leg(pb, target, mats, args):
@@ -519,19 +523,22 @@ def optimizer_leg(pb, target, mats, args):
     vpmc.robust_optimize(mats, cls, x.clone(), 1.0, iterations=3)
     hist, ms, setup_ms = vpmc.robust_optimize(mats, cls, x, 1.0, iterations=args.opt_iterations)
     idx = vpmc.target_indices(mats, cls, 1.0, x)
+    n_tr = int(np.sum(cls_np > 0))
     per_it = ms / 1000.0 / args.opt_iterations
     b = optimizer_bytes(mats, cls_np)
     peak = float(measured_peaks().get("hbm_gbs", 6800.0))
     gbs = b / per_it / 1e9
-    return {"iterations": args.opt_iterations, "ms_per_iteration": 1000.0 * per_it,
+    return {"iterations": args.opt_iterations, "ms_per_iteration": 1000.0 * per_it, "setup_ms": setup_ms,
+            "target_ring_rows": n_tr,
             "objective_first": float(hist[0]), "objective_last": float(hist[-1]),
             "worst_V100": float(idx[:, 0].min()), "worst_Dmin": float(idx[:, 1].min()),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "bytes_per_iteration": b, "traffic": None,
-                         "kernel": "k_spmv_obj x13 + k_select + k_spmvT + k_adam_proj",
+                         "kernel": "k_fwd (13 scenarios) + k_bwd_adam",
                          "peak_note": "hbm_gbs of MEASURED_PEAKS.json (STREAM-style copy)"},
-            "note": "13 SpMV, worst-case selection, one transposed SpMV and the Adam step per iteration, "
-                    "all on the device; target 8.4 cc sphere, ring = 10 mm shell"}
+            "note": "per iteration: 13 products on the compact target/ring rows (built once per call, "
+                    "setup_ms), worst-case selection, the transposed product and the Adam step, all on the "
+                    "device; target 8.4 cc sphere, ring = 10 mm shell"}
 
 
 def e2e_leg(pb, spots, scens, opts, args):
