@@ -14,8 +14,9 @@
 //   k_fwd        d_s = A_s x on the compact rows of every scenario (a warp per
 //                row) and the scenario's objective f_s (FP64 block sums);
 //   k_bwd_adam   s* = first s with the largest f_s (every block), records it;
-//                g_j = sum_i A_s*,ij f'(d_i) down spot j's compact column (a
-//                warp per spot, FP64 sum), then Adam on x_j, clamped at zero.
+//                g_j = sum_i A_s*,ij f'(d_i) down spot j's transposed column
+//                (a warp per 512-entry chunk, FP64 partial sums), then Adam on
+//                x_j, clamped at zero, by the last chunk of spot j.
 // Both stream their compact arrays once per iteration: HBM-bound.
 // Full-matrix products (dose of the weights, target indices over all
 // voxels) use k_spmv_obj: a sub-warp per row of the caller's CSR.
@@ -161,6 +162,7 @@ __global__ void k_init_minmax(int* minmax, int n_scen)
 
 constexpr int kPadRow = 8;                      // compact CSR row padding (entries)
 constexpr int kPadCol = 4;                      // CSC column padding (entries)
+constexpr int kSetupSmemCols = 25600;           // setup counts in shared memory up to this many spots
 
 // len[s n_tr + i] = entries of target/ring row tr_rows[i] in scenario s.
 __global__ void k_tr_len(const Csr* __restrict__ mats, const int* __restrict__ tr_rows, int n_tr,
@@ -174,56 +176,103 @@ __global__ void k_tr_len(const Csr* __restrict__ mats, const int* __restrict__ t
     len[(long long)s * n_tr + i] = __ldg(rp + r + 1) - __ldg(rp + r);
 }
 
+constexpr int kSetupRows = 32;                  // compact rows per setup block (8 warps x 4)
+
 // Copies the target/ring rows into the compact CSR (a warp per row and
 // scenario; pads and entries with an out-of-range spot become (0, 0.0)) and
-// counts each spot's entries for the transpose.
-__global__ void k_tr_gather(const Csr* __restrict__ mats, const int* __restrict__ tr_rows, int n_tr, int n_cols,
-                            const long long* __restrict__ crp, unsigned short* __restrict__ ccol,
-                            float* __restrict__ cval, int* __restrict__ ccount)
+// counts each spot's entries for the transpose.  kSmem: the block counts in
+// shared memory (n_cols ints) and adds its counts to the global ones once.
+template <bool kSmem>
+__global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats, const int* __restrict__ tr_rows,
+                                                   int n_tr, int n_cols, const long long* __restrict__ crp,
+                                                   unsigned short* __restrict__ ccol, float* __restrict__ cval,
+                                                   int* __restrict__ ccount)
 {
-    const int s = blockIdx.y, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n_tr) return;
+    extern __shared__ int hist_s[];
+    const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* cnt = ccount + (long long)s * n_cols;
+    if (kSmem) {
+        for (int j = threadIdx.x; j < n_cols; j += blockDim.x) hist_s[j] = 0;
+        __syncthreads();
+    }
     const Csr A = mats[s];
-    const int r = __ldg(tr_rows + i);
-    const long long b = __ldg(A.row_ptr + r), len = __ldg(A.row_ptr + r + 1) - b;
-    const long long dst = crp[(long long)s * (n_tr + 1) + i], plen = crp[(long long)s * (n_tr + 1) + i + 1] - dst;
-    for (long long k = lane; k < plen; k += 32) {
-        int j = 0;
-        float v = 0.0f;
-        if (k < len) {
-            j = __ldg(A.col + b + k);
-            if ((unsigned)j < (unsigned)n_cols) {
-                v = __ldg(A.val + b + k);
-                atomicAdd(ccount + (long long)s * n_cols + j, 1);
-            } else {
-                j = 0;
+    for (int r = 0; r < kSetupRows / 8; ++r) {
+        const int i = blockIdx.x * kSetupRows + r * 8 + warp;
+        if (i >= n_tr) break;
+        const int row = __ldg(tr_rows + i);
+        const long long b = __ldg(A.row_ptr + row), len = __ldg(A.row_ptr + row + 1) - b;
+        const long long dst = crp[(long long)s * (n_tr + 1) + i];
+        const long long plen = crp[(long long)s * (n_tr + 1) + i + 1] - dst;
+        for (long long k = lane; k < plen; k += 32) {
+            int j = 0;
+            float v = 0.0f;
+            if (k < len) {
+                j = __ldg(A.col + b + k);
+                if ((unsigned)j < (unsigned)n_cols) {
+                    v = __ldg(A.val + b + k);
+                    atomicAdd(kSmem ? hist_s + j : cnt + j, 1);
+                } else {
+                    j = 0;
+                }
             }
+            ccol[dst + k] = (unsigned short)j;
+            cval[dst + k] = v;
         }
-        ccol[dst + k] = (unsigned short)j;
-        cval[dst + k] = v;
+    }
+    if (kSmem) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < n_cols; j += blockDim.x)
+            if (hist_s[j]) atomicAdd(cnt + j, hist_s[j]);
     }
 }
 
-// Scatters the target/ring rows' entries into the transpose: (compact row
-// index, value) in spot j's column segment.  The order inside a segment
-// follows the atomics; the gradient sums it in FP64.
-__global__ void k_csc_fill(const Csr* __restrict__ mats, const int* __restrict__ tr_rows, int n_tr, int n_cols,
-                           const long long* __restrict__ tcp, int* __restrict__ fill, int* __restrict__ trow,
-                           float* __restrict__ tval)
+// Scatters the compact rows' entries into the transpose: (compact row index,
+// value) in spot j's column segment, skipping (0, 0.0) pads (an entry that
+// is itself (0, 0.0) leaves a zero slot, which adds nothing).  The order
+// inside a segment follows the atomics; the gradient sums it in FP64.
+// kSmem: the block counts its entries per spot in shared memory, reserves
+// each spot's range with one global atomic, then places its entries.
+template <bool kSmem>
+__global__ void __launch_bounds__(256) k_csc_fill(const long long* __restrict__ crp,
+                                                  const unsigned short* __restrict__ ccol,
+                                                  const float* __restrict__ cval, int n_tr, int n_cols,
+                                                  const long long* __restrict__ tcp, int* __restrict__ fill,
+                                                  int* __restrict__ trow, float* __restrict__ tval)
 {
-    const int s = blockIdx.y, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n_tr) return;
-    const Csr A = mats[s];
-    const int r = __ldg(tr_rows + i);
-    const long long b = __ldg(A.row_ptr + r), e = __ldg(A.row_ptr + r + 1);
-    for (long long k = b + lane; k < e; k += 32) {
-        const int j = __ldg(A.col + k);
-        if ((unsigned)j >= (unsigned)n_cols) continue;
-        const long long pos = tcp[(long long)s * (n_cols + 1) + j] + atomicAdd(fill + (long long)s * n_cols + j, 1);
-        trow[pos] = i;
-        tval[pos] = __ldg(A.val + k);
+    extern __shared__ int sm_fill[];
+    int* cnt = sm_fill;
+    int* cur = sm_fill + n_cols;
+    const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long* cp = tcp + (long long)s * (n_cols + 1);
+    int* fl = fill + (long long)s * n_cols;
+    if (kSmem) {
+        for (int j = threadIdx.x; j < n_cols; j += blockDim.x) cnt[j] = 0;
+        __syncthreads();
+        for (int r = 0; r < kSetupRows / 8; ++r) {
+            const int i = blockIdx.x * kSetupRows + r * 8 + warp;
+            if (i >= n_tr) break;
+            const long long b = crp[(long long)s * (n_tr + 1) + i], e = crp[(long long)s * (n_tr + 1) + i + 1];
+            for (long long k = b + lane; k < e; k += 32) {
+                const int j = ccol[k];
+                if (j != 0 || cval[k] != 0.0f) atomicAdd(cnt + j, 1);
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n_cols; j += blockDim.x) cur[j] = cnt[j] ? atomicAdd(fl + j, cnt[j]) : 0;
+        __syncthreads();
+    }
+    for (int r = 0; r < kSetupRows / 8; ++r) {
+        const int i = blockIdx.x * kSetupRows + r * 8 + warp;
+        if (i >= n_tr) break;
+        const long long b = crp[(long long)s * (n_tr + 1) + i], e = crp[(long long)s * (n_tr + 1) + i + 1];
+        for (long long k = b + lane; k < e; k += 32) {
+            const int j = ccol[k];
+            const float v = cval[k];
+            if (j == 0 && v == 0.0f) continue;
+            const long long pos = cp[j] + (kSmem ? atomicAdd(cur + j, 1) : atomicAdd(fl + j, 1));
+            trow[pos] = i;
+            tval[pos] = v;
+        }
     }
 }
 
@@ -272,14 +321,29 @@ __global__ void __launch_bounds__(256) k_fwd(const long long* __restrict__ crp, 
     }
 }
 
-// Worst scenario, gradient down each spot's compact column and the Adam step
-// (Kingma & Ba 2015) clamped at zero; grid (spots / 8), 256 threads.
-__global__ void __launch_bounds__(256) k_bwd_adam(const long long* __restrict__ tcp, const int* __restrict__ trow,
+// A piece of one spot's transposed column: entries [b, b + n) of the
+// transpose (n a multiple of 4, at most kChunk; n = 0 for a spot without
+// entries, which still takes its Adam step with g = 0).
+struct Chunk {
+    long long b;
+    int j, n;
+};
+constexpr int kChunk = 512;
+
+// Worst scenario, gradient and Adam step (Kingma & Ba 2015) clamped at zero.
+// A warp per chunk of the worst scenario's transpose adds its FP64 partial
+// sum to g_j; the last of spot j's chunks to arrive (counter per spot) takes
+// g_j, resets it and its counter, and updates x_j, m_j, v_j.  Grid: the
+// largest chunk count over the scenarios / 8, 256 threads.
+__global__ void __launch_bounds__(256) k_bwd_adam(const Chunk* __restrict__ chunks,
+                                                  const long long* __restrict__ chunk_off,
+                                                  const int* __restrict__ nchunk, const int* __restrict__ trow,
                                                   const float* __restrict__ tval, int n_cols, int n_tr,
                                                   const float* __restrict__ dose_tr,
                                                   const unsigned char* __restrict__ tr_cls, ObjParams q,
                                                   const double* __restrict__ fsum_cur, double* __restrict__ fsum_next,
-                                                  int n_scen, float* __restrict__ hist, int it, float* __restrict__ x,
+                                                  int n_scen, float* __restrict__ hist, int it, double* __restrict__ g,
+                                                  int* __restrict__ arrived, float* __restrict__ x,
                                                   float* __restrict__ m, float* __restrict__ v, float step, float c1,
                                                   float c2, float eps)
 {
@@ -294,15 +358,15 @@ __global__ void __launch_bounds__(256) k_bwd_adam(const long long* __restrict__ 
     if (blockIdx.x == 0 && threadIdx.x < n_scen) fsum_next[threadIdx.x] = 0.0;
     __syncthreads();
     const int s = s_star, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (j >= n_cols) return;                          // warp-uniform
-    const long long b = __ldg(tcp + (long long)s * (n_cols + 1) + j);
-    const long long e = __ldg(tcp + (long long)s * (n_cols + 1) + j + 1);
+    const long long c = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const long long c0 = __ldg(chunk_off + s), c1n = __ldg(chunk_off + s + 1);
+    if (c >= c1n - c0) return;                        // warp-uniform
+    const Chunk ch = chunks[c0 + c];
     const float* d = dose_tr + (long long)s * n_tr;
     double acc = 0.0;
-    for (long long k = b + lane * kPadCol; k < e; k += 32 * kPadCol) {
-        const int4 r = __ldcs(reinterpret_cast<const int4*>(trow + k));
-        const float4 a = __ldcs(reinterpret_cast<const float4*>(tval + k));
+    for (int k = lane * 4; k < ch.n; k += 128) {
+        const int4 r = __ldcs(reinterpret_cast<const int4*>(trow + ch.b + k));
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(tval + ch.b + k));
         acc += (double)a.x * (double)obj_grad(__ldg(d + r.x), __ldg(tr_cls + r.x), q);
         acc += (double)a.y * (double)obj_grad(__ldg(d + r.y), __ldg(tr_cls + r.y), q);
         acc += (double)a.z * (double)obj_grad(__ldg(d + r.z), __ldg(tr_cls + r.z), q);
@@ -311,11 +375,20 @@ __global__ void __launch_bounds__(256) k_bwd_adam(const long long* __restrict__ 
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
     if (lane == 0) {
-        const float g = (float)acc;
-        const float mj = fmaf(0.9f, m[j], 0.1f * g), vj = fmaf(0.999f, v[j], 0.001f * g * g);
-        m[j] = mj;
-        v[j] = vj;
-        x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
+        const int j = ch.j;
+        if (acc != 0.0) atomicAdd(g + j, acc);
+        __threadfence();
+        const int total = __ldg(nchunk + (long long)s * n_cols + j);
+        if (atomicAdd(arrived + j, 1) == total - 1) {
+            __threadfence();
+            const float gj = (float)__longlong_as_double(
+                (long long)atomicExch(reinterpret_cast<unsigned long long*>(g + j), 0ull));
+            arrived[j] = 0;
+            const float mj = fmaf(0.9f, m[j], 0.1f * gj), vj = fmaf(0.999f, v[j], 0.001f * gj * gj);
+            m[j] = mj;
+            v[j] = vj;
+            x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
+        }
     }
 }
 
@@ -368,6 +441,11 @@ struct RobustWs {
     int* fill = nullptr;
     int* trow = nullptr;
     float* tval = nullptr;
+    Chunk* chunks = nullptr;                    // every scenario's transpose chunks
+    long long* chunk_off = nullptr;             // [S + 1]
+    int* nchunk = nullptr;                      // [S x n_cols]
+    double* g = nullptr;
+    int* arrived = nullptr;
     float* dose_tr = nullptr;
     double* fsum = nullptr;                     // [2 x S]: this iteration's sums, the next one's
     float* m = nullptr;
@@ -377,6 +455,7 @@ struct RobustWs {
     {
         cudaFree(mats); cudaFree(tr_rows); cudaFree(tr_cls); cudaFree(len); cudaFree(crp); cudaFree(ccol);
         cudaFree(cval); cudaFree(ccount); cudaFree(tcp); cudaFree(fill); cudaFree(trow); cudaFree(tval);
+        cudaFree(chunks); cudaFree(chunk_off); cudaFree(nchunk); cudaFree(g); cudaFree(arrived);
         cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v); cudaFree(hist);
     }
 };
@@ -442,8 +521,16 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     OPT_TRY(dalloc(&w.cval, (size_t)total_c));
     OPT_TRY(dalloc(&w.ccount, (size_t)S * n_cols));
     OPT_TRY(cudaMemsetAsync(w.ccount, 0, sizeof(int) * (size_t)S * n_cols, st));
-    const dim3 gw((unsigned)((n_tr + 7) / 8), (unsigned)S);
-    k_tr_gather<<<gw, 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount);
+    const dim3 gw((unsigned)((n_tr + kSetupRows - 1) / kSetupRows), (unsigned)S);
+    const bool smem_setup = n_cols <= kSetupSmemCols;
+    if (smem_setup) {
+        const int sm1 = (int)(sizeof(int) * n_cols), sm2 = 2 * sm1;
+        OPT_TRY(cudaFuncSetAttribute(k_tr_gather<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
+        OPT_TRY(cudaFuncSetAttribute(k_csc_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+        k_tr_gather<true><<<gw, 256, sm1, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount);
+    } else {
+        k_tr_gather<false><<<gw, 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount);
+    }
     OPT_TRY(cudaGetLastError());
     // transpose layout
     std::vector<int> cnt((size_t)S * n_cols);
@@ -458,6 +545,29 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
         }
         tcp[(size_t)s * (n_cols + 1) + n_cols] = total_t;
     }
+    std::vector<Chunk> chunks;
+    std::vector<long long> chunk_off(S + 1, 0);
+    std::vector<int> nchunk((size_t)S * n_cols);
+    long long max_chunks = 0;
+    for (int s = 0; s < S; ++s) {
+        chunk_off[s] = (long long)chunks.size();
+        for (int j = 0; j < n_cols; ++j) {
+            const long long b = tcp[(size_t)s * (n_cols + 1) + j], e = tcp[(size_t)s * (n_cols + 1) + j + 1];
+            int k = 0;
+            for (long long c = b; c < e || (c == b && k == 0); c += kChunk, ++k)
+                chunks.push_back(Chunk{c, j, (int)std::min<long long>(kChunk, e - c)});
+            nchunk[(size_t)s * n_cols + j] = k;
+        }
+        max_chunks = std::max(max_chunks, (long long)chunks.size() - chunk_off[s]);
+    }
+    chunk_off[S] = (long long)chunks.size();
+    OPT_TRY(dalloc(&w.chunks, chunks.size()));
+    OPT_TRY(dalloc(&w.chunk_off, chunk_off.size()));
+    OPT_TRY(dalloc(&w.nchunk, nchunk.size()));
+    OPT_TRY(cudaMemcpyAsync(w.chunks, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice, st));
+    OPT_TRY(cudaMemcpyAsync(w.chunk_off, chunk_off.data(), sizeof(long long) * chunk_off.size(),
+                            cudaMemcpyHostToDevice, st));
+    OPT_TRY(cudaMemcpyAsync(w.nchunk, nchunk.data(), sizeof(int) * nchunk.size(), cudaMemcpyHostToDevice, st));
     OPT_TRY(dalloc(&w.tcp, tcp.size()));
     OPT_TRY(cudaMemcpyAsync(w.tcp, tcp.data(), sizeof(long long) * tcp.size(), cudaMemcpyHostToDevice, st));
     OPT_TRY(dalloc(&w.trow, (size_t)total_t));
@@ -466,13 +576,21 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     OPT_TRY(cudaMemsetAsync(w.tval, 0, sizeof(float) * (size_t)std::max<long long>(total_t, 1), st));
     OPT_TRY(dalloc(&w.fill, (size_t)S * n_cols));
     OPT_TRY(cudaMemsetAsync(w.fill, 0, sizeof(int) * (size_t)S * n_cols, st));
-    k_csc_fill<<<gw, 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.tcp, w.fill, w.trow, w.tval);
+    if (smem_setup)
+        k_csc_fill<true><<<gw, 256, 2 * sizeof(int) * n_cols, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.tcp, w.fill,
+                                                                     w.trow, w.tval);
+    else
+        k_csc_fill<false><<<gw, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.tcp, w.fill, w.trow, w.tval);
     OPT_TRY(cudaGetLastError());
     // iteration state
     OPT_TRY(dalloc(&w.dose_tr, (size_t)S * n_tr));
     OPT_TRY(dalloc(&w.fsum, (size_t)2 * S));
     OPT_TRY(dalloc(&w.m, (size_t)n_cols));
     OPT_TRY(dalloc(&w.v, (size_t)n_cols));
+    OPT_TRY(dalloc(&w.g, (size_t)n_cols));
+    OPT_TRY(dalloc(&w.arrived, (size_t)n_cols));
+    OPT_TRY(cudaMemsetAsync(w.g, 0, sizeof(double) * n_cols, st));
+    OPT_TRY(cudaMemsetAsync(w.arrived, 0, sizeof(int) * n_cols, st));
     OPT_TRY(dalloc(&w.hist, (size_t)std::max(spec.iterations, 1)));
     OPT_TRY(cudaMemsetAsync(w.fsum, 0, sizeof(double) * 2 * S, st));
     OPT_TRY(cudaMemsetAsync(w.m, 0, sizeof(float) * n_cols, st));
@@ -482,14 +600,15 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
                       1.0f / (float)std::max<long long>(spec.n_target, 1),
                       1.0f / (float)std::max<long long>(spec.n_ring, 1)};
     const dim3 gf((unsigned)std::max((n_tr + 7) / 8, 1), (unsigned)S);
-    const unsigned gb = (unsigned)((n_cols + 7) / 8);
+    const unsigned gb = (unsigned)((max_chunks + 7) / 8);
     for (int it = 0; it < spec.iterations; ++it) {
         double* cur = w.fsum + (it & 1) * S;
         double* nxt = w.fsum + ((it + 1) & 1) * S;
         k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, cur);
         const double t = it + 1;
-        k_bwd_adam<<<gb, 256, 0, st>>>(w.tcp, w.trow, w.tval, n_cols, n_tr, w.dose_tr, w.tr_cls, q, cur, nxt, S,
-                                       w.hist, it, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
+        k_bwd_adam<<<gb, 256, 0, st>>>(w.chunks, w.chunk_off, w.nchunk, w.trow, w.tval, n_cols, n_tr, w.dose_tr,
+                                       w.tr_cls, q, cur, nxt, S, w.hist, it, w.g, w.arrived, x, w.m, w.v, spec.step,
+                                       (float)(1.0 / (1.0 - std::pow(0.9, t))),
                                        (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
     }
     OPT_TRY(cudaGetLastError());
