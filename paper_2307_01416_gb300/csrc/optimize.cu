@@ -15,8 +15,9 @@
 //                row) and the scenario's objective f_s (FP64 block sums);
 //   k_bwd_adam   s* = first s with the largest f_s (every block), records it;
 //                g_j = sum_i A_s*,ij f'(d_i) down spot j's transposed column
-//                (a warp per 512-entry chunk, FP64 partial sums), then Adam on
-//                x_j, clamped at zero, by the last chunk of spot j.
+//                (a warp per 512-entry chunk; the chunks' partial sums are
+//                added in a fixed order), then Adam on x_j, clamped at zero,
+//                by the last chunk of spot j.
 // Both stream their compact arrays once per iteration: HBM-bound.
 // Full-matrix products (dose of the weights, target indices over all
 // voxels) use k_spmv_obj: a sub-warp per row of the caller's CSR.
@@ -162,7 +163,7 @@ __global__ void k_init_minmax(int* minmax, int n_scen)
 
 constexpr int kPadRow = 8;                      // compact CSR row padding (entries)
 constexpr int kPadCol = 4;                      // CSC column padding (entries)
-constexpr int kSetupSmemCols = 25600;           // setup counts in shared memory up to this many spots
+constexpr int kSetupSmemCols = 25600;           // ordered transpose (shared-memory cursors) up to this many spots
 
 // len[s n_tr + i] = entries of target/ring row tr_rows[i] in scenario s.
 __global__ void k_tr_len(const Csr* __restrict__ mats, const int* __restrict__ tr_rows, int n_tr,
@@ -180,22 +181,24 @@ constexpr int kSetupRows = 32;                  // compact rows per setup block 
 
 // Copies the target/ring rows into the compact CSR (a warp per row and
 // scenario; pads and entries with an out-of-range spot become (0, 0.0)) and
-// counts each spot's entries for the transpose.  kSmem: the block counts in
-// shared memory (n_cols ints) and adds its counts to the global ones once.
-template <bool kSmem>
+// counts, per spot, the entries the transpose will hold (every entry but a
+// (0, 0.0) one).  kBlockCounts: the block counts in shared memory (n_cols
+// ints) and stores its whole count row, bcnt[(s nb + block) n_cols + j];
+// otherwise it adds to the per-scenario totals ccount with global atomics.
+template <bool kBlockCounts>
 __global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats, const int* __restrict__ tr_rows,
                                                    int n_tr, int n_cols, const long long* __restrict__ crp,
                                                    unsigned short* __restrict__ ccol, float* __restrict__ cval,
-                                                   int* __restrict__ ccount)
+                                                   int* __restrict__ ccount, int* __restrict__ bcnt)
 {
     extern __shared__ int hist_s[];
     const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int* cnt = ccount + (long long)s * n_cols;
-    if (kSmem) {
+    if (kBlockCounts) {
         for (int j = threadIdx.x; j < n_cols; j += blockDim.x) hist_s[j] = 0;
         __syncthreads();
     }
     const Csr A = mats[s];
+    int* cnt = kBlockCounts ? hist_s : ccount + (long long)s * n_cols;
     for (int r = 0; r < kSetupRows / 8; ++r) {
         const int i = blockIdx.x * kSetupRows + r * 8 + warp;
         if (i >= n_tr) break;
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats,
                 j = __ldg(A.col + b + k);
                 if ((unsigned)j < (unsigned)n_cols) {
                     v = __ldg(A.val + b + k);
-                    atomicAdd(kSmem ? hist_s + j : cnt + j, 1);
+                    if (j != 0 || v != 0.0f) atomicAdd(cnt + j, 1);
                 } else {
                     j = 0;
                 }
@@ -219,48 +222,76 @@ __global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats,
             cval[dst + k] = v;
         }
     }
-    if (kSmem) {
+    if (kBlockCounts) {
         __syncthreads();
-        for (int j = threadIdx.x; j < n_cols; j += blockDim.x)
-            if (hist_s[j]) atomicAdd(cnt + j, hist_s[j]);
+        int* out = bcnt + ((long long)s * gridDim.x + blockIdx.x) * n_cols;
+        for (int j = threadIdx.x; j < n_cols; j += blockDim.x) out[j] = hist_s[j];
     }
 }
 
-// Scatters the compact rows' entries into the transpose: (compact row index,
-// value) in spot j's column segment, skipping (0, 0.0) pads (an entry that
-// is itself (0, 0.0) leaves a zero slot, which adds nothing).  The order
-// inside a segment follows the atomics; the gradient sums it in FP64.
-// kSmem: the block counts its entries per spot in shared memory, reserves
-// each spot's range with one global atomic, then places its entries.
-template <bool kSmem>
-__global__ void __launch_bounds__(256) k_csc_fill(const long long* __restrict__ crp,
-                                                  const unsigned short* __restrict__ ccol,
-                                                  const float* __restrict__ cval, int n_tr, int n_cols,
-                                                  const long long* __restrict__ tcp, int* __restrict__ fill,
-                                                  int* __restrict__ trow, float* __restrict__ tval)
+// Per scenario and spot: the blocks' counts become exclusive prefixes over
+// the blocks (in block order) and their sum the spot's total.
+__global__ void k_col_scan(int* __restrict__ bcnt, int nb, int n_cols, int* __restrict__ ccount)
 {
-    extern __shared__ int sm_fill[];
-    int* cnt = sm_fill;
-    int* cur = sm_fill + n_cols;
+    const int s = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_cols) return;
+    int run = 0;
+    int* c = bcnt + (long long)s * nb * n_cols + j;
+    for (int b = 0; b < nb; ++b) {
+        const int v = c[(long long)b * n_cols];
+        c[(long long)b * n_cols] = run;
+        run += v;
+    }
+    ccount[(long long)s * n_cols + j] = run;
+}
+
+// Transpose in row order: block b of scenario s places its rows one after
+// the other; spot j's entries of this block start at tcp[j] + (entries of j
+// in the blocks before), so every segment is sorted by compact row index and
+// the layout does not depend on scheduling (a row that repeats a spot places
+// its repeats in atomic order).
+__global__ void __launch_bounds__(256) k_csc_fill_ordered(const long long* __restrict__ crp,
+                                                          const unsigned short* __restrict__ ccol,
+                                                          const float* __restrict__ cval, int n_tr, int n_cols,
+                                                          const long long* __restrict__ tcp,
+                                                          const int* __restrict__ bprefix, int* __restrict__ trow,
+                                                          float* __restrict__ tval)
+{
+    extern __shared__ int cursor[];
+    const int s = blockIdx.y;
+    const long long* cp = tcp + (long long)s * (n_cols + 1);
+    const int* pre = bprefix + ((long long)s * gridDim.x + blockIdx.x) * n_cols;
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) cursor[j] = pre[j];
+    __syncthreads();
+    for (int r = 0; r < kSetupRows; ++r) {
+        const int i = blockIdx.x * kSetupRows + r;
+        if (i >= n_tr) break;                             // block-uniform
+        const long long b = crp[(long long)s * (n_tr + 1) + i], e = crp[(long long)s * (n_tr + 1) + i + 1];
+        for (long long k = b + threadIdx.x; k < e; k += blockDim.x) {
+            const int j = ccol[k];
+            const float v = cval[k];
+            if (j == 0 && v == 0.0f) continue;
+            const long long pos = __ldg(cp + j) + atomicAdd(cursor + j, 1);
+            trow[pos] = i;
+            tval[pos] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// The same placement with one global cursor per spot (atomics): for more
+// spots than shared memory holds.  The order inside a segment follows the
+// atomics.
+__global__ void __launch_bounds__(256) k_csc_fill_atomic(const long long* __restrict__ crp,
+                                                         const unsigned short* __restrict__ ccol,
+                                                         const float* __restrict__ cval, int n_tr, int n_cols,
+                                                         const long long* __restrict__ tcp, int* __restrict__ fill,
+                                                         int* __restrict__ trow, float* __restrict__ tval)
+{
     const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long* cp = tcp + (long long)s * (n_cols + 1);
     int* fl = fill + (long long)s * n_cols;
-    if (kSmem) {
-        for (int j = threadIdx.x; j < n_cols; j += blockDim.x) cnt[j] = 0;
-        __syncthreads();
-        for (int r = 0; r < kSetupRows / 8; ++r) {
-            const int i = blockIdx.x * kSetupRows + r * 8 + warp;
-            if (i >= n_tr) break;
-            const long long b = crp[(long long)s * (n_tr + 1) + i], e = crp[(long long)s * (n_tr + 1) + i + 1];
-            for (long long k = b + lane; k < e; k += 32) {
-                const int j = ccol[k];
-                if (j != 0 || cval[k] != 0.0f) atomicAdd(cnt + j, 1);
-            }
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < n_cols; j += blockDim.x) cur[j] = cnt[j] ? atomicAdd(fl + j, cnt[j]) : 0;
-        __syncthreads();
-    }
     for (int r = 0; r < kSetupRows / 8; ++r) {
         const int i = blockIdx.x * kSetupRows + r * 8 + warp;
         if (i >= n_tr) break;
@@ -269,7 +300,7 @@ __global__ void __launch_bounds__(256) k_csc_fill(const long long* __restrict__ 
             const int j = ccol[k];
             const float v = cval[k];
             if (j == 0 && v == 0.0f) continue;
-            const long long pos = cp[j] + (kSmem ? atomicAdd(cur + j, 1) : atomicAdd(fl + j, 1));
+            const long long pos = cp[j] + atomicAdd(fl + j, 1);
             trow[pos] = i;
             tval[pos] = v;
         }
@@ -323,29 +354,31 @@ __global__ void __launch_bounds__(256) k_fwd(const long long* __restrict__ crp, 
 
 // A piece of one spot's transposed column: entries [b, b + n) of the
 // transpose (n a multiple of 4, at most kChunk; n = 0 for a spot without
-// entries, which still takes its Adam step with g = 0).
+// entries, which still takes its Adam step with g = 0).  first: index of the
+// spot's first chunk in the scenario's list; total: the spot's chunk count.
 struct Chunk {
     long long b;
-    int j, n;
+    int j, n, first, total;
 };
 constexpr int kChunk = 512;
 
 // Worst scenario, gradient and Adam step (Kingma & Ba 2015) clamped at zero.
-// A warp per chunk of the worst scenario's transpose adds its FP64 partial
-// sum to g_j; the last of spot j's chunks to arrive (counter per spot) takes
-// g_j, resets it and its counter, and updates x_j, m_j, v_j.  Grid: the
-// largest chunk count over the scenarios / 8, 256 threads.
+// A warp per chunk of the worst scenario's transpose: FP32 sums per lane (at
+// most 16 terms), an FP64 warp sum stored as the chunk's partial; the last
+// of spot j's chunks to arrive (counter per spot) adds the spot's partials
+// in chunk order (the same sum whatever the arrival order), resets the
+// counter and updates x_j, m_j, v_j.  Grid: the largest chunk count over the
+// scenarios / 8, 256 threads.
 __global__ void __launch_bounds__(256) k_bwd_adam(const Chunk* __restrict__ chunks,
                                                   const long long* __restrict__ chunk_off,
-                                                  const int* __restrict__ nchunk, const int* __restrict__ trow,
-                                                  const float* __restrict__ tval, int n_cols, int n_tr,
-                                                  const float* __restrict__ dose_tr,
+                                                  const int* __restrict__ trow, const float* __restrict__ tval,
+                                                  int n_tr, const float* __restrict__ dose_tr,
                                                   const unsigned char* __restrict__ tr_cls, ObjParams q,
                                                   const double* __restrict__ fsum_cur, double* __restrict__ fsum_next,
-                                                  int n_scen, float* __restrict__ hist, int it, double* __restrict__ g,
-                                                  int* __restrict__ arrived, float* __restrict__ x,
-                                                  float* __restrict__ m, float* __restrict__ v, float step, float c1,
-                                                  float c2, float eps)
+                                                  int n_scen, float* __restrict__ hist, int it,
+                                                  double* __restrict__ partial, int* __restrict__ arrived,
+                                                  float* __restrict__ x, float* __restrict__ m, float* __restrict__ v,
+                                                  float step, float c1, float c2, float eps)
 {
     __shared__ int s_star;
     if (threadIdx.x == 0) {
@@ -363,27 +396,28 @@ __global__ void __launch_bounds__(256) k_bwd_adam(const Chunk* __restrict__ chun
     if (c >= c1n - c0) return;                        // warp-uniform
     const Chunk ch = chunks[c0 + c];
     const float* d = dose_tr + (long long)s * n_tr;
-    double acc = 0.0;
+    float accf = 0.0f;
     for (int k = lane * 4; k < ch.n; k += 128) {
         const int4 r = __ldcs(reinterpret_cast<const int4*>(trow + ch.b + k));
         const float4 a = __ldcs(reinterpret_cast<const float4*>(tval + ch.b + k));
-        acc += (double)a.x * (double)obj_grad(__ldg(d + r.x), __ldg(tr_cls + r.x), q);
-        acc += (double)a.y * (double)obj_grad(__ldg(d + r.y), __ldg(tr_cls + r.y), q);
-        acc += (double)a.z * (double)obj_grad(__ldg(d + r.z), __ldg(tr_cls + r.z), q);
-        acc += (double)a.w * (double)obj_grad(__ldg(d + r.w), __ldg(tr_cls + r.w), q);
+        accf = fmaf(a.x, obj_grad(__ldg(d + r.x), __ldg(tr_cls + r.x), q), accf);
+        accf = fmaf(a.y, obj_grad(__ldg(d + r.y), __ldg(tr_cls + r.y), q), accf);
+        accf = fmaf(a.z, obj_grad(__ldg(d + r.z), __ldg(tr_cls + r.z), q), accf);
+        accf = fmaf(a.w, obj_grad(__ldg(d + r.w), __ldg(tr_cls + r.w), q), accf);
     }
+    double acc = (double)accf;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
     if (lane == 0) {
         const int j = ch.j;
-        if (acc != 0.0) atomicAdd(g + j, acc);
+        partial[c] = acc;
         __threadfence();
-        const int total = __ldg(nchunk + (long long)s * n_cols + j);
-        if (atomicAdd(arrived + j, 1) == total - 1) {
+        if (atomicAdd(arrived + j, 1) == ch.total - 1) {
             __threadfence();
-            const float gj = (float)__longlong_as_double(
-                (long long)atomicExch(reinterpret_cast<unsigned long long*>(g + j), 0ull));
+            double gsum = 0.0;
+            for (int k = 0; k < ch.total; ++k) gsum += __ldcg(partial + ch.first + k);
             arrived[j] = 0;
+            const float gj = (float)gsum;
             const float mj = fmaf(0.9f, m[j], 0.1f * gj), vj = fmaf(0.999f, v[j], 0.001f * gj * gj);
             m[j] = mj;
             v[j] = vj;
@@ -443,8 +477,8 @@ struct RobustWs {
     float* tval = nullptr;
     Chunk* chunks = nullptr;                    // every scenario's transpose chunks
     long long* chunk_off = nullptr;             // [S + 1]
-    int* nchunk = nullptr;                      // [S x n_cols]
-    double* g = nullptr;
+    int* bcnt = nullptr;                        // [S x blocks x n_cols] setup counts
+    double* partial = nullptr;                  // [largest chunk count]
     int* arrived = nullptr;
     float* dose_tr = nullptr;
     double* fsum = nullptr;                     // [2 x S]: this iteration's sums, the next one's
@@ -455,7 +489,7 @@ struct RobustWs {
     {
         cudaFree(mats); cudaFree(tr_rows); cudaFree(tr_cls); cudaFree(len); cudaFree(crp); cudaFree(ccol);
         cudaFree(cval); cudaFree(ccount); cudaFree(tcp); cudaFree(fill); cudaFree(trow); cudaFree(tval);
-        cudaFree(chunks); cudaFree(chunk_off); cudaFree(nchunk); cudaFree(g); cudaFree(arrived);
+        cudaFree(chunks); cudaFree(chunk_off); cudaFree(bcnt); cudaFree(partial); cudaFree(arrived);
         cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v); cudaFree(hist);
     }
 };
@@ -521,15 +555,22 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     OPT_TRY(dalloc(&w.cval, (size_t)total_c));
     OPT_TRY(dalloc(&w.ccount, (size_t)S * n_cols));
     OPT_TRY(cudaMemsetAsync(w.ccount, 0, sizeof(int) * (size_t)S * n_cols, st));
-    const dim3 gw((unsigned)((n_tr + kSetupRows - 1) / kSetupRows), (unsigned)S);
-    const bool smem_setup = n_cols <= kSetupSmemCols;
-    if (smem_setup) {
-        const int sm1 = (int)(sizeof(int) * n_cols), sm2 = 2 * sm1;
+    const int nb = (n_tr + kSetupRows - 1) / kSetupRows;
+    const dim3 gw((unsigned)nb, (unsigned)S);
+    // ordered transpose when the per-block counts and the cursors fit
+    const bool ordered = n_cols <= kSetupSmemCols && (size_t)S * nb * n_cols * sizeof(int) <= ((size_t)1 << 30);
+    if (ordered) {
+        OPT_TRY(dalloc(&w.bcnt, (size_t)S * nb * n_cols));
+        const int sm1 = (int)(sizeof(int) * n_cols);
         OPT_TRY(cudaFuncSetAttribute(k_tr_gather<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
-        OPT_TRY(cudaFuncSetAttribute(k_csc_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
-        k_tr_gather<true><<<gw, 256, sm1, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount);
+        k_tr_gather<true><<<gw, 256, sm1, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount,
+                                                w.bcnt);
+        OPT_TRY(cudaGetLastError());
+        k_col_scan<<<dim3((unsigned)((n_cols + 255) / 256), (unsigned)S), 256, 0, st>>>(w.bcnt, nb, n_cols,
+                                                                                        w.ccount);
     } else {
-        k_tr_gather<false><<<gw, 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount);
+        k_tr_gather<false><<<gw, 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount,
+                                               nullptr);
     }
     OPT_TRY(cudaGetLastError());
     // transpose layout
@@ -547,49 +588,50 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     }
     std::vector<Chunk> chunks;
     std::vector<long long> chunk_off(S + 1, 0);
-    std::vector<int> nchunk((size_t)S * n_cols);
     long long max_chunks = 0;
     for (int s = 0; s < S; ++s) {
         chunk_off[s] = (long long)chunks.size();
         for (int j = 0; j < n_cols; ++j) {
             const long long b = tcp[(size_t)s * (n_cols + 1) + j], e = tcp[(size_t)s * (n_cols + 1) + j + 1];
-            int k = 0;
-            for (long long c = b; c < e || (c == b && k == 0); c += kChunk, ++k)
-                chunks.push_back(Chunk{c, j, (int)std::min<long long>(kChunk, e - c)});
-            nchunk[(size_t)s * n_cols + j] = k;
+            const int first = (int)((long long)chunks.size() - chunk_off[s]);
+            const int total = e > b ? (int)((e - b + kChunk - 1) / kChunk) : 1;
+            for (int k = 0; k < total; ++k) {
+                const long long c = b + (long long)k * kChunk;
+                chunks.push_back(Chunk{c, j, (int)std::max<long long>(0, std::min<long long>(kChunk, e - c)), first,
+                                       total});
+            }
         }
         max_chunks = std::max(max_chunks, (long long)chunks.size() - chunk_off[s]);
     }
     chunk_off[S] = (long long)chunks.size();
     OPT_TRY(dalloc(&w.chunks, chunks.size()));
     OPT_TRY(dalloc(&w.chunk_off, chunk_off.size()));
-    OPT_TRY(dalloc(&w.nchunk, nchunk.size()));
     OPT_TRY(cudaMemcpyAsync(w.chunks, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice, st));
     OPT_TRY(cudaMemcpyAsync(w.chunk_off, chunk_off.data(), sizeof(long long) * chunk_off.size(),
                             cudaMemcpyHostToDevice, st));
-    OPT_TRY(cudaMemcpyAsync(w.nchunk, nchunk.data(), sizeof(int) * nchunk.size(), cudaMemcpyHostToDevice, st));
     OPT_TRY(dalloc(&w.tcp, tcp.size()));
     OPT_TRY(cudaMemcpyAsync(w.tcp, tcp.data(), sizeof(long long) * tcp.size(), cudaMemcpyHostToDevice, st));
     OPT_TRY(dalloc(&w.trow, (size_t)total_t));
     OPT_TRY(dalloc(&w.tval, (size_t)total_t));
     OPT_TRY(cudaMemsetAsync(w.trow, 0, sizeof(int) * (size_t)std::max<long long>(total_t, 1), st));
     OPT_TRY(cudaMemsetAsync(w.tval, 0, sizeof(float) * (size_t)std::max<long long>(total_t, 1), st));
-    OPT_TRY(dalloc(&w.fill, (size_t)S * n_cols));
-    OPT_TRY(cudaMemsetAsync(w.fill, 0, sizeof(int) * (size_t)S * n_cols, st));
-    if (smem_setup)
-        k_csc_fill<true><<<gw, 256, 2 * sizeof(int) * n_cols, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.tcp, w.fill,
-                                                                     w.trow, w.tval);
-    else
-        k_csc_fill<false><<<gw, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.tcp, w.fill, w.trow, w.tval);
+    if (ordered) {
+        const int sm2 = (int)(sizeof(int) * n_cols);
+        OPT_TRY(cudaFuncSetAttribute(k_csc_fill_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+        k_csc_fill_ordered<<<gw, 256, sm2, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.tcp, w.bcnt, w.trow, w.tval);
+    } else {
+        OPT_TRY(dalloc(&w.fill, (size_t)S * n_cols));
+        OPT_TRY(cudaMemsetAsync(w.fill, 0, sizeof(int) * (size_t)S * n_cols, st));
+        k_csc_fill_atomic<<<gw, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.tcp, w.fill, w.trow, w.tval);
+    }
     OPT_TRY(cudaGetLastError());
     // iteration state
     OPT_TRY(dalloc(&w.dose_tr, (size_t)S * n_tr));
     OPT_TRY(dalloc(&w.fsum, (size_t)2 * S));
     OPT_TRY(dalloc(&w.m, (size_t)n_cols));
     OPT_TRY(dalloc(&w.v, (size_t)n_cols));
-    OPT_TRY(dalloc(&w.g, (size_t)n_cols));
+    OPT_TRY(dalloc(&w.partial, (size_t)max_chunks));
     OPT_TRY(dalloc(&w.arrived, (size_t)n_cols));
-    OPT_TRY(cudaMemsetAsync(w.g, 0, sizeof(double) * n_cols, st));
     OPT_TRY(cudaMemsetAsync(w.arrived, 0, sizeof(int) * n_cols, st));
     OPT_TRY(dalloc(&w.hist, (size_t)std::max(spec.iterations, 1)));
     OPT_TRY(cudaMemsetAsync(w.fsum, 0, sizeof(double) * 2 * S, st));
@@ -606,8 +648,8 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
         double* nxt = w.fsum + ((it + 1) & 1) * S;
         k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, cur);
         const double t = it + 1;
-        k_bwd_adam<<<gb, 256, 0, st>>>(w.chunks, w.chunk_off, w.nchunk, w.trow, w.tval, n_cols, n_tr, w.dose_tr,
-                                       w.tr_cls, q, cur, nxt, S, w.hist, it, w.g, w.arrived, x, w.m, w.v, spec.step,
+        k_bwd_adam<<<gb, 256, 0, st>>>(w.chunks, w.chunk_off, w.trow, w.tval, n_tr, w.dose_tr, w.tr_cls, q, cur, nxt,
+                                       S, w.hist, it, w.partial, w.arrived, x, w.m, w.v, spec.step,
                                        (float)(1.0 / (1.0 - std::pow(0.9, t))),
                                        (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
     }

@@ -157,3 +157,65 @@ def test_head_influence_matrices_full_size(torch):
     assert got[s, 1] == pytest.approx(r["Dmin"], rel=1e-5, abs=1e-6)
     amb = int(np.sum((cls_np == 1) & (np.abs(d - 1.0) <= 1e-5)))
     assert abs(got[s, 0] - r["V100"]) * np.sum(cls_np == 1) <= amb + 1e-9
+
+
+def _duplicates_and_strays(m, seed):
+    """The same matrix with 2 % of its entries split into two halves in the
+    same row (summed by a product) and a stray entry with a column beyond
+    the last spot in 1 % of the rows (skipped)."""
+    g = np.random.default_rng(seed)
+    rp, col, val = m["row_ptr"], m["col"], m["val"]
+    n_rows, n_cols = m["shape"]
+    rows = np.repeat(np.arange(n_rows), np.diff(rp))
+    split = g.random(col.size) < 0.02
+    v = val.copy()
+    v[split] *= 0.5                                   # exact in binary32
+    r2 = np.concatenate([rows, rows[split]])
+    c2 = np.concatenate([col, col[split]])
+    v2 = np.concatenate([v, v[split]])
+    stray = np.flatnonzero(g.random(n_rows) < 0.01)
+    r2 = np.concatenate([r2, stray])
+    c2 = np.concatenate([c2, np.full(stray.size, n_cols + 5, dtype=np.int32)])
+    v2 = np.concatenate([v2, np.ones(stray.size, dtype=np.float32)])
+    o = np.argsort(r2, kind="stable")
+    row_ptr = np.zeros(n_rows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r2, minlength=n_rows), out=row_ptr[1:])
+    return {"row_ptr": row_ptr, "col": c2[o].astype(np.int32), "val": v2[o].astype(np.float32), "shape": m["shape"]}
+
+
+def test_duplicate_and_out_of_range_entries(torch):
+    """Repeated (row, spot) entries add up and entries with a spot index
+    outside [0, n_cols) are skipped: the trajectory equals the oracle's on the
+    clean matrices."""
+    from paper_2307_01416_gb300 import vpmc
+    shape, n, S, seed, lvl = CASES["3 scenarios, ragged grid"]
+    mats, cls, x0 = _case(shape, n, S, seed, lvl)
+    dirty = [_duplicates_and_strays(m, 100 + k) for k, m in enumerate(mats)]
+    assert all(d["val"].size > m["val"].size for d, m in zip(dirty, mats))
+    p = Q.OptParams(prescription=DP, lr=0.1)
+    x_ref, h_ref = Q.optimise([_sp(m) for m in mats], x0.astype(np.float64), cls, p, 40)
+    x = torch.from_numpy(x0.copy()).cuda()
+    h, _, _ = vpmc.robust_optimize([_dev(torch, m) for m in dirty], torch.from_numpy(cls).cuda(), x, DP,
+                                   iterations=40, lr=0.1)
+    assert np.max(np.abs(h - h_ref) / h_ref) <= 1e-4
+    assert np.max(np.abs(x.cpu().numpy() - x_ref)) <= 1e-4 * np.mean(x0)
+    d = vpmc.weights_dose(_dev(torch, dirty[0]), torch.from_numpy(x0).cuda()).cpu().numpy()
+    ref = _sp(mats[0]) @ x0.astype(np.float64)
+    assert np.max(np.abs(d - ref)) <= 2e-6 * np.max(ref)
+
+
+def test_repeat_runs_are_bit_identical(torch):
+    """The transpose is laid out in row order and the gradient's chunk sums
+    are added in a fixed order, so two calls give the same bits."""
+    from paper_2307_01416_gb300 import vpmc
+    shape, n, S, seed, lvl = CASES["13 scenarios, start 1.6 D_p"]
+    mats, cls, x0 = _case(shape, n, S, seed, lvl)
+    dm = [_dev(torch, m) for m in mats]
+    c = torch.from_numpy(cls).cuda()
+    out = []
+    for _ in range(2):
+        x = torch.from_numpy(x0.copy()).cuda()
+        h, _, _ = vpmc.robust_optimize(dm, c, x, DP, iterations=30, lr=0.1)
+        out.append((h, x.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
