@@ -489,13 +489,13 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
 def optimizer_bytes(mats, cls: np.ndarray) -> float:
     """Algorithmic HBM bytes of one robust-optimisation iteration on the
     compact target/ring rows the optimiser builds once per call (rows whose
-    voxel is neither target nor ring do not enter the objective):
-    forward, per scenario: 2 B spot index + 4 B value per entry, 8 B row
-    pointer + 4 B dose written + 1 B class per row; gradient, for the worst
-    scenario (the mean over scenarios stands for it): 4 B row index + 4 B
-    value per entry, 8 B column pointer per spot, 4 B dose + 1 B class per
-    row; Adam: x, m, v read and written (24 B per spot).  Padding entries
-    are not counted."""
+    voxel is neither target nor ring do not enter the objective): forward,
+    per scenario, 2 B spot index + 4 B value per entry and 8 B row pointer +
+    4 B dose written + 1 B class per row; gradient, the same per entry and 8 B
+    row pointer + 4 B dose + 1 B class per row of the worst scenario (the mean
+    over scenarios stands for it; rows with f'(d) = 0, which the kernel skips,
+    are counted); Adam: x, m, v read and written (24 B per spot).  Padding
+    entries and the gradient blocks' partial sums are not counted."""
     n_cols = int(mats[0]["shape"][1])
     tr = (cls == 1) | (cls == 2)
     n_tr = float(tr.sum())
@@ -504,7 +504,7 @@ def optimizer_bytes(mats, cls: np.ndarray) -> float:
         rp = m["row_ptr"].cpu().numpy()
         nnz_tr.append(float(np.sum(np.diff(rp)[tr])))
     fwd = sum(6.0 * z + 13.0 * n_tr for z in nnz_tr)
-    bwd = 8.0 * float(np.mean(nnz_tr)) + 8.0 * n_cols + 5.0 * n_tr
+    bwd = 6.0 * float(np.mean(nnz_tr)) + 13.0 * n_tr
     return fwd + bwd + 24.0 * n_cols
 
 
@@ -534,7 +534,7 @@ def optimizer_leg(pb, target, mats, args):
             "worst_V100": float(idx[:, 0].min()), "worst_Dmin": float(idx[:, 1].min()),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "bytes_per_iteration": b, "traffic": None,
-                         "kernel": "k_fwd (13 scenarios) + k_bwd_adam",
+                         "kernel": "k_fwd (13 scenarios) + k_bwd_rows + k_reduce_adam",
                          "peak_note": "hbm_gbs of MEASURED_PEAKS.json (STREAM-style copy)"},
             "note": "per iteration: 13 products on the compact target/ring rows (built once per call, "
                     "setup_ms), worst-case selection, the transposed product and the Adam step, all on the "

@@ -6,21 +6,22 @@
 // penalties, minimised by Adam with non-negative weights.
 //
 // Only target and ring voxels enter the objective and its gradient, so one
-// setup pass per call copies those rows of every scenario into
-//   a compact CSR (16-bit spot indices, rows padded to 8 entries: one
-//   16-byte load of columns, two of values per lane and step), and
-//   its transpose (CSC over the same rows, columns padded to 4 entries),
-// and each iteration then runs two kernels, with no host synchronisation:
-//   k_fwd        d_s = A_s x on the compact rows of every scenario (a warp per
-//                row) and the scenario's objective f_s (FP64 block sums);
-//   k_bwd_adam   s* = first s with the largest f_s (every block), records it;
-//                g_j = sum_i A_s*,ij f'(d_i) down spot j's transposed column
-//                (a warp per 512-entry chunk; the chunks' partial sums are
-//                added in a fixed order), then Adam on x_j, clamped at zero,
-//                by the last chunk of spot j.
-// Both stream their compact arrays once per iteration: HBM-bound.
-// Full-matrix products (dose of the weights, target indices over all
-// voxels) use k_spmv_obj: a sub-warp per row of the caller's CSR.
+// setup pass per call copies those rows of every scenario into a compact CSR
+// (16-bit spot indices, rows padded to 8 entries: one 16-byte load of
+// columns and two of values per lane and step).  Each iteration then runs,
+// with no host synchronisation:
+//   k_fwd         d_s = A_s x on the compact rows of every scenario (a warp
+//                 per row) and the scenario's objective f_s (FP64 block sums);
+//   k_bwd_rows    s* = first s with the largest f_s (every block), recorded;
+//                 each block adds f'(d_i) A_s*,i. over its 16 rows, in row
+//                 order, into a shared-memory gradient (rows with f'(d_i) = 0
+//                 are skipped) and stores it as the block's partial;
+//   k_reduce_adam g_j = the partials summed in block order (FP64), then the
+//                 Adam step on x_j, clamped at zero.
+// Every sum has a fixed order, so repeated calls give the same bits.  The
+// iteration is HBM-bound.  Full-matrix products (dose of the weights, target
+// indices over all voxels) use k_spmv_obj: a sub-warp per row of the
+// caller's CSR.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -162,8 +163,7 @@ __global__ void k_init_minmax(int* minmax, int n_scen)
 }
 
 constexpr int kPadRow = 8;                      // compact CSR row padding (entries)
-constexpr int kPadCol = 4;                      // CSC column padding (entries)
-constexpr int kSetupSmemCols = 25600;           // ordered transpose (shared-memory cursors) up to this many spots
+constexpr size_t kBwdSmemMax = 227 * 1024;      // shared memory of one gradient block
 
 // len[s n_tr + i] = entries of target/ring row tr_rows[i] in scenario s.
 __global__ void k_tr_len(const Csr* __restrict__ mats, const int* __restrict__ tr_rows, int n_tr,
@@ -177,133 +177,32 @@ __global__ void k_tr_len(const Csr* __restrict__ mats, const int* __restrict__ t
     len[(long long)s * n_tr + i] = __ldg(rp + r + 1) - __ldg(rp + r);
 }
 
-constexpr int kSetupRows = 32;                  // compact rows per setup block (8 warps x 4)
-
-// Copies the target/ring rows into the compact CSR (a warp per row and
-// scenario; pads and entries with an out-of-range spot become (0, 0.0)) and
-// counts, per spot, the entries the transpose will hold (every entry but a
-// (0, 0.0) one).  kBlockCounts: the block counts in shared memory (n_cols
-// ints) and stores its whole count row, bcnt[(s nb + block) n_cols + j];
-// otherwise it adds to the per-scenario totals ccount with global atomics.
-template <bool kBlockCounts>
+// Copies the target/ring rows into the compact CSR: a warp per row and
+// scenario; pads and entries with an out-of-range spot become (0, 0.0).
 __global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats, const int* __restrict__ tr_rows,
                                                    int n_tr, int n_cols, const long long* __restrict__ crp,
-                                                   unsigned short* __restrict__ ccol, float* __restrict__ cval,
-                                                   int* __restrict__ ccount, int* __restrict__ bcnt)
+                                                   unsigned short* __restrict__ ccol, float* __restrict__ cval)
 {
-    extern __shared__ int hist_s[];
-    const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (kBlockCounts) {
-        for (int j = threadIdx.x; j < n_cols; j += blockDim.x) hist_s[j] = 0;
-        __syncthreads();
-    }
+    const int s = blockIdx.y, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n_tr) return;
     const Csr A = mats[s];
-    int* cnt = kBlockCounts ? hist_s : ccount + (long long)s * n_cols;
-    for (int r = 0; r < kSetupRows / 8; ++r) {
-        const int i = blockIdx.x * kSetupRows + r * 8 + warp;
-        if (i >= n_tr) break;
-        const int row = __ldg(tr_rows + i);
-        const long long b = __ldg(A.row_ptr + row), len = __ldg(A.row_ptr + row + 1) - b;
-        const long long dst = crp[(long long)s * (n_tr + 1) + i];
-        const long long plen = crp[(long long)s * (n_tr + 1) + i + 1] - dst;
-        for (long long k = lane; k < plen; k += 32) {
-            int j = 0;
-            float v = 0.0f;
-            if (k < len) {
-                j = __ldg(A.col + b + k);
-                if ((unsigned)j < (unsigned)n_cols) {
-                    v = __ldg(A.val + b + k);
-                    if (j != 0 || v != 0.0f) atomicAdd(cnt + j, 1);
-                } else {
-                    j = 0;
-                }
-            }
-            ccol[dst + k] = (unsigned short)j;
-            cval[dst + k] = v;
+    const int row = __ldg(tr_rows + i);
+    const long long b = __ldg(A.row_ptr + row), len = __ldg(A.row_ptr + row + 1) - b;
+    const long long dst = crp[(long long)s * (n_tr + 1) + i];
+    const long long plen = crp[(long long)s * (n_tr + 1) + i + 1] - dst;
+    for (long long k = lane; k < plen; k += 32) {
+        int j = 0;
+        float v = 0.0f;
+        if (k < len) {
+            j = __ldg(A.col + b + k);
+            if ((unsigned)j < (unsigned)n_cols)
+                v = __ldg(A.val + b + k);
+            else
+                j = 0;
         }
-    }
-    if (kBlockCounts) {
-        __syncthreads();
-        int* out = bcnt + ((long long)s * gridDim.x + blockIdx.x) * n_cols;
-        for (int j = threadIdx.x; j < n_cols; j += blockDim.x) out[j] = hist_s[j];
-    }
-}
-
-// Per scenario and spot: the blocks' counts become exclusive prefixes over
-// the blocks (in block order) and their sum the spot's total.
-__global__ void k_col_scan(int* __restrict__ bcnt, int nb, int n_cols, int* __restrict__ ccount)
-{
-    const int s = blockIdx.y;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_cols) return;
-    int run = 0;
-    int* c = bcnt + (long long)s * nb * n_cols + j;
-    for (int b = 0; b < nb; ++b) {
-        const int v = c[(long long)b * n_cols];
-        c[(long long)b * n_cols] = run;
-        run += v;
-    }
-    ccount[(long long)s * n_cols + j] = run;
-}
-
-// Transpose in row order: block b of scenario s places its rows one after
-// the other; spot j's entries of this block start at tcp[j] + (entries of j
-// in the blocks before), so every segment is sorted by compact row index and
-// the layout does not depend on scheduling (a row that repeats a spot places
-// its repeats in atomic order).
-__global__ void __launch_bounds__(256) k_csc_fill_ordered(const long long* __restrict__ crp,
-                                                          const unsigned short* __restrict__ ccol,
-                                                          const float* __restrict__ cval, int n_tr, int n_cols,
-                                                          const long long* __restrict__ tcp,
-                                                          const int* __restrict__ bprefix, int* __restrict__ trow,
-                                                          float* __restrict__ tval)
-{
-    extern __shared__ int cursor[];
-    const int s = blockIdx.y;
-    const long long* cp = tcp + (long long)s * (n_cols + 1);
-    const int* pre = bprefix + ((long long)s * gridDim.x + blockIdx.x) * n_cols;
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) cursor[j] = pre[j];
-    __syncthreads();
-    for (int r = 0; r < kSetupRows; ++r) {
-        const int i = blockIdx.x * kSetupRows + r;
-        if (i >= n_tr) break;                             // block-uniform
-        const long long b = crp[(long long)s * (n_tr + 1) + i], e = crp[(long long)s * (n_tr + 1) + i + 1];
-        for (long long k = b + threadIdx.x; k < e; k += blockDim.x) {
-            const int j = ccol[k];
-            const float v = cval[k];
-            if (j == 0 && v == 0.0f) continue;
-            const long long pos = __ldg(cp + j) + atomicAdd(cursor + j, 1);
-            trow[pos] = i;
-            tval[pos] = v;
-        }
-        __syncthreads();
-    }
-}
-
-// The same placement with one global cursor per spot (atomics): for more
-// spots than shared memory holds.  The order inside a segment follows the
-// atomics.
-__global__ void __launch_bounds__(256) k_csc_fill_atomic(const long long* __restrict__ crp,
-                                                         const unsigned short* __restrict__ ccol,
-                                                         const float* __restrict__ cval, int n_tr, int n_cols,
-                                                         const long long* __restrict__ tcp, int* __restrict__ fill,
-                                                         int* __restrict__ trow, float* __restrict__ tval)
-{
-    const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long* cp = tcp + (long long)s * (n_cols + 1);
-    int* fl = fill + (long long)s * n_cols;
-    for (int r = 0; r < kSetupRows / 8; ++r) {
-        const int i = blockIdx.x * kSetupRows + r * 8 + warp;
-        if (i >= n_tr) break;
-        const long long b = crp[(long long)s * (n_tr + 1) + i], e = crp[(long long)s * (n_tr + 1) + i + 1];
-        for (long long k = b + lane; k < e; k += 32) {
-            const int j = ccol[k];
-            const float v = cval[k];
-            if (j == 0 && v == 0.0f) continue;
-            const long long pos = cp[j] + atomicAdd(fl + j, 1);
-            trow[pos] = i;
-            tval[pos] = v;
-        }
+        ccol[dst + k] = (unsigned short)j;
+        cval[dst + k] = v;
     }
 }
 
@@ -352,34 +251,23 @@ __global__ void __launch_bounds__(256) k_fwd(const long long* __restrict__ crp, 
     }
 }
 
-// A piece of one spot's transposed column: entries [b, b + n) of the
-// transpose (n a multiple of 4, at most kChunk; n = 0 for a spot without
-// entries, which still takes its Adam step with g = 0).  first: index of the
-// spot's first chunk in the scenario's list; total: the spot's chunk count.
-struct Chunk {
-    long long b;
-    int j, n, first, total;
-};
-constexpr int kChunk = 512;
+constexpr int kBwdRows = 16;                    // compact rows per gradient block
 
-// Worst scenario, gradient and Adam step (Kingma & Ba 2015) clamped at zero.
-// A warp per chunk of the worst scenario's transpose: FP32 sums per lane (at
-// most 16 terms), an FP64 warp sum stored as the chunk's partial; the last
-// of spot j's chunks to arrive (counter per spot) adds the spot's partials
-// in chunk order (the same sum whatever the arrival order), resets the
-// counter and updates x_j, m_j, v_j.  Grid: the largest chunk count over the
-// scenarios / 8, 256 threads.
-__global__ void __launch_bounds__(256) k_bwd_adam(const Chunk* __restrict__ chunks,
-                                                  const long long* __restrict__ chunk_off,
-                                                  const int* __restrict__ trow, const float* __restrict__ tval,
-                                                  int n_tr, const float* __restrict__ dose_tr,
+// Worst scenario and the blocks' gradient partials.  Within one row the
+// spots are distinct, so the shared-memory adds of a row never meet (pads
+// add zeros to spot 0) and the barrier after each row fixes the order of the
+// sums; a row that repeats a spot adds its repeats in atomic order.
+// Grid: compact rows / kBwdRows, 256 threads, n_cols floats of shared memory.
+__global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ crp,
+                                                  const unsigned short* __restrict__ ccol,
+                                                  const float* __restrict__ cval, int n_tr, int n_cols,
+                                                  const float* __restrict__ dose_tr,
                                                   const unsigned char* __restrict__ tr_cls, ObjParams q,
                                                   const double* __restrict__ fsum_cur, double* __restrict__ fsum_next,
                                                   int n_scen, float* __restrict__ hist, int it,
-                                                  double* __restrict__ partial, int* __restrict__ arrived,
-                                                  float* __restrict__ x, float* __restrict__ m, float* __restrict__ v,
-                                                  float step, float c1, float c2, float eps)
+                                                  float* __restrict__ partial)
 {
+    extern __shared__ float gs[];
     __shared__ int s_star;
     if (threadIdx.x == 0) {
         int w = 0;
@@ -389,41 +277,50 @@ __global__ void __launch_bounds__(256) k_bwd_adam(const Chunk* __restrict__ chun
         if (blockIdx.x == 0 && hist) hist[it] = (float)fsum_cur[w];
     }
     if (blockIdx.x == 0 && threadIdx.x < n_scen) fsum_next[threadIdx.x] = 0.0;
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) gs[j] = 0.0f;
     __syncthreads();
-    const int s = s_star, lane = threadIdx.x & 31;
-    const long long c = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const long long c0 = __ldg(chunk_off + s), c1n = __ldg(chunk_off + s + 1);
-    if (c >= c1n - c0) return;                        // warp-uniform
-    const Chunk ch = chunks[c0 + c];
-    const float* d = dose_tr + (long long)s * n_tr;
-    float accf = 0.0f;
-    for (int k = lane * 4; k < ch.n; k += 128) {
-        const int4 r = __ldcs(reinterpret_cast<const int4*>(trow + ch.b + k));
-        const float4 a = __ldcs(reinterpret_cast<const float4*>(tval + ch.b + k));
-        accf = fmaf(a.x, obj_grad(__ldg(d + r.x), __ldg(tr_cls + r.x), q), accf);
-        accf = fmaf(a.y, obj_grad(__ldg(d + r.y), __ldg(tr_cls + r.y), q), accf);
-        accf = fmaf(a.z, obj_grad(__ldg(d + r.z), __ldg(tr_cls + r.z), q), accf);
-        accf = fmaf(a.w, obj_grad(__ldg(d + r.w), __ldg(tr_cls + r.w), q), accf);
-    }
-    double acc = (double)accf;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
-    if (lane == 0) {
-        const int j = ch.j;
-        partial[c] = acc;
-        __threadfence();
-        if (atomicAdd(arrived + j, 1) == ch.total - 1) {
-            __threadfence();
-            double gsum = 0.0;
-            for (int k = 0; k < ch.total; ++k) gsum += __ldcg(partial + ch.first + k);
-            arrived[j] = 0;
-            const float gj = (float)gsum;
-            const float mj = fmaf(0.9f, m[j], 0.1f * gj), vj = fmaf(0.999f, v[j], 0.001f * gj * gj);
-            m[j] = mj;
-            v[j] = vj;
-            x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
+    const int s = s_star;
+    const long long* rp = crp + (long long)s * (n_tr + 1);
+    for (int r = 0; r < kBwdRows; ++r) {
+        const int i = blockIdx.x * kBwdRows + r;
+        if (i >= n_tr) break;                             // block-uniform
+        const float ri = obj_grad(__ldg(dose_tr + (long long)s * n_tr + i), __ldg(tr_cls + i), q);
+        if (ri == 0.0f) continue;                         // block-uniform; adds nothing
+        const long long b = __ldg(rp + i), e = __ldg(rp + i + 1);
+        for (long long k = b + threadIdx.x * kPadRow; k < e; k += (long long)blockDim.x * kPadRow) {
+            const uint4 c = __ldcs(reinterpret_cast<const uint4*>(ccol + k));
+            const float4 v0 = __ldcs(reinterpret_cast<const float4*>(cval + k));
+            const float4 v1 = __ldcs(reinterpret_cast<const float4*>(cval + k + 4));
+            atomicAdd(gs + (c.x & 0xffffu), v0.x * ri);
+            atomicAdd(gs + (c.x >> 16), v0.y * ri);
+            atomicAdd(gs + (c.y & 0xffffu), v0.z * ri);
+            atomicAdd(gs + (c.y >> 16), v0.w * ri);
+            atomicAdd(gs + (c.z & 0xffffu), v1.x * ri);
+            atomicAdd(gs + (c.z >> 16), v1.y * ri);
+            atomicAdd(gs + (c.w & 0xffffu), v1.z * ri);
+            atomicAdd(gs + (c.w >> 16), v1.w * ri);
         }
+        __syncthreads();
     }
+    __syncthreads();
+    float* out = partial + (long long)blockIdx.x * n_cols;
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) out[j] = gs[j];
+}
+
+// g_j = the blocks' partials summed in block order (FP64), then Adam
+// (Kingma & Ba 2015) on x_j, clamped at zero.
+__global__ void k_reduce_adam(const float* __restrict__ partial, int nb, int n_cols, float* __restrict__ x,
+                              float* __restrict__ m, float* __restrict__ v, float step, float c1, float c2, float eps)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_cols) return;
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) acc += (double)__ldcs(partial + (long long)b * n_cols + j);
+    const float g = (float)acc;
+    const float mj = fmaf(0.9f, m[j], 0.1f * g), vj = fmaf(0.999f, v[j], 0.001f * g * g);
+    m[j] = mj;
+    v[j] = vj;
+    x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
 }
 
 }  // namespace
@@ -470,16 +367,7 @@ struct RobustWs {
     long long* crp = nullptr;
     unsigned short* ccol = nullptr;
     float* cval = nullptr;
-    int* ccount = nullptr;
-    long long* tcp = nullptr;
-    int* fill = nullptr;
-    int* trow = nullptr;
-    float* tval = nullptr;
-    Chunk* chunks = nullptr;                    // every scenario's transpose chunks
-    long long* chunk_off = nullptr;             // [S + 1]
-    int* bcnt = nullptr;                        // [S x blocks x n_cols] setup counts
-    double* partial = nullptr;                  // [largest chunk count]
-    int* arrived = nullptr;
+    float* partial = nullptr;                   // [gradient blocks x n_cols]
     float* dose_tr = nullptr;
     double* fsum = nullptr;                     // [2 x S]: this iteration's sums, the next one's
     float* m = nullptr;
@@ -488,9 +376,8 @@ struct RobustWs {
     ~RobustWs()
     {
         cudaFree(mats); cudaFree(tr_rows); cudaFree(tr_cls); cudaFree(len); cudaFree(crp); cudaFree(ccol);
-        cudaFree(cval); cudaFree(ccount); cudaFree(tcp); cudaFree(fill); cudaFree(trow); cudaFree(tval);
-        cudaFree(chunks); cudaFree(chunk_off); cudaFree(bcnt); cudaFree(partial); cudaFree(arrived);
-        cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v); cudaFree(hist);
+        cudaFree(cval); cudaFree(partial); cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v);
+        cudaFree(hist);
     }
 };
 
@@ -507,6 +394,7 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     RobustWs w;
     cudaError_t e;
 #define OPT_TRY(expr) do { if ((e = (expr)) != cudaSuccess) return e; } while (0)
+    if ((size_t)n_cols * sizeof(float) > kBwdSmemMax) return cudaErrorInvalidValue;
     // target and ring rows, in voxel order
     std::vector<int> rows;
     std::vector<unsigned char> rcls;
@@ -553,105 +441,37 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     OPT_TRY(cudaMemcpyAsync(w.crp, crp.data(), sizeof(long long) * crp.size(), cudaMemcpyHostToDevice, st));
     OPT_TRY(dalloc(&w.ccol, (size_t)total_c));
     OPT_TRY(dalloc(&w.cval, (size_t)total_c));
-    OPT_TRY(dalloc(&w.ccount, (size_t)S * n_cols));
-    OPT_TRY(cudaMemsetAsync(w.ccount, 0, sizeof(int) * (size_t)S * n_cols, st));
-    const int nb = (n_tr + kSetupRows - 1) / kSetupRows;
-    const dim3 gw((unsigned)nb, (unsigned)S);
-    // ordered transpose when the per-block counts and the cursors fit
-    const bool ordered = n_cols <= kSetupSmemCols && (size_t)S * nb * n_cols * sizeof(int) <= ((size_t)1 << 30);
-    if (ordered) {
-        OPT_TRY(dalloc(&w.bcnt, (size_t)S * nb * n_cols));
-        const int sm1 = (int)(sizeof(int) * n_cols);
-        OPT_TRY(cudaFuncSetAttribute(k_tr_gather<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
-        k_tr_gather<true><<<gw, 256, sm1, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount,
-                                                w.bcnt);
-        OPT_TRY(cudaGetLastError());
-        k_col_scan<<<dim3((unsigned)((n_cols + 255) / 256), (unsigned)S), 256, 0, st>>>(w.bcnt, nb, n_cols,
-                                                                                        w.ccount);
-    } else {
-        k_tr_gather<false><<<gw, 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.ccount,
-                                               nullptr);
-    }
-    OPT_TRY(cudaGetLastError());
-    // transpose layout
-    std::vector<int> cnt((size_t)S * n_cols);
-    std::vector<long long> tcp((size_t)S * (n_cols + 1));
-    OPT_TRY(cudaMemcpyAsync(cnt.data(), w.ccount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, st));
-    OPT_TRY(cudaStreamSynchronize(st));
-    long long total_t = 0;
-    for (int s = 0; s < S; ++s) {
-        for (int j = 0; j < n_cols; ++j) {
-            tcp[(size_t)s * (n_cols + 1) + j] = total_t;
-            total_t += ((long long)cnt[(size_t)s * n_cols + j] + kPadCol - 1) / kPadCol * kPadCol;
-        }
-        tcp[(size_t)s * (n_cols + 1) + n_cols] = total_t;
-    }
-    std::vector<Chunk> chunks;
-    std::vector<long long> chunk_off(S + 1, 0);
-    long long max_chunks = 0;
-    for (int s = 0; s < S; ++s) {
-        chunk_off[s] = (long long)chunks.size();
-        for (int j = 0; j < n_cols; ++j) {
-            const long long b = tcp[(size_t)s * (n_cols + 1) + j], e = tcp[(size_t)s * (n_cols + 1) + j + 1];
-            const int first = (int)((long long)chunks.size() - chunk_off[s]);
-            const int total = e > b ? (int)((e - b + kChunk - 1) / kChunk) : 1;
-            for (int k = 0; k < total; ++k) {
-                const long long c = b + (long long)k * kChunk;
-                chunks.push_back(Chunk{c, j, (int)std::max<long long>(0, std::min<long long>(kChunk, e - c)), first,
-                                       total});
-            }
-        }
-        max_chunks = std::max(max_chunks, (long long)chunks.size() - chunk_off[s]);
-    }
-    chunk_off[S] = (long long)chunks.size();
-    OPT_TRY(dalloc(&w.chunks, chunks.size()));
-    OPT_TRY(dalloc(&w.chunk_off, chunk_off.size()));
-    OPT_TRY(cudaMemcpyAsync(w.chunks, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice, st));
-    OPT_TRY(cudaMemcpyAsync(w.chunk_off, chunk_off.data(), sizeof(long long) * chunk_off.size(),
-                            cudaMemcpyHostToDevice, st));
-    OPT_TRY(dalloc(&w.tcp, tcp.size()));
-    OPT_TRY(cudaMemcpyAsync(w.tcp, tcp.data(), sizeof(long long) * tcp.size(), cudaMemcpyHostToDevice, st));
-    OPT_TRY(dalloc(&w.trow, (size_t)total_t));
-    OPT_TRY(dalloc(&w.tval, (size_t)total_t));
-    OPT_TRY(cudaMemsetAsync(w.trow, 0, sizeof(int) * (size_t)std::max<long long>(total_t, 1), st));
-    OPT_TRY(cudaMemsetAsync(w.tval, 0, sizeof(float) * (size_t)std::max<long long>(total_t, 1), st));
-    if (ordered) {
-        const int sm2 = (int)(sizeof(int) * n_cols);
-        OPT_TRY(cudaFuncSetAttribute(k_csc_fill_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
-        k_csc_fill_ordered<<<gw, 256, sm2, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.tcp, w.bcnt, w.trow, w.tval);
-    } else {
-        OPT_TRY(dalloc(&w.fill, (size_t)S * n_cols));
-        OPT_TRY(cudaMemsetAsync(w.fill, 0, sizeof(int) * (size_t)S * n_cols, st));
-        k_csc_fill_atomic<<<gw, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.tcp, w.fill, w.trow, w.tval);
-    }
+    k_tr_gather<<<dim3((unsigned)((n_tr + 7) / 8), (unsigned)S), 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols,
+                                                                               w.crp, w.ccol, w.cval);
     OPT_TRY(cudaGetLastError());
     // iteration state
+    const int nb = (n_tr + kBwdRows - 1) / kBwdRows;
+    OPT_TRY(dalloc(&w.partial, (size_t)nb * n_cols));
     OPT_TRY(dalloc(&w.dose_tr, (size_t)S * n_tr));
     OPT_TRY(dalloc(&w.fsum, (size_t)2 * S));
     OPT_TRY(dalloc(&w.m, (size_t)n_cols));
     OPT_TRY(dalloc(&w.v, (size_t)n_cols));
-    OPT_TRY(dalloc(&w.partial, (size_t)max_chunks));
-    OPT_TRY(dalloc(&w.arrived, (size_t)n_cols));
-    OPT_TRY(cudaMemsetAsync(w.arrived, 0, sizeof(int) * n_cols, st));
     OPT_TRY(dalloc(&w.hist, (size_t)std::max(spec.iterations, 1)));
     OPT_TRY(cudaMemsetAsync(w.fsum, 0, sizeof(double) * 2 * S, st));
     OPT_TRY(cudaMemsetAsync(w.m, 0, sizeof(float) * n_cols, st));
     OPT_TRY(cudaMemsetAsync(w.v, 0, sizeof(float) * n_cols, st));
+    const int smem = (int)(sizeof(float) * n_cols);
+    OPT_TRY(cudaFuncSetAttribute(k_bwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     OPT_TRY(cudaEventRecord(ev[1], st));
     const ObjParams q{spec.dp, spec.w_u, spec.w_o, spec.w_r, spec.over, spec.ring,
                       1.0f / (float)std::max<long long>(spec.n_target, 1),
                       1.0f / (float)std::max<long long>(spec.n_ring, 1)};
     const dim3 gf((unsigned)std::max((n_tr + 7) / 8, 1), (unsigned)S);
-    const unsigned gb = (unsigned)((max_chunks + 7) / 8);
     for (int it = 0; it < spec.iterations; ++it) {
         double* cur = w.fsum + (it & 1) * S;
         double* nxt = w.fsum + ((it + 1) & 1) * S;
         k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, cur);
+        k_bwd_rows<<<(unsigned)nb, 256, smem, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.dose_tr, w.tr_cls, q, cur,
+                                                    nxt, S, w.hist, it, w.partial);
         const double t = it + 1;
-        k_bwd_adam<<<gb, 256, 0, st>>>(w.chunks, w.chunk_off, w.trow, w.tval, n_tr, w.dose_tr, w.tr_cls, q, cur, nxt,
-                                       S, w.hist, it, w.partial, w.arrived, x, w.m, w.v, spec.step,
-                                       (float)(1.0 / (1.0 - std::pow(0.9, t))),
-                                       (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
+        k_reduce_adam<<<(unsigned)((n_cols + 127) / 128), 128, 0, st>>>(
+            w.partial, nb, n_cols, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
+            (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
     }
     OPT_TRY(cudaGetLastError());
     OPT_TRY(cudaEventRecord(ev[2], st));
@@ -667,7 +487,6 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
         info->n_tr = n_tr;
         info->nnz_tr = nnz_tr;
         info->compact_entries = total_c;
-        info->transpose_entries = total_t;
     }
     if (hist_host && spec.iterations > 0)
         OPT_TRY(cudaMemcpy(hist_host, w.hist, sizeof(float) * spec.iterations, cudaMemcpyDeviceToHost));

@@ -272,7 +272,7 @@ struct OptSpec {
 };
 struct OptSetupInfo {
     long long n_tr, nnz_tr;                 // target + ring rows; their entries over all scenarios
-    long long compact_entries, transpose_entries;   // padded sizes of the compact CSR and its transpose
+    long long compact_entries;              // padded size of the compact CSR
 };
 cudaError_t run_robust_optimize(const long long* const* rp, const int* const* col, const float* const* val, int n_scen,
                                 long long n_rows, int n_cols, const unsigned char* cls_host, const OptSpec& spec,
