@@ -13,11 +13,11 @@
 //   k_fwd         d_s = A_s x on the compact rows of every scenario (a warp
 //                 per row) and the scenario's objective f_s (FP64 block sums);
 //   k_bwd_rows    s* = first s with the largest f_s (every block), recorded;
-//                 each block adds f'(d_i) A_s*,i. over its 16 rows, in row
+//                 each block adds f'(d_i) A_s*,i. over its 8 rows, in row
 //                 order, into a shared-memory gradient (rows with f'(d_i) = 0
 //                 are skipped) and stores it as the block's partial;
-//   k_reduce_adam g_j = the partials summed in block order (FP64), then the
-//                 Adam step on x_j, clamped at zero.
+//   k_reduce_adam g_j = the partials summed in a fixed order, then the Adam
+//                 step on x_j, clamped at zero.
 // Every sum has a fixed order, so repeated calls give the same bits.  The
 // iteration is HBM-bound.  Full-matrix products (dose of the weights, target
 // indices over all voxels) use k_spmv_obj: a sub-warp per row of the
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256) k_fwd(const long long* __restrict__ crp, 
     }
 }
 
-constexpr int kBwdRows = 16;                    // compact rows per gradient block
+constexpr int kBwdRows = 8;                     // compact rows per gradient block
 
 // Worst scenario and the blocks' gradient partials.  Within one row the
 // spots are distinct, so the shared-memory adds of a row never meet (pads
@@ -307,15 +307,28 @@ __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ 
     for (int j = threadIdx.x; j < n_cols; j += blockDim.x) out[j] = gs[j];
 }
 
-// g_j = the blocks' partials summed in block order (FP64), then Adam
-// (Kingma & Ba 2015) on x_j, clamped at zero.
-__global__ void k_reduce_adam(const float* __restrict__ partial, int nb, int n_cols, float* __restrict__ x,
-                              float* __restrict__ m, float* __restrict__ v, float step, float c1, float c2, float eps)
+// g_j = the blocks' partials in a fixed order: slice t of 16 sums (FP32) the
+// partials of blocks t, t + 16, ..., then the 16 slice sums are added in
+// order (FP64); then Adam (Kingma & Ba 2015) on x_j, clamped at zero.
+// Grid: n_cols / 32, 512 threads (32 spots x 16 slices).
+__global__ void __launch_bounds__(512) k_reduce_adam(const float* __restrict__ partial, int nb, int n_cols,
+                                                     float* __restrict__ x, float* __restrict__ m,
+                                                     float* __restrict__ v, float step, float c1, float c2, float eps)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_cols) return;
+    __shared__ float red[16][33];
+    const int c = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + c;
+    float a = 0.0f;
+    if (j < n_cols) {
+#pragma unroll 4
+        for (int b = sl; b < nb; b += 16) a += __ldcs(partial + (long long)b * n_cols + j);
+    }
+    red[sl][c] = a;
+    __syncthreads();
+    if (sl != 0 || j >= n_cols) return;
     double acc = 0.0;
-    for (int b = 0; b < nb; ++b) acc += (double)__ldcs(partial + (long long)b * n_cols + j);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc += (double)red[k][c];
     const float g = (float)acc;
     const float mj = fmaf(0.9f, m[j], 0.1f * g), vj = fmaf(0.999f, v[j], 0.001f * g * g);
     m[j] = mj;
@@ -469,7 +482,7 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
         k_bwd_rows<<<(unsigned)nb, 256, smem, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.dose_tr, w.tr_cls, q, cur,
                                                     nxt, S, w.hist, it, w.partial);
         const double t = it + 1;
-        k_reduce_adam<<<(unsigned)((n_cols + 127) / 128), 128, 0, st>>>(
+        k_reduce_adam<<<(unsigned)((n_cols + 31) / 32), 512, 0, st>>>(
             w.partial, nb, n_cols, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
             (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
     }
