@@ -179,9 +179,12 @@ __global__ void k_tr_len(const Csr* __restrict__ mats, const int* __restrict__ t
 
 // Copies the target/ring rows into the compact CSR: a warp per row and
 // scenario; pads and entries with an out-of-range spot become (0, 0.0).
+// Sets *unordered if a row's spot indices are not strictly increasing (a
+// row may then repeat a spot).
 __global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats, const int* __restrict__ tr_rows,
                                                    int n_tr, int n_cols, const long long* __restrict__ crp,
-                                                   unsigned short* __restrict__ ccol, float* __restrict__ cval)
+                                                   unsigned short* __restrict__ ccol, float* __restrict__ cval,
+                                                   int* __restrict__ unordered)
 {
     const int s = blockIdx.y, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats,
         float v = 0.0f;
         if (k < len) {
             j = __ldg(A.col + b + k);
+            if (k > 0 && j <= __ldg(A.col + b + k - 1)) *unordered = 1;
             if ((unsigned)j < (unsigned)n_cols)
                 v = __ldg(A.val + b + k);
             else
@@ -253,11 +257,16 @@ __global__ void __launch_bounds__(256) k_fwd(const long long* __restrict__ crp, 
 
 constexpr int kBwdRows = 8;                     // compact rows per gradient block
 
-// Worst scenario and the blocks' gradient partials.  Within one row the
-// spots are distinct, so the shared-memory adds of a row never meet (pads
-// add zeros to spot 0) and the barrier after each row fixes the order of the
-// sums; a row that repeats a spot adds its repeats in atomic order.
-// Grid: compact rows / kBwdRows, 256 threads, n_cols floats of shared memory.
+// Worst scenario and the blocks' gradient partials: each block adds
+// f'(d_i) A_s*,ij over its rows, one row after the other (a barrier after
+// each), into a shared-memory gradient.  Pads and zero values add nothing
+// and are skipped.  kAtomic = false when every row's spots are strictly
+// increasing: a row's adds then touch distinct spots and are plain
+// read-add-writes; kAtomic = true for rows that may repeat a spot (shared
+// atomics; the repeats of a row add in atomic order).  Either way the sum
+// order of every spot is the row order.  Grid: compact rows / kBwdRows, 256
+// threads, n_cols floats of shared memory.
+template <bool kAtomic>
 __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ crp,
                                                   const unsigned short* __restrict__ ccol,
                                                   const float* __restrict__ cval, int n_tr, int n_cols,
@@ -281,6 +290,14 @@ __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ 
     __syncthreads();
     const int s = s_star;
     const long long* rp = crp + (long long)s * (n_tr + 1);
+    auto add = [&](unsigned j, float a, float ri) {
+        if (a != 0.0f) {
+            if (kAtomic)
+                atomicAdd(gs + j, a * ri);
+            else
+                gs[j] = fmaf(a, ri, gs[j]);
+        }
+    };
     for (int r = 0; r < kBwdRows; ++r) {
         const int i = blockIdx.x * kBwdRows + r;
         if (i >= n_tr) break;                             // block-uniform
@@ -291,14 +308,14 @@ __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ 
             const uint4 c = __ldcs(reinterpret_cast<const uint4*>(ccol + k));
             const float4 v0 = __ldcs(reinterpret_cast<const float4*>(cval + k));
             const float4 v1 = __ldcs(reinterpret_cast<const float4*>(cval + k + 4));
-            atomicAdd(gs + (c.x & 0xffffu), v0.x * ri);
-            atomicAdd(gs + (c.x >> 16), v0.y * ri);
-            atomicAdd(gs + (c.y & 0xffffu), v0.z * ri);
-            atomicAdd(gs + (c.y >> 16), v0.w * ri);
-            atomicAdd(gs + (c.z & 0xffffu), v1.x * ri);
-            atomicAdd(gs + (c.z >> 16), v1.y * ri);
-            atomicAdd(gs + (c.w & 0xffffu), v1.z * ri);
-            atomicAdd(gs + (c.w >> 16), v1.w * ri);
+            add(c.x & 0xffffu, v0.x, ri);
+            add(c.x >> 16, v0.y, ri);
+            add(c.y & 0xffffu, v0.z, ri);
+            add(c.y >> 16, v0.w, ri);
+            add(c.z & 0xffffu, v1.x, ri);
+            add(c.z >> 16, v1.y, ri);
+            add(c.w & 0xffffu, v1.z, ri);
+            add(c.w >> 16, v1.w, ri);
         }
         __syncthreads();
     }
@@ -307,28 +324,29 @@ __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ 
     for (int j = threadIdx.x; j < n_cols; j += blockDim.x) out[j] = gs[j];
 }
 
-// g_j = the blocks' partials in a fixed order: slice t of 16 sums (FP32) the
-// partials of blocks t, t + 16, ..., then the 16 slice sums are added in
+// g_j = the blocks' partials in a fixed order: slice t of 64 sums (FP32) the
+// partials of blocks t, t + 64, ..., then the 64 slice sums are added in
 // order (FP64); then Adam (Kingma & Ba 2015) on x_j, clamped at zero.
-// Grid: n_cols / 32, 512 threads (32 spots x 16 slices).
-__global__ void __launch_bounds__(512) k_reduce_adam(const float* __restrict__ partial, int nb, int n_cols,
-                                                     float* __restrict__ x, float* __restrict__ m,
-                                                     float* __restrict__ v, float step, float c1, float c2, float eps)
+// Grid: n_cols / 16, 1024 threads (16 spots x 64 slices).
+__global__ void __launch_bounds__(1024) k_reduce_adam(const float* __restrict__ partial, int nb, int n_cols,
+                                                      float* __restrict__ x, float* __restrict__ m,
+                                                      float* __restrict__ v, float step, float c1, float c2,
+                                                      float eps)
 {
-    __shared__ float red[16][33];
-    const int c = threadIdx.x & 31, sl = threadIdx.x >> 5;
-    const int j = blockIdx.x * 32 + c;
+    __shared__ float red[64][17];
+    const int c = threadIdx.x & 15, sl = threadIdx.x >> 4;
+    const int j = blockIdx.x * 16 + c;
     float a = 0.0f;
     if (j < n_cols) {
 #pragma unroll 4
-        for (int b = sl; b < nb; b += 16) a += __ldcs(partial + (long long)b * n_cols + j);
+        for (int b = sl; b < nb; b += 64) a += __ldcs(partial + (long long)b * n_cols + j);
     }
     red[sl][c] = a;
     __syncthreads();
     if (sl != 0 || j >= n_cols) return;
     double acc = 0.0;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) acc += (double)red[k][c];
+#pragma unroll 8
+    for (int k = 0; k < 64; ++k) acc += (double)red[k][c];
     const float g = (float)acc;
     const float mj = fmaf(0.9f, m[j], 0.1f * g), vj = fmaf(0.999f, v[j], 0.001f * g * g);
     m[j] = mj;
@@ -381,6 +399,7 @@ struct RobustWs {
     unsigned short* ccol = nullptr;
     float* cval = nullptr;
     float* partial = nullptr;                   // [gradient blocks x n_cols]
+    int* unordered = nullptr;
     float* dose_tr = nullptr;
     double* fsum = nullptr;                     // [2 x S]: this iteration's sums, the next one's
     float* m = nullptr;
@@ -389,7 +408,7 @@ struct RobustWs {
     ~RobustWs()
     {
         cudaFree(mats); cudaFree(tr_rows); cudaFree(tr_cls); cudaFree(len); cudaFree(crp); cudaFree(ccol);
-        cudaFree(cval); cudaFree(partial); cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v);
+        cudaFree(cval); cudaFree(partial); cudaFree(unordered); cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v);
         cudaFree(hist);
     }
 };
@@ -454,9 +473,14 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     OPT_TRY(cudaMemcpyAsync(w.crp, crp.data(), sizeof(long long) * crp.size(), cudaMemcpyHostToDevice, st));
     OPT_TRY(dalloc(&w.ccol, (size_t)total_c));
     OPT_TRY(dalloc(&w.cval, (size_t)total_c));
+    OPT_TRY(dalloc(&w.unordered, 1));
+    OPT_TRY(cudaMemsetAsync(w.unordered, 0, sizeof(int), st));
     k_tr_gather<<<dim3((unsigned)((n_tr + 7) / 8), (unsigned)S), 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols,
-                                                                               w.crp, w.ccol, w.cval);
+                                                                               w.crp, w.ccol, w.cval, w.unordered);
     OPT_TRY(cudaGetLastError());
+    int unordered = 0;
+    OPT_TRY(cudaMemcpyAsync(&unordered, w.unordered, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OPT_TRY(cudaStreamSynchronize(st));
     // iteration state
     const int nb = (n_tr + kBwdRows - 1) / kBwdRows;
     OPT_TRY(dalloc(&w.partial, (size_t)nb * n_cols));
@@ -469,7 +493,8 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     OPT_TRY(cudaMemsetAsync(w.m, 0, sizeof(float) * n_cols, st));
     OPT_TRY(cudaMemsetAsync(w.v, 0, sizeof(float) * n_cols, st));
     const int smem = (int)(sizeof(float) * n_cols);
-    OPT_TRY(cudaFuncSetAttribute(k_bwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    auto* bwd = unordered ? k_bwd_rows<true> : k_bwd_rows<false>;
+    OPT_TRY(cudaFuncSetAttribute(bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     OPT_TRY(cudaEventRecord(ev[1], st));
     const ObjParams q{spec.dp, spec.w_u, spec.w_o, spec.w_r, spec.over, spec.ring,
                       1.0f / (float)std::max<long long>(spec.n_target, 1),
@@ -479,10 +504,10 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
         double* cur = w.fsum + (it & 1) * S;
         double* nxt = w.fsum + ((it + 1) & 1) * S;
         k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, cur);
-        k_bwd_rows<<<(unsigned)nb, 256, smem, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.dose_tr, w.tr_cls, q, cur,
-                                                    nxt, S, w.hist, it, w.partial);
+        bwd<<<(unsigned)nb, 256, smem, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.dose_tr, w.tr_cls, q, cur, nxt, S,
+                                             w.hist, it, w.partial);
         const double t = it + 1;
-        k_reduce_adam<<<(unsigned)((n_cols + 31) / 32), 512, 0, st>>>(
+        k_reduce_adam<<<(unsigned)((n_cols + 15) / 16), 1024, 0, st>>>(
             w.partial, nb, n_cols, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
             (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
     }
