@@ -278,6 +278,8 @@ __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ 
 {
     extern __shared__ float gs[];
     __shared__ int s_star;
+    __shared__ float s_ri[kBwdRows];
+    __shared__ long long s_b[kBwdRows], s_e[kBwdRows];
     if (threadIdx.x == 0) {
         int w = 0;
         for (int k = 1; k < n_scen; ++k)
@@ -289,7 +291,21 @@ __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ 
     for (int j = threadIdx.x; j < n_cols; j += blockDim.x) gs[j] = 0.0f;
     __syncthreads();
     const int s = s_star;
-    const long long* rp = crp + (long long)s * (n_tr + 1);
+    // the block's rows: f'(d_i) and entry range, loaded together
+    if (threadIdx.x < kBwdRows) {
+        const int i = blockIdx.x * kBwdRows + threadIdx.x;
+        float ri = 0.0f;
+        long long b = 0, e = 0;
+        if (i < n_tr) {
+            ri = obj_grad(__ldg(dose_tr + (long long)s * n_tr + i), __ldg(tr_cls + i), q);
+            b = __ldg(crp + (long long)s * (n_tr + 1) + i);
+            e = __ldg(crp + (long long)s * (n_tr + 1) + i + 1);
+        }
+        s_ri[threadIdx.x] = ri;
+        s_b[threadIdx.x] = b;
+        s_e[threadIdx.x] = ri != 0.0f ? e : b;          // rows with f' = 0 add nothing: empty
+    }
+    __syncthreads();
     auto add = [&](unsigned j, float a, float ri) {
         if (a != 0.0f) {
             if (kAtomic)
@@ -298,55 +314,74 @@ __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ 
                 gs[j] = fmaf(a, ri, gs[j]);
         }
     };
+    auto add8 = [&](const uint4& c, const float4& v0, const float4& v1, float ri) {
+        add(c.x & 0xffffu, v0.x, ri);
+        add(c.x >> 16, v0.y, ri);
+        add(c.y & 0xffffu, v0.z, ri);
+        add(c.y >> 16, v0.w, ri);
+        add(c.z & 0xffffu, v1.x, ri);
+        add(c.z >> 16, v1.y, ri);
+        add(c.w & 0xffffu, v1.z, ri);
+        add(c.w >> 16, v1.w, ri);
+    };
+    const long long lane8 = (long long)threadIdx.x * kPadRow, stride = (long long)blockDim.x * kPadRow;
+    // first step of row 0 in registers; each iteration loads the next row's
+    // first step before adding the current one
+    uint4 c = make_uint4(0u, 0u, 0u, 0u);
+    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+    if (s_b[0] + lane8 < s_e[0]) {
+        c = __ldcs(reinterpret_cast<const uint4*>(ccol + s_b[0] + lane8));
+        v0 = __ldcs(reinterpret_cast<const float4*>(cval + s_b[0] + lane8));
+        v1 = __ldcs(reinterpret_cast<const float4*>(cval + s_b[0] + lane8 + 4));
+    }
     for (int r = 0; r < kBwdRows; ++r) {
-        const int i = blockIdx.x * kBwdRows + r;
-        if (i >= n_tr) break;                             // block-uniform
-        const float ri = obj_grad(__ldg(dose_tr + (long long)s * n_tr + i), __ldg(tr_cls + i), q);
-        if (ri == 0.0f) continue;                         // block-uniform; adds nothing
-        const long long b = __ldg(rp + i), e = __ldg(rp + i + 1);
-        for (long long k = b + threadIdx.x * kPadRow; k < e; k += (long long)blockDim.x * kPadRow) {
-            const uint4 c = __ldcs(reinterpret_cast<const uint4*>(ccol + k));
-            const float4 v0 = __ldcs(reinterpret_cast<const float4*>(cval + k));
-            const float4 v1 = __ldcs(reinterpret_cast<const float4*>(cval + k + 4));
-            add(c.x & 0xffffu, v0.x, ri);
-            add(c.x >> 16, v0.y, ri);
-            add(c.y & 0xffffu, v0.z, ri);
-            add(c.y >> 16, v0.w, ri);
-            add(c.z & 0xffffu, v1.x, ri);
-            add(c.z >> 16, v1.y, ri);
-            add(c.w & 0xffffu, v1.z, ri);
-            add(c.w >> 16, v1.w, ri);
+        uint4 cn = make_uint4(0u, 0u, 0u, 0u);
+        float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
+        if (r + 1 < kBwdRows && s_b[r + 1] + lane8 < s_e[r + 1]) {
+            cn = __ldcs(reinterpret_cast<const uint4*>(ccol + s_b[r + 1] + lane8));
+            w0 = __ldcs(reinterpret_cast<const float4*>(cval + s_b[r + 1] + lane8));
+            w1 = __ldcs(reinterpret_cast<const float4*>(cval + s_b[r + 1] + lane8 + 4));
         }
-        __syncthreads();
+        const float ri = s_ri[r];
+        const long long b = s_b[r], e = s_e[r];
+        if (b + lane8 < e) add8(c, v0, v1, ri);
+        for (long long k = b + lane8 + stride; k < e; k += stride) {          // rows longer than one step
+            add8(__ldcs(reinterpret_cast<const uint4*>(ccol + k)), __ldcs(reinterpret_cast<const float4*>(cval + k)),
+                 __ldcs(reinterpret_cast<const float4*>(cval + k + 4)), ri);
+        }
+        if (b < e) __syncthreads();                       // block-uniform
+        c = cn;
+        v0 = w0;
+        v1 = w1;
     }
     __syncthreads();
     float* out = partial + (long long)blockIdx.x * n_cols;
     for (int j = threadIdx.x; j < n_cols; j += blockDim.x) out[j] = gs[j];
 }
 
-// g_j = the blocks' partials in a fixed order: slice t of 64 sums (FP32) the
-// partials of blocks t, t + 64, ..., then the 64 slice sums are added in
+// g_j = the blocks' partials in a fixed order: slice t of 32 sums (FP32) the
+// partials of blocks t, t + 32, ..., then the 32 slice sums are added in
 // order (FP64); then Adam (Kingma & Ba 2015) on x_j, clamped at zero.
-// Grid: n_cols / 16, 1024 threads (16 spots x 64 slices).
-__global__ void __launch_bounds__(1024) k_reduce_adam(const float* __restrict__ partial, int nb, int n_cols,
+// Grid: n_cols / 16, 512 threads (16 spots x 32 slices).
+__global__ void __launch_bounds__(512) k_reduce_adam(const float* __restrict__ partial, int nb, int n_cols,
                                                       float* __restrict__ x, float* __restrict__ m,
                                                       float* __restrict__ v, float step, float c1, float c2,
                                                       float eps)
 {
-    __shared__ float red[64][17];
+    __shared__ float red[32][17];
     const int c = threadIdx.x & 15, sl = threadIdx.x >> 4;
     const int j = blockIdx.x * 16 + c;
     float a = 0.0f;
     if (j < n_cols) {
-#pragma unroll 4
-        for (int b = sl; b < nb; b += 64) a += __ldcs(partial + (long long)b * n_cols + j);
+#pragma unroll 8
+        for (int b = sl; b < nb; b += 32) a += __ldcs(partial + (long long)b * n_cols + j);
     }
     red[sl][c] = a;
     __syncthreads();
     if (sl != 0 || j >= n_cols) return;
     double acc = 0.0;
 #pragma unroll 8
-    for (int k = 0; k < 64; ++k) acc += (double)red[k][c];
+    for (int k = 0; k < 32; ++k) acc += (double)red[k][c];
     const float g = (float)acc;
     const float mj = fmaf(0.9f, m[j], 0.1f * g), vj = fmaf(0.999f, v[j], 0.001f * g * g);
     m[j] = mj;
@@ -507,7 +542,7 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
         bwd<<<(unsigned)nb, 256, smem, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.dose_tr, w.tr_cls, q, cur, nxt, S,
                                              w.hist, it, w.partial);
         const double t = it + 1;
-        k_reduce_adam<<<(unsigned)((n_cols + 15) / 16), 1024, 0, st>>>(
+        k_reduce_adam<<<(unsigned)((n_cols + 15) / 16), 512, 0, st>>>(
             w.partial, nb, n_cols, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
             (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
     }
