@@ -278,17 +278,20 @@ __global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ 
 {
     extern __shared__ float gs[];
     __shared__ int s_star;
+    __shared__ double s_f[kMaxScen];
     __shared__ float s_ri[kBwdRows];
     __shared__ long long s_b[kBwdRows], s_e[kBwdRows];
+    if (threadIdx.x < n_scen) s_f[threadIdx.x] = fsum_cur[threadIdx.x];
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) gs[j] = 0.0f;
+    __syncthreads();
     if (threadIdx.x == 0) {
         int w = 0;
         for (int k = 1; k < n_scen; ++k)
-            if (fsum_cur[k] > fsum_cur[w]) w = k;
+            if (s_f[k] > s_f[w]) w = k;
         s_star = w;
-        if (blockIdx.x == 0 && hist) hist[it] = (float)fsum_cur[w];
+        if (blockIdx.x == 0 && hist) hist[it] = (float)s_f[w];
     }
     if (blockIdx.x == 0 && threadIdx.x < n_scen) fsum_next[threadIdx.x] = 0.0;
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) gs[j] = 0.0f;
     __syncthreads();
     const int s = s_star;
     // the block's rows: f'(d_i) and entry range, loaded together
