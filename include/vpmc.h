@@ -321,7 +321,7 @@ typedef struct {
 } vpmc_opt_params;
 
 /* mats: n_scen CSR (device buffers, e.g. from vpmc_influence_matrix), all of
- * the same shape, at most 58,000 columns and 2^31 - 1 rows; row_ptr must be
+ * the same shape, at most 28,000 columns and 2^31 - 1 rows; row_ptr must be
  * non-decreasing from 0 to nnz (not checked); entries whose column lies
  * outside [0, n_cols) are skipped.  voxel_class_dev: uint8 [n_rows], device
  * (1 target, 2 ring, other values ignored; at least one target voxel).
@@ -333,7 +333,8 @@ typedef struct {
  * Only target and ring voxels enter the objective, so the call first copies
  * their rows of every matrix into a compact form (scratch of about 6 bytes
  * per such entry, allocated and freed by the call), then iterates on those.
- * Repeated calls with the same inputs give the same bits.  Synchronous. */
+ * The gradient is summed in 64-bit fixed point, so repeated calls with the
+ * same inputs give the same bits.  Synchronous. */
 vpmc_status vpmc_robust_optimize(const vpmc_csr* mats, int n_scen, const uint8_t* voxel_class_dev,
                                  const vpmc_opt_params* params, float* x_dev, float* history, float* ms,
                                  void* stream);

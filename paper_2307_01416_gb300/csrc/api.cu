@@ -1507,7 +1507,7 @@ vpmc_status check_opt_inputs(const vpmc_csr* mats, int n_scen, const uint8_t* cl
         in->val.push_back(mats[s].val);
     }
     if (in->n_rows <= 0 || mats[0].n_cols <= 0) return fail(VPMC_ERR_ARG, "empty matrices");
-    if (mats[0].n_cols > 58000) return fail(VPMC_ERR_ARG, "%lld columns: at most 58,000", (long long)mats[0].n_cols);
+    if (mats[0].n_cols > 28000) return fail(VPMC_ERR_ARG, "%lld columns: at most 28,000", (long long)mats[0].n_cols);
     if (in->n_rows > INT32_MAX) return fail(VPMC_ERR_ARG, "more than 2^31 - 1 rows");
     std::vector<unsigned char>& h = in->cls;
     h.resize((size_t)in->n_rows);

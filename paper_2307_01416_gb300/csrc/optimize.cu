@@ -11,17 +11,18 @@
 // columns and two of values per lane and step).  Each iteration then runs,
 // with no host synchronisation:
 //   k_fwd         d_s = A_s x on the compact rows of every scenario (a warp
-//                 per row) and the scenario's objective f_s (FP64 block sums);
-//   k_bwd_rows    s* = first s with the largest f_s (every block), recorded;
-//                 each block adds f'(d_i) A_s*,i. over its 8 rows, in row
-//                 order, into a shared-memory gradient (rows with f'(d_i) = 0
-//                 are skipped) and stores it as the block's partial;
-//   k_reduce_adam g_j = the partials summed in a fixed order, then the Adam
-//                 step on x_j, clamped at zero.
-// Every sum has a fixed order, so repeated calls give the same bits.  The
-// iteration is HBM-bound.  Full-matrix products (dose of the weights, target
-// indices over all voxels) use k_spmv_obj: a sub-warp per row of the
-// caller's CSR.
+//                 per row), the scenario's objective f_s (FP64 block sums) and
+//                 max_i |f'(d_i)|;
+//   k_bwd_fixed   s* = first s with the largest f_s (every block), recorded;
+//                 g = A_s*^T f'(d_s*) over the compact rows (a warp per row)
+//                 as 64-bit fixed-point sums: shared-memory atomics per
+//                 block, one global atomic per spot and block;
+//   k_adam_fixed  g_j back to floating point, then the Adam step on x_j,
+//                 clamped at zero.
+// Integer sums do not depend on the order of the adds, so repeated calls
+// give the same bits.  The iteration is HBM-bound.  Full-matrix products
+// (dose of the weights, target indices over all voxels) use k_spmv_obj: a
+// sub-warp per row of the caller's CSR.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -184,16 +185,17 @@ __global__ void k_tr_len(const Csr* __restrict__ mats, const int* __restrict__ t
 __global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats, const int* __restrict__ tr_rows,
                                                    int n_tr, int n_cols, const long long* __restrict__ crp,
                                                    unsigned short* __restrict__ ccol, float* __restrict__ cval,
-                                                   int* __restrict__ unordered)
+                                                   int* __restrict__ unordered, unsigned* __restrict__ max_abs)
 {
     const int s = blockIdx.y, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n_tr) return;
+    if (i >= n_tr) return;                            // warp-uniform
     const Csr A = mats[s];
     const int row = __ldg(tr_rows + i);
     const long long b = __ldg(A.row_ptr + row), len = __ldg(A.row_ptr + row + 1) - b;
     const long long dst = crp[(long long)s * (n_tr + 1) + i];
     const long long plen = crp[(long long)s * (n_tr + 1) + i + 1] - dst;
+    unsigned amax = 0u;                               // |a| as bits: non-negative floats order as integers
     for (long long k = lane; k < plen; k += 32) {
         int j = 0;
         float v = 0.0f;
@@ -207,18 +209,24 @@ __global__ void __launch_bounds__(256) k_tr_gather(const Csr* __restrict__ mats,
         }
         ccol[dst + k] = (unsigned short)j;
         cval[dst + k] = v;
+        amax = max(amax, __float_as_uint(fabsf(v)));
     }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) amax = max(amax, __shfl_xor_sync(kFullMask, amax, o));
+    if (lane == 0 && amax) atomicMax(max_abs + s, amax);
 }
 
-// d_s on the compact rows and f_s; grid (rows / 8, scenarios), 256 threads.
+// d_s on the compact rows, f_s and max_i |f'(d_i)| (as float bits); grid
+// (rows / 8, scenarios), 256 threads.
 __global__ void __launch_bounds__(256) k_fwd(const long long* __restrict__ crp, const unsigned short* __restrict__ ccol,
                                              const float* __restrict__ cval, int n_tr, const float* __restrict__ x,
                                              const unsigned char* __restrict__ tr_cls, ObjParams q,
-                                             float* __restrict__ dose_tr, double* __restrict__ fsum)
+                                             float* __restrict__ dose_tr, double* __restrict__ fsum,
+                                             unsigned* __restrict__ max_r)
 {
     const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.x * 8 + warp;
-    float f = 0.0f;
+    float f = 0.0f, rabs = 0.0f;
     if (i < n_tr) {                                   // warp-uniform
         const long long b = __ldg(crp + (long long)s * (n_tr + 1) + i);
         const long long e = __ldg(crp + (long long)s * (n_tr + 1) + i + 1);
@@ -241,152 +249,132 @@ __global__ void __launch_bounds__(256) k_fwd(const long long* __restrict__ crp, 
         for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
         if (lane == 0) {
             dose_tr[(long long)s * n_tr + i] = acc;
-            f = obj_term(acc, __ldg(tr_cls + i), q);
+            const unsigned char c = __ldg(tr_cls + i);
+            f = obj_term(acc, c, q);
+            rabs = fabsf(obj_grad(acc, c, q));
         }
     }
-    __shared__ float part[8];
-    if (lane == 0) part[warp] = f;
+    __shared__ float part[8], pmax[8];
+    if (lane == 0) {
+        part[warp] = f;
+        pmax[warp] = rabs;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float t = 0.0f;
+        float t = 0.0f, mx = 0.0f;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) t += part[w];
+        for (int w = 0; w < 8; ++w) {
+            t += part[w];
+            mx = fmaxf(mx, pmax[w]);
+        }
         if (t != 0.0f) atomicAdd(fsum + s, (double)t);
+        if (mx > 0.0f) atomicMax(max_r + s, __float_as_uint(mx));
     }
 }
 
-constexpr int kBwdRows = 8;                     // compact rows per gradient block
-
-// Worst scenario and the blocks' gradient partials: each block adds
-// f'(d_i) A_s*,ij over its rows, one row after the other (a barrier after
-// each), into a shared-memory gradient.  Pads and zero values add nothing
-// and are skipped.  kAtomic = false when every row's spots are strictly
-// increasing: a row's adds then touch distinct spots and are plain
-// read-add-writes; kAtomic = true for rows that may repeat a spot (shared
-// atomics; the repeats of a row add in atomic order).  Either way the sum
-// order of every spot is the row order.  Grid: compact rows / kBwdRows, 256
-// threads, n_cols floats of shared memory.
-template <bool kAtomic>
-__global__ void __launch_bounds__(256) k_bwd_rows(const long long* __restrict__ crp,
-                                                  const unsigned short* __restrict__ ccol,
-                                                  const float* __restrict__ cval, int n_tr, int n_cols,
-                                                  const float* __restrict__ dose_tr,
-                                                  const unsigned char* __restrict__ tr_cls, ObjParams q,
-                                                  const double* __restrict__ fsum_cur, double* __restrict__ fsum_next,
-                                                  int n_scen, float* __restrict__ hist, int it,
-                                                  float* __restrict__ partial)
+// p 2^k as a 64-bit integer, truncated toward zero (p a binary32 with
+// |p| 2^k < 2^63; zero and subnormal p give 0).  Integer operations only.
+__device__ __forceinline__ long long to_fixed_pow2(float p, int k)
 {
-    extern __shared__ float gs[];
-    __shared__ int s_star;
+    const unsigned bits = __float_as_uint(p);
+    const int ex = (int)((bits >> 23) & 0xffu);
+    if (ex == 0) return 0;
+    const long long mant = (long long)((bits & 0x7fffffu) | 0x800000u);
+    const int sh = ex - 150 + k;                      // p 2^k = mant 2^sh
+    long long v;
+    if (sh >= 0)
+        v = mant << sh;
+    else
+        v = sh > -24 ? (mant >> -sh) : 0;
+    return (bits >> 31) ? -v : v;
+}
+
+// Worst scenario and the gradient in 64-bit fixed point.  The scale 2^k,
+// k = 62 - ceil(log2 B) with B = max_i |f'(d_i)| x (compact rows) x max |a|
+// of the worst scenario, bounds every partial sum by 2^62 (the row count is
+// replaced by the scenario's entry count when a row may repeat a spot).  Each warp takes
+// whole rows (rows with f'(d_i) = 0 add nothing and are skipped), adds
+// a f'(d_i) 2^k to a shared-memory copy of g per block; the block adds its
+// copy to g with one atomic per spot.  Grid: number of SMs, 1024 threads,
+// n_cols x 8 bytes of shared memory.
+__global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict__ crp,
+                                                    const unsigned short* __restrict__ ccol,
+                                                    const float* __restrict__ cval, int n_tr, int n_cols,
+                                                    const float* __restrict__ dose_tr,
+                                                    const unsigned char* __restrict__ tr_cls, ObjParams q,
+                                                    const double* __restrict__ fsum_cur,
+                                                    const unsigned* __restrict__ max_r_cur,
+                                                    double* __restrict__ fsum_next, unsigned* __restrict__ max_r_next,
+                                                    const unsigned* __restrict__ max_abs,
+                                                    const float* __restrict__ count_bound, int n_scen,
+                                                    float* __restrict__ hist, int it,
+                                                    unsigned long long* __restrict__ g, int* __restrict__ g_shift)
+{
+    extern __shared__ unsigned long long gs[];
     __shared__ double s_f[kMaxScen];
-    __shared__ float s_ri[kBwdRows];
-    __shared__ long long s_b[kBwdRows], s_e[kBwdRows];
+    __shared__ int s_star, s_k;
     if (threadIdx.x < n_scen) s_f[threadIdx.x] = fsum_cur[threadIdx.x];
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) gs[j] = 0.0f;
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) gs[j] = 0ull;
     __syncthreads();
     if (threadIdx.x == 0) {
         int w = 0;
         for (int k = 1; k < n_scen; ++k)
             if (s_f[k] > s_f[w]) w = k;
+        const float bound = __uint_as_float(max_r_cur[w]) * count_bound[w] * __uint_as_float(max_abs[w]);
+        int e = 129;                                  // an overflowed bound: above any binary32
+        if (bound <= 3.4028235e38f) frexpf(bound, &e);  // bound < 2^e
         s_star = w;
-        if (blockIdx.x == 0 && hist) hist[it] = (float)s_f[w];
-    }
-    if (blockIdx.x == 0 && threadIdx.x < n_scen) fsum_next[threadIdx.x] = 0.0;
-    __syncthreads();
-    const int s = s_star;
-    // the block's rows: f'(d_i) and entry range, loaded together
-    if (threadIdx.x < kBwdRows) {
-        const int i = blockIdx.x * kBwdRows + threadIdx.x;
-        float ri = 0.0f;
-        long long b = 0, e = 0;
-        if (i < n_tr) {
-            ri = obj_grad(__ldg(dose_tr + (long long)s * n_tr + i), __ldg(tr_cls + i), q);
-            b = __ldg(crp + (long long)s * (n_tr + 1) + i);
-            e = __ldg(crp + (long long)s * (n_tr + 1) + i + 1);
+        s_k = bound > 0.0f ? 62 - e : 0;
+        if (blockIdx.x == 0) {
+            if (hist) hist[it] = (float)s_f[w];
+            *g_shift = s_k;
         }
-        s_ri[threadIdx.x] = ri;
-        s_b[threadIdx.x] = b;
-        s_e[threadIdx.x] = ri != 0.0f ? e : b;          // rows with f' = 0 add nothing: empty
     }
     __syncthreads();
-    auto add = [&](unsigned j, float a, float ri) {
-        if (a != 0.0f) {
-            if (kAtomic)
-                atomicAdd(gs + j, a * ri);
-            else
-                gs[j] = fmaf(a, ri, gs[j]);
-        }
-    };
-    auto add8 = [&](const uint4& c, const float4& v0, const float4& v1, float ri) {
-        add(c.x & 0xffffu, v0.x, ri);
-        add(c.x >> 16, v0.y, ri);
-        add(c.y & 0xffffu, v0.z, ri);
-        add(c.y >> 16, v0.w, ri);
-        add(c.z & 0xffffu, v1.x, ri);
-        add(c.z >> 16, v1.y, ri);
-        add(c.w & 0xffffu, v1.z, ri);
-        add(c.w >> 16, v1.w, ri);
-    };
-    const long long lane8 = (long long)threadIdx.x * kPadRow, stride = (long long)blockDim.x * kPadRow;
-    // first step of row 0 in registers; each iteration loads the next row's
-    // first step before adding the current one
-    uint4 c = make_uint4(0u, 0u, 0u, 0u);
-    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-    if (s_b[0] + lane8 < s_e[0]) {
-        c = __ldcs(reinterpret_cast<const uint4*>(ccol + s_b[0] + lane8));
-        v0 = __ldcs(reinterpret_cast<const float4*>(cval + s_b[0] + lane8));
-        v1 = __ldcs(reinterpret_cast<const float4*>(cval + s_b[0] + lane8 + 4));
+    if (blockIdx.x == 0 && threadIdx.x < n_scen) {
+        fsum_next[threadIdx.x] = 0.0;
+        max_r_next[threadIdx.x] = 0u;
     }
-    for (int r = 0; r < kBwdRows; ++r) {
-        uint4 cn = make_uint4(0u, 0u, 0u, 0u);
-        float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
-        if (r + 1 < kBwdRows && s_b[r + 1] + lane8 < s_e[r + 1]) {
-            cn = __ldcs(reinterpret_cast<const uint4*>(ccol + s_b[r + 1] + lane8));
-            w0 = __ldcs(reinterpret_cast<const float4*>(cval + s_b[r + 1] + lane8));
-            w1 = __ldcs(reinterpret_cast<const float4*>(cval + s_b[r + 1] + lane8 + 4));
+    const int s = s_star, kq = s_k, lane = threadIdx.x & 31;
+    const long long* rp = crp + (long long)s * (n_tr + 1);
+    const float* d = dose_tr + (long long)s * n_tr;
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n_tr;
+         i += gridDim.x * (blockDim.x >> 5)) {
+        const float ri = obj_grad(__ldg(d + i), __ldg(tr_cls + i), q);
+        if (ri == 0.0f) continue;                     // warp-uniform
+        const long long b = __ldg(rp + i), e = __ldg(rp + i + 1);
+#pragma unroll 2
+        for (long long k = b + lane * kPadRow; k < e; k += 32 * kPadRow) {
+            const uint4 c = __ldcs(reinterpret_cast<const uint4*>(ccol + k));
+            const float4 v0 = __ldcs(reinterpret_cast<const float4*>(cval + k));
+            const float4 v1 = __ldcs(reinterpret_cast<const float4*>(cval + k + 4));
+            const unsigned js[8] = {c.x & 0xffffu, c.x >> 16, c.y & 0xffffu, c.y >> 16,
+                                    c.z & 0xffffu, c.z >> 16, c.w & 0xffffu, c.w >> 16};
+            const float as[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const long long fx = to_fixed_pow2(as[t] * ri, kq);
+                if (fx != 0) atomicAdd(gs + js[t], (unsigned long long)fx);
+            }
         }
-        const float ri = s_ri[r];
-        const long long b = s_b[r], e = s_e[r];
-        if (b + lane8 < e) add8(c, v0, v1, ri);
-        for (long long k = b + lane8 + stride; k < e; k += stride) {          // rows longer than one step
-            add8(__ldcs(reinterpret_cast<const uint4*>(ccol + k)), __ldcs(reinterpret_cast<const float4*>(cval + k)),
-                 __ldcs(reinterpret_cast<const float4*>(cval + k + 4)), ri);
-        }
-        if (b < e) __syncthreads();                       // block-uniform
-        c = cn;
-        v0 = w0;
-        v1 = w1;
     }
     __syncthreads();
-    float* out = partial + (long long)blockIdx.x * n_cols;
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) out[j] = gs[j];
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x)
+        if (gs[j] != 0ull) atomicAdd(g + j, gs[j]);
 }
 
-// g_j = the blocks' partials in a fixed order: slice t of 32 sums (FP32) the
-// partials of blocks t, t + 32, ..., then the 32 slice sums are added in
-// order (FP64); then Adam (Kingma & Ba 2015) on x_j, clamped at zero.
-// Grid: n_cols / 16, 512 threads (16 spots x 32 slices).
-__global__ void __launch_bounds__(512) k_reduce_adam(const float* __restrict__ partial, int nb, int n_cols,
-                                                      float* __restrict__ x, float* __restrict__ m,
-                                                      float* __restrict__ v, float step, float c1, float c2,
-                                                      float eps)
+// g_j = (fixed-point sum) 2^-k, reset for the next iteration, then Adam
+// (Kingma & Ba 2015) on x_j, clamped at zero.
+__global__ void k_adam_fixed(unsigned long long* __restrict__ g, const int* __restrict__ g_shift, int n_cols,
+                             float* __restrict__ x, float* __restrict__ m, float* __restrict__ v, float step,
+                             float c1, float c2, float eps)
 {
-    __shared__ float red[32][17];
-    const int c = threadIdx.x & 15, sl = threadIdx.x >> 4;
-    const int j = blockIdx.x * 16 + c;
-    float a = 0.0f;
-    if (j < n_cols) {
-#pragma unroll 8
-        for (int b = sl; b < nb; b += 32) a += __ldcs(partial + (long long)b * n_cols + j);
-    }
-    red[sl][c] = a;
-    __syncthreads();
-    if (sl != 0 || j >= n_cols) return;
-    double acc = 0.0;
-#pragma unroll 8
-    for (int k = 0; k < 32; ++k) acc += (double)red[k][c];
-    const float g = (float)acc;
-    const float mj = fmaf(0.9f, m[j], 0.1f * g), vj = fmaf(0.999f, v[j], 0.001f * g * g);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_cols) return;
+    const long long gi = (long long)g[j];
+    g[j] = 0ull;
+    const float gj = (float)ldexp((double)gi, -*g_shift);
+    const float mj = fmaf(0.9f, m[j], 0.1f * gj), vj = fmaf(0.999f, v[j], 0.001f * gj * gj);
     m[j] = mj;
     v[j] = vj;
     x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
@@ -436,7 +424,11 @@ struct RobustWs {
     long long* crp = nullptr;
     unsigned short* ccol = nullptr;
     float* cval = nullptr;
-    float* partial = nullptr;                   // [gradient blocks x n_cols]
+    unsigned long long* g = nullptr;            // [n_cols] fixed-point gradient
+    int* g_shift = nullptr;
+    unsigned* max_abs = nullptr;                // [S] max |a| (float bits)
+    unsigned* max_r = nullptr;                  // [2 x S] max |f'(d)| (float bits)
+    float* count_bound = nullptr;               // [S] entries of a spot over the compact rows, at most
     int* unordered = nullptr;
     float* dose_tr = nullptr;
     double* fsum = nullptr;                     // [2 x S]: this iteration's sums, the next one's
@@ -446,7 +438,9 @@ struct RobustWs {
     ~RobustWs()
     {
         cudaFree(mats); cudaFree(tr_rows); cudaFree(tr_cls); cudaFree(len); cudaFree(crp); cudaFree(ccol);
-        cudaFree(cval); cudaFree(partial); cudaFree(unordered); cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v);
+        cudaFree(cval); cudaFree(g); cudaFree(g_shift); cudaFree(max_abs); cudaFree(max_r); cudaFree(count_bound);
+        cudaFree(unordered);
+        cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v);
         cudaFree(hist);
     }
 };
@@ -464,7 +458,7 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     RobustWs w;
     cudaError_t e;
 #define OPT_TRY(expr) do { if ((e = (expr)) != cudaSuccess) return e; } while (0)
-    if ((size_t)n_cols * sizeof(float) > kBwdSmemMax) return cudaErrorInvalidValue;
+    if ((size_t)n_cols * sizeof(unsigned long long) > kBwdSmemMax) return cudaErrorInvalidValue;
     // target and ring rows, in voxel order
     std::vector<int> rows;
     std::vector<unsigned char> rcls;
@@ -512,41 +506,58 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     OPT_TRY(dalloc(&w.ccol, (size_t)total_c));
     OPT_TRY(dalloc(&w.cval, (size_t)total_c));
     OPT_TRY(dalloc(&w.unordered, 1));
+    OPT_TRY(dalloc(&w.max_abs, S));
     OPT_TRY(cudaMemsetAsync(w.unordered, 0, sizeof(int), st));
-    k_tr_gather<<<dim3((unsigned)((n_tr + 7) / 8), (unsigned)S), 256, 0, st>>>(w.mats, w.tr_rows, n_tr, n_cols,
-                                                                               w.crp, w.ccol, w.cval, w.unordered);
+    OPT_TRY(cudaMemsetAsync(w.max_abs, 0, sizeof(unsigned) * S, st));
+    k_tr_gather<<<dim3((unsigned)((n_tr + 7) / 8), (unsigned)S), 256, 0, st>>>(
+        w.mats, w.tr_rows, n_tr, n_cols, w.crp, w.ccol, w.cval, w.unordered, w.max_abs);
     OPT_TRY(cudaGetLastError());
     int unordered = 0;
     OPT_TRY(cudaMemcpyAsync(&unordered, w.unordered, sizeof(int), cudaMemcpyDeviceToHost, st));
     OPT_TRY(cudaStreamSynchronize(st));
+    std::vector<float> cb(S);
+    for (int s = 0; s < S; ++s) {
+        long long nz = 0;
+        for (int i = 0; i < n_tr; ++i) nz += len[(size_t)s * n_tr + i];
+        cb[s] = (float)(unordered ? std::max<long long>(nz, 1) : n_tr);
+    }
+    OPT_TRY(dalloc(&w.count_bound, S));
+    OPT_TRY(cudaMemcpyAsync(w.count_bound, cb.data(), sizeof(float) * S, cudaMemcpyHostToDevice, st));
     // iteration state
-    const int nb = (n_tr + kBwdRows - 1) / kBwdRows;
-    OPT_TRY(dalloc(&w.partial, (size_t)nb * n_cols));
+    OPT_TRY(dalloc(&w.g, (size_t)n_cols));
+    OPT_TRY(dalloc(&w.g_shift, 1));
+    OPT_TRY(dalloc(&w.max_r, (size_t)2 * S));
     OPT_TRY(dalloc(&w.dose_tr, (size_t)S * n_tr));
     OPT_TRY(dalloc(&w.fsum, (size_t)2 * S));
     OPT_TRY(dalloc(&w.m, (size_t)n_cols));
     OPT_TRY(dalloc(&w.v, (size_t)n_cols));
     OPT_TRY(dalloc(&w.hist, (size_t)std::max(spec.iterations, 1)));
+    OPT_TRY(cudaMemsetAsync(w.g, 0, sizeof(unsigned long long) * n_cols, st));
+    OPT_TRY(cudaMemsetAsync(w.max_r, 0, sizeof(unsigned) * 2 * S, st));
     OPT_TRY(cudaMemsetAsync(w.fsum, 0, sizeof(double) * 2 * S, st));
     OPT_TRY(cudaMemsetAsync(w.m, 0, sizeof(float) * n_cols, st));
     OPT_TRY(cudaMemsetAsync(w.v, 0, sizeof(float) * n_cols, st));
-    const int smem = (int)(sizeof(float) * n_cols);
-    auto* bwd = unordered ? k_bwd_rows<true> : k_bwd_rows<false>;
-    OPT_TRY(cudaFuncSetAttribute(bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem = (int)(sizeof(unsigned long long) * n_cols);
+    OPT_TRY(cudaFuncSetAttribute(k_bwd_fixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int dev = 0, nsm = 0;
+    OPT_TRY(cudaGetDevice(&dev));
+    OPT_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     OPT_TRY(cudaEventRecord(ev[1], st));
     const ObjParams q{spec.dp, spec.w_u, spec.w_o, spec.w_r, spec.over, spec.ring,
                       1.0f / (float)std::max<long long>(spec.n_target, 1),
                       1.0f / (float)std::max<long long>(spec.n_ring, 1)};
     const dim3 gf((unsigned)std::max((n_tr + 7) / 8, 1), (unsigned)S);
     for (int it = 0; it < spec.iterations; ++it) {
-        double* cur = w.fsum + (it & 1) * S;
-        double* nxt = w.fsum + ((it + 1) & 1) * S;
-        k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, cur);
-        bwd<<<(unsigned)nb, 256, smem, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.dose_tr, w.tr_cls, q, cur, nxt, S,
-                                             w.hist, it, w.partial);
+        const int cu = it & 1, nx = (it + 1) & 1;
+        k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, w.fsum + cu * S,
+                                  w.max_r + cu * S);
+        k_bwd_fixed<<<(unsigned)nsm, 1024, smem, st>>>(w.crp, w.ccol, w.cval, n_tr, n_cols, w.dose_tr, w.tr_cls, q,
+                                                       w.fsum + cu * S, w.max_r + cu * S, w.fsum + nx * S,
+                                                       w.max_r + nx * S, w.max_abs, w.count_bound, S, w.hist, it, w.g,
+                                                       w.g_shift);
         const double t = it + 1;
-        k_reduce_adam<<<(unsigned)((n_cols + 15) / 16), 512, 0, st>>>(
-            w.partial, nb, n_cols, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
+        k_adam_fixed<<<(unsigned)((n_cols + 255) / 256), 256, 0, st>>>(
+            w.g, w.g_shift, n_cols, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
             (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
     }
     OPT_TRY(cudaGetLastError());
