@@ -292,11 +292,14 @@ __device__ __forceinline__ long long to_fixed_pow2(float p, int k)
 // Worst scenario and the gradient in 64-bit fixed point.  The scale 2^k,
 // k = 62 - ceil(log2 B) with B = max_i |f'(d_i)| x (compact rows) x max |a|
 // of the worst scenario, bounds every partial sum by 2^62 (the row count is
-// replaced by the scenario's entry count when a row may repeat a spot).  Each warp takes
-// whole rows (rows with f'(d_i) = 0 add nothing and are skipped), adds
-// a f'(d_i) 2^k to a shared-memory copy of g per block; the block adds its
-// copy to g with one atomic per spot.  Grid: number of SMs, 1024 threads,
-// n_cols x 8 bytes of shared memory.
+// replaced by the scenario's entry count when a row may repeat a spot).
+// Each warp takes whole rows (consecutive rows go to different blocks; rows
+// with f'(d_i) = 0 add nothing and are skipped) and adds a f'(d_i) 2^k to a
+// shared-memory copy of g per block, held as two 32-bit words per spot: the
+// low word by a native 32-bit atomic whose returned old value gives the
+// carry, the high word by a second one (exact, whatever the order).  The
+// block adds its copy to g with one 64-bit atomic per spot.  Grid: number of
+// SMs, 1024 threads, n_cols x 8 bytes of shared memory.
 __global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict__ crp,
                                                     const unsigned short* __restrict__ ccol,
                                                     const float* __restrict__ cval, int n_tr, int n_cols,
@@ -310,11 +313,13 @@ __global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict_
                                                     float* __restrict__ hist, int it,
                                                     unsigned long long* __restrict__ g, int* __restrict__ g_shift)
 {
-    extern __shared__ unsigned long long gs[];
+    extern __shared__ unsigned gsw[];
+    unsigned* lo = gsw;
+    unsigned* hi = gsw + n_cols;
     __shared__ double s_f[kMaxScen];
     __shared__ int s_star, s_k;
     if (threadIdx.x < n_scen) s_f[threadIdx.x] = fsum_cur[threadIdx.x];
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) gs[j] = 0ull;
+    for (int j = threadIdx.x; j < 2 * n_cols; j += blockDim.x) gsw[j] = 0u;
     __syncthreads();
     if (threadIdx.x == 0) {
         int w = 0;
@@ -338,8 +343,8 @@ __global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict_
     const int s = s_star, kq = s_k, lane = threadIdx.x & 31;
     const long long* rp = crp + (long long)s * (n_tr + 1);
     const float* d = dose_tr + (long long)s * n_tr;
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n_tr;
-         i += gridDim.x * (blockDim.x >> 5)) {
+    const int warps = blockDim.x >> 5;
+    for (int i = blockIdx.x + gridDim.x * (threadIdx.x >> 5); i < n_tr; i += gridDim.x * warps) {
         const float ri = obj_grad(__ldg(d + i), __ldg(tr_cls + i), q);
         if (ri == 0.0f) continue;                     // warp-uniform
         const long long b = __ldg(rp + i), e = __ldg(rp + i + 1);
@@ -353,14 +358,21 @@ __global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict_
             const float as[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const long long fx = to_fixed_pow2(as[t] * ri, kq);
-                if (fx != 0) atomicAdd(gs + js[t], (unsigned long long)fx);
+                const unsigned long long fx = (unsigned long long)to_fixed_pow2(as[t] * ri, kq);
+                if (fx != 0ull) {
+                    const unsigned l = (unsigned)fx;
+                    const unsigned old = atomicAdd(lo + js[t], l);
+                    const unsigned h = (unsigned)(fx >> 32) + (old + l < old ? 1u : 0u);
+                    if (h) atomicAdd(hi + js[t], h);
+                }
             }
         }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x)
-        if (gs[j] != 0ull) atomicAdd(g + j, gs[j]);
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) {
+        const unsigned long long t = ((unsigned long long)hi[j] << 32) | lo[j];
+        if (t != 0ull) atomicAdd(g + j, t);
+    }
 }
 
 // g_j = (fixed-point sum) 2^-k, reset for the next iteration, then Adam
