@@ -534,7 +534,7 @@ def optimizer_leg(pb, target, mats, args):
             "worst_V100": float(idx[:, 0].min()), "worst_Dmin": float(idx[:, 1].min()),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "bytes_per_iteration": b, "traffic": None,
-                         "kernel": "k_fwd (13 scenarios) + k_bwd_rows + k_reduce_adam",
+                         "kernel": "k_fwd (13 scenarios) + k_bwd_fixed + k_adam_fixed",
                          "peak_note": "hbm_gbs of MEASURED_PEAKS.json (STREAM-style copy)"},
             "note": "per iteration: 13 products on the compact target/ring rows (built once per call, "
                     "setup_ms), worst-case selection, the transposed product and the Adam step, all on the "
