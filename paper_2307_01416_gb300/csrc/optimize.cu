@@ -289,28 +289,24 @@ __device__ __forceinline__ long long to_fixed_pow2(float p, int k)
     return (bits >> 31) ? -v : v;
 }
 
-// A piece of one compact row: entries [b, b + n), n a multiple of 8 and at
-// most kRowChunk; i is the compact row.  Long rows are split so that the
-// gradient's warps get pieces of similar length.
-struct RowChunk {
-    long long b;
-    int n, i;
-};
+// Rows are cut into pieces of at most kRowChunk entries so that the
+// gradient's warps get work of similar length: piece c of the worst
+// scenario is row c / per_row, entries [k kRowChunk, (k + 1) kRowChunk) of it
+// with k = c % per_row (empty when the row is shorter).
 constexpr int kRowChunk = 1024;
 
 // Worst scenario and the gradient in 64-bit fixed point.  The scale 2^k,
 // k = 62 - ceil(log2 B) with B = max_i |f'(d_i)| x (compact rows) x max |a|
 // of the worst scenario, bounds every partial sum by 2^62 (the row count is
 // replaced by the scenario's entry count when a row may repeat a spot).
-// Each warp takes row chunks (consecutive chunks go to different blocks;
+// Each warp takes row pieces (consecutive pieces go to different blocks;
 // rows with f'(d_i) = 0 add nothing and are skipped) and adds a f'(d_i) 2^k to a
 // shared-memory copy of g per block, held as two 32-bit words per spot: the
 // low word by a native 32-bit atomic whose returned old value gives the
 // carry, the high word by a second one (exact, whatever the order).  The
 // block adds its copy to g with one 64-bit atomic per spot.  Grid: number of
 // SMs, 1024 threads, n_cols x 8 bytes of shared memory.
-__global__ void __launch_bounds__(1024) k_bwd_fixed(const RowChunk* __restrict__ chunks,
-                                                    const long long* __restrict__ chunk_off,
+__global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict__ crp, int per_row,
                                                     const unsigned short* __restrict__ ccol,
                                                     const float* __restrict__ cval, int n_tr, int n_cols,
                                                     const float* __restrict__ dose_tr,
@@ -353,13 +349,17 @@ __global__ void __launch_bounds__(1024) k_bwd_fixed(const RowChunk* __restrict__
     const int s = s_star, kq = s_k, lane = threadIdx.x & 31;
     const float* d = dose_tr + (long long)s * n_tr;
     const int warps = blockDim.x >> 5;
-    const long long c0 = __ldg(chunk_off + s), nc = __ldg(chunk_off + s + 1) - c0;
+    const long long* rp = crp + (long long)s * (n_tr + 1);
+    const long long nc = (long long)n_tr * per_row;
     for (long long ci = blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5); ci < nc;
          ci += (long long)gridDim.x * warps) {
-        const RowChunk ch = chunks[c0 + ci];
-        const float ri = obj_grad(__ldg(d + ch.i), __ldg(tr_cls + ch.i), q);
+        const int i = (int)(ci / per_row);
+        const long long rb = __ldg(rp + i), re = __ldg(rp + i + 1);
+        const long long b = rb + (ci - (long long)i * per_row) * kRowChunk;
+        if (b >= re) continue;                        // warp-uniform: the row is shorter
+        const float ri = obj_grad(__ldg(d + i), __ldg(tr_cls + i), q);
         if (ri == 0.0f) continue;                     // warp-uniform
-        const long long b = ch.b, e = ch.b + ch.n;
+        const long long e = min(b + kRowChunk, re);
 #pragma unroll 2
         for (long long k = b + lane * kPadRow; k < e; k += 32 * kPadRow) {
             const uint4 c = __ldcs(reinterpret_cast<const uint4*>(ccol + k));
@@ -448,8 +448,6 @@ struct RobustWs {
     long long* crp = nullptr;
     unsigned short* ccol = nullptr;
     float* cval = nullptr;
-    RowChunk* chunks = nullptr;                 // every scenario's row chunks
-    long long* chunk_off = nullptr;             // [S + 1]
     unsigned long long* g = nullptr;            // [n_cols] fixed-point gradient
     int* g_shift = nullptr;
     unsigned* max_abs = nullptr;                // [S] max |a| (float bits)
@@ -464,7 +462,7 @@ struct RobustWs {
     ~RobustWs()
     {
         cudaFree(mats); cudaFree(tr_rows); cudaFree(tr_cls); cudaFree(len); cudaFree(crp); cudaFree(ccol);
-        cudaFree(cval); cudaFree(chunks); cudaFree(chunk_off); cudaFree(g); cudaFree(g_shift); cudaFree(max_abs); cudaFree(max_r); cudaFree(count_bound);
+        cudaFree(cval); cudaFree(g); cudaFree(g_shift); cudaFree(max_abs); cudaFree(max_r); cudaFree(count_bound);
         cudaFree(unordered);
         cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v);
         cudaFree(hist);
@@ -529,22 +527,11 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     }
     OPT_TRY(dalloc(&w.crp, crp.size()));
     OPT_TRY(cudaMemcpyAsync(w.crp, crp.data(), sizeof(long long) * crp.size(), cudaMemcpyHostToDevice, st));
-    std::vector<RowChunk> chunks;
-    std::vector<long long> chunk_off(S + 1, 0);
-    for (int s = 0; s < S; ++s) {
-        chunk_off[s] = (long long)chunks.size();
-        for (int i = 0; i < n_tr; ++i) {
-            const long long b = crp[(size_t)s * (n_tr + 1) + i], e = crp[(size_t)s * (n_tr + 1) + i + 1];
-            for (long long k = b; k < e; k += kRowChunk)
-                chunks.push_back(RowChunk{k, (int)std::min<long long>(kRowChunk, e - k), i});
-        }
-    }
-    chunk_off[S] = (long long)chunks.size();
-    OPT_TRY(dalloc(&w.chunks, chunks.size()));
-    OPT_TRY(dalloc(&w.chunk_off, chunk_off.size()));
-    OPT_TRY(cudaMemcpyAsync(w.chunks, chunks.data(), sizeof(RowChunk) * chunks.size(), cudaMemcpyHostToDevice, st));
-    OPT_TRY(cudaMemcpyAsync(w.chunk_off, chunk_off.data(), sizeof(long long) * chunk_off.size(),
-                            cudaMemcpyHostToDevice, st));
+    long long longest = 0;
+    for (int s = 0; s < S; ++s)
+        for (int i = 0; i < n_tr; ++i)
+            longest = std::max(longest, crp[(size_t)s * (n_tr + 1) + i + 1] - crp[(size_t)s * (n_tr + 1) + i]);
+    const int per_row = (int)std::max<long long>(1, (longest + kRowChunk - 1) / kRowChunk);
     OPT_TRY(dalloc(&w.ccol, (size_t)total_c));
     OPT_TRY(dalloc(&w.cval, (size_t)total_c));
     OPT_TRY(dalloc(&w.unordered, 1));
@@ -593,7 +580,7 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
         const int cu = it & 1, nx = (it + 1) & 1;
         k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, w.fsum + cu * S,
                                   w.max_r + cu * S);
-        k_bwd_fixed<<<(unsigned)nsm, 1024, smem, st>>>(w.chunks, w.chunk_off, w.ccol, w.cval, n_tr, n_cols, w.dose_tr,
+        k_bwd_fixed<<<(unsigned)nsm, 1024, smem, st>>>(w.crp, per_row, w.ccol, w.cval, n_tr, n_cols, w.dose_tr,
                                                        w.tr_cls, q,
                                                        w.fsum + cu * S, w.max_r + cu * S, w.fsum + nx * S,
                                                        w.max_r + nx * S, w.max_abs, w.count_bound, S, w.hist, it, w.g,
