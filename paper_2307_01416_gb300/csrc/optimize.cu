@@ -14,11 +14,11 @@
 //                 per row), the scenario's objective f_s (FP64 block sums) and
 //                 max_i |f'(d_i)|;
 //   k_bwd_fixed   s* = first s with the largest f_s (every block), recorded;
-//                 g = A_s*^T f'(d_s*) over the compact rows (a warp per row
-//                 piece) as 64-bit fixed-point sums: shared-memory atomics
-//                 per block, one global atomic per spot and block; the last
-//                 block converts g back to floating point and takes the Adam
-//                 step on x, clamped at zero.
+//                 g = A_s*^T f'(d_s*) over the compact rows (a warp per row)
+//                 as 64-bit fixed-point sums: shared-memory atomics per
+//                 block, one global atomic per spot and block;
+//   k_adam_fixed  g_j back to floating point, then the Adam step on x_j,
+//                 clamped at zero.
 // Integer sums do not depend on the order of the adds, so repeated calls
 // give the same bits.  The iteration is HBM-bound.  Full-matrix products
 // (dose of the weights, target indices over all voxels) use k_spmv_obj: a
@@ -304,11 +304,8 @@ constexpr int kRowChunk = 1024;
 // shared-memory copy of g per block, held as two 32-bit words per spot: the
 // low word by a native 32-bit atomic whose returned old value gives the
 // carry, the high word by a second one (exact, whatever the order).  The
-// block adds its copy to g with one 64-bit atomic per spot; the last block
-// to finish (a counter; no block waits) converts g back to floating point,
-// resets it and takes the Adam step (Kingma & Ba 2015) on x, clamped at
-// zero.  Grid: number of SMs, 1024 threads, n_cols x 8 bytes of shared
-// memory.
+// block adds its copy to g with one 64-bit atomic per spot.  Grid: number of
+// SMs, 1024 threads, n_cols x 8 bytes of shared memory.
 __global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict__ crp, int per_row,
                                                     const unsigned short* __restrict__ ccol,
                                                     const float* __restrict__ cval, int n_tr, int n_cols,
@@ -320,10 +317,7 @@ __global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict_
                                                     const unsigned* __restrict__ max_abs,
                                                     const float* __restrict__ count_bound, int n_scen,
                                                     float* __restrict__ hist, int it,
-                                                    unsigned long long* __restrict__ g,
-                                                    unsigned* __restrict__ blocks_done, float* __restrict__ x,
-                                                    float* __restrict__ m, float* __restrict__ v, float step,
-                                                    float c1, float c2, float eps)
+                                                    unsigned long long* __restrict__ g, int* __restrict__ g_shift)
 {
     extern __shared__ unsigned gsw[];
     unsigned* lo = gsw;
@@ -342,7 +336,10 @@ __global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict_
         if (bound <= 3.4028235e38f) frexpf(bound, &e);  // bound < 2^e
         s_star = w;
         s_k = bound > 0.0f ? 62 - e : 0;
-        if (blockIdx.x == 0 && hist) hist[it] = (float)s_f[w];
+        if (blockIdx.x == 0) {
+            if (hist) hist[it] = (float)s_f[w];
+            *g_shift = s_k;
+        }
     }
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x < n_scen) {
@@ -388,23 +385,23 @@ __global__ void __launch_bounds__(1024) k_bwd_fixed(const long long* __restrict_
         const unsigned long long t = ((unsigned long long)hi[j] << 32) | lo[j];
         if (t != 0ull) atomicAdd(g + j, t);
     }
-    // the last block to finish takes the Adam step (no block waits)
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(blocks_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) {
-        const long long gi = (long long)atomicExch(g + j, 0ull);      // the final sum; reset for the next iteration
-        const float gj = (float)ldexp((double)gi, -kq);
-        const float mj = fmaf(0.9f, m[j], 0.1f * gj), vj = fmaf(0.999f, v[j], 0.001f * gj * gj);
-        m[j] = mj;
-        v[j] = vj;
-        x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
-    }
-    if (threadIdx.x == 0) *blocks_done = 0u;
+}
+
+// g_j = (fixed-point sum) 2^-k, reset for the next iteration, then Adam
+// (Kingma & Ba 2015) on x_j, clamped at zero.
+__global__ void k_adam_fixed(unsigned long long* __restrict__ g, const int* __restrict__ g_shift, int n_cols,
+                             float* __restrict__ x, float* __restrict__ m, float* __restrict__ v, float step,
+                             float c1, float c2, float eps)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_cols) return;
+    const long long gi = (long long)g[j];
+    g[j] = 0ull;
+    const float gj = (float)ldexp((double)gi, -*g_shift);
+    const float mj = fmaf(0.9f, m[j], 0.1f * gj), vj = fmaf(0.999f, v[j], 0.001f * gj * gj);
+    m[j] = mj;
+    v[j] = vj;
+    x[j] = fmaxf(x[j] - step * (mj * c1) / (sqrtf(vj * c2) + eps), 0.0f);
 }
 
 }  // namespace
@@ -452,7 +449,7 @@ struct RobustWs {
     unsigned short* ccol = nullptr;
     float* cval = nullptr;
     unsigned long long* g = nullptr;            // [n_cols] fixed-point gradient
-    unsigned* blocks_done = nullptr;
+    int* g_shift = nullptr;
     unsigned* max_abs = nullptr;                // [S] max |a| (float bits)
     unsigned* max_r = nullptr;                  // [2 x S] max |f'(d)| (float bits)
     float* count_bound = nullptr;               // [S] entries of a spot over the compact rows, at most
@@ -465,7 +462,7 @@ struct RobustWs {
     ~RobustWs()
     {
         cudaFree(mats); cudaFree(tr_rows); cudaFree(tr_cls); cudaFree(len); cudaFree(crp); cudaFree(ccol);
-        cudaFree(cval); cudaFree(g); cudaFree(blocks_done); cudaFree(max_abs); cudaFree(max_r); cudaFree(count_bound);
+        cudaFree(cval); cudaFree(g); cudaFree(g_shift); cudaFree(max_abs); cudaFree(max_r); cudaFree(count_bound);
         cudaFree(unordered);
         cudaFree(dose_tr); cudaFree(fsum); cudaFree(m); cudaFree(v);
         cudaFree(hist);
@@ -557,8 +554,7 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
     OPT_TRY(cudaMemcpyAsync(w.count_bound, cb.data(), sizeof(float) * S, cudaMemcpyHostToDevice, st));
     // iteration state
     OPT_TRY(dalloc(&w.g, (size_t)n_cols));
-    OPT_TRY(dalloc(&w.blocks_done, 1));
-    OPT_TRY(cudaMemsetAsync(w.blocks_done, 0, sizeof(unsigned), st));
+    OPT_TRY(dalloc(&w.g_shift, 1));
     OPT_TRY(dalloc(&w.max_r, (size_t)2 * S));
     OPT_TRY(dalloc(&w.dose_tr, (size_t)S * n_tr));
     OPT_TRY(dalloc(&w.fsum, (size_t)2 * S));
@@ -584,11 +580,15 @@ cudaError_t run_robust_optimize(const long long* const* rp, const int* const* co
         const int cu = it & 1, nx = (it + 1) & 1;
         k_fwd<<<gf, 256, 0, st>>>(w.crp, w.ccol, w.cval, n_tr, x, w.tr_cls, q, w.dose_tr, w.fsum + cu * S,
                                   w.max_r + cu * S);
+        k_bwd_fixed<<<(unsigned)nsm, 1024, smem, st>>>(w.crp, per_row, w.ccol, w.cval, n_tr, n_cols, w.dose_tr,
+                                                       w.tr_cls, q,
+                                                       w.fsum + cu * S, w.max_r + cu * S, w.fsum + nx * S,
+                                                       w.max_r + nx * S, w.max_abs, w.count_bound, S, w.hist, it, w.g,
+                                                       w.g_shift);
         const double t = it + 1;
-        k_bwd_fixed<<<(unsigned)nsm, 1024, smem, st>>>(
-            w.crp, per_row, w.ccol, w.cval, n_tr, n_cols, w.dose_tr, w.tr_cls, q, w.fsum + cu * S, w.max_r + cu * S,
-            w.fsum + nx * S, w.max_r + nx * S, w.max_abs, w.count_bound, S, w.hist, it, w.g, w.blocks_done, x, w.m, w.v,
-            spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))), (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
+        k_adam_fixed<<<(unsigned)((n_cols + 255) / 256), 256, 0, st>>>(
+            w.g, w.g_shift, n_cols, x, w.m, w.v, spec.step, (float)(1.0 / (1.0 - std::pow(0.9, t))),
+            (float)(1.0 / (1.0 - std::pow(0.999, t))), spec.eps);
     }
     OPT_TRY(cudaGetLastError());
     OPT_TRY(cudaEventRecord(ev[2], st));
