@@ -209,6 +209,38 @@ def pencil_beam_water(n_hist: int = 100_000, energy: float = 100.0, sigma: float
     return pb, spots
 
 
+def machine_energies(n: int = 97, e_lo: float = 71.3, e_hi: float = 228.8) -> np.ndarray:
+    """The single-beamlet sweep's energies (Sec. 2.D.1: 97 machine energies
+    from 71.3 to 228.8 MeV; their spacing is not given, read as uniform)."""
+    return np.linspace(e_lo, e_hi, n)
+
+
+def edge_beamlet_problem(range_shifter: bool, depth_mm: float = 350.0, lateral_mm: float = 40.0,
+                         spacing: float = 1.0, opening_diameter_mm: float = 10.0, n_vertices: int = 256):
+    """Sec. 2.D.1 single-beamlet geometry: water phantom on a 1 mm grid
+    (lateral_mm square, depth_mm deep; surface at z = 0, isocentre on it),
+    30 mm brass aperture with a 1 cm circular opening (regular n-gon) whose
+    downstream face is 100 mm upstream of the surface; APRS adds a 45 mm-WET
+    range shifter 10 mm upstream of the block (AP: none)."""
+    shape = (int(round(lateral_mm / spacing)), int(round(lateral_mm / spacing)), int(round(depth_mm / spacing)))
+    g, hu = water_phantom(shape, (spacing,) * 3, (-lateral_mm / 2, -lateral_mm / 2, 0.0))
+    ap_down = 100.0
+    rs_down = ap_down + 30.0 + 10.0
+    src = (rs_down + 45.0 + 10.0) if range_shifter else (ap_down + 30.0 + 10.0)
+    beam = Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0), source_to_iso=src,
+                rs_present=range_shifter, rs_wet=45.0, rs_radius=30.5, rs_down_to_iso=rs_down,
+                ap_present=True, ap_thickness=30.0, ap_down_to_iso=ap_down,
+                polygon=regular_polygon(0.5 * opening_diameter_mm, n_vertices))
+    return Problem(ct=g, hu=hu, curve=HUCurve(), scoring=g, beams=[beam])
+
+
+def edge_beamlet_spot(energy: float, n_hist: int, opening_diameter_mm: float = 10.0, div_mrad: float = 2.0):
+    """One beamlet along the beam axis centred on the opening's edge
+    (x = radius, y = 0 at the isocentre plane), sigma of spot_sigma_mm."""
+    return make_spots([(0, float(energy), 0.5 * opening_diameter_mm, 0.0, float(spot_sigma_mm(energy)),
+                        div_mrad, int(n_hist), 1.0)])
+
+
 def water_aperture_case(opening_diameter_mm: float, range_shifter: bool, hist_per_layer: int = 1_000_000,
                         e_first: float = 100.0, e_last: float = 160.0, n_vertices: int = 256,
                         shape=(100, 100, 150), spacing=(2.0, 2.0, 2.0), max_layers: Optional[int] = None):

@@ -1,0 +1,152 @@
+"""Single-beamlet edge sweep (Sec. 2.D.1): one beamlet along the beam axis
+centred on the edge of a 1 cm opening in 30 mm brass, water phantom on a
+1 mm grid, with (APRS) and without (AP) the 45 mm-WET range shifter, at the
+paper's 97 energies from 71.3 to 228.8 MeV.  The paper compares its engine
+with MCsquare; here the GPU path is compared with the FP64 oracle.
+
+* the three energies the paper illustrates (82.0, 140.2, 228.8 MeV) on both
+  machines: per history in deterministic mode, and statistically in full
+  physics (3D dose within the combined batch uncertainty, 2%/2mm/10% gamma,
+  integrated depth dose);
+* all 97 x 2 beamlets on the GPU: properties that hold at any size (energy
+  conservation, the distal edge of the depth dose moving deeper with energy,
+  the range shifter pulling it back by about its water-equivalent
+  thickness, the block stopping the protons that hit it below about
+  155 MeV)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2307_01416_gb300 import workloads as W
+from tests.test_gpu_parity import _per_history_parity
+
+pytestmark = pytest.mark.gpu
+
+PAPER_ENERGIES = (82.0, 140.2, 228.8)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    return torch
+
+
+def _depth_mm(energy, rs):
+    return float(np.ceil(W.bk_range_for_energy(energy) - (45.0 if rs else 0.0) + 20.0))
+
+
+@pytest.mark.parametrize("rs", [False, True], ids=["AP", "APRS"])
+@pytest.mark.parametrize("energy", PAPER_ENERGIES)
+def test_edge_beamlet_per_history(torch_cuda, energy, rs):
+    pb = W.edge_beamlet_problem(rs, depth_mm=_depth_mm(energy, rs))
+    spots = W.edge_beamlet_spot(energy, 3000)
+    det = W.Options(seed=2024, mcs=False, straggling=False, nuclear=True)
+    _, st, rec, _, orec = _per_history_parity(pb, spots, W.Scenario(), det, max_flagged=0.02)
+    # the beamlet is centred on the rim of the opening: about 70 % of it meets
+    # the brass, which stops it below about 155 MeV (after the range shifter
+    # for APRS) and lets it through, slowed down, at the top energy
+    stopped = np.mean(orec["fate"] == O.FATE_AP)
+    assert np.mean(rec["fate"] == O.FATE_AP) == pytest.approx(stopped, abs=1e-3)
+    if energy < 150.0:
+        assert 0.5 < stopped < 0.85, stopped
+    else:
+        assert stopped < 0.2, stopped
+    assert st["e_aperture"] > 0.1 * st["e_in"]
+
+
+@pytest.mark.parametrize("rs", [False, True], ids=["AP", "APRS"])
+@pytest.mark.parametrize("energy", PAPER_ENERGIES)
+def test_edge_beamlet_full_physics_statistical(torch_cuda, energy, rs):
+    """GPU 20 x 1e5 histories against the oracle 20 x 1e4, doses per history.
+    Above 10 % of the maximum on the 1 mm grid, |z| (difference over the
+    combined batch standard error, 19 degrees of freedom) exceeds 3 in at most
+    4 % of the voxels and 8 nowhere; the integrated depth dose agrees within 5
+    combined standard errors in every 1 mm bin; the peaks coincide to 1 mm.
+    Calibration, two oracle runs of the same sizes (1e6 and 2e5 histories)
+    against each other: 2.1-2.2 % of voxels above 3, |z| <= 5.9, depth dose
+    |z| <= 3.3.  The 2%/2mm/10% gamma of the paper's comparison needs both
+    doses below 0.5 % uncertainty; with the oracle at 2e5 histories the same
+    calibration pair reaches 94.6-99.0 %, so gamma is asserted at >= 93 %."""
+    from paper_2307_01416_gb300 import vpmc
+    pb = W.edge_beamlet_problem(rs, depth_mm=_depth_mm(energy, rs))
+    rho = O.scoring_density(pb)
+    g = pb.scoring
+    shp = (g.shape[2], g.shape[1], g.shape[0])
+    eng = vpmc.Engine(pb)
+    dg, do = [], []
+    for b in range(20):
+        d, st, _ = eng.run_spots(W.edge_beamlet_spot(energy, 100_000), W.Scenario(), W.Options(seed=7000 + b))
+        assert st["errors"] == 0
+        dg.append(d.cpu().numpy().astype(np.float64).ravel() / 100_000)
+        q, tl, _ = O.run(pb, O.oracle_spots(W.edge_beamlet_spot(energy, 10_000)), W.Scenario(),
+                         W.Options(seed=9000 + b))
+        assert tl["errors"] == 0
+        do.append(O.dose_from_q(pb, q, 24, rho) / 10_000)
+    eng.close()
+    dg, do = np.stack(dg), np.stack(do)
+    n = dg.shape[0]
+    mg, mo = dg.mean(0), do.mean(0)
+    sg, so = dg.std(0, ddof=1) / math.sqrt(n), do.std(0, ddof=1) / math.sqrt(n)
+    sel = mo >= 0.1 * mo.max()
+    assert sel.sum() > 500
+    z = np.abs(mg - mo)[sel] / np.sqrt(sg[sel] ** 2 + so[sel] ** 2)
+    assert np.mean(z > 3.0) <= 0.04 and z.max() < 8.0, (np.mean(z > 3.0), z.max())
+    gam = O.gamma_pass_rate(mo.reshape(shp), mg.reshape(shp), g.spacing)
+    assert gam >= 93.0, gam
+    # integrated depth dose per 1 mm bin (dose x density: energy per depth), batch by batch
+    ig = (dg * rho).reshape(n, *shp).sum(axis=(2, 3))
+    io = (do * rho).reshape(n, *shp).sum(axis=(2, 3))
+    mig, mio = ig.mean(0), io.mean(0)
+    se = np.sqrt(ig.var(0, ddof=1) / n + io.var(0, ddof=1) / n)
+    keep = mio >= 0.1 * mio.max()
+    zi = np.abs(mig - mio)[keep] / se[keep]
+    assert zi.max() < 5.0, zi.max()
+    assert abs(int(np.argmax(mig)) - int(np.argmax(mio))) <= 1
+
+
+def _distal_depth_mm(dose, pb, level=0.2):
+    """Deepest depth (mm) whose integrated depth dose is at least level x its
+    maximum: the beamlet's open part sets it even when the part that went
+    through the brass makes the higher, shallower peak."""
+    g = pb.scoring
+    idd = dose.reshape(g.shape[2], g.shape[1], g.shape[0]).sum(axis=(1, 2))
+    return (np.flatnonzero(idd >= level * idd.max())[-1] + 0.5) * g.spacing[2]
+
+
+def test_sweep_97_energies_both_machines(torch_cuda):
+    """All 194 beamlets (1e5 histories each) on one geometry per machine."""
+    from paper_2307_01416_gb300 import vpmc
+    energies = W.machine_energies()
+    assert energies.size == 97 and energies[0] == 71.3 and energies[-1] == 228.8
+    peaks, frac_ap = {}, {}
+    for rs in (False, True):
+        pb = W.edge_beamlet_problem(rs)
+        eng = vpmc.Engine(pb)
+        pk, fa = [], []
+        for e in energies:
+            d, st, _ = eng.run_spots(W.edge_beamlet_spot(e, 100_000), W.Scenario(), W.Options(seed=11))
+            assert st["errors"] == 0
+            tot = st["e_dep"] + st["e_leak"] + st["e_rs"] + st["e_aperture"]
+            assert abs(tot / st["e_in"] - 1.0) < 1e-6
+            pk.append(_distal_depth_mm(d.cpu().numpy().astype(np.float64), pb))
+            fa.append(st["e_aperture"] / st["e_in"])
+        eng.close()
+        peaks[rs], frac_ap[rs] = np.array(pk), np.array(fa)
+    for rs in (False, True):
+        # the distal edge moves deeper with energy (1 mm bins)
+        assert np.all(np.diff(peaks[rs]) >= -1.0), peaks[rs]
+        assert peaks[rs][-1] - peaks[rs][0] > 250.0
+    # the range shifter pulls it back by ~45 mm of water (PMMA WET, 1 mm bins)
+    deep = peaks[False] > 60.0
+    shift = peaks[False][deep] - peaks[True][deep]
+    assert np.all(np.abs(shift - 45.0) <= 3.0), shift
+    # below ~155 MeV the 30 mm block stops what hits it: about 70 % of the beamlet's energy
+    low = energies < 150.0
+    assert np.all((frac_ap[False][low] > 0.55) & (frac_ap[False][low] < 0.85)), frac_ap[False][low]
+    # at the top energies part of it goes through the brass and deposits downstream
+    assert frac_ap[False][-1] < frac_ap[False][low].min()
