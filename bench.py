@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-aperture leg")
     ap.add_argument("--no-optimizer", action="store_true", help="skip the robust-optimisation leg")
+    ap.add_argument("--no-edge-sweep", action="store_true", help="skip the single-beamlet edge sweep leg")
+    ap.add_argument("--edge-hist", type=int, default=1_000_000, help="histories per beamlet of the edge sweep")
     ap.add_argument("--opt-iterations", type=int, default=50)
     ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im", "opt"], default=None,
                     help="small fixed-launch transport case for ncu captures (nominal scenario, every 10th spot): "
@@ -320,6 +322,9 @@ def main():
         if not args.no_optimizer and world == 1:
             opt = optimizer_leg(pb, target, last_mats, args)
         del last_mats
+        edge = None
+        if not args.no_edge_sweep and world == 1:
+            edge = edge_sweep_leg(args, peak_tops)
         sur = None
         if not args.no_surrogate and world == 1 and not args.small:
             sur = surrogate_leg(pb, spots, scens, opts, args, value)
@@ -334,7 +339,7 @@ def main():
                           "parallelism": "independent sets per GPU" if world > 1 else "1 GPU"},
                "s_per_im_set": ms_per_step / 1000.0,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
-               "surrogate": sur, "optimizer": opt}
+               "surrogate": sur, "optimizer": opt, "edge_sweep": edge}
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
@@ -539,6 +544,48 @@ def optimizer_leg(pb, target, mats, args):
             "note": "per iteration: 13 products on the compact target/ring rows (built once per call, "
                     "setup_ms), worst-case selection, the transposed product and the Adam step, all on the "
                     "device; target 8.4 cc sphere, ring = 10 mm shell"}
+
+
+def edge_sweep_leg(args, peak_tops):
+    """The single-beamlet edge sweep (Sec. 2.D.1): 97 energies from 71.3 to
+    228.8 MeV, one beamlet on the rim of a 1 cm opening in 30 mm brass, water
+    on a 1 mm grid (40 x 40 x 350 mm), without (AP) and with (APRS) the 45 mm
+    range shifter; args.edge_hist histories per beamlet, full physics.  One
+    untimed beamlet per machine, then the 97 timed on the device (CUDA events
+    around the machine's beamlets; dose grids stay on the device)."""
+    import torch
+    from paper_2307_01416_gb300 import vpmc
+    energies = W.machine_energies()
+    total_s, hist, steps, kern_ms, launches = 0.0, 0, 0, 0.0, 0
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for rs in (False, True):
+            pb = W.edge_beamlet_problem(rs)
+            eng = vpmc.Engine(pb, stream=stream)
+            eng.run_spots(W.edge_beamlet_spot(150.0, args.edge_hist), W.Scenario(), W.Options(seed=5))
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for k, e in enumerate(energies):
+                d, st, _ = eng.run_spots(W.edge_beamlet_spot(e, args.edge_hist), W.Scenario(),
+                                         W.Options(seed=100 + k))
+                hist += st["histories"]
+                steps += st["steps"]
+                kern_ms += st["ms"]
+                launches += st["launches"]
+                del d
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            total_s += ev0.elapsed_time(ev1) / 1000.0
+            eng.close()
+    achieved = steps * OPS_PER_STEP / (kern_ms / 1000.0) / 1e12
+    return {"beamlets": 2 * int(energies.size), "histories_per_beamlet": args.edge_hist, "histories": hist,
+            "s_per_sweep": total_s, "value": hist / total_s, "unit": "protons/s", "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                         "frac": achieved / peak_tops, "kernel": "k_source_rs+k_aperture+k_patient"},
+            "note": "97 energies 71.3-228.8 MeV x (AP, APRS), beamlet on the rim of a 1 cm opening in 30 mm "
+                    "brass, water 40x40x350 mm at 1 mm; parity vs the oracle in tests/test_gpu_edge_sweep.py"}
 
 
 def e2e_leg(pb, spots, scens, opts, args):
