@@ -62,51 +62,59 @@ def test_edge_beamlet_per_history(torch_cuda, energy, rs):
 @pytest.mark.parametrize("rs", [False, True], ids=["AP", "APRS"])
 @pytest.mark.parametrize("energy", PAPER_ENERGIES)
 def test_edge_beamlet_full_physics_statistical(torch_cuda, energy, rs):
-    """GPU 20 x 1e5 histories against the oracle 20 x 1e4, doses per history.
-    Above 10 % of the maximum on the 1 mm grid, |z| (difference over the
-    combined batch standard error, 19 degrees of freedom) exceeds 3 in at most
-    4 % of the voxels and 8 nowhere; the integrated depth dose agrees within 5
-    combined standard errors in every 1 mm bin; the peaks coincide to 1 mm.
-    Calibration, two oracle runs of the same sizes (1e6 and 2e5 histories)
-    against each other: 2.1-2.2 % of voxels above 3, |z| <= 5.9, depth dose
-    |z| <= 3.3.  The 2%/2mm/10% gamma of the paper's comparison needs both
-    doses below 0.5 % uncertainty; with the oracle at 2e5 histories the same
-    calibration pair reaches 94.6-99.0 %, so gamma is asserted at >= 93 %."""
+    """Doses per history, 20 batches per side.  Per voxel, above 10 % of the
+    maximum on the 1 mm grid: GPU batches of 1e4 histories against oracle
+    batches of 1e4, |z| (difference over the combined batch standard error)
+    above 3 in at most 1 % of the voxels and above 6 nowhere.  The batch
+    sizes are equal because a voxel's batch dose is right-skewed at this size:
+    against a 10x larger batch the small batches' low draws pair with low
+    standard errors and bias z upward (GPU 1e5 batches against GPU 1e4 batches
+    put 5.9 % of the voxels above 3; equal GPU and oracle batches put 0.2 %).
+    Integrated depth dose: GPU batches of 1e5 against the oracle's, within 5
+    combined standard errors in every 1 mm bin (a bin sums thousands of
+    voxels), peaks within 1 mm.  The paper's 2%/2mm/10% gamma needs both
+    doses below 0.5 % uncertainty; GPU 2e6 histories against the oracle's 2e5
+    reach 94.6-99.6 % in oracle-against-oracle calibration at these sizes,
+    so gamma is asserted at >= 93 %."""
     from paper_2307_01416_gb300 import vpmc
     pb = W.edge_beamlet_problem(rs, depth_mm=_depth_mm(energy, rs))
     rho = O.scoring_density(pb)
     g = pb.scoring
     shp = (g.shape[2], g.shape[1], g.shape[0])
     eng = vpmc.Engine(pb)
-    dg, do = [], []
+    big, small, orc = [], [], []
     for b in range(20):
         d, st, _ = eng.run_spots(W.edge_beamlet_spot(energy, 100_000), W.Scenario(), W.Options(seed=7000 + b))
         assert st["errors"] == 0
-        dg.append(d.cpu().numpy().astype(np.float64).ravel() / 100_000)
+        big.append(d.cpu().numpy().astype(np.float64).ravel() / 100_000)
+        d, st, _ = eng.run_spots(W.edge_beamlet_spot(energy, 10_000), W.Scenario(), W.Options(seed=8000 + b))
+        assert st["errors"] == 0
+        small.append(d.cpu().numpy().astype(np.float64).ravel() / 10_000)
         q, tl, _ = O.run(pb, O.oracle_spots(W.edge_beamlet_spot(energy, 10_000)), W.Scenario(),
                          W.Options(seed=9000 + b))
         assert tl["errors"] == 0
-        do.append(O.dose_from_q(pb, q, 24, rho) / 10_000)
+        orc.append(O.dose_from_q(pb, q, 24, rho) / 10_000)
     eng.close()
-    dg, do = np.stack(dg), np.stack(do)
-    n = dg.shape[0]
-    mg, mo = dg.mean(0), do.mean(0)
-    sg, so = dg.std(0, ddof=1) / math.sqrt(n), do.std(0, ddof=1) / math.sqrt(n)
+    big, small, orc = np.stack(big), np.stack(small), np.stack(orc)
+    n = orc.shape[0]
+    mo, so = orc.mean(0), orc.std(0, ddof=1) / math.sqrt(n)
+    ms, ss = small.mean(0), small.std(0, ddof=1) / math.sqrt(n)
     sel = mo >= 0.1 * mo.max()
     assert sel.sum() > 500
-    z = np.abs(mg - mo)[sel] / np.sqrt(sg[sel] ** 2 + so[sel] ** 2)
-    assert np.mean(z > 3.0) <= 0.04 and z.max() < 8.0, (np.mean(z > 3.0), z.max())
-    gam = O.gamma_pass_rate(mo.reshape(shp), mg.reshape(shp), g.spacing)
+    z = np.abs(ms - mo)[sel] / np.sqrt(ss[sel] ** 2 + so[sel] ** 2)
+    assert np.mean(z > 3.0) <= 0.01 and z.max() < 6.0, (np.mean(z > 3.0), z.max())
+    mb = big.mean(0)
+    gam = O.gamma_pass_rate(mo.reshape(shp), mb.reshape(shp), g.spacing)
     assert gam >= 93.0, gam
     # integrated depth dose per 1 mm bin (dose x density: energy per depth), batch by batch
-    ig = (dg * rho).reshape(n, *shp).sum(axis=(2, 3))
-    io = (do * rho).reshape(n, *shp).sum(axis=(2, 3))
-    mig, mio = ig.mean(0), io.mean(0)
-    se = np.sqrt(ig.var(0, ddof=1) / n + io.var(0, ddof=1) / n)
+    ib = (big * rho).reshape(n, *shp).sum(axis=(2, 3))
+    io = (orc * rho).reshape(n, *shp).sum(axis=(2, 3))
+    mib, mio = ib.mean(0), io.mean(0)
+    se = np.sqrt(ib.var(0, ddof=1) / n + io.var(0, ddof=1) / n)
     keep = mio >= 0.1 * mio.max()
-    zi = np.abs(mig - mio)[keep] / se[keep]
+    zi = np.abs(mib - mio)[keep] / se[keep]
     assert zi.max() < 5.0, zi.max()
-    assert abs(int(np.argmax(mig)) - int(np.argmax(mio))) <= 1
+    assert abs(int(np.argmax(mib)) - int(np.argmax(mio))) <= 1
 
 
 def _distal_depth_mm(dose, pb, level=0.2):
