@@ -57,7 +57,7 @@ class _Beam(C.Structure):
                 ("source_to_iso", C.c_double),
                 ("rs_present", C.c_int), ("rs_wet", C.c_double), ("rs_radius", C.c_double), ("rs_down_to_iso", C.c_double),
                 ("ap_present", C.c_int), ("ap_thickness", C.c_double), ("ap_down_to_iso", C.c_double),
-                ("poly_offset", C.c_int), ("nvert", C.c_int)]
+                ("poly_offset", C.c_int), ("nvert", C.c_int), ("ap_sad", C.c_double)]
 
 
 class _Scen(C.Structure):
@@ -126,6 +126,7 @@ def lib():
                                               C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int64)]
             L.orc_gamma_pass_rate.restype = C.c_double
             L.orc_nearest_edge.argtypes = [dp, C.c_int, C.c_double, C.c_double, dp]
+            L.orc_aperture_query.argtypes = [C.POINTER(_Beam), dp, dp, dp, dp]
             L.orc_surrogate_features.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double, dp, C.c_double,
                                                  dp, dp]
             L.orc_surrogate_tracks.argtypes = [C.POINTER(_Beam), C.c_void_p, C.c_int, C.c_int64, C.POINTER(_Opts),
@@ -263,6 +264,7 @@ def _beams(beams):
         a.rs_wet, a.rs_radius, a.rs_down_to_iso = b.rs_wet, b.rs_radius, b.rs_down_to_iso
         a.ap_present = int(b.ap_present)
         a.ap_thickness, a.ap_down_to_iso = b.ap_thickness, b.ap_down_to_iso
+        a.ap_sad = float(getattr(b, "ap_sad", 0.0))
         if b.ap_present:
             p = np.ascontiguousarray(b.polygon, dtype=np.float64)
             polys.append(p)
@@ -384,6 +386,18 @@ def step_sample(table, kappa, rho, za, x0, e, s_geom=float("inf"), mcs=True, str
 
 
 # ------------------------------------------------------------ learned surrogate
+def aperture_query(beam, p, d):
+    """(in the opening, first wall hit distance, wall distance) of the point
+    p and direction d (BEV, t along the beam from the isocentre) for the
+    beam's aperture, parallel or divergent walls."""
+    arr, xy = _beams([beam])
+    out = np.zeros(3)
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    lib().orc_aperture_query(C.byref(arr[0]), _dp(xy), _dp(pp), _dp(dd), _dp(out))
+    return bool(out[0]), float(out[1]), float(out[2])
+
+
 def nearest_edge(poly: np.ndarray, x: float, y: float):
     """(distance, nearest x, nearest y, curvature there) of the polygon boundary."""
     p = np.ascontiguousarray(poly, dtype=np.float64)

@@ -320,7 +320,91 @@ typedef struct {
     int ap_present;
     double ap_thickness, ap_down_to_iso;
     int poly_offset, nvert;           /* vertices in the shared xy array      */
+    double ap_sad;                    /* divergent walls: virtual source at
+                                         t = -ap_sad (0: walls parallel to
+                                         the beam axis)                       */
 } orc_beam;
+
+/* ------------------------------------------------------------------ */
+/* Divergent aperture walls (the authors' next step, Sec. 4).  Reading:  */
+/* the polygon is the opening at the block's downstream face t_dn; each  */
+/* wall is the plane through the virtual source S = (0, 0, -sad) and one */
+/* polygon edge there, so the opening at depth t is the polygon scaled   */
+/* by (t + sad) / (t_dn + sad).  ap_sad = 0 keeps parallel walls.        */
+/* ------------------------------------------------------------------ */
+
+/* Scale of the opening at depth t relative to the downstream face. */
+static double ap_scale(const orc_beam* bm, double t)
+{
+    if (!(bm->ap_sad > 0.0)) return 1.0;
+    double tdn = -bm->ap_down_to_iso;
+    return (t + bm->ap_sad) / (tdn + bm->ap_sad);
+}
+
+/* Is (x, y, t) inside the opening? */
+static int ap_in_opening(const orc_beam* bm, const double* poly, double x, double y, double t)
+{
+    double s = ap_scale(bm, t);
+    return orc_point_in_polygon(poly, bm->nvert, x / s, y / s);
+}
+
+/* Wall distance used by the tie flag and the range rejection: the distance,
+ * in the plane of constant depth through the point, to the opening's
+ * contour at that depth, times the cosine of the largest wall tilt, so that
+ * it never exceeds the 3D distance to a wall (parallel walls: the plain 2D
+ * distance). */
+static double ap_wall_distance(const orc_beam* bm, const double* poly, double x, double y, double t)
+{
+    if (!(bm->ap_sad > 0.0)) return orc_wall_distance(poly, bm->nvert, x, y);
+    double s = ap_scale(bm, t);
+    double K = -bm->ap_down_to_iso + bm->ap_sad, rc = 0.0;
+    for (int i = 0; i < bm->nvert; ++i) {
+        double r = hypot(poly[2 * i], poly[2 * i + 1]);
+        if (r > rc) rc = r;
+    }
+    return s * orc_wall_distance(poly, bm->nvert, x / s, y / s) * (K / sqrt(K * K + rc * rc));
+}
+
+/* Smallest s > 0 at which p + s d meets a wall: each wall is the plane
+ * through S and the edge (A, B) at t_dn; the hit must lie between the
+ * plane's two edge rays (its projection from S onto t_dn falls on the edge).
+ * Parallel walls: the 2D ray-edge test. */
+static double ap_first_wall_hit(const orc_beam* bm, const double* poly, const double p[3], const double d[3])
+{
+    if (!(bm->ap_sad > 0.0)) return orc_first_wall_hit(poly, bm->nvert, p[0], p[1], d[0], d[1]);
+    double tdn = -bm->ap_down_to_iso, sad = bm->ap_sad;
+    double S[3] = {0.0, 0.0, -sad};
+    double best = INFINITY;
+    for (int i = 0; i < bm->nvert; ++i) {
+        int j = (i + 1) % bm->nvert;
+        double A[3] = {poly[2 * i], poly[2 * i + 1], tdn}, B[3] = {poly[2 * j], poly[2 * j + 1], tdn};
+        double a[3], b[3], n[3];
+        for (int k = 0; k < 3; ++k) { a[k] = A[k] - S[k]; b[k] = B[k] - S[k]; }
+        n[0] = a[1] * b[2] - a[2] * b[1];
+        n[1] = a[2] * b[0] - a[0] * b[2];
+        n[2] = a[0] * b[1] - a[1] * b[0];
+        double den = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
+        if (den == 0.0) continue;
+        double s = (n[0] * (A[0] - p[0]) + n[1] * (A[1] - p[1]) + n[2] * (A[2] - p[2])) / den;
+        if (!(s > 0.0) || s >= best) continue;
+        double q[3] = {p[0] + s * d[0], p[1] + s * d[1], p[2] + s * d[2]};
+        double f = (tdn + sad) / (q[2] + sad);           /* project from S onto t_dn */
+        double qx = q[0] * f, qy = q[1] * f;
+        double ex = B[0] - A[0], ey = B[1] - A[1];
+        double lam = ((qx - A[0]) * ex + (qy - A[1]) * ey) / (ex * ex + ey * ey);
+        if (lam >= 0.0 && lam <= 1.0) best = s;
+    }
+    return best;
+}
+
+/* Test hook: (in the opening, first wall hit, wall distance) of a point and
+ * direction for a beam's aperture; poly is that beam's polygon. */
+void orc_aperture_query(const orc_beam* bm, const double* poly, const double p[3], const double d[3], double out[3])
+{
+    out[0] = ap_in_opening(bm, poly, p[0], p[1], p[2]);
+    out[1] = ap_first_wall_hit(bm, poly, p, d);
+    out[2] = ap_wall_distance(bm, poly, p[0], p[1], p[2]);
+}
 
 typedef struct {
     int beam;
@@ -571,11 +655,11 @@ static int aperture_block(const orc_beam* bm, const double* poly, orc_particle* 
         if (pt->d[2] > 0.0) sg = (tdn - pt->p[2]) / pt->d[2];
         else if (pt->d[2] < 0.0) { sg = (tup - pt->p[2]) / pt->d[2]; down = 0; }
         if (sg < 0.0) sg = 0.0;   /* scattering offsets can leave it past the plane */
-        if (orc_wall_distance(poly, bm->nvert, pt->p[0], pt->p[1]) < ORC_TIE_MM) rec->flags |= 1;
-        int in_open = !forced_brass && orc_point_in_polygon(poly, bm->nvert, pt->p[0], pt->p[1]);
+        if (ap_wall_distance(bm, poly, pt->p[0], pt->p[1], pt->p[2]) < ORC_TIE_MM) rec->flags |= 1;
+        int in_open = !forced_brass && ap_in_opening(bm, poly, pt->p[0], pt->p[1], pt->p[2]);
         if (in_open) {
             /* opening: keep velocity and direction up to a wall or the exit */
-            double sw = orc_first_wall_hit(poly, bm->nvert, pt->p[0], pt->p[1], pt->d[0], pt->d[1]);
+            double sw = ap_first_wall_hit(bm, poly, pt->p, pt->d);
             if (sw < sg) {
                 for (int k = 0; k < 3; ++k) pt->p[k] += sw * pt->d[k];
                 rec->track += sw;
@@ -596,7 +680,7 @@ static int aperture_block(const orc_beam* bm, const double* poly, orc_particle* 
             double dlim = pt->p[2] - tup;
             if (tdn - pt->p[2] < dlim) dlim = tdn - pt->p[2];
             if (rmax < dlim + ORC_TIE_MM) {
-                double dw = orc_wall_distance(poly, bm->nvert, pt->p[0], pt->p[1]);
+                double dw = ap_wall_distance(bm, poly, pt->p[0], pt->p[1], pt->p[2]);
                 if (dw < dlim) dlim = dw;
                 if (fabs(rmax - dlim) < ORC_TIE_MM) rec->flags |= 16;
                 if (rmax < dlim) {

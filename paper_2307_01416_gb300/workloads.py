@@ -75,7 +75,8 @@ class Beam:
     ap_present: bool = False
     ap_thickness: float = 30.0
     ap_down_to_iso: float = 150.0
-    polygon: Optional[np.ndarray] = None   # (n, 2) BEV mm, opening contour
+    polygon: Optional[np.ndarray] = None   # (n, 2) BEV mm, opening contour at the block's downstream face
+    ap_sad: float = 0.0                    # divergent walls: virtual source this far upstream of the isocentre (0: parallel)
 
 
 @dataclasses.dataclass

@@ -1,0 +1,140 @@
+"""Pins of the oracle's divergent aperture (the authors' next step, Sec. 4):
+walls are the planes through a virtual source on the beam axis and the
+opening's edges at the block's downstream face.  Checked against the cone
+of a circular opening in closed form, the parallel-wall limit, rays from the
+virtual source, and the transmission of a parallel beam through a block
+whose opening grows downstream."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2307_01416_gb300 import workloads as W
+
+R_REF, SAD, T_DN, THICK = 5.0, 2000.0, -100.0, 30.0
+
+
+def _beam(sad, n=4096, r=R_REF):
+    return W.Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0), source_to_iso=200.0,
+                  ap_present=True, ap_thickness=THICK, ap_down_to_iso=-T_DN, polygon=W.regular_polygon(r, n),
+                  ap_sad=sad)
+
+
+def _cone_radius(t, sad=SAD, r=R_REF):
+    return r * (t + sad) / (T_DN + sad)
+
+
+def test_wall_hit_and_opening_match_the_cone():
+    """A 4096-gon opening: its divergent walls approximate the cone
+    r(t) = R (t + sad) / (t_dn + sad); the first hit of rays starting inside
+    equals the cone's closed form (quadratic), the in-opening test the cone's
+    (away from the contour by more than the polygon's sagitta)."""
+    b = _beam(SAD)
+    g = np.random.default_rng(3)
+    k = R_REF / (T_DN + SAD)
+    for _ in range(200):
+        t0 = g.uniform(T_DN - THICK, T_DN)
+        r0 = g.uniform(0.0, 0.9) * _cone_radius(t0)
+        ph = g.uniform(0.0, 2 * math.pi)
+        p = np.array([r0 * math.cos(ph), r0 * math.sin(ph), t0])
+        d = np.array([g.normal(0, 0.1), g.normal(0, 0.1), 1.0])
+        d /= np.linalg.norm(d)
+        inside, sw, _ = O.aperture_query(b, p, d)
+        assert inside
+        # |p_xy + s d_xy| = k (p_t + s d_t + sad)
+        a2 = d[0] ** 2 + d[1] ** 2 - (k * d[2]) ** 2
+        a1 = 2 * (p[0] * d[0] + p[1] * d[1]) - 2 * k * k * (p[2] + SAD) * d[2]
+        a0 = p[0] ** 2 + p[1] ** 2 - (k * (p[2] + SAD)) ** 2
+        s = (-a1 + math.sqrt(a1 * a1 - 4 * a2 * a0)) / (2 * a2)
+        assert sw == pytest.approx(s, rel=1e-6, abs=2e-4), (p, d, sw, s)
+    for _ in range(400):
+        t0 = g.uniform(T_DN - THICK, T_DN)
+        r0 = g.uniform(0.0, 2.0) * _cone_radius(t0)
+        if abs(r0 - _cone_radius(t0)) < 1e-4:
+            continue
+        p = np.array([r0, 0.3 * r0, t0]) / math.hypot(1.0, 0.3) * np.array([1.0, 1.0, math.hypot(1.0, 0.3)])
+        inside, _, _ = O.aperture_query(b, p, np.array([0.0, 0.0, 1.0]))
+        assert inside == (math.hypot(p[0], p[1]) < _cone_radius(t0))
+
+
+def test_wall_distance_is_the_distance_to_the_cone():
+    """For a circular opening the depth-plane distance times the cosine of
+    the wall tilt is the exact 3D distance to the cone (inside and outside)."""
+    b = _beam(SAD)
+    k = R_REF / (T_DN + SAD)
+    g = np.random.default_rng(4)
+    for _ in range(200):
+        t0 = g.uniform(T_DN - THICK, T_DN)
+        r0 = g.uniform(0.0, 3.0) * _cone_radius(t0)
+        p = np.array([r0, 0.0, t0])
+        _, _, dw = O.aperture_query(b, p, np.array([0.0, 0.0, 1.0]))
+        exact = abs(r0 - k * (t0 + SAD)) / math.sqrt(1.0 + k * k)
+        assert dw == pytest.approx(exact, abs=2e-5)
+
+
+def test_parallel_limit():
+    """As the virtual source recedes, the divergent walls become the parallel ones."""
+    g = np.random.default_rng(5)
+    par, far = _beam(0.0, n=64), _beam(1e9, n=64)
+    for _ in range(200):
+        p = np.array([g.uniform(-4, 4), g.uniform(-4, 4), g.uniform(T_DN - THICK, T_DN)])
+        d = np.array([g.normal(0, 0.2), g.normal(0, 0.2), 1.0])
+        d /= np.linalg.norm(d)
+        a, b = O.aperture_query(par, p, d), O.aperture_query(far, p, d)
+        assert a[0] == b[0]
+        assert b[1] == pytest.approx(a[1], rel=1e-6, abs=1e-6)
+        assert b[2] == pytest.approx(a[2], rel=1e-6, abs=1e-6)
+
+
+def test_rays_from_the_virtual_source_miss_the_walls():
+    """A ray from the virtual source through a point of the opening at the
+    downstream face stays inside the opening through the whole block."""
+    b = _beam(SAD, n=48)
+    g = np.random.default_rng(6)
+    poly = W.regular_polygon(R_REF, 48)
+    for _ in range(200):
+        q = np.array([g.uniform(-R_REF, R_REF), g.uniform(-R_REF, R_REF)])
+        if not O.point_in_polygon(poly, q[0], q[1]) or O.wall_distance(poly, q[0], q[1]) < 1e-3:
+            continue
+        d = np.array([q[0], q[1], T_DN + SAD])
+        d /= np.linalg.norm(d)
+        s_up = (T_DN - THICK + SAD) / d[2]              # from the source to the entrance plane
+        p = np.array([0.0, 0.0, -SAD]) + s_up * d
+        inside, sw, _ = O.aperture_query(b, p, d)
+        assert inside
+        assert sw > THICK / d[2] - 1e-9
+
+
+@pytest.mark.parametrize("energy", [100.0, 150.0])
+def test_parallel_beam_transmission_through_a_growing_opening(energy):
+    """Deterministic transport (no scattering or straggling, no nuclear
+    removal) of a parallel Gaussian beam, sigma s, centred on the axis,
+    through a block with a 256-gon opening of radius R at the downstream face
+    and a virtual source 300 mm upstream: a ray at radius r enters the brass
+    at the entrance unless r < r(t_up), and reaches the opening after
+    r (t_dn + sad) / R - sad - t_up mm of brass.  Below ~155 MeV it is
+    transmitted iff that path is below the CSDA range in brass R_b, i.e.
+    r < r(t_up + R_b): T = 1 - exp(-r(t_up + R_b)^2 / 2 s^2)."""
+    sad, r_ref, s, n = 300.0, 6.0, 4.0, 60000
+    ct = W.Grid((20, 20, 10), (2.0, 2.0, 2.0), (-20.0, -20.0, 0.0))
+    hu = np.zeros((10, 20, 20), dtype=np.int16)
+    beam = W.Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0), source_to_iso=150.0,
+                  ap_present=True, ap_thickness=THICK, ap_down_to_iso=-T_DN, polygon=W.regular_polygon(r_ref, 256),
+                  ap_sad=sad)
+    pb = W.Problem(ct=ct, hu=hu, curve=W.HUCurve(), scoring=ct, beams=[beam])
+    spots = W.make_spots([(0, energy, 0.0, 0.0, s, 0.0, n, 1.0)])
+    op = W.Options(seed=5, mcs=False, straggling=False, nuclear=False)
+    q, tl, rec = O.run(pb, O.oracle_spots(spots), W.Scenario(), op, records=n)
+    t = np.mean(rec["fate"] != O.FATE_AP)
+    rb = O.csda_range(O.BRASS, energy) / 8.53          # mm: the range table is in g/cm^3 x mm, brass 8.53 g/cc
+    t_up = T_DN - THICK
+    r_t = r_ref * min(t_up + rb + sad, T_DN + sad) / (T_DN + sad)
+    ref = 1.0 - math.exp(-r_t * r_t / (2 * s * s))
+    assert abs(t - ref) < 4 * math.sqrt(ref * (1 - ref) / n) + 5e-4, (t, ref, rb)
+    # at 100 MeV (brass range ~14 mm) it differs from the parallel-wall block
+    # by much more than the noise; at 150 MeV the range nearly spans the block
+    par = 1.0 - math.exp(-r_ref * r_ref / (2 * s * s))
+    if energy < 120.0:
+        assert abs(par - ref) > 10 * math.sqrt(ref * (1 - ref) / n)
+    assert abs(tl["e_in"] - tl["e_dep"] - tl["e_ap"] - tl["e_leak"]) / tl["e_in"] < 1e-9
