@@ -63,9 +63,16 @@ typedef struct { int nx, ny, nz; double dx, dy, dz; double origin[3]; } vpmc_gri
  * plane is t = -source_to_iso_mm and must lie upstream of every device.
  * Range shifter: PMMA slab of water-equivalent thickness rs_wet_mm (geometric
  * thickness = rs_wet_mm / SPR_PMMA(150 MeV)) and radius rs_radius_mm.
- * Aperture: non-divergent brass block of thickness ap_thickness_mm whose
- * opening is the polygon poly_xy (n_vertices (u, v) pairs in mm, any
- * orientation, simple); at most 1024 vertices over all beams of a context. */
+ * Aperture: brass block of thickness ap_thickness_mm whose opening is the
+ * polygon poly_xy (n_vertices (u, v) pairs in mm, any orientation, simple)
+ * at the block's downstream face; at most 1024 vertices over all beams of a
+ * context.  ap_sad_mm = 0: walls parallel to the beam axis (Sec. 2.B).
+ * ap_sad_mm > 0: divergent walls (the authors' next step, Sec. 4): each wall
+ * is the plane through the virtual source at t = -ap_sad_mm on the beam
+ * axis and one polygon edge, so the opening at depth t is the polygon
+ * scaled by (t + ap_sad_mm) / (t_dn + ap_sad_mm); the source must lie
+ * upstream of the block.  The learned aperture surrogate (vpmc_opts.surrogate)
+ * is trained on parallel walls and is refused for divergent blocks. */
 typedef struct {
     double dir[3], bev_x[3], iso[3];
     double source_to_iso_mm;
@@ -75,6 +82,7 @@ typedef struct {
     double ap_thickness_mm, ap_down_to_iso_mm;
     const double* poly_xy;
     int n_vertices;
+    double ap_sad_mm;
 } vpmc_beam;
 
 /* One pencil-beam spot (Sec. 2.D.2): mono-energetic (energy_mev <= 250),

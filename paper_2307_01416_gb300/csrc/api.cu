@@ -197,6 +197,19 @@ vpmc_status check_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots)
     return VPMC_OK;
 }
 
+// The learned aperture surrogate is trained on parallel walls: refuse it for
+// spots of a beam with a divergent block.
+vpmc_status check_surrogate_walls(const vpmc_ctx* c, const vpmc_spot* spots, int n_spots, int surrogate)
+{
+    if (!surrogate) return VPMC_OK;
+    for (int i = 0; i < n_spots; ++i) {
+        const DevBeam& b = c->beams[spots[i].beam];
+        if (b.ap && b.ap_sad > 0.0f)
+            return fail(VPMC_ERR_ARG, "beam %d: the surrogate models parallel aperture walls only", spots[i].beam);
+    }
+    return VPMC_OK;
+}
+
 vpmc_status check_opts(const vpmc_opts* o)
 {
     if (!o) return VPMC_OK;
@@ -578,15 +591,33 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
         poly.assign(b->poly_xy, b->poly_xy + 2 * b->n_vertices);
         for (double x : poly)
             if (!std::isfinite(x)) return fail(VPMC_ERR_ARG, "aperture polygon has a non-finite vertex");
-        ras.resize(kRaster * kRaster);
-        ras_lb.resize(kRaster * kRaster);
-        // range rejection needs wall distances up to half the block thickness only
-        build_raster(poly.data(), b->n_vertices, 0.5 * b->ap_thickness_mm + 1.0, ras.data(), ras_lb.data(), d.ras_lo,
-                     d.ras_inv, &d.ras_diag);
-        d.nvert = b->n_vertices;
         double rc = 0.0;
         for (int i = 0; i < b->n_vertices; ++i) rc = std::max(rc, std::hypot(poly[2 * i], poly[2 * i + 1]));
         d.r_circ = (float)rc;
+        // divergent walls: the raster is in the downstream face's (projected)
+        // coordinates, where a real distance is the projected one x the scale
+        // at that depth (>= the entrance's) x the cosine of the wall tilt
+        double margin_scale = 1.0;
+        if (!(b->ap_sad_mm >= 0.0) || !std::isfinite(b->ap_sad_mm)) return fail(VPMC_ERR_ARG, "ap_sad_mm must be >= 0");
+        if (b->ap_sad_mm > 0.0) {
+            const double K = -b->ap_down_to_iso_mm + b->ap_sad_mm;
+            const double k_up = -b->ap_down_to_iso_mm - b->ap_thickness_mm + b->ap_sad_mm;
+            if (!(k_up > 0.0)) return fail(VPMC_ERR_ARG, "the virtual source must lie upstream of the aperture");
+            d.ap_sad = (float)b->ap_sad_mm;
+            d.ap_K = (float)K;
+            d.ap_cos = (float)(K / std::sqrt(K * K + rc * rc));
+            margin_scale = 1.0 / ((k_up / K) * (K / std::sqrt(K * K + rc * rc)));
+        } else {
+            d.ap_sad = 0.0f;
+            d.ap_K = 1.0f;
+            d.ap_cos = 1.0f;
+        }
+        ras.resize(kRaster * kRaster);
+        ras_lb.resize(kRaster * kRaster);
+        // range rejection needs wall distances up to half the block thickness only
+        build_raster(poly.data(), b->n_vertices, (0.5 * b->ap_thickness_mm + 1.0) * margin_scale, ras.data(),
+                     ras_lb.data(), d.ras_lo, d.ras_inv, &d.ras_diag);
+        d.nvert = b->n_vertices;
     }
     if (first_device < 1e300 && !(-b->source_to_iso_mm < first_device))
         return fail(VPMC_ERR_ARG, "source plane must lie upstream of every device");
@@ -627,6 +658,8 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
     if (st != VPMC_OK) return st;
     if (o.surrogate && !c->sur_ready) return fail(VPMC_ERR_STATE, "surrogate requested before its weights were set");
     st = check_spots(c, spots, n_spots);
+    if (st != VPMC_OK) return st;
+    st = check_surrogate_walls(c, spots, n_spots, o.surrogate);
     if (st != VPMC_OK) return st;
     DevScen sc{{0.0f, 0.0f, 0.0f}, 1.0f};
     if (scen) {
@@ -817,6 +850,8 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     if (st != VPMC_OK) return st;
     if (o.surrogate && !c->sur_ready) return fail(VPMC_ERR_STATE, "surrogate requested before its weights were set");
     st = check_spots(c, spots, n_spots);
+    if (st != VPMC_OK) return st;
+    st = check_surrogate_walls(c, spots, n_spots, o.surrogate);
     if (st != VPMC_OK) return st;
     if (n_spots == 0) return fail(VPMC_ERR_ARG, "no spots");
     for (int i = 1; i < n_spots; ++i)
@@ -1398,8 +1433,8 @@ vpmc_status vpmc_surrogate_tracks(vpmc_ctx* c, const int* beam_ids, int n_beams,
     for (int g = 0; g < n_beams; ++g) {
         const int b = beam_ids[g];
         if (b < 0 || b >= kMaxBeams || !c->beam_set[b]) return fail(VPMC_ERR_STATE, "beam %d is not set", b);
-        if (!c->beams[b].ap || c->beams[b].rs)
-            return fail(VPMC_ERR_ARG, "beam %d: training tracks need an aperture and no range shifter", b);
+        if (!c->beams[b].ap || c->beams[b].rs || c->beams[b].ap_sad > 0.0f)
+            return fail(VPMC_ERR_ARG, "beam %d: training tracks need a parallel-wall aperture and no range shifter", b);
         DevItem it{};
         it.hist_off = (long long)g * tracks_per_beam;
         it.spot = g;

@@ -795,6 +795,10 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
         bool down = true;
         bool ap_pending = false, was_forced = false, at_entry = false, need_pip = false;
         int cls = 0, q_off = 0, q_n = 0;
+        // opening coordinates: the point projected from the virtual source onto
+        // the downstream face (divergent walls; the point itself for parallel
+        // walls) and the opening's scale at the point's depth
+        float pu = 0.0f, pv = 0.0f, sc = 1.0f;
         if (alive) {
             const DevItem& I = P.items[L.item];
             const DevBeam& B = beams[__ldg(&I.beam)];
@@ -811,24 +815,44 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                 ap_pending = true;
                 was_forced = L.forced > 0;
                 at_entry = L.forced < 0;
-                cls = was_forced ? 0 : raster_class(B, P.raster, L.p[0], L.p[1]);
+                pu = L.p[0];
+                pv = L.p[1];
+                if (B.ap_sad > 0.0f) {
+                    sc = (L.p[2] + B.ap_sad) / B.ap_K;
+                    const float inv = 1.0f / sc;
+                    pu *= inv;
+                    pv *= inv;
+                }
+                cls = was_forced ? 0 : raster_class(B, P.raster, pu, pv);
                 need_pip = cls == 2;
                 q_off = B.poly_off;
                 q_n = B.nvert;
             }
         }
         // ---- exact opening test for lanes near an edge (warp-cooperative) ----
-        const bool pip_in = coop_point_in_polygon(need_pip, L.p[0], L.p[1], poly, q_off, q_n, lane);
+        const bool pip_in = coop_point_in_polygon(need_pip, pu, pv, poly, q_off, q_n, lane);
         bool open = false, need_hit = false, need_dist = false, absorb = false;
         float rmax = 0.0f;
+        // flight direction in opening coordinates: along p + s d the projected
+        // point moves as q(0) + g(s) (hx, hy) with g(s) = s c / (c + s d_t),
+        // c = t + sad (parallel walls: g = s and (hx, hy) = d_xy)
+        float hx = L.d[0], hy = L.d[1], cdiv = 0.0f;
         if (ap_pending) {
             const DevBeam& B = beams[__ldg(&P.items[L.item].beam)];
             open = cls == 1 || (cls == 2 && pip_in);
             if (open) {
-                // a flight whose lateral travel stays below the wall-distance bound of
-                // its start cell cannot meet a wall
-                const float lat = s_geom * sqrtf(L.d[0] * L.d[0] + L.d[1] * L.d[1]);
-                need_hit = !(lat < wall_lower_bound(B, P.raster_lb, L.p[0], L.p[1]));
+                float g_exit = s_geom;
+                if (B.ap_sad > 0.0f) {
+                    cdiv = L.p[2] + B.ap_sad;
+                    const float f = B.ap_K / (cdiv * cdiv);
+                    hx = f * (L.d[0] * cdiv - L.p[0] * L.d[2]);
+                    hy = f * (L.d[1] * cdiv - L.p[1] * L.d[2]);
+                    g_exit = s_geom * cdiv / (cdiv + s_geom * L.d[2]);
+                }
+                // a flight whose lateral travel (opening coordinates) stays below the
+                // wall-distance bound of its start cell cannot meet a wall
+                const float lat = g_exit * sqrtf(hx * hx + hy * hy);
+                need_hit = !(lat < wall_lower_bound(B, P.raster_lb, pu, pv));
             } else if (P.range_rejection && !was_forced) {
                 // a proton whose longest possible remaining path (1.2 x its residual
                 // CSDA range) cannot reach the opening or a face of the block is
@@ -836,14 +860,16 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                 rmax = 1.2f * L.R * __fdividef(1.0f, brass.rho);
                 const float dpl = fminf(L.p[2] - B.ap_tup, B.ap_tdn - L.p[2]);
                 if (rmax < dpl) {
-                    const float fx = (L.p[0] - B.ras_lo[0]) * B.ras_inv[0];
-                    const float fy = (L.p[1] - B.ras_lo[1]) * B.ras_inv[1];
+                    const float fx = (pu - B.ras_lo[0]) * B.ras_inv[0];
+                    const float fy = (pv - B.ras_lo[1]) * B.ras_inv[1];
                     if (!(fx >= 0.0f && fx < (float)kRaster && fy >= 0.0f && fy < (float)kRaster)) {
                         absorb = true;              // beyond the raster: farther than half the thickness
                     } else {
-                        const float lb = __ldg(P.raster_lb + B.ras_off + (int)fy * kRaster + (int)fx);
+                        // real distances: opening-coordinate ones x scale x cos(largest tilt)
+                        const float to_real = sc * B.ap_cos;
+                        const float lb = __ldg(P.raster_lb + B.ras_off + (int)fy * kRaster + (int)fx) * to_real;
                         if (rmax < lb) absorb = true;
-                        else if (rmax < lb + B.ras_diag) need_dist = true;
+                        else if (rmax < lb + B.ras_diag * to_real) need_dist = true;
                     }
                 }
             }
@@ -921,8 +947,14 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             }
         }
         // ---- exact wall hit and wall distance (warp-cooperative) ----
-        const float sw = coop_first_wall_hit(need_hit, L.p[0], L.p[1], L.d[0], L.d[1], poly, q_off, q_n, lane);
-        const float dw = coop_wall_distance(need_dist, L.p[0], L.p[1], poly, q_off, q_n, lane);
+        float sw = coop_first_wall_hit(need_hit, pu, pv, hx, hy, poly, q_off, q_n, lane);
+        const float dw = coop_wall_distance(need_dist, pu, pv, poly, q_off, q_n, lane) * sc *
+                         (ap_pending ? beams[__ldg(&P.items[L.item].beam)].ap_cos : 1.0f);
+        if (cdiv > 0.0f && isfinite(sw)) {
+            // back from g to the path length: s = g c / (c - g d_t)
+            const float den = cdiv - sw * L.d[2];
+            sw = den > 0.0f ? sw * cdiv / den : __int_as_float(0x7f800000);
+        }
         if (alive) {
             const DevItem& I = P.items[L.item];
             const DevBeam& B = beams[__ldg(&I.beam)];

@@ -50,6 +50,9 @@ struct DevBeam {
     int ras_off;                     // offset into the raster arrays (class bytes, distance bounds)
     float ras_diag;                  // raster cell diagonal
     float r_circ;                    // largest vertex distance from the beam axis (training tracks)
+    float ap_sad;                    // divergent walls: virtual source at t = -ap_sad (0: parallel walls)
+    float ap_K;                      // ap_tdn + ap_sad: opening scale at depth t = (t + ap_sad) / ap_K
+    float ap_cos;                    // cosine of the largest wall tilt (1 for parallel walls)
 };
 
 struct DevScen {

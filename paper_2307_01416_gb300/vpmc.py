@@ -46,7 +46,7 @@ class vpmc_beam(C.Structure):
                 ("rs_present", C.c_int), ("rs_wet_mm", C.c_double), ("rs_radius_mm", C.c_double),
                 ("rs_down_to_iso_mm", C.c_double),
                 ("ap_present", C.c_int), ("ap_thickness_mm", C.c_double), ("ap_down_to_iso_mm", C.c_double),
-                ("poly_xy", C.POINTER(C.c_double)), ("n_vertices", C.c_int)]
+                ("poly_xy", C.POINTER(C.c_double)), ("n_vertices", C.c_int), ("ap_sad_mm", C.c_double)]
 
 
 class vpmc_spot(C.Structure):
@@ -221,7 +221,8 @@ class Engine:
         s = vpmc_beam((C.c_double * 3)(*b.direction), (C.c_double * 3)(*b.bev_x), (C.c_double * 3)(*b.iso),
                       float(b.source_to_iso), int(b.rs_present), float(b.rs_wet), float(b.rs_radius),
                       float(b.rs_down_to_iso), int(b.ap_present), float(b.ap_thickness), float(b.ap_down_to_iso),
-                      poly.ctypes.data_as(C.POINTER(C.c_double)) if poly is not None else None, nv)
+                      poly.ctypes.data_as(C.POINTER(C.c_double)) if poly is not None else None, nv,
+                      float(getattr(b, "ap_sad", 0.0)))
         _check(lib().vpmc_set_aperture(self._ctx, int(beam_id), C.byref(s)))
 
     def run_spots(self, spots: np.ndarray, scenario: Optional[W.Scenario] = None, opts: Optional[W.Options] = None,
