@@ -61,7 +61,7 @@ def test_divergence_changes_the_transmission(torch_cuda):
 
 
 def test_divergent_aperture_full_physics_statistical(torch_cuda):
-    pb, spots = _divergent_case(300.0, True, hist_per_layer=6000, max_layers=2, shape=(50, 50, 100))
+    pb, spots = _divergent_case(300.0, True, opening=20.0, hist_per_layer=6000, max_layers=2, shape=(50, 50, 100))
     frac3, zmax, gam, nsel = _statistical_parity(pb, spots, 3000, 7000)
     assert nsel > 200
     assert frac3 <= 0.005 and zmax < 5.0, (frac3, zmax)
