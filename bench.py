@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-aperture leg")
     ap.add_argument("--no-optimizer", action="store_true", help="skip the robust-optimisation leg")
     ap.add_argument("--no-edge-sweep", action="store_true", help="skip the single-beamlet edge sweep leg")
+    ap.add_argument("--no-divergent", action="store_true", help="skip the divergent-aperture leg")
+    ap.add_argument("--divergent-sad", type=float, default=2000.0)
     ap.add_argument("--edge-hist", type=int, default=1_000_000, help="histories per beamlet of the edge sweep")
     ap.add_argument("--opt-iterations", type=int, default=50)
     ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im", "opt"], default=None,
@@ -325,6 +327,9 @@ def main():
         edge = None
         if not args.no_edge_sweep and world == 1:
             edge = edge_sweep_leg(args, peak_tops)
+        div = None
+        if not args.no_divergent and world == 1:
+            div = divergent_leg(pb, spots, scens, opts, args, value, peak_tops)
         sur = None
         if not args.no_surrogate and world == 1 and not args.small:
             sur = surrogate_leg(pb, spots, scens, opts, args, value)
@@ -339,7 +344,7 @@ def main():
                           "parallelism": "independent sets per GPU" if world > 1 else "1 GPU"},
                "s_per_im_set": ms_per_step / 1000.0,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
-               "surrogate": sur, "optimizer": opt, "edge_sweep": edge}
+               "surrogate": sur, "optimizer": opt, "edge_sweep": edge, "divergent_aperture": div}
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
@@ -606,6 +611,42 @@ def edge_sweep_leg(args, peak_tops):
             "value": out[best]["value"], "s_per_sweep": out[best]["s_per_sweep"], "best": best, **out,
             "note": "97 energies 71.3-228.8 MeV x (AP, APRS), beamlet on the rim of a 1 cm opening in 30 mm "
                     "brass, water 40x40x350 mm at 1 mm; parity vs the oracle in tests/test_gpu_edge_sweep.py"}
+
+
+def divergent_leg(pb, spots, scens, opts, args, plain_value, peak_tops):
+    """The same 13-scenario set with divergent aperture walls (virtual source
+    args.divergent_sad mm upstream of the isocentre; the polygons are the
+    openings at the blocks' downstream faces): one untimed and one timed set."""
+    import copy
+    import torch
+    from paper_2307_01416_gb300 import vpmc
+    dpb = copy.deepcopy(pb)
+    for b in dpb.beams:
+        b.ap_sad = float(args.divergent_sad)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        eng = vpmc.Engine(dpb, stream=stream)
+        mats, _ = eng.influence_matrix(spots, scens, opts)
+        del mats
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        mats, st = eng.influence_matrix(spots, scens, opts)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1000.0
+        nnz = sum(int(m["val"].numel()) for m in mats)
+        del mats
+        eng.close()
+    achieved = st["steps"] * OPS_PER_STEP / (st["ms"] / 1000.0) / 1e12
+    return {"sad_mm": float(args.divergent_sad), "value": st["histories"] / t, "unit": "protons/s",
+            "s_per_im_set": t, "relative_to_parallel": st["histories"] / t / plain_value, "nnz_per_set": nnz,
+            "gpu_launches": st["launches"] + 1,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                         "frac": achieved / peak_tops, "kernel": "k_source_rs+k_aperture+k_patient"},
+            "note": "same workload and seeds as the main line, divergent brass walls; parity vs the oracle in "
+                    "tests/test_gpu_divergent.py"}
 
 
 def e2e_leg(pb, spots, scens, opts, args):
