@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--no-optimizer", action="store_true", help="skip the robust-optimisation leg")
     ap.add_argument("--no-edge-sweep", action="store_true", help="skip the single-beamlet edge sweep leg")
     ap.add_argument("--no-divergent", action="store_true", help="skip the divergent-aperture leg")
+    ap.add_argument("--no-dynamic", action="store_true", help="skip the energy-layer-specific aperture leg")
     ap.add_argument("--divergent-sad", type=float, default=2000.0)
     ap.add_argument("--edge-hist", type=int, default=1_000_000, help="histories per beamlet of the edge sweep")
     ap.add_argument("--opt-iterations", type=int, default=50)
@@ -330,6 +331,9 @@ def main():
         div = None
         if not args.no_divergent and world == 1:
             div = divergent_leg(pb, spots, scens, opts, args, value, peak_tops)
+        dyn = None
+        if not args.no_dynamic and world == 1:
+            dyn = dynamic_leg(scens, opts, value, peak_tops)
         sur = None
         if not args.no_surrogate and world == 1 and not args.small:
             sur = surrogate_leg(pb, spots, scens, opts, args, value)
@@ -344,7 +348,8 @@ def main():
                           "parallelism": "independent sets per GPU" if world > 1 else "1 GPU"},
                "s_per_im_set": ms_per_step / 1000.0,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
-               "surrogate": sur, "optimizer": opt, "edge_sweep": edge, "divergent_aperture": div}
+               "surrogate": sur, "optimizer": opt, "edge_sweep": edge, "divergent_aperture": div,
+               "dynamic_aperture": dyn}
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
@@ -647,6 +652,40 @@ def divergent_leg(pb, spots, scens, opts, args, plain_value, peak_tops):
                          "frac": achieved / peak_tops, "kernel": "k_source_rs+k_aperture+k_patient"},
             "note": "same workload and seeds as the main line, divergent brass walls; parity vs the oracle in "
                     "tests/test_gpu_divergent.py"}
+
+
+def dynamic_leg(scens, opts, plain_value, peak_tops):
+    """The 13-scenario set with energy-layer-specific apertures: the same
+    spots and histories, one beam entry per (field, layer) whose opening is
+    the target's cross-section at the layer's depth plus 5 mm (36 entries):
+    one untimed and one timed set."""
+    import torch
+    from paper_2307_01416_gb300 import vpmc
+    pb, spots, _, _ = W.head_plan(8.4, dynamic_aperture=True)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        eng = vpmc.Engine(pb, stream=stream)
+        mats, _ = eng.influence_matrix(spots, scens, opts)
+        del mats
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        mats, st = eng.influence_matrix(spots, scens, opts)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1000.0
+        nnz = sum(int(m["val"].numel()) for m in mats)
+        del mats
+        eng.close()
+    achieved = st["steps"] * OPS_PER_STEP / (st["ms"] / 1000.0) / 1e12
+    return {"beam_entries": len(pb.beams), "value": st["histories"] / t, "unit": "protons/s", "s_per_im_set": t,
+            "relative_to_static": st["histories"] / t / plain_value, "nnz_per_set": nnz,
+            "e_aperture_fraction": st["e_aperture"] / st["e_in"], "gpu_launches": st["launches"] + 1,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                         "frac": achieved / peak_tops, "kernel": "k_source_rs+k_aperture+k_patient"},
+            "note": "same spots, histories and seeds as the main line; per-layer openings; parity vs the oracle "
+                    "in tests/test_gpu_dynamic_aperture.py"}
 
 
 def e2e_leg(pb, spots, scens, opts, args):

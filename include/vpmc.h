@@ -65,7 +65,7 @@ typedef struct { int nx, ny, nz; double dx, dy, dz; double origin[3]; } vpmc_gri
  * thickness = rs_wet_mm / SPR_PMMA(150 MeV)) and radius rs_radius_mm.
  * Aperture: brass block of thickness ap_thickness_mm whose opening is the
  * polygon poly_xy (n_vertices (u, v) pairs in mm, any orientation, simple)
- * at the block's downstream face; at most 1024 vertices over all beams of a
+ * at the block's downstream face; at most 4096 vertices over all beams of a
  * context.  ap_sad_mm = 0: walls parallel to the beam axis (Sec. 2.B).
  * ap_sad_mm > 0: divergent walls (the authors' next step, Sec. 4): each wall
  * is the plane through the virtual source at t = -ap_sad_mm on the beam
@@ -172,9 +172,13 @@ void vpmc_default_opts(vpmc_opts* opts);
 vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_device, const vpmc_grid* ct,
                                  const vpmc_hu_curve* curve, const vpmc_grid* dose_grid, void* cuda_stream);
 
-/* Set field beam_id (0..15) (Sec. 2.B: range shifter and aperture geometry,
- * crossing-number opening).  Copies the polygon and builds its BEV
- * classification raster.  Synchronous. */
+/* Set beam entry beam_id (0..63) (Sec. 2.B: range shifter and aperture
+ * geometry, crossing-number opening).  Copies the polygon and builds its BEV
+ * classification raster.  Synchronous.  An energy-layer-specific (dynamic)
+ * aperture (the authors' future work, Sec. 4) is one entry per (field,
+ * energy layer): the same field geometry with that layer's opening, the
+ * layer's spots referring to it; spots must be sorted by entry for
+ * vpmc_influence_matrix. */
 vpmc_status vpmc_set_aperture(vpmc_ctx* ctx, int beam_id, const vpmc_beam* beam);
 
 /* Dose of a set of spots in one scenario (Sec. 2.C, 2.D): transports every

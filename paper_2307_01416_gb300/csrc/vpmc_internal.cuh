@@ -13,9 +13,9 @@ constexpr int kNR = 4096;            // uniform residual-range grid
 constexpr int kNMat = 3;             // 0 water (patient media, SPR-scaled), 1 PMMA, 2 brass
 constexpr int kHULo = -1024;
 constexpr int kNHU = 4096;           // HU -1024..3071
-constexpr int kMaxBeams = 16;
+constexpr int kMaxBeams = 64;            // beam entries: fields, or (field, energy layer) pairs
 constexpr int kMaxScen = 64;
-constexpr int kMaxPolyVerts = 1024;
+constexpr int kMaxPolyVerts = 4096;
 constexpr int kRaster = 256;         // BEV raster per beam (cells per side): opening class, wall-distance bound
 constexpr float kEcut = 0.5f;        // MeV
 constexpr int kMaxIter = 200000;     // iterations per history before it is stopped as an error

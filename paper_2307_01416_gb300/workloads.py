@@ -368,11 +368,19 @@ def radiological_depths(g: Grid, hu: np.ndarray, curve: HUCurve, start, directio
 
 def head_plan(volume_cc: float = 8.4, ct_seed: int = 1234, target_seed: int = 1235, gantries=(0.0, 90.0, 270.0),
               range_shifter: bool = True, spot_spacing: float = 3.0, margin_mm: float = 5.0, n_vertices: int = 64,
-              hist_lo: int = 1000, hist_hi: int = 20000, hist_seed: int = 77, scoring_mm: float = 2.0):
+              hist_lo: int = 1000, hist_hi: int = 20000, hist_seed: int = 77, scoring_mm: float = 2.0,
+              dynamic_aperture: bool = False, ap_sad: float = 0.0):
     """Three-field SRS plan on the synthetic head: apertures = target projection
     + margin (regular n-gon), 45 mm WET range shifter, spots on a 3 mm grid over
     the opening, layers 3 mm WET apart covering the target depth +/- 5 mm,
-    n_hist per spot log-uniform in [hist_lo, hist_hi]."""
+    n_hist per spot log-uniform in [hist_lo, hist_hi].
+
+    dynamic_aperture (the authors' future work, Sec. 4): one beam entry per
+    (field, energy layer) with the field's geometry and its own opening: the
+    target's cross-section at the depth of the layer's range (water-equivalent
+    range minus the shifter's, mapped to depth along the central ray) plus
+    the margin.  Spots and histories are those of the static plan; each
+    refers to its layer's entry.  ap_sad > 0 makes every block divergent."""
     g, hu, _ = head_ct(ct_seed)
     center, r_t = head_target(volume_cc, target_seed)
     ext = [g.shape[i] * g.spacing[i] for i in range(3)]
@@ -402,11 +410,21 @@ def head_plan(volume_cc: float = 8.4, ct_seed: int = 1234, target_seed: int = 12
         e_hi = min(max(e_hi, e_lo), 230.0)
         energies = layer_energies(e_lo, e_hi, 3.0)
         xy = grid_spots_in_disk(r_open + spot_spacing, spot_spacing)
+        bm.ap_sad = float(ap_sad)
+        if dynamic_aperture:
+            beams.pop()
         for e in energies:
             nh = np.exp(rng.uniform(np.log(hist_lo), np.log(hist_hi), size=len(xy))).astype(np.int64)
             sig = float(spot_sigma_mm(e))
+            entry = bi
+            if dynamic_aperture:
+                depth = float(np.interp(float(bk_range_for_energy(e)) - rs, wet, s))     # along the central ray
+                dz = depth - 200.0                                                     # from the target centre
+                r_layer = math.sqrt(max(r_t * r_t - dz * dz, 0.0)) + margin_mm
+                beams.append(dataclasses.replace(bm, polygon=regular_polygon(r_layer, n_vertices)))
+                entry = len(beams) - 1
             for (x, y), n in zip(xy, nh):
-                rows.append((bi, float(e), float(x), float(y), sig, 2.0, int(n), 1.0))
+                rows.append((entry, float(e), float(x), float(y), sig, 2.0, int(n), 1.0))
     pb = Problem(ct=g, hu=hu, curve=curve, scoring=sg, beams=beams)
     return pb, make_spots(rows), center, r_t
 

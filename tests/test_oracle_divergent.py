@@ -138,3 +138,24 @@ def test_parallel_beam_transmission_through_a_growing_opening(energy):
     if energy < 120.0:
         assert abs(par - ref) > 10 * math.sqrt(ref * (1 - ref) / n)
     assert abs(tl["e_in"] - tl["e_dep"] - tl["e_ap"] - tl["e_leak"]) / tl["e_in"] < 1e-9
+
+
+def test_dynamic_aperture_plan_entries():
+    """The dynamic head plan: one entry per (field, layer) sharing the field's
+    geometry; openings never wider than the static one, equal to it at the
+    target's widest cross-section and the bare margin beyond its depth; the
+    same spots and histories as the static plan, sorted by entry."""
+    pb, sp, c, r_t = W.head_plan(8.4)
+    pd, sd, _, _ = W.head_plan(8.4, dynamic_aperture=True)
+    assert np.array_equal(sp["n_hist"], sd["n_hist"]) and np.array_equal(sp["energy"], sd["energy"])
+    assert np.all(np.diff(sd["beam"]) >= 0) and len(pd.beams) == len(np.unique(sd["beam"]))
+    r_static = r_t + 5.0
+    radii = np.array([np.hypot(b.polygon[:, 0], b.polygon[:, 1]).max() for b in pd.beams])
+    assert radii.max() == pytest.approx(r_static, rel=2e-3) and np.all(radii <= r_static + 1e-9)
+    assert radii.min() == pytest.approx(5.0)
+    for b in pd.beams:
+        f = pb.beams[[np.allclose(b.direction, s.direction) for s in pb.beams].index(True)]
+        assert b.ap_thickness == f.ap_thickness and b.rs_present == f.rs_present and b.iso == f.iso
+    # the layer's entry: spots of one (field, energy) refer to one entry
+    for e in np.unique(sd["energy"]):
+        assert len(np.unique(sd["beam"][sd["energy"] == e])) <= 3
