@@ -450,7 +450,11 @@ typedef struct {
                            cosine below 0.01 |delta SPR| (the crossing point
                            moves by (position rounding) / cosine);
                            bit 4: a brass range-rejection test decided within
-                           ORC_TIE_MM of its threshold                      */
+                           ORC_TIE_MM of its threshold;
+                           bit 5: the end point is ill-conditioned: moving
+                           the start by ORC_COND_MM moves it by more than
+                           1e-4 of the track;
+                           bit 6: so are the fate or the scored energy      */
     int32_t pad;
     double path;        /* path length travelled in the patient grid, mm     */
     double track;       /* whole track length from the source plane, mm      */
@@ -607,7 +611,7 @@ typedef struct {
     const orc_scen* sc;
     const orc_opts* op;
     int mode;               /* 0 dose grid (weighted), 1 per-spot columns */
-    int64_t* q;             /* deposit target                             */
+    int64_t* q;             /* deposit target (NULL: score nothing)       */
     int64_t nvox;
 } orc_run_ctx;
 
@@ -707,7 +711,7 @@ static int aperture_block(const orc_beam* bm, const double* poly, orc_particle* 
 }
 
 static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_index, int64_t h,
-                              orc_record* rec, double* tl)
+                              orc_record* rec, double* tl, const double* shift)
 {
     const orc_problem* pb = rc->pb;
     const orc_beam* bm = &pb->beams[sp->beam];
@@ -729,6 +733,7 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
     stream_normals4(&st, 0u, 0u, z);
     double a0 = sp->x + sp->sigma * z[0];
     double b0 = sp->y + sp->sigma * z[1];
+    if (shift) { a0 += shift[0]; b0 += shift[1]; }
     double tha = sp->div_mrad * 1e-3 * z[2];
     double thb = sp->div_mrad * 1e-3 * z[3];
     double nrm = sqrt(1.0 + tha * tha + thb * thb);
@@ -877,10 +882,12 @@ static void transport_history(orc_run_ctx* rc, const orc_spot* sp, int spot_inde
             rec->track += so.s;
             /* score the step's deposit in the voxel where the step starts */
             {
-                int64_t q = (int64_t)nearbyint(so.dE * (rc->mode == 0 ? sp->weight : 1.0) * fscale);
-                int64_t* dst = rc->mode == 0 ? &rc->q[sidx] : &rc->q[(int64_t)spot_index * rc->nvox + sidx];
+                if (rc->q) {
+                    int64_t q = (int64_t)nearbyint(so.dE * (rc->mode == 0 ? sp->weight : 1.0) * fscale);
+                    int64_t* dst = rc->mode == 0 ? &rc->q[sidx] : &rc->q[(int64_t)spot_index * rc->nvox + sidx];
 #pragma omp atomic
-                *dst += q;
+                    *dst += q;
+                }
                 rec->e_dep += so.dE;
                 rec->q_dep += (int64_t)nearbyint(so.dE * fscale);
                 tl[1] += so.dE;
@@ -945,6 +952,31 @@ finish:
  *         the spot weight;  mode 1: q holds n_spots unweighted columns.
  * tally: ORC_NTALLY doubles (added to).  rec: optional per-history records
  * in spot order, history order; only the first rec_cap are written. */
+/* Conditioning of a recorded history: the same history (same random
+ * numbers) with its start moved by +-ORC_COND_MM along each BEV axis, scored
+ * nowhere.  A rounding-level change of the path that moves the end point by
+ * more than 1e-4 of the track (a face met at grazing incidence just before a
+ * change of material, a crossing order that flips) sets bit 5; one that
+ * changes the fate or the scored energy by more than 1e-4 sets bit 6. */
+#define ORC_COND_MM 2e-5
+static void condition_flags(const orc_run_ctx* rc, const orc_spot* sp, int spot_index, int64_t h, orc_record* r)
+{
+    orc_run_ctx dry = *rc;
+    dry.q = NULL;
+    static const double dirs[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+    for (int k = 0; k < 4; ++k) {
+        double tl[ORC_NTALLY] = {0};
+        double shift[2] = {ORC_COND_MM * dirs[k][0], ORC_COND_MM * dirs[k][1]};
+        orc_record p;
+        transport_history(&dry, sp, spot_index, h, &p, tl, shift);
+        double track = r->track > 1.0 ? r->track : 1.0;
+        double dx = p.pos[0] - r->pos[0], dy = p.pos[1] - r->pos[1], dz = p.pos[2] - r->pos[2];
+        if (sqrt(dx * dx + dy * dy + dz * dz) > 1e-4 * track) r->flags |= 32;
+        double escale = fabs(r->e_dep) > 1.0 ? fabs(r->e_dep) : 1.0;
+        if (p.fate != r->fate || fabs(p.e_dep - r->e_dep) > 1e-4 * escale) r->flags |= 64;
+    }
+}
+
 int orc_run(const orc_grid* ct, const int16_t* hu, const orc_curve* curve, const orc_grid* sg,
             const orc_beam* beams, const double* poly_xy,
             const orc_spot* spots, int n_spots, const orc_scen* sc, const orc_opts* op,
@@ -974,7 +1006,8 @@ int orc_run(const orc_grid* ct, const int16_t* hu, const orc_curve* curve, const
             const orc_spot* sp = &spots[lo];
             int64_t h = sp->h_begin + (gi - off[lo]);
             orc_record* r = (rec && gi < rec_cap) ? &rec[gi] : &tmp;
-            transport_history(&rc, sp, lo, h, r, tl);
+            transport_history(&rc, sp, lo, h, r, tl, NULL);
+            if (r != &tmp) condition_flags(&rc, sp, lo, h, r);
         }
 #pragma omp critical
         for (int i = 0; i < ORC_NTALLY; ++i) tally[i] += tl[i];
