@@ -69,54 +69,69 @@ def test_structure_threshold_and_energy(fullset):
 
 
 def test_columns_sum_to_the_dose(fullset):
-    """Nominal scenario: the columns x n_hist summed over the spots equal the
-    dose of the same spots and seed above 10 % of its maximum, to 1e-3 (the
-    dropped sub-threshold entries are below 1e-4 of their column maxima)."""
+    """Nominal scenario: with no entry dropped (threshold 0) the columns x
+    n_hist summed over the spots equal the dose of the same spots and seed to
+    1e-5 above 10 % of its maximum (measured 9e-8: FP32 rounding of the
+    column values); with the benchmark's threshold the sum stays below the
+    dose (only entries are dropped)."""
+    from paper_2307_01416_gb300 import vpmc
     pb, spots, scens, mats, st, dose = fullset
-    m = mats[0]
-    col = m["col"].cpu().numpy()
-    val = m["val"].cpu().numpy().astype(np.float64)
-    rows = np.repeat(np.arange(m["shape"][0]), np.diff(m["row_ptr"].cpu().numpy()))
-    s = np.zeros(m["shape"][0])
-    np.add.at(s, rows, val * spots["n_hist"][col].astype(np.float64))
+    eng = vpmc.Engine(pb)
+    exact, _ = eng.influence_matrix(spots, [scens[0]], W.Options(seed=SEED), rel_threshold=0.0)
+    eng.close()
     sel = dose >= 0.1 * dose.max()
     assert sel.sum() > 5000
-    assert np.max(np.abs(s[sel] - dose[sel]) / dose[sel]) < 1e-3
+    for m, tol_lo, tol_hi in ((exact[0], 1e-5, 1e-5), (mats[0], 0.05, 1e-5)):
+        col = m["col"].cpu().numpy()
+        val = m["val"].cpu().numpy().astype(np.float64)
+        rows = np.repeat(np.arange(m["shape"][0]), np.diff(m["row_ptr"].cpu().numpy()))
+        tot = np.zeros(m["shape"][0])
+        np.add.at(tot, rows, val * spots["n_hist"][col].astype(np.float64))
+        rel = (tot[sel] - dose[sel]) / dose[sel]
+        assert rel.min() > -tol_lo and rel.max() < tol_hi, (rel.min(), rel.max())
 
 
 def test_sampled_columns_against_the_oracle(fullset):
     """The columns of five spots in two scenarios, recomputed by the oracle
-    with the same seed and spot keys: the column's energy (dose x mass)
-    within 1e-2, and above 10 % of the column maximum the median voxel
-    within 1e-3 (the histories are the same draws; the few ill-conditioned
-    ones that diverge change a handful of voxels)."""
+    with the same seed and spot keys (the same random numbers), and with the
+    next seed (an independent sample): against the same-seed oracle the
+    column's energy (dose x mass) agrees to 1e-3 and, above 10 % of the
+    column maximum, the median voxel to 5e-3 and to a twentieth of the
+    independent sample's median difference.  Measured: energy within 4e-4,
+    medians 2e-7 to 2e-3, against 0.11 to 1.0 between independent samples."""
     pb, spots, scens, mats, st, _ = fullset
     rho = O.scoring_density(pb)
     vol = pb.scoring.voxel_mm3 * 1e-3
     idx = np.array(SAMPLE)
     sub = spots[idx]
     for s in SCEN_SAMPLE:
-        q, tl, _ = O.run(pb, O.oracle_spots(sub, spot_keys=idx), scens[s], W.Options(seed=SEED), mode=1)
-        d = q.astype(np.float64) * 2.0 ** -24 * O.MEV_PER_G_TO_GY / vol / rho[None, :]
-        d /= sub["n_hist"].astype(np.float64)[:, None]
+        ds = []
+        for seed in (SEED, SEED + 1):
+            q, tl, _ = O.run(pb, O.oracle_spots(sub, spot_keys=idx), scens[s], W.Options(seed=seed), mode=1)
+            d = q.astype(np.float64) * 2.0 ** -24 * O.MEV_PER_G_TO_GY / vol / rho[None, :]
+            ds.append(d / sub["n_hist"].astype(np.float64)[:, None])
         for k, j in enumerate(idx):
-            o = d[k]
+            o, o2 = ds[0][k], ds[1][k]
             if o.max() <= 0.0:
                 continue
             o = np.where(o >= 1e-4 * o.max(), o, 0.0)
+            o2 = np.where(o2 >= 1e-4 * o2.max(), o2, 0.0)
             g = _column(mats[s], int(j))
-            assert abs((g * rho).sum() / (o * rho).sum() - 1.0) < 1e-2, (s, j)
+            assert abs((g * rho).sum() / (o * rho).sum() - 1.0) < 1e-3, (s, j)
             sel = o >= 0.1 * o.max()
-            rel = np.abs(g[sel] - o[sel]) / o[sel]
-            assert np.median(rel) < 1e-3, (s, j, np.median(rel), np.percentile(rel, 95))
+            same = np.median(np.abs(g[sel] - o[sel]) / o[sel])
+            indep = np.median(np.abs(o2[sel] - o[sel]) / o[sel])
+            assert same < 5e-3 and same < 0.05 * indep, (s, j, same, indep)
 
 
 def test_sampled_histories_full_physics(fullset):
-    """The histories of the sampled spots (nominal scenario, full physics):
-    the scored energy of each history agrees with the oracle's to 1e-4 for
-    at least 97 % of them (the rest diverged after an ill-conditioned step
-    and are ordinary samples of the same distribution), and the fates of the
-    agreeing ones match."""
+    """The histories of the sampled spots (nominal scenario, full physics,
+    same random numbers as the oracle): fates agree for 99.9 %, scored
+    energies to 1e-4 for 99.5 %, end points to 1e-3 of the track for 95 %.
+    Measured: 99.99 %, 99.8 %, 97.3 %; 91 % keep the oracle's step count
+    exactly -- a step-count change (an FP32 tie of two step limits)
+    re-aligns every later draw, after which the history is an independent
+    sample of the same distribution."""
     from paper_2307_01416_gb300 import vpmc
     pb, spots, scens, mats, st, _ = fullset
     only = spots.copy()
@@ -129,7 +144,8 @@ def test_sampled_histories_full_physics(fullset):
     _, _, rec = eng.run_spots(only, scens[0], W.Options(seed=SEED), records=n)
     eng.close()
     _, _, orec = O.run(pb, O.oracle_spots(only), scens[0], W.Options(seed=SEED), records=n)
-    scale = np.maximum(np.abs(orec["e_dep"]), 1.0)
-    agree = np.abs(rec["e_dep"] - orec["e_dep"]) / scale < 1e-4
-    assert agree.mean() >= 0.97, agree.mean()
-    assert np.all(rec["fate"][agree] == orec["fate"][agree])
+    fate = rec["fate"] == orec["fate"]
+    energy = np.abs(rec["e_dep"] - orec["e_dep"]) / np.maximum(np.abs(orec["e_dep"]), 1.0) < 1e-4
+    pos = np.linalg.norm(rec["pos"] - orec["pos"], axis=1) / np.maximum(orec["track"], 1.0) < 1e-3
+    assert fate.mean() >= 0.999 and energy.mean() >= 0.995 and pos.mean() >= 0.95, (fate.mean(), energy.mean(),
+                                                                                   pos.mean())
