@@ -34,8 +34,12 @@ METRIC = "protons/s; s per 13-scenario influence-matrix set at 0.5% unc."
 WORKLOAD = ("13-scenario robust influence-matrix set, synthetic head 256x256x160 CT (1x1x1.5 mm), 2 mm scoring grid, "
             "8.4 cc target, 3 fields 0/90/270 deg, 45 mm WET range shifter, brass apertures (target + 5 mm), "
             "3 mm spots, 1e3-2e4 histories/spot")
-# Lane-operations of one condensed-history step of the full-physics method
-# (the model and its itemisation are stated in the design doc).
+# Lane-operations of one condensed-history step of the full-physics method,
+# counted for a minimal implementation of the step's formulas: one
+# Philox4x32-10 block 80, six uniforms 22, three Box-Muller pairs 24, four
+# table interpolations 32, step selection 12, two-grid DDA 33, Bohr 15,
+# Highland 10, rotation and displacement 45, scoring 11, position update and
+# voxel confinement 15.
 OPS_PER_STEP = 300
 L2_FLUSH_BYTES = 512 << 20
 
