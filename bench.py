@@ -40,7 +40,7 @@ WORKLOAD = ("13-scenario robust influence-matrix set, synthetic head 256x256x160
 # table interpolations 32, step selection 12, two-grid DDA 33, Bohr 15,
 # Highland 10, rotation and displacement 45, scoring 11, position update and
 # voxel confinement 15.
-OPS_PER_STEP = 300
+OPS_PER_STEP = 299
 L2_FLUSH_BYTES = 512 << 20
 
 
