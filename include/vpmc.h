@@ -118,6 +118,11 @@ typedef struct {
     int straggling;         /* Bohr straggling on/off                                     */
     int nuclear;            /* nuclear removal (1.2 %/cm x density) on/off                */
     int frac_bits;          /* fixed-point scale of deposits, 2^-frac_bits MeV (default 24) */
+    /* Autotuned launch: the first dose (or influence-matrix) call of a
+     * context times a few launch configurations on a sample of its
+     * histories; the choice is kept by the context and, for later contexts
+     * on the same device with the same grids, field devices and fixed launch
+     * options, by the process.  Results do not depend on the choice. */
     int aggregate;          /* -1 autotuned, 0 plain atomics, 1 warp-aggregated atomics   */
     int block_size;         /* 0 autotuned, else patient-kernel threads per block (multiple of 32, <= 768) */
     int blocks_per_sm;      /* 0 autotuned                                                */

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/vpmc.h"
@@ -402,6 +403,73 @@ vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc
     return VPMC_OK;
 }
 
+// Process-wide cache of tuned launch configurations.  The launch choices
+// change speed only (results are identical for every choice), so a context
+// whose device, grids, field devices and fixed launch options match an
+// earlier one reuses that tuning instead of timing ~30 launches again.
+struct TuneKey {
+    int device, kind;                 // kind 0: dose path, 1: influence matrices
+    int ct[3], sg[3];
+    unsigned long long fields;        // per set beam: range shifter, aperture, divergent walls, vertex count
+    int block, aggregate, chunk;      // launch options the caller fixed
+    bool operator==(const TuneKey& o) const
+    {
+        return device == o.device && kind == o.kind && ct[0] == o.ct[0] && ct[1] == o.ct[1] && ct[2] == o.ct[2] &&
+               sg[0] == o.sg[0] && sg[1] == o.sg[1] && sg[2] == o.sg[2] && fields == o.fields &&
+               block == o.block && aggregate == o.aggregate && chunk == o.chunk;
+    }
+};
+
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneResult>> g_tune_cache;
+
+TuneKey tune_key(const vpmc_ctx* c, int kind, const vpmc_opts& o)
+{
+    TuneKey k{};
+    k.device = c->device;
+    k.kind = kind;
+    for (int i = 0; i < 3; ++i) {
+        k.ct[i] = c->ctg.n[i];
+        k.sg[i] = c->sg.n[i];
+    }
+    unsigned long long h = 1469598103934665603ull;             // FNV-1a over the fields' device kinds
+    for (int b = 0; b < kMaxBeams; ++b) {
+        const unsigned long long v = !c->beam_set[b] ? 0ull
+                                     : 1ull | (unsigned long long)c->beams[b].rs << 1 |
+                                           (unsigned long long)c->beams[b].ap << 2 |
+                                           (unsigned long long)(c->beams[b].ap_sad > 0.0f) << 3 |
+                                           (unsigned long long)c->beams[b].nvert << 4;
+        h = (h ^ v) * 1099511628211ull;
+    }
+    k.fields = h;
+    k.block = o.block_size;
+    k.aggregate = o.aggregate;
+    k.chunk = o.chunk;
+    return k;
+}
+
+bool tune_cache_get(const TuneKey& k, TuneResult* out)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& e : g_tune_cache)
+        if (e.first == k) {
+            *out = e.second;
+            return true;
+        }
+    return false;
+}
+
+void tune_cache_put(const TuneKey& k, const TuneResult& t)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto& e : g_tune_cache)
+        if (e.first == k) {
+            e.second = t;
+            return;
+        }
+    g_tune_cache.emplace_back(k, t);
+}
+
 TuneResult resolve_launch(const vpmc_opts& o, const TuneResult& t)
 {
     TuneResult r = t;
@@ -722,9 +790,13 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
         if (st != VPMC_OK) return st;
         const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
         if (want_tune && !c->tune_dose.valid) {
-            st = autotune(c, p, &c->tune_dose, o);
-            if (st != VPMC_OK) return st;
-            CUDA_TRY(cudaMemsetAsync(c->d_acc, 0, c->nvox * sizeof(unsigned long long), c->stream));
+            const TuneKey key = tune_key(c, 0, o);
+            if (!tune_cache_get(key, &c->tune_dose)) {
+                st = autotune(c, p, &c->tune_dose, o);
+                if (st != VPMC_OK) return st;
+                CUDA_TRY(cudaMemsetAsync(c->d_acc, 0, c->nvox * sizeof(unsigned long long), c->stream));
+                tune_cache_put(key, c->tune_dose);
+            }
         }
         const TuneResult t = resolve_launch(o, c->tune_dose);
         st = reset_counters(c);
@@ -1017,10 +1089,14 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         p.ovf_count = d_ovf_count;
         const bool want_tune = o.block_size == 0 || o.aggregate < 0 || o.chunk == 0;
         if (want_tune && !c->tune_im.valid) {
-            p.ovf = c->d_ovf;
-            p.ovf_cap = c->ovf_cap;
-            IM_TRY(cudaMemsetAsync(d_ovf_count, 0, sizeof(unsigned long long), c->stream));
-            IM_ST(autotune(c, p, &c->tune_im, o));
+            const TuneKey key = tune_key(c, 1, o);
+            if (!tune_cache_get(key, &c->tune_im)) {
+                p.ovf = c->d_ovf;
+                p.ovf_cap = c->ovf_cap;
+                IM_TRY(cudaMemsetAsync(d_ovf_count, 0, sizeof(unsigned long long), c->stream));
+                IM_ST(autotune(c, p, &c->tune_im, o));
+                tune_cache_put(key, c->tune_im);
+            }
         }
         const TuneResult tr = resolve_launch(o, c->tune_im);
         unsigned long long n_ovf = 0;
