@@ -363,7 +363,7 @@ def main():
 
 def run_ncu_case(args):
     """Every 10th spot of the set's nominal scenario (about 3.3e6 histories,
-    full physics) with a fixed launch (k_source_rs 768 threads, k_aperture 512, k_patient 640,
+    full physics) with a fixed launch (k_source_rs 768 threads, k_aperture 512, k_patient 896,
     chunk 32): one launch of each transport kernel per step.  'dose' scores a
     16 MB grid (warp-aggregated atomics); 'im' scores the spots' influence-matrix
     columns (about 1 GB of column scratch, plain atomics), the bench's own
@@ -379,10 +379,10 @@ def run_ncu_case(args):
     opts = W.Options(seed=1234)
     for i in range(args.warmup + args.steps):
         if args.ncu_case == "im":
-            mats, st = eng.influence_matrix(sub, [W.Scenario()], opts, block_size=640, aggregate=0, chunk=32)
+            mats, st = eng.influence_matrix(sub, [W.Scenario()], opts, block_size=896, aggregate=0, chunk=32)
             del mats
         else:
-            dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=640, aggregate=1, chunk=32)
+            dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=896, aggregate=1, chunk=32)
         print(json.dumps({"case": "ncu-" + args.ncu_case, "iter": i, "histories": st["histories"],
                           "steps": st["steps"], "kernel_ms": st["ms"],
                           "steps_per_s": st["steps"] / (st["ms"] / 1000.0)}))

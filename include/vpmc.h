@@ -124,7 +124,7 @@ typedef struct {
      * on the same device with the same grids, field devices and fixed launch
      * options, by the process.  Results do not depend on the choice. */
     int aggregate;          /* -1 autotuned, 0 plain atomics, 1 warp-aggregated atomics   */
-    int block_size;         /* 0 autotuned, else patient-kernel threads per block (multiple of 32, <= 768) */
+    int block_size;         /* 0 autotuned, else patient-kernel threads per block (multiple of 32, <= 896) */
     int blocks_per_sm;      /* 0 autotuned                                                */
     int chunk;              /* histories taken per warp refill (0 = default)              */
     vpmc_history_record* history_out;  /* device buffer or NULL                          */

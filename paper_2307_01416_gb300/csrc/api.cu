@@ -215,8 +215,9 @@ vpmc_status check_opts(const vpmc_opts* o)
 {
     if (!o) return VPMC_OK;
     if (o->frac_bits < 0 || o->frac_bits > 40) return fail(VPMC_ERR_ARG, "frac_bits %d outside [0, 40]", o->frac_bits);
-    if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 768 || o->block_size % 32))
-        return fail(VPMC_ERR_ARG, "block_size %d: must be 0 or a multiple of 32 in [32, 768]", o->block_size);
+    if (o->block_size != 0 && (o->block_size < 32 || o->block_size > patient_max_block() || o->block_size % 32))
+        return fail(VPMC_ERR_ARG, "block_size %d: must be 0 or a multiple of 32 in [32, %d]", o->block_size,
+                    patient_max_block());
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 1)
         return fail(VPMC_ERR_ARG, "blocks_per_sm %d: the kernel's shared memory allows one block per SM", o->blocks_per_sm);
     if (o->chunk < 0 || o->chunk > 4096) return fail(VPMC_ERR_ARG, "chunk %d outside [0, 4096]", o->chunk);
@@ -230,6 +231,7 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
 {
     TransportParams p{};
     p.tables = c->d_tables;
+    p.water = c->water_mat;
     p.ct = c->d_ct;
     p.ctg = c->ctg;
     p.sg = c->sg;
@@ -381,10 +383,10 @@ vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc
     // patient kernel on the histories the last devices launch handed over
     t_best = 1e30f;
     for (int rep = 0; rep < 2; ++rep)
-        for (int block : {512, 640, 768})
+        for (int block : {512, 640, 768, 896})
             for (int agg : {0, 1})
                 for (int chunk : {32, 128}) {
-                    if (o.block_size && block != o.block_size) continue;
+                    if (block > patient_max_block() || (o.block_size && block != o.block_size)) continue;
                     if (o.aggregate >= 0 && agg != o.aggregate) continue;
                     if (o.chunk && chunk != o.chunk) continue;
                     p.aggregate = agg;
@@ -588,6 +590,7 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     std::vector<unsigned char> img_bytes(sizeof(TablesImage));
     TablesImage* img = reinterpret_cast<TablesImage*>(img_bytes.data());
     build_tables(c->curve15, img);
+    c->water_mat = img->mat[kWater];
     CTX_TRY(dev_alloc(&c->d_tables, 1));
     CTX_TRY(cudaMemcpyAsync(c->d_tables, img, sizeof(TablesImage), cudaMemcpyHostToDevice, c->stream));
     CTX_TRY(dev_alloc(&c->d_curve, 15));
@@ -1084,6 +1087,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         p.n_scen = n_scen;
         p.total = total;
         p.scratch = c->d_scratch;
+        p.unit_weight = 1;              // every item's wscale is 2^F
         p.records = nullptr;
         p.rec_cap = 0;
         p.ovf_count = d_ovf_count;

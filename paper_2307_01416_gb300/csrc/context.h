@@ -33,6 +33,7 @@ struct vpmc_ctx {
     double curve15[15]{};
     int16_t* d_ct = nullptr;
     vpmc::TablesImage* d_tables = nullptr;
+    vpmc::MatConst water_mat{};          // the tables image's water entry (a launch constant)
     double* d_curve = nullptr;
     double* d_rho = nullptr;
     unsigned long long* d_acc = nullptr;       // dose accumulator (scoring grid)

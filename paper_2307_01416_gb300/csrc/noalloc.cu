@@ -173,6 +173,7 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
 
     TransportParams p{};
     p.tables = c->d_tables;
+    p.water = c->water_mat;
     p.ct = c->d_ct;
     p.ctg = c->ctg;
     p.sg = c->sg;

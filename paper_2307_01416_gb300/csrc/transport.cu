@@ -309,7 +309,20 @@ struct Lane {
     unsigned long long qdep;
 };
 
-__device__ __forceinline__ void ch_step(const Medium& m, float s_geom, Lane& L, const TransportParams& P, uint2 key,
+// State of the history a patient lane carries.  Its global index and work
+// item stay in shared memory: they are read only when the history ends.
+struct PatientLane {
+    float p[3], d[3];
+    float E, R, nlam;
+    uint32_t step;              // condensed-history steps so far (RNG counter)
+    uint32_t hist;              // history index within its spot
+    int iters;
+    int ic[3], is[3];
+    unsigned long long hdep;    // fixed-point energy the history deposited in the patient
+};
+
+template <class LaneT>
+__device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L, const TransportParams& P, uint2 key,
                                         StepResult& o)
 {
     const float E = L.E;
@@ -440,18 +453,24 @@ struct WorkPool {
     }
 };
 
+__device__ __forceinline__ void put_record(const TransportParams& P, long long g, int fate, uint32_t steps,
+                                           unsigned long long q, float e, const float pos[3])
+{
+    HistRecord r;
+    r.q_dep = (long long)q;
+    r.fate = fate;
+    r.steps = (int)steps;
+    r.e_dep = (float)((double)q / (double)P.fscale);
+    r.e_end = (fate == kLeak || fate == kErr) ? e : 0.0f;
+    r.pos[0] = pos[0]; r.pos[1] = pos[1]; r.pos[2] = pos[2];
+    r.pad = 0.0f;
+    P.records[g] = r;
+}
+
 __device__ __forceinline__ void write_record(const TransportParams& P, const Lane& L, int fate, const float pos[3],
                                              unsigned long long acc_dep)
 {
-    HistRecord r;
-    r.q_dep = (long long)(acc_dep - L.qdep);
-    r.fate = fate;
-    r.steps = (int)L.step;
-    r.e_dep = (float)((double)(acc_dep - L.qdep) / (double)P.fscale);
-    r.e_end = (fate == kLeak || fate == kErr) ? L.E : 0.0f;
-    r.pos[0] = pos[0]; r.pos[1] = pos[1]; r.pos[2] = pos[2];
-    r.pad = 0.0f;
-    P.records[L.g] = r;
+    put_record(P, L.g, fate, L.step, acc_dep - L.qdep, L.E, pos);
 }
 
 __device__ __forceinline__ void warp_add_stats(const TransportParams& P, unsigned long long (&v)[kNStats], int lane)
@@ -1092,9 +1111,14 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
 // ============================================================================
 // Voxelised patient.
 // ============================================================================
-__global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
+__global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const TransportParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    long long* s_g = reinterpret_cast<long long*>(smem + PatientSmem::G);
+    long long* s_pool = reinterpret_cast<long long*>(smem + PatientSmem::Pool) + 2 * warp;
+    int* s_item = reinterpret_cast<int*>(smem + PatientSmem::Item);
     {
         float* R = reinterpret_cast<float*>(smem + PatientSmem::R);
         float* Et = reinterpret_cast<float*>(smem + PatientSmem::Einv);
@@ -1102,34 +1126,28 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
         for (int i = threadIdx.x; i < kNR; i += blockDim.x) Et[i] = P.tables->Einv[kWater][i];
         float2* hu = reinterpret_cast<float2*>(smem + PatientSmem::HU);
         for (int i = threadIdx.x; i < kNHU; i += blockDim.x) hu[i] = P.tables->hu[i];
-        MatConst* mt = reinterpret_cast<MatConst*>(smem + PatientSmem::Mat);
-        if (threadIdx.x < kNMat) mt[threadIdx.x] = P.tables->mat[threadIdx.x];
         DevScen* sc = reinterpret_cast<DevScen*>(smem + PatientSmem::Scens);
         for (int i = threadIdx.x; i < P.n_scen; i += blockDim.x) sc[i] = P.scens[i];
+        if (lane == 0) { s_pool[0] = 0; s_pool[1] = 0; }
+        s_g[threadIdx.x] = 0;
+        s_item[threadIdx.x] = 0;
     }
     __syncthreads();
     Medium water;
     water.Rt = reinterpret_cast<const float*>(smem + PatientSmem::R);
     water.Et = reinterpret_cast<const float*>(smem + PatientSmem::Einv);
     const float2* hu_lut = reinterpret_cast<const float2*>(smem + PatientSmem::HU);
-    const MatConst* mat = reinterpret_cast<const MatConst*>(smem + PatientSmem::Mat);
     const DevScen* scens = reinterpret_cast<const DevScen*>(smem + PatientSmem::Scens);
-    water.inv_dR = mat[kWater].inv_dR;
-    water.za = mat[kWater].za;
-    water.inv_x0 = mat[kWater].inv_x0;
+    water.inv_dR = P.water.inv_dR;
+    water.za = P.water.za;
+    water.inv_x0 = P.water.inv_x0;
 
-    const long long total = min((long long)*P.phase_count, P.phase_cap);
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    WorkPool pool;
     bool alive = false, done = false;
-    Lane L;
-    L.item = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.stage = 2; L.forced = 0;
-    L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
+    PatientLane L;
+    L.hist = 0; L.hdep = 0ull; L.iters = 0; L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; L.ic[k] = 0; L.is[k] = 0; }
-    unsigned long long acc_dep = 0, acc_leak = 0, acc_nuc = 0, acc_steps = 0, acc_err = 0;
-    uint2 key = make_uint2(0u, 0u);
+    uint32_t key1 = 0u;
     float spr_scale = 1.0f;
     DevBox bx;
     bx.base = 0; bx.lo[0] = bx.lo[1] = bx.lo[2] = 0; bx.n[0] = bx.n[1] = bx.n[2] = 0;
@@ -1138,68 +1156,80 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
     for (;;) {
         // ---- histories handed over by the devices kernel ----
         unsigned need = __ballot_sync(kFull, !alive && !done);
-        while (need) {
-            if (pool.next >= pool.end) {
-                if (!pool.refill(P, 0, total, lane)) {
-                    if (!alive) done = true;
-                    break;
-                }
-            }
-            const int take = (int)min((long long)__popc(need), pool.end - pool.next);
-            const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
-            if (mine) {
-                const PhaseRec r = P.phase[pool.next + __popc(need & lt_mask)];
-                if (r.item >= 0) {        // item -1: a slot the aperture surrogate left empty
-                    const DevItem I = P.items[r.item];
-                    L.item = r.item;
-                    L.g = r.g;
-                    L.hist = (uint32_t)(r.g - I.hist_off);
-                    L.step = r.step;
-                    L.iters = 0;
-                    L.E = r.E;
-                    L.nlam = r.nlam;
-                    L.qdep = acc_dep;
-                    key = make_uint2(P.key0, P.key1_hi ^ (uint32_t)I.spot);
-                    spr_scale = scens[I.scen].spr_scale;
-                    bx = P.boxes[I.box];
-                    wsc = I.wscale;
-                    // ray / grid box entry
-                    float tmin = -__int_as_float(0x7f800000), tmax = __int_as_float(0x7f800000);
-    #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const float lo = P.ctg.lo[k], hi = P.ctg.lo[k] + P.ctg.n[k] * P.ctg.d[k];
-                        if (r.d[k] != 0.0f) {
-                            float t1 = (lo - r.p[k]) / r.d[k], t2 = (hi - r.p[k]) / r.d[k];
-                            if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
-                            tmin = fmaxf(tmin, t1);
-                            tmax = fminf(tmax, t2);
-                        } else if (r.p[k] < lo || r.p[k] > hi) {
-                            tmax = -__int_as_float(0x7f800000);
-                        }
+        if (need) {
+            // the warp's pool lives in shared memory between refills, so that
+            // it holds no registers across the step
+            WorkPool pool;
+            pool.next = s_pool[0];
+            pool.end = s_pool[1];
+            const unsigned lt_mask = (1u << lane) - 1u;
+            while (need) {
+                if (pool.next >= pool.end) {
+                    const long long total = min((long long)*P.phase_count, P.phase_cap);
+                    if (!pool.refill(P, 0, total, lane)) {
+                        if (!alive) done = true;
+                        break;
                     }
-                    const float tin = fmaxf(tmin, 0.0f);
-    #pragma unroll
-                    for (int k = 0; k < 3; ++k) { L.p[k] = r.p[k]; L.d[k] = r.d[k]; }
-                    if (!(tmax > tin)) {
-                        // misses the grid
-                        acc_leak += to_fixed(L.E, P.fscale, P.fx32);
-                        if (P.records && L.g < P.rec_cap) write_record(P, L, kLeak, L.p, acc_dep);
-                    } else {
-    #pragma unroll
+                }
+                const int take = (int)min((long long)__popc(need), pool.end - pool.next);
+                const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
+                if (mine) {
+                    const PhaseRec r = P.phase[pool.next + __popc(need & lt_mask)];
+                    if (r.item >= 0) {        // item -1: a slot the aperture surrogate left empty
+                        const DevItem I = P.items[r.item];
+                        s_item[threadIdx.x] = r.item;
+                        s_g[threadIdx.x] = r.g;
+                        L.hist = (uint32_t)(r.g - I.hist_off);
+                        L.step = r.step;
+                        L.iters = 0;
+                        L.E = r.E;
+                        L.nlam = r.nlam;
+                        L.hdep = 0ull;
+                        key1 = P.key1_hi ^ (uint32_t)I.spot;
+                        spr_scale = scens[I.scen].spr_scale;
+                        bx = P.boxes[I.box];
+                        wsc = I.wscale;
+                        // ray / grid box entry
+                        float tmin = -__int_as_float(0x7f800000), tmax = __int_as_float(0x7f800000);
+#pragma unroll
                         for (int k = 0; k < 3; ++k) {
-                            L.p[k] = fmaf(tin, L.d[k], L.p[k]);
-                            const int a = (int)floorf((L.p[k] - P.ctg.lo[k]) / P.ctg.d[k]);
-                            L.ic[k] = min(max(a, 0), P.ctg.n[k] - 1);
-                            const int b = (int)floorf((L.p[k] - P.sg.lo[k]) / P.sg.d[k]);
-                            L.is[k] = min(max(b, 0), P.sg.n[k] - 1);
+                            const float lo = P.ctg.lo[k], hi = P.ctg.lo[k] + P.ctg.n[k] * P.ctg.d[k];
+                            if (r.d[k] != 0.0f) {
+                                float t1 = (lo - r.p[k]) / r.d[k], t2 = (hi - r.p[k]) / r.d[k];
+                                if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
+                                tmin = fmaxf(tmin, t1);
+                                tmax = fminf(tmax, t2);
+                            } else if (r.p[k] < lo || r.p[k] > hi) {
+                                tmax = -__int_as_float(0x7f800000);
+                            }
                         }
-                        L.R = range_of(water.Rt, L.E);
-                        alive = true;
+                        const float tin = fmaxf(tmin, 0.0f);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) { L.p[k] = r.p[k]; L.d[k] = r.d[k]; }
+                        if (!(tmax > tin)) {
+                            // misses the grid
+                            atomicAdd(P.stats + kStLeak, to_fixed(L.E, P.fscale, P.fx32));
+                            if (P.records && r.g < P.rec_cap) put_record(P, r.g, kLeak, L.step, 0ull, L.E, L.p);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                L.p[k] = fmaf(tin, L.d[k], L.p[k]);
+                                const int a = (int)floorf((L.p[k] - P.ctg.lo[k]) / P.ctg.d[k]);
+                                L.ic[k] = min(max(a, 0), P.ctg.n[k] - 1);
+                                const int b = (int)floorf((L.p[k] - P.sg.lo[k]) / P.sg.d[k]);
+                                L.is[k] = min(max(b, 0), P.sg.n[k] - 1);
+                            }
+                            L.R = range_of(water.Rt, L.E);
+                            alive = true;
+                        }
                     }
                 }
+                pool.next += take;
+                need = __ballot_sync(kFull, !alive && !done);
             }
-            pool.next += take;
-            need = __ballot_sync(kFull, !alive && !done);
+            __syncwarp();
+            if (lane == 0) { s_pool[0] = pool.next; s_pool[1] = pool.end; }
+            __syncwarp();
         }
         if (!__any_sync(kFull, alive)) {
             if (__all_sync(kFull, done || alive)) break;
@@ -1242,10 +1272,10 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
                 const float d_old[3] = {L.d[0], L.d[1], L.d[2]};
                 const int lx = L.is[0] - bx.lo[0], ly = L.is[1] - bx.lo[1], lz = L.is[2] - bx.lo[2];
                 const int is0 = L.is[0], is1 = L.is[1], is2 = L.is[2];
-                ch_step(water, s_geom, L, P, key, o);
-                acc_steps += 1;
+                ch_step(water, s_geom, L, P, make_uint2(P.key0, key1), o);
                 const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
-                const unsigned long long q = wsc == P.fscale ? qs : to_fixed(o.dE, wsc, false);
+                unsigned long long q = qs;
+                if (!P.unit_weight && wsc != P.fscale) q = to_fixed(o.dE, wsc, false);
                 // score into the scoring voxel where the step started
                 if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] && ly < bx.n[1] && lz < bx.n[2]) {
                     dep_key = bx.base + (long long)(lx + bx.n[0] * (ly + bx.n[1] * lz));   // box < 2^31 voxels
@@ -1256,14 +1286,14 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
                     if ((long long)slot < P.ovf_cap) {
                         OvfRec rr;
                         rr.voxel = is0 + P.sg.n[0] * (is1 + P.sg.n[1] * is2);
-                        rr.item = L.item;
+                        rr.item = s_item[threadIdx.x];
                         rr.q = q;
                         P.ovf[slot] = rr;
                     }
                 }
-                acc_dep += qs;
+                L.hdep += qs;
                 if (o.killed) {
-                    if (o.killed == 2) acc_nuc += qs;
+                    if (o.killed == 2) atomicAdd(P.stats + kStNuc, qs);
                     fate = o.killed == 2 ? kNuc : kStop;
                 } else {
                     if (o.lim == 1) {
@@ -1291,9 +1321,16 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
                 }
             }
             if (fate >= 0) {
-                if (fate == kLeak || fate == kErr) acc_leak += to_fixed(L.E, P.fscale, P.fx32);
-                if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }
-                if (P.records && L.g < P.rec_cap) write_record(P, L, fate, L.p, acc_dep);
+                // the history's totals go straight to the launch's counters
+                // (one history ends every few hundred steps of a lane)
+                if (L.hdep) atomicAdd(P.stats + kStDep, L.hdep);
+                atomicAdd(P.stats + kStSteps, (unsigned long long)min(L.iters, kMaxIter));
+                if (fate == kLeak || fate == kErr) atomicAdd(P.stats + kStLeak, to_fixed(L.E, P.fscale, P.fx32));
+                if (fate == kErr) { atomicAdd(P.stats + kStErr, 1ull); atomicOr(P.status, 1); }
+                if (P.records) {
+                    const long long g = s_g[threadIdx.x];
+                    if (g < P.rec_cap) put_record(P, g, fate, L.step, L.hdep, L.E, L.p);
+                }
                 alive = false;
             }
         }
@@ -1301,14 +1338,12 @@ __global__ void __launch_bounds__(768, 1) k_patient(const TransportParams P)
         if (P.aggregate) deposit_aggregated(P.scratch, dep_key, dep_q);
         else if (dep_key >= 0 && dep_q) atomicAdd(P.scratch + dep_key, dep_q);
     }
-    unsigned long long v[kNStats] = {acc_dep, acc_leak, 0ull, 0ull, acc_nuc, acc_steps, acc_err};
-    warp_add_stats(P, v, lane);
 }
 
 size_t devices_smem_bytes() { return SourceSmem::Bytes > ApertureSmem::Bytes ? SourceSmem::Bytes : ApertureSmem::Bytes; }
 size_t patient_smem_bytes() { return PatientSmem::Bytes; }
 int devices_max_block() { return 640; }
-int patient_max_block() { return 768; }
+int patient_max_block() { return kPatientMaxBlock; }
 
 template <int kMode>
 static cudaError_t launch_aperture_mode(const TransportParams& p, int grid, int block, cudaStream_t s)

@@ -189,6 +189,8 @@ struct TransportParams {
     int mcs, straggling, nuclear;
     float fscale;                    // 2^F
     int fx32;                        // 2^F <= 2^24: every energy x 2^F fits 32 bits (E <= 250 MeV)
+    int unit_weight;                 // every item's wscale is 2^F (influence-matrix columns)
+    MatConst water;                  // the patient medium's constants (the tables image's water entry)
     int aggregate;
     int chunk;
     // learned aperture surrogate
@@ -223,13 +225,18 @@ struct ApertureSmem {                // aperture block
     static constexpr size_t Poly = Scens + sizeof(DevScen) * kMaxScen;
     static constexpr size_t Bytes = Poly + sizeof(float2) * kMaxPolyVerts;
 };
+constexpr int kPatientMaxBlock = 896;
 struct PatientSmem {                 // voxelised patient
     static constexpr size_t R = 0;                                            // water
     static constexpr size_t Einv = R + sizeof(float) * kNEPad;
     static constexpr size_t HU = Einv + sizeof(float) * kNR;
-    static constexpr size_t Mat = HU + sizeof(float2) * kNHU;
-    static constexpr size_t Scens = Mat + sizeof(MatConst) * kNMat;
-    static constexpr size_t Bytes = Scens + sizeof(DevScen) * kMaxScen;
+    static constexpr size_t Scens = HU + sizeof(float2) * kNHU;
+    // per thread: global index and work item of the history it carries (read
+    // only when a history ends); per warp: the work pool [next, end)
+    static constexpr size_t G = (Scens + sizeof(DevScen) * kMaxScen + 15) & ~size_t(15);
+    static constexpr size_t Pool = G + sizeof(long long) * kPatientMaxBlock;
+    static constexpr size_t Item = Pool + 2 * sizeof(long long) * (kPatientMaxBlock / 32);
+    static constexpr size_t Bytes = Item + sizeof(int) * kPatientMaxBlock;
 };
 
 // Host-side launchers (transport.cu, finalize.cu).

@@ -117,7 +117,7 @@ def test_launch_configuration_does_not_change_results(torch_cuda):
     eng = _engine(pb)
     op = W.Options(seed=7)
     ref = None
-    for block, agg, chunk in ((512, 1, 32), (256, 0, 128), (384, 1, 64)):
+    for block, agg, chunk in ((512, 1, 32), (256, 0, 128), (384, 1, 64), (896, 0, 32)):
         d, st, _ = eng.run_spots(spots, W.Scenario(), op, block_size=block, aggregate=agg, chunk=chunk)
         d = d.cpu().numpy()
         if ref is None:
