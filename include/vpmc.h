@@ -120,7 +120,8 @@ typedef struct {
     int frac_bits;          /* fixed-point scale of deposits, 2^-frac_bits MeV (default 24) */
     /* Autotuned launch: the first dose (or influence-matrix) call of a
      * context times a few launch configurations on a sample of its
-     * histories; the choice is kept by the context and, for later contexts
+     * histories (up to 24 per thread of the largest block, about 3.3e6 on
+     * 152 SMs); the choice is kept by the context and, for later contexts
      * on the same device with the same grids, field devices and fixed launch
      * options, by the process.  Results do not depend on the choice. */
     int aggregate;          /* -1 autotuned, 0 plain atomics, 1 warp-aggregated atomics   */

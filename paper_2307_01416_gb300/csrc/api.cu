@@ -352,11 +352,16 @@ float time_launch(vpmc_ctx* c, cudaError_t (*fn)(const TransportParams&, int, in
 }
 
 // Chooses the two kernels' block sizes, warp aggregation and refill chunk by
-// timing short launches over a prefix of the work (results are discarded;
-// the caller zeroes the scoring buffers afterwards).
+// timing launches over a prefix of the work (results are discarded; the
+// caller zeroes the scoring buffers afterwards).  The prefix gives every lane
+// of the largest block about 24 histories: in a launch of only a few
+// histories per lane the tail (the last long histories of each warp) decides
+// the time and favours small blocks, which lose on long launches (13-scenario
+// head set: 768 threads chosen on 4 histories per lane, 4.7 % slower than the
+// 896 chosen on 24).
 vpmc_status autotune(vpmc_ctx* c, TransportParams p, TuneResult* out, const vpmc_opts& o)
 {
-    const long long sample = std::min<long long>(p.total, (long long)c->num_sms * 640 * 4);
+    const long long sample = std::min<long long>(p.total, (long long)c->num_sms * patient_max_block() * 24);
     TuneResult best;
     best.valid = true;
     if (o.block_size) best.block = o.block_size;
