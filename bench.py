@@ -129,9 +129,10 @@ class ClockSampler:
 
 
 def transport_traffic(steps_per_launch: float):
-    """DRAM bytes (read + write) of one set's transport, scaled from the ncu
-    capture summarised in profiles/k_transport_head_im13.md by condensed-history
-    steps; None when the kernels changed since the capture (source hash)."""
+    """DRAM bytes (read + write) of one set's transport, scaled by
+    condensed-history steps from the ncu capture summarised in
+    profiles/k_transport_head_im_subset_traffic.md; None when the kernels
+    changed since the capture (source hash)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_transport_traffic.txt")
     try:
