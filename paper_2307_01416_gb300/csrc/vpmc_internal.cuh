@@ -238,6 +238,12 @@ struct PatientSmem {                 // voxelised patient
     static constexpr size_t Item = Pool + 2 * sizeof(long long) * (kPatientMaxBlock / 32);
     static constexpr size_t Bytes = Item + sizeof(int) * kPatientMaxBlock;
 };
+// One block per SM of each transport kernel: every layout fits the 227 KB a
+// block may opt in to.
+static_assert(SourceSmem::Bytes <= 227 * 1024, "source kernel shared memory");
+static_assert(ApertureSmem::Bytes <= 227 * 1024, "aperture kernel shared memory");
+static_assert(PatientSmem::Bytes <= 227 * 1024, "patient kernel shared memory");
+static_assert(kPatientMaxBlock % 32 == 0, "whole warps");
 
 // Host-side launchers (transport.cu, finalize.cu).
 // Transport of histories [p.hist_begin, p.total): the beam-line kernels
