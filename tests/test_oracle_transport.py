@@ -234,6 +234,22 @@ def test_gamma_against_brute_force():
     assert O.gamma_pass_rate(const, const * 1.021, sp) == 0.0
 
 
+def test_gamma_one_voxel_shift_analytic_pattern():
+    """A linear ramp along x against the same ramp shifted by one 1 mm voxel:
+    every voxel finds its dose 1 mm away (gamma 0.5) except the column whose
+    match lies outside the grid, where the 1-voxel dose step is 2.9x the 2 %
+    criterion.  The pass rate is (nx - 1) / nx exactly, whichever way the
+    field moves; the ramp is linear, so the trilinear sub-grid is exact."""
+    nz, ny, nx = 3, 4, 8
+    x = np.arange(nx, dtype=np.float64)[None, None, :] * np.ones((nz, ny, 1))
+    ref = x + 10.0                      # all voxels above 10 % of the maximum (17)
+    sp = (1.0, 1.0, 1.0)
+    assert O.gamma_pass_rate(ref, ref - 1.0, sp) == pytest.approx(100.0 * (nx - 1) / nx, abs=1e-12)
+    assert O.gamma_pass_rate(ref, ref + 1.0, sp) == pytest.approx(100.0 * (nx - 1) / nx, abs=1e-12)
+    # a two-voxel shift is still within the 2 mm DTA for the interior
+    assert O.gamma_pass_rate(ref, ref - 2.0, sp) == pytest.approx(100.0 * (nx - 2) / nx, abs=1e-12)
+
+
 def test_scoring_density_volume_weighted():
     """Scoring-voxel density = volume-weighted mean of overlapping CT voxels
     (brute force on a common 0.5 mm sub-grid)."""
