@@ -210,7 +210,7 @@ def test_multiple_scattering_accumulates_through_a_slab(energy):
     L_j)^2], with E_j from the range table; the same in y, and x, y
     uncorrelated.  Dropping the offsets or their correlation with the angle
     moves Var(x) by ~7 %, advancing along the new direction by ~15 %, and
-    theta0 at the entrance energy by ~20 % at 100 MeV (tolerance 2.8 %)."""
+    theta0 at the entrance energy by ~6.5 % at 100 MeV (tolerance 2.8 %)."""
     N, s, n = 20, 0.99, 40000
     ct = W.Grid((1, 1, N), (200.0, 200.0, s), (-100.0, -100.0, 0.0))
     hu = np.zeros((N, 1, 1), dtype=np.int16)
