@@ -278,3 +278,26 @@ def test_range_rejection_leaves_gpu_dose_unchanged(torch_cuda):
     assert s1["e_dep"] == s0["e_dep"] and s1["e_leak"] == s0["e_leak"]
     assert abs(s1["e_aperture"] / s0["e_aperture"] - 1.0) < 1e-6
     assert s1["steps"] < 0.6 * s0["steps"]
+
+
+def test_empty_work_lists_and_single_histories(torch_cuda):
+    """Edge cases of the work list.  No spots, or only spots without
+    histories, give an all-zero dose and zero counters (nothing is
+    transported); an influence-matrix call without spots is refused.  One
+    history alone, and one warp plus one (33), match the oracle history by
+    history (the same random numbers as the first histories of the 20,000
+    above: the oracle flags none of them)."""
+    pb, spots = W.pencil_beam_water(n_hist=10)
+    eng = _engine(pb)
+    none = spots.copy()
+    none["n_hist"] = 0
+    for sub in (spots[:0], none):
+        d, st, _ = eng.run_spots(sub, W.Scenario(), DET)
+        assert float(d.abs().max()) == 0.0
+        assert st["histories"] == 0 and st["steps"] == 0 and st["e_dep"] == 0.0 and st["errors"] == 0
+    with pytest.raises(RuntimeError):
+        eng.influence_matrix(spots[:0], [W.Scenario()], DET)
+    eng.close()
+    for n in (1, 33):
+        pb, spots = W.pencil_beam_water(n_hist=n)
+        _per_history_parity(pb, spots, W.Scenario(), DET)
