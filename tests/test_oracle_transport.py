@@ -198,6 +198,30 @@ def test_columns_sum_to_dose_grid_and_threshold():
         np.testing.assert_array_equal(im[:, j].toarray().ravel()[kept], col[kept].astype(np.float32))
 
 
+def test_range_shifter_pulls_the_range_back_by_its_wet():
+    """Deterministic, no scattering, straggling or nuclear removal: a 45 mm
+    WET PMMA range shifter (thickness 45 mm / SPR_PMMA(150 MeV), reading c10)
+    pulls the CSDA end point in water back by 45 mm, up to the variation of
+    the PMMA/water stopping-power ratio with energy (below 0.05 mm from 100 to
+    160 MeV).  The energy it keeps is the water energy of the remaining range.
+    A ray outside its 30.5 mm radius flies past it: full range, nothing kept."""
+    g, hu = W.water_phantom((50, 50, 200), (2.0, 2.0, 1.0), (-50.0, -50.0, 0.0))
+    beam = W.Beam(direction=(0.0, 0.0, 1.0), bev_x=(1.0, 0.0, 0.0), iso=(0.0, 0.0, 0.0), source_to_iso=120.0,
+                  rs_present=True, rs_wet=45.0, rs_radius=30.5, rs_down_to_iso=50.0)
+    pb = W.Problem(ct=g, hu=hu, curve=W.HUCurve(), scoring=g, beams=[beam])
+    det = W.Options(seed=3, mcs=False, straggling=False, nuclear=False)
+    for e0 in (100.0, 130.0, 160.0):
+        for x, wet in ((0.0, 45.0), (40.0, 0.0)):
+            sp = W.make_spots([(0, e0, x, 0.0, 0.0, 0.0, 4, 1.0)])
+            _, tl, rec = O.run(pb, O.oracle_spots(sp), W.Scenario(), det, records=4)
+            assert np.all(rec["fate"] == O.FATE_STOP)
+            z = rec["pos"][:, 2]
+            assert np.ptp(z) == 0.0
+            assert abs(O.csda_range(O.WATER, e0) - z[0] - wet) < (0.05 if wet else 1e-9), (e0, x, z[0])
+            e_kept = tl["e_rs"] / 4.0
+            assert abs(e_kept - (e0 - O.energy_at_range(O.WATER, z[0]))) < 1e-6 * e0
+
+
 @pytest.mark.parametrize("energy", [200.0, 100.0])
 def test_multiple_scattering_accumulates_through_a_slab(energy):
     """MCS only (straggling and nuclear off), a pencil beam through N water
