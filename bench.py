@@ -129,10 +129,11 @@ class ClockSampler:
 
 
 def transport_traffic(steps_per_launch: float):
-    """DRAM bytes (read + write) of one set's transport, scaled by
-    condensed-history steps from the ncu capture summarised in
-    profiles/k_transport_head_im_subset_traffic.md; None when the kernels
-    changed since the capture (source hash)."""
+    """DRAM bytes (read + write) of one set's transport: the bytes per
+    condensed-history step that an ncu capture of the three transport
+    kernels measured on the small influence-matrix case (dram__bytes_read.sum
+    + dram__bytes_write.sum over its steps), scaled by the set's steps; None
+    when the kernels changed since that capture (source hash)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_transport_traffic.txt")
     try:

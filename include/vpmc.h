@@ -140,6 +140,12 @@ typedef struct {
                                exit plane instead of condensed-history stepping (needs
                                vpmc_surrogate_set_weights or _train first); the others
                                use the plain path                                         */
+    int64_t timeout_iters;  /* iterations a history may take in each transport kernel before
+                               it is stopped as an error (0 = default 200,000; at most
+                               2^31 - 1).  A history that reaches it ends with fate 5, its
+                               remaining energy goes to e_leak, and the kernel latches bit 0
+                               of the device status word: the call (or, for an asynchronous
+                               call, the next call on the context) returns VPMC_ERR_TIMEOUT */
 } vpmc_opts;
 
 /* Totals of one call.  Energies in MeV (fixed-point sums, unweighted). */
@@ -163,7 +169,8 @@ typedef struct {
 } vpmc_csr;
 
 /* Fill opts with defaults: seed 1234, all physics on, frac_bits 24,
- * autotuned launch, no records, brass range rejection on. */
+ * autotuned launch, no records, brass range rejection on, iteration cap
+ * 200,000. */
 void vpmc_default_opts(vpmc_opts* opts);
 
 /* Create a context (Sec. 2.A physics tables; Sec. 2.D.3 patient CT).
@@ -184,7 +191,11 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
  * aperture (the authors' future work, Sec. 4) is one entry per (field,
  * energy layer): the same field geometry with that layer's opening, the
  * layer's spots referring to it; spots must be sorted by entry for
- * vpmc_influence_matrix. */
+ * vpmc_influence_matrix.  VPMC_ERR_ARG (the entry keeps its previous state)
+ * for dir and bev_x not orthonormal, a polygon of fewer than 3 vertices, a
+ * non-finite vertex, or one that is not simple: two edges that are not
+ * neighbours touch or cross, or two neighbouring edges overlap or a vertex
+ * repeats. */
 vpmc_status vpmc_set_aperture(vpmc_ctx* ctx, int beam_id, const vpmc_beam* beam);
 
 /* Dose of a set of spots in one scenario (Sec. 2.C, 2.D): transports every
@@ -192,27 +203,36 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* ctx, int beam_id, const vpmc_beam* beam)
  * float32 array on the scoring grid, caller-owned) = sum over deposits of
  * dE * weight / (rho * V) in Gy.  scen may be NULL (nominal).  Asynchronous
  * on the context stream unless stats_out is non-NULL, in which case it
- * synchronises and fills the totals. */
+ * synchronises, fills the totals and returns VPMC_ERR_TIMEOUT or
+ * VPMC_ERR_DEVICE_FLAG when a kernel latched its status word.  An
+ * asynchronous call leaves that word to the next call on the context, which
+ * first waits for the earlier call's work and, if the word is set, returns
+ * that error without running (the earlier call's dose is then not valid).
+ * Spot errors: VPMC_ERR_STATE for a beam id that was not set,
+ * VPMC_ERR_ARG for an energy outside (0.5, 250] MeV (NaN included), n_hist
+ * outside [0, 2^32), a negative or non-finite sigma, divergence or weight. */
 vpmc_status vpmc_run_spots(vpmc_ctx* ctx, const vpmc_spot* spots, int n_spots, const vpmc_scenario* scen,
                            const vpmc_opts* opts, float* dose_dev, vpmc_stats* stats_out);
 
 /* The dose of vpmc_run_spots computed without allocating any memory in the
  * call.  The paper has no counterpart: this serves callers that cannot let a
- * call allocate device memory -- work recorded into a CUDA stream capture
- * (cudaMalloc is not a capturable stream operation), serving loops where the
- * implicit device-wide synchronisation of cudaMalloc/cudaFree would stall
- * other streams, and hosts whose memory pool owns all device memory.  The
- * context (vpmc_create_geometry, vpmc_set_aperture) must already exist; it is
- * the only allocation, made once at set-up.  Scratch (64-bit accumulator, work
- * items, beam-line hand-off buffer, counters) lives in one fixed device array
- * of about 29 MiB that every GPU loading the library holds until the process
- * exits; its limits are 2,097,152 scoring voxels and 16,384 spots with
- * histories per call (VPMC_ERR_ARG beyond them).  The first call on a device
- * resolves that array's device address (cudaGetSymbolAddress), so it should
- * come before any stream capture.  All calls on a device share the array and
- * clear it at their start: calls that overlap on the GPU (other streams,
- * other threads) race and corrupt each other.  Arguments, output and the
- * synchronisation rule for stats_out are those of vpmc_run_spots; the launch
+ * call allocate device memory -- serving loops where the implicit
+ * device-wide synchronisation of cudaMalloc/cudaFree would stall other
+ * streams, and hosts whose memory pool owns all device memory.  The context
+ * (vpmc_create_geometry, vpmc_set_aperture) must already exist; it is the
+ * only allocation, made once at set-up.  Scratch (64-bit accumulator, work
+ * items, beam-line hand-off buffer, counters, status word) lives in one fixed
+ * device array of about 29 MiB that every GPU loading the library holds until
+ * the process exits; its limits are 2,097,152 scoring voxels and 16,384 spots
+ * with histories per call (VPMC_ERR_ARG beyond them).  The first call on a
+ * device resolves that array's device address (cudaGetSymbolAddress).  All
+ * calls on a device share the array and clear it at their start: calls that
+ * overlap on the GPU (other streams, other threads) race and corrupt each
+ * other.  The work list is copied from host stack memory during the call, so
+ * a stream that is capturing is refused (VPMC_ERR_STATE).  Arguments, output
+ * and the status rules (stats_out, and the latched status word read by the
+ * next call on the same device) are those of vpmc_run_spots, with the plain
+ * aperture only (opts->surrogate = 1 is VPMC_ERR_ARG); the launch
  * configuration is the context's tuned one (or opts') without autotuning. */
 vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* ctx, const vpmc_spot* spots, int n_spots, const vpmc_scenario* scen,
                                    const vpmc_opts* opts, float* dose_dev, vpmc_stats* stats_out);

@@ -66,7 +66,7 @@ class _Scen(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("mcs", C.c_int), ("straggling", C.c_int), ("nuclear", C.c_int),
-                ("frac_bits", C.c_int), ("range_rejection", C.c_int)]
+                ("frac_bits", C.c_int)]
 
 
 SPOT_DTYPE = np.dtype([("beam", np.int32), ("spot_key", np.int32), ("energy", np.float64), ("x", np.float64),
@@ -75,7 +75,7 @@ SPOT_DTYPE = np.dtype([("beam", np.int32), ("spot_key", np.int32), ("energy", np
 RECORD_DTYPE = np.dtype([("fate", np.int32), ("steps", np.int32), ("e_dep", np.float64), ("e_end", np.float64),
                          ("pos", np.float64, (3,)), ("q_dep", np.int64), ("flags", np.int32), ("pad", np.int32),
                          ("path", np.float64), ("track", np.float64)], align=True)
-FLAG_NEAR_WALL, FLAG_NEAR_RIM, FLAG_NUC_LOW_DENSITY, FLAG_GRAZING_FACE, FLAG_REJECTION_TIE = 1, 2, 4, 8, 16
+FLAG_NEAR_WALL, FLAG_NEAR_RIM, FLAG_NUC_LOW_DENSITY, FLAG_GRAZING_FACE = 1, 2, 4, 8
 
 _lib = None
 _lock = threading.Lock()
@@ -302,8 +302,7 @@ def run(problem, spots_o: np.ndarray, scenario, opts, mode: int = 0, records: in
     cv = _curve(problem.curve)
     beams, xy = _beams(problem.beams)
     sc = _Scen((C.c_double * 3)(*scenario.shift), scenario.spr_scale)
-    op = _Opts(int(opts.seed), int(opts.mcs), int(opts.straggling), int(opts.nuclear), int(opts.frac_bits),
-               int(getattr(opts, "range_rejection", True)))
+    op = _Opts(int(opts.seed), int(opts.mcs), int(opts.straggling), int(opts.nuclear), int(opts.frac_bits))
     nv = problem.scoring.nvox
     sp = np.ascontiguousarray(spots_o, dtype=SPOT_DTYPE)
     q = np.zeros(nv if mode == 0 else len(sp) * nv, dtype=np.int64)
@@ -423,8 +422,7 @@ def surrogate_tracks(beams, n_tracks: int, opts, nthreads: int = 0):
     target (N, 5), fate (N,) (-1: left through the exit plane) and flags (N,)."""
     L = lib()
     arr, xy = _beams(beams)
-    op = _Opts(int(opts.seed), int(opts.mcs), int(opts.straggling), int(opts.nuclear), int(opts.frac_bits),
-               int(getattr(opts, "range_rejection", True)))
+    op = _Opts(int(opts.seed), int(opts.mcs), int(opts.straggling), int(opts.nuclear), int(opts.frac_bits))
     n = len(beams) * int(n_tracks)
     feat, target = np.zeros((n, 6)), np.zeros((n, 5))
     label, fate, flags = (np.zeros(n, dtype=np.int32) for _ in range(3))

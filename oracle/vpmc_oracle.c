@@ -420,7 +420,6 @@ typedef struct {
     uint64_t seed;
     int mcs, straggling, nuclear;
     int frac_bits;
-    int range_rejection;    /* absorb brass protons that cannot leave the block */
 } orc_opts;
 
 typedef struct {
@@ -449,8 +448,7 @@ typedef struct {
                            bit 3: a CT voxel face crossed at a direction
                            cosine below 0.01 |delta SPR| (the crossing point
                            moves by (position rounding) / cosine);
-                           bit 4: a brass range-rejection test decided within
-                           ORC_TIE_MM of its threshold;
+                           bit 4: unused;
                            bit 5: the end point is ill-conditioned: moving
                            the start by ORC_COND_MM moves it by more than
                            1e-4 of the track;
@@ -638,7 +636,7 @@ static void bev_to_patient(const orc_beam* bm, const orc_scen* sc, const double 
  * direction up to a wall or the exit plane; a wall hit forces the next step
  * into brass.  In brass it takes a condensed-history step with brass
  * physics.  Returns 0 when it leaves through the exit plane, else FATE_AP
- * (absorbed: stopped, nuclear removal or range rejection), FATE_LEAK (left
+ * (absorbed: stopped or nuclear removal), FATE_LEAK (left
  * upstream) or FATE_ERR (iteration cap). */
 static int aperture_block(const orc_beam* bm, const double* poly, orc_particle* pt, const orc_opts* op,
                           orc_stream* st, orc_record* rec, double* tl, long* iter)
@@ -674,25 +672,6 @@ static int aperture_block(const orc_beam* bm, const double* poly, orc_particle* 
             for (int k = 0; k < 3; ++k) pt->p[k] += sg * pt->d[k];
             rec->track += sg;
             return down ? 0 : FATE_LEAK;
-        }
-        /* brass: a proton whose longest possible remaining path (1.2 x
-         * its residual CSDA range; range straggling is ~1.2 %) cannot
-         * reach the opening or either face of the block is absorbed now:
-         * its energy stays in the brass either way */
-        if (op->range_rejection) {
-            double rmax = 1.2 * pt->R / ORC_MAT[ORC_BRASS].rho;
-            double dlim = pt->p[2] - tup;
-            if (tdn - pt->p[2] < dlim) dlim = tdn - pt->p[2];
-            if (rmax < dlim + ORC_TIE_MM) {
-                double dw = ap_wall_distance(bm, poly, pt->p[0], pt->p[1], pt->p[2]);
-                if (dw < dlim) dlim = dw;
-                if (fabs(rmax - dlim) < ORC_TIE_MM) rec->flags |= 16;
-                if (rmax < dlim) {
-                    tl[4] += pt->E;
-                    pt->E = 0.0;
-                    return FATE_AP;
-                }
-            }
         }
         /* brass: condensed-history step with brass physics */
         forced_brass = 0;
@@ -1356,7 +1335,7 @@ void orc_step_sample(int table, double kappa, double rho, double za, double X0,
 {
     orc_init_tables();
     orc_medium med = {table, kappa, rho, za, X0};
-    orc_opts op = {seed, mcs, straggling, nuclear, 24, 0};
+    orc_opts op = {seed, mcs, straggling, nuclear, 24};
     orc_stream st;
     st.key[0] = (uint32_t)seed;
     st.key[1] = (uint32_t)(seed >> 32) ^ (uint32_t)spot_key;

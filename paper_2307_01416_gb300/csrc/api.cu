@@ -44,6 +44,8 @@ vpmc_status vpmc::report_error(vpmc_status st, const char* fmt, ...)
     return st;
 }
 
+void vpmc::clear_error() { g_error.clear(); }
+
 namespace {
 
 #define CUDA_TRY(expr)                                                                             \
@@ -180,6 +182,52 @@ vpmc_status upload_beams(vpmc_ctx* c)
     return VPMC_OK;
 }
 
+// A polygon (n >= 3 vertices, xy pairs) is simple when no two edges meet
+// except neighbours at their shared vertex, and neighbours do not fold back
+// onto each other.  Closed-segment tests with orientation signs in FP64;
+// O(n^2) edge pairs (a 4096-gon takes a few tens of ms, once per beam).
+bool polygon_is_simple(const double* xy, int n, int* e1, int* e2)
+{
+    auto orient = [&](int a, int b, int c) {
+        const double v = (xy[2 * b] - xy[2 * a]) * (xy[2 * c + 1] - xy[2 * a + 1]) -
+                         (xy[2 * b + 1] - xy[2 * a + 1]) * (xy[2 * c] - xy[2 * a]);
+        return (v > 0.0) - (v < 0.0);
+    };
+    auto within = [&](int a, int b, int p) {         // p collinear with a-b: inside its bounding box
+        return std::min(xy[2 * a], xy[2 * b]) <= xy[2 * p] && xy[2 * p] <= std::max(xy[2 * a], xy[2 * b]) &&
+               std::min(xy[2 * a + 1], xy[2 * b + 1]) <= xy[2 * p + 1] &&
+               xy[2 * p + 1] <= std::max(xy[2 * a + 1], xy[2 * b + 1]);
+    };
+    for (int i = 0; i < n; ++i) {
+        const int a = i, b = (i + 1) % n, c = (i + 2) % n;
+        *e1 = i;
+        *e2 = (i + 1) % n;
+        if (xy[2 * a] == xy[2 * b] && xy[2 * a + 1] == xy[2 * b + 1]) return false;    // repeated vertex
+        // neighbours a-b and b-c fold back: collinear with c on the side of a
+        if (orient(a, b, c) == 0 && (xy[2 * c] - xy[2 * b]) * (xy[2 * a] - xy[2 * b]) +
+                                            (xy[2 * c + 1] - xy[2 * b + 1]) * (xy[2 * a + 1] - xy[2 * b + 1]) > 0.0)
+            return false;
+    }
+    for (int i = 0; i < n; ++i) {
+        const int p1 = i, p2 = (i + 1) % n;
+        for (int j = i + 2; j < n; ++j) {
+            if (i == 0 && j == n - 1) continue;      // neighbours through the closing edge
+            const int q1 = j, q2 = (j + 1) % n;
+            const int d1 = orient(q1, q2, p1), d2 = orient(q1, q2, p2);
+            const int d3 = orient(p1, p2, q1), d4 = orient(p1, p2, q2);
+            const bool meet = (d1 * d2 < 0 && d3 * d4 < 0) || (d1 == 0 && within(q1, q2, p1)) ||
+                              (d2 == 0 && within(q1, q2, p2)) || (d3 == 0 && within(p1, p2, q1)) ||
+                              (d4 == 0 && within(p1, p2, q2));
+            if (meet) {
+                *e1 = i;
+                *e2 = j;
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
 // Checks shared by the dose and influence-matrix paths.
 vpmc_status check_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots)
 {
@@ -224,6 +272,27 @@ vpmc_status check_opts(const vpmc_opts* o)
     if (o->history_cap < 0 || (o->history_cap > 0 && !o->history_out))
         return fail(VPMC_ERR_ARG, "history_cap > 0 needs history_out");
     if (o->surrogate != 0 && o->surrogate != 1) return fail(VPMC_ERR_ARG, "surrogate must be 0 or 1");
+    if (o->timeout_iters < 0 || o->timeout_iters > 0x7fffffffll)
+        return fail(VPMC_ERR_ARG, "timeout_iters %lld outside [0, 2^31 - 1]", (long long)o->timeout_iters);
+    return VPMC_OK;
+}
+
+// The status word that an earlier asynchronous dose call left unread: waits
+// for that call's work, then reports what its kernels latched.
+vpmc_status pending_status(vpmc_ctx* c)
+{
+    if (!c->status_pending) return VPMC_OK;
+    const bool sur = c->status_pending == 2;
+    c->status_pending = 0;
+    int status = 0, ss = 0;
+    CUDA_TRY(cudaMemcpyAsync(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
+    if (sur && c->sur.status) CUDA_TRY(cudaMemcpyAsync(&ss, c->sur.status, sizeof ss, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (status & 1) return fail(VPMC_ERR_TIMEOUT, "an earlier asynchronous call: histories reached the iteration cap");
+    if (status & 6)
+        return fail(VPMC_ERR_DEVICE_FLAG, "an earlier asynchronous call: hand-off or query buffer overflow (status %d)",
+                    status);
+    if (ss) return fail(VPMC_ERR_TIMEOUT, "an earlier asynchronous call: a surrogate tensor-core wait timed out");
     return VPMC_OK;
 }
 
@@ -256,6 +325,7 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     p.nuclear = o.nuclear;
     p.fscale = std::ldexp(1.0f, o.frac_bits);
     p.fx32 = o.frac_bits <= 24 ? 1 : 0;
+    p.max_iter = o.timeout_iters > 0 ? (int)o.timeout_iters : kMaxIter;
     p.records = reinterpret_cast<HistRecord*>(o.history_out);
     p.rec_cap = o.history_out ? o.history_cap : 0;
     p.phase = c->d_phase;
@@ -667,6 +737,9 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
         poly.assign(b->poly_xy, b->poly_xy + 2 * b->n_vertices);
         for (double x : poly)
             if (!std::isfinite(x)) return fail(VPMC_ERR_ARG, "aperture polygon has a non-finite vertex");
+        int e1 = 0, e2 = 0;
+        if (!polygon_is_simple(poly.data(), b->n_vertices, &e1, &e2))
+            return fail(VPMC_ERR_ARG, "aperture polygon is not simple: edges %d and %d meet or overlap", e1, e2);
         double rc = 0.0;
         for (int i = 0; i < b->n_vertices; ++i) rc = std::max(rc, std::hypot(poly[2 * i], poly[2 * i + 1]));
         d.r_circ = (float)rc;
@@ -736,6 +809,8 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
     st = check_spots(c, spots, n_spots);
     if (st != VPMC_OK) return st;
     st = check_surrogate_walls(c, spots, n_spots, o.surrogate);
+    if (st != VPMC_OK) return st;
+    st = pending_status(c);
     if (st != VPMC_OK) return st;
     DevScen sc{{0.0f, 0.0f, 0.0f}, 1.0f};
     if (scen) {
@@ -813,6 +888,7 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
         st = enqueue_transport(c, p, total, t);
         if (st != VPMC_OK) return st;
         CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+        if (!stats_out) c->status_pending = p.surrogate ? 2 : 1;
     }
     const double scale = std::ldexp(1.0, -o.frac_bits) * 1.602176634e-10 /
                          (c->sg_spacing[0] * c->sg_spacing[1] * c->sg_spacing[2] * 1e-3);
@@ -934,6 +1010,8 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     st = check_surrogate_walls(c, spots, n_spots, o.surrogate);
     if (st != VPMC_OK) return st;
     if (n_spots == 0) return fail(VPMC_ERR_ARG, "no spots");
+    st = pending_status(c);
+    if (st != VPMC_OK) return st;
     for (int i = 1; i < n_spots; ++i)
         if (spots[i].beam < spots[i - 1].beam) return fail(VPMC_ERR_ARG, "spots must be sorted by beam id");
     for (int s = 0; s < n_scen; ++s)
@@ -1514,6 +1592,8 @@ vpmc_status vpmc_surrogate_tracks(vpmc_ctx* c, const int* beam_ids, int n_beams,
     vpmc_status st = check_opts(&o);
     if (st != VPMC_OK) return st;
     if (use_surrogate && !c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights");
+    st = pending_status(c);
+    if (st != VPMC_OK) return st;
     std::vector<DevItem> items(n_beams);
     for (int g = 0; g < n_beams; ++g) {
         const int b = beam_ids[g];

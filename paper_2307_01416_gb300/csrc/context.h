@@ -76,6 +76,9 @@ struct vpmc_ctx {
     unsigned long long* d_sq_count = nullptr;
     vpmc::TuneResult tune_dose, tune_im;
     long long launches = 0;                    // kernels launched since creation
+    // an asynchronous dose call left its status word unread (1; 2: with the
+    // surrogate's status word too): the next call reads it first
+    int status_pending = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -83,4 +86,6 @@ namespace vpmc {
 // Records an error message for vpmc_last_error() on the calling thread and
 // returns st (printf-style message).
 vpmc_status report_error(vpmc_status st, const char* fmt, ...);
+// Clears the calling thread's message (at the start of every entry point).
+void clear_error();
 }  // namespace vpmc

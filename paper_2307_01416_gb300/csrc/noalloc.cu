@@ -2,14 +2,13 @@
 //
 // vpmc_run_spots takes its scratch (64-bit accumulator, work items, hand-off
 // buffer, counters) from the context, which grows it with cudaMalloc when a
-// call needs more.  Some callers cannot let a call allocate: code that records
-// work into a CUDA stream capture (cudaMalloc is not a capturable stream
-// operation), serving loops where the implicit device synchronisation of
-// cudaMalloc/cudaFree would stall other streams, and hosts whose memory pool
-// owns all device memory.  vpmc_run_spots_noalloc gives them the same dose
-// with its scratch in one file-scope device array of fixed size, resolved
-// once per device.  The context must already exist (vpmc_create_geometry and
-// vpmc_set_aperture allocate, once, at set-up).
+// call needs more.  Some callers cannot let a call allocate: serving loops
+// where the implicit device synchronisation of cudaMalloc/cudaFree would
+// stall other streams, and hosts whose memory pool owns all device memory.
+// vpmc_run_spots_noalloc gives them the same dose with its scratch in one
+// file-scope device array of fixed size, resolved once per device.  The
+// context must already exist (vpmc_create_geometry and vpmc_set_aperture
+// allocate, once, at set-up).
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -44,6 +43,13 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
+// per device: an asynchronous call (no stats_out) left the array's status
+// word unread, with the stream it ran on; the next call on the device reads it
+struct Pending {
+    bool set = false;
+    cudaStream_t stream = nullptr;
+};
+Pending g_pending[kMaxDevices];
 
 // Device address of the scratch array on the current device; resolved by the
 // first call on that device.
@@ -70,10 +76,41 @@ vpmc_status scratch_address(int device, unsigned char** out)
 
 }  // namespace
 
+namespace {
+
+// Reads the status word that an earlier asynchronous call on this device
+// left unread and reports its error.  It first waits for that call's work:
+// the stream, when the earlier call ran on this call's stream, else the
+// whole device (that stream may belong to another context, or be gone).
+vpmc_status pending_status(int device, cudaStream_t stream)
+{
+    cudaStream_t s = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (!g_pending[device].set) return VPMC_OK;
+        g_pending[device].set = false;
+        s = g_pending[device].stream;
+    }
+    int st_word = 0;
+    if (s == stream) NA_TRY(cudaStreamSynchronize(stream));
+    else NA_TRY(cudaDeviceSynchronize());
+    NA_TRY(cudaMemcpyAsync(&st_word, g_addr[device] + kOffStatus, sizeof st_word, cudaMemcpyDeviceToHost, stream));
+    NA_TRY(cudaStreamSynchronize(stream));
+    if (st_word & 1)
+        return report_error(VPMC_ERR_TIMEOUT, "an earlier asynchronous call: histories reached the iteration cap");
+    if (st_word & 6)
+        return report_error(VPMC_ERR_DEVICE_FLAG, "an earlier asynchronous call: hand-off buffer overflow (status %d)",
+                            st_word);
+    return VPMC_OK;
+}
+
+}  // namespace
+
 extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spots, int n_spots,
                                               const vpmc_scenario* scen, const vpmc_opts* opts_in, float* dose_dev,
                                               vpmc_stats* stats_out)
 {
+    clear_error();
     (void)cudaGetLastError();
     if (!c || !dose_dev) return report_error(VPMC_ERR_ARG, "null context or dose buffer");
     if (c->nvox > kMaxVoxels)
@@ -90,6 +127,9 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     if (o.chunk < 0 || o.chunk > 4096) return report_error(VPMC_ERR_ARG, "chunk %d outside [0, 4096]", o.chunk);
     if (o.history_cap < 0 || (o.history_cap > 0 && !o.history_out))
         return report_error(VPMC_ERR_ARG, "history_cap > 0 needs history_out");
+    if (o.surrogate) return report_error(VPMC_ERR_ARG, "this entry point runs the plain aperture transport only");
+    if (o.timeout_iters < 0 || o.timeout_iters > 0x7fffffffll)
+        return report_error(VPMC_ERR_ARG, "timeout_iters outside [0, 2^31 - 1]");
     DevScen sc{{0.0f, 0.0f, 0.0f}, 1.0f};
     if (scen) {
         if (!(scen->spr_scale > 0)) return report_error(VPMC_ERR_ARG, "scenario spr_scale must be positive");
@@ -100,9 +140,16 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     NA_TRY(cudaGetDevice(&device));
     if (device != c->device) return report_error(VPMC_ERR_STATE, "the context belongs to device %d, current is %d",
                                                  c->device, device);
+    // the work list below is copied from host stack memory during the call
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NA_TRY(cudaStreamIsCapturing(c->stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return report_error(VPMC_ERR_STATE, "the context's stream is capturing; this call copies host stack memory");
     unsigned char* base = nullptr;
     const vpmc_status sa = scratch_address(device, &base);
     if (sa != VPMC_OK) return sa;
+    const vpmc_status ps = pending_status(device, c->stream);
+    if (ps != VPMC_OK) return ps;
     unsigned long long* acc = reinterpret_cast<unsigned long long*>(base + kOffAcc);
     DevItem* items = reinterpret_cast<DevItem*>(base + kOffItems);
     DevBox* box = reinterpret_cast<DevBox*>(base + kOffBox);
@@ -207,6 +254,8 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     p.straggling = o.straggling;
     p.nuclear = o.nuclear;
     p.fscale = std::ldexp(1.0f, o.frac_bits);
+    p.fx32 = o.frac_bits <= 24 ? 1 : 0;
+    p.max_iter = o.timeout_iters > 0 ? (int)o.timeout_iters : kMaxIter;
     p.records = reinterpret_cast<HistRecord*>(o.history_out);
     p.rec_cap = o.history_out ? o.history_cap : 0;
     const TuneResult& t = c->tune_dose;
@@ -230,6 +279,11 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
                          (c->sg_spacing[0] * c->sg_spacing[1] * c->sg_spacing[2] * 1e-3);
     NA_TRY(launch_dose_normalise(acc, c->d_rho, c->nvox, scale, dose_dev, c->stream));
     ++c->launches;
+    if (!stats_out && n_items) {
+        std::lock_guard<std::mutex> lock(g_mu);
+        g_pending[device].set = true;
+        g_pending[device].stream = c->stream;
+    }
     if (stats_out) {
         NA_TRY(cudaStreamSynchronize(c->stream));
         unsigned long long h[3 + kNStats];
@@ -254,6 +308,7 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
         *stats_out = r;
         if (st_word & 1) return report_error(VPMC_ERR_TIMEOUT, "%lld histories reached the iteration cap",
                                              (long long)r.errors);
+        if (st_word & 6) return report_error(VPMC_ERR_DEVICE_FLAG, "hand-off buffer overflow (status %d)", st_word);
     }
     return VPMC_OK;
 }

@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
         if (alive) {
             const DevItem& I = P.items[L.item];
             const DevBeam& B = beams[__ldg(&I.beam)];
-            if (++L.iters > kMaxIter) {
+            if (++L.iters > P.max_iter) {
                 fate = kErr;
             } else if (L.stage < 0) {
                 if (B.rs) {
@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
         if (alive) {
             const DevItem& I = P.items[L.item];
             const DevBeam& B = beams[__ldg(&I.beam)];
-            if (++L.iters > kMaxIter) {
+            if (++L.iters > P.max_iter) {
                 fate = kErr;
             } else if (L.stage < 0) {
                 advance = true;
@@ -1241,7 +1241,7 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
         unsigned long long dep_q = 0ull;
         if (alive) {
             int fate = -1;
-            if (++L.iters > kMaxIter) {
+            if (++L.iters > P.max_iter) {
                 fate = kErr;
             } else {
                 const int cidx = L.ic[0] + P.ctg.n[0] * (L.ic[1] + P.ctg.n[1] * L.ic[2]);   // CT < 2^31 voxels
@@ -1324,7 +1324,7 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                 // the history's totals go straight to the launch's counters
                 // (one history ends every few hundred steps of a lane)
                 if (L.hdep) atomicAdd(P.stats + kStDep, L.hdep);
-                atomicAdd(P.stats + kStSteps, (unsigned long long)min(L.iters, kMaxIter));
+                atomicAdd(P.stats + kStSteps, (unsigned long long)min(L.iters, P.max_iter));
                 if (fate == kLeak || fate == kErr) atomicAdd(P.stats + kStLeak, to_fixed(L.E, P.fscale, P.fx32));
                 if (fate == kErr) { atomicAdd(P.stats + kStErr, 1ull); atomicOr(P.status, 1); }
                 if (P.records) {

@@ -18,7 +18,7 @@ constexpr int kMaxScen = 64;
 constexpr int kMaxPolyVerts = 4096;
 constexpr int kRaster = 256;         // BEV raster per beam (cells per side): opening class, wall-distance bound
 constexpr float kEcut = 0.5f;        // MeV
-constexpr int kMaxIter = 200000;     // iterations per history before it is stopped as an error
+constexpr int kMaxIter = 200000;     // default cap on a history's iterations in one kernel (then it is an error)
 
 enum Material { kWater = 0, kPMMA = 1, kBrass = 2 };
 enum Fate { kStop = 0, kNuc = 1, kLeak = 2, kAbsRS = 3, kAbsAp = 4, kErr = 5 };
@@ -183,6 +183,7 @@ struct TransportParams {
     long long ovf_cap;
     unsigned long long* stats;       // kNStats counters
     int* status;                     // device status word (bit 0: iteration cap)
+    int max_iter;                    // iterations a history may take in one kernel
     HistRecord* records;
     long long rec_cap;
     uint32_t key0, key1_hi;

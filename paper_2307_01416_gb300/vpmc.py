@@ -62,7 +62,8 @@ class vpmc_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("mcs", C.c_int), ("straggling", C.c_int), ("nuclear", C.c_int),
                 ("frac_bits", C.c_int), ("aggregate", C.c_int), ("block_size", C.c_int),
                 ("blocks_per_sm", C.c_int), ("chunk", C.c_int), ("history_out", C.c_void_p),
-                ("history_cap", C.c_int64), ("range_rejection", C.c_int), ("surrogate", C.c_int)]
+                ("history_cap", C.c_int64), ("range_rejection", C.c_int), ("surrogate", C.c_int),
+                ("timeout_iters", C.c_int64)]
 
 
 class vpmc_opt_params(C.Structure):
@@ -162,12 +163,14 @@ def _curve(c: W.HUCurve) -> vpmc_hu_curve:
     return vpmc_hu_curve((C.c_double * 5)(*c.hu), (C.c_double * 5)(*c.density), (C.c_double * 5)(*c.spr))
 
 
-def make_opts(o: W.Options, aggregate: int = -1, block_size: int = 0, chunk: int = 0) -> vpmc_opts:
+def make_opts(o: W.Options, aggregate: int = -1, block_size: int = 0, chunk: int = 0,
+              timeout_iters: int = 0) -> vpmc_opts:
     v = vpmc_opts()
     lib().vpmc_default_opts(C.byref(v))
     v.seed, v.mcs, v.straggling, v.nuclear, v.frac_bits = int(o.seed), int(o.mcs), int(o.straggling), int(o.nuclear), \
         int(o.frac_bits)
     v.aggregate, v.block_size, v.chunk = aggregate, block_size, chunk
+    v.timeout_iters = int(timeout_iters)
     v.range_rejection = int(getattr(o, "range_rejection", True))
     v.surrogate = int(getattr(o, "surrogate", False))
     return v

@@ -287,3 +287,29 @@ def test_step_rule_limits():
     r = O.step_sample(O.WATER, 1.0, 1.0, 0.555087, 36.08, 200.0, mcs=False, straggling=False, nuclear=True,
                       nlam=0.0006)
     assert abs(r["s"] - 0.5) < 1e-12 and r["killed"] == 2 and r["dE"] == 200.0
+
+
+# ----------------------------------------------------------------- dose unit
+def _dose_of(energy_q, frac_bits, spacing, rho):
+    g = W.Grid((len(energy_q), 1, 1), spacing, (0.0, 0.0, 0.0))
+    pb = W.Problem(ct=g, hu=np.zeros((1, 1, len(energy_q)), dtype=np.int16), curve=W.HUCurve(), scoring=g, beams=[])
+    return O.dose_from_q(pb, np.asarray(energy_q, dtype=np.int64), frac_bits, np.asarray(rho, dtype=np.float64))
+
+
+def test_dose_from_fixed_point_hand_values():
+    """Dose-to-medium of scored energy, against values worked out by hand
+    from the SI definitions (1 eV = 1.602176634e-19 J exactly, 1 Gy = 1 J/kg):
+    1 MeV per gram is 1.602176634e-10 Gy.
+      - 1 MeV in a 10 mm cube (1 cm^3) of density 1: 1 g, 1.602176634e-10 Gy;
+      - the same energy in density 2: 0.801088317e-10 Gy;
+      - 3 MeV at frac_bits 10 (q = 3072) in a 2 mm cube (0.008 cm^3) of
+        density 2.5 (0.02 g): 150 MeV/g, 2.403264951e-8 Gy;
+      - 0.25 MeV (q = 2^22 at frac_bits 24) in 1 x 1 x 1.5 mm (0.0015 cm^3) of
+        density 0.5 (0.00075 g): 333.33 MeV/g, 5.340588780e-8 Gy."""
+    d = _dose_of([1 << 24, 1 << 24], 24, (10.0, 10.0, 10.0), [1.0, 2.0])
+    assert d[0] == pytest.approx(1.602176634e-10, rel=1e-12)
+    assert d[1] == pytest.approx(0.801088317e-10, rel=1e-9)
+    d = _dose_of([3072], 10, (2.0, 2.0, 2.0), [2.5])
+    assert d[0] == pytest.approx(2.403264951e-8, rel=1e-9)
+    d = _dose_of([1 << 22], 24, (1.0, 1.0, 1.5), [0.5])
+    assert d[0] == pytest.approx(5.340588780e-8, rel=1e-9)

@@ -63,3 +63,31 @@ def test_no_alloc_rejects_grids_beyond_its_array(torch_cuda):
         eng.run_spots_noalloc(spots, out)
     assert err.value.status == -1 and "at most" in str(err.value)
     eng.close()
+
+
+def test_no_alloc_reports_latched_errors_and_refuses_the_surrogate(torch_cuda):
+    """The fixed array holds a status word too.  A call with statistics
+    reports a history that reached the iteration cap itself; a call without
+    leaves the word to the next call on the device, which reports it and does
+    not run.  The learned surrogate is not available on this entry point."""
+    torch = torch_cuda
+    from paper_2307_01416_gb300 import vpmc
+    pb, spots = W.pencil_beam_water(n_hist=200, shape=(20, 20, 60))
+    eng = vpmc.Engine(pb)
+    ref, _, _ = eng.run_spots(spots, W.Scenario(), W.Options(seed=4))
+    ref = ref.cpu().numpy()
+    out = torch.zeros(ref.shape, dtype=torch.float32, device="cuda")
+    with pytest.raises(vpmc.VpmcError) as err:
+        eng.run_spots_noalloc(spots, out, W.Scenario(), W.Options(seed=4), timeout_iters=50)
+    assert err.value.status == -4
+    assert eng.run_spots_noalloc(spots, out, W.Scenario(), W.Options(seed=4), stats=False, timeout_iters=50) is None
+    with pytest.raises(vpmc.VpmcError) as err:
+        eng.run_spots_noalloc(spots, out, W.Scenario(), W.Options(seed=4))
+    assert err.value.status == -4 and "earlier asynchronous call" in str(err.value)
+    st = eng.run_spots_noalloc(spots, out, W.Scenario(), W.Options(seed=4))
+    assert st["errors"] == 0
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-6, atol=0.0)
+    with pytest.raises(vpmc.VpmcError) as err:
+        eng.run_spots_noalloc(spots, out, W.Scenario(), W.Options(seed=4, surrogate=True))
+    assert err.value.status == -1
+    eng.close()
