@@ -33,7 +33,7 @@ from paper_2307_01416_gb300 import workloads as W  # noqa: E402
 METRIC = "protons/s; s per 13-scenario influence-matrix set at 0.5% unc."
 WORKLOAD = ("13-scenario robust influence-matrix set, synthetic head 256x256x160 CT (1x1x1.5 mm), 2 mm scoring grid, "
             "8.4 cc target, 3 fields 0/90/270 deg, 45 mm WET range shifter, brass apertures (target + 5 mm), "
-            "3 mm spots, 1e3-2e4 histories/spot")
+            "3 mm spots, log-uniform 1e3-2e4 histories/spot scaled to 0.5% uncertainty of the nominal composite")
 # Lane-operations of one condensed-history step of the full-physics method,
 # counted for a minimal implementation of the step's formulas: one
 # Philox4x32-10 block 80, six uniforms 22, three Box-Muller pairs 24, four
@@ -72,7 +72,7 @@ def parse_args():
 
 
 def build_workload(small: bool):
-    pb, spots, center, r = W.head_plan(8.4)
+    pb, spots, center, r = W.im_set_plan()
     if small:
         spots = spots.copy()
         spots["n_hist"] = np.maximum(spots["n_hist"] // 50, 20)
@@ -153,6 +153,31 @@ def measured_peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+# ----------------------------------------------------------------------------- statistical uncertainty
+SIGMA_TARGET = 0.005
+
+
+def nominal_sigma_rel(eng, pb, spots, seed: int, n_batches: int = 10):
+    """Statistical uncertainty of the set's nominal composite dose (every
+    spot, weight 1 per history) by the batch method: n_batches independent
+    dose runs, each with 1/n_batches of every spot's histories; sigma_rel =
+    mean SE / D over tissue voxels at or above half the maximum."""
+    from paper_2307_01416_gb300 import uncertainty as U
+    mask = W.tissue_mask(pb)
+    sub = spots.copy()
+    sub["n_hist"] = U.split_histories(spots["n_hist"], n_batches)
+    doses = []
+    for b in range(n_batches):
+        d, _, _ = eng.run_spots(sub, W.Scenario(), W.Options(seed=seed + 100003 * (b + 1)))
+        doses.append(d.reshape(-1).double().cpu().numpy())
+    s, nvox = U.batch_sigma_rel(np.stack(doses), mask, level=0.5)
+    return {"sigma_rel": s, "target": SIGMA_TARGET, "voxels": nvox, "batches": n_batches,
+            "histories": n_batches * int(sub["n_hist"].sum()), "hist_scale": W.IM_SET_HIST_SCALE,
+            "method": "batch method: %d independent dose runs of the nominal scenario, each 1/%d of every spot's "
+                      "histories; mean SE/D over tissue voxels (HU >= -500) at >= 50%% of the maximum"
+                      % (n_batches, n_batches)}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -303,6 +328,7 @@ def main():
         torch.cuda.synchronize()
         ck = clocks.stop()
         t = ev0.elapsed_time(ev1) / 1000.0
+        unc = nominal_sigma_rel(eng, pb, spots, opts.seed) if rank == 0 else None   # untimed
         eng.close()                                # frees the set's column scratch before the e2e leg
     t, hist_all = reduce_over_ranks(t, hist, world, "cuda")
     value = hist_all / t
@@ -350,6 +376,7 @@ def main():
                "config": {"workload": WORKLOAD + (" (reduced histories)" if args.small else ""),
                           "scenarios": len(scens), "spots_per_scenario": int(len(spots)),
                           "histories_per_set": int(set_hist), "nnz_per_set": nnz,
+                          "sigma_rel": unc["sigma_rel"] if unc else None, "uncertainty": unc,
                           "l2": "512 MiB buffer written between sets; the set's 100+ GB column scratch exceeds L2",
                           "parallelism": "independent sets per GPU" if world > 1 else "1 GPU"},
                "s_per_im_set": ms_per_step / 1000.0,
@@ -386,7 +413,8 @@ def run_ncu_case(args):
         else:
             dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=896, aggregate=1, chunk=32)
         print(json.dumps({"case": "ncu-" + args.ncu_case, "iter": i, "histories": st["histories"],
-                          "steps": st["steps"], "kernel_ms": st["ms"],
+                          "steps": st["steps"], "steps_rs": st["steps_rs"], "steps_aperture": st["steps_aperture"],
+                          "kernel_ms": st["ms"],
                           "steps_per_s": st["steps"] / (st["ms"] / 1000.0)}))
     eng.close()
     return 0
@@ -667,7 +695,7 @@ def dynamic_leg(scens, opts, plain_value, peak_tops):
     one untimed and one timed set."""
     import torch
     from paper_2307_01416_gb300 import vpmc
-    pb, spots, _, _ = W.head_plan(8.4, dynamic_aperture=True)
+    pb, spots, _, _ = W.im_set_plan(dynamic_aperture=True)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         eng = vpmc.Engine(pb, stream=stream)

@@ -155,6 +155,8 @@ typedef struct {
     float ms;               /* device time of the transport launch(es), CUDA events */
     int64_t launches;       /* kernels this call launched (autotuning included) */
     int64_t ovf_records;    /* influence matrix: deposits outside their column's dense box */
+    int64_t steps_rs;       /* condensed-history steps in the range shifter (included in steps) */
+    int64_t steps_aperture; /* condensed-history steps in the brass block (included in steps) */
 } vpmc_stats;
 
 /* Sparse influence matrix of one scenario: rows = scoring voxels (x-fastest),

@@ -570,6 +570,8 @@ vpmc_status read_stats(vpmc_ctx* c, int frac_bits, vpmc_stats* acc, bool add)
     acc->e_nuc += h[kStNuc] * sc;
     acc->steps += (int64_t)h[kStSteps];
     acc->errors += (int64_t)h[kStErr];
+    acc->steps_rs += (int64_t)h[kStStepsRS];
+    acc->steps_aperture += (int64_t)h[kStStepsAp];
     return VPMC_OK;
 }
 

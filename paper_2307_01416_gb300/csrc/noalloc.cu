@@ -297,6 +297,8 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
         r.histories = total;
         r.steps = (int64_t)v[kStSteps];
         r.errors = (int64_t)v[kStErr];
+        r.steps_rs = (int64_t)v[kStStepsRS];
+        r.steps_aperture = (int64_t)v[kStStepsAp];
         r.e_in = e_in;
         r.e_dep = v[kStDep] * q;
         r.e_leak = v[kStLeak] * q;

@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
             }
         }
     }
-    unsigned long long v[kNStats] = {0ull, acc_leak, acc_rs, 0ull, acc_nuc, acc_steps, acc_err};
+    unsigned long long v[kNStats] = {0ull, acc_leak, acc_rs, 0ull, acc_nuc, acc_steps, acc_err, acc_steps, 0ull};
     warp_add_stats(P, v, lane);
 }
 
@@ -1104,7 +1104,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             }
         }
     }
-    unsigned long long v[kNStats] = {0ull, acc_leak, 0ull, acc_ap, acc_nuc, acc_steps, acc_err};
+    unsigned long long v[kNStats] = {0ull, acc_leak, 0ull, acc_ap, acc_nuc, acc_steps, acc_err, 0ull, acc_steps};
     warp_add_stats(P, v, lane);
 }
 

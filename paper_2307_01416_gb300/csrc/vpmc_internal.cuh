@@ -22,7 +22,9 @@ constexpr int kMaxIter = 200000;     // default cap on a history's iterations in
 
 enum Material { kWater = 0, kPMMA = 1, kBrass = 2 };
 enum Fate { kStop = 0, kNuc = 1, kLeak = 2, kAbsRS = 3, kAbsAp = 4, kErr = 5 };
-enum Stat { kStDep = 0, kStLeak, kStRS, kStAp, kStNuc, kStSteps, kStErr, kNStats };
+// kStSteps counts condensed-history steps in every medium; kStStepsRS and
+// kStStepsAp the range shifter's and the brass block's share of them.
+enum Stat { kStDep = 0, kStLeak, kStRS, kStAp, kStNuc, kStSteps, kStErr, kStStepsRS, kStStepsAp, kNStats };
 
 struct MatConst {
     float za;          // Z/A

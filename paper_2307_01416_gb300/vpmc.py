@@ -75,7 +75,7 @@ class vpmc_stats(C.Structure):
     _fields_ = [("histories", C.c_int64), ("steps", C.c_int64), ("errors", C.c_int64), ("e_in", C.c_double),
                 ("e_dep", C.c_double), ("e_leak", C.c_double), ("e_rs", C.c_double), ("e_aperture", C.c_double),
                 ("e_nuc", C.c_double), ("ms", C.c_float), ("launches", C.c_int64),
-                ("ovf_records", C.c_int64)]
+                ("ovf_records", C.c_int64), ("steps_rs", C.c_int64), ("steps_aperture", C.c_int64)]
 
 
 class vpmc_csr(C.Structure):

@@ -369,11 +369,12 @@ def radiological_depths(g: Grid, hu: np.ndarray, curve: HUCurve, start, directio
 def head_plan(volume_cc: float = 8.4, ct_seed: int = 1234, target_seed: int = 1235, gantries=(0.0, 90.0, 270.0),
               range_shifter: bool = True, spot_spacing: float = 3.0, margin_mm: float = 5.0, n_vertices: int = 64,
               hist_lo: int = 1000, hist_hi: int = 20000, hist_seed: int = 77, scoring_mm: float = 2.0,
-              dynamic_aperture: bool = False, ap_sad: float = 0.0):
+              dynamic_aperture: bool = False, ap_sad: float = 0.0, hist_scale: float = 1.0):
     """Three-field SRS plan on the synthetic head: apertures = target projection
     + margin (regular n-gon), 45 mm WET range shifter, spots on a 3 mm grid over
     the opening, layers 3 mm WET apart covering the target depth +/- 5 mm,
-    n_hist per spot log-uniform in [hist_lo, hist_hi].
+    n_hist per spot log-uniform in [hist_lo, hist_hi], then multiplied by
+    hist_scale (rounded up) when it is not 1.
 
     dynamic_aperture (the authors' future work, Sec. 4): one beam entry per
     (field, energy layer) with the field's geometry and its own opening: the
@@ -415,6 +416,8 @@ def head_plan(volume_cc: float = 8.4, ct_seed: int = 1234, target_seed: int = 12
             beams.pop()
         for e in energies:
             nh = np.exp(rng.uniform(np.log(hist_lo), np.log(hist_hi), size=len(xy))).astype(np.int64)
+            if hist_scale != 1.0:
+                nh = np.ceil(nh * float(hist_scale)).astype(np.int64)
             sig = float(spot_sigma_mm(e))
             entry = bi
             if dynamic_aperture:
@@ -427,6 +430,20 @@ def head_plan(volume_cc: float = 8.4, ct_seed: int = 1234, target_seed: int = 12
                 rows.append((entry, float(e), float(x), float(y), sig, 2.0, int(n), 1.0))
     pb = Problem(ct=g, hu=hu, curve=curve, scoring=sg, beams=beams)
     return pb, make_spots(rows), center, r_t
+
+
+# Histories per spot of the 13-scenario influence-matrix set (the benchmarked
+# workload): the head plan's log-uniform counts times this factor, which the
+# batch method (paper_2307_01416_gb300.uncertainty, 10 batches) measured to
+# bring the nominal composite dose to 0.5 % over the tissue voxels at or
+# above half its maximum (Sec. 2.D.3: plans at about 0.5 %).
+IM_SET_HIST_SCALE = 1.0
+
+
+def im_set_plan(dynamic_aperture: bool = False, ap_sad: float = 0.0):
+    """The benchmarked influence-matrix plan: head_plan(8.4 cc) with the
+    histories scaled to 0.5 % uncertainty."""
+    return head_plan(8.4, hist_scale=IM_SET_HIST_SCALE, dynamic_aperture=dynamic_aperture, ap_sad=ap_sad)
 
 
 # --------------------------------------------------------------------------
@@ -464,6 +481,21 @@ def structure_classes(grid: Grid, center, r_target: float, ring_mm: float = 10.0
     c[r <= r_target + ring_mm] = 2
     c[r <= r_target] = 1
     return np.ascontiguousarray(c.transpose(2, 1, 0)).reshape(-1)
+
+
+def tissue_mask(problem: Problem, hu_min: float = -500.0) -> np.ndarray:
+    """bool per scoring voxel (x fastest): the CT voxel at the scoring
+    voxel's centre has HU >= hu_min (tissue and bone; the head's air cavities
+    and the air around it are excluded, where dose-to-medium of a few
+    deposits exceeds the tissue maximum).  -500 HU is about 0.5 g/cc on the
+    default curve."""
+    g, s = problem.ct, problem.scoring
+    idx = []
+    for k in range(3):
+        c = s.centers(k)
+        idx.append(np.clip(np.floor((c - g.origin[k]) / g.spacing[k]).astype(np.int64), 0, g.shape[k] - 1))
+    hu = np.asarray(problem.hu)[np.ix_(idx[2], idx[1], idx[0])]
+    return np.ascontiguousarray(hu >= hu_min).reshape(-1)
 
 
 def synthetic_spot_matrices(shape=(36, 36, 40), n_spots: int = 300, n_scen: int = 3, seed: int = 11,

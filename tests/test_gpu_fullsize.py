@@ -31,7 +31,7 @@ def fullset():
         pytest.skip("no CUDA device")
     torch.cuda.set_device(0)
     from paper_2307_01416_gb300 import vpmc
-    pb, spots, _, _ = W.head_plan(8.4)
+    pb, spots, _, _ = W.im_set_plan()
     scens = W.robust_scenarios()
     eng = vpmc.Engine(pb)
     mats, st = eng.influence_matrix(spots, scens, W.Options(seed=SEED))
@@ -139,9 +139,10 @@ def test_sampled_histories_full_physics(fullset):
     keep[list(SAMPLE)] = True
     only["n_hist"] = np.where(keep, np.minimum(spots["n_hist"], 3000), 0)
     n = int(only["n_hist"].sum())
-    # the whole spot list with zero histories elsewhere keeps every spot's RNG key
+    # the whole spot list with zero histories elsewhere keeps every spot's RNG
+    # key; the GPU takes the plain brass steps of the oracle (no range rejection)
     eng = vpmc.Engine(pb)
-    _, _, rec = eng.run_spots(only, scens[0], W.Options(seed=SEED), records=n)
+    _, _, rec = eng.run_spots(only, scens[0], W.Options(seed=SEED, range_rejection=False), records=n)
     eng.close()
     _, _, orec = O.run(pb, O.oracle_spots(only), scens[0], W.Options(seed=SEED), records=n)
     fate = rec["fate"] == orec["fate"]

@@ -113,3 +113,23 @@ def test_head_plan_sizes():
     assert pb.scoring.spacing == (2.0, 2.0, 2.0) and pb.scoring.shape == (128, 128, 120)
     assert np.all(spots["div_mrad"] == 2.0)
     assert np.allclose(spots["sigma"], W.spot_sigma_mm(spots["energy"]))
+
+
+def test_tissue_mask_follows_the_ct_at_scoring_voxel_centres():
+    """A 2 mm scoring voxel is tissue when the 1 mm CT voxel at its centre
+    is; air (-1000 HU) and lung-like -600 HU are not, -400 HU is."""
+    g = W.Grid((8, 4, 6), (1.0, 1.0, 1.5), (0.0, 0.0, 0.0))
+    hu = np.zeros((6, 4, 8), dtype=np.int16)
+    hu[:, :, :4] = -1000            # x < 4 mm: air
+    hu[:, :, 5] = -600              # the CT column holding the centre of scoring x-voxel 2
+    hu[:3, :, 7] = -400
+    sg = W.Grid((4, 2, 4), (2.0, 2.0, 2.25), (0.0, 0.0, 0.0))
+    pb = W.Problem(ct=g, hu=hu, curve=W.HUCurve(), scoring=sg, beams=[])
+    m = W.tissue_mask(pb).reshape(4, 2, 4)
+    assert not m[:, :, :2].any()
+    assert not m[:, :, 2].any()
+    # scoring x-voxel 3 has its centre at 7 mm (CT column 7): -400 HU in the
+    # first three CT slices (z < 4.5 mm: scoring z-voxels 0 and 1), water above
+    assert m[:, :, 3].all()
+    pb2, _ = W.pencil_beam_water(n_hist=1, shape=(10, 10, 10))
+    assert W.tissue_mask(pb2).all()
