@@ -35,12 +35,23 @@ WORKLOAD = ("13-scenario robust influence-matrix set, synthetic head 256x256x160
             "8.4 cc target, 3 fields 0/90/270 deg, 45 mm WET range shifter, brass apertures (target + 5 mm), "
             "3 mm spots, log-uniform 1e3-2e4 histories/spot scaled to 0.5% uncertainty of the nominal composite")
 # Lane-operations of one condensed-history step of the full-physics method,
-# counted for a minimal implementation of the step's formulas: one
-# Philox4x32-10 block 80, six uniforms 22, three Box-Muller pairs 24, four
-# table interpolations 32, step selection 12, two-grid DDA 33, Bohr 15,
-# Highland 10, rotation and displacement 45, scoring 11, position update and
-# voxel confinement 15.
+# counted for a minimal implementation of the step's formulas.  In the
+# patient: one Philox4x32-10 block 80, six uniforms 22, three Box-Muller
+# pairs 24, four table interpolations 32, step selection 12, two-grid DDA 33,
+# Bohr 15, Highland 10, rotation and displacement 45, scoring 11, position
+# update 6 and voxel confinement 9.  In a homogeneous slab (range shifter,
+# brass block) there is no voxel grid: no DDA, scoring or confinement, and the
+# geometry limit is the distance to the slab's exit plane (4); in the brass
+# the opening test adds a raster look-up (8).
 OPS_PER_STEP = 299
+OPS_PER_STEP_RS = 299 - 33 - 11 - 9 + 4
+OPS_PER_STEP_BRASS = OPS_PER_STEP_RS + 8
+
+
+def algorithmic_ops(st: dict) -> float:
+    """Lane-operations of the condensed-history steps a call counted, by medium."""
+    rs, ap = st["steps_rs"], st["steps_aperture"]
+    return (st["steps"] - rs - ap) * OPS_PER_STEP + rs * OPS_PER_STEP_RS + ap * OPS_PER_STEP_BRASS
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -134,17 +145,26 @@ def transport_traffic(steps_per_launch: float):
     kernels measured on the small influence-matrix case (dram__bytes_read.sum
     + dram__bytes_write.sum over its steps), scaled by the set's steps; None
     when the kernels changed since that capture (source hash)."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "k_transport_traffic.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
     except OSError:
         return None
-    src = os.path.join(ROOT, "paper_2307_01416_gb300", "csrc", "transport.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if kv.get("transport_cu_sha256") != digest:
+    if kv.get("transport_sha256") != transport_source_digest():
         return None
     return float(kv["dram_bytes_per_step"]) * steps_per_launch
+
+
+TRANSPORT_SOURCES = ("transport_common.cuh", "devices.cu", "patient.cu")
+
+
+def transport_source_digest() -> str:
+    """sha256 over the transport kernels' sources, in a fixed order."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRANSPORT_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2307_01416_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
 
 
 def measured_peaks():
@@ -311,12 +331,15 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        kern_ms, steps, hist, nnz = 0.0, 0, 0, 0
+        kern_ms, steps, hist, nnz, ops, ms_patient, patient_steps = 0.0, 0, 0, 0, 0.0, 0.0, 0
         for _ in range(args.steps):
             flush.fill_(1.0)                       # evict L2 between sets
             mats, st = eng.influence_matrix(spots, scens, opts)
             kern_ms += st["ms"]
             steps += st["steps"]
+            ops += algorithmic_ops(st)
+            ms_patient += st["ms_patient"]
+            patient_steps += st["steps"] - st["steps_rs"] - st["steps_aperture"]
             hist += st["histories"]
             launches += st["launches"] + 1
             nnz = sum(int(m["val"].numel()) for m in mats)
@@ -340,13 +363,24 @@ def main():
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
         peak_tops = nsm * 4 * 32 * sm_max * 1e6 / 1e12
-        achieved = steps * OPS_PER_STEP / (kern_ms / 1000.0) / 1e12
+        achieved = ops / (kern_ms / 1000.0) / 1e12
         traffic = transport_traffic(steps / args.steps)
+        l2 = vpmc.measure_l2_atomics()                 # untimed: the secondary bound's peak
+        adds_rate = patient_steps / (ms_patient / 1000.0) if ms_patient > 0 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": traffic, "kernel": "k_source_rs+k_aperture+k_patient",
                 "peak_note": "%d SMs x 4 sub-partitions x 32 lanes x %.0f MHz (max SM clock) lane-ops/s; "
-                             "%d lane-ops per condensed-history step" % (nsm, sm_max, OPS_PER_STEP),
-                "kernel_ms_per_step": kern_ms / args.steps, "steps_per_launch": steps / args.steps}
+                             "lane-ops per condensed-history step: %d in the patient, %d in the range shifter, "
+                             "%d in the brass" % (nsm, sm_max, OPS_PER_STEP, OPS_PER_STEP_RS, OPS_PER_STEP_BRASS),
+                "kernel_ms_per_step": kern_ms / args.steps, "steps_per_launch": steps / args.steps,
+                "ops_per_step": ops / max(steps, 1),
+                "l2_atomic": {"kernel": "k_patient", "unit": "adds/s",
+                              "achieved": adds_rate, "peak": l2["adds_per_s"],
+                              "frac": adds_rate / l2["adds_per_s"] if adds_rate else None,
+                              "k_patient_ms_per_step": ms_patient / args.steps,
+                              "note": "one 64-bit scoring add per patient step (plain atomics; warp aggregation "
+                                      "would issue fewer) over k_patient's CUDA-event time; peak = "
+                                      "vpmc_measure_l2_atomics over a 32 MiB buffer"}}
         e2e = None
         if not args.no_e2e:
             e2e = e2e_leg(pb, spots, scens, opts, args)
@@ -414,7 +448,8 @@ def run_ncu_case(args):
             dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=896, aggregate=1, chunk=32)
         print(json.dumps({"case": "ncu-" + args.ncu_case, "iter": i, "histories": st["histories"],
                           "steps": st["steps"], "steps_rs": st["steps_rs"], "steps_aperture": st["steps_aperture"],
-                          "kernel_ms": st["ms"],
+                          "kernel_ms": st["ms"], "ms_devices": st["ms_devices"], "ms_patient": st["ms_patient"],
+                          "ops_per_step": algorithmic_ops(st) / max(st["steps"], 1),
                           "steps_per_s": st["steps"] / (st["ms"] / 1000.0)}))
     eng.close()
     return 0
@@ -467,7 +502,7 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
     import dataclasses
     import torch
     from paper_2307_01416_gb300 import vpmc
-    tpb, epochs, batch = 4_000_000, 20, 16384
+    tpb, epochs, batch = 12_500_000, 20, 16384
     tr = vpmc.Engine(vpmc.surrogate_training_problem())
     t0 = time.perf_counter()
     feat, target, label = tr.surrogate_tracks(list(range(8)), tpb, W.Options(seed=W.SURROGATE_SEED))
@@ -606,7 +641,7 @@ def edge_sweep_leg(args, peak_tops):
     out = {}
     with torch.cuda.stream(stream):
         for mode in ("per_beamlet", "batched"):
-            total_s, hist, steps, kern_ms, launches = 0.0, 0, 0, 0.0, 0
+            total_s, hist, steps, kern_ms, launches, ops = 0.0, 0, 0, 0.0, 0, 0.0
             for rs in (False, True):
                 pb = W.edge_beamlet_problem(rs)
                 eng = vpmc.Engine(pb, stream=stream)
@@ -626,6 +661,7 @@ def edge_sweep_leg(args, peak_tops):
                                                  W.Options(seed=100 + k))
                         hist += st["histories"]
                         steps += st["steps"]
+                        ops += algorithmic_ops(st)
                         kern_ms += st["ms"]
                         launches += st["launches"]
                         del d
@@ -633,6 +669,7 @@ def edge_sweep_leg(args, peak_tops):
                     m, st = eng.influence_matrix(spots, [W.Scenario()], W.Options(seed=100))
                     hist += st["histories"]
                     steps += st["steps"]
+                    ops += algorithmic_ops(st)
                     kern_ms += st["ms"]
                     launches += st["launches"] + 1
                     del m
@@ -640,7 +677,7 @@ def edge_sweep_leg(args, peak_tops):
                 torch.cuda.synchronize()
                 total_s += ev0.elapsed_time(ev1) / 1000.0
                 eng.close()
-            achieved = steps * OPS_PER_STEP / (kern_ms / 1000.0) / 1e12
+            achieved = ops / (kern_ms / 1000.0) / 1e12
             out[mode] = {"s_per_sweep": total_s, "value": hist / total_s, "histories": hist,
                          "gpu_launches": launches,
                          "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
@@ -678,7 +715,7 @@ def divergent_leg(pb, spots, scens, opts, args, plain_value, peak_tops):
         nnz = sum(int(m["val"].numel()) for m in mats)
         del mats
         eng.close()
-    achieved = st["steps"] * OPS_PER_STEP / (st["ms"] / 1000.0) / 1e12
+    achieved = algorithmic_ops(st) / (st["ms"] / 1000.0) / 1e12
     return {"sad_mm": float(args.divergent_sad), "value": st["histories"] / t, "unit": "protons/s",
             "s_per_im_set": t, "relative_to_parallel": st["histories"] / t / plain_value, "nnz_per_set": nnz,
             "gpu_launches": st["launches"] + 1,
@@ -712,7 +749,7 @@ def dynamic_leg(scens, opts, plain_value, peak_tops):
         nnz = sum(int(m["val"].numel()) for m in mats)
         del mats
         eng.close()
-    achieved = st["steps"] * OPS_PER_STEP / (st["ms"] / 1000.0) / 1e12
+    achieved = algorithmic_ops(st) / (st["ms"] / 1000.0) / 1e12
     return {"beam_entries": len(pb.beams), "value": st["histories"] / t, "unit": "protons/s", "s_per_im_set": t,
             "relative_to_static": st["histories"] / t / plain_value, "nnz_per_set": nnz,
             "e_aperture_fraction": st["e_aperture"] / st["e_in"], "gpu_launches": st["launches"] + 1,

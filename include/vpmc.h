@@ -157,6 +157,10 @@ typedef struct {
     int64_t ovf_records;    /* influence matrix: deposits outside their column's dense box */
     int64_t steps_rs;       /* condensed-history steps in the range shifter (included in steps) */
     int64_t steps_aperture; /* condensed-history steps in the brass block (included in steps) */
+    float ms_devices;       /* device time of the beam-line kernels (source, range shifter, aperture,
+                               surrogate draws) within ms, CUDA events; 0 for vpmc_run_spots_noalloc */
+    float ms_patient;       /* device time of the patient kernel within ms, CUDA events; 0 for
+                               vpmc_run_spots_noalloc */
 } vpmc_stats;
 
 /* Sparse influence matrix of one scenario: rows = scoring voxels (x-fastest),
@@ -280,7 +284,9 @@ vpmc_status vpmc_free_csr(vpmc_csr* csr, int n);
  *   y2 = (exit - entry) . t - T (d_in . t) / d_in,z
  *   y3 = (d_out - d_in) . n / 0.05,  y4 = (d_out - d_in) . t / 0.05
  * Training domain: E in [40, 230] MeV, |d . n| and |d . t| <= 0.12,
- * curvature in [-0.001, 0.26] / mm, block thickness 30 mm.  With
+ * curvature in [-0.001, 0.26] / mm, block thickness 30 mm, and |x5| >= 0.06
+ * (away from the stopping threshold, where the exit energy has a sharp
+ * edge that the mixture does not follow).  With
  * opts->surrogate = 1, a brass entry outside this domain takes the plain
  * path.  A brass entry whose 1.2 x CSDA range is below both its edge distance
  * and the thickness is absorbed without a draw.
@@ -391,6 +397,24 @@ vpmc_status vpmc_weights_dose(const vpmc_csr* mat, const float* x_dev, float* do
  * out is a host array.  Synchronous. */
 vpmc_status vpmc_target_indices(const vpmc_csr* mats, int n_scen, const uint8_t* voxel_class_dev,
                                 float prescription, const float* x_dev, double* out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement.  The paper has no counterpart.
+ * ------------------------------------------------------------------------ */
+
+/* The current device's rate of 64-bit atomic adds resolved in L2: the
+ * secondary bound of the transport's scoring, which adds each
+ * condensed-history step's fixed-point deposit to a voxel with one such add.
+ * 4 x SMs blocks of 1024 threads each make `iters` adds of 1 to entries of a
+ * device buffer of n_entries 64-bit words (a power of two in [32, 2^26];
+ * 2^22 words, 32 MiB, stay in L2), chosen by a hash of (thread, iteration),
+ * results unused.  One untimed pass, then a timed one between CUDA events
+ * on `stream` (a cudaStream_t, NULL = legacy default).  Outputs: adds_per_s
+ * (timed pass), adds_out (adds of the timed pass) and sum_out (the buffer's
+ * sum after both passes: 2 x adds_out when every add landed); the last two
+ * may be NULL.  The call allocates and frees its buffer.  Synchronous. */
+vpmc_status vpmc_measure_l2_atomics(int64_t n_entries, int iters, double* adds_per_s, int64_t* adds_out,
+                                    int64_t* sum_out, void* stream);
 
 /* Destroy a context and free its device memory. */
 void vpmc_destroy(vpmc_ctx* ctx);

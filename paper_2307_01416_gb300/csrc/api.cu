@@ -301,10 +301,10 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     TransportParams p{};
     p.tables = c->d_tables;
     p.water = c->water_mat;
-    p.ct = c->d_ct;
+    p.ct_lut = reinterpret_cast<const uint16_t*>(c->d_ct);
     p.ctg = c->ctg;
     p.sg = c->sg;
-    p.same_grid = c->same_grid ? 1 : 0;
+    for (int k = 0; k < 3; ++k) p.nest_shift[k] = c->nest_shift[k];
     p.beams = c->d_beams;
     p.n_beams = kMaxBeams;
     p.scens = c->d_scens;
@@ -388,12 +388,17 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
         p.sq_cap = c->sq_cap;
         p.sq_count = c->d_sq_count;
     }
+    // the batch events are recorded as event nodes when the transport is
+    // captured into a graph (external records), or directly otherwise
+    c->kev_batches = 0;
     for (long long h0 = 0; h0 < total; h0 += c->phase_cap) {
+        const int b = c->kev_batches < vpmc_ctx::kTimedBatches ? c->kev_batches++ : -1;
         p.hist_begin = h0;
         p.total = std::min(total, h0 + c->phase_cap);
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
         CUDA_TRY(cudaMemsetAsync(c->d_phase_count, 0, sizeof(unsigned long long), c->stream));
         if (p.surrogate) CUDA_TRY(cudaMemsetAsync(c->d_sq_count, 0, sizeof(unsigned long long), c->stream));
+        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b], c->stream, cudaEventRecordExternal));
         CUDA_TRY(launch_devices(p, c->num_sms, t.dev_block, c->stream));
         if (p.surrogate) {
             // brass entries in the surrogate's domain: one network draw each
@@ -401,7 +406,9 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
             c->launches += 1;
         }
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
+        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b + 1], c->stream, cudaEventRecordExternal));
         CUDA_TRY(launch_patient(p, c->num_sms, t.block, c->stream));
+        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b + 2], c->stream, cudaEventRecordExternal));
         c->launches += 3;
     }
     return VPMC_OK;
@@ -557,6 +564,20 @@ TuneResult resolve_launch(const vpmc_opts& o, const TuneResult& t)
     return r;
 }
 
+// Device time of the beam-line kernels and of the patient kernel over the
+// batches the last transport recorded (its work has completed).
+vpmc_status add_kernel_times(vpmc_ctx* c, vpmc_stats* acc)
+{
+    for (int b = 0; b < c->kev_batches; ++b) {
+        float a = 0.0f, p = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&a, c->kev[3 * b], c->kev[3 * b + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&p, c->kev[3 * b + 1], c->kev[3 * b + 2]));
+        acc->ms_devices += a;
+        acc->ms_patient += p;
+    }
+    return VPMC_OK;
+}
+
 vpmc_status read_stats(vpmc_ctx* c, int frac_bits, vpmc_stats* acc, bool add)
 {
     unsigned long long h[kNStats];
@@ -644,8 +665,17 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     c->ctg = to_grid3(*ct);
     c->sg = to_grid3(*dose_grid);
     for (int k = 0; k < 3; ++k) { c->ct_spacing[k] = cd[k]; c->sg_spacing[k] = sd[k]; }
-    c->same_grid = true;
-    for (int k = 0; k < 3; ++k) c->same_grid = c->same_grid && cn[k] == sn[k] && cd[k] == sd[k];
+    // nested axes: the scoring grid's faces are CT faces (same FP32 origin,
+    // FP32 spacing 2^sh x the CT's, 2^sh CT voxels per scoring voxel)
+    for (int k = 0; k < 3; ++k) {
+        c->nest_shift[k] = -1;
+        for (int sh = 0; sh <= 3; ++sh)
+            if (c->sg.lo[k] == c->ctg.lo[k] && c->sg.d[k] == std::ldexp(c->ctg.d[k], sh) &&
+                (long long)sn[k] << sh == (long long)cn[k]) {
+                c->nest_shift[k] = sh;
+                break;
+            }
+    }
     c->nvox = (long long)sn[0] * sn[1] * sn[2];
     for (int i = 0; i < 5; ++i) {
         c->curve15[i] = curve->hu[i];
@@ -675,6 +705,8 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     CTX_TRY(dev_alloc(&c->d_rho, c->nvox));
     CTX_TRY(launch_scoring_density(c->d_ct, c->ctg, c->sg, c->d_curve, c->ct_spacing, c->sg_spacing, c->d_rho,
                                    c->stream));
+    // from here on the CT holds the kernels' table index per voxel
+    CTX_TRY(launch_ct_lut_index(c->d_ct, nct, c->stream));
     CTX_TRY(dev_alloc(&c->d_beams, kMaxBeams));
     CTX_TRY(dev_alloc(&c->d_counter, 1));
     CTX_TRY(dev_alloc(&c->d_phase_count, 1));
@@ -684,6 +716,7 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     CTX_TRY(dev_alloc(&c->d_scens, kMaxScen));
     CTX_TRY(cudaEventCreate(&c->ev0));
     CTX_TRY(cudaEventCreate(&c->ev1));
+    for (cudaEvent_t& e : c->kev) CTX_TRY(cudaEventCreate(&e));
     CTX_TRY(cudaStreamSynchronize(c->stream));
 #undef CTX_TRY
     st = upload_beams(c);
@@ -904,6 +937,8 @@ vpmc_status vpmc_run_spots(vpmc_ctx* c, const vpmc_spot* spots, int n_spots, con
             float ms = 0.0f;
             CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
             stats.ms = ms;
+            st = add_kernel_times(c, &stats);
+            if (st != VPMC_OK) return st;
             int status = 0;
             CUDA_TRY(cudaMemcpy(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost));
             stats.histories = total;
@@ -1221,6 +1256,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         IM_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
         total_ms += ms;
         IM_ST(read_stats(c, o.frac_bits, &stats, true));
+        IM_ST(add_kernel_times(c, &stats));
         int status = 0;
         IM_TRY(cudaMemcpy(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost));
         if (status & 1) {
@@ -1393,6 +1429,8 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->sur.status);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (cudaEvent_t e : c->kev)
+        if (e) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

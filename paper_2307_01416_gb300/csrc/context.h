@@ -28,10 +28,10 @@ struct vpmc_ctx {
     bool own_stream = false;
     vpmc::Grid3 ctg{}, sg{};
     double ct_spacing[3]{}, sg_spacing[3]{};
-    bool same_grid = false;
+    int nest_shift[3]{-1, -1, -1};      // per axis: scoring spacing = CT spacing << shift, same origin (-1: not)
     long long nvox = 0;
     double curve15[15]{};
-    int16_t* d_ct = nullptr;
+    int16_t* d_ct = nullptr;                  // CT: HU until the scoring densities are built, then table indices
     vpmc::TablesImage* d_tables = nullptr;
     vpmc::MatConst water_mat{};          // the tables image's water entry (a launch constant)
     double* d_curve = nullptr;
@@ -76,6 +76,11 @@ struct vpmc_ctx {
     unsigned long long* d_sq_count = nullptr;
     vpmc::TuneResult tune_dose, tune_im;
     long long launches = 0;                    // kernels launched since creation
+    // per transport batch: events before the beam-line kernels, between them
+    // and the patient kernel, and after it (the first kTimedBatches batches)
+    static constexpr int kTimedBatches = 64;
+    cudaEvent_t kev[3 * kTimedBatches]{};
+    int kev_batches = 0;                       // batches the last enqueued transport recorded
     // an asynchronous dose call left its status word unread (1; 2: with the
     // surrogate's status word too): the next call reads it first
     int status_pending = 0;

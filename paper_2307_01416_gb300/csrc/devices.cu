@@ -1,4 +1,4 @@
-// Persistent proton transport kernels for sm_103a.
+// Persistent transport kernels of the beam-line devices for sm_103a.
 //
 // One history per thread (paper Sec. 2.A: every history follows one identical
 // model, so no secondary particles are spawned).  Warps are persistent: a warp
@@ -10,63 +10,15 @@
 // optional range shifter; k_aperture takes it through the brass aperture
 // (Sec. 2.B: at every step inside the aperture slab a crossing-number test
 // decides opening -> straight flight, or brass -> condensed-history step with
-// brass physics); k_patient transports it through the voxelised patient and
-// scores every step's deposit into a 64-bit fixed-point accumulator
-// (optionally aggregated over the lanes of a warp that hit the same voxel,
-// then one atomic per voxel).
-//
-// Physics of one condensed-history step (same definition as the CPU oracle):
-//   step = min(1 mm, 1 % energy-loss length, geometry limit, nuclear point);
-//   mean loss from the residual range carried with the particle,
-//   E' = E(R - s * kappa); Bohr straggling; Highland scattering with the PDG
-//   correlated (angle, offset) pair in two planes; nuclear removal at
-//   0.0012 / mm x density with the removed energy deposited locally.
-// Random numbers: Philox4x32-10, key = (seed lo, spot ^ seed hi), counter =
-// (history, step, slot, 0): slot 0 source (23-bit uniforms), slot 1 one
-// condensed-history step (six 21-bit uniforms for scattering and
-// straggling), slot 3 nuclear free path; the surrogate uses slots 4-6.
-#include "device_common.cuh"
-#include "vpmc_internal.cuh"
+// brass physics); k_patient (patient.cu) transports it through the voxelised
+// patient.
+#include "transport_common.cuh"
 
 namespace vpmc {
 namespace {
 
 using namespace dev;
-
-constexpr float kMp = 938.272f;
-
-// Box-Muller with hardware approximations (per-step physics).  u1 <= 1 - 2^-22,
-// so -2 ln u1 > 0; the clamp only guards the approximate logarithm.
-__device__ __forceinline__ float2 box_muller_fast(float u1, float u2)
-{
-    const float l = fmaxf(-2.0f * __logf(u1), 0.0f);
-    const float r = l * rsqrtf(fmaxf(l, 1e-30f));
-    float s, c;
-    __sincosf(6.28318530717958647f * u2, &s, &c);
-    return make_float2(r * c, r * s);
-}
-
-__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
-
-__device__ __forceinline__ float range_of(const float* __restrict__ R, float E)
-{
-    if (E <= 0.0f) return 0.0f;
-    const float x = E * 10.0f;
-    const int i = min((int)x, kNE - 2);
-    const float f = x - (float)i;
-    const float r0 = R[i];
-    return fmaf(f, R[i + 1] - r0, r0);
-}
-
-__device__ __forceinline__ float energy_of(const float* __restrict__ Et, float inv_dR, float R)
-{
-    if (R <= 0.0f) return kEcut;
-    const float x = R * inv_dR;
-    const int j = min((int)x, kNR - 2);
-    const float f = x - (float)j;
-    const float e0 = Et[j];
-    return fmaf(f, Et[j + 1] - e0, e0);
-}
+using namespace tr;
 
 // Lower bound of the distance from (a, b) to the polygon boundary from the
 // raster (0 outside it or in a cell an edge passes through).
@@ -234,256 +186,6 @@ __device__ __forceinline__ float4 coop_nearest_edge(bool need, float x, float y,
     return result;
 }
 
-// Duff et al. 2017, "Building an orthonormal basis, revisited".
-__device__ __forceinline__ void orthonormal_basis(const float n[3], float b1[3], float b2[3])
-{
-    const float sign = copysignf(1.0f, n[2]);
-    const float a = __fdividef(-1.0f, sign + n[2]);
-    const float b = n[0] * n[1] * a;
-    b1[0] = 1.0f + sign * n[0] * n[0] * a;
-    b1[1] = sign * b;
-    b1[2] = -sign * n[0];
-    b2[0] = b;
-    b2[1] = sign + n[1] * n[1] * a;
-    b2[2] = -n[1];
-}
-
-// n-th (0-based) set bit of m; m must have more than n bits set.
-__device__ __forceinline__ int nth_set_bit(unsigned m, int n)
-{
-    int pos = 0;
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-        const unsigned low = (unsigned)((1ull << (pos + w)) - 1ull);
-        if (__popc(m & low) <= n) pos += w;
-    }
-    return pos;
-}
-
-// Every lane of the warp calls this.  key < 0: no deposit.  Lanes with the
-// same key are summed (tree over the peer group) and the lowest peer issues
-// one 64-bit atomic.
-__device__ __forceinline__ void deposit_aggregated(unsigned long long* __restrict__ dst, long long key,
-                                                   unsigned long long q)
-{
-    const unsigned peers = __match_any_sync(kFull, key);
-    const int lane = threadIdx.x & 31;
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    const int cnt = __popc(peers);
-    const unsigned maxcnt = __reduce_max_sync(kFull, (unsigned)cnt);
-    unsigned long long sum = q;
-    for (int k = 1; k < (int)maxcnt; k <<= 1) {
-        const int src_rank = rank + k;
-        const int src = src_rank < cnt ? nth_set_bit(peers, src_rank) : lane;
-        const unsigned long long other = __shfl_sync(kFull, sum, src);
-        if ((rank & (2 * k - 1)) == 0 && src_rank < cnt) sum += other;
-    }
-    if (rank == 0 && key >= 0 && sum != 0ull) atomicAdd(dst + key, sum);
-}
-
-struct Medium {
-    const float* Rt;   // residual range table
-    const float* Et;   // energy table on the uniform range grid
-    float inv_dR, kappa, rho, za, inv_x0;
-};
-
-struct StepResult {
-    float s, dE;
-    float disp[3];
-    int lim;        // 0 none, 1 geometry, 2 nuclear
-    int killed;     // 1 stopped, 2 nuclear
-};
-
-// State of the history a lane carries.
-struct Lane {
-    float p[3], d[3];
-    float E, R, nlam;
-    uint32_t step;  // condensed-history steps so far (RNG counter)
-    uint32_t hist;  // history index within its spot
-    int stage;      // devices: -1 just born, 0 range shifter, 1 aperture
-    int forced;     // aperture: 1 the next step is in brass (after a wall hit), -1 on the entrance plane
-    int ic[3], is[3];
-    int item;
-    int iters;
-    long long g;
-    unsigned long long qdep;
-};
-
-// State of the history a patient lane carries.  Its global index and work
-// item stay in shared memory: they are read only when the history ends.
-struct PatientLane {
-    float p[3], d[3];
-    float E, R, nlam;
-    uint32_t step;              // condensed-history steps so far (RNG counter)
-    uint32_t hist;              // history index within its spot
-    int iters;
-    int ic[3], is[3];
-    unsigned long long hdep;    // fixed-point energy the history deposited in the patient
-};
-
-template <class LaneT>
-__device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L, const TransportParams& P, uint2 key,
-                                        StepResult& o)
-{
-    const float E = L.E;
-    const float R0 = L.R;
-    const float inv_kappa = __fdividef(1.0f, m.kappa);
-    float s1 = (R0 - range_of(m.Rt, 0.99f * E)) * inv_kappa;
-    if (!(s1 > 0.0f)) s1 = R0 * inv_kappa;
-    const float mu = P.nuclear ? 0.0012f * m.rho : 0.0f;
-    float s = 1.0f;
-    int lim = 0;
-    if (s1 < s) s = s1;
-    if (s_geom < s) { s = s_geom; lim = 1; }
-    if (mu > 0.0f) {
-        const float sn = __fdividef(L.nlam, mu);
-        if (sn < s) { s = sn; lim = 2; }
-    }
-    L.step += 1;
-    if (lim == 2) L.nlam = 0.0f; else L.nlam -= mu * s;
-
-    // random numbers of this step: one block, counter (history, step, 1, 0),
-    // six 21-bit uniforms -- the top 21 bits of each word (scattering) and the
-    // low bits of words 0|1 and 2|3 (straggling)
-    uint4 r = make_uint4(L.hist, L.step, 1u, 0u);
-    if (P.mcs || P.straggling) r = philox(r, key);
-
-    const float R1 = R0 - s * m.kappa;
-    const float Emean = R1 > 0.0f ? energy_of(m.Et, m.inv_dR, R1) : kEcut;
-    float dE = E - Emean;
-    const float pc2 = E * (E + 2.0f * kMp);               // (pc)^2
-    const float inv_etot = __fdividef(1.0f, E + kMp);
-    if (P.straggling) {
-        const float beta2 = pc2 * inv_etot * inv_etot;
-        const float2 z = box_muller_fast(u21(((r.x & 0x7FFu) << 10) | (r.y & 0x3FFu)),
-                                         u21(((r.z & 0x7FFu) << 10) | (r.w & 0x3FFu)));
-        const float var = 0.01569f * m.rho * m.za * s * __fdividef(1.0f - 0.5f * beta2, 1.0f - beta2);
-        dE += fast_sqrt(var) * z.x;
-    }
-    dE = fminf(fmaxf(dE, 0.0f), E);
-    const float Enew = E - dE;
-    float Rnew = R1;
-    if (P.straggling) {
-        Rnew = R1 + (range_of(m.Rt, Enew) - range_of(m.Rt, Emean));
-        if (!(Rnew > 0.0f)) Rnew = range_of(m.Rt, Enew);
-    }
-    L.R = Rnew;
-
-    o.s = s;
-    o.lim = lim;
-    o.disp[0] = o.disp[1] = o.disp[2] = 0.0f;
-    o.killed = lim == 2 ? 2 : (Enew <= kEcut ? 1 : 0);
-    if (o.killed) { o.dE = E; L.E = 0.0f; }
-    else { o.dE = dE; L.E = Enew; }
-
-#pragma unroll
-    for (int k = 0; k < 3; ++k) L.p[k] = fmaf(s, L.d[k], L.p[k]);
-
-    if (P.mcs && !o.killed) {
-        const float x = s * m.rho * m.inv_x0;
-        float th0 = 0.0f;
-        if (x >= 1e-6f) th0 = __fdividef(13.6f, pc2 * inv_etot) * fast_sqrt(x) * (1.0f + 0.038f * __logf(x));
-        const float2 za = box_muller_fast(u21(r.x >> 11), u21(r.y >> 11));
-        const float2 zb = box_muller_fast(u21(r.z >> 11), u21(r.w >> 11));
-        const float th1 = za.y * th0, th2 = zb.y * th0;
-        const float dx1 = s * th0 * fmaf(za.x, 0.28867513459481287f, 0.5f * za.y);
-        const float dx2 = s * th0 * fmaf(zb.x, 0.28867513459481287f, 0.5f * zb.y);
-        float e1[3], e2[3];
-        orthonormal_basis(L.d, e1, e2);
-        const float th = fast_sqrt(th1 * th1 + th2 * th2);
-        float sn, c;
-        __sincosf(th, &sn, &c);
-        const float sc = th > 0.0f ? __fdividef(sn, th) : 1.0f;
-        float nd[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            o.disp[k] = dx1 * e1[k] + dx2 * e2[k];
-            nd[k] = c * L.d[k] + sc * (th1 * e1[k] + th2 * e2[k]);
-        }
-        const float inv = rsqrtf(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) L.d[k] = nd[k] * inv;
-    }
-}
-
-// Fixed-point value round-half-even(e * scale) of an energy.  Below 2^32 (any
-// energy up to 250 MeV at scales up to 2^24) the 32-bit conversion gives the
-// same integer as the 64-bit one, which would occupy the FP64 pipe.
-__device__ __forceinline__ unsigned long long to_fixed(float e, float scale, bool fits32)
-{
-    return fits32 ? (unsigned long long)__float2uint_rn(e * scale) : __float2ull_rn(e * scale);
-}
-
-// Largest i with items[i].hist_off <= g, searched by the whole warp: each
-// round the 32 lanes probe 32 evenly spaced entries (g is warp-uniform).
-__device__ __forceinline__ int find_item_warp(const DevItem* __restrict__ items, int n, long long g, int lane)
-{
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int step = (hi - lo + 31) >> 5;
-        const int idx = lo + lane * step;
-        const bool le = idx < hi && __ldg(&items[idx].hist_off) <= g;
-        const unsigned m = __ballot_sync(kFull, le);
-        const int last = 31 - __clz(m);
-        lo = lo + last * step;
-        hi = min(lo + step, hi);
-    }
-    return lo;
-}
-
-// Warp-uniform pool of work indices [pool_next, pool_end) taken from a global
-// counter in chunks.  Returns false once the work (or the launch) has ended.
-struct WorkPool {
-    long long next = 0, end = 0;
-    __device__ __forceinline__ bool refill(const TransportParams& P, long long begin, long long total, int lane)
-    {
-        unsigned long long base = 0;
-        int abort = 0;
-        if (lane == 0) {
-            base = atomicAdd(P.counter, (unsigned long long)P.chunk);
-            abort = *reinterpret_cast<volatile int*>(P.status);   // a latched error ends the launch early
-        }
-        base = __shfl_sync(kFull, base, 0);
-        abort = __shfl_sync(kFull, abort, 0);
-        const long long b = begin + (long long)base;
-        if (abort || b >= total) return false;
-        next = b;
-        end = min(b + P.chunk, total);
-        return true;
-    }
-};
-
-__device__ __forceinline__ void put_record(const TransportParams& P, long long g, int fate, uint32_t steps,
-                                           unsigned long long q, float e, const float pos[3])
-{
-    HistRecord r;
-    r.q_dep = (long long)q;
-    r.fate = fate;
-    r.steps = (int)steps;
-    r.e_dep = (float)((double)q / (double)P.fscale);
-    r.e_end = (fate == kLeak || fate == kErr) ? e : 0.0f;
-    r.pos[0] = pos[0]; r.pos[1] = pos[1]; r.pos[2] = pos[2];
-    r.pad = 0.0f;
-    P.records[g] = r;
-}
-
-__device__ __forceinline__ void write_record(const TransportParams& P, const Lane& L, int fate, const float pos[3],
-                                             unsigned long long acc_dep)
-{
-    put_record(P, L.g, fate, L.step, acc_dep - L.qdep, L.E, pos);
-}
-
-__device__ __forceinline__ void warp_add_stats(const TransportParams& P, unsigned long long (&v)[kNStats], int lane)
-{
-#pragma unroll
-    for (int k = 0; k < kNStats; ++k) {
-        unsigned long long x = v[k];
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-        if (lane == 0 && x) atomicAdd(P.stats + k, x);
-    }
-}
-
 }  // namespace
 
 // ============================================================================
@@ -498,8 +200,8 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     {
-        float* R = reinterpret_cast<float*>(smem + SourceSmem::R);
-        float* Et = reinterpret_cast<float*>(smem + SourceSmem::Einv);
+        float2* R = reinterpret_cast<float2*>(smem + SourceSmem::R);
+        float2* Et = reinterpret_cast<float2*>(smem + SourceSmem::Einv);
         for (int i = threadIdx.x; i < kNEPad; i += blockDim.x) R[i] = P.tables->R[kPMMA][i];
         for (int i = threadIdx.x; i < kNR; i += blockDim.x) Et[i] = P.tables->Einv[kPMMA][i];
         MatConst* mt = reinterpret_cast<MatConst*>(smem + SourceSmem::Mat);
@@ -511,8 +213,8 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
     const MatConst* mat = reinterpret_cast<const MatConst*>(smem + SourceSmem::Mat);
     const DevBeam* beams = reinterpret_cast<const DevBeam*>(smem + SourceSmem::Beams);
     Medium pmma;
-    pmma.Rt = reinterpret_cast<const float*>(smem + SourceSmem::R);
-    pmma.Et = reinterpret_cast<const float*>(smem + SourceSmem::Einv);
+    pmma.Rt = reinterpret_cast<const float2*>(smem + SourceSmem::R);
+    pmma.Et = reinterpret_cast<const float2*>(smem + SourceSmem::Einv);
     pmma.inv_dR = mat[kPMMA].inv_dR; pmma.kappa = mat[kPMMA].rho;
     pmma.rho = mat[kPMMA].rho; pmma.za = mat[kPMMA].za; pmma.inv_x0 = mat[kPMMA].inv_x0;
 
@@ -686,8 +388,8 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
     extern __shared__ __align__(16) unsigned char smem[];
     {
         // brass rows of the tables, material constants, beams, scenarios, polygons
-        float* R = reinterpret_cast<float*>(smem + ApertureSmem::R);
-        float* Et = reinterpret_cast<float*>(smem + ApertureSmem::Einv);
+        float2* R = reinterpret_cast<float2*>(smem + ApertureSmem::R);
+        float2* Et = reinterpret_cast<float2*>(smem + ApertureSmem::Einv);
         for (int i = threadIdx.x; i < kNEPad; i += blockDim.x) R[i] = P.tables->R[kBrass][i];
         for (int i = threadIdx.x; i < kNR; i += blockDim.x) Et[i] = P.tables->Einv[kBrass][i];
         MatConst* mt = reinterpret_cast<MatConst*>(smem + ApertureSmem::Mat);
@@ -705,8 +407,8 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
     const DevScen* scens = reinterpret_cast<const DevScen*>(smem + ApertureSmem::Scens);
     const float2* poly = reinterpret_cast<const float2*>(smem + ApertureSmem::Poly);
     Medium brass;
-    brass.Rt = reinterpret_cast<const float*>(smem + ApertureSmem::R);
-    brass.Et = reinterpret_cast<const float*>(smem + ApertureSmem::Einv);
+    brass.Rt = reinterpret_cast<const float2*>(smem + ApertureSmem::R);
+    brass.Et = reinterpret_cast<const float2*>(smem + ApertureSmem::Einv);
     brass.inv_dR = mat[kBrass].inv_dR; brass.kappa = mat[kBrass].rho;
     brass.rho = mat[kBrass].rho; brass.za = mat[kBrass].za; brass.inv_x0 = mat[kBrass].inv_x0;
     // histories handed over by the source kernel (training tracks: born here)
@@ -925,7 +627,8 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                     absorb = true;                  // cannot reach the opening or the exit face
                 } else if (L.E >= sur::kELo && L.E <= sur::kEHi && fabsf(un) <= sur::kAngMax &&
                            fabsf(ut) <= sur::kAngMax && ne.w >= sur::kKappaLo && ne.w <= sur::kKappaHi &&
-                           fabsf(T - sur::kThickness) < 1e-3f && dist > 0.0f) {
+                           fabsf(T - sur::kThickness) < 1e-3f && dist > 0.0f &&
+                           fabsf(feat[5]) >= sur::kNearThreshold) {
                     sur_emit = true;                // in the training domain: one network draw
                 }
             }
@@ -1108,242 +811,8 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
     warp_add_stats(P, v, lane);
 }
 
-// ============================================================================
-// Voxelised patient.
-// ============================================================================
-__global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const TransportParams P)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    long long* s_g = reinterpret_cast<long long*>(smem + PatientSmem::G);
-    long long* s_pool = reinterpret_cast<long long*>(smem + PatientSmem::Pool) + 2 * warp;
-    int* s_item = reinterpret_cast<int*>(smem + PatientSmem::Item);
-    {
-        float* R = reinterpret_cast<float*>(smem + PatientSmem::R);
-        float* Et = reinterpret_cast<float*>(smem + PatientSmem::Einv);
-        for (int i = threadIdx.x; i < kNEPad; i += blockDim.x) R[i] = P.tables->R[kWater][i];
-        for (int i = threadIdx.x; i < kNR; i += blockDim.x) Et[i] = P.tables->Einv[kWater][i];
-        float2* hu = reinterpret_cast<float2*>(smem + PatientSmem::HU);
-        for (int i = threadIdx.x; i < kNHU; i += blockDim.x) hu[i] = P.tables->hu[i];
-        DevScen* sc = reinterpret_cast<DevScen*>(smem + PatientSmem::Scens);
-        for (int i = threadIdx.x; i < P.n_scen; i += blockDim.x) sc[i] = P.scens[i];
-        if (lane == 0) { s_pool[0] = 0; s_pool[1] = 0; }
-        s_g[threadIdx.x] = 0;
-        s_item[threadIdx.x] = 0;
-    }
-    __syncthreads();
-    Medium water;
-    water.Rt = reinterpret_cast<const float*>(smem + PatientSmem::R);
-    water.Et = reinterpret_cast<const float*>(smem + PatientSmem::Einv);
-    const float2* hu_lut = reinterpret_cast<const float2*>(smem + PatientSmem::HU);
-    const DevScen* scens = reinterpret_cast<const DevScen*>(smem + PatientSmem::Scens);
-    water.inv_dR = P.water.inv_dR;
-    water.za = P.water.za;
-    water.inv_x0 = P.water.inv_x0;
-
-    bool alive = false, done = false;
-    PatientLane L;
-    L.hist = 0; L.hdep = 0ull; L.iters = 0; L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; L.ic[k] = 0; L.is[k] = 0; }
-    uint32_t key1 = 0u;
-    float spr_scale = 1.0f;
-    DevBox bx;
-    bx.base = 0; bx.lo[0] = bx.lo[1] = bx.lo[2] = 0; bx.n[0] = bx.n[1] = bx.n[2] = 0;
-    float wsc = 0.0f;
-
-    for (;;) {
-        // ---- histories handed over by the devices kernel ----
-        unsigned need = __ballot_sync(kFull, !alive && !done);
-        if (need) {
-            // the warp's pool lives in shared memory between refills, so that
-            // it holds no registers across the step
-            WorkPool pool;
-            pool.next = s_pool[0];
-            pool.end = s_pool[1];
-            const unsigned lt_mask = (1u << lane) - 1u;
-            while (need) {
-                if (pool.next >= pool.end) {
-                    const long long total = min((long long)*P.phase_count, P.phase_cap);
-                    if (!pool.refill(P, 0, total, lane)) {
-                        if (!alive) done = true;
-                        break;
-                    }
-                }
-                const int take = (int)min((long long)__popc(need), pool.end - pool.next);
-                const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
-                if (mine) {
-                    const PhaseRec r = P.phase[pool.next + __popc(need & lt_mask)];
-                    if (r.item >= 0) {        // item -1: a slot the aperture surrogate left empty
-                        const DevItem I = P.items[r.item];
-                        s_item[threadIdx.x] = r.item;
-                        s_g[threadIdx.x] = r.g;
-                        L.hist = (uint32_t)(r.g - I.hist_off);
-                        L.step = r.step;
-                        L.iters = 0;
-                        L.E = r.E;
-                        L.nlam = r.nlam;
-                        L.hdep = 0ull;
-                        key1 = P.key1_hi ^ (uint32_t)I.spot;
-                        spr_scale = scens[I.scen].spr_scale;
-                        bx = P.boxes[I.box];
-                        wsc = I.wscale;
-                        // ray / grid box entry
-                        float tmin = -__int_as_float(0x7f800000), tmax = __int_as_float(0x7f800000);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float lo = P.ctg.lo[k], hi = P.ctg.lo[k] + P.ctg.n[k] * P.ctg.d[k];
-                            if (r.d[k] != 0.0f) {
-                                float t1 = (lo - r.p[k]) / r.d[k], t2 = (hi - r.p[k]) / r.d[k];
-                                if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
-                                tmin = fmaxf(tmin, t1);
-                                tmax = fminf(tmax, t2);
-                            } else if (r.p[k] < lo || r.p[k] > hi) {
-                                tmax = -__int_as_float(0x7f800000);
-                            }
-                        }
-                        const float tin = fmaxf(tmin, 0.0f);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) { L.p[k] = r.p[k]; L.d[k] = r.d[k]; }
-                        if (!(tmax > tin)) {
-                            // misses the grid
-                            atomicAdd(P.stats + kStLeak, to_fixed(L.E, P.fscale, P.fx32));
-                            if (P.records && r.g < P.rec_cap) put_record(P, r.g, kLeak, L.step, 0ull, L.E, L.p);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                L.p[k] = fmaf(tin, L.d[k], L.p[k]);
-                                const int a = (int)floorf((L.p[k] - P.ctg.lo[k]) / P.ctg.d[k]);
-                                L.ic[k] = min(max(a, 0), P.ctg.n[k] - 1);
-                                const int b = (int)floorf((L.p[k] - P.sg.lo[k]) / P.sg.d[k]);
-                                L.is[k] = min(max(b, 0), P.sg.n[k] - 1);
-                            }
-                            L.R = range_of(water.Rt, L.E);
-                            alive = true;
-                        }
-                    }
-                }
-                pool.next += take;
-                need = __ballot_sync(kFull, !alive && !done);
-            }
-            __syncwarp();
-            if (lane == 0) { s_pool[0] = pool.next; s_pool[1] = pool.end; }
-            __syncwarp();
-        }
-        if (!__any_sync(kFull, alive)) {
-            if (__all_sync(kFull, done || alive)) break;
-            continue;
-        }
-
-        // ---- one condensed-history step of every live history ----
-        long long dep_key = -1;
-        unsigned long long dep_q = 0ull;
-        if (alive) {
-            int fate = -1;
-            if (++L.iters > P.max_iter) {
-                fate = kErr;
-            } else {
-                const int cidx = L.ic[0] + P.ctg.n[0] * (L.ic[1] + P.ctg.n[1] * L.ic[2]);   // CT < 2^31 voxels
-                const int h = min(max((int)__ldg(P.ct + cidx), kHULo), kHULo + kNHU - 1);
-                const float2 rs = hu_lut[h - kHULo];
-                water.kappa = rs.y * spr_scale;
-                water.rho = rs.x;
-                // distance to the next voxel boundary of either grid
-                float dc[3], ds[3], s_geom = __int_as_float(0x7f800000);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    dc[k] = ds[k] = __int_as_float(0x7f800000);
-                    const float Dk = L.d[k];
-                    if (Dk != 0.0f) {
-                        const float inv = __fdividef(1.0f, Dk);
-                        const int up = Dk > 0.0f ? 1 : 0;
-                        const float bc = P.ctg.lo[k] + (float)(L.ic[k] + up) * P.ctg.d[k];
-                        dc[k] = fmaxf((bc - L.p[k]) * inv, 0.0f);
-                        if (P.same_grid) ds[k] = dc[k];
-                        else {
-                            const float bs = P.sg.lo[k] + (float)(L.is[k] + up) * P.sg.d[k];
-                            ds[k] = fmaxf((bs - L.p[k]) * inv, 0.0f);
-                        }
-                    }
-                    s_geom = fminf(s_geom, fminf(dc[k], ds[k]));
-                }
-                StepResult o;
-                const float d_old[3] = {L.d[0], L.d[1], L.d[2]};
-                const int lx = L.is[0] - bx.lo[0], ly = L.is[1] - bx.lo[1], lz = L.is[2] - bx.lo[2];
-                const int is0 = L.is[0], is1 = L.is[1], is2 = L.is[2];
-                ch_step(water, s_geom, L, P, make_uint2(P.key0, key1), o);
-                const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
-                unsigned long long q = qs;
-                if (!P.unit_weight && wsc != P.fscale) q = to_fixed(o.dE, wsc, false);
-                // score into the scoring voxel where the step started
-                if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] && ly < bx.n[1] && lz < bx.n[2]) {
-                    dep_key = bx.base + (long long)(lx + bx.n[0] * (ly + bx.n[1] * lz));   // box < 2^31 voxels
-                    dep_q = q;
-                } else if (o.dE > 0.0f && P.ovf) {
-                    // rare tail outside the item's box: append a record
-                    const unsigned long long slot = atomicAdd(P.ovf_count, 1ull);
-                    if ((long long)slot < P.ovf_cap) {
-                        OvfRec rr;
-                        rr.voxel = is0 + P.sg.n[0] * (is1 + P.sg.n[1] * is2);
-                        rr.item = s_item[threadIdx.x];
-                        rr.q = q;
-                        P.ovf[slot] = rr;
-                    }
-                }
-                L.hdep += qs;
-                if (o.killed) {
-                    if (o.killed == 2) atomicAdd(P.stats + kStNuc, qs);
-                    fate = o.killed == 2 ? kNuc : kStop;
-                } else {
-                    if (o.lim == 1) {
-                        bool out = false;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const int sg = d_old[k] > 0.0f ? 1 : -1;
-                            if (d_old[k] != 0.0f && dc[k] == o.s) L.ic[k] += sg;
-                            if (d_old[k] != 0.0f && ds[k] == o.s) L.is[k] += sg;
-                            out |= L.ic[k] < 0 || L.ic[k] >= P.ctg.n[k] || L.is[k] < 0 || L.is[k] >= P.sg.n[k];
-                        }
-                        if (out) fate = kLeak;
-                    }
-                    if (fate < 0) {
-                        // lateral displacement, confined to the current voxel of both grids
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float vlo = fmaxf(P.ctg.lo[k] + (float)L.ic[k] * P.ctg.d[k],
-                                                    P.sg.lo[k] + (float)L.is[k] * P.sg.d[k]);
-                            const float vhi = fminf(P.ctg.lo[k] + (float)(L.ic[k] + 1) * P.ctg.d[k],
-                                                    P.sg.lo[k] + (float)(L.is[k] + 1) * P.sg.d[k]);
-                            L.p[k] = fminf(fmaxf(L.p[k] + o.disp[k], vlo), vhi);
-                        }
-                    }
-                }
-            }
-            if (fate >= 0) {
-                // the history's totals go straight to the launch's counters
-                // (one history ends every few hundred steps of a lane)
-                if (L.hdep) atomicAdd(P.stats + kStDep, L.hdep);
-                atomicAdd(P.stats + kStSteps, (unsigned long long)min(L.iters, P.max_iter));
-                if (fate == kLeak || fate == kErr) atomicAdd(P.stats + kStLeak, to_fixed(L.E, P.fscale, P.fx32));
-                if (fate == kErr) { atomicAdd(P.stats + kStErr, 1ull); atomicOr(P.status, 1); }
-                if (P.records) {
-                    const long long g = s_g[threadIdx.x];
-                    if (g < P.rec_cap) put_record(P, g, fate, L.step, L.hdep, L.E, L.p);
-                }
-                alive = false;
-            }
-        }
-        // ---- scoring (all lanes together) ----
-        if (P.aggregate) deposit_aggregated(P.scratch, dep_key, dep_q);
-        else if (dep_key >= 0 && dep_q) atomicAdd(P.scratch + dep_key, dep_q);
-    }
-}
-
 size_t devices_smem_bytes() { return SourceSmem::Bytes > ApertureSmem::Bytes ? SourceSmem::Bytes : ApertureSmem::Bytes; }
-size_t patient_smem_bytes() { return PatientSmem::Bytes; }
 int devices_max_block() { return 640; }
-int patient_max_block() { return kPatientMaxBlock; }
 
 template <int kMode>
 static cudaError_t launch_aperture_mode(const TransportParams& p, int grid, int block, cudaStream_t s)
@@ -1382,19 +851,6 @@ cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaSt
     case 3: return launch_aperture_mode<3>(p, grid, block, s);
     default: return launch_aperture_mode<0>(p, grid, block, s);
     }
-}
-
-cudaError_t launch_patient(const TransportParams& p, int grid, int block, cudaStream_t s)
-{
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_patient, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)PatientSmem::Bytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    k_patient<<<grid, block, PatientSmem::Bytes, s>>>(p);
-    return cudaGetLastError();
 }
 
 }  // namespace vpmc

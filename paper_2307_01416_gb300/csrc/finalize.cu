@@ -127,14 +127,26 @@ __global__ void k_csr_rows(const CsrBuildParams p, int fill)
         const DevBox bb = p.boxes[p.beam_box[b]];
         const long long l = box_local(bb, x, y, z);
         if (l < 0) continue;
-        for (int t = 0; t < cnt; ++t) {
-            const int it = p.beam_first[b] + t;
-            while (j < nrec && rec[j].item - p.item_base < it) {
-                emit(rec[j].item - p.item_base, rec[j].q);
-                ++j;
+        // the beam's columns are consecutive boxes of one shape: spot t of the
+        // beam at first + t * size; loads go out eight at a time so that
+        // several are in flight (the scratch is streamed once per pass)
+        const int first = p.beam_first[b];
+        const long long size = (long long)bb.n[0] * bb.n[1] * bb.n[2];
+        const unsigned long long* col0 = p.scratch + p.boxes[p.items[first].box].base + l;
+        for (int t0 = 0; t0 < cnt; t0 += 8) {
+            unsigned long long q[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) q[u] = t0 + u < cnt ? __ldcs(col0 + (long long)(t0 + u) * size) : 0ull;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (t0 + u >= cnt) break;
+                const int it = first + t0 + u;
+                while (j < nrec && rec[j].item - p.item_base < it) {
+                    emit(rec[j].item - p.item_base, rec[j].q);
+                    ++j;
+                }
+                if (q[u] != 0ull) emit(it, q[u]);
             }
-            const unsigned long long q = p.scratch[p.boxes[p.items[it].box].base + l];
-            if (q != 0ull) emit(it, q);
         }
     }
     for (; j < nrec; ++j) emit(rec[j].item - p.item_base, rec[j].q);

@@ -221,10 +221,10 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     TransportParams p{};
     p.tables = c->d_tables;
     p.water = c->water_mat;
-    p.ct = c->d_ct;
+    p.ct_lut = reinterpret_cast<const uint16_t*>(c->d_ct);
     p.ctg = c->ctg;
     p.sg = c->sg;
-    p.same_grid = c->same_grid ? 1 : 0;
+    for (int k = 0; k < 3; ++k) p.nest_shift[k] = c->nest_shift[k];
     p.beams = c->d_beams;
     p.n_beams = kMaxBeams;
     p.scens = dscen;

@@ -164,9 +164,18 @@ void build_tables(const double* curve15, TablesImage* img)
         std::vector<double> range, energy;
         double d_range = 0.0;
         build_material(kMaterials[mat], range, energy, d_range);
-        for (int k = 0; k < kNE; ++k) img->R[mat][k] = (float)range[k];
-        for (int k = kNE; k < kNEPad; ++k) img->R[mat][k] = (float)range[kNE - 1];
-        for (int j = 0; j < kNR; ++j) img->Einv[mat][j] = (float)energy[j];
+        // FP32 values and the FP32 differences to the next entry (zero after
+        // the last), as the kernels interpolate them
+        for (int k = 0; k < kNEPad; ++k) {
+            const float v = (float)range[std::min(k, kNE - 1)];
+            const float next = (float)range[std::min(k + 1, kNE - 1)];
+            img->R[mat][k] = make_float2(v, next - v);
+        }
+        for (int j = 0; j < kNR; ++j) {
+            const float v = (float)energy[j];
+            const float next = (float)energy[std::min(j + 1, kNR - 1)];
+            img->Einv[mat][j] = make_float2(v, next - v);
+        }
         img->mat[mat].za = (float)kMaterials[mat].z_over_a;
         img->mat[mat].rho = (float)kMaterials[mat].density;
         img->mat[mat].inv_x0 = (float)(1.0 / (kMaterials[mat].radiation_length_gcm2 * 10.0));

@@ -34,8 +34,8 @@ struct MatConst {
 };
 
 struct TablesImage {                 // global-memory image, copied to shared memory
-    float R[kNMat][kNEPad];          // residual range R(E_k), mm * g/cc
-    float Einv[kNMat][kNR];          // E at R_j = j * dR
+    float2 R[kNMat][kNEPad];         // (R(E_k), R(E_{k+1}) - R(E_k)): residual range, mm * g/cc
+    float2 Einv[kNMat][kNR];         // (E(R_j), E(R_{j+1}) - E(R_j)) at R_j = j * dR
     float2 hu[kNHU];                 // (density, SPR) per HU
     MatConst mat[kNMat];
 };
@@ -129,6 +129,11 @@ constexpr float kDirScale = 0.05f;
 constexpr float kSMin = -8.0f, kSMax = 4.0f;
 constexpr float kThickness = 30.0f;  // block thickness of the training geometries, mm
 constexpr float kKappaLo = -1e-3f, kKappaHi = 0.26f;
+// Near the stopping threshold (brass CSDA range within 6 % of the thickness)
+// a proton leaves the block with a few MeV or not at all: the exit energy
+// distribution has a sharp edge that the mixture does not follow.  Those
+// entries take the plain path.
+constexpr float kNearThreshold = 0.06f;
 }  // namespace sur
 
 // One proton handed from the beam-line kernel to the surrogate: its state on
@@ -155,9 +160,9 @@ struct HistRecord {                  // mirrors vpmc_history_record
 
 struct TransportParams {
     const TablesImage* tables;
-    const int16_t* ct;
+    const uint16_t* ct_lut;          // per CT voxel: index into the (density, SPR) table
     Grid3 ctg, sg;
-    int same_grid;
+    int nest_shift[3];               // per axis: scoring spacing = CT spacing << shift, same origin (-1: not nested)
     const DevBeam* beams;
     int n_beams;
     const DevScen* scens;
@@ -214,15 +219,15 @@ struct TransportParams {
 // Shared-memory layouts of the two transport kernels.
 struct SourceSmem {                  // source and range shifter
     static constexpr size_t R = 0;                                            // PMMA
-    static constexpr size_t Einv = R + sizeof(float) * kNEPad;
-    static constexpr size_t Mat = Einv + sizeof(float) * kNR;
+    static constexpr size_t Einv = R + sizeof(float2) * kNEPad;
+    static constexpr size_t Mat = Einv + sizeof(float2) * kNR;
     static constexpr size_t Beams = Mat + sizeof(MatConst) * kNMat;
     static constexpr size_t Bytes = Beams + sizeof(DevBeam) * kMaxBeams;
 };
 struct ApertureSmem {                // aperture block
     static constexpr size_t R = 0;                                            // brass
-    static constexpr size_t Einv = R + sizeof(float) * kNEPad;
-    static constexpr size_t Mat = Einv + sizeof(float) * kNR;
+    static constexpr size_t Einv = R + sizeof(float2) * kNEPad;
+    static constexpr size_t Mat = Einv + sizeof(float2) * kNR;
     static constexpr size_t Beams = Mat + sizeof(MatConst) * kNMat;
     static constexpr size_t Scens = Beams + sizeof(DevBeam) * kMaxBeams;
     static constexpr size_t Poly = Scens + sizeof(DevScen) * kMaxScen;
@@ -231,8 +236,8 @@ struct ApertureSmem {                // aperture block
 constexpr int kPatientMaxBlock = 896;
 struct PatientSmem {                 // voxelised patient
     static constexpr size_t R = 0;                                            // water
-    static constexpr size_t Einv = R + sizeof(float) * kNEPad;
-    static constexpr size_t HU = Einv + sizeof(float) * kNR;
+    static constexpr size_t Einv = R + sizeof(float2) * kNEPad;
+    static constexpr size_t HU = Einv + sizeof(float2) * kNR;
     static constexpr size_t Scens = HU + sizeof(float2) * kNHU;
     // per thread: global index and work item of the history it carries (read
     // only when a history ends); per warp: the work pool [next, end)
@@ -256,6 +261,11 @@ static_assert(kPatientMaxBlock % 32 == 0, "whole warps");
 // All launches are persistent grids of one block per SM.
 cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaStream_t s);
 cudaError_t launch_patient(const TransportParams& p, int grid, int block, cudaStream_t s);
+// Which compiled nesting of the patient kernel serves these grids (bit k: axis k nested).
+int patient_nest_variant(const int nest_shift[3]);
+// Converts a device CT of hounsfield units, in place, to indices into the
+// kernels' (density, SPR) table (HU clamped to [-1024, 3071]).
+cudaError_t launch_ct_lut_index(int16_t* ct, long long n, cudaStream_t s);
 size_t devices_smem_bytes();
 size_t patient_smem_bytes();
 int patient_max_block();

@@ -75,7 +75,8 @@ class vpmc_stats(C.Structure):
     _fields_ = [("histories", C.c_int64), ("steps", C.c_int64), ("errors", C.c_int64), ("e_in", C.c_double),
                 ("e_dep", C.c_double), ("e_leak", C.c_double), ("e_rs", C.c_double), ("e_aperture", C.c_double),
                 ("e_nuc", C.c_double), ("ms", C.c_float), ("launches", C.c_int64),
-                ("ovf_records", C.c_int64), ("steps_rs", C.c_int64), ("steps_aperture", C.c_int64)]
+                ("ovf_records", C.c_int64), ("steps_rs", C.c_int64), ("steps_aperture", C.c_int64),
+                ("ms_devices", C.c_float), ("ms_patient", C.c_float)]
 
 
 class vpmc_csr(C.Structure):
@@ -91,7 +92,7 @@ EXPORTED = ["vpmc_default_opts", "vpmc_create_geometry", "vpmc_set_aperture", "v
             "vpmc_run_spots_noalloc", "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_destroy", "vpmc_last_error",
             "vpmc_surrogate_init", "vpmc_surrogate_set_weights", "vpmc_surrogate_get_weights",
             "vpmc_surrogate_tracks", "vpmc_surrogate_forward", "vpmc_surrogate_gradient", "vpmc_surrogate_train",
-            "vpmc_robust_optimize", "vpmc_target_indices", "vpmc_weights_dose"]
+            "vpmc_robust_optimize", "vpmc_target_indices", "vpmc_weights_dose", "vpmc_measure_l2_atomics"]
 
 SUR_NPARAMS = 23213            # VPMC_SUR_NPARAMS
 SUR_IN, SUR_OUT, SUR_Y = 6, 45, 5
@@ -138,6 +139,9 @@ def lib():
                                        C.POINTER(C.c_float), C.POINTER(C.c_float), vp]
     L.vpmc_target_indices.argtypes = [C.POINTER(vpmc_csr), C.c_int, vp, C.c_float, vp, C.POINTER(C.c_double), vp]
     L.vpmc_weights_dose.argtypes = [C.POINTER(vpmc_csr), vp, vp, vp]
+    L.vpmc_measure_l2_atomics.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int64), vp]
+    L.vpmc_measure_l2_atomics.restype = C.c_int
     for f in ("vpmc_robust_optimize", "vpmc_target_indices", "vpmc_weights_dose"):
         getattr(L, f).restype = C.c_int
     for f in ("vpmc_create_geometry", "vpmc_set_aperture", "vpmc_run_spots", "vpmc_run_spots_noalloc",
@@ -447,6 +451,19 @@ def target_indices(mats, voxel_class, prescription: float, x, stream=None) -> np
                                      C.c_void_p(x.data_ptr()), out.ctypes.data_as(C.POINTER(C.c_double)),
                                      C.c_void_p(st.cuda_stream)))
     return out.reshape(len(mats), 4)
+
+
+def measure_l2_atomics(n_entries: int = 1 << 22, iters: int = 256, stream=None) -> dict:
+    """The device's rate of 64-bit atomic adds resolved in L2 (adds/s), with
+    the adds of the timed pass and the buffer's sum after both passes."""
+    import torch
+    rate = C.c_double(0.0)
+    adds = C.c_int64(0)
+    total = C.c_int64(0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().vpmc_measure_l2_atomics(int(n_entries), int(iters), C.byref(rate), C.byref(adds), C.byref(total),
+                                         C.c_void_p(st.cuda_stream)))
+    return {"adds_per_s": rate.value, "adds": adds.value, "sum": total.value, "n_entries": int(n_entries)}
 
 
 def weights_dose(mat, x, stream=None):

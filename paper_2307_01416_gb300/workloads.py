@@ -436,8 +436,9 @@ def head_plan(volume_cc: float = 8.4, ct_seed: int = 1234, target_seed: int = 12
 # workload): the head plan's log-uniform counts times this factor, which the
 # batch method (paper_2307_01416_gb300.uncertainty, 10 batches) measured to
 # bring the nominal composite dose to 0.5 % over the tissue voxels at or
-# above half its maximum (Sec. 2.D.3: plans at about 0.5 %).
-IM_SET_HIST_SCALE = 1.0
+# above half its maximum (Sec. 2.D.3: plans at about 0.5 %): 0.5545 % at the
+# unscaled counts, so (0.5545 / 0.5)^2 = 1.23, rounded up.
+IM_SET_HIST_SCALE = 1.25
 
 
 def im_set_plan(dynamic_aperture: bool = False, ap_sad: float = 0.0):

@@ -99,6 +99,10 @@ def test_gradient_matches_oracle(eng):
         a, b = Gg[k].reshape(-1), G[k].reshape(-1)
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         assert rel < 1e-2, (k, rel)
+        # element by element: a wrong tensor-memory column or a dropped tile
+        # moves single entries far beyond the operands' BF16 rounding
+        worst = np.max(np.abs(a - b)) / np.abs(b).max()
+        assert worst < 1e-2, (k, worst, int(np.argmax(np.abs(a - b))))
 
 
 def test_adam_step_matches_oracle(eng):
@@ -215,9 +219,13 @@ def test_network_draws_match_oracle(eng):
     # entries take the plain path (its label, not a draw)
     a = np.abs(r["feat"][:, 2:4])                  # |u| / 0.04; the domain is |u| <= 0.12
     edge = np.any(np.abs(a - 3.0) < 5e-3, axis=1)   # FP32 and FP64 may fall on either side
-    inside = np.all(a < 3.0, axis=1) & ~edge
-    outside = np.any(a > 3.0, axis=1) & ~edge
-    assert inside.mean() > 0.99
+    # brass CSDA range within 6 % of the thickness: the plain path as well
+    x5 = r["feat"][:, 5]
+    near = np.abs(x5) < 0.06
+    near_edge = np.abs(np.abs(x5) - 0.06) < 1e-4
+    inside = np.all(a < 3.0, axis=1) & ~edge & ~near & ~near_edge
+    outside = (np.any(a > 3.0, axis=1) | near) & ~edge & ~near_edge
+    assert inside.mean() > 0.9
     np.testing.assert_array_equal(lg[outside & ~flagged], r["label"][outside & ~flagged])
     # an entry whose 1.2 x CSDA range is below both its edge distance and the
     # thickness is absorbed without a draw (the start radius is r_c + d, and a
