@@ -390,6 +390,9 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
     }
     // the batch events are recorded as event nodes when the transport is
     // captured into a graph (external records), or directly otherwise
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(c->stream, &cap));
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     c->kev_batches = 0;
     for (long long h0 = 0; h0 < total; h0 += c->phase_cap) {
         const int b = c->kev_batches < vpmc_ctx::kTimedBatches ? c->kev_batches++ : -1;
@@ -398,7 +401,7 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
         CUDA_TRY(cudaMemsetAsync(c->d_phase_count, 0, sizeof(unsigned long long), c->stream));
         if (p.surrogate) CUDA_TRY(cudaMemsetAsync(c->d_sq_count, 0, sizeof(unsigned long long), c->stream));
-        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b], c->stream, cudaEventRecordExternal));
+        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b], c->stream, rec_flags));
         CUDA_TRY(launch_devices(p, c->num_sms, t.dev_block, c->stream));
         if (p.surrogate) {
             // brass entries in the surrogate's domain: one network draw each
@@ -406,9 +409,9 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
             c->launches += 1;
         }
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
-        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b + 1], c->stream, cudaEventRecordExternal));
+        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b + 1], c->stream, rec_flags));
         CUDA_TRY(launch_patient(p, c->num_sms, t.block, c->stream));
-        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b + 2], c->stream, cudaEventRecordExternal));
+        if (b >= 0) CUDA_TRY(cudaEventRecordWithFlags(c->kev[3 * b + 2], c->stream, rec_flags));
         c->launches += 3;
     }
     return VPMC_OK;

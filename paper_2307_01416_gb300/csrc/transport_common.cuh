@@ -24,18 +24,26 @@ using namespace dev;
 
 constexpr float kMp = 938.272f;
 
+// Hardware square root (approximate, relative error about 2^-22), 0 for x <= 0.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Box-Muller with hardware approximations (per-step physics).  u1 <= 1 - 2^-22,
 // so -2 ln u1 > 0; the clamp only guards the approximate logarithm.
 __device__ __forceinline__ float2 box_muller_fast(float u1, float u2)
 {
-    const float l = fmaxf(-2.0f * __logf(u1), 0.0f);
-    const float r = l * rsqrtf(fmaxf(l, 1e-30f));
+    const float l = fmaxf(__log2f(u1) * -1.38629436111989061f, 0.0f);      // -2 ln u1
+    const float r = sqrt_approx(l);
     float s, c;
     __sincosf(6.28318530717958647f * u2, &s, &c);
     return make_float2(r * c, r * s);
 }
 
-__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ float fast_sqrt(float x) { return sqrt_approx(fmaxf(x, 0.0f)); }
 
 // Residual range R(E) by linear interpolation on the 0.1 MeV grid.  Each
 // entry holds (R_k, R_{k+1} - R_k) (the last one a zero difference), so a
@@ -176,12 +184,14 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
     const float Emean = R1 > 0.0f ? energy_of(m.Et, m.inv_dR, R1) : kEcut;
     float dE = E - Emean;
     const float pc2 = E * (E + 2.0f * kMp);               // (pc)^2
-    const float inv_etot = __fdividef(1.0f, E + kMp);
+    const float etot = E + kMp;
+    const float inv_etot = __fdividef(1.0f, etot);
     if (P.straggling) {
-        const float beta2 = pc2 * inv_etot * inv_etot;
+        // (1 - beta^2 / 2) / (1 - beta^2) = gamma^2 - (beta gamma)^2 / 2 = (Etot^2 - (pc)^2 / 2) / Mp^2
         const float2 z = box_muller_fast(u21(((r.x & 0x7FFu) << 10) | (r.y & 0x3FFu)),
                                          u21(((r.z & 0x7FFu) << 10) | (r.w & 0x3FFu)));
-        const float var = 0.01569f * m.rho * m.za * s * __fdividef(1.0f - 0.5f * beta2, 1.0f - beta2);
+        const float rel = fmaf(etot, etot, -0.5f * pc2) * (0.01569f / (kMp * kMp));
+        const float var = m.rho * m.za * s * rel;
         dE += fast_sqrt(var) * z.x;
     }
     dE = fminf(fmaxf(dE, 0.0f), E);
@@ -206,7 +216,8 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
     if (P.mcs && !o.killed) {
         const float x = s * m.rho * m.inv_x0;
         float th0 = 0.0f;
-        if (x >= 1e-6f) th0 = __fdividef(13.6f, pc2 * inv_etot) * fast_sqrt(x) * (1.0f + 0.038f * __logf(x));
+        if (x >= 1e-6f)         // 1 + 0.038 ln x = 1 + (0.038 ln 2) log2 x
+            th0 = __fdividef(13.6f, pc2 * inv_etot) * fast_sqrt(x) * fmaf(0.02633959f, __log2f(x), 1.0f);
         const float2 za = box_muller_fast(u21(r.x >> 11), u21(r.y >> 11));
         const float2 zb = box_muller_fast(u21(r.z >> 11), u21(r.w >> 11));
         const float th1 = za.y * th0, th2 = zb.y * th0;
