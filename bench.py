@@ -381,28 +381,16 @@ def main():
                               "note": "one 64-bit scoring add per patient step (plain atomics; warp aggregation "
                                       "would issue fewer) over k_patient's CUDA-event time; peak = "
                                       "vpmc_measure_l2_atomics over a 32 MiB buffer"}}
-        e2e = None
-        if not args.no_e2e:
-            e2e = e2e_leg(pb, spots, scens, opts, args)
-        cpu = None
-        if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_baseline(pb, spots, args.cpu_seconds)
-        opt = None
-        if not args.no_optimizer and world == 1:
-            opt = optimizer_leg(pb, target, last_mats, args)
+        e2e = _leg(lambda: e2e_leg(pb, spots, scens, opts, args), not args.no_e2e)
+        cpu = _leg(lambda: cpu_baseline(pb, spots, args.cpu_seconds), not args.no_cpu_baseline and world == 1)
+        opt = _leg(lambda: optimizer_leg(pb, target, last_mats, args), not args.no_optimizer and world == 1)
         del last_mats
-        edge = None
-        if not args.no_edge_sweep and world == 1:
-            edge = edge_sweep_leg(args, peak_tops)
-        div = None
-        if not args.no_divergent and world == 1:
-            div = divergent_leg(pb, spots, scens, opts, args, value, peak_tops)
-        dyn = None
-        if not args.no_dynamic and world == 1:
-            dyn = dynamic_leg(scens, opts, value, peak_tops)
-        sur = None
-        if not args.no_surrogate and world == 1 and not args.small:
-            sur = surrogate_leg(pb, spots, scens, opts, args, value)
+        edge = _leg(lambda: edge_sweep_leg(args, peak_tops), not args.no_edge_sweep and world == 1)
+        div = _leg(lambda: divergent_leg(pb, spots, scens, opts, args, value, peak_tops),
+                   not args.no_divergent and world == 1)
+        dyn = _leg(lambda: dynamic_leg(scens, opts, value, peak_tops), not args.no_dynamic and world == 1)
+        sur = _leg(lambda: surrogate_leg(pb, spots, scens, opts, args, value),
+                   not args.no_surrogate and world == 1 and not args.small)
         set_hist = float(spots["n_hist"].sum()) * len(scens)
         out = {"metric": METRIC, "value": value, "unit": "protons/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -422,6 +410,19 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def _leg(fn, enabled: bool):
+    """One secondary leg of the bench line: its dict, None when disabled, or
+    {"error": ...} when it raised (the main measurement still prints)."""
+    if not enabled:
+        return None
+    try:
+        return fn()
+    except Exception as e:                                      # noqa: BLE001
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
 def run_ncu_case(args):
@@ -502,7 +503,7 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
     import dataclasses
     import torch
     from paper_2307_01416_gb300 import vpmc
-    tpb, epochs, batch = 12_500_000, 20, 16384
+    tpb, epochs, batch = 12_500_000, 7, 16384
     tr = vpmc.Engine(vpmc.surrogate_training_problem())
     t0 = time.perf_counter()
     feat, target, label = tr.surrogate_tracks(list(range(8)), tpb, W.Options(seed=W.SURROGATE_SEED))
@@ -773,7 +774,10 @@ def e2e_leg(pb, spots, scens, opts, args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         eng = vpmc.Engine(pb, host_ct=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         mats, st = eng.influence_matrix(spots, scens, opts)
+        t2 = time.perf_counter()
         if host is None:
             host = [{k: torch.empty(m[k].shape, dtype=m[k].dtype, pin_memory=True) for k in ("row_ptr", "col", "val")}
                     for m in mats]
@@ -785,8 +789,11 @@ def e2e_leg(pb, spots, scens, opts, args):
                 h[k].copy_(m[k], non_blocking=True)
                 nb += m[k].numel() * m[k].element_size()
         torch.cuda.synchronize()
+        t3 = time.perf_counter()
         eng.close()
         dt = time.perf_counter() - t0
+        print("e2e step %d: context %.3f s, influence matrices %.3f s (device %.3f s), copy back %.3f s, close %.3f s"
+              % (i, t1 - t0, t2 - t1, st["ms"] / 1000.0, t3 - t2, time.perf_counter() - t3), file=sys.stderr)
         if i == 0:
             continue                                   # first pass allocates the pinned buffers
         t_tot += dt

@@ -342,7 +342,9 @@ vpmc_status vpmc_surrogate_gradient(vpmc_ctx* ctx, const float* feat_dev, const 
 /* Adam training (beta 0.9 / 0.999, eps 1e-8) over n tracks: minibatches of
  * `batch` rows, `epochs` passes, each in its own batch order.  Learning rate
  * follows a cosine from lr to lr_min over all steps.  epoch_loss: optional
- * host array [epochs], the mean loss of each pass.  Synchronous. */
+ * host array [epochs], the mean loss of each pass.  A pass whose loss is not
+ * finite stops the training with VPMC_ERR_STATE (the parameters are then
+ * not usable).  Synchronous. */
 vpmc_status vpmc_surrogate_train(vpmc_ctx* ctx, const float* feat_dev, const float* target_dev,
                                  const int32_t* label_dev, int64_t n, int batch, int epochs, float lr, float lr_min,
                                  float* epoch_loss);

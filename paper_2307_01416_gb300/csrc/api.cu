@@ -1615,6 +1615,8 @@ vpmc_status vpmc_surrogate_train(vpmc_ctx* c, const float* feat_dev, const float
         if (epoch_loss) epoch_loss[e] = (float)(h[0] / (double)n);
         vpmc_status st = surrogate_status(c);
         if (st != VPMC_OK) return st;
+        if (!std::isfinite(h[0]))
+            return fail(VPMC_ERR_STATE, "training diverged in epoch %d (non-finite loss); lower lr or fewer steps", e);
     }
     return VPMC_OK;
 }
