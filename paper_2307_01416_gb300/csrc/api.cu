@@ -1654,6 +1654,10 @@ vpmc_status vpmc_surrogate_tracks(vpmc_ctx* c, const int* beam_ids, int n_beams,
     const long long total = (long long)n_beams * tracks_per_beam;
     float* d_frame = nullptr;
     CUDA_TRY(dev_alloc(&d_frame, (size_t)total * 8));
+    if (cudaMemsetAsync(d_frame, 0, (size_t)total * 8 * sizeof(float), c->stream) != cudaSuccess) {
+        cudaFree(d_frame);
+        return fail(VPMC_ERR_CUDA, "frame buffer reset failed");
+    }
     auto done = [&](vpmc_status s) {
         cudaFree(d_frame);
         return s;

@@ -596,7 +596,10 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             }
         }
         // ---- brass entry: edge frame and surrogate inputs (warp-cooperative) ----
-        const bool entry_q = ap_pending && !open && at_entry && (kTrack || kSur);
+        // training tracks record their inputs at birth whatever the opening
+        // test says (a start that rounds onto the opening's boundary can test
+        // inside); the surrogate draws only for brass entries
+        const bool entry_q = ap_pending && at_entry && (kTrack || (kSur && !open));
         const float4 ne = coop_nearest_edge(entry_q, L.p[0], L.p[1], poly, P.poly_kappa, q_off, q_n, lane);
         bool sur_emit = false;
         float feat[6], fnx = 0.0f, fny = 0.0f;
@@ -622,7 +625,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                 fr[0] = L.p[0]; fr[1] = L.p[1]; fr[2] = L.d[2]; fr[3] = fnx;
                 fr[4] = fny; fr[5] = un; fr[6] = ut; fr[7] = L.E;
             }
-            if (kSur) {
+            if (kSur && !open) {
                 if (1.2f * rmm < fminf(dist, T)) {
                     absorb = true;                  // cannot reach the opening or the exit face
                 } else if (L.E >= sur::kELo && L.E <= sur::kEHi && fabsf(un) <= sur::kAngMax &&
