@@ -781,15 +781,20 @@ def e2e_leg(pb, spots, scens, opts, args):
         if host is None:
             host = [{k: torch.empty(m[k].shape, dtype=m[k].dtype, pin_memory=True) for k in ("row_ptr", "col", "val")}
                     for m in mats]
-        nb = 0
+        nb, realloc = 0, 0
+        torch.cuda.synchronize()
+        t2b = time.perf_counter()
         for m, h in zip(mats, host):
             for k in ("row_ptr", "col", "val"):
                 if h[k].numel() != m[k].numel():
                     h[k] = torch.empty(m[k].shape, dtype=m[k].dtype, pin_memory=True)
+                    realloc += 1
                 h[k].copy_(m[k], non_blocking=True)
                 nb += m[k].numel() * m[k].element_size()
         torch.cuda.synchronize()
         t3 = time.perf_counter()
+        print("e2e step %d: %d pinned reallocations; %.1f GB back in %.3f s after %.3f s of queued device work"
+              % (i, realloc, nb / 1e9, t3 - t2b, t2b - t2), file=sys.stderr)
         eng.close()
         dt = time.perf_counter() - t0
         print("e2e step %d: context %.3f s, influence matrices %.3f s (device %.3f s), copy back %.3f s, close %.3f s"

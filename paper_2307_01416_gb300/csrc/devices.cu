@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
     int pool_item = 0;
     bool alive = false, done = false;
     Lane L;
-    L.item = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.stage = 0; L.forced = 0;
+    L.item = 0; L.beam = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.stage = 0; L.forced = 0;
     L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; }
@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
                 const DevItem I = P.items[it];
                 const DevBeam& B = beams[I.beam];
                 L.item = it;
+                L.beam = I.beam;
                 L.g = g;
                 L.hist = (uint32_t)(g - I.hist_off);
                 L.step = 0;
@@ -287,13 +288,12 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
         bool handoff = false;
         int fate = -1;
         if (alive) {
-            const DevItem& I = P.items[L.item];
-            const DevBeam& B = beams[__ldg(&I.beam)];
+            const DevBeam& B = beams[L.beam];
             if (++L.iters > P.max_iter) {
                 fate = kErr;
             } else if (L.stage < 0) {
                 if (B.rs) {
-                    const float sdr = (B.rs_tup - L.p[2]) / L.d[2];
+                    const float sdr = __fdividef(B.rs_tup - L.p[2], L.d[2]);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
                     L.R = range_of(pmma.Rt, L.E);
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
                 // outside the slab's radius: straight flight to its exit plane
                 if (!(L.d[2] > 0.0f)) fate = kLeak;
                 else {
-                    const float sf = (B.rs_tdn - L.p[2]) / L.d[2];
+                    const float sf = __fdividef(B.rs_tdn - L.p[2], L.d[2]);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sf, L.d[k], L.p[k]);
                     handoff = true;
@@ -313,8 +313,8 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
             } else {
                 float s_geom = __int_as_float(0x7f800000);
                 bool down = true;
-                if (L.d[2] > 0.0f) s_geom = (B.rs_tdn - L.p[2]) / L.d[2];
-                else if (L.d[2] < 0.0f) { s_geom = (B.rs_tup - L.p[2]) / L.d[2]; down = false; }
+                if (L.d[2] > 0.0f) s_geom = __fdividef(B.rs_tdn - L.p[2], L.d[2]);
+                else if (L.d[2] < 0.0f) { s_geom = __fdividef(B.rs_tup - L.p[2], L.d[2]); down = false; }
                 s_geom = fmaxf(s_geom, 0.0f);       // scattering offsets can leave it past the plane
                 StepResult o;
                 ch_step(pmma, s_geom, L, P, key, o);
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
                 if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }
                 if (P.records && L.g < P.rec_cap) {
                     float pos[3];
-                    bev_to_patient(B, P.scens[__ldg(&I.scen)], L.p, pos);
+                    bev_to_patient(B, P.scens[__ldg(&P.items[L.item].scen)], L.p, pos);
                     write_record(P, L, fate, pos, 0ull);
                 }
                 alive = false;
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
     int pool_item = 0;
     bool alive = false, done = false;
     Lane L;
-    L.item = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.stage = 0; L.forced = 0;
+    L.item = 0; L.beam = 0; L.g = 0; L.hist = 0; L.qdep = 0ull; L.iters = 0; L.stage = 0; L.forced = 0;
     L.step = 0; L.E = 0.0f; L.R = 0.0f; L.nlam = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) { L.p[k] = 0.0f; L.d[k] = 0.0f; }
@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                     const DevItem I = P.items[it];
                     const DevBeam& B = beams[I.beam];
                     L.item = it;
+                    L.beam = I.beam;
                     L.g = g;
                     L.hist = (uint32_t)(g - I.hist_off);
                     L.step = 0;
@@ -485,6 +486,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                     const PhaseRec r = P.mid[g];
                     const DevItem I = P.items[r.item];
                     L.item = r.item;
+                    L.beam = I.beam;
                     L.g = r.g;
                     L.hist = (uint32_t)(r.g - I.hist_off);
                     L.step = r.step;
@@ -521,8 +523,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
         // walls) and the opening's scale at the point's depth
         float pu = 0.0f, pv = 0.0f, sc = 1.0f;
         if (alive) {
-            const DevItem& I = P.items[L.item];
-            const DevBeam& B = beams[__ldg(&I.beam)];
+            const DevBeam& B = beams[L.beam];
             if (++L.iters > P.max_iter) {
                 fate = kErr;
             } else if (L.stage < 0) {
@@ -530,8 +531,8 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             } else {
                 // ---- aperture block: geometry needing exact polygon tests is
                 // requested here and served below by the whole warp ----
-                if (L.d[2] > 0.0f) s_geom = (B.ap_tdn - L.p[2]) / L.d[2];
-                else if (L.d[2] < 0.0f) { s_geom = (B.ap_tup - L.p[2]) / L.d[2]; down = false; }
+                if (L.d[2] > 0.0f) s_geom = __fdividef(B.ap_tdn - L.p[2], L.d[2]);
+                else if (L.d[2] < 0.0f) { s_geom = __fdividef(B.ap_tup - L.p[2], L.d[2]); down = false; }
                 s_geom = fmaxf(s_geom, 0.0f);       // scattering offsets can leave it past the plane
                 ap_pending = true;
                 was_forced = L.forced > 0;
@@ -559,7 +560,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
         // c = t + sad (parallel walls: g = s and (hx, hy) = d_xy)
         float hx = L.d[0], hy = L.d[1], cdiv = 0.0f;
         if (ap_pending) {
-            const DevBeam& B = beams[__ldg(&P.items[L.item].beam)];
+            const DevBeam& B = beams[L.beam];
             open = cls == 1 || (cls == 2 && pip_in);
             if (open) {
                 float g_exit = s_geom;
@@ -604,7 +605,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
         bool sur_emit = false;
         float feat[6], fnx = 0.0f, fny = 0.0f;
         if (entry_q) {
-            const DevBeam& B = beams[__ldg(&P.items[L.item].beam)];
+            const DevBeam& B = beams[L.beam];
             const float T = B.ap_tdn - B.ap_tup;
             const float dist = ne.x;
             const float inv = dist > 0.0f ? 1.0f / dist : 0.0f;
@@ -674,15 +675,14 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
         // ---- exact wall hit and wall distance (warp-cooperative) ----
         float sw = coop_first_wall_hit(need_hit, pu, pv, hx, hy, poly, q_off, q_n, lane);
         const float dw = coop_wall_distance(need_dist, pu, pv, poly, q_off, q_n, lane) * sc *
-                         (ap_pending ? beams[__ldg(&P.items[L.item].beam)].ap_cos : 1.0f);
+                         (ap_pending ? beams[L.beam].ap_cos : 1.0f);
         if (cdiv > 0.0f && isfinite(sw)) {
             // back from g to the path length: s = g c / (c - g d_t)
             const float den = cdiv - sw * L.d[2];
             sw = den > 0.0f ? sw * cdiv / den : __int_as_float(0x7f800000);
         }
         if (alive) {
-            const DevItem& I = P.items[L.item];
-            const DevBeam& B = beams[__ldg(&I.beam)];
+            const DevBeam& B = beams[L.beam];
             if (ap_pending) {
                 if (open) {
                     // opening: keep velocity and direction up to a wall or the exit
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                 if (from < 1 && B.ap) {
                     if (!(L.d[2] > 0.0f)) fate = kLeak;
                     else {
-                        const float sdr = (B.ap_tup - L.p[2]) / L.d[2];
+                        const float sdr = __fdividef(B.ap_tup - L.p[2], L.d[2]);
 #pragma unroll
                         for (int k = 0; k < 3; ++k) L.p[k] = fmaf(sdr, L.d[k], L.p[k]);
                         L.R = range_of(brass.Rt, L.E);
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                 if (fate == kErr) { acc_err += 1; atomicOr(P.status, 1); }
                 if (P.records && L.g < P.rec_cap) {
                     float pos[3];
-                    bev_to_patient(B, scens[__ldg(&I.scen)], L.p, pos);
+                    bev_to_patient(B, scens[__ldg(&P.items[L.item].scen)], L.p, pos);
                     write_record(P, L, fate, pos, 0ull);
                 }
                 if (kTrack && L.g < P.total) {
@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
         if (kTrack) {
             if (handoff) {
                 // training track: targets from the exit state against the entry frame
-                const DevBeam& B = beams[__ldg(&P.items[L.item].beam)];
+                const DevBeam& B = beams[L.beam];
                 const float T = B.ap_tdn - B.ap_tup;
                 const float* fr = P.trk_frame + 8 * L.g;
                 const float nx = fr[3], ny = fr[4], un = fr[5], ut = fr[6], E0 = fr[7];
@@ -789,9 +789,8 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             base = __shfl_sync(kFull, base, leader);
             if (handoff) {
                 const long long slot = (long long)base + __popc(hmask & lt_mask);
-                const DevItem& I = P.items[L.item];
-                const DevBeam& B = beams[__ldg(&I.beam)];
-                const DevScen& SC = scens[__ldg(&I.scen)];
+                const DevBeam& B = beams[L.beam];
+                const DevScen& SC = scens[__ldg(&P.items[L.item].scen)];
                 if (slot < P.phase_cap) {
                     PhaseRec r;
                     bev_to_patient(B, SC, L.p, r.p);

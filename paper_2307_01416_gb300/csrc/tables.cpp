@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "tables.h"
@@ -207,7 +208,9 @@ void build_raster(const double* xy, int n, double margin, unsigned char* cells, 
     // FP32 placement of a point can move it by a few ulps across a cell border,
     // so a cell is classified only if no edge comes within eps of it
     const double eps = 1e-3 * std::max(cw, ch) + 1e-4 * (std::fabs(xmin) + std::fabs(ymin) + 1.0);
-    for (int cy = 0; cy < kRaster; ++cy)
+    // rows are independent: split them over the host's threads
+    auto rows = [&](int cy_begin, int cy_end) {
+    for (int cy = cy_begin; cy < cy_end; ++cy)
         for (int cx = 0; cx < kRaster; ++cx) {
             const double x0 = xmin + cx * cw - eps, x1 = xmin + (cx + 1) * cw + eps;
             const double y0 = ymin + cy * ch - eps, y1 = ymin + (cy + 1) * ch + eps;
@@ -233,6 +236,12 @@ void build_raster(const double* xy, int n, double margin, unsigned char* cells, 
             }
             lower[cy * kRaster + cx] = (float)lb;
         }
+    };
+    const int nt = (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(rows, t * kRaster / nt, (t + 1) * kRaster / nt);
+    rows(0, kRaster / nt);
+    for (std::thread& th : pool) th.join();
 }
 
 void hu_curve_props(const double* curve15, double hu, double* rho, double* spr) { curve_props(curve15, hu, rho, spr); }

@@ -136,6 +136,7 @@ struct Lane {
     int forced;     // aperture: 1 the next step is in brass (after a wall hit), -1 on the entrance plane
     int ic[3], is[3];
     int item;
+    int beam;       // the item's beam entry (kept so that each iteration reads it from a register)
     int iters;
     long long g;
     unsigned long long qdep;
@@ -225,17 +226,30 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
         const float dx2 = s * th0 * fmaf(zb.x, 0.28867513459481287f, 0.5f * zb.y);
         float e1[3], e2[3];
         orthonormal_basis(L.d, e1, e2);
-        const float th = fast_sqrt(th1 * th1 + th2 * th2);
-        float sn, c;
-        __sincosf(th, &sn, &c);
-        const float sc = th > 0.0f ? __fdividef(sn, th) : 1.0f;
+        // deflection by theta = |(th1, th2)|: cos(theta) and sin(theta)/theta.
+        // Up to theta^2 = 0.09 their Taylor series in theta^2, cut after the
+        // theta^6 terms, are exact to a few 1e-9 -- below FP32 rounding
+        // (almost every step: theta0 is a few mrad); beyond, the functions
+        const float t = fmaf(th1, th1, th2 * th2);
+        float c, sc;
+        if (t <= 0.09f) {
+            c = fmaf(t, fmaf(t, fmaf(t, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f), 1.0f);
+            sc = fmaf(t, fmaf(t, fmaf(t, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+        } else {
+            const float th = sqrt_approx(t);
+            float sn;
+            __sincosf(th, &sn, &c);
+            sc = __fdividef(sn, th);
+        }
         float nd[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             o.disp[k] = dx1 * e1[k] + dx2 * e2[k];
             nd[k] = c * L.d[k] + sc * (th1 * e1[k] + th2 * e2[k]);
         }
-        const float inv = rsqrtf(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
+        // |nd| = 1 to rounding: one Newton step of 1/sqrt(n2) from 1 renormalises
+        const float n2 = fmaf(nd[0], nd[0], fmaf(nd[1], nd[1], nd[2] * nd[2]));
+        const float inv = fmaf(-0.5f, n2, 1.5f);
 #pragma unroll
         for (int k = 0; k < 3; ++k) L.d[k] = nd[k] * inv;
     }
