@@ -804,6 +804,7 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
         // range rejection needs wall distances up to half the block thickness only
         build_raster(poly.data(), b->n_vertices, (0.5 * b->ap_thickness_mm + 1.0) * margin_scale, ras.data(),
                      ras_lb.data(), d.ras_lo, d.ras_inv, &d.ras_diag);
+        d.ras_margin = (float)((0.5 * b->ap_thickness_mm + 1.0) * margin_scale * (1.0 - 1e-6));
         d.nvert = b->n_vertices;
     }
     if (first_device < 1e300 && !(-b->source_to_iso_mm < first_device))

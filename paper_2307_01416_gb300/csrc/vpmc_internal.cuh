@@ -51,6 +51,7 @@ struct DevBeam {
     float ras_lo[2], ras_inv[2];     // raster origin and 1/cell size
     int ras_off;                     // offset into the raster arrays (class bytes, distance bounds)
     float ras_diag;                  // raster cell diagonal
+    float ras_margin;                // points outside the raster are at least this far from the boundary
     float r_circ;                    // largest vertex distance from the beam axis (training tracks)
     float ap_sad;                    // divergent walls: virtual source at t = -ap_sad (0: parallel walls)
     float ap_K;                      // ap_tdn + ap_sad: opening scale at depth t = (t + ap_sad) / ap_K
