@@ -336,6 +336,8 @@ TransportParams base_params(vpmc_ctx* c, const vpmc_opts& o)
     p.mid_count = c->d_mid_count;
     p.poly_kappa = c->d_poly_kappa;
     p.surrogate = o.surrogate && c->sur_ready ? 1 : 0;
+    p.n_rep = 1;                    // set by the influence-matrix path when scenarios share the beam line
+    p.rep_cap = c->phase_cap;
     return p;
 }
 
@@ -371,14 +373,20 @@ vpmc_status ensure_phase(vpmc_ctx* c, long long total, bool surrogate = false)
 }
 
 // Enqueues the transport of histories [0, total) of p's items: batches of at
-// most phase_cap histories, each the devices kernel then the patient kernel.
+// most phase_cap / n_rep histories, each the devices kernel then the patient
+// kernel (which takes n_rep copies of every survivor, one per scenario).
 vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, const TuneResult& t)
 {
+    if (p.n_rep < 1) p.n_rep = 1;
+    const long long batch = c->phase_cap / p.n_rep;
+    if (batch < 1) return fail(VPMC_ERR_STATE, "hand-off buffer smaller than one record per scenario");
     p.phase = c->d_phase;
     p.phase_cap = c->phase_cap;
     p.phase_count = c->d_phase_count;
+    p.rep_cap = batch;
+    p.rep_hist = p.n_rep > 1 ? p.rep_hist : total;
     p.mid = c->d_mid;
-    p.mid_cap = c->phase_cap;
+    p.mid_cap = batch;
     p.mid_count = c->d_mid_count;
     p.aggregate = t.aggregate;
     p.chunk = t.chunk;
@@ -394,10 +402,10 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
     CUDA_TRY(cudaStreamIsCapturing(c->stream, &cap));
     const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     c->kev_batches = 0;
-    for (long long h0 = 0; h0 < total; h0 += c->phase_cap) {
+    for (long long h0 = 0; h0 < total; h0 += batch) {
         const int b = c->kev_batches < vpmc_ctx::kTimedBatches ? c->kev_batches++ : -1;
         p.hist_begin = h0;
-        p.total = std::min(total, h0 + c->phase_cap);
+        p.total = std::min(total, h0 + batch);
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
         CUDA_TRY(cudaMemsetAsync(c->d_phase_count, 0, sizeof(unsigned long long), c->stream));
         if (p.surrogate) CUDA_TRY(cudaMemsetAsync(c->d_sq_count, 0, sizeof(unsigned long long), c->stream));
@@ -804,7 +812,6 @@ vpmc_status vpmc_set_aperture(vpmc_ctx* c, int beam_id, const vpmc_beam* b)
         // range rejection needs wall distances up to half the block thickness only
         build_raster(poly.data(), b->n_vertices, (0.5 * b->ap_thickness_mm + 1.0) * margin_scale, ras.data(),
                      ras_lb.data(), d.ras_lo, d.ras_inv, &d.ras_diag);
-        d.ras_margin = (float)((0.5 * b->ap_thickness_mm + 1.0) * margin_scale * (1.0 - 1e-6));
         d.nvert = b->n_vertices;
     }
     if (first_device < 1e300 && !(-b->source_to_iso_mm < first_device))
@@ -1206,10 +1213,19 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         IM_ST(ensure_phase(c, total, o.surrogate && c->sur_ready));
         TransportParams p = base_params(c, o);
         p.items = c->d_items;
-        p.n_items = (int)items.size();
+        // the wave's scenarios share the beam-line transport (the random
+        // numbers do not depend on the scenario): the beam-line kernels run
+        // over the first scenario's items, and each survivor is handed to the
+        // patient kernel once per scenario
+        const long long per_scen = total / ns;
+        p.n_items = n_spots;
+        p.n_rep = ns;
+        p.rep_items = n_spots;
+        p.rep_hist = per_scen;
+        p.rep_cap = c->phase_cap / ns;
         p.boxes = c->d_boxes;
         p.n_scen = n_scen;
-        p.total = total;
+        p.total = per_scen;
         p.scratch = c->d_scratch;
         p.unit_weight = 1;              // every item's wscale is 2^F
         p.records = nullptr;
@@ -1238,7 +1254,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             IM_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            vpmc_status qs = enqueue_transport(c, p, total, tr);
+            vpmc_status qs = enqueue_transport(c, p, per_scen, tr);
             cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
             IM_ST(qs);
             IM_TRY(ce);

@@ -20,10 +20,6 @@ namespace {
 using namespace dev;
 using namespace tr;
 
-// Brass steps a lane may take inside one iteration of the aperture kernel
-// while it is certainly away from the opening.
-constexpr int kInner = 8;
-
 // Lower bound of the distance from (a, b) to the polygon boundary from the
 // raster (0 outside it or in a cell an edge passes through).
 __device__ __forceinline__ float wall_lower_bound(const DevBeam& B, const float* __restrict__ lower, float a, float b)
@@ -39,22 +35,6 @@ __device__ __forceinline__ float wall_lower_bound(const DevBeam& B, const float*
 // the requests one by one, each lane evaluating every 32nd edge with the same
 // per-edge arithmetic as a serial loop, and the warp reduces the results.
 // Every lane of the warp must call these (need = false for non-requesters).
-
-// Raster class of (a, b) and the lower bound of its distance to the boundary
-// (points outside the raster: class 0, at least the raster's margin away).
-__device__ __forceinline__ int raster_class_lb(const DevBeam& B, const unsigned char* __restrict__ raster,
-                                               const float* __restrict__ lower, float a, float b, float* lb)
-{
-    const float fx = (a - B.ras_lo[0]) * B.ras_inv[0];
-    const float fy = (b - B.ras_lo[1]) * B.ras_inv[1];
-    if (!(fx >= 0.0f && fx < (float)kRaster && fy >= 0.0f && fy < (float)kRaster)) {
-        *lb = B.ras_margin;
-        return 0;
-    }
-    const int cell = B.ras_off + (int)fy * kRaster + (int)fx;
-    *lb = __ldg(lower + cell);
-    return __ldg(raster + cell);
-}
 
 // Raster class of (a, b): 0 outside the opening, 1 inside, 2 near an edge.
 __device__ __forceinline__ int raster_class(const DevBeam& B, const unsigned char* __restrict__ raster, float a, float b)
@@ -387,7 +367,10 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
             }
         }
     }
-    unsigned long long v[kNStats] = {0ull, acc_leak, acc_rs, 0ull, acc_nuc, acc_steps, acc_err, acc_steps, 0ull};
+    // energies and errors count once per scenario sharing the transport; steps as taken
+    const unsigned long long nr = (unsigned long long)P.n_rep;
+    unsigned long long v[kNStats] = {0ull, acc_leak * nr, acc_rs * nr, 0ull, acc_nuc * nr, acc_steps, acc_err * nr,
+                                     acc_steps, 0ull};
     warp_add_stats(P, v, lane);
 }
 
@@ -538,7 +521,6 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
         bool down = true;
         bool ap_pending = false, was_forced = false, at_entry = false, need_pip = false;
         int cls = 0, q_off = 0, q_n = 0;
-        float lb_open = 0.0f;           // lower bound of the in-plane distance to the opening (class 0)
         // opening coordinates: the point projected from the virtual source onto
         // the downstream face (divergent walls; the point itself for parallel
         // walls) and the opening's scale at the point's depth
@@ -566,7 +548,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                     pu *= inv;
                     pv *= inv;
                 }
-                if (!was_forced) cls = raster_class_lb(B, P.raster, P.raster_lb, pu, pv, &lb_open);
+                cls = was_forced ? 0 : raster_class(B, P.raster, pu, pv);
                 need_pip = cls == 2;
                 q_off = B.poly_off;
                 q_n = B.nvert;
@@ -747,44 +729,6 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                     for (int k = 0; k < 3; ++k) L.p[k] += o.disp[k];
                     if (o.lim == 1) { if (down) advance = true; else fate = kLeak; }
                 }
-                // Deeper in the brass (parallel walls, a cell no edge crosses) the
-                // step's start point stays out of the opening while the in-plane
-                // distance it has moved is below the cell's distance bound: further
-                // steps follow here without the opening tests (the same steps and
-                // random numbers the outer loop would take), at most kInner of them.
-                // Range rejection uses the remaining distance as its bound.
-                float budget = lb_open - (o.s + fabsf(o.disp[0]) + fabsf(o.disp[1]));
-                if (!(cls == 0 && !was_forced && B.ap_sad == 0.0f)) budget = 0.0f;
-                for (int k = 0; k < kInner && fate < 0 && !advance && budget > 0.0f; ++k) {
-                    if (++L.iters > P.max_iter) { fate = kErr; break; }
-                    if (P.range_rejection) {
-                        const float rm = 1.2f * L.R * __fdividef(1.0f, brass.rho);
-                        if (rm < fminf(fminf(L.p[2] - B.ap_tup, B.ap_tdn - L.p[2]), budget)) {
-                            acc_ap += to_fixed(L.E, P.fscale, P.fx32);
-                            L.E = 0.0f;
-                            fate = kAbsAp;
-                            break;
-                        }
-                    }
-                    float sg = __int_as_float(0x7f800000);
-                    down = true;
-                    if (L.d[2] > 0.0f) sg = __fdividef(B.ap_tdn - L.p[2], L.d[2]);
-                    else if (L.d[2] < 0.0f) { sg = __fdividef(B.ap_tup - L.p[2], L.d[2]); down = false; }
-                    sg = fmaxf(sg, 0.0f);
-                    ch_step(brass, sg, L, P, key, o);
-                    acc_steps += 1;
-                    const unsigned long long q2 = to_fixed(o.dE, P.fscale, P.fx32);
-                    acc_ap += q2;
-                    if (o.killed) {
-                        if (o.killed == 2) acc_nuc += q2;
-                        fate = kAbsAp;
-                        break;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) L.p[j] += o.disp[j];
-                    if (o.lim == 1) { if (down) advance = true; else fate = kLeak; break; }
-                    budget -= o.s + fabsf(o.disp[0]) + fabsf(o.disp[1]);
-                }
             }
             if (advance && fate < 0) {
                 // the single place where a history changes stage
@@ -849,18 +793,21 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             if (handoff) {
                 const long long slot = (long long)base + __popc(hmask & lt_mask);
                 const DevBeam& B = beams[L.beam];
-                const DevScen& SC = scens[__ldg(&P.items[L.item].scen)];
-                if (slot < P.phase_cap) {
+                if (slot < P.rep_cap) {
+                    // one copy per scenario sharing the transport, with that scenario's shift
+                    const int scen0 = __ldg(&P.items[L.item].scen);
                     PhaseRec r;
-                    bev_to_patient(B, SC, L.p, r.p);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) r.d[k] = L.d[0] * B.u[k] + L.d[1] * B.v[k] + L.d[2] * B.w[k];
                     r.E = L.E;
                     r.nlam = L.nlam;
                     r.step = L.step;
-                    r.item = L.item;
-                    r.g = L.g;
-                    P.phase[slot] = r;
+                    for (int s = 0; s < P.n_rep; ++s) {
+                        bev_to_patient(B, scens[scen0 + s], L.p, r.p);
+                        r.item = L.item + s * P.rep_items;
+                        r.g = L.g + s * P.rep_hist;
+                        P.phase[s * P.rep_cap + slot] = r;
+                    }
                 } else {
                     atomicOr(P.status, 2);          // hand-off buffer too small (host sizes it to the batch)
                 }
@@ -868,7 +815,10 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             }
         }
     }
-    unsigned long long v[kNStats] = {0ull, acc_leak, 0ull, acc_ap, acc_nuc, acc_steps, acc_err, 0ull, acc_steps};
+    // energies and errors count once per scenario sharing the transport; steps as taken
+    const unsigned long long nr = (unsigned long long)P.n_rep;
+    unsigned long long v[kNStats] = {0ull, acc_leak * nr, 0ull, acc_ap * nr, acc_nuc * nr, acc_steps, acc_err * nr,
+                                     0ull, acc_steps};
     warp_add_stats(P, v, lane);
 }
 

@@ -245,6 +245,8 @@ extern "C" vpmc_status vpmc_run_spots_noalloc(vpmc_ctx* c, const vpmc_spot* spot
     p.scratch = acc;
     p.phase = phase;
     p.phase_cap = kBatch;
+    p.n_rep = 1;
+    p.rep_cap = kBatch;
     p.mid = mid;
     p.mid_cap = kBatch;
     p.ovf = nullptr;

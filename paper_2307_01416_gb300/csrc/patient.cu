@@ -77,9 +77,11 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
             pool.end = s_pool[1];
             const unsigned lt_mask = (1u << lane) - 1u;
             while (need) {
+                // the work is n_rep regions (one per scenario sharing the
+                // beam-line transport) of cnt records each
+                const long long cnt = min((long long)*P.phase_count, P.rep_cap);
                 if (pool.next >= pool.end) {
-                    const long long total = min((long long)*P.phase_count, P.phase_cap);
-                    if (!pool.refill(P, 0, total, lane)) {
+                    if (!pool.refill(P, 0, cnt * P.n_rep, lane)) {
                         if (!alive) done = true;
                         break;
                     }
@@ -87,7 +89,9 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                 const int take = (int)min((long long)__popc(need), pool.end - pool.next);
                 const bool mine = ((need >> lane) & 1u) && __popc(need & lt_mask) < take;
                 if (mine) {
-                    const PhaseRec r = P.phase[pool.next + __popc(need & lt_mask)];
+                    const long long w = pool.next + __popc(need & lt_mask);
+                    const long long reg = w / cnt;
+                    const PhaseRec r = P.phase[reg * P.rep_cap + (w - reg * cnt)];
                     if (r.item >= 0) {        // item -1: a slot the aperture surrogate left empty
                         const DevItem I = P.items[r.item];
                         s_item[threadIdx.x] = r.item;

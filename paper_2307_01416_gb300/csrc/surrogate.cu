@@ -448,6 +448,9 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
 
         bool emit = false;
         PhaseRec rec;
+        float pb[3] = {0.0f, 0.0f, 0.0f};       // exit point, BEV frame
+        int scen0 = 0;
+        const DevBeam* Bp = P.beams;
         if (row < nq) {
             const SurQuery q = qs[r];
             const DevItem& I = P.items[q.item];
@@ -477,10 +480,12 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
                     vt *= sc;
                 }
                 if (trans && E1 > kEcut && E1 <= q.E && isfinite(dn + dt + vn + vt)) {
-                    const DevScen& SC = P.scens[I.scen];
-                    const float pb[3] = {q.px + dn * q.nx - dt * q.ny, q.py + dn * q.ny + dt * q.nx, B.ap_tdn};
+                    scen0 = I.scen;
+                    Bp = &B;
+                    pb[0] = q.px + dn * q.nx - dt * q.ny;
+                    pb[1] = q.py + dn * q.ny + dt * q.nx;
+                    pb[2] = B.ap_tdn;
                     const float db[3] = {vn * q.nx - vt * q.ny, vn * q.ny + vt * q.nx, sqrtf(1.0f - vn * vn - vt * vt)};
-                    bev_to_patient(B, SC, pb, rec.p);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) rec.d[k] = db[0] * B.u[k] + db[1] * B.v[k] + db[2] * B.w[k];
                     rec.E = E1;
@@ -494,9 +499,9 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
                     rec.item = q.item;
                     rec.g = q.g;
                     emit = true;
-                    acc_ap += __float2ull_rn((q.E - E1) * P.fscale);
+                    acc_ap += __float2ull_rn((q.E - E1) * P.fscale) * (unsigned long long)P.n_rep;
                 } else {
-                    acc_ap += __float2ull_rn(q.E * P.fscale);
+                    acc_ap += __float2ull_rn(q.E * P.fscale) * (unsigned long long)P.n_rep;
                     if (P.records && q.g < P.rec_cap) {
                         HistRecord hr;
                         hr.q_dep = 0;
@@ -504,8 +509,8 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
                         hr.steps = (int)q.step;
                         hr.e_dep = 0.0f;
                         hr.e_end = 0.0f;
-                        const float pb[3] = {q.px, q.py, B.ap_tup};
-                        bev_to_patient(B, P.scens[I.scen], pb, hr.pos);
+                        const float pe[3] = {q.px, q.py, B.ap_tup};
+                        bev_to_patient(B, P.scens[I.scen], pe, hr.pos);
                         hr.pad = 0.0f;
                         P.records[q.g] = hr;
                     }
@@ -516,12 +521,22 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
         // an absorbed proton leaves the slot empty (item -1)
         if (row < nq && !P.track_mode) {
             const long long slot = qs[r].slot;
-            if (slot >= 0 && slot < P.phase_cap) {
+            if (slot >= 0 && slot < P.rep_cap) {
                 if (!emit) {
                     rec = PhaseRec{};
                     rec.item = -1;
                 }
-                P.phase[slot] = rec;
+                // one copy per scenario sharing the beam-line transport
+                const int item0 = rec.item;
+                const long long g0 = rec.g;
+                for (int s = 0; s < P.n_rep; ++s) {
+                    if (emit) {
+                        bev_to_patient(*Bp, P.scens[scen0 + s], pb, rec.p);
+                        rec.item = item0 + s * P.rep_items;
+                        rec.g = g0 + s * P.rep_hist;
+                    }
+                    P.phase[s * P.rep_cap + slot] = rec;
+                }
             } else {
                 atomicOr(P.status, 2);
             }

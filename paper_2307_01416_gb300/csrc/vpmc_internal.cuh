@@ -51,7 +51,6 @@ struct DevBeam {
     float ras_lo[2], ras_inv[2];     // raster origin and 1/cell size
     int ras_off;                     // offset into the raster arrays (class bytes, distance bounds)
     float ras_diag;                  // raster cell diagonal
-    float ras_margin;                // points outside the raster are at least this far from the boundary
     float r_circ;                    // largest vertex distance from the beam axis (training tracks)
     float ap_sad;                    // divergent walls: virtual source at t = -ap_sad (0: parallel walls)
     float ap_K;                      // ap_tdn + ap_sad: opening scale at depth t = (t + ap_sad) / ap_K
@@ -186,6 +185,15 @@ struct TransportParams {
     PhaseRec* phase;                 // histories handed from the aperture to the patient kernel
     unsigned long long* phase_count;
     long long phase_cap;
+    // Scenarios share the beam-line transport: the random numbers do not
+    // depend on the scenario, so a history's source, range shifter and
+    // aperture are the same in all of them.  The beam-line kernels run over
+    // the first scenario's items only and hand each survivor to the patient
+    // kernel once per scenario, copy s into region s of the hand-off buffer.
+    int n_rep;                       // scenarios sharing the beam-line transport (1: none)
+    int rep_items;                   // items per scenario: copy s refers to item + s * rep_items
+    long long rep_hist;              // histories per scenario: copy s has global index g + s * rep_hist
+    long long rep_cap;               // records of one region of the hand-off buffer
     OvfRec* ovf;                     // out-of-box deposits (NULL: none expected)
     unsigned long long* ovf_count;   // records appended (may exceed ovf_cap: then re-run)
     long long ovf_cap;
