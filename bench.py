@@ -503,7 +503,7 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
     import dataclasses
     import torch
     from paper_2307_01416_gb300 import vpmc
-    tpb, epochs, batch = 12_500_000, 7, 16384
+    tpb, epochs, batch = 12_500_000, 10, 65536
     tr = vpmc.Engine(vpmc.surrogate_training_problem())
     t0 = time.perf_counter()
     feat, target, label = tr.surrogate_tracks(list(range(8)), tpb, W.Options(seed=W.SURROGATE_SEED))
@@ -513,7 +513,7 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
-    losses = tr.surrogate_train(feat, target, label, batch=batch, epochs=epochs, lr=2e-3, lr_min=2e-5)
+    losses = tr.surrogate_train(feat, target, label, batch=batch, epochs=epochs, lr=4e-3, lr_min=4e-5)
     ev1.record()
     torch.cuda.synchronize()
     train_s = ev0.elapsed_time(ev1) / 1000.0

@@ -24,7 +24,7 @@ def weights():
         pytest.skip("no CUDA device")
     torch.cuda.set_device(0)
     from paper_2307_01416_gb300 import vpmc
-    w, losses = vpmc.train_surrogate(tracks_per_beam=12_500_000, epochs=7, batch=16384, lr=2e-3, lr_min=2e-5)
+    w, losses = vpmc.train_surrogate(tracks_per_beam=12_500_000, epochs=10, batch=65536, lr=4e-3, lr_min=4e-5)
     assert np.all(np.isfinite(losses)) and losses[-1] < losses[0]
     return w
 
