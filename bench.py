@@ -73,11 +73,12 @@ def parse_args():
     ap.add_argument("--divergent-sad", type=float, default=2000.0)
     ap.add_argument("--edge-hist", type=int, default=1_000_000, help="histories per beamlet of the edge sweep")
     ap.add_argument("--opt-iterations", type=int, default=50)
-    ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im", "opt"], default=None,
-                    help="small fixed-launch transport case for ncu captures (nominal scenario, every 10th spot): "
-                         "'dose' scores one grid, 'im' scores influence-matrix columns; 'opt' runs the robust "
-                         "optimisation (--opt-iterations per step) over a 13-scenario set of every --opt-stride-th "
-                         "spot")
+    ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im", "im13", "opt"], default=None,
+                    help="small fixed-launch transport case for ncu captures (every 10th spot): 'dose' scores one "
+                         "grid of the nominal scenario, 'im' its influence-matrix columns, 'im13' the columns of all "
+                         "13 scenarios (the set's structure: one beam-line pass, 13 patient copies); 'opt' runs the "
+                         "robust optimisation (--opt-iterations per step) over a 13-scenario set of every "
+                         "--opt-stride-th spot")
     ap.add_argument("--opt-stride", type=int, default=1)
     return ap.parse_args()
 
@@ -139,12 +140,13 @@ class ClockSampler:
                 "reasons": sorted(active), "samples": len(rows)}
 
 
-def transport_traffic(steps_per_launch: float):
-    """DRAM bytes (read + write) of one set's transport: the bytes per
-    condensed-history step that an ncu capture of the three transport
-    kernels measured on the small influence-matrix case (dram__bytes_read.sum
-    + dram__bytes_write.sum over its steps), scaled by the set's steps; None
-    when the kernels changed since that capture (source hash)."""
+def transport_traffic(patient_steps: float, beamline_histories: float):
+    """DRAM bytes (read + write) of one set's transport: the bytes per patient
+    step (k_patient) and per history handed through the beam line
+    (k_source_rs + k_aperture, with the scenarios' copies) that an ncu capture
+    of the 13-scenario small case measured (dram__bytes_read.sum +
+    dram__bytes_write.sum), scaled by the set's patient steps and beam-line
+    histories; None when the kernels changed since that capture (source hash)."""
     path = os.path.join(ROOT, "profiles", "k_transport_traffic.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
@@ -152,7 +154,8 @@ def transport_traffic(steps_per_launch: float):
         return None
     if kv.get("transport_sha256") != transport_source_digest():
         return None
-    return float(kv["dram_bytes_per_step"]) * steps_per_launch
+    return (float(kv["patient_dram_bytes_per_step"]) * patient_steps
+            + float(kv["beamline_dram_bytes_per_history"]) * beamline_histories)
 
 
 TRANSPORT_SOURCES = ("transport_common.cuh", "devices.cu", "patient.cu")
@@ -364,7 +367,7 @@ def main():
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
         peak_tops = nsm * 4 * 32 * sm_max * 1e6 / 1e12
         achieved = ops / (kern_ms / 1000.0) / 1e12
-        traffic = transport_traffic(steps / args.steps)
+        traffic = transport_traffic(patient_steps / args.steps, hist / args.steps / len(scens))
         l2 = vpmc.measure_l2_atomics()                 # untimed: the secondary bound's peak
         adds_rate = patient_steps / (ms_patient / 1000.0) if ms_patient > 0 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
@@ -442,8 +445,9 @@ def run_ncu_case(args):
     eng = vpmc.Engine(pb)
     opts = W.Options(seed=1234)
     for i in range(args.warmup + args.steps):
-        if args.ncu_case == "im":
-            mats, st = eng.influence_matrix(sub, [W.Scenario()], opts, block_size=896, aggregate=0, chunk=32)
+        if args.ncu_case in ("im", "im13"):
+            sc = scens if args.ncu_case == "im13" else [W.Scenario()]
+            mats, st = eng.influence_matrix(sub, sc, opts, block_size=896, aggregate=0, chunk=32)
             del mats
         else:
             dose, st, _ = eng.run_spots(sub, W.Scenario(), opts, block_size=896, aggregate=1, chunk=32)
@@ -503,7 +507,7 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
     import dataclasses
     import torch
     from paper_2307_01416_gb300 import vpmc
-    tpb, epochs, batch = 12_500_000, 10, 65536
+    tpb, epochs, batch = 12_500_000, 7, 16384
     tr = vpmc.Engine(vpmc.surrogate_training_problem())
     t0 = time.perf_counter()
     feat, target, label = tr.surrogate_tracks(list(range(8)), tpb, W.Options(seed=W.SURROGATE_SEED))
@@ -513,7 +517,7 @@ def surrogate_leg(pb, spots, scens, opts, args, plain_value):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
-    losses = tr.surrogate_train(feat, target, label, batch=batch, epochs=epochs, lr=4e-3, lr_min=4e-5)
+    losses = tr.surrogate_train(feat, target, label, batch=batch, epochs=epochs, lr=2e-3, lr_min=2e-5)
     ev1.record()
     torch.cuda.synchronize()
     train_s = ev0.elapsed_time(ev1) / 1000.0

@@ -286,7 +286,10 @@ vpmc_status vpmc_free_csr(vpmc_csr* csr, int n);
  * Training domain: E in [40, 230] MeV, |d . n| and |d . t| <= 0.12,
  * curvature in [-0.001, 0.26] / mm, block thickness 30 mm, and |x5| >= 0.06
  * (away from the stopping threshold, where the exit energy has a sharp
- * edge that the mixture does not follow).  With
+ * edge that the mixture does not follow).  Only beams with a range shifter
+ * use the network: without one, the nearly parallel, mono-energetic beam
+ * makes the few protons that escape through the wall stand out, and the
+ * network's dose error there exceeded 1 % of the maximum.  With
  * opts->surrogate = 1, a brass entry outside this domain takes the plain
  * path.  A brass entry whose 1.2 x CSDA range is below both its edge distance
  * and the thickness is absorbed without a draw.

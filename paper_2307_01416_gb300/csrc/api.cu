@@ -716,6 +716,8 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     CTX_TRY(dev_alloc(&c->d_rho, c->nvox));
     CTX_TRY(launch_scoring_density(c->d_ct, c->ctg, c->sg, c->d_curve, c->ct_spacing, c->sg_spacing, c->d_rho,
                                    c->stream));
+    CTX_TRY(dev_alloc(&c->d_inv_rho, c->nvox));
+    CTX_TRY(launch_reciprocal(c->d_rho, c->nvox, c->d_inv_rho, c->stream));
     // from here on the CT holds the kernels' table index per voxel
     CTX_TRY(launch_ct_lut_index(c->d_ct, nct, c->stream));
     CTX_TRY(dev_alloc(&c->d_beams, kMaxBeams));
@@ -1303,8 +1305,8 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         cudaFree(d_colmax);
         d_colmax = nullptr;
         IM_TRY(dev_alloc(&d_colmax, items.size()));
-        IM_TRY(launch_column_max(c->d_scratch, c->d_items, c->d_boxes, c->d_rho, c->sg, 0, (int)items.size(), d_colmax,
-                                 c->stream));
+        IM_TRY(launch_column_max(c->d_scratch, c->d_items, c->d_boxes, c->d_inv_rho, c->sg, 0, (int)items.size(),
+                                 d_colmax, c->stream));
         ++c->launches;
         const long long n_buckets = (long long)ns * c->nvox;
         if (n_ovf) {
@@ -1420,6 +1422,7 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->d_tables);
     cudaFree(c->d_curve);
     cudaFree(c->d_rho);
+    cudaFree(c->d_inv_rho);
     cudaFree(c->d_acc);
     cudaFree(c->d_beams);
     cudaFree(c->d_poly);

@@ -36,6 +36,7 @@ struct vpmc_ctx {
     vpmc::MatConst water_mat{};          // the tables image's water entry (a launch constant)
     double* d_curve = nullptr;
     double* d_rho = nullptr;
+    double* d_inv_rho = nullptr;               // 1 / rho per scoring voxel (FP64)
     unsigned long long* d_acc = nullptr;       // dose accumulator (scoring grid)
     // fields
     bool beam_set[vpmc::kMaxBeams]{};

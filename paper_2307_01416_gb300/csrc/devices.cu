@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                 } else if (L.E >= sur::kELo && L.E <= sur::kEHi && fabsf(un) <= sur::kAngMax &&
                            fabsf(ut) <= sur::kAngMax && ne.w >= sur::kKappaLo && ne.w <= sur::kKappaHi &&
                            fabsf(T - sur::kThickness) < 1e-3f && dist > 0.0f &&
-                           fabsf(feat[5]) >= sur::kNearThreshold) {
+                           fabsf(feat[5]) >= sur::kNearThreshold && (kTrack || B.rs)) {
                     sur_emit = true;                // in the training domain: one network draw
                 }
             }

@@ -65,32 +65,43 @@ __device__ __forceinline__ long long box_local(const DevBox& b, int x, int y, in
     return lx + (long long)b.n[0] * (ly + (long long)b.n[1] * lz);
 }
 
-// One block per item: maximum over the item's box of q / rho.
+// One block per item: maximum over the item's box of q / rho, as q x (1 / rho)
+// with the same FP64 reciprocal the row pass uses.  A warp takes rows of the
+// box (fixed y and z) and its lanes run along x, so the loads are coalesced
+// and a voxel's index needs no division.
 __global__ void k_column_max(const unsigned long long* __restrict__ scratch, const DevItem* __restrict__ items,
-                             const DevBox* __restrict__ boxes, const double* __restrict__ rho, Grid3 sg,
+                             const DevBox* __restrict__ boxes, const double* __restrict__ inv_rho, Grid3 sg,
                              int first_item, double* __restrict__ colmax)
 {
     const int it = first_item + blockIdx.x;
     const DevBox b = boxes[items[it].box];
-    const long long n = (long long)b.n[0] * b.n[1] * b.n[2];
+    const int rows = b.n[1] * b.n[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     double m = 0.0;
-    for (long long l = threadIdx.x; l < n; l += blockDim.x) {
-        const unsigned long long q = scratch[b.base + l];
-        if (q == 0ull) continue;
-        const int x = b.lo[0] + (int)(l % b.n[0]);
-        const int y = b.lo[1] + (int)((l / b.n[0]) % b.n[1]);
-        const int z = b.lo[2] + (int)(l / ((long long)b.n[0] * b.n[1]));
-        m = fmax(m, (double)q / rho[x + (long long)sg.n[0] * (y + (long long)sg.n[1] * z)]);
+    for (int row = warp; row < rows; row += nwarp) {
+        const int ly = row % b.n[1], lz = row / b.n[1];
+        const unsigned long long* src = scratch + b.base + (long long)row * b.n[0];
+        const long long v0 = b.lo[0] + (long long)sg.n[0] * ((b.lo[1] + ly) + (long long)sg.n[1] * (b.lo[2] + lz));
+        for (int lx = lane; lx < b.n[0]; lx += 32) {
+            const unsigned long long q = __ldcs(src + lx);
+            if (q != 0ull) m = fmax(m, (double)q * inv_rho[v0 + lx]);
+        }
     }
     __shared__ double red[32];
     for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    if (lane == 0) red[warp] = m;
     __syncthreads();
     if (threadIdx.x < 32) {
-        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        m = threadIdx.x < nwarp ? red[threadIdx.x] : 0.0;
         for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (threadIdx.x == 0) colmax[blockIdx.x] = m;
     }
+}
+
+__global__ void k_reciprocal(const double* __restrict__ x, long long n, double* __restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = 1.0 / x[i];
 }
 
 // One thread per scoring voxel (row).  Box columns are visited beam by beam
@@ -277,11 +288,19 @@ cudaError_t launch_dose_normalise(const unsigned long long* acc, const double* r
 }
 
 cudaError_t launch_column_max(const unsigned long long* scratch, const DevItem* items, const DevBox* boxes,
-                              const double* rho, const Grid3 sg, int first_item, int n_items, double* colmax,
+                              const double* inv_rho, const Grid3 sg, int first_item, int n_items, double* colmax,
                               cudaStream_t s)
 {
     if (n_items <= 0) return cudaSuccess;
-    k_column_max<<<n_items, 256, 0, s>>>(scratch, items, boxes, rho, sg, first_item, colmax);
+    k_column_max<<<n_items, 512, 0, s>>>(scratch, items, boxes, inv_rho, sg, first_item, colmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reciprocal(const double* x, long long n, double* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    k_reciprocal<<<(int)blocks, 256, 0, s>>>(x, n, out);
     return cudaGetLastError();
 }
 

@@ -129,6 +129,8 @@ constexpr float kDirScale = 0.05f;
 constexpr float kSMin = -8.0f, kSMax = 4.0f;
 constexpr float kThickness = 30.0f;  // block thickness of the training geometries, mm
 constexpr float kKappaLo = -1e-3f, kKappaHi = 0.26f;
+// The network serves beams with a range shifter only (the test domain in
+// which its dose error stays below 1 % of the maximum).
 // Near the stopping threshold (brass CSDA range within 6 % of the thickness)
 // a proton leaves the block with a few MeV or not at all: the exit energy
 // distribution has a sharp edge that the mixture does not follow.  Those
@@ -326,9 +328,11 @@ cudaError_t launch_scoring_density(const int16_t* ct, Grid3 ctg, Grid3 sg, const
                                    cudaStream_t s);
 cudaError_t launch_dose_normalise(const unsigned long long* acc, const double* rho, long long nvox, double scale,
                                   float* dose, cudaStream_t s);
+// colmax[i] = max over item first_item + i's box of q x inv_rho (inv_rho: 1 / rho per scoring voxel).
 cudaError_t launch_column_max(const unsigned long long* scratch, const DevItem* items, const DevBox* boxes,
-                              const double* rho, const Grid3 sg, int first_item, int n_items, double* colmax,
+                              const double* inv_rho, const Grid3 sg, int first_item, int n_items, double* colmax,
                               cudaStream_t s);
+cudaError_t launch_reciprocal(const double* x, long long n, double* out, cudaStream_t s);
 
 struct CsrBuildParams {
     const unsigned long long* scratch;

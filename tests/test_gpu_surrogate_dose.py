@@ -24,7 +24,7 @@ def weights():
         pytest.skip("no CUDA device")
     torch.cuda.set_device(0)
     from paper_2307_01416_gb300 import vpmc
-    w, losses = vpmc.train_surrogate(tracks_per_beam=12_500_000, epochs=10, batch=65536, lr=4e-3, lr_min=4e-5)
+    w, losses = vpmc.train_surrogate(tracks_per_beam=12_500_000, epochs=7, batch=16384, lr=2e-3, lr_min=2e-5)
     assert np.all(np.isfinite(losses)) and losses[-1] < losses[0]
     return w
 
@@ -71,9 +71,26 @@ def test_head_plan_dose_error_all_scenarios(weights):
         assert gam >= 99.5, out
 
 
-@pytest.mark.parametrize("opening,rs", [(10.0, True), (40.0, True), (20.0, False), (10.0, False)])
-def test_water_aperture_dose_error(weights, opening, rs):
-    pb, spots = W.water_aperture_case(opening, rs, hist_per_layer=300_000)
+@pytest.mark.parametrize("opening", [10.0, 20.0])
+def test_beams_without_range_shifter_keep_the_plain_path(weights, opening):
+    """Without a range shifter the network's dose error reached 1.1-2.2 % of
+    the maximum (10 and 20 mm openings, different trainings): such beams
+    take the plain aperture transport with opts.surrogate = 1, so the dose
+    is the plain one, bit for bit."""
+    from paper_2307_01416_gb300 import vpmc
+    pb, spots = W.water_aperture_case(opening, False, hist_per_layer=20_000, max_layers=4)
+    e = vpmc.Engine(pb)
+    e.surrogate_set_weights(weights)
+    d0, s0, _ = e.run_spots(spots, W.Scenario(), W.Options(seed=77))
+    d1, s1, _ = e.run_spots(spots, W.Scenario(), W.Options(seed=77, surrogate=True))
+    e.close()
+    assert np.array_equal(d0.cpu().numpy(), d1.cpu().numpy())
+    assert s0["steps"] == s1["steps"] and s0["e_aperture"] == s1["e_aperture"]
+
+
+@pytest.mark.parametrize("opening", [10.0, 20.0, 40.0])
+def test_water_aperture_dose_error(weights, opening):
+    pb, spots = W.water_aperture_case(opening, True, hist_per_layer=300_000)
     r = _paired(pb, spots, weights)
     assert r["max_err"] <= 0.01, r
     assert abs(r["mean_err"]) <= 0.005, r
