@@ -75,8 +75,8 @@ def test_head_plan_dose_error_all_scenarios(weights):
 def test_beams_without_range_shifter_keep_the_plain_path(weights, opening):
     """Without a range shifter the network's dose error reached 1.1-2.2 % of
     the maximum (10 and 20 mm openings, different trainings): such beams
-    take the plain aperture transport with opts.surrogate = 1, so the dose
-    is the plain one, bit for bit."""
+    take the plain aperture transport with opts.surrogate = 1, so the
+    patient dose is the plain one, bit for bit."""
     from paper_2307_01416_gb300 import vpmc
     pb, spots = W.water_aperture_case(opening, False, hist_per_layer=20_000, max_layers=4)
     e = vpmc.Engine(pb)
@@ -85,7 +85,10 @@ def test_beams_without_range_shifter_keep_the_plain_path(weights, opening):
     d1, s1, _ = e.run_spots(spots, W.Scenario(), W.Options(seed=77, surrogate=True))
     e.close()
     assert np.array_equal(d0.cpu().numpy(), d1.cpu().numpy())
-    assert s0["steps"] == s1["steps"] and s0["e_aperture"] == s1["e_aperture"]
+    assert s0["e_dep"] == s1["e_dep"] and s0["e_leak"] == s1["e_leak"]
+    # brass entries that can reach neither the opening nor the exit face are
+    # absorbed at once on the surrogate path: the same energy, fewer steps
+    assert abs(s1["e_aperture"] / s0["e_aperture"] - 1.0) < 1e-6
 
 
 @pytest.mark.parametrize("opening", [10.0, 20.0, 40.0])
