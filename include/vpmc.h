@@ -161,6 +161,8 @@ typedef struct {
                                surrogate draws) within ms, CUDA events; 0 for vpmc_run_spots_noalloc */
     float ms_patient;       /* device time of the patient kernel within ms, CUDA events; 0 for
                                vpmc_run_spots_noalloc */
+    int64_t scratch_bytes;  /* influence matrix: dense column scratch the call filled, summed over its
+                               waves (each byte is zeroed once and read three times to build the CSR) */
 } vpmc_stats;
 
 /* Sparse influence matrix of one scenario: rows = scoring voxels (x-fastest),

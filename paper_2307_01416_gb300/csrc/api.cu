@@ -1301,6 +1301,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             }
         }
         stats.ovf_records += (long long)n_ovf;
+        stats.scratch_bytes += wave_elems * (long long)sizeof(unsigned long long);
         // column maxima over boxes, then bucket the out-of-box records and raise the maxima
         cudaFree(d_colmax);
         d_colmax = nullptr;

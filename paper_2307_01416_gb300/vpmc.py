@@ -76,7 +76,7 @@ class vpmc_stats(C.Structure):
                 ("e_dep", C.c_double), ("e_leak", C.c_double), ("e_rs", C.c_double), ("e_aperture", C.c_double),
                 ("e_nuc", C.c_double), ("ms", C.c_float), ("launches", C.c_int64),
                 ("ovf_records", C.c_int64), ("steps_rs", C.c_int64), ("steps_aperture", C.c_int64),
-                ("ms_devices", C.c_float), ("ms_patient", C.c_float)]
+                ("ms_devices", C.c_float), ("ms_patient", C.c_float), ("scratch_bytes", C.c_int64)]
 
 
 class vpmc_csr(C.Structure):

@@ -81,10 +81,19 @@ def test_water_pencil_beam_per_history(torch_cuda):
     pb, spots = W.pencil_beam_water(n_hist=20000)
     dose, st, rec, q_o, orec = _per_history_parity(pb, spots, W.Scenario(), DET)
     assert (rec["fate"] == O.FATE_NUC).sum() > 100
-    # per-voxel deposits of the deterministic run agree too
+    # the deterministic dose grid, voxel by voxel: 99.9 % of the voxels within
+    # 1e-4 of the maximum dose and all within 2e-3 (a track that runs almost
+    # parallel to a voxel face crosses it at a point that moves by position
+    # rounding / cosine, which shifts a deposit to the neighbour), and the
+    # total to 1e-5
     d_o = O.dose_from_q(pb, q_o, DET.frac_bits).reshape(dose.shape)
     d_g = dose.cpu().numpy().astype(np.float64)
     assert np.abs(d_g.sum() / d_o.sum() - 1.0) < 1e-5
+    dev = np.abs(d_g - d_o) / d_o.max()
+    touched = (d_g > 0) | (d_o > 0)
+    assert touched.sum() > 1000
+    assert np.quantile(dev[touched], 0.999) < 1e-4 and dev.max() < 2e-3, (np.quantile(dev[touched], 0.999),
+                                                                             dev.max())
 
 
 @pytest.mark.parametrize("rs", [False, True])
