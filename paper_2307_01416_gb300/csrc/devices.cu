@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
                 else if (L.d[2] < 0.0f) { s_geom = __fdividef(B.rs_tup - L.p[2], L.d[2]); down = false; }
                 s_geom = fmaxf(s_geom, 0.0f);       // scattering offsets can leave it past the plane
                 StepResult o;
-                ch_step(pmma, s_geom, L, P, key, o);
+                ch_step<false>(pmma, s_geom, L, P, key, o);
                 acc_steps += 1;
                 const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
                 acc_rs += qs;
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             }
             if (do_ch) {
                 StepResult o;
-                ch_step(m, s_geom, L, P, key, o);
+                ch_step<false>(m, s_geom, L, P, key, o);
                 acc_steps += 1;
                 const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
                 acc_ap += qs;

@@ -14,7 +14,11 @@
 // second face distance and the scoring index is the CT index shifted right
 // by sh.  The kernel is compiled for three nestings (kNest bit k: axis k
 // nested): none, x and y (the 2 mm scoring grid over a 1 x 1 x 1.5 mm CT),
-// and all three (one grid).  The results do not depend on the variant.
+// and all three (one grid).  Each is compiled for three modes: the launch's
+// switches read at run time; full physics known at compile time; and full
+// physics with influence-matrix scoring (unit item weights, 32-bit
+// fixed-point conversion, plain atomics) known at compile time.  The results
+// do not depend on the variant.
 #include "transport_common.cuh"
 
 namespace vpmc {
@@ -23,9 +27,13 @@ namespace {
 using namespace dev;
 using namespace tr;
 
-template <int kNest>
+constexpr int kModeAllPhysics = 1;   // scattering, straggling and nuclear removal on
+constexpr int kModeIMScoring = 2;    // unit item weights, fx32, plain atomics
+
+template <int kNest, int kMode>
 __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const TransportParams P)
 {
+    constexpr bool kIM = (kMode & kModeIMScoring) != 0;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -112,7 +120,8 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                         for (int k = 0; k < 3; ++k) {
                             const float lo = P.ctg.lo[k], hi = P.ctg.lo[k] + P.ctg.n[k] * P.ctg.d[k];
                             if (r.d[k] != 0.0f) {
-                                float t1 = (lo - r.p[k]) / r.d[k], t2 = (hi - r.p[k]) / r.d[k];
+                                const float inv = __fdividef(1.0f, r.d[k]);
+                                float t1 = (lo - r.p[k]) * inv, t2 = (hi - r.p[k]) * inv;
                                 if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
                                 tmin = fmaxf(tmin, t1);
                                 tmax = fminf(tmax, t2);
@@ -131,10 +140,10 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
 #pragma unroll
                             for (int k = 0; k < 3; ++k) {
                                 L.p[k] = fmaf(tin, L.d[k], L.p[k]);
-                                const int a = (int)floorf((L.p[k] - P.ctg.lo[k]) / P.ctg.d[k]);
+                                const int a = (int)floorf(__fdividef(L.p[k] - P.ctg.lo[k], P.ctg.d[k]));
                                 L.ic[k] = min(max(a, 0), P.ctg.n[k] - 1);
                                 if (!((kNest >> k) & 1)) {
-                                    const int b = (int)floorf((L.p[k] - P.sg.lo[k]) / P.sg.d[k]);
+                                    const int b = (int)floorf(__fdividef(L.p[k] - P.sg.lo[k], P.sg.d[k]));
                                     L.is[k] = min(max(b, 0), P.sg.n[k] - 1);
                                 }
                             }
@@ -199,10 +208,10 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                 int sv[3];                  // scoring voxel where the step starts
 #pragma unroll
                 for (int k = 0; k < 3; ++k) sv[k] = ((kNest >> k) & 1) ? (L.ic[k] >> P.nest_shift[k]) : L.is[k];
-                ch_step(water, s_geom, L, P, make_uint2(P.key0, key1), o);
-                const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
+                ch_step<(kMode & kModeAllPhysics) != 0>(water, s_geom, L, P, make_uint2(P.key0, key1), o);
+                const unsigned long long qs = to_fixed(o.dE, P.fscale, kIM || P.fx32);
                 unsigned long long q = qs;
-                if (!P.unit_weight && wsc != P.fscale) q = to_fixed(o.dE, wsc, false);
+                if (!kIM && !P.unit_weight && wsc != P.fscale) q = to_fixed(o.dE, wsc, false);
                 // score into the scoring voxel where the step started
                 const int lx = sv[0] - bx.lo[0], ly = sv[1] - bx.lo[1], lz = sv[2] - bx.lo[2];
                 if ((unsigned)lx < (unsigned)bx.n[0] && (unsigned)ly < (unsigned)bx.n[1] &&
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
             }
         }
         // ---- scoring (all lanes together) ----
-        if (P.aggregate) deposit_aggregated(P.scratch, dep_key, dep_q);
+        if (!kIM && P.aggregate) deposit_aggregated(P.scratch, dep_key, dep_q);
         else if (dep_key >= 0 && dep_q) atomicAdd(P.scratch + dep_key, dep_q);
     }
 }
@@ -291,18 +300,27 @@ __global__ void k_ct_lut_index(int16_t* ct, long long n)
     }
 }
 
-template <int kNest>
-cudaError_t launch_patient_nest(const TransportParams& p, int grid, int block, cudaStream_t s)
+template <int kNest, int kMode>
+cudaError_t launch_patient_variant(const TransportParams& p, int grid, int block, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_patient<kNest>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_patient<kNest, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)PatientSmem::Bytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_patient<kNest><<<grid, block, PatientSmem::Bytes, s>>>(p);
+    k_patient<kNest, kMode><<<grid, block, PatientSmem::Bytes, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int kNest>
+cudaError_t launch_patient_nest(const TransportParams& p, int grid, int block, cudaStream_t s)
+{
+    if (!(p.mcs && p.straggling && p.nuclear)) return launch_patient_variant<kNest, 0>(p, grid, block, s);
+    if (p.unit_weight && p.fx32 && !p.aggregate)
+        return launch_patient_variant<kNest, kModeAllPhysics | kModeIMScoring>(p, grid, block, s);
+    return launch_patient_variant<kNest, kModeAllPhysics>(p, grid, block, s);
 }
 
 }  // namespace

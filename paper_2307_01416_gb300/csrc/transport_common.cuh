@@ -154,21 +154,27 @@ struct PatientLane {
     unsigned long long hdep;    // fixed-point energy the history deposited in the patient
 };
 
-template <class LaneT>
+// kAllPhysics: scattering, straggling and nuclear removal all on, known at
+// compile time, so that the step carries none of their switches; otherwise
+// the launch's switches decide.
+template <bool kAllPhysics, class LaneT>
 __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L, const TransportParams& P, uint2 key,
                                         StepResult& o)
 {
+    const bool mcs = kAllPhysics || P.mcs, straggling = kAllPhysics || P.straggling,
+               nuclear = kAllPhysics || P.nuclear;
     const float E = L.E;
     const float R0 = L.R;
     const float inv_kappa = __fdividef(1.0f, m.kappa);
     float s1 = (R0 - range_of(m.Rt, 0.99f * E)) * inv_kappa;
     if (!(s1 > 0.0f)) s1 = R0 * inv_kappa;
-    const float mu = P.nuclear ? 0.0012f * m.rho : 0.0f;
+    const float mu = nuclear ? 0.0012f * m.rho : 0.0f;
     float s = 1.0f;
     int lim = 0;
     if (s1 < s) s = s1;
     if (s_geom < s) { s = s_geom; lim = 1; }
-    if (mu > 0.0f) {
+    // (with mu = 0 the quotient is +inf or NaN and never limits the step)
+    if (kAllPhysics || mu > 0.0f) {
         const float sn = __fdividef(L.nlam, mu);
         if (sn < s) { s = sn; lim = 2; }
     }
@@ -179,7 +185,7 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
     // six 21-bit uniforms -- the top 21 bits of each word (scattering) and the
     // low bits of words 0|1 and 2|3 (straggling)
     uint4 r = make_uint4(L.hist, L.step, 1u, 0u);
-    if (P.mcs || P.straggling) r = philox(r, key);
+    if (mcs || straggling) r = philox(r, key);
 
     const float R1 = R0 - s * m.kappa;
     const float Emean = R1 > 0.0f ? energy_of(m.Et, m.inv_dR, R1) : kEcut;
@@ -187,7 +193,7 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
     const float pc2 = E * (E + 2.0f * kMp);               // (pc)^2
     const float etot = E + kMp;
     const float inv_etot = __fdividef(1.0f, etot);
-    if (P.straggling) {
+    if (straggling) {
         // (1 - beta^2 / 2) / (1 - beta^2) = gamma^2 - (beta gamma)^2 / 2 = (Etot^2 - (pc)^2 / 2) / Mp^2
         const float2 z = box_muller_fast(u21(((r.x & 0x7FFu) << 10) | (r.y & 0x3FFu)),
                                          u21(((r.z & 0x7FFu) << 10) | (r.w & 0x3FFu)));
@@ -198,7 +204,7 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
     dE = fminf(fmaxf(dE, 0.0f), E);
     const float Enew = E - dE;
     float Rnew = R1;
-    if (P.straggling) {
+    if (straggling) {
         Rnew = R1 + (range_of(m.Rt, Enew) - range_of(m.Rt, Emean));
         if (!(Rnew > 0.0f)) Rnew = range_of(m.Rt, Enew);
     }
@@ -214,7 +220,7 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
 #pragma unroll
     for (int k = 0; k < 3; ++k) L.p[k] = fmaf(s, L.d[k], L.p[k]);
 
-    if (P.mcs && !o.killed) {
+    if (mcs && !o.killed) {
         const float x = s * m.rho * m.inv_x0;
         float th0 = 0.0f;
         if (x >= 1e-6f)         // 1 + 0.038 ln x = 1 + (0.038 ln 2) log2 x
