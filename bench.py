@@ -334,7 +334,7 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        kern_ms, steps, hist, nnz, ops, ms_patient, patient_steps, scratch_b = 0.0, 0, 0, 0, 0.0, 0.0, 0, 0
+        kern_ms, steps, hist, nnz, ops, ms_patient, patient_steps, scratch_b, ovf = 0.0, 0, 0, 0, 0.0, 0.0, 0, 0, 0
         for _ in range(args.steps):
             flush.fill_(1.0)                       # evict L2 between sets
             mats, st = eng.influence_matrix(spots, scens, opts)
@@ -344,6 +344,7 @@ def main():
             ms_patient += st["ms_patient"]
             patient_steps += st["steps"] - st["steps_rs"] - st["steps_aperture"]
             scratch_b += st["scratch_bytes"]
+            ovf += st["ovf_records"]
             hist += st["histories"]
             launches += st["launches"] + 1
             nnz = sum(int(m["val"].numel()) for m in mats)
@@ -378,11 +379,13 @@ def main():
         fin_ms = ms_per_step - kern_ms / args.steps
         fin_b = 4 * scratch_b / args.steps + csr_b
         finalise = {"ms_per_set": fin_ms, "bytes_per_set": fin_b, "nnz_per_set": nnz,
+                    "scratch_bytes_per_set": scratch_b / args.steps, "out_of_box_records_per_set": ovf / args.steps,
                     "algorithmic_bytes_per_set": 16.0 * nnz,
                     "gbs": fin_b / (fin_ms * 1e-3) / 1e9 if fin_ms > 0 else None,
                     "note": "set time minus the transport kernels' CUDA-event time; scratch = dense per-(scenario, "
-                            "spot) column boxes, zeroed, scanned for column maxima, then read by the count and fill "
-                            "passes of the CSR"}
+                            "spot) column boxes cut at each energy layer's reach along its field, zeroed, scanned for "
+                            "column maxima, then read by the count and fill passes of the CSR; deposits beyond a box "
+                            "are out-of-box records, merged into the CSR"}
         adds_rate = patient_steps / (ms_patient / 1000.0) if ms_patient > 0 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": traffic, "kernel": "k_source_rs+k_aperture+k_patient",

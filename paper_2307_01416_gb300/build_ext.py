@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["devices.cu", "patient.cu", "surrogate.cu", "optimize.cu", "finalize.cu", "api.cu", "noalloc.cu", "measure.cu", "tables.cpp"]
+SOURCES = ["devices.cu", "patient.cu", "surrogate.cu", "optimize.cu", "finalize.cu", "im_plan.cu", "api.cu", "noalloc.cu", "measure.cu", "tables.cpp"]
 
 
 def _nvcc() -> str:

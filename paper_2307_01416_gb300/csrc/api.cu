@@ -709,6 +709,7 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     TablesImage* img = reinterpret_cast<TablesImage*>(img_bytes.data());
     build_tables(c->curve15, img);
     c->water_mat = img->mat[kWater];
+    c->range_water.assign(img->R[kWater], img->R[kWater] + kNEPad);
     CTX_TRY(dev_alloc(&c->d_tables, 1));
     CTX_TRY(cudaMemcpyAsync(c->d_tables, img, sizeof(TablesImage), cudaMemcpyHostToDevice, c->stream));
     CTX_TRY(dev_alloc(&c->d_curve, 15));
@@ -977,55 +978,75 @@ namespace {
 
 struct BoxSpec { int lo[3], n[3]; };
 
-// Axis-aligned box (scoring voxels) that holds the field of beam b in
-// scenario sc: the aperture opening (or the spots' extent) plus a lateral
-// margin, over the grid's whole depth along the beam.
-BoxSpec field_box(vpmc_ctx* c, int b, const vpmc_scenario& sc, const vpmc_spot* spots, int n_spots, double margin)
+// Beam b's field in scenario sc, in the beam frame (origin base = isocentre +
+// shift, axes u, v across and w along the beam): the lateral extent of the
+// aperture opening (or of the spots, 4 sigma) and the depth range [t0, t1] of
+// the scoring grid along w.
+struct FieldFrame {
+    double a0, a1, b0, b1;
+    double base[3];
+    double t0, t1;
+};
+
+FieldFrame field_frame(vpmc_ctx* c, int b, const vpmc_scenario& sc, const vpmc_spot* spots, int n_spots)
 {
     const DevBeam& B = c->beams[b];
-    double a0 = 1e300, a1 = -1e300, b0 = 1e300, b1 = -1e300;
+    FieldFrame f;
+    f.a0 = f.b0 = 1e300;
+    f.a1 = f.b1 = -1e300;
     if (B.ap) {
         const std::vector<double>& p = c->poly[b];
         for (size_t i = 0; i + 1 < p.size(); i += 2) {
-            a0 = std::min(a0, p[i]); a1 = std::max(a1, p[i]);
-            b0 = std::min(b0, p[i + 1]); b1 = std::max(b1, p[i + 1]);
+            f.a0 = std::min(f.a0, p[i]); f.a1 = std::max(f.a1, p[i]);
+            f.b0 = std::min(f.b0, p[i + 1]); f.b1 = std::max(f.b1, p[i + 1]);
         }
     } else {
         for (int i = 0; i < n_spots; ++i)
             if (spots[i].beam == b) {
                 const double r = 4.0 * spots[i].sigma_mm;
-                a0 = std::min(a0, spots[i].x_mm - r); a1 = std::max(a1, spots[i].x_mm + r);
-                b0 = std::min(b0, spots[i].y_mm - r); b1 = std::max(b1, spots[i].y_mm + r);
+                f.a0 = std::min(f.a0, spots[i].x_mm - r); f.a1 = std::max(f.a1, spots[i].x_mm + r);
+                f.b0 = std::min(f.b0, spots[i].y_mm - r); f.b1 = std::max(f.b1, spots[i].y_mm + r);
             }
     }
-    a0 -= margin; a1 += margin; b0 -= margin; b1 += margin;
-    double lo[3], hi[3], base[3];
+    double lo[3], hi[3];
     for (int k = 0; k < 3; ++k) {
         lo[k] = c->sg.lo[k];
         hi[k] = c->sg.lo[k] + c->sg.n[k] * c->sg_spacing[k];
-        base[k] = (double)B.iso[k] + sc.shift_mm[k];
+        f.base[k] = (double)B.iso[k] + sc.shift_mm[k];
     }
     // depth range: projections of the grid corners on the beam axis
-    double t0 = 1e300, t1 = -1e300;
+    f.t0 = 1e300;
+    f.t1 = -1e300;
     for (int m = 0; m < 8; ++m) {
         double t = 0.0;
-        for (int k = 0; k < 3; ++k) t += (((m >> k) & 1 ? hi[k] : lo[k]) - base[k]) * (double)B.w[k];
-        t0 = std::min(t0, t);
-        t1 = std::max(t1, t);
+        for (int k = 0; k < 3; ++k) t += (((m >> k) & 1 ? hi[k] : lo[k]) - f.base[k]) * (double)B.w[k];
+        f.t0 = std::min(f.t0, t);
+        f.t1 = std::max(f.t1, t);
     }
+    return f;
+}
+
+// Axis-aligned box (scoring voxels) that holds the field's lateral extent plus
+// a margin over the depths [t0, min(t1, t_cap)].
+BoxSpec frame_box(vpmc_ctx* c, int b, const FieldFrame& f, double margin, double t_cap)
+{
+    const DevBeam& B = c->beams[b];
+    const double a0 = f.a0 - margin, a1 = f.a1 + margin, b0 = f.b0 - margin, b1 = f.b1 + margin;
+    const double t_hi = std::max(std::min(f.t1, t_cap), f.t0);
     double plo[3] = {1e300, 1e300, 1e300}, phi[3] = {-1e300, -1e300, -1e300};
     for (int m = 0; m < 8; ++m) {
-        const double a = m & 1 ? a1 : a0, bb = m & 2 ? b1 : b0, t = m & 4 ? t1 : t0;
+        const double a = m & 1 ? a1 : a0, bb = m & 2 ? b1 : b0, t = m & 4 ? t_hi : f.t0;
         for (int k = 0; k < 3; ++k) {
-            const double x = base[k] + a * B.u[k] + bb * B.v[k] + t * B.w[k];
+            const double x = f.base[k] + a * B.u[k] + bb * B.v[k] + t * B.w[k];
             plo[k] = std::min(plo[k], x);
             phi[k] = std::max(phi[k], x);
         }
     }
     BoxSpec s;
     for (int k = 0; k < 3; ++k) {
-        int i0 = (int)std::floor((plo[k] - lo[k]) / c->sg_spacing[k]);
-        int i1 = (int)std::ceil((phi[k] - lo[k]) / c->sg_spacing[k]);
+        const double lo = c->sg.lo[k];
+        int i0 = (int)std::floor((plo[k] - lo) / c->sg_spacing[k]);
+        int i1 = (int)std::ceil((phi[k] - lo) / c->sg_spacing[k]);
         i0 = std::max(i0, 0);
         i1 = std::min(i1, c->sg.n[k]);
         s.lo[k] = i0;
@@ -1033,6 +1054,25 @@ BoxSpec field_box(vpmc_ctx* c, int b, const vpmc_scenario& sc, const vpmc_spot* 
     }
     return s;
 }
+
+// Residual range in water (mm) at energy e, from the host copy of the table
+// the kernels interpolate.
+double water_range(const vpmc_ctx* c, double e)
+{
+    const double x = std::max(e, 0.0) * 10.0;
+    const int i = std::min((int)x, kNE - 1);
+    const float2 v = c->range_water[i];
+    return (double)v.x + (x - i) * (double)v.y;
+}
+
+// A run: consecutive spots of one beam whose column boxes share a shape (one
+// energy layer, or several merged).  r_lim: water-equivalent path (mm) beyond
+// which none of the run's protons deposits -- the water range behind the
+// range shifter, with 5 % + 3 mm for range straggling and table rounding.
+struct Run {
+    int first, count, beam;
+    double r_lim;
+};
 
 long long box_elems(const BoxSpec& s) { return (long long)s.n[0] * s.n[1] * s.n[2]; }
 
@@ -1082,16 +1122,117 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         for (int k = 0; k < 3; ++k) dscen[s].shift[k] = (float)scen[s].shift_mm[k];
         dscen[s].spr_scale = (float)scen[s].spr_scale;
     }
-    // one box per (scenario, beam): the field plus a lateral margin, full depth
-    std::vector<BoxSpec> spec((size_t)n_scen * nb);
+    // runs: consecutive spots of one beam and one energy, at most kMaxRuns per
+    // beam (adjacent runs merged beyond that)
+    constexpr int kMaxRuns = 64;
+    std::vector<Run> runs;
+    for (int b = 0; b < nb; ++b) {
+        if (!beam_count[b]) continue;
+        const DevBeam& B = c->beams[b];
+        const double rs_wet = B.rs ? (double)(B.rs_tdn - B.rs_tup) * pmma_stopping_power_ratio(150.0) : 0.0;
+        std::vector<Run> br;
+        for (int j = beam_first[b]; j < beam_first[b] + beam_count[b]; ++j) {
+            const double r = std::max(water_range(c, spots[j].energy_mev) - 0.97 * rs_wet, 0.0) * 1.05 + 3.0;
+            if (br.empty() || spots[j].energy_mev != spots[br.back().first].energy_mev)
+                br.push_back(Run{j, 0, b, 0.0});
+            br.back().count += 1;
+            br.back().r_lim = std::max(br.back().r_lim, r);
+        }
+        const int merge = ((int)br.size() + kMaxRuns - 1) / kMaxRuns;
+        for (size_t i = 0; i < br.size(); i += merge) {
+            Run m = br[i];
+            for (size_t k = i + 1; k < std::min(br.size(), i + merge); ++k) {
+                m.count += br[k].count;
+                m.r_lim = std::max(m.r_lim, br[k].r_lim);
+            }
+            runs.push_back(m);
+        }
+    }
+    const int nr = (int)runs.size();
+    // each run's reach along its field's axis in each scenario (one kernel
+    // marching rays through the CT), then its box: the field plus a lateral
+    // margin, from the grid's near end to the reach plus a margin
+    std::vector<FieldFrame> frames((size_t)n_scen * nb);
+    std::vector<float> reach((size_t)n_scen * nr, 0.0f);
+    {
+        std::vector<DepthJob> jobs;
+        std::vector<float> rl;
+        std::vector<int> slot((size_t)n_scen * nr);     // (scenario, run) -> entry of rl / reach
+        for (int s = 0; s < n_scen; ++s)
+            for (int b = 0; b < nb; ++b) {
+                if (!beam_count[b]) continue;
+                const FieldFrame f = field_frame(c, b, scen[s], spots, n_spots);
+                frames[(size_t)s * nb + b] = f;
+                const DevBeam& B = c->beams[b];
+                std::vector<int> mine;
+                for (int r = 0; r < nr; ++r)
+                    if (runs[r].beam == b) mine.push_back(r);
+                std::sort(mine.begin(), mine.end(), [&](int x, int y) { return runs[x].r_lim < runs[y].r_lim; });
+                DepthJob J{};
+                for (int k = 0; k < 3; ++k) {
+                    J.base[k] = (float)f.base[k];
+                    J.u[k] = B.u[k]; J.v[k] = B.v[k]; J.w[k] = B.w[k];
+                }
+                const double lat = 10.0, da = 2.0;
+                J.a0 = (float)(f.a0 - lat);
+                J.b0 = (float)(f.b0 - lat);
+                J.da = (float)da;
+                J.na = std::max(1, (int)std::ceil((f.a1 - f.a0 + 2 * lat) / da) + 1);
+                J.nb = std::max(1, (int)std::ceil((f.b1 - f.b0 + 2 * lat) / da) + 1);
+                J.t0 = (float)f.t0;
+                J.t1 = (float)f.t1;
+                J.dt = 0.5f;
+                J.spr_scale = (float)scen[s].spr_scale;
+                J.run_off = (int)rl.size();
+                J.run_n = (int)mine.size();
+                for (int r : mine) {
+                    slot[(size_t)s * nr + r] = (int)rl.size();
+                    rl.push_back((float)runs[r].r_lim);
+                }
+                jobs.push_back(J);
+            }
+        DepthJob* d_jobs = nullptr;
+        float* d_rl = nullptr;
+        unsigned* d_reach = nullptr;
+        std::vector<unsigned> h_reach(rl.size(), 0u);
+        cudaError_t e = dev_alloc(&d_jobs, jobs.size());
+        if (e == cudaSuccess) e = dev_alloc(&d_rl, rl.size());
+        if (e == cudaSuccess) e = dev_alloc(&d_reach, rl.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(DepthJob), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_rl, rl.data(), rl.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_reach, 0, rl.size() * sizeof(unsigned), c->stream);
+        if (e == cudaSuccess)
+            e = launch_depth_bounds(reinterpret_cast<const uint16_t*>(c->d_ct), c->d_tables, c->ctg, d_jobs,
+                                    (int)jobs.size(), d_rl, d_reach, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_reach.data(), d_reach, rl.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(d_jobs);
+        cudaFree(d_rl);
+        cudaFree(d_reach);
+        if (e != cudaSuccess)
+            return fail(e == cudaErrorMemoryAllocation ? VPMC_ERR_OOM : VPMC_ERR_CUDA, "column-box depths: %s",
+                        cudaGetErrorString(e));
+        ++c->launches;
+        for (size_t i = 0; i < slot.size(); ++i) {
+            unsigned bits = h_reach[slot[i]];
+            float v;
+            std::memcpy(&v, &bits, sizeof v);
+            reach[i] = v;
+        }
+    }
+    std::vector<BoxSpec> spec((size_t)n_scen * nr);
     std::vector<long long> scen_elems(n_scen, 0);
     long long per_scen_elems_max = 0;
     for (int s = 0; s < n_scen; ++s) {
-        for (int b = 0; b < nb; ++b)
-            if (beam_count[b]) {
-                spec[(size_t)s * nb + b] = field_box(c, b, scen[s], spots, n_spots, 25.0);
-                scen_elems[s] += box_elems(spec[(size_t)s * nb + b]) * beam_count[b];
-            }
+        for (int r = 0; r < nr; ++r) {
+            const FieldFrame& f = frames[(size_t)s * nb + runs[r].beam];
+            spec[(size_t)s * nr + r] = frame_box(c, runs[r].beam, f, 25.0, f.t0 + reach[(size_t)s * nr + r] + 5.0);
+            scen_elems[s] += box_elems(spec[(size_t)s * nr + r]) * runs[r].count;
+        }
         per_scen_elems_max = std::max(per_scen_elems_max, scen_elems[s]);
     }
     size_t free_b = 0, total_b = 0;
@@ -1111,6 +1252,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     double* d_colmax = nullptr;
     double* d_item_scale = nullptr;
     long long* d_rowcnt = nullptr;
+    long long* d_nnz = nullptr;
     long long* d_scan_tmp = nullptr;
     int* d_beam_meta = nullptr;
     long long* d_bucket_off = nullptr;
@@ -1119,7 +1261,8 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     OvfRec* d_ovf_sorted = nullptr;
     unsigned long long* d_ovf_count = nullptr;
     auto release = [&]() {
-        cudaFree(d_colmax); cudaFree(d_item_scale); cudaFree(d_rowcnt); cudaFree(d_scan_tmp); cudaFree(d_beam_meta);
+        cudaFree(d_colmax); cudaFree(d_item_scale); cudaFree(d_rowcnt); cudaFree(d_nnz); cudaFree(d_scan_tmp);
+        cudaFree(d_beam_meta);
         cudaFree(d_bucket_off); cudaFree(d_bucket_cur); cudaFree(d_bucket_len); cudaFree(d_ovf_sorted);
         cudaFree(d_ovf_count);
     };
@@ -1140,9 +1283,10 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     } while (0)
     IM_TRY(dev_alloc(&d_item_scale, n_spots));
     IM_TRY(cudaMemcpy(d_item_scale, item_scale.data(), n_spots * sizeof(double), cudaMemcpyHostToDevice));
-    IM_TRY(dev_alloc(&d_rowcnt, c->nvox + 1));
+    IM_TRY(dev_alloc(&d_rowcnt, (size_t)n_scen * (c->nvox + 1)));
+    IM_TRY(dev_alloc(&d_nnz, (size_t)n_scen));
     IM_TRY(dev_alloc(&d_scan_tmp, scan_tmp_elems((long long)n_scen * c->nvox + 1)));
-    IM_TRY(dev_alloc(&d_beam_meta, 3 * (size_t)nb));
+    IM_TRY(dev_alloc(&d_beam_meta, 3 * (size_t)nr * n_scen));
     IM_TRY(dev_alloc(&d_ovf_count, 1));
     IM_TRY(cudaMemcpy(c->d_scens, dscen.data(), n_scen * sizeof(DevScen), cudaMemcpyHostToDevice));
 
@@ -1172,19 +1316,18 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         // items (scenario-major, spot order) and their boxes
         std::vector<DevItem> items((size_t)ns * n_spots);
         std::vector<DevBox> boxes;
-        std::vector<int> beam_box((size_t)ns * nb, 0);
-        boxes.reserve(items.size() + (size_t)ns * nb);
+        std::vector<int> run_box((size_t)ns * nr, 0);
+        boxes.reserve(items.size() + (size_t)ns * nr);
         long long base = 0, total = 0;
         for (int s = s0; s < s1; ++s) {
-            for (int b = 0; b < nb; ++b) {
-                if (!beam_count[b]) continue;
-                const BoxSpec& sp = spec[(size_t)s * nb + b];
+            for (int r = 0; r < nr; ++r) {
+                const BoxSpec& sp = spec[(size_t)s * nr + r];
                 DevBox bx{};
                 for (int k = 0; k < 3; ++k) { bx.lo[k] = sp.lo[k]; bx.n[k] = sp.n[k]; }
                 bx.base = base;
-                beam_box[(size_t)(s - s0) * nb + b] = (int)boxes.size();
+                run_box[(size_t)(s - s0) * nr + r] = (int)boxes.size();
                 boxes.push_back(bx);
-                for (int j = beam_first[b]; j < beam_first[b] + beam_count[b]; ++j) {
+                for (int j = runs[r].first; j < runs[r].first + runs[r].count; ++j) {
                     const vpmc_spot& sp_j = spots[j];
                     DevItem it{};
                     it.hist_off = total;
@@ -1196,7 +1339,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
                     it.wscale = (float)fs;
                     it.spot = j;
                     it.scen = s;
-                    it.beam = b;
+                    it.beam = runs[r].beam;
                     DevBox ib = bx;
                     ib.base = base;
                     base += box_elems(sp);
@@ -1329,27 +1472,35 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
                                     c->stream));
             c->launches += 3 + scan_launches(n_buckets + 1);
         }
-        // CSR per scenario
+        // CSR per scenario: every scenario's count pass and row-pointer scan,
+        // one read of the entry counts, then the fill passes
+        std::vector<int> meta(3 * (size_t)nr * ns, 0);
+        for (int s = s0; s < s1; ++s) {
+            int* m = meta.data() + 3 * (size_t)nr * (s - s0);
+            for (int r = 0; r < nr; ++r) {
+                m[r] = runs[r].first;
+                m[nr + r] = runs[r].count;
+                m[2 * nr + r] = run_box[(size_t)(s - s0) * nr + r];
+            }
+        }
+        IM_TRY(cudaMemcpyAsync(d_beam_meta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               c->stream));
+        std::vector<CsrBuildParams> cps(ns);
         for (int s = s0; s < s1; ++s) {
             const int first = (s - s0) * n_spots;
-            std::vector<int> meta(3 * (size_t)nb, 0);
-            for (int b = 0; b < nb; ++b) {
-                meta[b] = beam_first[b];
-                meta[nb + b] = beam_count[b];
-                meta[2 * nb + b] = beam_box[(size_t)(s - s0) * nb + b];
-            }
-            IM_TRY(cudaMemcpyAsync(d_beam_meta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice,
-                                   c->stream));
-            CsrBuildParams cp{};
+            const int* m = d_beam_meta + 3 * (size_t)nr * (s - s0);
+            long long* rowcnt = d_rowcnt + (size_t)(s - s0) * (c->nvox + 1);
+            CsrBuildParams& cp = cps[s - s0];
+            cp = CsrBuildParams{};
             cp.scratch = c->d_scratch;
             cp.items = c->d_items + first;
             cp.boxes = c->d_boxes;
             cp.rho = c->d_rho;
             cp.colmax = d_colmax + first;
-            cp.beam_first = d_beam_meta;
-            cp.beam_count = d_beam_meta + nb;
-            cp.beam_box = d_beam_meta + 2 * nb;
-            cp.n_beams = nb;
+            cp.run_first = m;
+            cp.run_count = m + nr;
+            cp.run_box = m + 2 * nr;
+            cp.n_runs = nr;
             cp.ovf = n_ovf ? d_ovf_sorted : nullptr;
             cp.bucket_off = n_ovf ? d_bucket_off + (long long)(s - s0) * c->nvox : nullptr;
             cp.bucket_len = n_ovf ? d_bucket_len + (long long)(s - s0) * c->nvox : nullptr;
@@ -1358,23 +1509,29 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cp.nvox = c->nvox;
             cp.rel_threshold = rel_threshold;
             cp.item_scale = d_item_scale;
-            cp.row_count = d_rowcnt;
+            cp.row_count = rowcnt;
             IM_TRY(launch_csr_pass(cp, 0, c->stream));
             ++c->launches;
             vpmc_csr& csr = out[s];
             csr.n_rows = c->nvox;
             csr.n_cols = n_spots;
             IM_TRY(dev_alloc(&csr.row_ptr, c->nvox + 1));
-            IM_TRY(cudaMemsetAsync(d_rowcnt + c->nvox, 0, sizeof(long long), c->stream));
-            IM_TRY(launch_exclusive_scan(d_rowcnt, reinterpret_cast<long long*>(csr.row_ptr), c->nvox + 1, d_scan_tmp,
+            IM_TRY(cudaMemsetAsync(rowcnt + c->nvox, 0, sizeof(long long), c->stream));
+            IM_TRY(launch_exclusive_scan(rowcnt, reinterpret_cast<long long*>(csr.row_ptr), c->nvox + 1, d_scan_tmp,
                                          c->stream));
             c->launches += scan_launches(c->nvox + 1);
-            long long nnz = 0;
-            IM_TRY(cudaMemcpyAsync(&nnz, csr.row_ptr + c->nvox, sizeof nnz, cudaMemcpyDeviceToHost, c->stream));
-            IM_TRY(cudaStreamSynchronize(c->stream));
-            csr.nnz = nnz;
-            IM_TRY(dev_alloc(&csr.col, nnz));
-            IM_TRY(dev_alloc(&csr.val, nnz));
+            IM_TRY(cudaMemcpyAsync(d_nnz + (s - s0), csr.row_ptr + c->nvox, sizeof(long long),
+                                   cudaMemcpyDeviceToDevice, c->stream));
+        }
+        std::vector<long long> nnz(ns, 0);
+        IM_TRY(cudaMemcpyAsync(nnz.data(), d_nnz, ns * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+        IM_TRY(cudaStreamSynchronize(c->stream));
+        for (int s = s0; s < s1; ++s) {
+            vpmc_csr& csr = out[s];
+            CsrBuildParams& cp = cps[s - s0];
+            csr.nnz = nnz[s - s0];
+            IM_TRY(dev_alloc(&csr.col, csr.nnz));
+            IM_TRY(dev_alloc(&csr.val, csr.nnz));
             cp.row_ptr = reinterpret_cast<const long long*>(csr.row_ptr);
             cp.col = csr.col;
             cp.val = csr.val;

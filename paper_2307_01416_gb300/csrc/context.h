@@ -34,6 +34,7 @@ struct vpmc_ctx {
     int16_t* d_ct = nullptr;                  // CT: HU until the scoring densities are built, then table indices
     vpmc::TablesImage* d_tables = nullptr;
     vpmc::MatConst water_mat{};          // the tables image's water entry (a launch constant)
+    std::vector<float2> range_water;         // host copy of the water range table (column-box depths)
     double* d_curve = nullptr;
     double* d_rho = nullptr;
     double* d_inv_rho = nullptr;               // 1 / rho per scoring voxel (FP64)

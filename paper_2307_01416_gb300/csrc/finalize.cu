@@ -58,33 +58,38 @@ __global__ void k_dose_normalise(const unsigned long long* __restrict__ acc, con
         dose[v] = (float)((double)acc[v] * scale / rho[v]);
 }
 
-__device__ __forceinline__ long long box_local(const DevBox& b, int x, int y, int z)
-{
-    const int lx = x - b.lo[0], ly = y - b.lo[1], lz = z - b.lo[2];
-    if (lx < 0 || ly < 0 || lz < 0 || lx >= b.n[0] || ly >= b.n[1] || lz >= b.n[2]) return -1;
-    return lx + (long long)b.n[0] * (ly + (long long)b.n[1] * lz);
-}
-
 // One block per item: maximum over the item's box of q / rho, as q x (1 / rho)
-// with the same FP64 reciprocal the row pass uses.  A warp takes rows of the
-// box (fixed y and z) and its lanes run along x, so the loads are coalesced
-// and a voxel's index needs no division.
+// with the same FP64 reciprocal the row pass uses.  The box is contiguous in
+// the scratch, so the block streams it as one array, four coalesced loads in
+// flight per thread; only a non-zero entry (a few per cent) needs its voxel's
+// coordinates and 1 / rho.
 __global__ void k_column_max(const unsigned long long* __restrict__ scratch, const DevItem* __restrict__ items,
                              const DevBox* __restrict__ boxes, const double* __restrict__ inv_rho, Grid3 sg,
                              int first_item, double* __restrict__ colmax)
 {
+    constexpr int kU = 4;
     const int it = first_item + blockIdx.x;
     const DevBox b = boxes[items[it].box];
-    const int rows = b.n[1] * b.n[2];
+    const long long size = (long long)b.n[0] * b.n[1] * b.n[2];
+    const unsigned long long* src = scratch + b.base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     double m = 0.0;
-    for (int row = warp; row < rows; row += nwarp) {
-        const int ly = row % b.n[1], lz = row / b.n[1];
-        const unsigned long long* src = scratch + b.base + (long long)row * b.n[0];
-        const long long v0 = b.lo[0] + (long long)sg.n[0] * ((b.lo[1] + ly) + (long long)sg.n[1] * (b.lo[2] + lz));
-        for (int lx = lane; lx < b.n[0]; lx += 32) {
-            const unsigned long long q = __ldcs(src + lx);
-            if (q != 0ull) m = fmax(m, (double)q * inv_rho[v0 + lx]);
+    for (long long i0 = threadIdx.x; i0 < size; i0 += (long long)kU * blockDim.x) {
+        unsigned long long q[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const long long i = i0 + (long long)u * blockDim.x;
+            q[u] = i < size ? __ldcs(src + i) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (q[u] == 0ull) continue;
+            const long long i = i0 + (long long)u * blockDim.x;
+            const int row = (int)(i / b.n[0]);
+            const int lx = (int)(i - (long long)row * b.n[0]);
+            const int ly = row % b.n[1], lz = row / b.n[1];
+            const long long v = (b.lo[0] + lx) + (long long)sg.n[0] * ((b.lo[1] + ly) + (long long)sg.n[1] * (b.lo[2] + lz));
+            m = fmax(m, (double)q[u] * inv_rho[v]);
         }
     }
     __shared__ double red[32];
@@ -104,22 +109,34 @@ __global__ void k_reciprocal(const double* __restrict__ x, long long n, double* 
         out[i] = 1.0 / x[i];
 }
 
-// One thread per scoring voxel (row).  Box columns are visited beam by beam
-// and, within a beam, in spot order (spots are sorted by beam, so this is
-// item order); the voxel's out-of-box records, sorted by item, are merged in
-// between, so a row's entries come out sorted by column.
+// One thread per scoring voxel (row).  Box columns are visited run by run (a
+// run: consecutive items of one field whose boxes have one shape and origin)
+// and, within a run, in item order (spots are sorted by beam, so this is
+// column order); the voxel's out-of-box records, sorted by item, are merged
+// in between, so a row's entries come out sorted by column.
+// A run's shape, origin and column range, staged in shared memory: every
+// thread of a block tests the same runs in the same order.
+struct RunRow {
+    int lo[3], n[3];
+    int first, cnt;
+    long long base0;                 // scratch offset of the run's first column box
+};
+constexpr int kRunsPerStage = 512;
+
 __global__ void k_csr_rows(const CsrBuildParams p, int fill)
 {
+    __shared__ RunRow runs[kRunsPerStage];
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v >= p.nvox) return;
-    const int x = (int)(v % p.sg.n[0]);
-    const int y = (int)((v / p.sg.n[0]) % p.sg.n[1]);
-    const int z = (int)(v / ((long long)p.sg.n[0] * p.sg.n[1]));
-    const double inv_rho = 1.0 / p.rho[v];
+    const bool row = v < p.nvox;
+    const long long vv = row ? v : 0;
+    const int x = (int)(vv % p.sg.n[0]);
+    const int y = (int)((vv / p.sg.n[0]) % p.sg.n[1]);
+    const int z = (int)(vv / ((long long)p.sg.n[0] * p.sg.n[1]));
+    const double inv_rho = row ? 1.0 / p.rho[vv] : 0.0;
     long long count = 0;
-    long long pos = fill ? p.row_ptr[v] : 0;
-    const OvfRec* rec = p.ovf ? p.ovf + p.bucket_off[v] : nullptr;
-    const int nrec = p.ovf ? p.bucket_len[v] : 0;
+    long long pos = (fill && row) ? p.row_ptr[vv] : 0;
+    const OvfRec* rec = (p.ovf && row) ? p.ovf + p.bucket_off[vv] : nullptr;
+    const int nrec = (p.ovf && row) ? p.bucket_len[vv] : 0;
     int j = 0;
     auto emit = [&](int it, unsigned long long q) {
         const double r = (double)q * inv_rho;
@@ -132,34 +149,51 @@ __global__ void k_csr_rows(const CsrBuildParams p, int fill)
             ++count;
         }
     };
-    for (int b = 0; b < p.n_beams; ++b) {
-        const int cnt = p.beam_count[b];
-        if (cnt == 0) continue;
-        const DevBox bb = p.boxes[p.beam_box[b]];
-        const long long l = box_local(bb, x, y, z);
-        if (l < 0) continue;
-        // the beam's columns are consecutive boxes of one shape: spot t of the
-        // beam at first + t * size; loads go out eight at a time so that
-        // several are in flight (the scratch is streamed once per pass)
-        const int first = p.beam_first[b];
-        const long long size = (long long)bb.n[0] * bb.n[1] * bb.n[2];
-        const unsigned long long* col0 = p.scratch + p.boxes[p.items[first].box].base + l;
-        for (int t0 = 0; t0 < cnt; t0 += 8) {
-            unsigned long long q[8];
+    for (int r0 = 0; r0 < p.n_runs; r0 += kRunsPerStage) {
+        const int nst = min(kRunsPerStage, p.n_runs - r0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nst; i += blockDim.x) {
+            const DevBox bb = p.boxes[p.run_box[r0 + i]];
+            RunRow rr;
+            for (int k = 0; k < 3; ++k) { rr.lo[k] = bb.lo[k]; rr.n[k] = bb.n[k]; }
+            rr.first = p.run_first[r0 + i];
+            rr.cnt = p.run_count[r0 + i];
+            rr.base0 = rr.cnt > 0 ? p.boxes[p.items[rr.first].box].base : 0;
+            runs[i] = rr;
+        }
+        __syncthreads();
+        if (!row) continue;
+        for (int b = 0; b < nst; ++b) {
+            const RunRow& rr = runs[b];
+            const int lx = x - rr.lo[0], ly = y - rr.lo[1], lz = z - rr.lo[2];
+            if (rr.cnt == 0 || (unsigned)lx >= (unsigned)rr.n[0] || (unsigned)ly >= (unsigned)rr.n[1] ||
+                (unsigned)lz >= (unsigned)rr.n[2])
+                continue;
+            const long long l = lx + (long long)rr.n[0] * (ly + (long long)rr.n[1] * lz);
+            // the run's columns are consecutive boxes of one shape: item t of
+            // the run at first + t * size; loads go out eight at a time so
+            // that several are in flight (the scratch is streamed once per pass)
+            const int first = rr.first, cnt = rr.cnt;
+            const long long size = (long long)rr.n[0] * rr.n[1] * rr.n[2];
+            const unsigned long long* col0 = p.scratch + rr.base0 + l;
+            for (int t0 = 0; t0 < cnt; t0 += 8) {
+                unsigned long long q[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) q[u] = t0 + u < cnt ? __ldcs(col0 + (long long)(t0 + u) * size) : 0ull;
+                for (int u = 0; u < 8; ++u) q[u] = t0 + u < cnt ? __ldcs(col0 + (long long)(t0 + u) * size) : 0ull;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (t0 + u >= cnt) break;
-                const int it = first + t0 + u;
-                while (j < nrec && rec[j].item - p.item_base < it) {
-                    emit(rec[j].item - p.item_base, rec[j].q);
-                    ++j;
+                for (int u = 0; u < 8; ++u) {
+                    if (t0 + u >= cnt) break;
+                    const int it = first + t0 + u;
+                    while (j < nrec && rec[j].item - p.item_base < it) {
+                        emit(rec[j].item - p.item_base, rec[j].q);
+                        ++j;
+                    }
+                    if (q[u] != 0ull) emit(it, q[u]);
                 }
-                if (q[u] != 0ull) emit(it, q[u]);
             }
         }
     }
+    if (!row) return;
     for (; j < nrec; ++j) emit(rec[j].item - p.item_base, rec[j].q);
     if (!fill) p.row_count[v] = count;
 }

@@ -179,8 +179,12 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                 water.kappa = rs.y * spr_scale;
                 water.rho = rs.x;
                 // the faces of the current voxel of each grid (the scoring
-                // grid's only on axes that are not nested), shared by the face
-                // distances and the lateral confinement below
+                // grid's only on axes that are not nested), shared by the
+                // lateral confinement and the face distances.  The previous
+                // step's lateral displacement is confined here, to the voxel
+                // the step ended in, so that the faces are computed once per
+                // step (not again after a crossing); nothing reads the
+                // position in between
                 float f0[3], f1[3], g0[3], g1[3];
                 float dc[3], ds[3], s_geom = __int_as_float(0x7f800000);
 #pragma unroll
@@ -191,6 +195,12 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                     if (!nested) {
                         g0[k] = P.sg.lo[k] + (float)L.is[k] * P.sg.d[k];
                         g1[k] = P.sg.lo[k] + (float)(L.is[k] + 1) * P.sg.d[k];
+                    }
+                    if (L.iters > 1) {
+                        // the previous step's lateral displacement, confined to the current voxel of both grids
+                        const float vlo = nested ? f0[k] : fmaxf(f0[k], g0[k]);
+                        const float vhi = nested ? f1[k] : fminf(f1[k], g1[k]);
+                        L.p[k] = fminf(fmaxf(L.p[k], vlo), vhi);
                     }
                     dc[k] = ds[k] = __int_as_float(0x7f800000);
                     const float Dk = L.d[k];
@@ -244,15 +254,11 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                             const int sg = d_old[k] > 0.0f ? 1 : -1;
                             if (d_old[k] != 0.0f && dc[k] == o.s) {
                                 L.ic[k] += sg;
-                                f0[k] = P.ctg.lo[k] + (float)L.ic[k] * P.ctg.d[k];
-                                f1[k] = P.ctg.lo[k] + (float)(L.ic[k] + 1) * P.ctg.d[k];
                             }
                             out |= (unsigned)L.ic[k] >= (unsigned)P.ctg.n[k];
                             if (!nested) {
                                 if (d_old[k] != 0.0f && ds[k] == o.s) {
                                     L.is[k] += sg;
-                                    g0[k] = P.sg.lo[k] + (float)L.is[k] * P.sg.d[k];
-                                    g1[k] = P.sg.lo[k] + (float)(L.is[k] + 1) * P.sg.d[k];
                                 }
                                 out |= (unsigned)L.is[k] >= (unsigned)P.sg.n[k];
                             }
@@ -260,14 +266,9 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                         if (out) fate = kLeak;
                     }
                     if (fate < 0) {
-                        // lateral displacement, confined to the current voxel of both grids
+                        // lateral displacement (confined at the next step's start)
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const bool nested = (kNest >> k) & 1;
-                            const float vlo = nested ? f0[k] : fmaxf(f0[k], g0[k]);
-                            const float vhi = nested ? f1[k] : fminf(f1[k], g1[k]);
-                            L.p[k] = fminf(fmaxf(L.p[k] + o.disp[k], vlo), vhi);
-                        }
+                        for (int k = 0; k < 3; ++k) L.p[k] += o.disp[k];
                     }
                 }
             }

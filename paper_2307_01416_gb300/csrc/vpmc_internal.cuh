@@ -340,10 +340,10 @@ struct CsrBuildParams {
     const DevBox* boxes;
     const double* rho;               // scoring-voxel densities
     const double* colmax;            // per item max of q / rho
-    const int* beam_first;           // per beam: first item index (relative)
-    const int* beam_count;
-    const int* beam_box;             // per beam: the box shared by its items (shape and origin)
-    int n_beams;
+    const int* run_first;            // per run of items sharing one box: first item index (relative)
+    const int* run_count;
+    const int* run_box;              // per run: the box shared by its items (shape and origin)
+    int n_runs;
     const OvfRec* ovf;               // out-of-box deposits bucketed by voxel, sorted by item, merged
     const long long* bucket_off;     // per voxel of this scenario: first record
     const int* bucket_len;           // per voxel: merged records
@@ -358,6 +358,23 @@ struct CsrBuildParams {
     float* val;
 };
 cudaError_t launch_csr_pass(const CsrBuildParams& p, int fill, cudaStream_t s);
+
+// Rays parallel to one field's axis (beam frame base + a u + b v + t w) over
+// a lateral grid of na x nb columns at spacing da, marched from t0 to t1 in
+// steps dt; runs [run_off, run_off + run_n) of r_lim (ascending) are the
+// water-equivalent ranges whose reach the job finds.
+struct DepthJob {
+    float base[3], u[3], v[3], w[3];
+    float a0, b0, da;
+    int na, nb;
+    float t0, t1, dt;
+    float spr_scale;
+    int run_off, run_n;
+};
+// reach[run] (FP32 bits, zeroed by the caller): the largest t - t0 over the
+// columns at which the water-equivalent path reaches r_lim[run].
+cudaError_t launch_depth_bounds(const uint16_t* ct, const TablesImage* tables, Grid3 ctg, const DepthJob* jobs,
+                                int n_jobs, const float* r_lim, unsigned* reach, cudaStream_t s);
 // Counting sort of out-of-box records into per-(scenario, voxel) buckets,
 // then per bucket: sort by item, merge duplicates, raise the column maxima.
 cudaError_t launch_ovf_count(const OvfRec* rec, long long n, int n_spots, long long nvox, long long* bucket_cnt,

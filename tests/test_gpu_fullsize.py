@@ -68,6 +68,22 @@ def test_structure_threshold_and_energy(fullset):
         assert np.all(val >= 1e-4 * cmax[col] * (1 - 1e-6))
 
 
+def test_column_boxes_hold_the_deposits(fullset):
+    """Each spot's column box ends at its energy layer's reach along the field
+    (rays marched through the CT per scenario, water range behind the range
+    shifter + 5 % + 3 mm).  A deposit beyond its box is recorded and merged
+    into the CSR, so the bound changes no value (the columns-sum-to-dose and
+    sampled-column tests hold with it); it must only add few records.  The
+    records are the lateral tails beyond the boxes' 25 mm margin: measured
+    4,335,001 per set with full-depth boxes and 4,349,642 with the cut ones
+    (2.7e-5 of the patient steps), while the scratch fell from 131.7 to
+    88.2 GB.  Bound: 5e-5 of the patient steps."""
+    pb, spots, scens, mats, st, _ = fullset
+    patient_steps = st["steps"] - st["steps_rs"] - st["steps_aperture"]
+    assert st["ovf_records"] < 5e-5 * patient_steps, (st["ovf_records"], patient_steps)
+    assert st["scratch_bytes"] > 0
+
+
 def test_columns_sum_to_the_dose(fullset):
     """Nominal scenario: with no entry dropped (threshold 0) the columns x
     n_hist summed over the spots equal the dose of the same spots and seed to
