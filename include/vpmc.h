@@ -22,12 +22,14 @@
  *     (vpmc_last_error).  No C++ exception crosses this boundary.  A kernel
  *     that meets an inconsistent state (iteration cap of a history, box
  *     overflow) records it in a device status word that the host reads.
- *   - Nothing here allocates host memory that the caller must free, except
- *     the CSR buffers of vpmc_influence_matrix (vpmc_free_csr).
+ *   - Nothing here allocates memory that the caller must free, except the
+ *     CSR buffers of vpmc_influence_matrix (vpmc_free_csr), unless the caller
+ *     supplies their allocator (vpmc_set_csr_allocator).
  */
 #ifndef VPMC_H
 #define VPMC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -255,8 +257,23 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* ctx, const vpmc_spot* spots, int n_s
                                   int n_scen, const vpmc_opts* opts, float rel_threshold, vpmc_csr* out,
                                   vpmc_stats* stats_out);
 
-/* Free the device buffers of n CSR matrices and zero the structs. */
+/* Free the device buffers of n CSR matrices and zero the structs.  Only for
+ * buffers the library allocated (no allocator set with
+ * vpmc_set_csr_allocator when they were made). */
 vpmc_status vpmc_free_csr(vpmc_csr* csr, int n);
+
+/* Allocator of the CSR buffers vpmc_influence_matrix returns: alloc(bytes,
+ * user) returns device memory of the context's device, at least 16-byte
+ * aligned, or NULL (the call then fails with VPMC_ERR_OOM).  It is called on
+ * the calling thread during vpmc_influence_matrix, three times per scenario
+ * (row_ptr, col, val; never with bytes = 0), and what it returns belongs to
+ * the caller: the library never frees it, also when the call fails, and
+ * vpmc_free_csr must not be used on it.  alloc = NULL restores allocation by
+ * the library.  Lets a caller take the matrices in its own memory pool
+ * without a copy and without device-wide allocation calls in the loop.
+ * VPMC_ERR_ARG: ctx NULL. */
+typedef void* (*vpmc_alloc_fn)(size_t bytes, void* user);
+vpmc_status vpmc_set_csr_allocator(vpmc_ctx* ctx, vpmc_alloc_fn alloc, void* user);
 
 /* ------------------------------------------------------------------------
  * Learned aperture surrogate.  The paper has no counterpart: its aperture

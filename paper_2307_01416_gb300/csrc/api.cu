@@ -64,6 +64,33 @@ cudaError_t dev_alloc(T** p, size_t n)
     return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
 }
 
+// n elements of T from a context's grow-only buffer (reallocated, contents
+// lost, only when it is too small).
+template <class T>
+cudaError_t ensure(DevBuf& b, size_t n, T** out)
+{
+    const size_t need = (n == 0 ? 1 : n) * sizeof(T);
+    if (need > b.bytes) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMalloc(&b.p, need);
+        if (e != cudaSuccess) {
+            *out = nullptr;
+            return e;
+        }
+        b.bytes = need;
+    }
+    *out = static_cast<T*>(b.p);
+    return cudaSuccess;
+}
+
+void free_buf(DevBuf& b)
+{
+    cudaFree(b.p);
+    b = DevBuf{};
+}
+
 }  // namespace
 
 
@@ -1195,9 +1222,9 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         float* d_rl = nullptr;
         unsigned* d_reach = nullptr;
         std::vector<unsigned> h_reach(rl.size(), 0u);
-        cudaError_t e = dev_alloc(&d_jobs, jobs.size());
-        if (e == cudaSuccess) e = dev_alloc(&d_rl, rl.size());
-        if (e == cudaSuccess) e = dev_alloc(&d_reach, rl.size());
+        cudaError_t e = ensure(c->im_jobs, jobs.size(), &d_jobs);
+        if (e == cudaSuccess) e = ensure(c->im_rlim, rl.size(), &d_rl);
+        if (e == cudaSuccess) e = ensure(c->im_reach, rl.size(), &d_reach);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(DepthJob), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess)
@@ -1210,9 +1237,6 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             e = cudaMemcpyAsync(h_reach.data(), d_reach, rl.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
                                 c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        cudaFree(d_jobs);
-        cudaFree(d_rl);
-        cudaFree(d_reach);
         if (e != cudaSuccess)
             return fail(e == cudaErrorMemoryAllocation ? VPMC_ERR_OOM : VPMC_ERR_CUDA, "column-box depths: %s",
                         cudaGetErrorString(e));
@@ -1260,18 +1284,29 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     int* d_bucket_len = nullptr;
     OvfRec* d_ovf_sorted = nullptr;
     unsigned long long* d_ovf_count = nullptr;
-    auto release = [&]() {
-        cudaFree(d_colmax); cudaFree(d_item_scale); cudaFree(d_rowcnt); cudaFree(d_nnz); cudaFree(d_scan_tmp);
-        cudaFree(d_beam_meta);
-        cudaFree(d_bucket_off); cudaFree(d_bucket_cur); cudaFree(d_bucket_len); cudaFree(d_ovf_sorted);
-        cudaFree(d_ovf_count);
+    // the work arrays are the context's (kept between calls); on failure the
+    // library's own CSR buffers are freed, a caller allocator's are left to it
+    auto release = [&]() {};
+    auto drop_outputs = [&]() {
+        if (c->csr_alloc) {
+            for (int s = 0; s < n_scen; ++s) out[s] = vpmc_csr{};
+        } else {
+            vpmc_free_csr(out, n_scen);
+        }
+    };
+    auto out_alloc = [&](void** p, size_t bytes) -> cudaError_t {
+        *p = nullptr;
+        if (!c->csr_alloc) return cudaMalloc(p, bytes == 0 ? 1 : bytes);
+        if (bytes == 0) return cudaSuccess;
+        *p = c->csr_alloc(bytes, c->csr_alloc_user);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
     };
 #define IM_TRY(expr)                                                                                    \
     do {                                                                                                \
         cudaError_t e_ = (expr);                                                                        \
         if (e_ != cudaSuccess) {                                                                        \
             release();                                                                                  \
-            vpmc_free_csr(out, n_scen);                                                                 \
+            drop_outputs();                                                                             \
             return fail(e_ == cudaErrorMemoryAllocation ? VPMC_ERR_OOM : VPMC_ERR_CUDA, "%s: %s", #expr, \
                         cudaGetErrorString(e_));                                                        \
         }                                                                                               \
@@ -1279,15 +1314,15 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
 #define IM_ST(expr)                                                                                     \
     do {                                                                                                \
         vpmc_status s_ = (expr);                                                                        \
-        if (s_ != VPMC_OK) { release(); vpmc_free_csr(out, n_scen); return s_; }                        \
+        if (s_ != VPMC_OK) { release(); drop_outputs(); return s_; }                                    \
     } while (0)
-    IM_TRY(dev_alloc(&d_item_scale, n_spots));
+    IM_TRY(ensure(c->im_item_scale, n_spots, &d_item_scale));
     IM_TRY(cudaMemcpy(d_item_scale, item_scale.data(), n_spots * sizeof(double), cudaMemcpyHostToDevice));
-    IM_TRY(dev_alloc(&d_rowcnt, (size_t)n_scen * (c->nvox + 1)));
-    IM_TRY(dev_alloc(&d_nnz, (size_t)n_scen));
-    IM_TRY(dev_alloc(&d_scan_tmp, scan_tmp_elems((long long)n_scen * c->nvox + 1)));
-    IM_TRY(dev_alloc(&d_beam_meta, 3 * (size_t)nr * n_scen));
-    IM_TRY(dev_alloc(&d_ovf_count, 1));
+    IM_TRY(ensure(c->im_rowcnt, (size_t)n_scen * (c->nvox + 1), &d_rowcnt));
+    IM_TRY(ensure(c->im_nnz, (size_t)n_scen, &d_nnz));
+    IM_TRY(ensure(c->im_scan_tmp, scan_tmp_elems((long long)n_scen * c->nvox + 1), &d_scan_tmp));
+    IM_TRY(ensure(c->im_meta, 3 * (size_t)nr * n_scen, &d_beam_meta));
+    IM_TRY(ensure(c->im_ovf_count, 1, &d_ovf_count));
     IM_TRY(cudaMemcpy(c->d_scens, dscen.data(), n_scen * sizeof(DevScen), cudaMemcpyHostToDevice));
 
     vpmc_stats stats{};
@@ -1426,12 +1461,12 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         IM_TRY(cudaMemcpy(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost));
         if (status & 1) {
             release();
-            vpmc_free_csr(out, n_scen);
+            drop_outputs();
             return fail(VPMC_ERR_TIMEOUT, "histories reached the iteration cap");
         }
         if (status & 6) {
             release();
-            vpmc_free_csr(out, n_scen);
+            drop_outputs();
             return fail(VPMC_ERR_DEVICE_FLAG, "hand-off or query buffer overflow (status %d)", status);
         }
         if (o.surrogate && c->sur_ready) {
@@ -1439,29 +1474,23 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             IM_TRY(cudaMemcpy(&ss, c->sur.status, sizeof ss, cudaMemcpyDeviceToHost));
             if (ss) {
                 release();
-                vpmc_free_csr(out, n_scen);
+                drop_outputs();
                 return fail(VPMC_ERR_TIMEOUT, "surrogate: a tensor-core wait timed out");
             }
         }
         stats.ovf_records += (long long)n_ovf;
         stats.scratch_bytes += wave_elems * (long long)sizeof(unsigned long long);
         // column maxima over boxes, then bucket the out-of-box records and raise the maxima
-        cudaFree(d_colmax);
-        d_colmax = nullptr;
-        IM_TRY(dev_alloc(&d_colmax, items.size()));
+        IM_TRY(ensure(c->im_colmax, items.size(), &d_colmax));
         IM_TRY(launch_column_max(c->d_scratch, c->d_items, c->d_boxes, c->d_inv_rho, c->sg, 0, (int)items.size(),
                                  d_colmax, c->stream));
         ++c->launches;
         const long long n_buckets = (long long)ns * c->nvox;
         if (n_ovf) {
-            cudaFree(d_bucket_off); cudaFree(d_bucket_cur); cudaFree(d_bucket_len); cudaFree(d_ovf_sorted);
-            d_bucket_off = d_bucket_cur = nullptr;
-            d_bucket_len = nullptr;
-            d_ovf_sorted = nullptr;
-            IM_TRY(dev_alloc(&d_bucket_off, n_buckets + 1));
-            IM_TRY(dev_alloc(&d_bucket_cur, n_buckets + 1));
-            IM_TRY(dev_alloc(&d_bucket_len, n_buckets));
-            IM_TRY(dev_alloc(&d_ovf_sorted, n_ovf));
+            IM_TRY(ensure(c->im_bucket_off, n_buckets + 1, &d_bucket_off));
+            IM_TRY(ensure(c->im_bucket_cur, n_buckets + 1, &d_bucket_cur));
+            IM_TRY(ensure(c->im_bucket_len, n_buckets, &d_bucket_len));
+            IM_TRY(ensure(c->im_ovf_sorted, n_ovf, &d_ovf_sorted));
             IM_TRY(cudaMemsetAsync(d_bucket_cur, 0, (n_buckets + 1) * sizeof(long long), c->stream));
             IM_TRY(launch_ovf_count(c->d_ovf, (long long)n_ovf, n_spots, c->nvox, d_bucket_cur, c->stream));
             IM_TRY(launch_exclusive_scan(d_bucket_cur, d_bucket_off, n_buckets + 1, d_scan_tmp, c->stream));
@@ -1515,7 +1544,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             vpmc_csr& csr = out[s];
             csr.n_rows = c->nvox;
             csr.n_cols = n_spots;
-            IM_TRY(dev_alloc(&csr.row_ptr, c->nvox + 1));
+            IM_TRY(out_alloc(reinterpret_cast<void**>(&csr.row_ptr), (c->nvox + 1) * sizeof(int64_t)));
             IM_TRY(cudaMemsetAsync(rowcnt + c->nvox, 0, sizeof(long long), c->stream));
             IM_TRY(launch_exclusive_scan(rowcnt, reinterpret_cast<long long*>(csr.row_ptr), c->nvox + 1, d_scan_tmp,
                                          c->stream));
@@ -1530,8 +1559,8 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             vpmc_csr& csr = out[s];
             CsrBuildParams& cp = cps[s - s0];
             csr.nnz = nnz[s - s0];
-            IM_TRY(dev_alloc(&csr.col, csr.nnz));
-            IM_TRY(dev_alloc(&csr.val, csr.nnz));
+            IM_TRY(out_alloc(reinterpret_cast<void**>(&csr.col), csr.nnz * sizeof(int32_t)));
+            IM_TRY(out_alloc(reinterpret_cast<void**>(&csr.val), csr.nnz * sizeof(float)));
             cp.row_ptr = reinterpret_cast<const long long*>(csr.row_ptr);
             cp.col = csr.col;
             cp.val = csr.val;
@@ -1557,6 +1586,15 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         stats.launches = c->launches - launches0;
         *stats_out = stats;
     }
+    return VPMC_OK;
+}
+
+vpmc_status vpmc_set_csr_allocator(vpmc_ctx* c, vpmc_alloc_fn alloc, void* user)
+{
+    g_error.clear();
+    if (!c) return fail(VPMC_ERR_ARG, "null context");
+    c->csr_alloc = alloc;
+    c->csr_alloc_user = alloc ? user : nullptr;
     return VPMC_OK;
 }
 
@@ -1608,6 +1646,10 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->sur.img);
     cudaFree(c->sur.loss);
     cudaFree(c->sur.status);
+    for (DevBuf* b : {&c->im_colmax, &c->im_item_scale, &c->im_rowcnt, &c->im_nnz, &c->im_scan_tmp, &c->im_meta,
+                      &c->im_bucket_off, &c->im_bucket_cur, &c->im_bucket_len, &c->im_ovf_sorted, &c->im_ovf_count,
+                      &c->im_jobs, &c->im_rlim, &c->im_reach})
+        free_buf(*b);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (cudaEvent_t e : c->kev)

@@ -19,6 +19,13 @@ struct TuneResult {
     int chunk = 32;
 };
 
+// Grow-only device buffer a context keeps between calls (the influence
+// matrix's work arrays), so that repeated calls of one size allocate nothing.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
 }  // namespace vpmc
 
 struct vpmc_ctx {
@@ -87,6 +94,12 @@ struct vpmc_ctx {
     // surrogate's status word too): the next call reads it first
     int status_pending = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // influence-matrix work arrays (kept, grown on demand)
+    vpmc::DevBuf im_colmax, im_item_scale, im_rowcnt, im_nnz, im_scan_tmp, im_meta, im_bucket_off, im_bucket_cur,
+        im_bucket_len, im_ovf_sorted, im_ovf_count, im_jobs, im_rlim, im_reach;
+    // allocator of the influence matrices' CSR buffers (NULL: the library's)
+    vpmc_alloc_fn csr_alloc = nullptr;
+    void* csr_alloc_user = nullptr;
 };
 
 namespace vpmc {

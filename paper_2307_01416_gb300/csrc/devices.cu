@@ -11,7 +11,8 @@
 // (Sec. 2.B: at every step inside the aperture slab a crossing-number test
 // decides opening -> straight flight, or brass -> condensed-history step with
 // brass physics); k_patient (patient.cu) transports it through the voxelised
-// patient.
+// patient.  Each kernel is compiled twice: with the physics switches read
+// from the launch, and with full physics known at compile time.
 #include "transport_common.cuh"
 
 namespace vpmc {
@@ -196,6 +197,7 @@ __device__ __forceinline__ float4 coop_nearest_edge(bool need, float x, float y,
 // radius: outside the radius a proton flies straight to the slab's exit plane.
 // Survivors go to the aperture kernel in the beam's-eye frame.  Every lane of
 // a warp runs the same slab step, so the warps stay converged.
+template <bool kAllPhysics>
 __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
                 L.d[0] = tha * nrm; L.d[1] = thb * nrm; L.d[2] = nrm;
                 L.p[0] = fmaf(B.t_src, tha, a0); L.p[1] = fmaf(B.t_src, thb, b0); L.p[2] = B.t_src;
                 L.E = I.E0;
-                if (P.nuclear) {
+                if (kAllPhysics || P.nuclear) {
                     const uint4 y = philox(make_uint4(L.hist, 0u, 3u, 0u), key);
                     L.nlam = -logf(u01(y.x));
                 } else {
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
                 else if (L.d[2] < 0.0f) { s_geom = __fdividef(B.rs_tup - L.p[2], L.d[2]); down = false; }
                 s_geom = fmaxf(s_geom, 0.0f);       // scattering offsets can leave it past the plane
                 StepResult o;
-                ch_step<false>(pmma, s_geom, L, P, key, o);
+                ch_step<kAllPhysics>(pmma, s_geom, L, P, key, o);
                 acc_steps += 1;
                 const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
                 acc_rs += qs;
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(768, 1) k_source_rs(const TransportParams P)
 // kMode bit 0: brass entries in the surrogate's domain become queries;
 // bit 1: training tracks (histories start on the aperture entrance plane and
 // record the surrogate's inputs and targets).
-template <int kMode>
+template <int kMode, bool kAllPhysics>
 __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
 {
     constexpr bool kSur = (kMode & 1) != 0;
@@ -479,7 +481,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
                         L.p[0] = rr * cph; L.p[1] = rr * sph; L.p[2] = B.ap_tup;
                         L.E = E;
                     }
-                    if (P.nuclear) {
+                    if (kAllPhysics || P.nuclear) {
                         const uint4 y = philox(make_uint4(L.hist, 0u, 3u, 0u), key);
                         L.nlam = -logf(u01(y.x));
                     } else {
@@ -717,7 +719,7 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
             }
             if (do_ch) {
                 StepResult o;
-                ch_step<false>(m, s_geom, L, P, key, o);
+                ch_step<kAllPhysics>(m, s_geom, L, P, key, o);
                 acc_steps += 1;
                 const unsigned long long qs = to_fixed(o.dE, P.fscale, P.fx32);
                 acc_ap += qs;
@@ -825,17 +827,38 @@ __global__ void __launch_bounds__(640, 1) k_aperture(const TransportParams P)
 size_t devices_smem_bytes() { return SourceSmem::Bytes > ApertureSmem::Bytes ? SourceSmem::Bytes : ApertureSmem::Bytes; }
 int devices_max_block() { return 640; }
 
-template <int kMode>
-static cudaError_t launch_aperture_mode(const TransportParams& p, int grid, int block, cudaStream_t s)
+template <int kMode, bool kAllPhysics>
+static cudaError_t launch_aperture_variant(const TransportParams& p, int grid, int block, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_aperture<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)ApertureSmem::Bytes);
+        cudaError_t e = cudaFuncSetAttribute(k_aperture<kMode, kAllPhysics>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ApertureSmem::Bytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_aperture<kMode><<<grid, block, ApertureSmem::Bytes, s>>>(p);
+    k_aperture<kMode, kAllPhysics><<<grid, block, ApertureSmem::Bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int kMode>
+static cudaError_t launch_aperture_mode(const TransportParams& p, int grid, int block, cudaStream_t s)
+{
+    if (p.mcs && p.straggling && p.nuclear) return launch_aperture_variant<kMode, true>(p, grid, block, s);
+    return launch_aperture_variant<kMode, false>(p, grid, block, s);
+}
+
+template <bool kAllPhysics>
+static cudaError_t launch_source_rs(const TransportParams& p, int grid, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_source_rs<kAllPhysics>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SourceSmem::Bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_source_rs<kAllPhysics><<<grid, 768, SourceSmem::Bytes, s>>>(p);      // 78 registers: 768 threads fit
     return cudaGetLastError();
 }
 
@@ -843,17 +866,10 @@ cudaError_t launch_devices(const TransportParams& p, int grid, int block, cudaSt
 {
     const int mode = (p.surrogate ? 1 : 0) | (p.track_mode ? 2 : 0);
     if (!p.track_mode) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(k_source_rs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)SourceSmem::Bytes);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
         cudaError_t e = cudaMemsetAsync(p.mid_count, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
-        k_source_rs<<<grid, 768, SourceSmem::Bytes, s>>>(p);      // 78 registers: 768 threads fit
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = (p.mcs && p.straggling && p.nuclear) ? launch_source_rs<true>(p, grid, s) : launch_source_rs<false>(p, grid, s);
+        if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
     }
     switch (mode) {

@@ -92,7 +92,11 @@ EXPORTED = ["vpmc_default_opts", "vpmc_create_geometry", "vpmc_set_aperture", "v
             "vpmc_run_spots_noalloc", "vpmc_influence_matrix", "vpmc_free_csr", "vpmc_destroy", "vpmc_last_error",
             "vpmc_surrogate_init", "vpmc_surrogate_set_weights", "vpmc_surrogate_get_weights",
             "vpmc_surrogate_tracks", "vpmc_surrogate_forward", "vpmc_surrogate_gradient", "vpmc_surrogate_train",
-            "vpmc_robust_optimize", "vpmc_target_indices", "vpmc_weights_dose", "vpmc_measure_l2_atomics"]
+            "vpmc_robust_optimize", "vpmc_target_indices", "vpmc_weights_dose", "vpmc_measure_l2_atomics",
+            "vpmc_set_csr_allocator"]
+
+# void* (*)(size_t bytes, void* user): the CSR output allocator (vpmc_set_csr_allocator)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 
 SUR_NPARAMS = 23213            # VPMC_SUR_NPARAMS
 SUR_IN, SUR_OUT, SUR_Y = 6, 45, 5
@@ -124,6 +128,8 @@ def lib():
     L.vpmc_influence_matrix.argtypes = [vp, C.POINTER(vpmc_spot), C.c_int, C.POINTER(vpmc_scenario), C.c_int,
                                         C.POINTER(vpmc_opts), C.c_float, C.POINTER(vpmc_csr), C.POINTER(vpmc_stats)]
     L.vpmc_free_csr.argtypes = [C.POINTER(vpmc_csr), C.c_int]
+    L.vpmc_set_csr_allocator.argtypes = [vp, ALLOC_FN, vp]
+    L.vpmc_set_csr_allocator.restype = C.c_int
     L.vpmc_destroy.argtypes = [vp]
     L.vpmc_destroy.restype = None
     fp = C.POINTER(C.c_float)
@@ -195,9 +201,13 @@ def scenario_struct(sc: W.Scenario) -> vpmc_scenario:
 class Engine:
     """One geometry (CT + scoring grid + fields) on the current CUDA device."""
 
-    def __init__(self, problem: W.Problem, stream=None, host_ct: bool = False):
+    def __init__(self, problem: W.Problem, stream=None, host_ct: bool = False, torch_outputs: bool = True):
         """host_ct: hand the library the host CT array (it copies it to the
-        device) instead of a device tensor."""
+        device) instead of a device tensor.  torch_outputs: the influence
+        matrices' CSR buffers are allocated by torch's caching allocator
+        through vpmc_set_csr_allocator and returned without a copy; False
+        lets the library allocate them, and they are copied into torch
+        tensors and freed (vpmc_free_csr)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("vpmc needs a CUDA device; there is no CPU path")
@@ -216,6 +226,21 @@ class Engine:
         _check(lib().vpmc_create_geometry(C.byref(self._ctx), C.c_void_p(ptr), on_dev, C.byref(ct), C.byref(cv),
                                           C.byref(sg), C.c_void_p(self.stream.cuda_stream)))
         del keep
+        self._outputs = None
+        if torch_outputs:
+            outputs, device = {}, self.device
+
+            def _alloc(nbytes, _user):
+                try:
+                    t = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+                except RuntimeError:
+                    return None
+                outputs[t.data_ptr()] = t
+                return t.data_ptr()
+
+            self._outputs = outputs
+            self._alloc_cb = ALLOC_FN(_alloc)          # the library keeps the pointer: keep the object
+            _check(lib().vpmc_set_csr_allocator(self._ctx, self._alloc_cb, None))
         for i, b in enumerate(problem.beams):
             self.set_beam(i, b)
 
@@ -282,14 +307,23 @@ class Engine:
         scs = (vpmc_scenario * len(scenarios))(*[scenario_struct(s) for s in scenarios])
         out = (vpmc_csr * len(scenarios))()
         st = vpmc_stats()
-        _check(lib().vpmc_influence_matrix(self._ctx, arr, len(spots), scs, len(scenarios), C.byref(o),
-                                           float(rel_threshold), out, C.byref(st)))
-        mats = []
+        if self._outputs is None:
+            _check(lib().vpmc_influence_matrix(self._ctx, arr, len(spots), scs, len(scenarios), C.byref(o),
+                                               float(rel_threshold), out, C.byref(st)))
+            mats = []
+            try:
+                for m in out:
+                    mats.append(_csr_to_torch(m, self.device))
+            finally:
+                lib().vpmc_free_csr(out, len(scenarios))
+            return mats, _stats_dict(st)
+        self._outputs.clear()
         try:
-            for m in out:
-                mats.append(_csr_to_torch(m, self.device))
+            _check(lib().vpmc_influence_matrix(self._ctx, arr, len(spots), scs, len(scenarios), C.byref(o),
+                                               float(rel_threshold), out, C.byref(st)))
+            mats = [_csr_from_outputs(m, self._outputs, self.device) for m in out]
         finally:
-            lib().vpmc_free_csr(out, len(scenarios))
+            self._outputs.clear()
         return mats, _stats_dict(st)
 
     # ---------------------------------------------------- learned aperture surrogate
@@ -367,6 +401,21 @@ class _DeviceView:
     def __init__(self, ptr: int, n: int, typestr: str):
         self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
                                           "version": 3, "strides": None}
+
+
+def _csr_from_outputs(m: vpmc_csr, outputs: dict, device):
+    """The CSR of one scenario as typed views of the torch buffers the output
+    allocator handed to the library (no copy)."""
+    import torch
+    out = {}
+    for name, ptr, n, dt in (("row_ptr", m.row_ptr, m.n_rows + 1, torch.int64), ("col", m.col, m.nnz, torch.int32),
+                             ("val", m.val, m.nnz, torch.float32)):
+        if n == 0:
+            out[name] = torch.empty(0, dtype=dt, device=device)
+        else:
+            out[name] = outputs.pop(int(ptr)).view(dt)[:n]
+    out["shape"] = (int(m.n_rows), int(m.n_cols))
+    return out
 
 
 def _csr_to_torch(m: vpmc_csr, device):

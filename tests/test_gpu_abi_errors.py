@@ -118,3 +118,36 @@ def test_iteration_cap_is_reported_by_the_call_and_latched_for_the_next(vpmc_mod
     _raises(vpmc, VPMC_ERR_TIMEOUT, eng.influence_matrix, spots, [W.Scenario()], W.Options(seed=9),
             timeout_iters=50)
     eng.close()
+
+
+def test_failing_output_allocator_is_out_of_memory(vpmc_mod):
+    """An output allocator that returns NULL makes vpmc_influence_matrix fail
+    with VPMC_ERR_OOM, leaves every output struct zeroed (the library frees
+    nothing it did not allocate) and the context usable; a NULL context is
+    VPMC_ERR_ARG."""
+    import ctypes as C
+    vpmc = vpmc_mod
+    assert vpmc.lib().vpmc_set_csr_allocator(None, vpmc.ALLOC_FN(lambda n, u: None), None) == VPMC_ERR_ARG
+    pb, spots = W.pencil_beam_water(n_hist=50, shape=(20, 20, 40))
+    eng = vpmc.Engine(pb)
+    calls = []
+
+    def refuse(nbytes, _user):
+        calls.append(int(nbytes))
+        return None
+
+    cb = vpmc.ALLOC_FN(refuse)
+    vpmc._check(vpmc.lib().vpmc_set_csr_allocator(eng._ctx, cb, None))
+    scs = (vpmc.vpmc_scenario * 1)(vpmc.scenario_struct(W.Scenario()))
+    out = (vpmc.vpmc_csr * 1)()
+    st = vpmc.vpmc_stats()
+    o = vpmc.make_opts(W.Options())
+    status = vpmc.lib().vpmc_influence_matrix(eng._ctx, vpmc.spot_array(spots), len(spots), scs, 1, C.byref(o),
+                                              1e-4, out, C.byref(st))
+    assert status == -3 and calls and all(n > 0 for n in calls)          # VPMC_ERR_OOM
+    assert out[0].row_ptr is None and out[0].col is None and out[0].val is None and out[0].nnz == 0
+    # the engine's own allocator back in place: the context still works
+    vpmc._check(vpmc.lib().vpmc_set_csr_allocator(eng._ctx, eng._alloc_cb, None))
+    mats, st = eng.influence_matrix(spots, [W.Scenario()], W.Options())
+    assert st["errors"] == 0 and mats[0]["val"].numel() > 0
+    eng.close()

@@ -227,6 +227,30 @@ def test_influence_matrix_deterministic_parity(torch_cuda):
     assert abs(tot / st["e_in"] - 1.0) < 1e-6
 
 
+def test_influence_matrix_output_allocators_agree(torch_cuda):
+    """The CSR buffers taken through the caller's allocator
+    (vpmc_set_csr_allocator: torch's caching allocator, no copy) and the
+    library's own (copied into torch tensors, then vpmc_free_csr) hold the
+    same matrices, bit for bit, over repeated calls on one context."""
+    from paper_2307_01416_gb300 import vpmc
+    torch = torch_cuda
+    pb, _ = W.pencil_beam_water(n_hist=10, shape=(30, 30, 60))
+    rows = [(0, e, x, 0.0, 4.0, 2.0, 200, 1.0) for e in (90.0, 110.0) for x in (-6.0, 5.0)]
+    spots = W.make_spots(rows)
+    scens = [W.robust_scenarios()[i] for i in (0, 3)]
+    res = []
+    for own in (True, False):
+        eng = vpmc.Engine(pb, torch_outputs=own)
+        for _ in range(2):
+            mats, _ = eng.influence_matrix(spots, scens, W.Options(seed=5))
+        eng.close()
+        res.append(mats)
+    for a, b in zip(*res):
+        assert a["shape"] == b["shape"]
+        for k in ("row_ptr", "col", "val"):
+            assert a[k].dtype == b[k].dtype and torch.equal(a[k], b[k])
+
+
 def test_influence_matrix_aperture_statistical(torch_cuda):
     """Full physics with range shifter and aperture, three scenarios: for each
     scenario the IM composite (columns x n_hist summed over spots) of the GPU
