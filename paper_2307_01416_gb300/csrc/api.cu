@@ -745,7 +745,8 @@ vpmc_status vpmc_create_geometry(vpmc_ctx** out, const int16_t* hu, int hu_on_de
     CTX_TRY(launch_scoring_density(c->d_ct, c->ctg, c->sg, c->d_curve, c->ct_spacing, c->sg_spacing, c->d_rho,
                                    c->stream));
     CTX_TRY(dev_alloc(&c->d_inv_rho, c->nvox));
-    CTX_TRY(launch_reciprocal(c->d_rho, c->nvox, c->d_inv_rho, c->stream));
+    CTX_TRY(dev_alloc(&c->d_inv_rho_f, c->nvox));
+    CTX_TRY(launch_reciprocal(c->d_rho, c->nvox, c->d_inv_rho, c->d_inv_rho_f, c->stream));
     // from here on the CT holds the kernels' table index per voxel
     CTX_TRY(launch_ct_lut_index(c->d_ct, nct, c->stream));
     CTX_TRY(dev_alloc(&c->d_beams, kMaxBeams));
@@ -1482,8 +1483,8 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         stats.scratch_bytes += wave_elems * (long long)sizeof(unsigned long long);
         // column maxima over boxes, then bucket the out-of-box records and raise the maxima
         IM_TRY(ensure(c->im_colmax, items.size(), &d_colmax));
-        IM_TRY(launch_column_max(c->d_scratch, c->d_items, c->d_boxes, c->d_inv_rho, c->sg, 0, (int)items.size(),
-                                 d_colmax, c->stream));
+        IM_TRY(launch_column_max(c->d_scratch, c->d_items, c->d_boxes, c->d_inv_rho, c->d_inv_rho_f, c->sg, 0,
+                                 (int)items.size(), d_colmax, c->stream));
         ++c->launches;
         const long long n_buckets = (long long)ns * c->nvox;
         if (n_ovf) {
@@ -1501,6 +1502,13 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
                                     c->stream));
             c->launches += 3 + scan_launches(n_buckets + 1);
         }
+        // per column: the threshold in FP64 and FP32 (the row passes' screen)
+        double* d_thr = nullptr;
+        float* d_thr_f = nullptr;
+        IM_TRY(ensure(c->im_thr, items.size(), &d_thr));
+        IM_TRY(ensure(c->im_thr_f, items.size(), &d_thr_f));
+        IM_TRY(launch_column_threshold(d_colmax, (int)items.size(), (double)rel_threshold, d_thr, d_thr_f, c->stream));
+        ++c->launches;
         // CSR per scenario: every scenario's count pass and row-pointer scan,
         // one read of the entry counts, then the fill passes
         std::vector<int> meta(3 * (size_t)nr * ns, 0);
@@ -1524,8 +1532,9 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cp.scratch = c->d_scratch;
             cp.items = c->d_items + first;
             cp.boxes = c->d_boxes;
-            cp.rho = c->d_rho;
-            cp.colmax = d_colmax + first;
+            cp.inv_rho = c->d_inv_rho;
+            cp.thr = d_thr + first;
+            cp.thr_f = d_thr_f + first;
             cp.run_first = m;
             cp.run_count = m + nr;
             cp.run_box = m + 2 * nr;
@@ -1536,7 +1545,6 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cp.item_base = first;
             cp.sg = c->sg;
             cp.nvox = c->nvox;
-            cp.rel_threshold = rel_threshold;
             cp.item_scale = d_item_scale;
             cp.row_count = rowcnt;
             IM_TRY(launch_csr_pass(cp, 0, c->stream));
@@ -1619,6 +1627,7 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->d_curve);
     cudaFree(c->d_rho);
     cudaFree(c->d_inv_rho);
+    cudaFree(c->d_inv_rho_f);
     cudaFree(c->d_acc);
     cudaFree(c->d_beams);
     cudaFree(c->d_poly);
@@ -1648,7 +1657,7 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->sur.status);
     for (DevBuf* b : {&c->im_colmax, &c->im_item_scale, &c->im_rowcnt, &c->im_nnz, &c->im_scan_tmp, &c->im_meta,
                       &c->im_bucket_off, &c->im_bucket_cur, &c->im_bucket_len, &c->im_ovf_sorted, &c->im_ovf_count,
-                      &c->im_jobs, &c->im_rlim, &c->im_reach})
+                      &c->im_jobs, &c->im_rlim, &c->im_reach, &c->im_thr, &c->im_thr_f})
         free_buf(*b);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);

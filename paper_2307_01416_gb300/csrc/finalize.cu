@@ -58,14 +58,31 @@ __global__ void k_dose_normalise(const unsigned long long* __restrict__ acc, con
         dose[v] = (float)((double)acc[v] * scale / rho[v]);
 }
 
+// FP32 screen of the FP64 quotient q / rho: q's two 32-bit halves converted
+// (64-bit conversions would take the FP64 pipe), times the FP32 reciprocal
+// density.  Its relative error against the FP64 value is below 2^-21, so a
+// comparison decided by more than kScreen (2^-19) in FP32 has the same
+// outcome in FP64; only the rest is redone in FP64.
+constexpr float kScreen = 1.0f / 524288.0f;
+
+__device__ __forceinline__ float quotient_f32(unsigned long long q, float inv_rho_f)
+{
+    const float qf = fmaf(__uint2float_rn((unsigned)(q >> 32)), 4294967296.0f, __uint2float_rn((unsigned)q));
+    return qf * inv_rho_f;
+}
+
 // One block per item: maximum over the item's box of q / rho, as q x (1 / rho)
 // with the same FP64 reciprocal the row pass uses.  The box is contiguous in
 // the scratch, so the block streams it as one array, four coalesced loads in
 // flight per thread; only a non-zero entry (a few per cent) needs its voxel's
-// coordinates and 1 / rho.
+// coordinates and 1 / rho.  Each thread tracks its maximum in FP32 and
+// evaluates in FP64 only the entries within the screen of it: the column's
+// FP64 maximum is among them (it is at least the running FP32 maximum x
+// (1 - 2^-19)), so the result is the FP64 maximum over all entries.
 __global__ void k_column_max(const unsigned long long* __restrict__ scratch, const DevItem* __restrict__ items,
-                             const DevBox* __restrict__ boxes, const double* __restrict__ inv_rho, Grid3 sg,
-                             int first_item, double* __restrict__ colmax)
+                             const DevBox* __restrict__ boxes, const double* __restrict__ inv_rho,
+                             const float* __restrict__ inv_rho_f, Grid3 sg, int first_item,
+                             double* __restrict__ colmax)
 {
     constexpr int kU = 4;
     const int it = first_item + blockIdx.x;
@@ -74,6 +91,7 @@ __global__ void k_column_max(const unsigned long long* __restrict__ scratch, con
     const unsigned long long* src = scratch + b.base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     double m = 0.0;
+    float mf = 0.0f;
     for (long long i0 = threadIdx.x; i0 < size; i0 += (long long)kU * blockDim.x) {
         unsigned long long q[kU];
 #pragma unroll
@@ -89,7 +107,11 @@ __global__ void k_column_max(const unsigned long long* __restrict__ scratch, con
             const int lx = (int)(i - (long long)row * b.n[0]);
             const int ly = row % b.n[1], lz = row / b.n[1];
             const long long v = (b.lo[0] + lx) + (long long)sg.n[0] * ((b.lo[1] + ly) + (long long)sg.n[1] * (b.lo[2] + lz));
-            m = fmax(m, (double)q[u] * inv_rho[v]);
+            const float rf = quotient_f32(q[u], inv_rho_f[v]);
+            if (rf >= mf * (1.0f - kScreen)) {
+                m = fmax(m, (double)q[u] * inv_rho[v]);
+                mf = fmaxf(mf, rf);
+            }
         }
     }
     __shared__ double red[32];
@@ -103,10 +125,25 @@ __global__ void k_column_max(const unsigned long long* __restrict__ scratch, con
     }
 }
 
-__global__ void k_reciprocal(const double* __restrict__ x, long long n, double* __restrict__ out)
+// Per item: the FP64 threshold rel x column maximum and its FP32 value.
+__global__ void k_column_threshold(const double* __restrict__ colmax, int n, double rel, double* __restrict__ thr,
+                                   float* __restrict__ thr_f)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = 1.0 / x[i];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double t = rel * colmax[i];
+    thr[i] = t;
+    thr_f[i] = (float)t;
+}
+
+__global__ void k_reciprocal(const double* __restrict__ x, long long n, double* __restrict__ out,
+                             float* __restrict__ out_f)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double r = 1.0 / x[i];
+        out[i] = r;
+        out_f[i] = (float)r;
+    }
 }
 
 // One thread per scoring voxel (row).  Box columns are visited run by run (a
@@ -132,18 +169,26 @@ __global__ void k_csr_rows(const CsrBuildParams p, int fill)
     const int x = (int)(vv % p.sg.n[0]);
     const int y = (int)((vv / p.sg.n[0]) % p.sg.n[1]);
     const int z = (int)(vv / ((long long)p.sg.n[0] * p.sg.n[1]));
-    const double inv_rho = row ? 1.0 / p.rho[vv] : 0.0;
+    const double inv_rho = row ? p.inv_rho[vv] : 0.0;
+    const float inv_rho_f = (float)inv_rho;
     long long count = 0;
     long long pos = (fill && row) ? p.row_ptr[vv] : 0;
     const OvfRec* rec = (p.ovf && row) ? p.ovf + p.bucket_off[vv] : nullptr;
     const int nrec = (p.ovf && row) ? p.bucket_len[vv] : 0;
     int j = 0;
+    // keep q / rho unless below the column's threshold, decided by the FP32
+    // screen and, within its margin, in FP64
     auto emit = [&](int it, unsigned long long q) {
-        const double r = (double)q * inv_rho;
-        if (r < p.rel_threshold * p.colmax[it]) return;
+        const float rf = quotient_f32(q, inv_rho_f);
+        const float tf = p.thr_f[it];
+        bool keep;
+        if (rf < tf * (1.0f - kScreen)) keep = false;
+        else if (rf > tf * (1.0f + kScreen)) keep = true;
+        else keep = !((double)q * inv_rho < p.thr[it]);
+        if (!keep) return;
         if (fill) {
             p.col[pos] = p.items[it].spot;
-            p.val[pos] = (float)(r * p.item_scale[it]);
+            p.val[pos] = (float)((double)q * inv_rho * p.item_scale[it]);
             ++pos;
         } else {
             ++count;
@@ -322,19 +367,26 @@ cudaError_t launch_dose_normalise(const unsigned long long* acc, const double* r
 }
 
 cudaError_t launch_column_max(const unsigned long long* scratch, const DevItem* items, const DevBox* boxes,
-                              const double* inv_rho, const Grid3 sg, int first_item, int n_items, double* colmax,
-                              cudaStream_t s)
+                              const double* inv_rho, const float* inv_rho_f, const Grid3 sg, int first_item,
+                              int n_items, double* colmax, cudaStream_t s)
 {
     if (n_items <= 0) return cudaSuccess;
-    k_column_max<<<n_items, 512, 0, s>>>(scratch, items, boxes, inv_rho, sg, first_item, colmax);
+    k_column_max<<<n_items, 512, 0, s>>>(scratch, items, boxes, inv_rho, inv_rho_f, sg, first_item, colmax);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reciprocal(const double* x, long long n, double* out, cudaStream_t s)
+cudaError_t launch_column_threshold(const double* colmax, int n, double rel, double* thr, float* thr_f, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_column_threshold<<<(n + 255) / 256, 256, 0, s>>>(colmax, n, rel, thr, thr_f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reciprocal(const double* x, long long n, double* out, float* out_f, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const long long blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
-    k_reciprocal<<<(int)blocks, 256, 0, s>>>(x, n, out);
+    k_reciprocal<<<(int)blocks, 256, 0, s>>>(x, n, out, out_f);
     return cudaGetLastError();
 }
 

@@ -328,18 +328,21 @@ cudaError_t launch_scoring_density(const int16_t* ct, Grid3 ctg, Grid3 sg, const
                                    cudaStream_t s);
 cudaError_t launch_dose_normalise(const unsigned long long* acc, const double* rho, long long nvox, double scale,
                                   float* dose, cudaStream_t s);
-// colmax[i] = max over item first_item + i's box of q x inv_rho (inv_rho: 1 / rho per scoring voxel).
+// colmax[i] = max over item first_item + i's box of q x inv_rho (inv_rho: 1 / rho per scoring voxel, FP64;
+// inv_rho_f: the same in FP32, for the screen).
 cudaError_t launch_column_max(const unsigned long long* scratch, const DevItem* items, const DevBox* boxes,
-                              const double* inv_rho, const Grid3 sg, int first_item, int n_items, double* colmax,
-                              cudaStream_t s);
-cudaError_t launch_reciprocal(const double* x, long long n, double* out, cudaStream_t s);
+                              const double* inv_rho, const float* inv_rho_f, const Grid3 sg, int first_item,
+                              int n_items, double* colmax, cudaStream_t s);
+// out = 1 / x in FP64, out_f its FP32 value.
+cudaError_t launch_reciprocal(const double* x, long long n, double* out, float* out_f, cudaStream_t s);
 
 struct CsrBuildParams {
     const unsigned long long* scratch;
     const DevItem* items;            // items of one scenario, in spot order (spots sorted by beam)
     const DevBox* boxes;
-    const double* rho;               // scoring-voxel densities
-    const double* colmax;            // per item max of q / rho
+    const double* inv_rho;           // per scoring voxel: 1 / density (FP64)
+    const double* thr;               // per item: rel_threshold x max of q / rho (FP64)
+    const float* thr_f;              // the same in FP32 (the screen)
     const int* run_first;            // per run of items sharing one box: first item index (relative)
     const int* run_count;
     const int* run_box;              // per run: the box shared by its items (shape and origin)
@@ -350,7 +353,6 @@ struct CsrBuildParams {
     int item_base;                   // item index of this scenario's first item in the launch
     Grid3 sg;
     long long nvox;
-    double rel_threshold;
     const double* item_scale;        // per item: 2^-F * (MeV/g -> Gy) / (V(cm^3) * n_hist)
     long long* row_count;            // [nvox + 1]
     const long long* row_ptr;        // for the fill pass
@@ -358,6 +360,8 @@ struct CsrBuildParams {
     float* val;
 };
 cudaError_t launch_csr_pass(const CsrBuildParams& p, int fill, cudaStream_t s);
+// thr[i] = rel x colmax[i] and its FP32 value, for the row passes' screen.
+cudaError_t launch_column_threshold(const double* colmax, int n, double rel, double* thr, float* thr_f, cudaStream_t s);
 
 // Rays parallel to one field's axis (beam frame base + a u + b v + t w) over
 // a lateral grid of na x nb columns at spacing da, marched from t0 to t1 in
