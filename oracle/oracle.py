@@ -66,7 +66,7 @@ class _Scen(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("mcs", C.c_int), ("straggling", C.c_int), ("nuclear", C.c_int),
-                ("frac_bits", C.c_int)]
+                ("frac_bits", C.c_int), ("fine_uniforms", C.c_int)]
 
 
 SPOT_DTYPE = np.dtype([("beam", np.int32), ("spot_key", np.int32), ("energy", np.float64), ("x", np.float64),
@@ -289,11 +289,14 @@ def oracle_spots(spots: np.ndarray, spot_keys=None, h_begin=None, n_hist=None) -
 
 
 def run(problem, spots_o: np.ndarray, scenario, opts, mode: int = 0, records: int = 0,
-        nthreads: int = 0):
+        nthreads: int = 0, fine_uniforms: bool = False):
     """Transport all histories of spots_o (oracle layout) for one scenario.
 
     mode 0 returns the weighted fixed-point grid (int64, scoring-grid size);
     mode 1 returns unweighted per-spot columns, shape (n_spots, nvox).
+    fine_uniforms: the step's six uniforms at 32-bit resolution from two
+    Philox blocks instead of the engines' 21-bit lattice (reading c17), for
+    the study of the lattice's Box-Muller tail; not the engines' stream.
     Returns (q, tallies dict, records array or None)."""
     L = lib()
     ct, sg = _grid(problem.ct), _grid(problem.scoring)
@@ -302,7 +305,8 @@ def run(problem, spots_o: np.ndarray, scenario, opts, mode: int = 0, records: in
     cv = _curve(problem.curve)
     beams, xy = _beams(problem.beams)
     sc = _Scen((C.c_double * 3)(*scenario.shift), scenario.spr_scale)
-    op = _Opts(int(opts.seed), int(opts.mcs), int(opts.straggling), int(opts.nuclear), int(opts.frac_bits))
+    op = _Opts(int(opts.seed), int(opts.mcs), int(opts.straggling), int(opts.nuclear), int(opts.frac_bits),
+               int(fine_uniforms))
     nv = problem.scoring.nvox
     sp = np.ascontiguousarray(spots_o, dtype=SPOT_DTYPE)
     q = np.zeros(nv if mode == 0 else len(sp) * nv, dtype=np.int64)
