@@ -1322,7 +1322,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
     IM_TRY(ensure(c->im_rowcnt, (size_t)n_scen * (c->nvox + 1), &d_rowcnt));
     IM_TRY(ensure(c->im_nnz, (size_t)n_scen, &d_nnz));
     IM_TRY(ensure(c->im_scan_tmp, scan_tmp_elems((long long)n_scen * c->nvox + 1), &d_scan_tmp));
-    IM_TRY(ensure(c->im_meta, 3 * (size_t)nr * n_scen, &d_beam_meta));
+    IM_TRY(ensure(c->im_meta, (4 * (size_t)nr + 1) * n_scen, &d_beam_meta));
     IM_TRY(ensure(c->im_ovf_count, 1, &d_ovf_count));
     IM_TRY(cudaMemcpy(c->d_scens, dscen.data(), n_scen * sizeof(DevScen), cudaMemcpyHostToDevice));
 
@@ -1511,21 +1511,28 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         ++c->launches;
         // CSR per scenario: every scenario's count pass and row-pointer scan,
         // one read of the entry counts, then the fill passes
-        std::vector<int> meta(3 * (size_t)nr * ns, 0);
+        const size_t meta_stride = 4 * (size_t)nr + 1;
+        std::vector<int> meta(meta_stride * ns, 0);
+        std::vector<int> count_blocks(ns, 0);
         for (int s = s0; s < s1; ++s) {
-            int* m = meta.data() + 3 * (size_t)nr * (s - s0);
+            int* m = meta.data() + meta_stride * (s - s0);
+            int blocks = 0;
             for (int r = 0; r < nr; ++r) {
                 m[r] = runs[r].first;
                 m[nr + r] = runs[r].count;
                 m[2 * nr + r] = run_box[(size_t)(s - s0) * nr + r];
+                m[3 * nr + r] = blocks;
+                blocks += (int)((box_elems(spec[(size_t)s * nr + r]) + kCountBlock - 1) / kCountBlock);
             }
+            m[4 * nr] = blocks;
+            count_blocks[s - s0] = blocks;
         }
         IM_TRY(cudaMemcpyAsync(d_beam_meta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice,
                                c->stream));
         std::vector<CsrBuildParams> cps(ns);
         for (int s = s0; s < s1; ++s) {
             const int first = (s - s0) * n_spots;
-            const int* m = d_beam_meta + 3 * (size_t)nr * (s - s0);
+            const int* m = d_beam_meta + meta_stride * (s - s0);
             long long* rowcnt = d_rowcnt + (size_t)(s - s0) * (c->nvox + 1);
             CsrBuildParams& cp = cps[s - s0];
             cp = CsrBuildParams{};
@@ -1538,6 +1545,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cp.run_first = m;
             cp.run_count = m + nr;
             cp.run_box = m + 2 * nr;
+            cp.run_block0 = m + 3 * nr;
             cp.n_runs = nr;
             cp.ovf = n_ovf ? d_ovf_sorted : nullptr;
             cp.bucket_off = n_ovf ? d_bucket_off + (long long)(s - s0) * c->nvox : nullptr;
@@ -1547,13 +1555,13 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cp.nvox = c->nvox;
             cp.item_scale = d_item_scale;
             cp.row_count = rowcnt;
-            IM_TRY(launch_csr_pass(cp, 0, c->stream));
-            ++c->launches;
+            IM_TRY(cudaMemsetAsync(rowcnt, 0, (c->nvox + 1) * sizeof(long long), c->stream));
+            IM_TRY(launch_csr_count(cp, count_blocks[s - s0], c->stream));
+            c->launches += n_ovf ? 2 : 1;
             vpmc_csr& csr = out[s];
             csr.n_rows = c->nvox;
             csr.n_cols = n_spots;
             IM_TRY(out_alloc(reinterpret_cast<void**>(&csr.row_ptr), (c->nvox + 1) * sizeof(int64_t)));
-            IM_TRY(cudaMemsetAsync(rowcnt + c->nvox, 0, sizeof(long long), c->stream));
             IM_TRY(launch_exclusive_scan(rowcnt, reinterpret_cast<long long*>(csr.row_ptr), c->nvox + 1, d_scan_tmp,
                                          c->stream));
             c->launches += scan_launches(c->nvox + 1);
@@ -1572,7 +1580,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cp.row_ptr = reinterpret_cast<const long long*>(csr.row_ptr);
             cp.col = csr.col;
             cp.val = csr.val;
-            IM_TRY(launch_csr_pass(cp, 1, c->stream));
+            IM_TRY(launch_csr_fill(cp, c->stream));
             ++c->launches;
         }
         IM_TRY(cudaStreamSynchronize(c->stream));

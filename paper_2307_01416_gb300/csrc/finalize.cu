@@ -146,11 +146,83 @@ __global__ void k_reciprocal(const double* __restrict__ x, long long n, double* 
     }
 }
 
-// One thread per scoring voxel (row).  Box columns are visited run by run (a
-// run: consecutive items of one field whose boxes have one shape and origin)
-// and, within a run, in item order (spots are sorted by beam, so this is
-// column order); the voxel's out-of-box records, sorted by item, are merged
-// in between, so a row's entries come out sorted by column.
+// Keep q / rho unless it is below the column's threshold: decided by the FP32
+// screen and, within its margin, in FP64 (the FP64 rule's outcome).
+__device__ __forceinline__ bool keep_entry(unsigned long long q, double inv_rho, float inv_rho_f, double thr,
+                                           float thr_f)
+{
+    const float rf = quotient_f32(q, inv_rho_f);
+    if (rf < thr_f * (1.0f - kScreen)) return false;
+    if (rf > thr_f * (1.0f + kScreen)) return true;
+    return !((double)q * inv_rho < thr);
+}
+
+// Count pass, box-major: one thread per (run, voxel of the run's box), a run
+// being consecutive items of one field whose boxes have one shape and origin.
+// The blocks of a run take consecutive voxels of its box, so each of its
+// columns is read with coalesced loads and no thread waits outside a box.
+// The kept entries of a (voxel, run) go to the voxel's row count with one
+// atomic add (a count does not depend on the order); the voxel's out-of-box
+// records are counted by k_csr_count_records.
+__global__ void k_csr_count_box(const CsrBuildParams p)
+{
+    __shared__ int s_run;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = p.n_runs;                  // run_block0[lo] <= blockIdx.x < run_block0[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (p.run_block0[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+        }
+        s_run = lo;
+    }
+    __syncthreads();
+    const int r = s_run;
+    const int cnt = p.run_count[r];
+    if (cnt == 0) return;
+    const DevBox bb = p.boxes[p.run_box[r]];
+    const long long size = (long long)bb.n[0] * bb.n[1] * bb.n[2];
+    const long long l = (long long)(blockIdx.x - p.run_block0[r]) * blockDim.x + threadIdx.x;
+    if (l >= size) return;
+    const int first = p.run_first[r];
+    const int row = (int)(l / bb.n[0]);
+    const int lx = (int)(l - (long long)row * bb.n[0]), ly = row % bb.n[1], lz = row / bb.n[1];
+    const long long v = (bb.lo[0] + lx) + (long long)p.sg.n[0] * ((bb.lo[1] + ly) + (long long)p.sg.n[1] * (bb.lo[2] + lz));
+    const double inv_rho = p.inv_rho[v];
+    const float inv_rho_f = (float)inv_rho;
+    const unsigned long long* col0 = p.scratch + p.boxes[p.items[first].box].base + l;
+    long long count = 0;
+    for (int t0 = 0; t0 < cnt; t0 += 8) {
+        unsigned long long q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = t0 + u < cnt ? __ldcs(col0 + (long long)(t0 + u) * size) : 0ull;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (q[u] == 0ull) continue;
+            const int it = first + t0 + u;
+            count += keep_entry(q[u], inv_rho, inv_rho_f, p.thr[it], p.thr_f[it]) ? 1 : 0;
+        }
+    }
+    if (count) atomicAdd(reinterpret_cast<unsigned long long*>(p.row_count + v), (unsigned long long)count);
+}
+
+// Count pass of the out-of-box records: one thread per voxel.
+__global__ void k_csr_count_records(const CsrBuildParams p)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= p.nvox) return;
+    const int nrec = p.bucket_len[v];
+    if (nrec == 0) return;
+    const OvfRec* rec = p.ovf + p.bucket_off[v];
+    const double inv_rho = p.inv_rho[v];
+    const float inv_rho_f = (float)inv_rho;
+    long long count = 0;
+    for (int j = 0; j < nrec; ++j) {
+        const int it = rec[j].item - p.item_base;
+        count += keep_entry(rec[j].q, inv_rho, inv_rho_f, p.thr[it], p.thr_f[it]) ? 1 : 0;
+    }
+    if (count) atomicAdd(reinterpret_cast<unsigned long long*>(p.row_count + v), (unsigned long long)count);
+}
+
 // A run's shape, origin and column range, staged in shared memory: every
 // thread of a block tests the same runs in the same order.
 struct RunRow {
@@ -160,7 +232,11 @@ struct RunRow {
 };
 constexpr int kRunsPerStage = 512;
 
-__global__ void k_csr_rows(const CsrBuildParams p, int fill)
+// Fill pass: one thread per scoring voxel (row).  Box columns are visited
+// run by run and, within a run, in item order (spots are sorted by beam, so
+// this is column order); the voxel's out-of-box records, sorted by item, are
+// merged in between, so a row's entries come out sorted by column.
+__global__ void k_csr_fill(const CsrBuildParams p)
 {
     __shared__ RunRow runs[kRunsPerStage];
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -171,28 +247,15 @@ __global__ void k_csr_rows(const CsrBuildParams p, int fill)
     const int z = (int)(vv / ((long long)p.sg.n[0] * p.sg.n[1]));
     const double inv_rho = row ? p.inv_rho[vv] : 0.0;
     const float inv_rho_f = (float)inv_rho;
-    long long count = 0;
-    long long pos = (fill && row) ? p.row_ptr[vv] : 0;
+    long long pos = row ? p.row_ptr[vv] : 0;
     const OvfRec* rec = (p.ovf && row) ? p.ovf + p.bucket_off[vv] : nullptr;
     const int nrec = (p.ovf && row) ? p.bucket_len[vv] : 0;
     int j = 0;
-    // keep q / rho unless below the column's threshold, decided by the FP32
-    // screen and, within its margin, in FP64
     auto emit = [&](int it, unsigned long long q) {
-        const float rf = quotient_f32(q, inv_rho_f);
-        const float tf = p.thr_f[it];
-        bool keep;
-        if (rf < tf * (1.0f - kScreen)) keep = false;
-        else if (rf > tf * (1.0f + kScreen)) keep = true;
-        else keep = !((double)q * inv_rho < p.thr[it]);
-        if (!keep) return;
-        if (fill) {
-            p.col[pos] = p.items[it].spot;
-            p.val[pos] = (float)((double)q * inv_rho * p.item_scale[it]);
-            ++pos;
-        } else {
-            ++count;
-        }
+        if (!keep_entry(q, inv_rho, inv_rho_f, p.thr[it], p.thr_f[it])) return;
+        p.col[pos] = p.items[it].spot;
+        p.val[pos] = (float)((double)q * inv_rho * p.item_scale[it]);
+        ++pos;
     };
     for (int r0 = 0; r0 < p.n_runs; r0 += kRunsPerStage) {
         const int nst = min(kRunsPerStage, p.n_runs - r0);
@@ -240,7 +303,6 @@ __global__ void k_csr_rows(const CsrBuildParams p, int fill)
     }
     if (!row) return;
     for (; j < nrec; ++j) emit(rec[j].item - p.item_base, rec[j].q);
-    if (!fill) p.row_count[v] = count;
 }
 
 __global__ void k_ovf_count(const OvfRec* __restrict__ rec, long long n, int n_spots, long long nvox,
@@ -390,11 +452,21 @@ cudaError_t launch_reciprocal(const double* x, long long n, double* out, float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_csr_pass(const CsrBuildParams& p, int fill, cudaStream_t s)
+cudaError_t launch_csr_count(const CsrBuildParams& p, int box_blocks, cudaStream_t s)
+{
+    if (box_blocks > 0) k_csr_count_box<<<box_blocks, kCountBlock, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !p.ovf) return e;
+    const int block = 256;
+    k_csr_count_records<<<(unsigned)((p.nvox + block - 1) / block), block, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_fill(const CsrBuildParams& p, cudaStream_t s)
 {
     const int block = 128;
     const long long grid = (p.nvox + block - 1) / block;
-    k_csr_rows<<<(unsigned)grid, block, 0, s>>>(p, fill);
+    k_csr_fill<<<(unsigned)grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -346,6 +346,7 @@ struct CsrBuildParams {
     const int* run_first;            // per run of items sharing one box: first item index (relative)
     const int* run_count;
     const int* run_box;              // per run: the box shared by its items (shape and origin)
+    const int* run_block0;           // [n_runs + 1]: first block of each run in the count pass (kCountBlock threads)
     int n_runs;
     const OvfRec* ovf;               // out-of-box deposits bucketed by voxel, sorted by item, merged
     const long long* bucket_off;     // per voxel of this scenario: first record
@@ -359,7 +360,12 @@ struct CsrBuildParams {
     int* col;
     float* val;
 };
-cudaError_t launch_csr_pass(const CsrBuildParams& p, int fill, cudaStream_t s);
+constexpr int kCountBlock = 256;      // threads per block of the box-major count pass
+// Row counts (p.row_count, zeroed by the caller) of one scenario: box entries
+// box-major over box_blocks blocks, then the out-of-box records.
+cudaError_t launch_csr_count(const CsrBuildParams& p, int box_blocks, cudaStream_t s);
+// Column indices and values into p.col / p.val at p.row_ptr.
+cudaError_t launch_csr_fill(const CsrBuildParams& p, cudaStream_t s);
 // thr[i] = rel x colmax[i] and its FP32 value, for the row passes' screen.
 cudaError_t launch_column_threshold(const double* colmax, int n, double rel, double* thr, float* thr_f, cudaStream_t s);
 
