@@ -1529,6 +1529,11 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
         }
         IM_TRY(cudaMemcpyAsync(d_beam_meta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice,
                                c->stream));
+        // one slot per box-major thread of every scenario of the wave
+        std::vector<size_t> slot0(ns + 1, 0);
+        for (int k = 0; k < ns; ++k) slot0[k + 1] = slot0[k] + (size_t)count_blocks[k] * kCountBlock;
+        unsigned* d_box_slot = nullptr;
+        IM_TRY(ensure(c->im_box_slot, slot0[ns], &d_box_slot));
         std::vector<CsrBuildParams> cps(ns);
         for (int s = s0; s < s1; ++s) {
             const int first = (s - s0) * n_spots;
@@ -1546,6 +1551,7 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cp.run_count = m + nr;
             cp.run_box = m + 2 * nr;
             cp.run_block0 = m + 3 * nr;
+            cp.box_slot = d_box_slot + slot0[s - s0];
             cp.n_runs = nr;
             cp.ovf = n_ovf ? d_ovf_sorted : nullptr;
             cp.bucket_off = n_ovf ? d_bucket_off + (long long)(s - s0) * c->nvox : nullptr;
@@ -1580,8 +1586,8 @@ vpmc_status vpmc_influence_matrix(vpmc_ctx* c, const vpmc_spot* spots, int n_spo
             cp.row_ptr = reinterpret_cast<const long long*>(csr.row_ptr);
             cp.col = csr.col;
             cp.val = csr.val;
-            IM_TRY(launch_csr_fill(cp, c->stream));
-            ++c->launches;
+            IM_TRY(launch_csr_fill(cp, count_blocks[s - s0], c->stream));
+            c->launches += 2;
         }
         IM_TRY(cudaStreamSynchronize(c->stream));
         s0 = s1;
@@ -1665,7 +1671,7 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->sur.status);
     for (DevBuf* b : {&c->im_colmax, &c->im_item_scale, &c->im_rowcnt, &c->im_nnz, &c->im_scan_tmp, &c->im_meta,
                       &c->im_bucket_off, &c->im_bucket_cur, &c->im_bucket_len, &c->im_ovf_sorted, &c->im_ovf_count,
-                      &c->im_jobs, &c->im_rlim, &c->im_reach, &c->im_thr, &c->im_thr_f})
+                      &c->im_jobs, &c->im_rlim, &c->im_reach, &c->im_thr, &c->im_thr_f, &c->im_box_slot})
         free_buf(*b);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);

@@ -97,7 +97,7 @@ struct vpmc_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // influence-matrix work arrays (kept, grown on demand)
     vpmc::DevBuf im_colmax, im_item_scale, im_rowcnt, im_nnz, im_scan_tmp, im_meta, im_bucket_off, im_bucket_cur,
-        im_bucket_len, im_ovf_sorted, im_ovf_count, im_jobs, im_rlim, im_reach, im_thr, im_thr_f;
+        im_bucket_len, im_ovf_sorted, im_ovf_count, im_jobs, im_rlim, im_reach, im_thr, im_thr_f, im_box_slot;
     // allocator of the influence matrices' CSR buffers (NULL: the library's)
     vpmc_alloc_fn csr_alloc = nullptr;
     void* csr_alloc_user = nullptr;

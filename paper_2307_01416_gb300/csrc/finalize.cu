@@ -203,6 +203,7 @@ __global__ void k_csr_count_box(const CsrBuildParams p)
         }
     }
     if (count) atomicAdd(reinterpret_cast<unsigned long long*>(p.row_count + v), (unsigned long long)count);
+    p.box_slot[blockIdx.x * (long long)blockDim.x + threadIdx.x] = (unsigned)count;
 }
 
 // Count pass of the out-of-box records: one thread per voxel.
@@ -228,15 +229,16 @@ __global__ void k_csr_count_records(const CsrBuildParams p)
 struct RunRow {
     int lo[3], n[3];
     int first, cnt;
-    long long base0;                 // scratch offset of the run's first column box
+    int block0;                      // the run's first block in the box-major passes
 };
 constexpr int kRunsPerStage = 512;
 
-// Fill pass: one thread per scoring voxel (row).  Box columns are visited
-// run by run and, within a run, in item order (spots are sorted by beam, so
-// this is column order); the voxel's out-of-box records, sorted by item, are
-// merged in between, so a row's entries come out sorted by column.
-__global__ void k_csr_fill(const CsrBuildParams p)
+// Fill pass, box-major, first part: one thread per voxel walks the runs in
+// column order.  For each run whose box holds the voxel it turns the
+// (voxel, run) count of the count pass into that segment's first position in
+// the row; the voxel's out-of-box records (sorted by item; their items' boxes
+// do not hold the voxel) are written in between, in column order.
+__global__ void k_csr_offsets(const CsrBuildParams p)
 {
     __shared__ RunRow runs[kRunsPerStage];
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -245,17 +247,20 @@ __global__ void k_csr_fill(const CsrBuildParams p)
     const int x = (int)(vv % p.sg.n[0]);
     const int y = (int)((vv / p.sg.n[0]) % p.sg.n[1]);
     const int z = (int)(vv / ((long long)p.sg.n[0] * p.sg.n[1]));
-    const double inv_rho = row ? p.inv_rho[vv] : 0.0;
-    const float inv_rho_f = (float)inv_rho;
     long long pos = row ? p.row_ptr[vv] : 0;
     const OvfRec* rec = (p.ovf && row) ? p.ovf + p.bucket_off[vv] : nullptr;
     const int nrec = (p.ovf && row) ? p.bucket_len[vv] : 0;
+    const double inv_rho = (row && nrec) ? p.inv_rho[vv] : 0.0;
+    const float inv_rho_f = (float)inv_rho;
     int j = 0;
-    auto emit = [&](int it, unsigned long long q) {
-        if (!keep_entry(q, inv_rho, inv_rho_f, p.thr[it], p.thr_f[it])) return;
-        p.col[pos] = p.items[it].spot;
-        p.val[pos] = (float)((double)q * inv_rho * p.item_scale[it]);
-        ++pos;
+    auto emit_records_before = [&](int item_end) {
+        for (; j < nrec && rec[j].item - p.item_base < item_end; ++j) {
+            const int it = rec[j].item - p.item_base;
+            if (!keep_entry(rec[j].q, inv_rho, inv_rho_f, p.thr[it], p.thr_f[it])) continue;
+            p.col[pos] = p.items[it].spot;
+            p.val[pos] = (float)((double)rec[j].q * inv_rho * p.item_scale[it]);
+            ++pos;
+        }
     };
     for (int r0 = 0; r0 < p.n_runs; r0 += kRunsPerStage) {
         const int nst = min(kRunsPerStage, p.n_runs - r0);
@@ -266,7 +271,7 @@ __global__ void k_csr_fill(const CsrBuildParams p)
             for (int k = 0; k < 3; ++k) { rr.lo[k] = bb.lo[k]; rr.n[k] = bb.n[k]; }
             rr.first = p.run_first[r0 + i];
             rr.cnt = p.run_count[r0 + i];
-            rr.base0 = rr.cnt > 0 ? p.boxes[p.items[rr.first].box].base : 0;
+            rr.block0 = p.run_block0[r0 + i];
             runs[i] = rr;
         }
         __syncthreads();
@@ -277,32 +282,62 @@ __global__ void k_csr_fill(const CsrBuildParams p)
             if (rr.cnt == 0 || (unsigned)lx >= (unsigned)rr.n[0] || (unsigned)ly >= (unsigned)rr.n[1] ||
                 (unsigned)lz >= (unsigned)rr.n[2])
                 continue;
+            emit_records_before(rr.first);
             const long long l = lx + (long long)rr.n[0] * (ly + (long long)rr.n[1] * lz);
-            // the run's columns are consecutive boxes of one shape: item t of
-            // the run at first + t * size; loads go out eight at a time so
-            // that several are in flight (the scratch is streamed once per pass)
-            const int first = rr.first, cnt = rr.cnt;
-            const long long size = (long long)rr.n[0] * rr.n[1] * rr.n[2];
-            const unsigned long long* col0 = p.scratch + rr.base0 + l;
-            for (int t0 = 0; t0 < cnt; t0 += 8) {
-                unsigned long long q[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) q[u] = t0 + u < cnt ? __ldcs(col0 + (long long)(t0 + u) * size) : 0ull;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (t0 + u >= cnt) break;
-                    const int it = first + t0 + u;
-                    while (j < nrec && rec[j].item - p.item_base < it) {
-                        emit(rec[j].item - p.item_base, rec[j].q);
-                        ++j;
-                    }
-                    if (q[u] != 0ull) emit(it, q[u]);
-                }
-            }
+            unsigned* slot = p.box_slot + (long long)rr.block0 * kCountBlock + l;
+            const unsigned c = *slot;
+            *slot = (unsigned)(pos - p.row_ptr[vv]);      // the segment's offset within the row
+            pos += c;
         }
     }
     if (!row) return;
-    for (; j < nrec; ++j) emit(rec[j].item - p.item_base, rec[j].q);
+    emit_records_before(0x7fffffff);
+}
+
+// Fill pass, box-major, second part: one thread per (run, voxel of the run's
+// box), as in the count pass, writes the segment's kept entries from the
+// position the first part left.
+__global__ void k_csr_fill_box(const CsrBuildParams p)
+{
+    __shared__ int s_run;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = p.n_runs;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (p.run_block0[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+        }
+        s_run = lo;
+    }
+    __syncthreads();
+    const int r = s_run;
+    const int cnt = p.run_count[r];
+    if (cnt == 0) return;
+    const DevBox bb = p.boxes[p.run_box[r]];
+    const long long size = (long long)bb.n[0] * bb.n[1] * bb.n[2];
+    const long long l = (long long)(blockIdx.x - p.run_block0[r]) * blockDim.x + threadIdx.x;
+    if (l >= size) return;
+    const int first = p.run_first[r];
+    const int row = (int)(l / bb.n[0]);
+    const int lx = (int)(l - (long long)row * bb.n[0]), ly = row % bb.n[1], lz = row / bb.n[1];
+    const long long v = (bb.lo[0] + lx) + (long long)p.sg.n[0] * ((bb.lo[1] + ly) + (long long)p.sg.n[1] * (bb.lo[2] + lz));
+    long long pos = p.row_ptr[v] + p.box_slot[blockIdx.x * (long long)blockDim.x + threadIdx.x];
+    const double inv_rho = p.inv_rho[v];
+    const float inv_rho_f = (float)inv_rho;
+    const unsigned long long* col0 = p.scratch + p.boxes[p.items[first].box].base + l;
+    for (int t0 = 0; t0 < cnt; t0 += 8) {
+        unsigned long long q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = t0 + u < cnt ? __ldcs(col0 + (long long)(t0 + u) * size) : 0ull;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (q[u] == 0ull) continue;
+            const int it = first + t0 + u;
+            if (!keep_entry(q[u], inv_rho, inv_rho_f, p.thr[it], p.thr_f[it])) continue;
+            p.col[pos] = p.items[it].spot;
+            p.val[pos] = (float)((double)q[u] * inv_rho * p.item_scale[it]);
+            ++pos;
+        }
+    }
 }
 
 __global__ void k_ovf_count(const OvfRec* __restrict__ rec, long long n, int n_spots, long long nvox,
@@ -462,11 +497,14 @@ cudaError_t launch_csr_count(const CsrBuildParams& p, int box_blocks, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_csr_fill(const CsrBuildParams& p, cudaStream_t s)
+cudaError_t launch_csr_fill(const CsrBuildParams& p, int box_blocks, cudaStream_t s)
 {
     const int block = 128;
     const long long grid = (p.nvox + block - 1) / block;
-    k_csr_fill<<<(unsigned)grid, block, 0, s>>>(p);
+    k_csr_offsets<<<(unsigned)grid, block, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || box_blocks <= 0) return e;
+    k_csr_fill_box<<<box_blocks, kCountBlock, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -346,7 +346,8 @@ struct CsrBuildParams {
     const int* run_first;            // per run of items sharing one box: first item index (relative)
     const int* run_count;
     const int* run_box;              // per run: the box shared by its items (shape and origin)
-    const int* run_block0;           // [n_runs + 1]: first block of each run in the count pass (kCountBlock threads)
+    const int* run_block0;           // [n_runs + 1]: first block of each run in the box-major passes (kCountBlock threads)
+    unsigned* box_slot;              // per box-major thread: its (voxel, run) count, then that segment's offset in the row
     int n_runs;
     const OvfRec* ovf;               // out-of-box deposits bucketed by voxel, sorted by item, merged
     const long long* bucket_off;     // per voxel of this scenario: first record
@@ -362,10 +363,13 @@ struct CsrBuildParams {
 };
 constexpr int kCountBlock = 256;      // threads per block of the box-major count pass
 // Row counts (p.row_count, zeroed by the caller) of one scenario: box entries
-// box-major over box_blocks blocks, then the out-of-box records.
+// box-major over box_blocks blocks (each (voxel, run) count kept in
+// p.box_slot), then the out-of-box records.
 cudaError_t launch_csr_count(const CsrBuildParams& p, int box_blocks, cudaStream_t s);
-// Column indices and values into p.col / p.val at p.row_ptr.
-cudaError_t launch_csr_fill(const CsrBuildParams& p, cudaStream_t s);
+// Column indices and values into p.col / p.val at p.row_ptr: the segments'
+// offsets and the out-of-box records per voxel, then the box entries
+// box-major over the same box_blocks blocks.
+cudaError_t launch_csr_fill(const CsrBuildParams& p, int box_blocks, cudaStream_t s);
 // thr[i] = rel x colmax[i] and its FP32 value, for the row passes' screen.
 cudaError_t launch_column_threshold(const double* colmax, int n, double rel, double* thr, float* thr_f, cudaStream_t s);
 
