@@ -73,7 +73,7 @@ __device__ __forceinline__ float quotient_f32(unsigned long long q, float inv_rh
 
 // One block per item: maximum over the item's box of q / rho, as q x (1 / rho)
 // with the same FP64 reciprocal the row pass uses.  The box is contiguous in
-// the scratch, so the block streams it as one array, four coalesced loads in
+// the scratch, so the block streams it as one array, eight coalesced loads in
 // flight per thread; only a non-zero entry (a few per cent) needs its voxel's
 // coordinates and 1 / rho.  Each thread tracks its maximum in FP32 and
 // evaluates in FP64 only the entries within the screen of it: the column's
@@ -84,7 +84,7 @@ __global__ void k_column_max(const unsigned long long* __restrict__ scratch, con
                              const float* __restrict__ inv_rho_f, Grid3 sg, int first_item,
                              double* __restrict__ colmax)
 {
-    constexpr int kU = 4;
+    constexpr int kU = 8;
     const int it = first_item + blockIdx.x;
     const DevBox b = boxes[items[it].box];
     const long long size = (long long)b.n[0] * b.n[1] * b.n[2];
