@@ -373,7 +373,7 @@ vpmc_status vpmc_surrogate_train(vpmc_ctx* ctx, const float* feat_dev, const flo
 
 /* ------------------------------------------------------------------------
  * Robust spot-weight optimisation over the scenarios' influence matrices
- * (Sec. 2.E: robust optimisation over 13 scenarios, judged by the target
+ * (Sec. 2.E: robust optimisation over 13 scenarios, evaluated by the target
  * indices of Table 3).  The paper's optimiser is an in-house trial-and-error
  * procedure; this one minimises the worst case over the scenarios of
  *   f(d) = w_under/|T| sum_T max(0, D_p - d)^2 + w_over/|T| sum_T max(0, d - over_frac D_p)^2
