@@ -440,7 +440,7 @@ vpmc_status enqueue_transport(vpmc_ctx* c, TransportParams p, long long total, c
         CUDA_TRY(launch_devices(p, c->num_sms, t.dev_block, c->stream));
         if (p.surrogate) {
             // brass entries in the surrogate's domain: one network draw each
-            CUDA_TRY(launch_sur_infer(c->sur, p, 2 * c->num_sms, c->stream));
+            CUDA_TRY(launch_sur_infer(c->sur, p, c->num_sms, c->stream));
             c->launches += 1;
         }
         CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
@@ -1793,7 +1793,7 @@ vpmc_status vpmc_surrogate_forward(vpmc_ctx* c, const float* feat_dev, int64_t n
     if ((reinterpret_cast<uintptr_t>(feat_dev) | reinterpret_cast<uintptr_t>(z_dev)) & 15u)
         return fail(VPMC_ERR_ARG, "feat_dev and z_dev must be 16-byte aligned");
     if (!c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights");
-    CUDA_TRY(launch_sur_forward(c->sur, feat_dev, n, z_dev, 2 * c->num_sms, c->stream));
+    CUDA_TRY(launch_sur_forward(c->sur, feat_dev, n, z_dev, c->num_sms, c->stream));
     ++c->launches;
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return surrogate_status(c);
@@ -1949,7 +1949,7 @@ vpmc_status vpmc_surrogate_tracks(vpmc_ctx* c, const int* beam_ids, int n_beams,
         cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream);
         if (e == cudaSuccess && use_surrogate) e = cudaMemsetAsync(c->d_sq_count, 0, sizeof(unsigned long long), c->stream);
         if (e == cudaSuccess) e = launch_devices(p, c->num_sms, block, c->stream);
-        if (e == cudaSuccess && use_surrogate) e = launch_sur_infer(c->sur, p, 2 * c->num_sms, c->stream);
+        if (e == cudaSuccess && use_surrogate) e = launch_sur_infer(c->sur, p, c->num_sms, c->stream);
         if (e != cudaSuccess) return done(fail(VPMC_ERR_CUDA, "track launch: %s", cudaGetErrorString(e)));
         c->launches += use_surrogate ? 2 : 1;
     }

@@ -181,6 +181,42 @@ __device__ __forceinline__ bool complete(uint32_t mbar, uint32_t& phase)
     return all;
 }
 
+// Barrier of one 128-thread warpgroup (named barrier 1 + g): the forward
+// kernels run one tile pipeline per warpgroup, so their steps synchronise
+// the group, not the CTA.
+__device__ __forceinline__ void group_sync(int g)
+{
+    asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "r"(kRows) : "memory");
+}
+
+// The same barrier, returning whether every thread of the group passed ok.
+__device__ __forceinline__ bool group_sync_and(int g, bool ok)
+{
+    uint32_t all;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(all) : "r"(ok ? 1u : 0u), "r"(1 + g), "r"(kRows) : "memory");
+    return all != 0u;
+}
+
+// publish / complete for one warpgroup's tile pipeline.
+__device__ __forceinline__ void publish_group(int g)
+{
+    fence_async_smem();
+    tc_fence_before();
+    group_sync(g);
+}
+
+__device__ __forceinline__ bool complete_group(int g, uint32_t mbar, uint32_t& phase)
+{
+    const bool ok = mbar_wait(mbar, phase);
+    phase ^= 1u;
+    const bool all = group_sync_and(g, ok);
+    tc_fence_after();
+    return all;
+}
+
 __device__ __forceinline__ void copy_to_smem(unsigned char* dst, const unsigned char* src, int bytes)
 {
     const uint4* s = reinterpret_cast<const uint4*>(src);
@@ -250,54 +286,67 @@ __device__ __forceinline__ void output_epilogue(uint32_t t_d3, const float* __re
 // Forward: network outputs of n feature rows, and the same network drawing
 // exit states for the transport's queries.
 // ============================================================================
+// A CTA runs kGroups tile pipelines, one per 128-thread warpgroup, sharing
+// one copy of the weight images: while one group's epilogue runs on the CUDA
+// cores, another group's GEMMs run on the tensor core.  Per group: its input,
+// hidden and staging tiles, its queries and its mbarrier; in tensor memory,
+// 128 columns (D1, then D2 over it once D1 is read, then D3).
+constexpr int kGroups = 3;
+constexpr int kFwdThreads = kGroups * kRows;
 struct FwdSmem {
     static constexpr int W = 0;                                   // W1, W2, W3 images
-    static constexpr int X = kImgW2T;                             // [128 x 16]
+    static constexpr int G0 = kImgW2T;                            // the groups' regions
+    // offsets within a group's region
+    static constexpr int X = 0;                                   // [128 x 16]
     static constexpr int H = X + kRows * kInPad * 2;              // [128 x 128]; also the output staging
     static constexpr int XS = H + kRows * kH * 2;                 // FP32 inputs of a tile, [128 x 6]
     static constexpr int QS = XS + kRows * kIn * 4;               // a tile's queries (inference)
     static constexpr int Bar = QS + kRows * (int)sizeof(SurQuery);
-    static constexpr int Slot = Bar + 8;
+    static constexpr int GBytes = (Bar + 8 + 127) / 128 * 128;
+    static constexpr int Slot = G0 + kGroups * GBytes;
     static constexpr int Bytes = Slot + 8;
 };
-constexpr uint32_t kFwdCols = 256;        // D1 at 0, D2 at 128, D3 at 0
+static_assert(FwdSmem::Bytes <= 232448, "forward CTA exceeds the shared memory of one SM");
+static_assert(FwdSmem::G0 % 128 == 0 && FwdSmem::GBytes % 128 == 0, "operand tiles 128-byte aligned");
+constexpr uint32_t kFwdCols = 512;        // allocation (a power of two); group g uses columns [128 g, 128 g + 128)
 
-// The three GEMMs of one tile whose inputs are in X; returns false when a
-// tensor-core wait failed.  On return the output accumulator holds z - b3.
-__device__ __forceinline__ bool forward_tile(unsigned char* sm, uint32_t tbase, uint32_t t_row, const SurNet& net,
-                                             uint32_t bar, uint32_t& phase, int r)
+// The three GEMMs of one tile whose inputs are in the group's X; returns
+// false when a tensor-core wait failed.  On return the group's accumulator
+// columns hold z - b3.
+__device__ __forceinline__ bool forward_tile(unsigned char* sm, unsigned char* gs, uint32_t tcol, uint32_t t_row,
+                                             const SurNet& net, uint32_t bar, uint32_t& phase, int r, int g)
 {
-    const uint32_t s0 = smem_addr(sm);
+    const uint32_t s0 = smem_addr(sm), gs0 = smem_addr(gs);
     uint32_t mask[4] = {0u, 0u, 0u, 0u};
-    publish();
-    if (threadIdx.x == 0) {
+    publish_group(g);
+    if (r == 0) {
         tc_fence_after();
-        mma_tile(tbase, s0 + FwdSmem::X, s0 + FwdSmem::W + kImgW1, kInPad, kH, false);
+        mma_tile(tcol, gs0 + FwdSmem::X, s0 + FwdSmem::W + kImgW1, kInPad, kH, false);
         umma_commit(bar);
     }
-    if (!complete(bar, phase)) return false;
-    hidden_epilogue<false>(t_row, net.params + ob1, sm + FwdSmem::H, nullptr, r, mask);
-    publish();
-    if (threadIdx.x == 0) {
+    if (!complete_group(g, bar, phase)) return false;
+    hidden_epilogue<false>(t_row, net.params + ob1, gs + FwdSmem::H, nullptr, r, mask);
+    publish_group(g);
+    if (r == 0) {
         tc_fence_after();
-        mma_tile(tbase + 128u, s0 + FwdSmem::H, s0 + FwdSmem::W + kImgW2, kH, kH, false);
+        mma_tile(tcol, gs0 + FwdSmem::H, s0 + FwdSmem::W + kImgW2, kH, kH, false);
         umma_commit(bar);
     }
-    if (!complete(bar, phase)) return false;
-    hidden_epilogue<false>(t_row + 128u, net.params + ob2, sm + FwdSmem::H, nullptr, r, mask);
-    publish();
-    if (threadIdx.x == 0) {
+    if (!complete_group(g, bar, phase)) return false;
+    hidden_epilogue<false>(t_row, net.params + ob2, gs + FwdSmem::H, nullptr, r, mask);
+    publish_group(g);
+    if (r == 0) {
         tc_fence_after();
-        mma_tile(tbase, s0 + FwdSmem::H, s0 + FwdSmem::W + kImgW3, kH, kOutPad, false);
+        mma_tile(tcol, gs0 + FwdSmem::H, s0 + FwdSmem::W + kImgW3, kH, kOutPad, false);
         umma_commit(bar);
     }
-    return complete(bar, phase);
+    return complete_group(g, bar, phase);
 }
 
 __device__ __forceinline__ void fwd_prologue(unsigned char* sm, const SurNet& net, uint32_t& tbase)
 {
     copy_to_smem(sm + FwdSmem::W, net.img, kImgW2T);
-    if (threadIdx.x == 0) mbar_init(smem_addr(sm + FwdSmem::Bar));
+    if (threadIdx.x < kGroups) mbar_init(smem_addr(sm + FwdSmem::G0 + threadIdx.x * FwdSmem::GBytes + FwdSmem::Bar));
     if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_addr(sm + FwdSmem::Slot), kFwdCols);
     tc_fence_before();
     __syncthreads();
@@ -305,14 +354,15 @@ __device__ __forceinline__ void fwd_prologue(unsigned char* sm, const SurNet& ne
     tbase = *reinterpret_cast<volatile uint32_t*>(sm + FwdSmem::Slot);
 }
 
-__device__ __forceinline__ void fwd_epilogue_free(unsigned char* sm, uint32_t tbase, uint32_t phase, bool ok,
-                                                  const SurNet& net)
+__device__ __forceinline__ void fwd_epilogue_free(unsigned char* sm, uint32_t tbase, uint32_t bar, uint32_t phase,
+                                                  bool ok, const SurNet& net)
 {
     if (!ok) {
         // a wait failed: latch the error and give the tensor core a last
-        // bounded chance to finish before its memory is released
-        if (threadIdx.x == 0) atomicOr(net.status, 1);
-        (void)mbar_wait(smem_addr(sm + FwdSmem::Bar), phase);
+        // bounded chance to finish this group's work before the memory is
+        // released
+        if ((threadIdx.x & (kRows - 1)) == 0) atomicOr(net.status, 1);
+        (void)mbar_wait(bar, phase);
     }
     tc_fence_before();
     __syncthreads();
@@ -322,20 +372,23 @@ __device__ __forceinline__ void fwd_epilogue_free(unsigned char* sm, uint32_t tb
     }
 }
 
-__global__ void __launch_bounds__(kRows, 2) k_sur_forward(const SurNet net, const float* __restrict__ x, long long n,
-                                                          float* __restrict__ z)
+__global__ void __launch_bounds__(kFwdThreads, 1) k_sur_forward(const SurNet net, const float* __restrict__ x,
+                                                                 long long n, float* __restrict__ z)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     uint32_t tbase;
     fwd_prologue(sm, net, tbase);
-    const int r = threadIdx.x;
-    const uint32_t t_row = tbase + ((uint32_t)((r >> 5) * 32) << 16);
-    const uint32_t bar = smem_addr(sm + FwdSmem::Bar);
+    const int g = threadIdx.x / kRows, r = threadIdx.x % kRows;
+    unsigned char* gs = sm + FwdSmem::G0 + g * FwdSmem::GBytes;
+    const uint32_t tcol = tbase + (uint32_t)(g * kRows);
+    const uint32_t t_row = tcol + ((uint32_t)((r >> 5) * 32) << 16);
+    const uint32_t bar = smem_addr(gs + FwdSmem::Bar);
     uint32_t phase = 0u;
     bool ok = true;
-    float* xs = reinterpret_cast<float*>(sm + FwdSmem::XS);
-    float* zs = reinterpret_cast<float*>(sm + FwdSmem::H);
-    for (long long tile = blockIdx.x; tile * kRows < n && ok; tile += gridDim.x) {
+    float* xs = reinterpret_cast<float*>(gs + FwdSmem::XS);
+    float* zs = reinterpret_cast<float*>(gs + FwdSmem::H);
+    for (long long tile = (long long)blockIdx.x * kGroups + g; tile * kRows < n && ok;
+         tile += (long long)gridDim.x * kGroups) {
         const long long row0 = tile * kRows;
         const int rows = (int)min((long long)kRows, n - row0);
         // the tile's inputs, rows x 6 contiguous floats: coalesced 16-byte loads
@@ -344,14 +397,14 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_forward(const SurNet net, cons
         const int nx = rows * kIn;
         for (int i = r; i < (nx >> 2); i += kRows) reinterpret_cast<float4*>(xs)[i] = __ldg(xg + i);
         for (int i = (nx & ~3) + r; i < nx; i += kRows) xs[i] = __ldg(x + kIn * row0 + i);
-        __syncthreads();
+        group_sync(g);
         float f[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         if (r < rows) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) f[k] = xs[kIn * r + k];
         }
-        store_input_row(sm + FwdSmem::X, r, f);
-        ok = forward_tile(sm, tbase, t_row, net, bar, phase, r);
+        store_input_row(gs + FwdSmem::X, r, f);
+        ok = forward_tile(sm, gs, tcol, t_row, net, bar, phase, r, g);
         if (!ok) break;
         float zz[kOutPad];
         output_epilogue(t_row, net.params + ob3, zz);
@@ -360,15 +413,15 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_forward(const SurNet net, cons
         // multiple of 16)
 #pragma unroll
         for (int j = 0; j < kOut; ++j) zs[kOut * r + j] = zz[j];
-        __syncthreads();
+        group_sync(g);
         float4* zg = reinterpret_cast<float4*>(z + kOut * row0);
         const int nz = rows * kOut;
         for (int i = r; i < (nz >> 2); i += kRows) zg[i] = reinterpret_cast<const float4*>(zs)[i];
         for (int i = (nz & ~3) + r; i < nz; i += kRows) z[kOut * row0 + i] = zs[i];
         tc_fence_before();
-        __syncthreads();
+        group_sync(g);
     }
-    fwd_epilogue_free(sm, tbase, phase, ok, net);
+    fwd_epilogue_free(sm, tbase, bar, phase, ok, net);
 }
 
 // Draw of one query from the network output z (see the sampler in the oracle):
@@ -407,22 +460,25 @@ __device__ __forceinline__ bool sample_exit(const float (&z)[kOutPad], uint4 ua,
     return trans;
 }
 
-__global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const TransportParams P)
+__global__ void __launch_bounds__(kFwdThreads, 1) k_sur_infer(const SurNet net, const TransportParams P)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     uint32_t tbase;
     fwd_prologue(sm, net, tbase);
-    const int r = threadIdx.x;
+    const int g = threadIdx.x / kRows, r = threadIdx.x % kRows;
     const int lane = r & 31;
-    const uint32_t t_row = tbase + ((uint32_t)((r >> 5) * 32) << 16);
-    const uint32_t bar = smem_addr(sm + FwdSmem::Bar);
+    unsigned char* gs = sm + FwdSmem::G0 + g * FwdSmem::GBytes;
+    const uint32_t tcol = tbase + (uint32_t)(g * kRows);
+    const uint32_t t_row = tcol + ((uint32_t)((r >> 5) * 32) << 16);
+    const uint32_t bar = smem_addr(gs + FwdSmem::Bar);
     uint32_t phase = 0u;
     bool ok = true;
     const long long nq = min((long long)*P.sq_count, P.sq_cap);
     unsigned long long acc_ap = 0ull;
-    SurQuery* qs = reinterpret_cast<SurQuery*>(sm + FwdSmem::QS);
+    SurQuery* qs = reinterpret_cast<SurQuery*>(gs + FwdSmem::QS);
     static_assert(sizeof(SurQuery) % 16 == 0, "query records are copied in 16-byte pieces");
-    for (long long tile = blockIdx.x; tile * kRows < nq && ok; tile += gridDim.x) {
+    for (long long tile = (long long)blockIdx.x * kGroups + g; tile * kRows < nq && ok;
+         tile += (long long)gridDim.x * kGroups) {
         const long long row = tile * kRows + r;
         const int rows = (int)min((long long)kRows, nq - tile * kRows);
         // the tile's query records, contiguous: coalesced 16-byte loads
@@ -432,19 +488,19 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
             const int n16 = rows * (int)(sizeof(SurQuery) / 16);
             for (int i = r; i < n16; i += kRows) dst[i] = src[i];
         }
-        __syncthreads();
+        group_sync(g);
         float f[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         if (r < rows) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) f[k] = qs[r].x[k];
         }
-        store_input_row(sm + FwdSmem::X, r, f);
-        ok = forward_tile(sm, tbase, t_row, net, bar, phase, r);
+        store_input_row(gs + FwdSmem::X, r, f);
+        ok = forward_tile(sm, gs, tcol, t_row, net, bar, phase, r, g);
         if (!ok) break;
         float zz[kOutPad];
         output_epilogue(t_row, net.params + ob3, zz);
         tc_fence_before();
-        __syncthreads();
+        group_sync(g);
 
         bool emit = false;
         PhaseRec rec;
@@ -541,12 +597,12 @@ __global__ void __launch_bounds__(kRows, 2) k_sur_infer(const SurNet net, const 
                 atomicOr(P.status, 2);
             }
         }
-        __syncthreads();                            // qs is refilled by the next tile
+        group_sync(g);                              // qs is refilled by the next tile
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) acc_ap += __shfl_xor_sync(kFull, acc_ap, o);
     if (lane == 0 && acc_ap) atomicAdd(P.stats + kStAp, acc_ap);
-    fwd_epilogue_free(sm, tbase, phase, ok, net);
+    fwd_epilogue_free(sm, tbase, bar, phase, ok, net);
 }
 
 // ============================================================================
@@ -909,7 +965,8 @@ cudaError_t launch_sur_forward(const SurNet& net, const float* x, long long n, f
     }
     if (n <= 0) return cudaSuccess;
     const long long tiles = (n + kRows - 1) / kRows;
-    k_sur_forward<<<(int)std::min<long long>(tiles, grid), kRows, FwdSmem::Bytes, s>>>(net, x, n, z);
+    const long long ctas = (tiles + kGroups - 1) / kGroups;
+    k_sur_forward<<<(int)std::min<long long>(ctas, grid), kFwdThreads, FwdSmem::Bytes, s>>>(net, x, n, z);
     return cudaGetLastError();
 }
 
@@ -921,7 +978,7 @@ cudaError_t launch_sur_infer(const SurNet& net, const TransportParams& p, int gr
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_sur_infer<<<grid, kRows, FwdSmem::Bytes, s>>>(net, p);
+    k_sur_infer<<<grid, kFwdThreads, FwdSmem::Bytes, s>>>(net, p);
     return cudaGetLastError();
 }
 
