@@ -270,6 +270,67 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t t_row, const float* __r
     }
 }
 
+// 16 consecutive FP32 columns of this thread's tensor-memory lane, issued and
+// not waited for: the registers are valid after tmem_wait16 on them.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Wait for this thread's outstanding tensor-memory loads; the registers pass
+// through the wait so that no use of them moves above it.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+// relu(D + b) of 16 columns [c0, c0 + 16) of row r, rounded to BF16 into the
+// K-major [128 x 128] tile dst.
+__device__ __forceinline__ void relu_pack16(const uint32_t (&v)[16], const float* __restrict__ bias, int c0,
+                                            unsigned char* dst, int r)
+{
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+        const float a0 = __uint_as_float(v[j]) + __ldg(bias + c0 + j);
+        const float a1 = __uint_as_float(v[j + 1]) + __ldg(bias + c0 + j + 1);
+        w[j >> 1] = pack_bf16(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
+    }
+    *reinterpret_cast<uint4*>(dst + kmaj(r, c0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(dst + kmaj(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// Hidden-layer epilogue of the forward path (no mask, no transposed copy):
+// the load of the next 16 columns is in flight while the current ones are
+// processed, so one tensor-memory round trip per layer is exposed, not four.
+__device__ __forceinline__ void hidden_epilogue_fwd(uint32_t t_row, const float* __restrict__ bias,
+                                                    unsigned char* dst, int r)
+{
+    uint32_t a[16], b[16];
+    tmem_ld16_async(t_row, a);
+    tmem_wait16(a);
+#pragma unroll
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+        tmem_ld16_async(t_row + (uint32_t)(c0 + 16), b);
+        relu_pack16(a, bias, c0, dst, r);
+        tmem_wait16(b);
+        if (c0 + 32 < kH) tmem_ld16_async(t_row + (uint32_t)(c0 + 32), a);
+        relu_pack16(b, bias, c0 + 16, dst, r);
+        if (c0 + 32 < kH) tmem_wait16(a);
+    }
+}
+
 // z = D3 + b3 for row r (48 columns, 45 used).
 __device__ __forceinline__ void output_epilogue(uint32_t t_d3, const float* __restrict__ b3, float (&z)[kOutPad])
 {
@@ -317,7 +378,6 @@ __device__ __forceinline__ bool forward_tile(unsigned char* sm, unsigned char* g
                                              const SurNet& net, uint32_t bar, uint32_t& phase, int r, int g)
 {
     const uint32_t s0 = smem_addr(sm), gs0 = smem_addr(gs);
-    uint32_t mask[4] = {0u, 0u, 0u, 0u};
     publish_group(g);
     if (r == 0) {
         tc_fence_after();
@@ -325,7 +385,7 @@ __device__ __forceinline__ bool forward_tile(unsigned char* sm, unsigned char* g
         umma_commit(bar);
     }
     if (!complete_group(g, bar, phase)) return false;
-    hidden_epilogue<false>(t_row, net.params + ob1, gs + FwdSmem::H, nullptr, r, mask);
+    hidden_epilogue_fwd(t_row, net.params + ob1, gs + FwdSmem::H, r);
     publish_group(g);
     if (r == 0) {
         tc_fence_after();
@@ -333,7 +393,7 @@ __device__ __forceinline__ bool forward_tile(unsigned char* sm, unsigned char* g
         umma_commit(bar);
     }
     if (!complete_group(g, bar, phase)) return false;
-    hidden_epilogue<false>(t_row, net.params + ob2, gs + FwdSmem::H, nullptr, r, mask);
+    hidden_epilogue_fwd(t_row, net.params + ob2, gs + FwdSmem::H, r);
     publish_group(g);
     if (r == 0) {
         tc_fence_after();
