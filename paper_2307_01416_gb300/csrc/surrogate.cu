@@ -238,38 +238,6 @@ __device__ __forceinline__ void store_input_row(unsigned char* X, int r, const f
     *reinterpret_cast<uint4*>(X + kmaj(r, 8, kInPad)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Hidden-layer epilogue of row r: h = relu(D + b) rounded to BF16 into the
-// K-major [128 x 128] tile dst; optionally the transposed copy (dstT, rows =
-// units, K = tile rows) and the ReLU mask (bit c: D + b > 0).
-template <bool kTransposed>
-__device__ __forceinline__ void hidden_epilogue(uint32_t t_row, const float* __restrict__ bias, unsigned char* dst,
-                                                unsigned char* dstT, int r, uint32_t (&mask)[4])
-{
-#pragma unroll 1
-    for (int c0 = 0; c0 < kH; c0 += 32) {
-        float v[32];
-        tmem_ld32(t_row + (uint32_t)c0, v);
-        uint32_t w[16];
-        uint32_t mbits = 0u;
-#pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-            const float a0 = v[j] + __ldg(bias + c0 + j), a1 = v[j + 1] + __ldg(bias + c0 + j + 1);
-            mbits |= (a0 > 0.0f ? 1u : 0u) << j;
-            mbits |= (a1 > 0.0f ? 1u : 0u) << (j + 1);
-            w[j >> 1] = pack_bf16(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
-            if (kTransposed) {
-                *reinterpret_cast<unsigned short*>(dstT + kmaj(c0 + j, r, kRows)) = (unsigned short)(w[j >> 1] & 0xFFFFu);
-                *reinterpret_cast<unsigned short*>(dstT + kmaj(c0 + j + 1, r, kRows)) = (unsigned short)(w[j >> 1] >> 16);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(dst + kmaj(r, c0 + 8 * q, kH)) =
-                make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-        mask[c0 >> 5] = mbits;
-    }
-}
-
 // 16 consecutive FP32 columns of this thread's tensor-memory lane, issued and
 // not waited for: the registers are valid after tmem_wait16 on them.
 __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16])
@@ -311,24 +279,59 @@ __device__ __forceinline__ void relu_pack16(const uint32_t (&v)[16], const float
     *reinterpret_cast<uint4*>(dst + kmaj(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-// Hidden-layer epilogue of the forward path (no mask, no transposed copy):
-// the load of the next 16 columns is in flight while the current ones are
-// processed, so one tensor-memory round trip per layer is exposed, not four.
-__device__ __forceinline__ void hidden_epilogue_fwd(uint32_t t_row, const float* __restrict__ bias,
-                                                    unsigned char* dst, int r)
+// Calls f(v, c) for the ncols (a multiple of 32) FP32 columns of this
+// thread's tensor-memory lane from t_row, 16 at a time: the load of the next
+// 16 is in flight while f works on the current ones, so one load round trip
+// is exposed per call, not one per chunk.
+template <class F>
+__device__ __forceinline__ void tmem_cols_pipelined(uint32_t t_row, int ncols, F&& f)
 {
     uint32_t a[16], b[16];
     tmem_ld16_async(t_row, a);
     tmem_wait16(a);
 #pragma unroll
-    for (int c0 = 0; c0 < kH; c0 += 32) {
+    for (int c0 = 0; c0 < ncols; c0 += 32) {
         tmem_ld16_async(t_row + (uint32_t)(c0 + 16), b);
-        relu_pack16(a, bias, c0, dst, r);
+        f(a, c0);
         tmem_wait16(b);
-        if (c0 + 32 < kH) tmem_ld16_async(t_row + (uint32_t)(c0 + 32), a);
-        relu_pack16(b, bias, c0 + 16, dst, r);
-        if (c0 + 32 < kH) tmem_wait16(a);
+        if (c0 + 32 < ncols) tmem_ld16_async(t_row + (uint32_t)(c0 + 32), a);
+        f(b, c0 + 16);
+        if (c0 + 32 < ncols) tmem_wait16(a);
     }
+}
+
+// Hidden-layer epilogue of the forward path: relu(D + b) to BF16 into the
+// K-major [128 x 128] tile dst.
+__device__ __forceinline__ void hidden_epilogue_fwd(uint32_t t_row, const float* __restrict__ bias,
+                                                    unsigned char* dst, int r)
+{
+    tmem_cols_pipelined(t_row, kH, [&](const uint32_t (&v)[16], int c0) { relu_pack16(v, bias, c0, dst, r); });
+}
+
+// Hidden-layer epilogue of training: relu(D + b) to BF16 into the K-major
+// tile dst and its transposed copy dstT (rows = units, K = tile rows), and the
+// ReLU mask (bit c of mask[c / 32]: D + b > 0; the caller zeroes mask).
+__device__ __forceinline__ void hidden_epilogue_train(uint32_t t_row, const float* __restrict__ bias,
+                                                      unsigned char* dst, unsigned char* dstT, int r,
+                                                      uint32_t (&mask)[4])
+{
+    tmem_cols_pipelined(t_row, kH, [&](const uint32_t (&v)[16], int c0) {
+        uint32_t w[8];
+        uint32_t mbits = 0u;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+            const float a0 = __uint_as_float(v[j]) + __ldg(bias + c0 + j);
+            const float a1 = __uint_as_float(v[j + 1]) + __ldg(bias + c0 + j + 1);
+            mbits |= (a0 > 0.0f ? 1u : 0u) << j;
+            mbits |= (a1 > 0.0f ? 1u : 0u) << (j + 1);
+            w[j >> 1] = pack_bf16(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
+            *reinterpret_cast<unsigned short*>(dstT + kmaj(c0 + j, r, kRows)) = (unsigned short)(w[j >> 1] & 0xFFFFu);
+            *reinterpret_cast<unsigned short*>(dstT + kmaj(c0 + j + 1, r, kRows)) = (unsigned short)(w[j >> 1] >> 16);
+        }
+        *reinterpret_cast<uint4*>(dst + kmaj(r, c0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(dst + kmaj(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
+        mask[c0 >> 5] |= mbits << (c0 & 31);
+    });
 }
 
 // z = D3 + b3 for row r (48 columns, 45 used).
@@ -805,7 +808,7 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
             umma_commit(bar);
         }
         if (!(ok = complete(bar, phase))) break;
-        hidden_epilogue<true>(t_row, net.params + ob1, sm + TrainSmem::A, sm + TrainSmem::Bt, r, m1);
+        hidden_epilogue_train(t_row, net.params + ob1, sm + TrainSmem::A, sm + TrainSmem::Bt, r, m1);
         // ---- layer 2 ----
         publish();
         if (r == 0) {
@@ -814,7 +817,7 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
             umma_commit(bar);
         }
         if (!(ok = complete(bar, phase))) break;
-        hidden_epilogue<true>(t_row + 128u, net.params + ob2, sm + TrainSmem::A, sm + TrainSmem::C, r, m2);
+        hidden_epilogue_train(t_row + 128u, net.params + ob2, sm + TrainSmem::A, sm + TrainSmem::C, r, m2);
         // ---- output layer ----
         publish();
         if (r == 0) {
@@ -865,27 +868,22 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
         }
         if (!(ok = complete(bar, phase))) break;
         // ---- da2 = dh2 * relu'(a2): K-major into A, transposed into C ----
-#pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 32) {
-            float v[32];
-            tmem_ld32(t_row + (uint32_t)c0, v);
-            uint32_t w[16];
-            const uint32_t mb = m2[c0 >> 5];
+        tmem_cols_pipelined(t_row, kH, [&](const uint32_t (&v)[16], int c0) {
+            const uint32_t mb = m2[c0 >> 5] >> (c0 & 31);
+            uint32_t w[8];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                const float a0 = ((mb >> j) & 1u) ? v[j] : 0.0f;
-                const float a1 = ((mb >> (j + 1)) & 1u) ? v[j + 1] : 0.0f;
+            for (int j = 0; j < 16; j += 2) {
+                const float a0 = ((mb >> j) & 1u) ? __uint_as_float(v[j]) : 0.0f;
+                const float a1 = ((mb >> (j + 1)) & 1u) ? __uint_as_float(v[j + 1]) : 0.0f;
                 w[j >> 1] = pack_bf16(a0, a1);
                 *reinterpret_cast<unsigned short*>(sm + TrainSmem::C + kmaj(c0 + j, r, kRows)) =
                     (unsigned short)(w[j >> 1] & 0xFFFFu);
                 *reinterpret_cast<unsigned short*>(sm + TrainSmem::C + kmaj(c0 + j + 1, r, kRows)) =
                     (unsigned short)(w[j >> 1] >> 16);
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4*>(sm + TrainSmem::A + kmaj(r, c0 + 8 * q, kH)) =
-                    make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-        }
+            *reinterpret_cast<uint4*>(sm + TrainSmem::A + kmaj(r, c0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(sm + TrainSmem::A + kmaj(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
+        });
         // ---- dh1 = da2 W2 and [dW2 | db2] += da2^T [h1 | 1] ----
         publish();
         if (r == 0) {
@@ -896,17 +894,14 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
         }
         if (!(ok = complete(bar, phase))) break;
         // ---- da1 = dh1 * relu'(a1), transposed into C ----
-#pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 32) {
-            float v[32];
-            tmem_ld32(t_row + 128u + (uint32_t)c0, v);
-            const uint32_t mb = m1[c0 >> 5];
+        tmem_cols_pipelined(t_row + 128u, kH, [&](const uint32_t (&v)[16], int c0) {
+            const uint32_t mb = m1[c0 >> 5] >> (c0 & 31);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float a = ((mb >> j) & 1u) ? v[j] : 0.0f;
+            for (int j = 0; j < 16; ++j) {
+                const float a = ((mb >> j) & 1u) ? __uint_as_float(v[j]) : 0.0f;
                 *reinterpret_cast<unsigned short*>(sm + TrainSmem::C + kmaj(c0 + j, r, kRows)) = bf16_bits(a);
             }
-        }
+        });
         // ---- [dW1 | db1] += da1^T [x | 1] ----
         publish();
         if (r == 0) {
