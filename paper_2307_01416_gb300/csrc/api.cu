@@ -1664,6 +1664,7 @@ void vpmc_destroy(vpmc_ctx* c)
     cudaFree(c->d_sq_count);
     cudaFree(c->sur.params);
     cudaFree(c->sur.grad);
+    cudaFree(c->sur.gpart);
     cudaFree(c->sur.m);
     cudaFree(c->sur.v);
     cudaFree(c->sur.img);
@@ -1694,6 +1695,8 @@ vpmc_status ensure_surrogate(vpmc_ctx* c)
     SurNet& n = c->sur;
     CUDA_TRY(dev_alloc(&n.params, sur::kNParams));
     CUDA_TRY(dev_alloc(&n.grad, sur::kNParams));
+    n.n_part_cap = c->num_sms;
+    CUDA_TRY(dev_alloc(&n.gpart, (size_t)n.n_part_cap * sur::kNParams));
     CUDA_TRY(dev_alloc(&n.m, sur::kNParams));
     CUDA_TRY(dev_alloc(&n.v, sur::kNParams));
     CUDA_TRY(dev_alloc(&n.img, sur::kImgBytes));
@@ -1808,9 +1811,11 @@ vpmc_status vpmc_surrogate_gradient(vpmc_ctx* c, const float* feat_dev, const fl
     if (!c->sur_ready) return fail(VPMC_ERR_STATE, "no surrogate weights");
     CUDA_TRY(cudaMemsetAsync(c->sur.grad, 0, sur::kNParams * sizeof(float), c->stream));
     CUDA_TRY(cudaMemsetAsync(c->sur.loss, 0, 2 * sizeof(double), c->stream));
+    int parts = 0;
     CUDA_TRY(launch_sur_train(c->sur, feat_dev, target_dev, label_dev, 0, n, n, (float)(1.0 / (double)n), c->num_sms,
-                              c->stream));
-    ++c->launches;
+                              &parts, c->stream));
+    CUDA_TRY(launch_sur_reduce(c->sur, parts, c->stream));
+    c->launches += 2;
     CUDA_TRY(cudaMemcpyAsync(grad_dev, c->sur.grad, sur::kNParams * sizeof(float), cudaMemcpyDeviceToDevice,
                              c->stream));
     CUDA_TRY(cudaMemsetAsync(c->sur.grad, 0, sur::kNParams * sizeof(float), c->stream));
@@ -1844,12 +1849,13 @@ vpmc_status vpmc_surrogate_train(vpmc_ctx* c, const float* feat_dev, const float
             const long long bj = (a * j + b) % nb;
             const long long first = bj * batch;
             const long long rows = std::min<long long>(batch, n - first);
+            int parts = 0;
             CUDA_TRY(launch_sur_train(c->sur, feat_dev, target_dev, label_dev, first, rows, n,
-                                      (float)(1.0 / (double)rows), c->num_sms, c->stream));
+                                      (float)(1.0 / (double)rows), c->num_sms, &parts, c->stream));
             ++c->sur_step;
             const double cosw = 0.5 * (1.0 + std::cos(3.14159265358979323846 * (double)t / (double)steps));
             const float lr_t = (float)(lr_min + (lr - lr_min) * cosw);
-            CUDA_TRY(launch_sur_adam(c->sur, c->sur_step, lr_t, c->stream));
+            CUDA_TRY(launch_sur_adam(c->sur, c->sur_step, lr_t, parts, c->stream));
             c->launches += 2;
         }
         double h[2] = {0.0, 0.0};

@@ -759,9 +759,11 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
                                                         long long first, long long rows, long long n, float inv_rows)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ float s_db3[kOutPad];              // the CTA's b3 gradient
     const uint32_t s0 = smem_addr(sm);
     const int r = threadIdx.x;
     const int lane = r & 31;
+    if (r < kOutPad) s_db3[r] = 0.0f;
     copy_to_smem(sm + TrainSmem::Img, net.img, kImgBytes);
     zero_smem(sm + TrainSmem::XT, kInPad * kRows * 2);
     zero_smem(sm + TrainSmem::Bt + kmaj(128, 0, kRows), 16 * kRows * 2);
@@ -856,7 +858,7 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
 #pragma unroll 1
         for (int j = 0; j < kOut; ++j) {
             const float s = warp_sum(g[j]);
-            if (lane == 0 && s != 0.0f) atomicAdd(net.grad + ob3 + j, s);
+            if (lane == 0 && s != 0.0f) atomicAdd(s_db3 + j, s);
         }
         // ---- dh2 = dz W3 and dW3^T += h2^T dz ----
         publish();
@@ -915,34 +917,41 @@ __global__ void __launch_bounds__(kRows, 1) k_sur_train(const SurNet net, const 
     // ---- loss and the accumulated weight gradients ----
     const float ls = warp_sum((float)loss_acc);
     if (lane == 0 && ls != 0.0f) atomicAdd(net.loss, (double)ls);
-    if (ok && tiles_done > 0) {
+    // the CTA's partial gradient, every parameter written once (plain stores;
+    // the Adam step sums the CTAs' partials: no contended atomics)
+    float* part = net.gpart + (long long)blockIdx.x * kNParams;
+    const bool have = ok && tiles_done > 0;
+    __syncthreads();                                // s_db3 complete
+    {
         const int h = r;
 #pragma unroll 1
         for (int c0 = 0; c0 < 144; c0 += 16) {
             float v[16];
-            tmem_ld16(t_row + kColW2 + (uint32_t)c0, v);
+            if (have) tmem_ld16(t_row + kColW2 + (uint32_t)c0, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int i = c0 + j;
-                if (i < kH) atomicAdd(net.grad + oW2 + h * kH + i, v[j]);
-                else if (i == kH) atomicAdd(net.grad + ob2 + h, v[j]);
+                const float gv = have ? v[j] : 0.0f;
+                if (i < kH) part[oW2 + h * kH + i] = gv;
+                else if (i == kH) part[ob2 + h] = gv;
             }
         }
 #pragma unroll 1
         for (int c0 = 0; c0 < kOutPad; c0 += 16) {
             float v[16];
-            tmem_ld16(t_row + kColW3T + (uint32_t)c0, v);
+            if (have) tmem_ld16(t_row + kColW3T + (uint32_t)c0, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-                if (c0 + j < kOut) atomicAdd(net.grad + oW3 + (c0 + j) * kH + h, v[j]);
+                if (c0 + j < kOut) part[oW3 + (c0 + j) * kH + h] = have ? v[j] : 0.0f;
         }
         {
             float v[16];
-            tmem_ld16(t_row + kColW1, v);
+            if (have) tmem_ld16(t_row + kColW1, v);
 #pragma unroll
-            for (int j = 0; j < kIn; ++j) atomicAdd(net.grad + oW1 + h * kIn + j, v[j]);
-            atomicAdd(net.grad + ob1 + h, v[kIn]);
+            for (int j = 0; j < kIn; ++j) part[oW1 + h * kIn + j] = have ? v[j] : 0.0f;
+            part[ob1 + h] = have ? v[kIn] : 0.0f;
         }
+        if (r < kOut) part[ob3 + r] = have ? s_db3[r] : 0.0f;
     }
     if (!ok) {
         if (r == 0) atomicOr(net.status, 1);
@@ -984,12 +993,25 @@ __global__ void k_sur_pack(const SurNet net)
 
 // Adam (Kingma & Ba 2015): moments, bias corrections c1 = 1 / (1 - beta1^t),
 // c2 = 1 / (1 - beta2^t); the gradient is cleared for the next step.
-__global__ void k_sur_adam(const SurNet net, float lr, float c1, float c2)
+// Sum of the parts CTAs' partial gradients of parameter k (coalesced over k).
+__device__ __forceinline__ float summed_grad(const SurNet& net, int k, int parts)
+{
+    float g = 0.0f;
+    for (int c = 0; c < parts; ++c) g += net.gpart[(long long)c * kNParams + k];
+    return g;
+}
+
+__global__ void k_sur_reduce(const SurNet net, int parts)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < kNParams) net.grad[k] = summed_grad(net, k, parts);
+}
+
+__global__ void k_sur_adam(const SurNet net, float lr, float c1, float c2, int parts)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= kNParams) return;
-    const float g = net.grad[k];
-    net.grad[k] = 0.0f;
+    const float g = summed_grad(net, k, parts);
     const float m = fmaf(0.9f, net.m[k], 0.1f * g);
     const float v = fmaf(0.999f, net.v[k], 0.001f * g * g);
     net.m[k] = m;
@@ -1038,8 +1060,9 @@ cudaError_t launch_sur_infer(const SurNet& net, const TransportParams& p, int gr
 }
 
 cudaError_t launch_sur_train(const SurNet& net, const float* x, const float* y, const int* label, long long first,
-                             long long rows, long long n, float inv_rows, int grid, cudaStream_t s)
+                             long long rows, long long n, float inv_rows, int grid, int* parts, cudaStream_t s)
 {
+    *parts = 0;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_sur_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TrainSmem::Bytes);
@@ -1048,16 +1071,23 @@ cudaError_t launch_sur_train(const SurNet& net, const float* x, const float* y, 
     }
     const long long tiles = (rows + kRows - 1) / kRows;
     if (tiles <= 0) return cudaSuccess;
-    k_sur_train<<<(int)std::min<long long>(tiles, grid), kRows, TrainSmem::Bytes, s>>>(net, x, y, label, first, rows, n,
-                                                                                   inv_rows);
+    const int ctas = (int)std::min<long long>(tiles, std::min(grid, net.n_part_cap));
+    k_sur_train<<<ctas, kRows, TrainSmem::Bytes, s>>>(net, x, y, label, first, rows, n, inv_rows);
+    *parts = ctas;
     return cudaGetLastError();
 }
 
-cudaError_t launch_sur_adam(const SurNet& net, int step, float lr, cudaStream_t s)
+cudaError_t launch_sur_reduce(const SurNet& net, int parts, cudaStream_t s)
+{
+    k_sur_reduce<<<(kNParams + 255) / 256, 256, 0, s>>>(net, parts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_adam(const SurNet& net, int step, float lr, int parts, cudaStream_t s)
 {
     const float c1 = (float)(1.0 / (1.0 - pow(0.9, step)));
     const float c2 = (float)(1.0 / (1.0 - pow(0.999, step)));
-    k_sur_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(net, lr, c1, c2);
+    k_sur_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(net, lr, c1, c2, parts);
     return cudaGetLastError();
 }
 

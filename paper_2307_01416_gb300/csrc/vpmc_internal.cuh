@@ -285,7 +285,9 @@ int devices_max_block();
 // Learned aperture surrogate (surrogate.cu).
 struct SurNet {
     float* params;                   // FP32 master parameters [kNParams]
-    float* grad;                     // [kNParams]
+    float* grad;                     // [kNParams]: the summed gradient (gradient entry point)
+    float* gpart;                    // [n_part_cap x kNParams]: one partial gradient per CTA of a training launch
+    int n_part_cap;
     float* m;                        // Adam moments
     float* v;
     unsigned char* img;              // BF16 operand images [kImgBytes]
@@ -294,9 +296,14 @@ struct SurNet {
 };
 cudaError_t launch_sur_pack(const SurNet& net, cudaStream_t s);
 cudaError_t launch_sur_forward(const SurNet& net, const float* x, long long n, float* z, int grid, cudaStream_t s);
+// One training launch over rows [first, first + rows); each of its *parts
+// CTAs writes its partial gradient into net.gpart.
 cudaError_t launch_sur_train(const SurNet& net, const float* x, const float* y, const int* label, long long first,
-                             long long rows, long long n, float inv_rows, int grid, cudaStream_t s);
-cudaError_t launch_sur_adam(const SurNet& net, int step, float lr, cudaStream_t s);
+                             long long rows, long long n, float inv_rows, int grid, int* parts, cudaStream_t s);
+// Adam step on the sum of the parts partial gradients.
+cudaError_t launch_sur_adam(const SurNet& net, int step, float lr, int parts, cudaStream_t s);
+// net.grad = the sum of the parts partial gradients.
+cudaError_t launch_sur_reduce(const SurNet& net, int parts, cudaStream_t s);
 cudaError_t launch_sur_infer(const SurNet& net, const TransportParams& p, int grid, cudaStream_t s);
 size_t sur_forward_smem_bytes();
 size_t sur_train_smem_bytes();
