@@ -162,11 +162,14 @@ TRANSPORT_SOURCES = ("transport_common.cuh", "devices.cu", "patient.cu")
 
 
 def transport_source_digest() -> str:
-    """sha256 over the transport kernels' sources, in a fixed order."""
+    """sha256 over the transport kernels' sources and their compile flags, in a
+    fixed order."""
     import hashlib
+    from paper_2307_01416_gb300 import build_ext
     h = hashlib.sha256()
     for name in TRANSPORT_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2307_01416_gb300", "csrc", name), "rb").read())
+        h.update(" ".join(build_ext.NVCC_FLAGS[:5] + build_ext.FILE_FLAGS.get(name, [])).encode())
     return h.hexdigest()
 
 
