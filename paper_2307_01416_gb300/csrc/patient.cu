@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
     uint32_t key1 = 0u;
     float spr_scale = 1.0f;
     DevBox bx;
+    unsigned long long* box_q = nullptr;
     bx.base = 0; bx.lo[0] = bx.lo[1] = bx.lo[2] = 0; bx.n[0] = bx.n[1] = bx.n[2] = 0;
     float wsc = 0.0f;
 
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                         key1 = P.key1_hi ^ (uint32_t)I.spot;
                         spr_scale = scens[I.scen].spr_scale;
                         bx = P.boxes[I.box];
+                        box_q = P.scratch + bx.base;
                         wsc = I.wscale;
                         // ray / grid box entry
                         float tmin = -__int_as_float(0x7f800000), tmax = __int_as_float(0x7f800000);
@@ -158,14 +160,15 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
             __syncwarp();
             if (lane == 0) { s_pool[0] = pool.next; s_pool[1] = pool.end; }
             __syncwarp();
-        }
-        if (!__any_sync(kFull, alive)) {
-            if (__all_sync(kFull, done || alive)) break;
-            continue;
+            // every lane is now alive or done: a warp without a live lane has
+            // finished.  A warp that needed no work has a live lane, since a
+            // history ends only in a step and its lane then needs work
+            if (!__any_sync(kFull, alive)) break;
         }
 
         // ---- one condensed-history step of every live history ----
-        long long dep_key = -1;
+        long long dep_key = -1;                  // voxel of the scratch (dose scoring)
+        unsigned long long* dep_ptr = nullptr;   // its address (influence-matrix scoring)
         unsigned long long dep_q = 0ull;
         if (alive) {
             int fate = -1;
@@ -184,32 +187,35 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                 // step's lateral displacement is confined here, to the voxel
                 // the step ended in, so that the faces are computed once per
                 // step (not again after a crossing); nothing reads the
-                // position in between
+                // position in between.  The first step confines the entry
+                // point to its voxel (a move of a rounding error at most).
+                // The far face's index converts exactly as i + 1 (indices are
+                // far below 2^24).  The position then lies in the voxel, so
+                // each face distance along the direction is >= 0 (or -0)
                 float f0[3], f1[3], g0[3], g1[3];
                 float dc[3], ds[3], s_geom = __int_as_float(0x7f800000);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const bool nested = (kNest >> k) & 1;
-                    f0[k] = P.ctg.lo[k] + (float)L.ic[k] * P.ctg.d[k];
-                    f1[k] = P.ctg.lo[k] + (float)(L.ic[k] + 1) * P.ctg.d[k];
+                    const float fc = (float)L.ic[k];
+                    f0[k] = P.ctg.lo[k] + fc * P.ctg.d[k];
+                    f1[k] = P.ctg.lo[k] + (fc + 1.0f) * P.ctg.d[k];
                     if (!nested) {
-                        g0[k] = P.sg.lo[k] + (float)L.is[k] * P.sg.d[k];
-                        g1[k] = P.sg.lo[k] + (float)(L.is[k] + 1) * P.sg.d[k];
+                        const float fs = (float)L.is[k];
+                        g0[k] = P.sg.lo[k] + fs * P.sg.d[k];
+                        g1[k] = P.sg.lo[k] + (fs + 1.0f) * P.sg.d[k];
                     }
-                    if (L.iters > 1) {
-                        // the previous step's lateral displacement, confined to the current voxel of both grids
-                        const float vlo = nested ? f0[k] : fmaxf(f0[k], g0[k]);
-                        const float vhi = nested ? f1[k] : fminf(f1[k], g1[k]);
-                        L.p[k] = fminf(fmaxf(L.p[k], vlo), vhi);
-                    }
+                    const float vlo = nested ? f0[k] : fmaxf(f0[k], g0[k]);
+                    const float vhi = nested ? f1[k] : fminf(f1[k], g1[k]);
+                    L.p[k] = fminf(fmaxf(L.p[k], vlo), vhi);
                     dc[k] = ds[k] = __int_as_float(0x7f800000);
                     const float Dk = L.d[k];
                     if (Dk != 0.0f) {
                         const float inv = __fdividef(1.0f, Dk);
                         const bool up = Dk > 0.0f;
-                        dc[k] = fmaxf(((up ? f1[k] : f0[k]) - L.p[k]) * inv, 0.0f);
+                        dc[k] = ((up ? f1[k] : f0[k]) - L.p[k]) * inv;
                         if (nested) ds[k] = dc[k];
-                        else ds[k] = fmaxf(((up ? g1[k] : g0[k]) - L.p[k]) * inv, 0.0f);
+                        else ds[k] = ((up ? g1[k] : g0[k]) - L.p[k]) * inv;
                     }
                     s_geom = fminf(s_geom, nested ? dc[k] : fminf(dc[k], ds[k]));
                 }
@@ -226,7 +232,8 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
                 const int lx = sv[0] - bx.lo[0], ly = sv[1] - bx.lo[1], lz = sv[2] - bx.lo[2];
                 if ((unsigned)lx < (unsigned)bx.n[0] && (unsigned)ly < (unsigned)bx.n[1] &&
                     (unsigned)lz < (unsigned)bx.n[2]) {
-                    dep_key = bx.base + (long long)(lx + bx.n[0] * (ly + bx.n[1] * lz));   // box < 2^31 voxels
+                    if (kIM) dep_ptr = box_q + (lx + bx.n[0] * (ly + bx.n[1] * lz));
+                    else dep_key = bx.base + (long long)(lx + bx.n[0] * (ly + bx.n[1] * lz));   // box < 2^31 voxels
                     dep_q = q;
                 } else if (o.dE > 0.0f && P.ovf) {
                     // rare tail outside the item's box: append a record
@@ -251,13 +258,14 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
                             const bool nested = (kNest >> k) & 1;
+                            // (dc and ds are +inf on an axis the direction does not move along)
                             const int sg = d_old[k] > 0.0f ? 1 : -1;
-                            if (d_old[k] != 0.0f && dc[k] == o.s) {
+                            if (dc[k] == o.s) {
                                 L.ic[k] += sg;
                             }
                             out |= (unsigned)L.ic[k] >= (unsigned)P.ctg.n[k];
                             if (!nested) {
-                                if (d_old[k] != 0.0f && ds[k] == o.s) {
+                                if (ds[k] == o.s) {
                                     L.is[k] += sg;
                                 }
                                 out |= (unsigned)L.is[k] >= (unsigned)P.sg.n[k];
@@ -287,7 +295,8 @@ __global__ void __launch_bounds__(kPatientMaxBlock, 1) k_patient(const Transport
             }
         }
         // ---- scoring (all lanes together) ----
-        if (!kIM && P.aggregate) deposit_aggregated(P.scratch, dep_key, dep_q);
+        if (kIM) { if (dep_ptr && dep_q) atomicAdd(dep_ptr, dep_q); }
+        else if (P.aggregate) deposit_aggregated(P.scratch, dep_key, dep_q);
         else if (dep_key >= 0 && dep_q) atomicAdd(P.scratch + dep_key, dep_q);
     }
 }
