@@ -220,7 +220,9 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
 #pragma unroll
     for (int k = 0; k < 3; ++k) L.p[k] = fmaf(s, L.d[k], L.p[k]);
 
-    if (mcs && !o.killed) {
+    // (also on the step that ends the history: the new direction and offset
+    // are then never read, and the step needs no branch around this block)
+    if (mcs) {
         const float x = s * m.rho * m.inv_x0;
         float th0 = 0.0f;
         if (x >= 1e-6f)         // 1 + 0.038 ln x = 1 + (0.038 ln 2) log2 x
