@@ -188,7 +188,10 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
     if (mcs || straggling) r = philox(r, key);
 
     const float R1 = R0 - s * m.kappa;
-    const float Emean = R1 > 0.0f ? energy_of(m.Et, m.inv_dR, R1) : kEcut;
+    // (looked up whatever the sign of R1, the index being clamped, so that the
+    // step selects instead of branching)
+    const float Eint = energy_of(m.Et, m.inv_dR, R1);
+    const float Emean = R1 > 0.0f ? Eint : kEcut;
     float dE = E - Emean;
     const float pc2 = E * (E + 2.0f * kMp);               // (pc)^2
     const float etot = E + kMp;
@@ -224,9 +227,10 @@ __device__ __forceinline__ void ch_step(const Medium& m, float s_geom, LaneT& L,
     // are then never read, and the step needs no branch around this block)
     if (mcs) {
         const float x = s * m.rho * m.inv_x0;
-        float th0 = 0.0f;
-        if (x >= 1e-6f)         // 1 + 0.038 ln x = 1 + (0.038 ln 2) log2 x
-            th0 = __fdividef(13.6f, pc2 * inv_etot) * fast_sqrt(x) * fmaf(0.02633959f, __log2f(x), 1.0f);
+        // 1 + 0.038 ln x = 1 + (0.038 ln 2) log2 x; evaluated for any x and
+        // selected (a NaN or infinity at x ~ 0 is discarded), without a branch
+        const float th0v = __fdividef(13.6f, pc2 * inv_etot) * fast_sqrt(x) * fmaf(0.02633959f, __log2f(x), 1.0f);
+        const float th0 = x >= 1e-6f ? th0v : 0.0f;
         const float2 za = box_muller_fast(u21(r.x >> 11), u21(r.y >> 11));
         const float2 zb = box_muller_fast(u21(r.z >> 11), u21(r.w >> 11));
         const float th1 = za.y * th0, th2 = zb.y * th0;
