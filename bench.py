@@ -73,12 +73,13 @@ def parse_args():
     ap.add_argument("--divergent-sad", type=float, default=2000.0)
     ap.add_argument("--edge-hist", type=int, default=1_000_000, help="histories per beamlet of the edge sweep")
     ap.add_argument("--opt-iterations", type=int, default=50)
-    ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im", "im13", "opt"], default=None,
+    ap.add_argument("--ncu-case", nargs="?", const="dose", choices=["dose", "im", "im13", "opt", "sur"], default=None,
                     help="small fixed-launch transport case for ncu captures (every 10th spot): 'dose' scores one "
                          "grid of the nominal scenario, 'im' its influence-matrix columns, 'im13' the columns of all "
                          "13 scenarios (the set's structure: one beam-line pass, 13 patient copies); 'opt' runs the "
                          "robust optimisation (--opt-iterations per step) over a 13-scenario set of every "
-                         "--opt-stride-th spot")
+                         "--opt-stride-th spot; 'sur' the surrogate network's tensor-core kernels (per step one "
+                         "forward pass over 2^22 rows and one training epoch over 2^20 tracks)")
     ap.add_argument("--opt-stride", type=int, default=1)
     return ap.parse_args()
 
@@ -449,6 +450,36 @@ def _leg(fn, enabled: bool):
         return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
+def run_sur_case(args):
+    """The surrogate network's tcgen05 kernels on 2^20 plain training tracks
+    (8 edge geometries): per step one forward pass over 2^22 rows (the tracks'
+    inputs four times; k_sur_forward) and one training epoch in batches of
+    16,384 (k_sur_train and k_sur_adam per batch), each timed with CUDA
+    events."""
+    import torch
+    from paper_2307_01416_gb300 import vpmc
+    torch.cuda.set_device(0)
+    tr = vpmc.Engine(vpmc.surrogate_training_problem())
+    feat, target, label = tr.surrogate_tracks(list(range(8)), 1 << 17, W.Options(seed=W.SURROGATE_SEED))
+    tr.surrogate_init(7)
+    x = feat.repeat(4, 1).contiguous()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for i in range(args.warmup + args.steps):
+        ev[0].record()
+        tr.surrogate_forward(x)
+        ev[1].record()
+        tr.surrogate_train(feat, target, label, batch=16384, epochs=1, lr=2e-3, lr_min=2e-3)
+        ev[2].record()
+        torch.cuda.synchronize()
+        fwd_ms, train_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        print(json.dumps({"case": "ncu-sur", "iter": i, "forward_rows": int(x.shape[0]), "forward_ms": fwd_ms,
+                          "forward_tflops": x.shape[0] * SUR_FWD_FLOP / (fwd_ms * 1e-3) / 1e12,
+                          "train_rows": int(feat.shape[0]), "train_ms": train_ms,
+                          "train_tflops": feat.shape[0] * SUR_TRAIN_FLOP / (train_ms * 1e-3) / 1e12}))
+    tr.close()
+    return 0
+
+
 def run_ncu_case(args):
     """Every 10th spot of the set's nominal scenario (about 3.3e6 histories,
     full physics) with a fixed launch (k_source_rs 768 threads, k_aperture 512, k_patient 896,
@@ -458,6 +489,8 @@ def run_ncu_case(args):
     scoring path, small enough for an ncu capture."""
     import torch
     from paper_2307_01416_gb300 import vpmc
+    if args.ncu_case == "sur":
+        return run_sur_case(args)
     pb, spots, scens, target = build_workload(False)
     if args.ncu_case == "opt":
         return run_opt_case(args, pb, spots, scens, target)
